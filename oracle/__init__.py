@@ -1,0 +1,177 @@
+"""CPU oracle of the dynamic-volume-line computation -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``dvl_oracle.c`` (a plain,
+sequential C restatement of the paper's Eq. 1-6 and Sec. 3.2) with ctypes and
+numpy; ``brute.py`` holds an independent exact-rational brute force for tiny
+inputs.  The CUDA library never imports, links or calls anything here.
+
+Parity status per function (see the tests that pin each one):
+
+* ``keys``       -- pinned: Morton against recursive Z-order traversal; Hilbert
+                    against bijectivity, unit steps and octree contiguity.
+* ``order``      -- pinned: against numpy's stable argsort.
+* ``update``     -- pinned: exact-rational brute force (``brute.py``), the P = 0
+                    closed form, constant-field closed forms, hand-worked golden
+                    fixtures, and sum/count invariants.
+* ``alpha_grad`` -- pinned: float64 central differences (the loss is quadratic
+                    in the control points once the assignment is fixed).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dvl_oracle.c")
+_HDR = os.path.join(_HERE, "dvl_oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+SFC_MORTON, SFC_HILBERT = 0, 1
+MINIMP_BEFORE_SCALE, MINIMP_AFTER_POWER = 0, 1
+VMAX_APPROX, VMAX_EXACT = 0, 1
+WIDTH_EDGE, WIDTH_VOLUME = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with strict IEEE semantics (no contraction)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
+    return _LIB
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_float), ("min_importance", ctypes.c_float),
+                ("width", ctypes.c_uint32), ("min_imp_mode", ctypes.c_uint32),
+                ("vmax_mode", ctypes.c_uint32), ("width_mode", ctypes.c_uint32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("vmax", ctypes.c_float), ("inv_vmax", ctypes.c_float),
+                ("f_upper", ctypes.c_float), ("Q", ctypes.c_int32), ("i", ctypes.c_int32),
+                ("j", ctypes.c_int32), ("linear", ctypes.c_int32), ("pow_exact", ctypes.c_int32),
+                ("F", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
+        _lib.orc_keys.argtypes = [u64, vp, vp, vp, vp, ctypes.c_int, vp]
+        _lib.orc_order.argtypes = [u64, vp, vp]
+        _lib.orc_update.argtypes = [u64, u32, vp, vp, u32, vp, vp, vp, ctypes.POINTER(Params)] + [vp] * 10 + [ctypes.POINTER(Stats)]
+        _lib.orc_alpha_grad.argtypes = [u64, u32, vp, vp, u32, u32, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp, vp]
+        for f in (_lib.orc_keys, _lib.orc_order, _lib.orc_update, _lib.orc_alpha_grad):
+            f.restype = ctypes.c_int
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def keys(lower: np.ndarray, level: np.ndarray, sfc: int) -> np.ndarray:
+    """u64 space-filling-curve key per cell (Morton or Hilbert of the exact
+    centroid 2*lower + 2^level, 21 bits per axis)."""
+    lower = np.ascontiguousarray(lower, np.int32)
+    level = np.ascontiguousarray(level, np.uint8)
+    n = level.shape[0]
+    out = np.empty(n, np.uint64)
+    rc = _L().orc_keys(n, _p(lower[0]), _p(lower[1]), _p(lower[2]), _p(level), sfc, _p(out))
+    if rc:
+        raise OracleError(f"orc_keys failed: {rc}")
+    return out
+
+
+def order(k: np.ndarray) -> np.ndarray:
+    """Stable permutation sorting the keys (ties keep input order)."""
+    k = np.ascontiguousarray(k, np.uint64)
+    perm = np.empty(k.shape[0], np.uint32)
+    rc = _L().orc_order(k.shape[0], _p(k), _p(perm))
+    if rc:
+        raise OracleError(f"orc_order failed: {rc}")
+    return perm
+
+
+def params(P=1.0, min_importance=0.025, width=1024, min_imp_mode=0, vmax_mode=0, width_mode=0):
+    return Params(P, min_importance, width, min_imp_mode, vmax_mode, width_mode)
+
+
+def update(fields: np.ndarray, level: np.ndarray, alpha: np.ndarray, dom_lo=None, dom_hi=None,
+           per_cell: bool = False, **kw) -> dict:
+    """One DVL update over cells already in curve order.
+
+    ``fields`` (M, N) float32, ``level`` (N,) uint8, ``alpha`` (M, T) float32.
+    ``dom_lo``/``dom_hi`` per field (NaN = data range).  Keyword arguments are
+    :func:`params`.  Returns bins (sum/min/max/mean/mean64/y per field and the
+    shared count), stats, and with ``per_cell`` the widths q and bins b1, b2.
+    """
+    prm = params(**kw)
+    fields = np.ascontiguousarray(fields, np.float32)
+    level = np.ascontiguousarray(level, np.uint8)
+    alpha = np.ascontiguousarray(alpha, np.float32)
+    M, n = fields.shape
+    T = alpha.shape[1]
+    W = prm.width
+    lo = np.full(M, np.nan, np.float32) if dom_lo is None else np.ascontiguousarray(dom_lo, np.float32)
+    hi = np.full(M, np.nan, np.float32) if dom_hi is None else np.ascontiguousarray(dom_hi, np.float32)
+    out = dict(sum=np.empty((M, W), np.float64), min=np.empty((M, W), np.float32),
+               max=np.empty((M, W), np.float32), mean=np.empty((M, W), np.float32),
+               mean64=np.empty((M, W), np.float64), y=np.empty((M, W), np.float32),
+               count=np.empty(W, np.uint32))
+    if per_cell:
+        out.update(q=np.empty(n, np.uint64), b1=np.empty(n, np.uint32), b2=np.empty(n, np.uint32))
+    st = Stats()
+    rc = _L().orc_update(n, M, _p(fields), _p(level), T, _p(alpha), _p(lo), _p(hi), ctypes.byref(prm),
+                         _p(out["sum"]), _p(out["min"]), _p(out["max"]), _p(out["mean"]),
+                         _p(out["mean64"]), _p(out["y"]), _p(out["count"]), _p(out.get("q")),
+                         _p(out.get("b1")), _p(out.get("b2")), ctypes.byref(st))
+    if rc:
+        raise OracleError(f"orc_update failed: {rc}")
+    out["stats"] = st.as_dict()
+    return out
+
+
+def alpha_grad(fields, level, ctrl, target, T=256, dom_lo=None, dom_hi=None, **kw) -> dict:
+    """Loss, per-pixel mean alpha and its gradient w.r.t. the control points."""
+    prm = params(**kw)
+    fields = np.ascontiguousarray(fields, np.float32)
+    level = np.ascontiguousarray(level, np.uint8)
+    ctrl = np.ascontiguousarray(ctrl, np.float32)
+    target = np.ascontiguousarray(target, np.float64)
+    M, n = fields.shape
+    K = ctrl.shape[1]
+    W = prm.width
+    lo = np.full(M, np.nan, np.float32) if dom_lo is None else np.ascontiguousarray(dom_lo, np.float32)
+    hi = np.full(M, np.nan, np.float32) if dom_hi is None else np.ascontiguousarray(dom_hi, np.float32)
+    abar = np.empty((M, W), np.float64)
+    grad = np.empty((M, K), np.float64)
+    loss = np.zeros(1, np.float64)
+    rc = _L().orc_alpha_grad(n, M, _p(fields), _p(level), T, K, _p(ctrl), _p(lo), _p(hi),
+                             ctypes.byref(prm), _p(target), _p(abar), _p(grad), _p(loss))
+    if rc:
+        raise OracleError(f"orc_alpha_grad failed: {rc}")
+    return dict(loss=float(loss[0]), abar=abar, grad=grad)
+
+
+def sorted_inputs(lower, level, fields, sfc):
+    """Keys, permutation and the cells' level/fields gathered into curve order."""
+    k = keys(lower, level, sfc)
+    perm = order(k)
+    return k, perm, np.ascontiguousarray(level[perm]), np.ascontiguousarray(fields[:, perm])

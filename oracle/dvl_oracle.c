@@ -1,0 +1,483 @@
+/*
+ * CPU oracle for the DVL computation -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain sequential restatement of the paper's method (Sec. 2.1, 2.2, 3.1-3.4),
+ * written for a reader checking it against the equations, not for speed.  Only
+ * the tests, the smoke check and the benchmark's CPU-baseline leg use it; the
+ * CUDA library shares no code with it.  Build: gcc -O2 -ffp-contract=off
+ * (no fused multiply-add, no fast-math) so that every float operation below is
+ * one correctly rounded IEEE operation.
+ *
+ * Readings of points the paper leaves open are stated where they are used.
+ */
+#include "dvl_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+
+#define SFC_BITS 21              /* bits per axis of the centroid grid */
+#define MAX_LEVEL 20             /* logical grid up to 2^20 finest cells */
+
+/* ------------------------------------------------------------------------- */
+/* Space-filling-curve keys (Sec. 2.2; cell = lower corner + level, Sec. 2.1) */
+/* ------------------------------------------------------------------------- */
+
+/* Morton (Z-order) code: bit k of axis d becomes key bit 3k+d (x lowest). */
+static uint64_t morton3(const uint32_t c[3])
+{
+    uint64_t key = 0;
+    for (int k = 0; k < SFC_BITS; ++k)
+        for (int d = 0; d < 3; ++d)
+            key |= (uint64_t)((c[d] >> k) & 1u) << (3 * k + d);
+    return key;
+}
+
+/* Hilbert code after J. Skilling, "Programming the Hilbert curve", AIP Conf.
+ * Proc. 707 (2004): the axes are turned into the "transposed" Hilbert index
+ * by undoing, from the coarsest bit plane to the finest, the reflections and
+ * axis exchanges the curve applies below each plane, then Gray-coding across
+ * the axes; the transposed index is read out one bit plane at a time, axis 0
+ * first.  The number of bit planes is fixed (21) so the key of a cell does
+ * not depend on the extent of the data set. */
+static uint64_t hilbert3(const uint32_t c[3])
+{
+    uint32_t X[3] = {c[0], c[1], c[2]};
+    const uint32_t top = 1u << (SFC_BITS - 1);
+    for (uint32_t plane = top; plane > 1; plane >>= 1) {
+        uint32_t below = plane - 1;
+        for (int d = 0; d < 3; ++d) {
+            if (X[d] & plane) {
+                X[0] ^= below;                      /* reflect the lower bits of axis 0 */
+            } else {
+                uint32_t diff = (X[0] ^ X[d]) & below;  /* swap lower bits of axes 0 and d */
+                X[0] ^= diff;
+                X[d] ^= diff;
+            }
+        }
+    }
+    X[1] ^= X[0];                                   /* Gray code across axes */
+    X[2] ^= X[1];
+    uint32_t flip = 0;
+    for (uint32_t plane = top; plane > 1; plane >>= 1)
+        if (X[2] & plane) flip ^= plane - 1;
+    for (int d = 0; d < 3; ++d) X[d] ^= flip;
+    uint64_t key = 0;
+    for (int b = SFC_BITS - 1; b >= 0; --b)
+        for (int d = 0; d < 3; ++d) key = (key << 1) | ((X[d] >> b) & 1u);
+    return key;
+}
+
+int orc_keys(uint64_t n, const int32_t* lx, const int32_t* ly, const int32_t* lz,
+             const uint8_t* level, int sfc, uint64_t* keys)
+{
+    if (sfc != ORC_SFC_MORTON && sfc != ORC_SFC_HILBERT) return -1;
+    for (uint64_t i = 0; i < n; ++i) {
+        int32_t lo[3] = {lx[i], ly[i], lz[i]};
+        if (level[i] > MAX_LEVEL) return -5;
+        int64_t w = (int64_t)1 << level[i];
+        uint32_t c[3];
+        for (int d = 0; d < 3; ++d) {
+            if (lo[d] < 0 || (int64_t)lo[d] + w > ((int64_t)1 << MAX_LEVEL)) return -5;
+            c[d] = (uint32_t)(2 * (int64_t)lo[d] + w);  /* centroid, half-cell units */
+        }
+        keys[i] = sfc == ORC_SFC_MORTON ? morton3(c) : hilbert3(c);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Stable order by key (Sec. 4: computed once, never changes)                */
+/* ------------------------------------------------------------------------- */
+
+typedef struct { uint64_t key; uint32_t idx; } kv;
+
+static int kv_cmp(const void* a, const void* b)
+{
+    const kv* x = (const kv*)a;
+    const kv* y = (const kv*)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);   /* ties keep input order */
+}
+
+int orc_order(uint64_t n, const uint64_t* keys, uint32_t* perm)
+{
+    if (n > 0xFFFFFFFFull) return -1;
+    kv* a = (kv*)malloc(sizeof(kv) * (n ? n : 1));
+    if (!a) return -3;
+    for (uint64_t i = 0; i < n; ++i) { a[i].key = keys[i]; a[i].idx = (uint32_t)i; }
+    qsort(a, n, sizeof(kv), kv_cmp);
+    for (uint64_t i = 0; i < n; ++i) perm[i] = a[i].idx;
+    free(a);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Per-update setup: normalisation, Eq. 5 ranges, Eq. 6 approximation         */
+/* ------------------------------------------------------------------------- */
+
+/* Normalised field value t = clamp((v - lo) * s, 0, 1) with s the float32
+ * reciprocal of (hi - lo) (Sec. 3.3: the field intensity is normalised before
+ * the transfer-function lookup).  s = 0 for an empty or non-finite span. */
+static float norm_scale(float lo, float hi)
+{
+    float span = hi - lo;
+    if (!(span > 0.0f) || !isfinite(span)) return 0.0f;
+    return 1.0f / span;
+}
+
+static float normalise(float v, float lo, float s)
+{
+    float t = (v - lo) * s;
+    if (!(t > 0.0f)) t = 0.0f;                  /* also maps NaN to 0 */
+    if (t > 1.0f) t = 1.0f;
+    return t;
+}
+
+/* Transfer-function entry of a normalised value: nearest-lower bucket of T
+ * equal buckets over [0, 1], the last bucket closed. */
+static uint32_t tf_entry(float t, uint32_t T)
+{
+    float x = t * (float)T;
+    uint32_t a = (uint32_t)floorf(x);
+    return a > T - 1 ? T - 1 : a;
+}
+
+/* x^P for the steepness exponent of Eq. 2/3.  When 2P is an integer in
+ * [0, 16] the power is a fixed sequence of correctly rounded operations
+ * (square root once if 2P is odd, then left-to-right products); 0^0 = 1.
+ * Otherwise powf is used and results are compared with a tolerance. */
+static int pow_is_exact(float P)
+{
+    float n2 = 2.0f * P;
+    return n2 >= 0.0f && n2 <= 16.0f && floorf(n2) == n2;
+}
+
+static float pow_steep(float x, float P)
+{
+    if (!pow_is_exact(P)) return powf(x, P);
+    int n2 = (int)(2.0f * P);
+    if (n2 == 0) return 1.0f;
+    float b;
+    int k;
+    if (n2 & 1) { b = sqrtf(x); k = n2; } else { b = x; k = n2 / 2; }
+    float y = b;
+    for (int i = 1; i < k; ++i) y = y * b;
+    return y;
+}
+
+static float pow2f_int(int e) { return ldexpf(1.0f, e); }
+
+/* Importance of one cell, Eq. 3, with the minimum importance of Eq. 2.
+ *   r = V * (1/maxV)            (float32 reciprocal of max V, Sec. 3.4)
+ *   before-scale mode:  f = (max(r, m) * 2^L)^P
+ *   after-power  mode:  f = max((r * 2^L)^P, m)
+ * The cell-width factor is 2^L (edge) or 8^L (volume, the alternative the
+ * paper mentions in Sec. 3.1). */
+static float importance(float V, float inv_vmax, int level, const orc_params* p)
+{
+    float r = V * inv_vmax;
+    int e = (int)level * (p->width_mode == ORC_WIDTH_VOLUME ? 3 : 1);
+    float f;
+    if (p->min_imp_mode == ORC_MINIMP_BEFORE_SCALE) {
+        if (r < p->min_importance) r = p->min_importance;
+        f = pow_steep(r * pow2f_int(e), p->P);
+    } else {
+        f = pow_steep(r * pow2f_int(e), p->P);
+        if (f < p->min_importance) f = p->min_importance;
+    }
+    return f;
+}
+
+static int bitlen64(uint64_t x)
+{
+    int b = 0;
+    while (x) { ++b; x >>= 1; }
+    return b;
+}
+
+/* ------------------------------------------------------------------------- */
+/* One DVL update                                                            */
+/* ------------------------------------------------------------------------- */
+
+int orc_update(uint64_t n, uint32_t M, const float* fields, const uint8_t* level,
+               uint32_t T, const float* alpha, const float* dom_lo, const float* dom_hi,
+               const orc_params* prm, double* sum, float* vmin, float* vmax, float* mean,
+               double* mean64, float* y, uint32_t* count, uint64_t* q_out, uint32_t* b1_out,
+               uint32_t* b2_out, orc_stats* st)
+{
+    const uint32_t W = prm->width;
+    if (M < 1 || M > 16 || T < 2 || W < 1 || !sum || !vmin || !vmax || !count) return -1;
+    for (uint64_t e = 0; e < (uint64_t)M * T; ++e)
+        if (!(alpha[e] >= 0.0f && alpha[e] <= 1.0f)) return -1;
+
+    /* Transfer-function domain per field: given, or the data range. */
+    float lo[16], s[16], dmin[16], dmax[16];
+    for (uint32_t m = 0; m < M; ++m) {
+        const float* v = fields + (uint64_t)m * n;
+        float a = INFINITY, b = -INFINITY;
+        for (uint64_t c = 0; c < n; ++c) {
+            if (v[c] < a) a = v[c];
+            if (v[c] > b) b = v[c];
+        }
+        if (n == 0) { a = 0.0f; b = 0.0f; }
+        dmin[m] = a;
+        dmax[m] = b;
+        float l = dom_lo[m], h = dom_hi[m];
+        if (isnan(l) && isnan(h)) { l = a; h = b; }
+        lo[m] = l;
+        s[m] = norm_scale(l, h);
+    }
+
+    /* Max local variation.  Approximate mode, Sec. 3.4: the TF entries the
+     * data reaches are [i_m, j_m] per field (entries of the data minimum and
+     * maximum); Eq. 5 takes their union [i, j]; Eq. 6 takes the largest
+     * spread max_m A(m,a) - min_m A(m,a) over a in [i, j].  Entries are
+     * paired across fields by index, exactly as Eq. 6 is written. */
+    int gi = (int)T - 1, gj = 0;
+    for (uint32_t m = 0; m < M; ++m) {
+        int im = (int)tf_entry(normalise(dmin[m], lo[m], s[m]), T);
+        int jm = (int)tf_entry(normalise(dmax[m], lo[m], s[m]), T);
+        if (im < gi) gi = im;
+        if (jm > gj) gj = jm;
+    }
+    if (gi > gj) { gi = 0; gj = 0; }
+    float Vmax = 0.0f;
+    if (prm->vmax_mode == ORC_VMAX_APPROX) {
+        for (int a = gi; a <= gj; ++a) {
+            float hi = alpha[a], lw = alpha[a];
+            for (uint32_t m = 1; m < M; ++m) {
+                float x = alpha[(uint64_t)m * T + a];
+                if (x > hi) hi = x;
+                if (x < lw) lw = x;
+            }
+            if (hi - lw > Vmax) Vmax = hi - lw;
+        }
+    } else {
+        /* Exact mode: max over cells of Eq. 1 (the reduction Sec. 3.4 avoids). */
+        for (uint64_t c = 0; c < n; ++c) {
+            float hi = 0.0f, lw = 1.0f;
+            for (uint32_t m = 0; m < M; ++m) {
+                float al = alpha[(uint64_t)m * T + tf_entry(normalise(fields[(uint64_t)m * n + c], lo[m], s[m]), T)];
+                if (al > hi) hi = al;
+                if (al < lw) lw = al;
+            }
+            if (hi - lw > Vmax) Vmax = hi - lw;
+        }
+    }
+    float inv_vmax = Vmax > 0.0f ? 1.0f / Vmax : 0.0f;
+
+    /* Fixed-point widths.  Every width is f <= f_upper (each operation above is
+     * monotone for non-negative arguments and V <= 1), so with
+     * f_upper <= 2^e and n < 2^nb the widths q = rint(f * 2^Q) with
+     * Q = 62 - nb - e add up to less than 2^62: the prefix sum of Eq. 4 is then
+     * exact integer arithmetic and does not depend on summation order. */
+    int max_level = 0;
+    for (uint64_t c = 0; c < n; ++c)
+        if (level[c] > max_level) max_level = level[c];
+    float f_upper = importance(1.0f, inv_vmax, max_level, prm);
+    if (Vmax == 0.0f) f_upper = importance(0.0f, 0.0f, max_level, prm);
+    if (!isfinite(f_upper)) return -5;
+    int ex = 0;
+    frexpf(f_upper, &ex);                     /* f_upper <= 2^ex */
+    if (!pow_is_exact(prm->P)) ex += 1;       /* powf is not monotone to the ulp */
+    int Q = 62 - bitlen64(n) - ex;
+    if (Q > 120) Q = 120;
+    if (Q < -120) return -5;
+    float scale = pow2f_int(Q);
+
+    uint64_t* q = q_out ? q_out : (uint64_t*)malloc(sizeof(uint64_t) * (n ? n : 1));
+    if (!q) return -3;
+    u128 F = 0;
+    for (uint64_t c = 0; c < n; ++c) {
+        /* Eq. 1: local variation of the per-field alpha (the intensities
+         * I(m,h) come from the alpha transfer function, Sec. 3). */
+        float hi = 0.0f, lw = 1.0f;
+        for (uint32_t m = 0; m < M; ++m) {
+            float t = normalise(fields[(uint64_t)m * n + c], lo[m], s[m]);
+            float al = alpha[(uint64_t)m * T + tf_entry(t, T)];
+            if (al > hi) hi = al;
+            if (al < lw) lw = al;
+        }
+        float V = hi - lw;
+        float f = importance(V, inv_vmax, level[c], prm);   /* Eq. 3 */
+        q[c] = (uint64_t)nearbyintf(f * scale);              /* round half to even */
+        F += q[c];
+    }
+    int linear = 0;
+    if (F == 0 && n > 0) {             /* all widths 0: fall back to equal widths */
+        linear = 1;
+        for (uint64_t c = 0; c < n; ++c) q[c] = 1;
+        F = n;
+    }
+
+    /* Bins (Sec. 3.2): cell c spans [E_c, I_c) with E_c = F(c-1), I_c = F(c)
+     * (Eq. 4), i.e. x in [E_c/F * W, I_c/F * W).  Pixel k covers
+     * [k, k+1) of that axis; the cell adds its value to every pixel its span
+     * touches: b1 = floor(E W / F), b2 = ceil(I W / F) - 1 (a zero-width cell
+     * touches only b1), clamped to W-1.  The cell's value is its normalised
+     * field value t; the per-pixel counter is shared by all fields. */
+    for (uint64_t k = 0; k < (uint64_t)M * W; ++k) { sum[k] = 0.0; vmin[k] = INFINITY; vmax[k] = -INFINITY; }
+    for (uint32_t k = 0; k < W; ++k) count[k] = 0;
+    u128 E = 0;
+    for (uint64_t c = 0; c < n; ++c) {
+        u128 I = E + q[c];
+        u128 b1 = E * W / F;
+        u128 b2 = I > E ? (I * W + F - 1) / F - 1 : b1;
+        if (b1 > W - 1) b1 = W - 1;
+        if (b2 > W - 1) b2 = W - 1;
+        if (b1_out) b1_out[c] = (uint32_t)b1;
+        if (b2_out) b2_out[c] = (uint32_t)b2;
+        for (uint32_t p = (uint32_t)b1; p <= (uint32_t)b2; ++p) {
+            count[p] += 1;
+            for (uint32_t m = 0; m < M; ++m) {
+                float t = normalise(fields[(uint64_t)m * n + c], lo[m], s[m]);
+                uint64_t k = (uint64_t)m * W + p;
+                sum[k] += (double)t;
+                if (t < vmin[k]) vmin[k] = t;
+                if (t > vmax[k]) vmax[k] = t;
+            }
+        }
+        E = I;
+    }
+
+    /* ApplyWeights and ApplyTransFunc (Sec. 3.2, 3.3, 4): mean per pixel, then
+     * the alpha of the mean is the bar height / polyline y.  Empty pixels
+     * (none exist when F > 0) report 0. */
+    for (uint32_t m = 0; m < M; ++m)
+        for (uint32_t p = 0; p < W; ++p) {
+            uint64_t k = (uint64_t)m * W + p;
+            double mu = count[p] ? sum[k] / (double)count[p] : 0.0;
+            float mf = (float)mu;
+            if (mean64) mean64[k] = mu;
+            if (mean) mean[k] = mf;
+            if (y) y[k] = count[p] ? alpha[(uint64_t)m * T + tf_entry(mf, T)] : 0.0f;
+            if (!count[p]) { vmin[k] = 0.0f; vmax[k] = 0.0f; }
+        }
+
+    if (st) {
+        st->vmax = Vmax;
+        st->inv_vmax = inv_vmax;
+        st->f_upper = f_upper;
+        st->Q = Q;
+        st->i = gi;
+        st->j = gj;
+        st->linear = linear;
+        st->pow_exact = pow_is_exact(prm->P);
+        st->F = (uint64_t)F;
+    }
+    if (!q_out) free(q);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Gradient of the per-pixel mean alpha w.r.t. alpha control points          */
+/* ------------------------------------------------------------------------- */
+
+/* Table entry e interpolates the control points linearly at e/(T-1), control
+ * point k sitting at k/(K-1).  Float32 sequence (used for the forward pass
+ * that fixes the bin assignment): x = e(K-1)/(T-1), k0 = floor(x),
+ * w = x - k0, A = c0 + w (c1 - c0). */
+static void ctrl_to_table(uint32_t T, uint32_t K, const float* ctrl, float* table)
+{
+    for (uint32_t e = 0; e < T; ++e) {
+        float x = (float)(e * (K - 1)) / (float)(T - 1);
+        uint32_t k0 = (uint32_t)floorf(x);
+        if (k0 > K - 2) k0 = K - 2;
+        float w = x - (float)k0;
+        float c0 = ctrl[k0], c1 = ctrl[k0 + 1];
+        table[e] = c0 + w * (c1 - c0);
+    }
+}
+
+int orc_alpha_grad(uint64_t n, uint32_t M, const float* fields, const uint8_t* level,
+                   uint32_t T, uint32_t K, const float* ctrl, const float* dom_lo,
+                   const float* dom_hi, const orc_params* prm, const double* target,
+                   double* abar, double* grad, double* loss)
+{
+    const uint32_t W = prm->width;
+    if (K < 2 || M < 1 || M > 16 || T < 2) return -1;
+    float* table = (float*)malloc(sizeof(float) * M * T);
+    double* sum = (double*)malloc(sizeof(double) * M * W);
+    float* vmn = (float*)malloc(sizeof(float) * M * W);
+    float* vmx = (float*)malloc(sizeof(float) * M * W);
+    uint32_t* cnt = (uint32_t*)malloc(sizeof(uint32_t) * W);
+    uint32_t* b1 = (uint32_t*)malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint32_t* b2 = (uint32_t*)malloc(sizeof(uint32_t) * (n ? n : 1));
+    double* gtab = (double*)calloc((size_t)M * T, sizeof(double));
+    int rc = -3;
+    if (!table || !sum || !vmn || !vmx || !cnt || !b1 || !b2 || !gtab) goto done;
+    for (uint64_t k = 0; k < (uint64_t)M * K; ++k)
+        if (!(ctrl[k] >= 0.0f && ctrl[k] <= 1.0f)) { rc = -1; goto done; }
+    /* the interpolated table stays in [0, 1] when the control points do */
+    for (uint32_t m = 0; m < M; ++m) ctrl_to_table(T, K, ctrl + (uint64_t)m * K, table + (uint64_t)m * T);
+    /* forward: fixes the assignment b1..b2 of every cell */
+    rc = orc_update(n, M, fields, level, T, table, dom_lo, dom_hi, prm, sum, vmn, vmx, NULL,
+                    NULL, NULL, cnt, NULL, b1, b2, NULL);
+    if (rc) goto done;
+
+    float lo[16], s[16];
+    for (uint32_t m = 0; m < M; ++m) {
+        const float* v = fields + (uint64_t)m * n;
+        float a = INFINITY, b = -INFINITY;
+        for (uint64_t c = 0; c < n; ++c) { if (v[c] < a) a = v[c]; if (v[c] > b) b = v[c]; }
+        float l = dom_lo[m], h = dom_hi[m];
+        if (isnan(l) && isnan(h)) { l = a; h = b; }
+        lo[m] = l;
+        s[m] = norm_scale(l, h);
+    }
+    /* abar[m][p]: mean over the covering cells of the alpha of the cell's
+     * entry, with the table taken in double from the control points. */
+    for (uint64_t k = 0; k < (uint64_t)M * W; ++k) abar[k] = 0.0;
+    double* tab64 = (double*)malloc(sizeof(double) * M * T);
+    if (!tab64) { rc = -3; goto done; }
+    for (uint32_t m = 0; m < M; ++m)
+        for (uint32_t e = 0; e < T; ++e) {
+            double x = (double)e * (double)(K - 1) / (double)(T - 1);
+            uint32_t k0 = (uint32_t)floor(x);
+            if (k0 > K - 2) k0 = K - 2;
+            double w = x - k0;
+            tab64[(uint64_t)m * T + e] = (1.0 - w) * ctrl[(uint64_t)m * K + k0] + w * ctrl[(uint64_t)m * K + k0 + 1];
+        }
+    for (uint64_t c = 0; c < n; ++c)
+        for (uint32_t p = b1[c]; p <= b2[c]; ++p)
+            for (uint32_t m = 0; m < M; ++m) {
+                uint32_t e = tf_entry(normalise(fields[(uint64_t)m * n + c], lo[m], s[m]), T);
+                abar[(uint64_t)m * W + p] += tab64[(uint64_t)m * T + e];
+            }
+    double L = 0.0;
+    for (uint32_t m = 0; m < M; ++m)
+        for (uint32_t p = 0; p < W; ++p) {
+            uint64_t k = (uint64_t)m * W + p;
+            abar[k] = cnt[p] ? abar[k] / cnt[p] : 0.0;
+            double d = abar[k] - target[k];
+            L += d * d;
+        }
+    /* adjoint: dL/dA_m[e] = sum over covering (cell, pixel) of 2 (abar-target)/count */
+    for (uint64_t c = 0; c < n; ++c)
+        for (uint32_t p = b1[c]; p <= b2[c]; ++p)
+            for (uint32_t m = 0; m < M; ++m) {
+                uint32_t e = tf_entry(normalise(fields[(uint64_t)m * n + c], lo[m], s[m]), T);
+                uint64_t k = (uint64_t)m * W + p;
+                gtab[(uint64_t)m * T + e] += 2.0 * (abar[k] - target[k]) / cnt[p];
+            }
+    /* chain rule through the linear interpolation of the control points */
+    for (uint64_t k = 0; k < (uint64_t)M * K; ++k) grad[k] = 0.0;
+    for (uint32_t m = 0; m < M; ++m)
+        for (uint32_t e = 0; e < T; ++e) {
+            double x = (double)e * (double)(K - 1) / (double)(T - 1);
+            uint32_t k0 = (uint32_t)floor(x);
+            if (k0 > K - 2) k0 = K - 2;
+            double w = x - k0, g = gtab[(uint64_t)m * T + e];
+            grad[(uint64_t)m * K + k0] += (1.0 - w) * g;
+            grad[(uint64_t)m * K + k0 + 1] += w * g;
+        }
+    *loss = L;
+    free(tab64);
+    rc = 0;
+done:
+    free(table); free(sum); free(vmn); free(vmx); free(cnt); free(b1); free(b2); free(gtab);
+    return rc;
+}

@@ -1,0 +1,90 @@
+/*
+ * CPU oracle for the dynamic-volume-line (DVL) computation on multi-field AMR
+ * data (Zellmann, Demirci, Gudukbay, "Visual Analysis of Large Multi-Field AMR
+ * Data on GPUs Using Interactive Volume Lines").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, sequential, deliberately slow
+ * restatement of the paper's definitions, used by the tests, by the smoke check
+ * and by the benchmark's CPU-baseline leg to check and time the CUDA library.
+ * The library never calls it, and the two share no code.
+ *
+ * Precision: integers are exact (u64 keys and widths, unsigned __int128 bin
+ * arithmetic), bin sums are accumulated in double.  The per-cell quantities
+ * that decide an integer (the transfer-function entry index, the fixed-point
+ * width) are computed as a fixed sequence of correctly rounded float32 IEEE
+ * operations, which is the precision the GPU kernels use for those decisions.
+ */
+#ifndef DVL_ORACLE_H
+#define DVL_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_SFC_MORTON = 0, ORC_SFC_HILBERT = 1 };
+enum { ORC_MINIMP_BEFORE_SCALE = 0, ORC_MINIMP_AFTER_POWER = 1 };
+enum { ORC_VMAX_APPROX = 0, ORC_VMAX_EXACT = 1 };
+enum { ORC_WIDTH_EDGE = 0, ORC_WIDTH_VOLUME = 1 };
+
+typedef struct {
+    float P;                 /* steepness exponent of Eq. 2/3 */
+    float min_importance;    /* minimum importance (paper default 0.025) */
+    uint32_t width;          /* plot width W in pixels (number of bins) */
+    uint32_t min_imp_mode;   /* ORC_MINIMP_* */
+    uint32_t vmax_mode;      /* ORC_VMAX_* */
+    uint32_t width_mode;     /* ORC_WIDTH_*: scale by 2^L or by 8^L */
+} orc_params;
+
+typedef struct {
+    float vmax;              /* max V used (Eq. 6 approximation or exact) */
+    float inv_vmax;          /* float32 reciprocal, 0 when vmax == 0 */
+    float f_upper;           /* upper bound of f over all cells */
+    int32_t Q;               /* fixed-point exponent: q = rint(f * 2^Q) */
+    int32_t i, j;            /* global TF index range of Eq. 5 */
+    int32_t linear;          /* 1 when every width was 0 and q := 1 was used */
+    int32_t pow_exact;       /* 1 when 2P is an integer in [0, 16] */
+    uint64_t F;              /* sum of the fixed-point widths (Eq. 4 total) */
+} orc_stats;
+
+/* Space-filling-curve key of every cell (Sec. 2.2: cells are represented by
+ * their centroid on a quantised grid).  c_d = 2*lower_d + 2^level is the
+ * exact centroid in half-finest-cell units, 21 bits per axis. */
+int orc_keys(uint64_t n, const int32_t* lx, const int32_t* ly, const int32_t* lz,
+             const uint8_t* level, int sfc, uint64_t* keys);
+
+/* Stable order of the cells by key (Sec. 4: the order is built once). */
+int orc_order(uint64_t n, const uint64_t* keys, uint32_t* perm);
+
+/* One DVL update over cells that are already in curve order.
+ *   fields:   M arrays of n floats (field-major, fields[m*n + c])
+ *   level:    n refinement levels (0 = finest)
+ *   alpha:    M tables of T alpha entries (alpha[m*T + e]) in [0, 1]
+ *   dom_lo/hi: transfer-function domain per field; NaN/NaN = data range
+ * Outputs (each may be NULL except the bins):
+ *   sum[M*W] (double), vmin/vmax/mean/y[M*W] (float), mean64[M*W], count[W],
+ *   q[n], b1[n], b2[n] per cell, stats.  Returns 0, or a negative code for
+ *   invalid arguments (-1) or a width bound that cannot be represented (-5). */
+int orc_update(uint64_t n, uint32_t M, const float* fields, const uint8_t* level,
+               uint32_t T, const float* alpha, const float* dom_lo, const float* dom_hi,
+               const orc_params* prm, double* sum, float* vmin, float* vmax, float* mean,
+               double* mean64, float* y, uint32_t* count, uint64_t* q, uint32_t* b1,
+               uint32_t* b2, orc_stats* stats);
+
+/* Gradient of L = sum_{m,p} (abar[m][p] - target[m][p])^2 with respect to K
+ * uniformly spaced alpha control points per field, where abar[m][p] is the
+ * mean over the cells covering bin p of the per-cell alpha of field m, and the
+ * table entry e is the linear interpolation of the control points at
+ * e/(T-1).  Bin assignment and entry indices are held fixed at the values
+ * of a forward update with the same inputs.  ctrl[M*K] are the parameters.
+ * Writes abar[M*W] (double), grad[M*K] (double), *loss.  See orc_update for
+ * the other arguments (the alpha table is built from ctrl). */
+int orc_alpha_grad(uint64_t n, uint32_t M, const float* fields, const uint8_t* level,
+                   uint32_t T, uint32_t K, const float* ctrl, const float* dom_lo,
+                   const float* dom_hi, const orc_params* prm, const double* target,
+                   double* abar, double* grad, double* loss);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
