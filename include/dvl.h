@@ -1,0 +1,226 @@
+/*
+ * dvl.h -- C ABI of the B300-native dynamic-volume-line (DVL) library.
+ *
+ * Computes the 1D "interactive volume line" plot of multi-field AMR data
+ * (Zellmann, Demirci, Gudukbay, "Visual Analysis of Large Multi-Field AMR
+ * Data on GPUs Using Interactive Volume Lines"): cells are ordered once along
+ * a space-filling curve, and on every alpha transfer-function (TF) or data
+ * change each cell gets an importance-scaled width, the widths are prefix-
+ * summed, and the cells are reduced into W per-pixel bins (min/max/mean).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a dvl_status (0 = DVL_OK, negative = error); no
+ *     exception, abort or trap crosses this boundary.  dvl_last_error() gives
+ *     a one-line message for the last failing call on a context.
+ *   - Input buffers are copied; the caller keeps ownership.  mem_kind says
+ *     whether a pointer is host memory (DVL_MEM_HOST; pageable or pinned) or
+ *     device memory of the context's GPU (DVL_MEM_DEVICE).
+ *   - The library owns all device memory it allocates (released by
+ *     dvl_destroy).  Output buffers are owned by the caller.
+ *   - GPU work is issued on the context's stream, in call order.  Calls that
+ *     return host-visible results (dvl_read_*, dvl_get_stats, dvl_sync)
+ *     synchronise that stream; dvl_update only enqueues.
+ *   - State machine: CREATED -> LOADED (dvl_load_amr) -> ORDERED
+ *     (dvl_build_order).  dvl_update needs ORDERED and a TF for every field;
+ *     otherwise DVL_ERR_STATE.
+ *   - A context is not thread safe; use one context per host thread.
+ */
+#ifndef DVL_H
+#define DVL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dvl_ctx dvl_ctx; /* opaque, library-owned */
+
+typedef enum {
+    DVL_OK = 0,
+    DVL_ERR_ARG = -1,         /* invalid argument (null, size, enum, value) */
+    DVL_ERR_STATE = -2,       /* call not allowed in the current state */
+    DVL_ERR_NOMEM = -3,       /* device or host allocation failed */
+    DVL_ERR_CUDA = -4,        /* CUDA runtime error (incl. no usable device) */
+    DVL_ERR_RANGE = -5,       /* input outside the supported domain */
+    DVL_ERR_TIMEOUT = -6,     /* a bounded device-side wait gave up */
+    DVL_ERR_UNSUPPORTED = -7  /* valid request this build does not support */
+} dvl_status;
+
+enum { DVL_SFC_MORTON = 0, DVL_SFC_HILBERT = 1 };
+enum { DVL_MEM_HOST = 0, DVL_MEM_DEVICE = 1 };
+enum { DVL_MINIMP_BEFORE_SCALE = 0, DVL_MINIMP_AFTER_POWER = 1 };
+enum { DVL_VMAX_APPROX = 0, DVL_VMAX_EXACT = 1 };
+enum { DVL_WIDTH_EDGE = 0, DVL_WIDTH_VOLUME = 1 };
+
+/* Limits of this build. */
+#define DVL_MAX_FIELDS 8          /* M */
+#define DVL_MAX_TF_ENTRIES 4096   /* T */
+#define DVL_MAX_WIDTH 65536       /* W */
+#define DVL_MAX_LEVEL 20          /* logical grid up to 2^20 finest cells */
+
+/* Parameters of one update (paper Eq. 2/3, Sec. 3.2).
+ *   P               steepness exponent, >= 0.  When 2P is an integer in
+ *                   [0, 16] the widths are bit-exact across CPU and GPU;
+ *                   other values use powf (results then agree to a tolerance).
+ *   min_importance  minimum importance m >= 0 (paper default 0.025).
+ *   width           W, number of pixel bins, 1..DVL_MAX_WIDTH.
+ *   min_imp_mode    DVL_MINIMP_BEFORE_SCALE: f = (max(V/maxV, m) 2^L)^P
+ *                   DVL_MINIMP_AFTER_POWER:  f = max((V/maxV 2^L)^P, m)
+ *   vmax_mode       DVL_VMAX_APPROX: max V from the TF entries the data range
+ *                   reaches (Sec. 3.4, Eq. 5/6); DVL_VMAX_EXACT: max over cells.
+ *   width_mode      DVL_WIDTH_EDGE: scale 2^L; DVL_WIDTH_VOLUME: 8^L (Sec. 3.1). */
+typedef struct {
+    float P;
+    float min_importance;
+    uint32_t width;
+    uint32_t min_imp_mode;
+    uint32_t vmax_mode;
+    uint32_t width_mode;
+} dvl_params;
+
+/* Destination of dvl_read_bins for one field.  Each pointer may be NULL
+ * (skipped); each non-NULL one holds W elements.  mean/min/max are of the
+ * normalised field value t in [0, 1] (Sec. 3.3) over the cells covering the
+ * pixel; y is the TF alpha of the mean (bar height / polyline y, Sec. 3.3);
+ * sum is the float64 sum of t; count is the number of covering cells (the
+ * per-pixel counter of Sec. 3.2, shared by all fields).  Empty pixels
+ * (count 0) report 0 everywhere. */
+typedef struct {
+    float* mean;
+    float* min;
+    float* max;
+    float* y;
+    double* sum;
+    uint32_t* count;
+    int mem_kind;
+} dvl_bins;
+
+/* Per-update scalars, for checking and display. */
+typedef struct {
+    float vmax;          /* max V used in Eq. 3 */
+    float inv_vmax;      /* float32 reciprocal of vmax (0 if vmax == 0) */
+    float f_upper;       /* upper bound of the importance over all cells */
+    int32_t Q;           /* fixed-point exponent: width q = rint(f * 2^Q) */
+    int32_t i, j;        /* global TF entry range of Eq. 5 */
+    int32_t linear;      /* 1 if every width was 0 and equal widths were used */
+    int32_t pow_exact;   /* 1 if 2P is an integer in [0, 16] */
+    uint64_t F;          /* sum of all fixed-point widths (Eq. 4 total) */
+    uint64_t n_cells;
+    uint32_t n_fields;
+    uint32_t max_level;
+} dvl_stats;
+
+/* Creates a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * of that device on which all work is issued, or NULL for a library-owned
+ * non-blocking stream.  Errors: DVL_ERR_ARG (out NULL), DVL_ERR_CUDA (no such
+ * device / no GPU), DVL_ERR_NOMEM. */
+int dvl_create(dvl_ctx** out, int device, void* cuda_stream);
+
+/* Waits for the context's work and releases everything it owns.  NULL is a
+ * no-op. */
+void dvl_destroy(dvl_ctx* ctx);
+
+/* Loads an AMR data set (paper Sec. 2.1: a cell is its lower corner on the
+ * logical grid plus its level, 0 = finest, width 2^level).
+ *   n_cells   N, 0 <= N < 2^32
+ *   lower     3*N int32, structure of arrays: x[0..N), y[0..N), z[0..N);
+ *             each cell must satisfy 0 <= lower and lower + 2^level <= 2^20
+ *   level     N uint8, <= DVL_MAX_LEVEL
+ *   fields    n_fields pointers to N float32 values each (finite)
+ * Replaces any previous data set and clears the order and the TFs.
+ * Errors: DVL_ERR_ARG, DVL_ERR_RANGE (cell outside the grid, level too high,
+ * non-finite value), DVL_ERR_NOMEM, DVL_ERR_CUDA. */
+int dvl_load_amr(dvl_ctx* ctx, uint64_t n_cells, const int32_t* lower, const uint8_t* level,
+                 uint32_t n_fields, const float* const* fields, int mem_kind);
+
+/* Builds the curve order once per data set (paper Sec. 2.2, Sec. 4): a
+ * 63-bit key per cell from its exact centroid 2*lower + 2^level (21 bits per
+ * axis), Morton or Hilbert (Skilling's construction), then a stable radix
+ * sort of the cells by key; fields and levels are gathered into curve order.
+ * Needs LOADED.  Errors: DVL_ERR_ARG (sfc), DVL_ERR_STATE, DVL_ERR_NOMEM,
+ * DVL_ERR_TIMEOUT, DVL_ERR_CUDA. */
+int dvl_build_order(dvl_ctx* ctx, int sfc);
+
+/* Replaces the field values of the loaded cells (a data change), keeping the
+ * cells and their order (re-gathered through the stored permutation).
+ * n_fields must equal the loaded count.  Needs ORDERED. */
+int dvl_set_fields(dvl_ctx* ctx, uint32_t n_fields, const float* const* fields, int mem_kind);
+
+/* Sets the alpha transfer function of one field (paper Sec. 3.3): n_entries
+ * alpha values in [0, 1] over the normalised domain, entry a covering
+ * t in [a/T, (a+1)/T) (the last entry closed).  The field value v maps to
+ * t = clamp((v - domain_lo) / (domain_hi - domain_lo), 0, 1); pass NaN for
+ * both bounds to use the field's data range.  All fields must use the same
+ * n_entries (2..DVL_MAX_TF_ENTRIES).  `alpha` is host memory; it is copied.
+ * Errors: DVL_ERR_ARG (field, size, alpha outside [0,1], lo >= hi),
+ * DVL_ERR_STATE (no data loaded). */
+int dvl_set_tf(dvl_ctx* ctx, uint32_t field, const float* alpha, uint32_t n_entries,
+               float domain_lo, float domain_hi);
+
+/* Enqueues one DVL update (paper Sec. 3-4): per cell and field the TF alpha,
+ * the local variation V (Eq. 1), the importance (Eq. 3), a fixed-point width,
+ * the device-wide prefix sum (Eq. 4), the projection of every cell into the
+ * pixels its span touches with per-pixel sum/min/max/count (Sec. 3.2), and
+ * the per-pixel mean and alpha.  Asynchronous; read results with
+ * dvl_read_bins.  Errors: DVL_ERR_ARG (params), DVL_ERR_STATE, DVL_ERR_NOMEM,
+ * DVL_ERR_CUDA.  Device-side failures (DVL_ERR_RANGE for a width bound that
+ * cannot be represented, DVL_ERR_TIMEOUT) surface at the next synchronising
+ * call. */
+int dvl_update(dvl_ctx* ctx, const dvl_params* params);
+
+/* Copies the bins of one field of the last update into `out` (see dvl_bins).
+ * Synchronises the context's stream for host destinations; device
+ * destinations are copied on the stream and the call then synchronises too,
+ * so device-side errors of the update are reported here. */
+int dvl_read_bins(dvl_ctx* ctx, uint32_t field, const dvl_bins* out);
+
+/* Scalars of the last update (synchronises). */
+int dvl_get_stats(dvl_ctx* ctx, dvl_stats* out);
+
+/* Copies the sorted curve keys (keys[k] = key of the k-th cell in curve
+ * order, N u64) and the permutation (perm[k] = input index of the k-th cell
+ * in curve order, N u32).  Either pointer may be NULL.  Needs ORDERED;
+ * synchronises. */
+int dvl_read_order(dvl_ctx* ctx, uint64_t* keys, uint32_t* perm, int mem_kind);
+
+/* Copies the fixed-point width q of every cell of the last update, in curve
+ * order (N u64).  A checking aid: recomputes the widths with the update's
+ * constants.  Synchronises. */
+int dvl_read_widths(dvl_ctx* ctx, uint64_t* q, int mem_kind);
+
+/* Waits for all enqueued work; returns the first device-side error
+ * (DVL_ERR_TIMEOUT, DVL_ERR_RANGE) raised since the last synchronising call. */
+int dvl_sync(dvl_ctx* ctx);
+
+/* Device time of each stage of the last dvl_update, in milliseconds, from
+ * CUDA events recorded on the context's stream between the kernels (only when
+ * DVL_OPT_TIMING is 1; otherwise DVL_ERR_STATE).  ms[0] = constants and
+ * clearing (plus the exact max-V pass if selected), ms[1] = width pass with the
+ * prefix scan, ms[2] = placement/reduction pass, ms[3] = finalize.  `n` is
+ * the capacity of ms (>= 4).  Synchronises. */
+int dvl_get_timings(dvl_ctx* ctx, double* ms, int n);
+
+/* Tuning and fault-injection options (for tests).
+ *   DVL_OPT_SPIN_LIMIT      iteration limit of every device-side wait
+ *                           (default 1<<22; each iteration sleeps ~100 ns)
+ *   DVL_OPT_FAULT_NO_PUBLISH  1 = the first tile of the next update's prefix
+ *                           scan never publishes its sum, so successors' waits
+ *                           run out (tests DVL_ERR_TIMEOUT); reset after one
+ *                           update.
+ *   DVL_OPT_TIMING          1 = record per-stage CUDA events in dvl_update
+ *                           (read with dvl_get_timings); 0 = off (default). */
+enum { DVL_OPT_SPIN_LIMIT = 1, DVL_OPT_FAULT_NO_PUBLISH = 2, DVL_OPT_TIMING = 3 };
+int dvl_set_option(dvl_ctx* ctx, int option, int64_t value);
+
+/* Static message for a status code. */
+const char* dvl_status_string(int status);
+
+/* Message of the last failing call on ctx (empty if none); never NULL. */
+const char* dvl_last_error(dvl_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DVL_H */

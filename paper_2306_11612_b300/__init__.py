@@ -1,0 +1,273 @@
+"""B300-native dynamic volume lines for multi-field AMR data.
+
+Thin ctypes binding over the C ABI of ``include/dvl.h`` (``lib/libdvl.so``,
+built from ``csrc/`` by ``_build.py``).  This module only marshals arguments:
+every step of the computation runs in the library's CUDA kernels.  It does not
+fall back to anything if the library is missing -- importing it then raises.
+
+Host arrays are numpy arrays (or CPU torch tensors); device arrays are CUDA
+torch tensors on the context's device.  PyTorch provides device memory and the
+stream; it computes nothing here.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from ._build import LIB as _LIB_PATH
+
+__all__ = ["DVL", "DVLError", "lib", "SFC_MORTON", "SFC_HILBERT"]
+
+OK, ERR_ARG, ERR_STATE, ERR_NOMEM, ERR_CUDA, ERR_RANGE, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+SFC_MORTON, SFC_HILBERT = 0, 1
+MEM_HOST, MEM_DEVICE = 0, 1
+MINIMP_BEFORE_SCALE, MINIMP_AFTER_POWER = 0, 1
+VMAX_APPROX, VMAX_EXACT = 0, 1
+WIDTH_EDGE, WIDTH_VOLUME = 0, 1
+OPT_SPIN_LIMIT, OPT_FAULT_NO_PUBLISH, OPT_TIMING = 1, 2, 3
+
+EXPORTS = ["dvl_create", "dvl_destroy", "dvl_load_amr", "dvl_build_order", "dvl_set_fields",
+           "dvl_set_tf", "dvl_update", "dvl_read_bins", "dvl_get_stats", "dvl_read_order",
+           "dvl_read_widths", "dvl_sync", "dvl_set_option", "dvl_get_timings", "dvl_status_string", "dvl_last_error"]
+
+
+class dvl_params(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_float), ("min_importance", ctypes.c_float), ("width", ctypes.c_uint32),
+                ("min_imp_mode", ctypes.c_uint32), ("vmax_mode", ctypes.c_uint32),
+                ("width_mode", ctypes.c_uint32)]
+
+
+class dvl_bins(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_void_p), ("min", ctypes.c_void_p), ("max", ctypes.c_void_p),
+                ("y", ctypes.c_void_p), ("sum", ctypes.c_void_p), ("count", ctypes.c_void_p),
+                ("mem_kind", ctypes.c_int)]
+
+
+class dvl_stats(ctypes.Structure):
+    _fields_ = [("vmax", ctypes.c_float), ("inv_vmax", ctypes.c_float), ("f_upper", ctypes.c_float),
+                ("Q", ctypes.c_int32), ("i", ctypes.c_int32), ("j", ctypes.c_int32),
+                ("linear", ctypes.c_int32), ("pow_exact", ctypes.c_int32), ("F", ctypes.c_uint64),
+                ("n_cells", ctypes.c_uint64), ("n_fields", ctypes.c_uint32), ("max_level", ctypes.c_uint32)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libdvl.so is not built ({_LIB_PATH}); run paper_2306_11612_b300/_build.py")
+    L = ctypes.CDLL(_LIB_PATH)
+    vp, u32, u64, i32, f32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_float
+    sig = {
+        "dvl_create": ([ctypes.POINTER(vp), i32, vp], i32),
+        "dvl_destroy": ([vp], None),
+        "dvl_load_amr": ([vp, u64, vp, vp, u32, vp, i32], i32),
+        "dvl_build_order": ([vp, i32], i32),
+        "dvl_set_fields": ([vp, u32, vp, i32], i32),
+        "dvl_set_tf": ([vp, u32, vp, u32, f32, f32], i32),
+        "dvl_update": ([vp, ctypes.POINTER(dvl_params)], i32),
+        "dvl_read_bins": ([vp, u32, ctypes.POINTER(dvl_bins)], i32),
+        "dvl_get_stats": ([vp, ctypes.POINTER(dvl_stats)], i32),
+        "dvl_read_order": ([vp, vp, vp, i32], i32),
+        "dvl_read_widths": ([vp, vp, i32], i32),
+        "dvl_sync": ([vp], i32),
+        "dvl_set_option": ([vp, i32, ctypes.c_int64], i32),
+        "dvl_get_timings": ([vp, ctypes.POINTER(ctypes.c_double), i32], i32),
+        "dvl_status_string": ([i32], ctypes.c_char_p),
+        "dvl_last_error": ([vp], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    return L
+
+
+lib = _load()
+
+
+class DVLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{lib.dvl_status_string(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr_kind(x):
+    """(pointer, mem_kind, keepalive) of a numpy array or torch tensor."""
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), (MEM_DEVICE if x.is_cuda else MEM_HOST), x
+    a = np.ascontiguousarray(x)
+    return a.ctypes.data, MEM_HOST, a
+
+
+class DVL:
+    """One library context (``dvl_ctx``) on one GPU."""
+
+    def __init__(self, device: int = 0, stream=None):
+        h = ctypes.c_void_p()
+        s = None
+        if stream is not None:
+            s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        rc = lib.dvl_create(ctypes.byref(h), device, s)
+        if rc:
+            raise DVLError(rc, "dvl_create")
+        self._h = h
+        self.device = device
+        self.n = 0
+        self.M = 0
+        self.W = 0
+
+    def _check(self, rc):
+        if rc:
+            raise DVLError(rc, lib.dvl_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.dvl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- once per data set ----
+    def dvl_load_amr(self, lower, level, fields):
+        """lower (3, N) int32, level (N,) uint8, fields (M, N) float32 (all host or all device)."""
+        lp, kind, k1 = _ptr_kind(lower)
+        vp_, kind2, k2 = _ptr_kind(level)
+        M = len(fields)
+        fps = []
+        keep = []
+        for f in fields:
+            p, k, kk = _ptr_kind(f)
+            if k != kind:
+                raise ValueError("all inputs must be in the same memory")
+            fps.append(p)
+            keep.append(kk)
+        if kind2 != kind:
+            raise ValueError("all inputs must be in the same memory")
+        n = int(level.shape[0])
+        arr = (ctypes.c_void_p * M)(*fps)
+        self._check(lib.dvl_load_amr(self._h, n, lp, vp_, M, arr, kind))
+        self.n, self.M = n, M
+
+    load_amr = dvl_load_amr
+
+    def dvl_build_order(self, sfc: int = SFC_HILBERT):
+        self._check(lib.dvl_build_order(self._h, sfc))
+
+    build_order = dvl_build_order
+
+    def dvl_set_fields(self, fields):
+        fps, keep, kind = [], [], None
+        for f in fields:
+            p, k, kk = _ptr_kind(f)
+            kind = k if kind is None else kind
+            fps.append(p)
+            keep.append(kk)
+        arr = (ctypes.c_void_p * len(fps))(*fps)
+        self._check(lib.dvl_set_fields(self._h, len(fps), arr, kind))
+
+    set_fields = dvl_set_fields
+
+    # ---- per edit ----
+    def dvl_set_tf(self, field: int, alpha, lo: float = math.nan, hi: float = math.nan):
+        a = np.ascontiguousarray(alpha, dtype=np.float32)
+        self._check(lib.dvl_set_tf(self._h, field, a.ctypes.data, a.shape[0], lo, hi))
+
+    set_tf = dvl_set_tf
+
+    def set_tfs(self, alphas, lo=None, hi=None):
+        for m in range(len(alphas)):
+            self.set_tf(m, alphas[m], math.nan if lo is None else lo[m], math.nan if hi is None else hi[m])
+
+    def dvl_update(self, P=1.0, min_importance=0.025, width=1024, min_imp_mode=0, vmax_mode=0, width_mode=0):
+        p = dvl_params(P, min_importance, width, min_imp_mode, vmax_mode, width_mode)
+        self._check(lib.dvl_update(self._h, ctypes.byref(p)))
+        self.W = width
+
+    update = dvl_update
+
+    def dvl_read_bins(self, field: int, out: dict | None = None) -> dict:
+        """Bins of one field.  ``out`` may map names (mean, min, max, y, sum,
+        count) to preallocated arrays/tensors (all host or all device); by
+        default fresh numpy arrays are returned."""
+        W = self.W
+        if out is None:
+            out = dict(mean=np.empty(W, np.float32), min=np.empty(W, np.float32), max=np.empty(W, np.float32),
+                       y=np.empty(W, np.float32), sum=np.empty(W, np.float64), count=np.empty(W, np.uint32))
+        b = dvl_bins()
+        kind = None
+        keep = []
+        for name in ("mean", "min", "max", "y", "sum", "count"):
+            if name in out and out[name] is not None:
+                p, k, kk = _ptr_kind(out[name])
+                if kind is not None and k != kind:
+                    raise ValueError("all outputs must be in the same memory")
+                kind = k
+                keep.append(kk)
+                setattr(b, name, p)
+        b.mem_kind = kind if kind is not None else MEM_HOST
+        self._check(lib.dvl_read_bins(self._h, field, ctypes.byref(b)))
+        return out
+
+    read_bins = dvl_read_bins
+
+    def dvl_get_stats(self) -> dict:
+        s = dvl_stats()
+        self._check(lib.dvl_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    get_stats = dvl_get_stats
+
+    def dvl_read_order(self):
+        keys = np.empty(self.n, np.uint64)
+        perm = np.empty(self.n, np.uint32)
+        self._check(lib.dvl_read_order(self._h, keys.ctypes.data, perm.ctypes.data, MEM_HOST))
+        return keys, perm
+
+    read_order = dvl_read_order
+
+    def dvl_read_widths(self):
+        q = np.empty(self.n, np.uint64)
+        self._check(lib.dvl_read_widths(self._h, q.ctypes.data, MEM_HOST))
+        return q
+
+    read_widths = dvl_read_widths
+
+    def dvl_sync(self):
+        self._check(lib.dvl_sync(self._h))
+
+    sync = dvl_sync
+
+    def dvl_set_option(self, option: int, value: int):
+        self._check(lib.dvl_set_option(self._h, option, value))
+
+    set_option = dvl_set_option
+
+    def dvl_get_timings(self):
+        """Per-stage device ms of the last update (needs OPT_TIMING=1):
+        prepare, width pass + scan, placement pass, finalize."""
+        ms = (ctypes.c_double * 4)()
+        self._check(lib.dvl_get_timings(self._h, ms, 4))
+        return list(ms)
+
+    get_timings = dvl_get_timings
+
+    @property
+    def handle(self):
+        return self._h

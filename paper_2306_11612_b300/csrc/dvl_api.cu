@@ -1,0 +1,641 @@
+// Host side of the C ABI declared in include/dvl.h: context and state
+// machine, argument validation, device memory, copies, and the ordering of
+// kernel launches on the context's stream.  All compute runs in the kernels
+// of sfc_sort.cu and update.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dvl_internal.h"
+
+using namespace dvl;
+
+struct dvl_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int state = 0;                    // 0 created, 1 loaded, 2 ordered
+    std::string last_error;
+
+    uint64_t n = 0;
+    uint32_t M = 0;
+    size_t pitch = 0;                 // elements per field / level row (padded)
+
+    // unsorted inputs
+    int32_t* d_lower = nullptr;       // 3 x pitch
+    uint8_t* d_level_in = nullptr;    // pitch
+    float* d_fin = nullptr;           // M x pitch
+    // curve order
+    float* d_val = nullptr;           // M x pitch
+    uint8_t* d_lev = nullptr;         // pitch
+    uint32_t* d_perm = nullptr;       // n
+    unsigned long long* d_keys = nullptr;   // n (sorted)
+    // sort scratch
+    unsigned long long* d_keys_alt = nullptr;
+    uint32_t* d_vals_alt = nullptr;
+    uint32_t* d_hist = nullptr;       // 8 x 256
+    unsigned long long* d_rs_status = nullptr;
+    uint32_t* d_rs_counters = nullptr;   // 8
+    uint32_t epoch = 0;
+    // metadata / errors
+    DataMeta* d_meta = nullptr;
+    uint32_t* d_err = nullptr;
+    // transfer functions
+    uint32_t T = 0;
+    std::vector<float> h_tf, h_dom;
+    std::vector<char> tf_set;
+    bool tf_dirty = false;
+    float* d_tf = nullptr;
+    float* d_dom = nullptr;
+    size_t tf_cap = 0;
+    // update scratch
+    UpdateConsts* d_consts = nullptr;
+    unsigned long long* d_tile_status = nullptr;
+    unsigned long long* d_chunk_prefix = nullptr;
+    uint32_t* d_counters = nullptr;
+    // bins
+    uint32_t W_cap = 0, W_last = 0;
+    bool have_update = false;
+    double* d_sum = nullptr;
+    uint32_t *d_vmin = nullptr, *d_vmax = nullptr, *d_count = nullptr;
+    float *d_mean = nullptr, *d_y = nullptr;
+    dvl_params last_prm{};
+    // options
+    int64_t spin_limit = 1 << 22;
+    int fault_no_publish = 0;
+    int timing = 0;
+    bool timed_last = false;
+    cudaEvent_t ev[5] = {};
+};
+
+namespace {
+
+int fail(dvl_ctx* c, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(dvl_ctx* c, int code, const char* fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->last_error = buf;
+    }
+    return code;
+}
+
+int cuda_fail(dvl_ctx* c, cudaError_t e, const char* what)
+{
+    cudaGetLastError();   // clear a sticky-free error so later calls can proceed
+    return fail(c, e == cudaErrorMemoryAllocation ? DVL_ERR_NOMEM : DVL_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+template <typename T>
+void dfree(T*& p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+template <typename T>
+cudaError_t dalloc(T*& p, size_t count)
+{
+    dfree(p);
+    if (!count) count = 1;
+    return cudaMalloc(reinterpret_cast<void**>(&p), count * sizeof(T));
+}
+
+size_t pad_to(uint64_t n, size_t q) { return (size_t)((n + q - 1) / q * q); }
+
+void free_dataset(dvl_ctx* c)
+{
+    dfree(c->d_lower); dfree(c->d_level_in); dfree(c->d_fin);
+    dfree(c->d_val); dfree(c->d_lev); dfree(c->d_perm); dfree(c->d_keys);
+    dfree(c->d_keys_alt); dfree(c->d_vals_alt); dfree(c->d_rs_status);
+    dfree(c->d_tile_status); dfree(c->d_chunk_prefix);
+    c->state = 0;
+    c->have_update = false;
+}
+
+// Maps and clears the device error word.
+int take_device_error(dvl_ctx* c)
+{
+    uint32_t e = 0;
+    CK(cudaMemcpyAsync(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost, c->stream), "read error word");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    if (!e) return DVL_OK;
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), c->stream), "clear error word");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    if (e & ERR_TIMEOUT) return fail(c, DVL_ERR_TIMEOUT, "a device-side wait exceeded its limit");
+    if (e & ERR_LEVEL) return fail(c, DVL_ERR_RANGE, "a cell level exceeds %d", DVL_MAX_LEVEL);
+    if (e & ERR_COORD) return fail(c, DVL_ERR_RANGE, "a cell lies outside the 2^20 logical grid");
+    if (e & ERR_NONFINITE) return fail(c, DVL_ERR_RANGE, "a field value is not finite");
+    if (e & ERR_RANGE) return fail(c, DVL_ERR_RANGE, "the importance bound is not representable");
+    return fail(c, DVL_ERR_CUDA, "unknown device error 0x%x", e);
+}
+
+cudaMemcpyKind kind_in(int mem_kind) { return mem_kind == DVL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+cudaMemcpyKind kind_out(int mem_kind) { return mem_kind == DVL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+int upload_fields(dvl_ctx* c, const float* const* fields, int mem_kind)
+{
+    for (uint32_t m = 0; m < c->M; ++m) {
+        if (!fields[m] && c->n) return fail(c, DVL_ERR_ARG, "field %u is NULL", m);
+        if (c->n)
+            CK(cudaMemcpyAsync(c->d_fin + m * c->pitch, fields[m], c->n * sizeof(float), kind_in(mem_kind),
+                               c->stream), "copy field");
+    }
+    return DVL_OK;
+}
+
+int compute_ranges(dvl_ctx* c)
+{
+    // reset the per-field min/max words (dmin, dmax lead DataMeta), then reduce
+    uint32_t init[2 * DVL_MAX_FIELDS];
+    for (int m = 0; m < DVL_MAX_FIELDS; ++m) { init[m] = 0xFFFFFFFFu; init[DVL_MAX_FIELDS + m] = 0u; }
+    CK(cudaMemcpyAsync(c->d_meta, init, sizeof init, cudaMemcpyHostToDevice, c->stream), "write meta");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    launch_field_ranges(c->stream, c->n, c->M, c->d_fin, c->pitch, c->d_meta, c->d_err);
+    CK(cudaGetLastError(), "field range kernel");
+    return DVL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dvl_status_string(int s)
+{
+    switch (s) {
+        case DVL_OK: return "ok";
+        case DVL_ERR_ARG: return "invalid argument";
+        case DVL_ERR_STATE: return "call not allowed in the current state";
+        case DVL_ERR_NOMEM: return "out of memory";
+        case DVL_ERR_CUDA: return "CUDA error";
+        case DVL_ERR_RANGE: return "input outside the supported domain";
+        case DVL_ERR_TIMEOUT: return "device-side wait timed out";
+        case DVL_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+const char* dvl_last_error(dvl_ctx* c) { return c ? c->last_error.c_str() : ""; }
+
+int dvl_create(dvl_ctx** out, int device, void* cuda_stream)
+{
+    if (!out) return DVL_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return DVL_ERR_CUDA;
+    }
+    if (device < 0 || device >= count) return DVL_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return DVL_ERR_CUDA;
+    dvl_ctx* c = new (std::nothrow) dvl_ctx;
+    if (!c) return DVL_ERR_NOMEM;
+    c->device = device;
+    if (cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return DVL_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = dalloc(c->d_meta, 1);
+    if (e == cudaSuccess) e = dalloc(c->d_err, 1);
+    if (e == cudaSuccess) e = dalloc(c->d_consts, 1);
+    if (e == cudaSuccess) e = dalloc(c->d_counters, 4);
+    if (e == cudaSuccess) e = dalloc(c->d_hist, 8 * RS_RADIX);
+    if (e == cudaSuccess) e = dalloc(c->d_rs_counters, 8);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_consts, 0, sizeof(UpdateConsts), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        dvl_destroy(c);
+        return e == cudaErrorMemoryAllocation ? DVL_ERR_NOMEM : DVL_ERR_CUDA;
+    }
+    *out = c;
+    return DVL_OK;
+}
+
+void dvl_destroy(dvl_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_dataset(c);
+    dfree(c->d_meta); dfree(c->d_err); dfree(c->d_consts); dfree(c->d_counters);
+    dfree(c->d_hist); dfree(c->d_rs_counters); dfree(c->d_tf); dfree(c->d_dom);
+    dfree(c->d_sum); dfree(c->d_vmin); dfree(c->d_vmax); dfree(c->d_count);
+    dfree(c->d_mean); dfree(c->d_y);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int dvl_set_option(dvl_ctx* c, int option, int64_t value)
+{
+    if (!c) return DVL_ERR_ARG;
+    switch (option) {
+        case DVL_OPT_SPIN_LIMIT:
+            if (value < 1) return fail(c, DVL_ERR_ARG, "spin limit must be >= 1");
+            c->spin_limit = value;
+            return DVL_OK;
+        case DVL_OPT_FAULT_NO_PUBLISH:
+            c->fault_no_publish = value ? 1 : 0;
+            return DVL_OK;
+        case DVL_OPT_TIMING:
+            c->timing = value ? 1 : 0;
+            if (c->timing && !c->ev[0]) {
+                cudaSetDevice(c->device);
+                for (auto& e : c->ev)
+                    if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "event");
+            }
+            return DVL_OK;
+        default:
+            return fail(c, DVL_ERR_ARG, "unknown option %d", option);
+    }
+}
+
+int dvl_load_amr(dvl_ctx* c, uint64_t n, const int32_t* lower, const uint8_t* level, uint32_t M,
+                 const float* const* fields, int mem_kind)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (n >= (1ull << 32)) return fail(c, DVL_ERR_ARG, "n_cells must be < 2^32");
+    if (M < 1 || M > DVL_MAX_FIELDS) return fail(c, DVL_ERR_ARG, "n_fields must be in [1, %d]", DVL_MAX_FIELDS);
+    if (mem_kind != DVL_MEM_HOST && mem_kind != DVL_MEM_DEVICE) return fail(c, DVL_ERR_ARG, "bad mem_kind");
+    if (n && (!lower || !level || !fields)) return fail(c, DVL_ERR_ARG, "NULL input");
+    cudaSetDevice(c->device);
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    free_dataset(c);
+    c->n = n;
+    c->M = M;
+    c->pitch = pad_to(n ? n : 1, PAD);
+    const size_t p = c->pitch;
+    CK(dalloc(c->d_lower, 3 * p), "alloc lower");
+    CK(dalloc(c->d_level_in, p), "alloc level");
+    CK(dalloc(c->d_fin, (size_t)M * p), "alloc fields");
+    CK(cudaMemsetAsync(c->d_fin, 0, (size_t)M * p * sizeof(float), c->stream), "clear");
+    CK(cudaMemsetAsync(c->d_level_in, 0, p, c->stream), "clear");
+    if (n) {
+        for (int d = 0; d < 3; ++d)
+            CK(cudaMemcpyAsync(c->d_lower + d * p, lower + d * n, n * sizeof(int32_t), kind_in(mem_kind),
+                               c->stream), "copy lower");
+        CK(cudaMemcpyAsync(c->d_level_in, level, n, kind_in(mem_kind), c->stream), "copy level");
+    }
+    int rc = upload_fields(c, fields, mem_kind);
+    if (rc) return rc;
+    DataMeta init;
+    for (int m = 0; m < DVL_MAX_FIELDS; ++m) { init.dmin[m] = 0xFFFFFFFFu; init.dmax[m] = 0u; }
+    init.max_level = 0;
+    init.pad = 0;
+    init.key_or = 0;
+    CK(cudaMemcpyAsync(c->d_meta, &init, sizeof init, cudaMemcpyHostToDevice, c->stream), "write meta");
+    launch_validate(c->stream, n, c->d_lower, c->d_level_in, M, nullptr, p, c->d_meta, c->d_err);
+    launch_field_ranges(c->stream, n, M, c->d_fin, p, c->d_meta, c->d_err);
+    CK(cudaGetLastError(), "validation kernels");
+    rc = take_device_error(c);     // synchronises: inputs are consumed on return
+    if (rc) { free_dataset(c); return rc; }
+    c->T = 0;
+    c->tf_set.assign(M, 0);
+    c->h_tf.clear();
+    c->h_dom.assign(2 * M, NAN);
+    c->tf_dirty = true;
+    c->state = 1;
+    return DVL_OK;
+}
+
+int dvl_build_order(dvl_ctx* c, int sfc)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (sfc != DVL_SFC_MORTON && sfc != DVL_SFC_HILBERT) return fail(c, DVL_ERR_ARG, "bad sfc");
+    if (c->state < 1) return fail(c, DVL_ERR_STATE, "no data set loaded");
+    cudaSetDevice(c->device);
+    const uint64_t n = c->n;
+    const size_t p = c->pitch;
+    CK(dalloc(c->d_keys, n), "alloc keys");
+    CK(dalloc(c->d_perm, n), "alloc perm");
+    CK(dalloc(c->d_keys_alt, n), "alloc keys");
+    CK(dalloc(c->d_vals_alt, n), "alloc vals");
+    const uint64_t rs_tiles = (n + RS_TILE - 1) / RS_TILE;
+    CK(dalloc(c->d_rs_status, rs_tiles * RS_RADIX), "alloc sort status");
+    CK(cudaMemsetAsync(c->d_rs_status, 0, (rs_tiles ? rs_tiles : 1) * RS_RADIX * 8, c->stream), "clear");
+    CK(cudaMemsetAsync(c->d_hist, 0, 8 * RS_RADIX * 4, c->stream), "clear");
+    CK(cudaMemsetAsync(c->d_rs_counters, 0, 8 * 4, c->stream), "clear");
+    CK(cudaMemsetAsync(&c->d_meta->key_or, 0, 8, c->stream), "clear");
+    launch_keys(c->stream, n, c->d_lower, p, c->d_level_in, sfc, c->d_keys, c->d_perm, c->d_hist, c->d_meta);
+    CK(cudaGetLastError(), "key kernel");
+    unsigned long long key_or = 0;
+    CK(cudaMemcpyAsync(&key_or, &c->d_meta->key_or, 8, cudaMemcpyDeviceToHost, c->stream), "read key bits");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    int bits = 0;
+    while (bits < 64 && (key_or >> bits)) ++bits;
+    const int passes = (bits + RS_BITS - 1) / RS_BITS;
+    unsigned long long *kin = c->d_keys, *kout = c->d_keys_alt;
+    uint32_t *vin = c->d_perm, *vout = c->d_vals_alt;
+    for (int ps = 0; ps < passes; ++ps) {
+        if (++c->epoch >= (1u << 24)) {     // tag space exhausted: clear and restart
+            CK(cudaMemsetAsync(c->d_rs_status, 0, rs_tiles * RS_RADIX * 8, c->stream), "clear");
+            c->epoch = 1;
+        }
+        CK(launch_onesweep(c->stream, n, kin, vin, kout, vout, ps * RS_BITS, c->d_hist + ps * RS_RADIX,
+                           c->d_rs_status, c->epoch, c->d_rs_counters + ps, c->d_err, c->spin_limit),
+           "radix pass");
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    // results live in kin/vin; make them the canonical arrays
+    if (kin != c->d_keys) std::swap(c->d_keys, c->d_keys_alt);
+    if (vin != c->d_perm) std::swap(c->d_perm, c->d_vals_alt);
+    dfree(c->d_keys_alt);
+    dfree(c->d_vals_alt);
+    dfree(c->d_rs_status);
+    CK(dalloc(c->d_val, (size_t)c->M * p), "alloc sorted fields");
+    CK(dalloc(c->d_lev, p), "alloc sorted levels");
+    CK(cudaMemsetAsync(c->d_val, 0, (size_t)c->M * p * sizeof(float), c->stream), "clear");
+    CK(cudaMemsetAsync(c->d_lev, 0, p, c->stream), "clear");
+    launch_gather(c->stream, n, c->d_perm, c->M, c->d_fin, p, c->d_level_in, c->d_val, p, c->d_lev);
+    CK(cudaGetLastError(), "gather kernel");
+    const uint64_t tiles = (n + TILE - 1) / TILE;
+    CK(dalloc(c->d_tile_status, tiles), "alloc scan state");
+    CK(dalloc(c->d_chunk_prefix, tiles * WARPS), "alloc scan state");
+    int rc = take_device_error(c);
+    if (rc) return rc;
+    // the unsorted coordinates are no longer needed; fields stay for set_fields
+    dfree(c->d_lower);
+    dfree(c->d_level_in);
+    c->state = 2;
+    return DVL_OK;
+}
+
+int dvl_set_fields(dvl_ctx* c, uint32_t M, const float* const* fields, int mem_kind)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (c->state < 2) return fail(c, DVL_ERR_STATE, "order not built");
+    if (M != c->M) return fail(c, DVL_ERR_ARG, "n_fields %u != loaded %u", M, c->M);
+    if (mem_kind != DVL_MEM_HOST && mem_kind != DVL_MEM_DEVICE) return fail(c, DVL_ERR_ARG, "bad mem_kind");
+    if (c->n && !fields) return fail(c, DVL_ERR_ARG, "NULL fields");
+    cudaSetDevice(c->device);
+    int rc = upload_fields(c, fields, mem_kind);
+    if (rc) return rc;
+    rc = compute_ranges(c);
+    if (rc) return rc;
+    launch_gather(c->stream, c->n, c->d_perm, c->M, c->d_fin, c->pitch, nullptr, c->d_val, c->pitch, nullptr);
+    CK(cudaGetLastError(), "gather kernel");
+    return take_device_error(c);
+}
+
+int dvl_set_tf(dvl_ctx* c, uint32_t field, const float* alpha, uint32_t T, float lo, float hi)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (c->state < 1) return fail(c, DVL_ERR_STATE, "no data set loaded");
+    if (field >= c->M) return fail(c, DVL_ERR_ARG, "field %u out of range", field);
+    if (!alpha) return fail(c, DVL_ERR_ARG, "alpha is NULL");
+    if (T < 2 || T > DVL_MAX_TF_ENTRIES) return fail(c, DVL_ERR_ARG, "n_entries must be in [2, %d]", DVL_MAX_TF_ENTRIES);
+    for (uint32_t e = 0; e < T; ++e)
+        if (!(alpha[e] >= 0.0f && alpha[e] <= 1.0f)) return fail(c, DVL_ERR_ARG, "alpha[%u] outside [0, 1]", e);
+    const bool dflt = std::isnan(lo) && std::isnan(hi);
+    if (!dflt && !(std::isfinite(lo) && std::isfinite(hi) && lo < hi))
+        return fail(c, DVL_ERR_ARG, "domain must be finite with lo < hi, or NaN/NaN");
+    if (T != c->T) {          // a new table size invalidates the other fields' tables
+        c->T = T;
+        c->h_tf.assign((size_t)c->M * T, 0.0f);
+        c->tf_set.assign(c->M, 0);
+    }
+    std::memcpy(&c->h_tf[(size_t)field * T], alpha, T * sizeof(float));
+    c->h_dom[field] = lo;
+    c->h_dom[c->M + field] = hi;
+    c->tf_set[field] = 1;
+    c->tf_dirty = true;
+    return DVL_OK;
+}
+
+static int check_params(dvl_ctx* c, const dvl_params* p)
+{
+    if (!p) return fail(c, DVL_ERR_ARG, "params is NULL");
+    if (!(p->P >= 0.0f) || !std::isfinite(p->P)) return fail(c, DVL_ERR_ARG, "P must be finite and >= 0");
+    if (!(p->min_importance >= 0.0f) || !std::isfinite(p->min_importance))
+        return fail(c, DVL_ERR_ARG, "min_importance must be finite and >= 0");
+    if (p->width < 1 || p->width > DVL_MAX_WIDTH) return fail(c, DVL_ERR_ARG, "width must be in [1, %d]", DVL_MAX_WIDTH);
+    if (p->min_imp_mode > 1 || p->vmax_mode > 1 || p->width_mode > 1) return fail(c, DVL_ERR_ARG, "bad mode");
+    return DVL_OK;
+}
+
+static int ensure_update_buffers(dvl_ctx* c, uint32_t W)
+{
+    if (c->tf_dirty) {
+        const size_t need = (size_t)c->M * c->T;
+        if (need > c->tf_cap) {
+            CK(dalloc(c->d_tf, need), "alloc TF");
+            CK(dalloc(c->d_dom, 2 * DVL_MAX_FIELDS), "alloc TF domain");
+            c->tf_cap = need;
+        }
+        CK(cudaMemcpyAsync(c->d_tf, c->h_tf.data(), need * sizeof(float), cudaMemcpyHostToDevice, c->stream),
+           "copy TF");
+        CK(cudaMemcpyAsync(c->d_dom, c->h_dom.data(), 2 * c->M * sizeof(float), cudaMemcpyHostToDevice,
+                           c->stream), "copy TF domain");
+        c->tf_dirty = false;
+    }
+    if (W > c->W_cap) {
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        const size_t MW = (size_t)c->M * W;
+        CK(dalloc(c->d_sum, MW), "alloc bins");
+        CK(dalloc(c->d_vmin, MW), "alloc bins");
+        CK(dalloc(c->d_vmax, MW), "alloc bins");
+        CK(dalloc(c->d_mean, MW), "alloc bins");
+        CK(dalloc(c->d_y, MW), "alloc bins");
+        CK(dalloc(c->d_count, W), "alloc bins");
+        c->W_cap = W;
+    }
+    return DVL_OK;
+}
+
+static UpdateArgs make_args(dvl_ctx* c, const dvl_params& p)
+{
+    UpdateArgs a;
+    a.n = c->n;
+    a.M = c->M;
+    a.T = c->T;
+    a.W = p.width;
+    a.val = c->d_val;
+    a.pitch = c->pitch;
+    a.lev = c->d_lev;
+    a.tf = c->d_tf;
+    a.dom = c->d_dom;
+    a.meta = c->d_meta;
+    a.consts = c->d_consts;
+    a.tile_status = c->d_tile_status;
+    a.chunk_prefix = c->d_chunk_prefix;
+    a.counters = c->d_counters;
+    a.sum = c->d_sum;
+    a.vmin = c->d_vmin;
+    a.vmax = c->d_vmax;
+    a.count = c->d_count;
+    a.mean = c->d_mean;
+    a.y = c->d_y;
+    a.err = c->d_err;
+    a.spin_limit = c->spin_limit;
+    a.fault_no_publish = c->fault_no_publish;
+    a.prm = p;
+    a.events = nullptr;
+    return a;
+}
+
+int dvl_update(dvl_ctx* c, const dvl_params* p)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    int rc = check_params(c, p);
+    if (rc) return rc;
+    if (c->state < 2) return fail(c, DVL_ERR_STATE, "order not built");
+    for (uint32_t m = 0; m < c->M; ++m)
+        if (!c->tf_set[m]) return fail(c, DVL_ERR_STATE, "field %u has no transfer function", m);
+    cudaSetDevice(c->device);
+    rc = ensure_update_buffers(c, p->width);
+    if (rc) return rc;
+    UpdateArgs a = make_args(c, *p);
+    a.events = c->timing ? c->ev : nullptr;
+    CK(launch_update(c->stream, a), "update kernels");
+    c->timed_last = c->timing != 0;
+    c->fault_no_publish = 0;
+    c->W_last = p->width;
+    c->last_prm = *p;
+    c->have_update = true;
+    return DVL_OK;
+}
+
+int dvl_read_bins(dvl_ctx* c, uint32_t field, const dvl_bins* out)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (!out) return fail(c, DVL_ERR_ARG, "out is NULL");
+    if (!c->have_update) return fail(c, DVL_ERR_STATE, "no update has run");
+    if (field >= c->M) return fail(c, DVL_ERR_ARG, "field %u out of range", field);
+    if (out->mem_kind != DVL_MEM_HOST && out->mem_kind != DVL_MEM_DEVICE) return fail(c, DVL_ERR_ARG, "bad mem_kind");
+    cudaSetDevice(c->device);
+    int rc = take_device_error(c);
+    if (rc) return rc;
+    const size_t W = c->W_last, off = (size_t)field * W;
+    const cudaMemcpyKind k = kind_out(out->mem_kind);
+    if (out->mean) CK(cudaMemcpyAsync(out->mean, c->d_mean + off, W * 4, k, c->stream), "copy mean");
+    if (out->min) CK(cudaMemcpyAsync(out->min, c->d_vmin + off, W * 4, k, c->stream), "copy min");
+    if (out->max) CK(cudaMemcpyAsync(out->max, c->d_vmax + off, W * 4, k, c->stream), "copy max");
+    if (out->y) CK(cudaMemcpyAsync(out->y, c->d_y + off, W * 4, k, c->stream), "copy y");
+    if (out->sum) CK(cudaMemcpyAsync(out->sum, c->d_sum + off, W * 8, k, c->stream), "copy sum");
+    if (out->count) CK(cudaMemcpyAsync(out->count, c->d_count, W * 4, k, c->stream), "copy count");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return DVL_OK;
+}
+
+int dvl_get_stats(dvl_ctx* c, dvl_stats* out)
+{
+    if (!c || !out) return fail(c, DVL_ERR_ARG, "NULL argument");
+    c->last_error.clear();
+    if (!c->have_update) return fail(c, DVL_ERR_STATE, "no update has run");
+    cudaSetDevice(c->device);
+    int rc = take_device_error(c);
+    if (rc) return rc;
+    UpdateConsts u;
+    DataMeta meta;
+    CK(cudaMemcpyAsync(&u, c->d_consts, sizeof u, cudaMemcpyDeviceToHost, c->stream), "read consts");
+    CK(cudaMemcpyAsync(&meta, c->d_meta, sizeof meta, cudaMemcpyDeviceToHost, c->stream), "read meta");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    out->vmax = u.vmax;
+    out->inv_vmax = u.inv_vmax;
+    out->f_upper = u.f_upper;
+    out->Q = u.Q;
+    out->i = u.i;
+    out->j = u.j;
+    out->linear = u.linear;
+    out->pow_exact = u.pow_n2 >= 0;
+    out->F = u.F;
+    out->n_cells = c->n;
+    out->n_fields = c->M;
+    out->max_level = meta.max_level;
+    return DVL_OK;
+}
+
+int dvl_read_order(dvl_ctx* c, uint64_t* keys, uint32_t* perm, int mem_kind)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (c->state < 2) return fail(c, DVL_ERR_STATE, "order not built");
+    if (mem_kind != DVL_MEM_HOST && mem_kind != DVL_MEM_DEVICE) return fail(c, DVL_ERR_ARG, "bad mem_kind");
+    cudaSetDevice(c->device);
+    if (keys && c->n) CK(cudaMemcpyAsync(keys, c->d_keys, c->n * 8, kind_out(mem_kind), c->stream), "copy keys");
+    if (perm && c->n) CK(cudaMemcpyAsync(perm, c->d_perm, c->n * 4, kind_out(mem_kind), c->stream), "copy perm");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return take_device_error(c);
+}
+
+int dvl_read_widths(dvl_ctx* c, uint64_t* q, int mem_kind)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (!q && c->n) return fail(c, DVL_ERR_ARG, "q is NULL");
+    if (!c->have_update) return fail(c, DVL_ERR_STATE, "no update has run");
+    if (mem_kind != DVL_MEM_HOST && mem_kind != DVL_MEM_DEVICE) return fail(c, DVL_ERR_ARG, "bad mem_kind");
+    cudaSetDevice(c->device);
+    if (!c->n) return DVL_OK;
+    unsigned long long* dq = nullptr;
+    if (mem_kind == DVL_MEM_DEVICE) {
+        dq = reinterpret_cast<unsigned long long*>(q);
+    } else {
+        CK(cudaMalloc(&dq, c->n * 8), "alloc widths");
+    }
+    UpdateArgs a = make_args(c, c->last_prm);
+    cudaError_t e = launch_widths(c->stream, a, dq);
+    if (e == cudaSuccess && mem_kind == DVL_MEM_HOST)
+        e = cudaMemcpyAsync(q, dq, c->n * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (mem_kind == DVL_MEM_HOST) cudaFree(dq);
+    if (e != cudaSuccess) return cuda_fail(c, e, "widths");
+    return take_device_error(c);
+}
+
+int dvl_get_timings(dvl_ctx* c, double* ms, int n)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (!ms || n < 4) return fail(c, DVL_ERR_ARG, "need room for 4 stage times");
+    if (!c->have_update || !c->timed_last) return fail(c, DVL_ERR_STATE, "last update was not timed");
+    cudaSetDevice(c->device);
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    for (int k = 0; k < 4; ++k) {
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, c->ev[k], c->ev[k + 1]), "event time");
+        ms[k] = t;
+    }
+    return take_device_error(c);
+}
+
+int dvl_sync(dvl_ctx* c)
+{
+    if (!c) return DVL_ERR_ARG;
+    cudaSetDevice(c->device);
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return take_device_error(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Internal declarations shared by the host orchestration (dvl_api.cu) and the
+// kernels (sfc_sort.cu, update.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dvl.h"
+
+namespace dvl {
+
+// ---- update geometry -------------------------------------------------------
+// One warp owns a chunk of CHUNK consecutive cells (curve order); a CTA of
+// WARPS warps owns one tile of the device-wide prefix scan.  A lane handles 4
+// consecutive cells per step (one float4 per field, one u32 of levels).
+constexpr int WARPS = 8;
+constexpr int CHUNK = 1024;
+constexpr int STEP = 128;                 // cells per warp step (32 lanes x 4)
+constexpr int STEPS = CHUNK / STEP;
+constexpr int TILE = WARPS * CHUNK;       // 8192 cells
+constexpr int PAD = 1024;                 // field/level arrays padded to this
+
+// ---- radix sort geometry ---------------------------------------------------
+constexpr int RS_THREADS = 256;
+constexpr int RS_KPT = 16;                // keys per thread
+constexpr int RS_TILE = RS_THREADS * RS_KPT;   // 4096 keys per tile
+constexpr int RS_BITS = 8;
+constexpr int RS_RADIX = 1 << RS_BITS;
+
+// ---- device error bits (dvl_ctx::d_err) -------------------------------------
+enum : uint32_t {
+    ERR_TIMEOUT = 1u,       // a bounded wait gave up
+    ERR_RANGE = 2u,         // width bound not representable / bad input value
+    ERR_LEVEL = 4u,         // cell level too high
+    ERR_COORD = 8u,         // cell outside the logical grid
+    ERR_NONFINITE = 16u,    // non-finite field value
+};
+
+// Per-update constants, written on the device by k_prepare / k_consts and
+// read by the update kernels.  Plain struct (also copied back for stats).
+struct UpdateConsts {
+    float lo[DVL_MAX_FIELDS];     // TF domain lower bound per field
+    float s[DVL_MAX_FIELDS];      // float32 reciprocal of the domain span (0 if empty)
+    float vmax, inv_vmax, f_upper, qscale;   // qscale = 2^Q
+    float P, min_imp;
+    int32_t Q, i, j, pow_n2;      // pow_n2 = 2P if exact mode, else -1
+    int32_t min_imp_mode, width_shift;       // width_shift = 1 (2^L) or 3 (8^L)
+    int32_t linear, pad0;
+    uint64_t F;                   // total width, set by the last scan tile
+    uint64_t F_div_W, F_mod_W;    // F = F_div_W * W + F_mod_W (for pixel bounds)
+};
+
+// Data-set metadata computed on the device at load time.
+struct DataMeta {
+    uint32_t dmin[DVL_MAX_FIELDS];   // order-preserving bits of the data min
+    uint32_t dmax[DVL_MAX_FIELDS];
+    uint32_t max_level;
+    uint32_t pad;
+    unsigned long long key_or;       // OR of all keys (significant bits)
+};
+
+}  // namespace dvl
+
+// ---- kernel launchers (all asynchronous on `s`) -----------------------------
+namespace dvl {
+
+// sfc_sort.cu
+void launch_validate(cudaStream_t s, uint64_t n, const int32_t* lower, const uint8_t* level,
+                     uint32_t M, float* const* fields, size_t pitch, DataMeta* meta, uint32_t* err);
+void launch_field_ranges(cudaStream_t s, uint64_t n, uint32_t M, const float* fields, size_t pitch,
+                         DataMeta* meta, uint32_t* err);
+void launch_keys(cudaStream_t s, uint64_t n, const int32_t* lower, size_t pitch, const uint8_t* level,
+                 int sfc, unsigned long long* keys, uint32_t* vals, uint32_t* hist /*8*256*/,
+                 DataMeta* meta);
+// One stable LSD pass over digit (key >> shift) & 255.  `status` holds
+// n_tiles*256 words tagged with `epoch` (never cleared between passes).
+cudaError_t launch_onesweep(cudaStream_t s, uint64_t n, const unsigned long long* kin,
+                            const uint32_t* vin, unsigned long long* kout, uint32_t* vout,
+                            int shift, const uint32_t* hist_digit, unsigned long long* status,
+                            uint32_t epoch, uint32_t* tile_counter, uint32_t* err, int64_t spin_limit);
+void launch_gather(cudaStream_t s, uint64_t n, const uint32_t* perm, uint32_t M, const float* fin,
+                   size_t pitch_in, const uint8_t* lin, float* fout, size_t pitch_out, uint8_t* lout);
+
+// update.cu
+struct UpdateArgs {
+    uint64_t n;
+    uint32_t M, T, W;
+    const float* val;          // M x pitch, curve order
+    size_t pitch;
+    const uint8_t* lev;        // pitch bytes, curve order
+    const float* tf;           // M x T alpha tables
+    const float* dom;          // 2*M: lo[M], hi[M]  (NaN,NaN = data range)
+    const DataMeta* meta;
+    UpdateConsts* consts;
+    unsigned long long* tile_status;   // n_tiles
+    unsigned long long* chunk_prefix;  // n_chunks
+    uint32_t* counters;        // [0] tile ticket, [1] tiles done
+    double* sum;               // M x W
+    uint32_t* vmin;            // M x W (float bits)
+    uint32_t* vmax;            // M x W (float bits)
+    uint32_t* count;           // W
+    float* mean;               // M x W
+    float* y;                  // M x W
+    uint32_t* err;
+    int64_t spin_limit;
+    int fault_no_publish;
+    dvl_params prm;
+    cudaEvent_t* events;       // 5 events recorded between the stages, or null
+};
+cudaError_t launch_update(cudaStream_t s, const UpdateArgs& a);
+cudaError_t launch_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* q);
+
+}  // namespace dvl

@@ -1,0 +1,693 @@
+// Per-edit stage of the DVL computation (paper Sec. 3-4), run on every alpha
+// transfer-function or data change over the cells in curve order.
+//
+//   k_prepare   TF domains, Eq. 5/6 max-variation approximation, fixed-point
+//               exponent; clears bins and scan state (one launch).
+//   k_passA     per cell: TF alpha per field, variation V (Eq. 1), importance
+//               f (Eq. 3), fixed-point width q; per-warp-chunk sums and a
+//               single-pass decoupled look-back scan over tiles (Eq. 4) that
+//               leaves the exclusive prefix of every chunk and the total F.
+//   k_passB     recomputes q, scans it within each warp step, places every
+//               cell into the pixels its [E, E+q) span touches (Sec. 3.2) and
+//               reduces runs of cells with the same pixel in registers; global
+//               atomics only when the pixel changes or the chunk ends.
+//   k_finalize  per pixel: mean = sum / count, alpha of the mean (Sec. 3.3).
+//
+// Widths are integers q = rint(f * 2^Q) (u64); Q is chosen so that the total
+// stays below 2^62, so the prefix sum is exact and independent of summation
+// order and the cell-to-pixel assignment is bit-identical to a sequential CPU
+// evaluation.  Every float operation that decides an integer (TF entry,
+// width) is a correctly rounded float32 operation (explicit __f*_rn intrinsics;
+// this file is built with -fmad=false).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dvl_internal.h"
+
+namespace dvl {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr unsigned long long FLAG_A = 1ull << 62;   // tile aggregate published
+constexpr unsigned long long FLAG_P = 2ull << 62;   // inclusive prefix published
+constexpr unsigned long long VAL_MASK = (1ull << 62) - 1;
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ float ordered_to_float(uint32_t u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+// 2^e as a float for -126 <= e <= 127 (exact).
+__device__ __forceinline__ float exp2i(int e) { return __int_as_float((127 + e) << 23); }
+
+// Normalised value t = clamp((v - lo) * s, 0, 1) (Sec. 3.3); NaN and -0 give +0.
+__device__ __forceinline__ float norm_t(float v, float lo, float s)
+{
+    float t = __fmul_rn(__fsub_rn(v, lo), s);
+    t = t > 0.0f ? t : 0.0f;
+    return t > 1.0f ? 1.0f : t;
+}
+
+// TF entry of t: min(floor(t T), T - 1).
+__device__ __forceinline__ uint32_t tf_entry(float t, float Tf, uint32_t Tm1)
+{
+    uint32_t a = (uint32_t)__fmul_rn(t, Tf);    // t*T >= 0: truncation == floor
+    return a < Tm1 ? a : Tm1;
+}
+
+// x^P (Eq. 2/3).  n2 = 2P for the exact modes: sqrt once if n2 is odd, then
+// left-to-right products; n2 < 0 selects powf.
+__device__ __forceinline__ float pow_steep(float x, int n2, float P)
+{
+    if (n2 < 0) return powf(x, P);
+    if (n2 == 0) return 1.0f;
+    float b;
+    int k;
+    if (n2 & 1) { b = __fsqrt_rn(x); k = n2; } else { b = x; k = n2 >> 1; }
+    float y = b;
+    for (int i = 1; i < k; ++i) y = __fmul_rn(y, b);
+    return y;
+}
+
+// Per-cell constants held in registers by the update kernels.
+template <int M>
+struct CellConsts {
+    float lo[M], s[M];
+    float inv_vmax, min_imp, qscale, P, Tf;
+    uint32_t Tm1;
+    int n2, mode, wshift;
+
+    __device__ __forceinline__ void load(const UpdateConsts* C, uint32_t T)
+    {
+#pragma unroll
+        for (int m = 0; m < M; ++m) { lo[m] = C->lo[m]; s[m] = C->s[m]; }
+        inv_vmax = C->inv_vmax;
+        min_imp = C->min_imp;
+        qscale = C->qscale;
+        P = C->P;
+        n2 = C->pow_n2;
+        mode = C->min_imp_mode;
+        wshift = C->width_shift;
+        Tf = (float)T;
+        Tm1 = T - 1;
+    }
+
+    // Eq. 3 with the minimum importance; r = V * (1/maxV) (float32).
+    __device__ __forceinline__ float importance(float V, uint32_t L) const
+    {
+        float r = __fmul_rn(V, inv_vmax);
+        float sc = exp2i((int)L * wshift);
+        float f;
+        if (mode == DVL_MINIMP_BEFORE_SCALE) {
+            r = r < min_imp ? min_imp : r;
+            f = pow_steep(__fmul_rn(r, sc), n2, P);
+        } else {
+            f = pow_steep(__fmul_rn(r, sc), n2, P);
+            f = f < min_imp ? min_imp : f;
+        }
+        return f;
+    }
+
+    // Eq. 1 over the M fields of one cell, from normalised values t[].
+    __device__ __forceinline__ float variation(const float* t, const float* s_tf, uint32_t T) const
+    {
+        float hi = 0.0f, lw = 1.0f;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            float al = s_tf[m * T + tf_entry(t[m], Tf, Tm1)];
+            hi = fmaxf(hi, al);
+            lw = fminf(lw, al);
+        }
+        return __fsub_rn(hi, lw);
+    }
+
+    __device__ __forceinline__ unsigned long long width(float f) const
+    {
+        return __float2ull_rn(__fmul_rn(f, qscale));
+    }
+};
+
+// Loads 4 consecutive cells at idx (idx % 4 == 0; arrays padded).
+template <int M>
+__device__ __forceinline__ void load4(const float* __restrict__ val, size_t pitch,
+                                      const uint8_t* __restrict__ lev, uint64_t idx,
+                                      float (&v)[4][M], uint32_t& L4)
+{
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        float4 x = __ldg(reinterpret_cast<const float4*>(val + m * pitch + idx));
+        v[0][m] = x.x; v[1][m] = x.y; v[2][m] = x.z; v[3][m] = x.w;
+    }
+    L4 = __ldg(reinterpret_cast<const uint32_t*>(lev + idx));
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long x, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// Constants (Sec. 3.4 and the fixed-point exponent)
+// ---------------------------------------------------------------------------
+
+__device__ int bitlen64(uint64_t x) { return x ? 64 - __clzll((long long)x) : 0; }
+
+// f_upper, Q, 2^Q from vmax (after vmax is known).
+__device__ void finish_consts(UpdateConsts* C, const UpdateArgs& a, uint32_t max_level)
+{
+    const float vmax = C->vmax;
+    const float inv = vmax > 0.0f ? __frcp_rn(vmax) : 0.0f;
+    C->inv_vmax = inv;
+    CellConsts<1> cc;
+    cc.inv_vmax = inv;
+    cc.min_imp = C->min_imp;
+    cc.P = C->P;
+    cc.n2 = C->pow_n2;
+    cc.mode = C->min_imp_mode;
+    cc.wshift = C->width_shift;
+    float fu = cc.importance(vmax > 0.0f ? 1.0f : 0.0f, max_level);
+    C->f_upper = fu;
+    int Q = 0;
+    if (!isfinite(fu)) {
+        atomicOr(a.err, ERR_RANGE);
+    } else {
+        int e = 0;
+        frexpf(fu, &e);
+        if (C->pow_n2 < 0) e += 1;
+        Q = 62 - bitlen64(a.n) - e;
+        if (Q > 120) Q = 120;
+        if (Q < -120) { atomicOr(a.err, ERR_RANGE); Q = 0; }
+    }
+    C->Q = Q;
+    C->qscale = exp2i(Q);
+    C->F = 0;
+    C->linear = 0;
+}
+
+__global__ void k_prepare(UpdateArgs a, uint32_t n_tiles)
+{
+    // clear bins and scan state
+    const uint64_t MW = (uint64_t)a.M * a.W;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < MW;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        a.sum[i] = 0.0;
+        a.vmin[i] = 0xFFFFFFFFu;
+        a.vmax[i] = 0u;
+        if (i < a.W) a.count[i] = 0u;
+    }
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_tiles;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        a.tile_status[i] = 0ull;
+    if (blockIdx.x != 0) return;
+
+    __shared__ int s_i[DVL_MAX_FIELDS], s_j[DVL_MAX_FIELDS];
+    __shared__ float s_spread[256];
+    UpdateConsts* C = a.consts;
+    const uint32_t M = a.M, T = a.T;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        a.counters[0] = 0u;
+        a.counters[1] = 0u;
+        C->P = a.prm.P;
+        C->min_imp = a.prm.min_importance;
+        C->min_imp_mode = (int)a.prm.min_imp_mode;
+        C->width_shift = a.prm.width_mode == DVL_WIDTH_VOLUME ? 3 : 1;
+        float n2 = 2.0f * a.prm.P;
+        C->pow_n2 = (n2 >= 0.0f && n2 <= 16.0f && floorf(n2) == n2) ? (int)n2 : -1;
+    }
+    if (tid < (int)M) {
+        float dmin = ordered_to_float(a.meta->dmin[tid]);
+        float dmax = ordered_to_float(a.meta->dmax[tid]);
+        if (a.n == 0) { dmin = 0.0f; dmax = 0.0f; }
+        float lo = a.dom[tid], hi = a.dom[M + tid];
+        if (isnan(lo) && isnan(hi)) { lo = dmin; hi = dmax; }
+        float span = __fsub_rn(hi, lo);
+        float s = (span > 0.0f && isfinite(span)) ? __frcp_rn(span) : 0.0f;
+        C->lo[tid] = lo;
+        C->s[tid] = s;
+        // Eq. 5: TF entries of the data minimum and maximum of this field
+        s_i[tid] = (int)tf_entry(norm_t(dmin, lo, s), (float)T, T - 1);
+        s_j[tid] = (int)tf_entry(norm_t(dmax, lo, s), (float)T, T - 1);
+    }
+    __syncthreads();
+    int gi = (int)T - 1, gj = 0;
+    for (uint32_t m = 0; m < M; ++m) { gi = min(gi, s_i[m]); gj = max(gj, s_j[m]); }
+    if (gi > gj) { gi = 0; gj = 0; }
+    // Eq. 6: largest spread max_m A(m,a) - min_m A(m,a) over a in [gi, gj]
+    float best = 0.0f;
+    for (int e = gi + tid; e <= gj; e += blockDim.x) {
+        float hi = a.tf[e], lw = a.tf[e];
+        for (uint32_t m = 1; m < M; ++m) {
+            float x = a.tf[m * T + e];
+            hi = fmaxf(hi, x);
+            lw = fminf(lw, x);
+        }
+        best = fmaxf(best, __fsub_rn(hi, lw));
+    }
+    s_spread[tid] = best;
+    __syncthreads();
+    if (tid == 0) {
+        C->i = gi;
+        C->j = gj;
+        if (a.prm.vmax_mode == DVL_VMAX_APPROX) {
+            float v = 0.0f;
+            for (int k = 0; k < (int)blockDim.x; ++k) v = fmaxf(v, s_spread[k]);
+            C->vmax = v;
+            finish_consts(C, a, a.meta->max_level);
+        } else {
+            C->vmax = 0.0f;   // filled by k_vmax_exact, then k_consts
+        }
+    }
+}
+
+// Exact max V over all cells (the reduction Sec. 3.4 avoids; optional mode).
+template <int M>
+__global__ __launch_bounds__(256) void k_vmax_exact(UpdateArgs a)
+{
+    extern __shared__ float s_tf[];
+    for (uint32_t i = threadIdx.x; i < a.M * a.T; i += blockDim.x) s_tf[i] = a.tf[i];
+    __syncthreads();
+    CellConsts<M> cc;
+    cc.load(a.consts, a.T);
+    float best = 0.0f;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        float t[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) t[m] = norm_t(a.val[m * a.pitch + i], cc.lo[m], cc.s[m]);
+        best = fmaxf(best, cc.variation(t, s_tf, a.T));
+    }
+    for (int o = 16; o; o >>= 1) best = fmaxf(best, __shfl_xor_sync(FULL, best, o));
+    if ((threadIdx.x & 31) == 0 && best > 0.0f)
+        atomicMax(reinterpret_cast<unsigned int*>(&a.consts->vmax), __float_as_uint(best));
+}
+
+__global__ void k_consts(UpdateArgs a) { finish_consts(a.consts, a, a.meta->max_level); }
+
+// ---------------------------------------------------------------------------
+// Pass A: widths, chunk sums, decoupled look-back scan over tiles
+// ---------------------------------------------------------------------------
+
+template <int M>
+__global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_tiles)
+{
+    extern __shared__ float s_tf[];
+    __shared__ unsigned long long s_wsum[WARPS];
+    __shared__ uint32_t s_tile;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint32_t i = tid; i < M * a.T; i += blockDim.x) s_tf[i] = a.tf[i];
+    if (tid == 0) s_tile = atomicAdd(&a.counters[0], 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    CellConsts<M> cc;
+    cc.load(a.consts, a.T);
+
+    const uint64_t base = ((uint64_t)tile * WARPS + warp) * CHUNK;
+    unsigned long long acc = 0;
+#pragma unroll 2
+    for (int st = 0; st < STEPS; ++st) {
+        const uint64_t idx = base + st * STEP + lane * 4;
+        if (idx < a.n) {
+            float v[4][M];
+            uint32_t L4;
+            load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float t[M];
+#pragma unroll
+                for (int m = 0; m < M; ++m) t[m] = norm_t(v[j][m], cc.lo[m], cc.s[m]);
+                float f = cc.importance(cc.variation(t, s_tf, a.T), (L4 >> (8 * j)) & 0xFF);
+                if (idx + j < a.n) acc += cc.width(f);
+            }
+        }
+    }
+    acc = warp_sum_u64(acc);
+    if (lane == 0) s_wsum[warp] = acc;
+    __syncthreads();
+    if (warp != 0) return;
+
+    // warp 0: chunk offsets within the tile, then the tile's exclusive prefix
+    unsigned long long w = lane < WARPS ? s_wsum[lane] : 0ull;
+    unsigned long long incl = warp_incl_scan_u64(w, lane);
+    const unsigned long long agg = __shfl_sync(FULL, incl, WARPS - 1);
+    unsigned long long* status = a.tile_status;
+    const bool skip = a.fault_no_publish && tile == 0;
+    if (lane == 0 && !skip) st_relaxed(status + tile, (tile == 0 ? FLAG_P : FLAG_A) | agg);
+    unsigned long long excl = 0;
+    if (tile > 0) {
+        int64_t end = (int64_t)tile - 1;          // window [end-31, end]
+        while (true) {
+            const int64_t j = end - lane;
+            unsigned long long s = FLAG_P;        // beyond tile 0: neutral
+            if (j >= 0) {
+                long long spins = 0;
+                while (true) {
+                    s = ld_relaxed(status + j);
+                    if (s >> 62) break;
+                    if (++spins > a.spin_limit) {
+                        atomicOr(a.err, ERR_TIMEOUT);
+                        s = FLAG_P;               // give up: count it as 0
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+            }
+            const unsigned pmask = __ballot_sync(FULL, (s & FLAG_P) != 0);
+            // lanes up to and including the nearest inclusive prefix contribute
+            const int first = pmask ? __ffs(pmask) - 1 : 31;
+            unsigned long long contrib = lane <= first ? (s & VAL_MASK) : 0ull;
+            excl += warp_sum_u64(contrib);
+            if (pmask) break;
+            end -= 32;
+        }
+        if (lane == 0 && !skip) st_relaxed(status + tile, FLAG_P | (excl + agg));
+    }
+    if (lane < WARPS) a.chunk_prefix[(uint64_t)tile * WARPS + lane] = excl + incl - w;
+    if (lane == 0 && tile == n_tiles - 1) {
+        UpdateConsts* C = a.consts;
+        unsigned long long F = excl + agg;
+        int linear = 0;
+        if (F == 0 && a.n > 0) { F = a.n; linear = 1; }   // all widths 0: equal widths
+        C->F = F;
+        C->linear = linear;
+        C->F_div_W = F / a.W;
+        C->F_mod_W = F % a.W;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass B: placement and per-pixel reduction
+// ---------------------------------------------------------------------------
+
+// Pixel boundaries: C(k) = ceil(k F / W) is the first position of pixel k,
+// D(k) = floor(k F / W); with F = a W + b, k F / W = k a + k b / W.
+struct PixelMap {
+    unsigned long long a, b, F;
+    uint32_t W;
+    __device__ __forceinline__ unsigned long long C(uint32_t k) const
+    {
+        unsigned long long kb = (unsigned long long)k * b;
+        return (unsigned long long)k * a + (kb + W - 1) / W;
+    }
+    __device__ __forceinline__ unsigned long long D(uint32_t k) const
+    {
+        return (unsigned long long)k * a + ((unsigned long long)k * b) / W;
+    }
+    __device__ __forceinline__ uint32_t estimate(unsigned long long x) const
+    {
+        float e = __fmul_rn((float)x, __fdiv_rn((float)W, (float)F));
+        uint32_t k = e > 0.0f ? (uint32_t)e : 0u;
+        return k < W - 1 ? k : W - 1;
+    }
+    // pixel containing start position x: max{k < W : C(k) <= x}
+    __device__ __forceinline__ uint32_t first_pixel(unsigned long long x) const
+    {
+        uint32_t k = estimate(x);
+        while (k + 1 < W && C(k + 1) <= x) ++k;
+        while (k > 0 && C(k) > x) --k;
+        return k;
+    }
+    // last pixel touched by a span ending at I > start: max{k < W : D(k) <= I-1}
+    __device__ __forceinline__ uint32_t last_pixel(unsigned long long I) const
+    {
+        unsigned long long y = I - 1;
+        uint32_t k = estimate(y);
+        while (k + 1 < W && D(k + 1) <= y) ++k;
+        while (k > 0 && D(k) > y) --k;
+        return k;
+    }
+};
+
+template <int M>
+struct Acc {
+    float s[M], mn[M], mx[M];
+    uint32_t cnt;
+    __device__ __forceinline__ void reset()
+    {
+#pragma unroll
+        for (int m = 0; m < M; ++m) { s[m] = 0.0f; mn[m] = 2.0f; mx[m] = -1.0f; }
+        cnt = 0;
+    }
+    __device__ __forceinline__ void add(const float* t)
+    {
+#pragma unroll
+        for (int m = 0; m < M; ++m) { s[m] += t[m]; mn[m] = fminf(mn[m], t[m]); mx[m] = fmaxf(mx[m], t[m]); }
+        ++cnt;
+    }
+    __device__ __forceinline__ void flush_to(const UpdateArgs& a, uint32_t p) const
+    {
+        if (!cnt) return;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const uint64_t k = (uint64_t)m * a.W + p;
+            atomicAdd(&a.sum[k], (double)s[m]);
+            atomicMin(&a.vmin[k], __float_as_uint(mn[m]));   // t >= 0: bit order = value order
+            atomicMax(&a.vmax[k], __float_as_uint(mx[m]));
+        }
+        atomicAdd(&a.count[p], cnt);
+    }
+    // warp-wide reduction, then one lane flushes
+    __device__ __forceinline__ void warp_flush(const UpdateArgs& a, uint32_t p, int lane)
+    {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                s[m] += __shfl_xor_sync(FULL, s[m], o);
+                mn[m] = fminf(mn[m], __shfl_xor_sync(FULL, mn[m], o));
+                mx[m] = fmaxf(mx[m], __shfl_xor_sync(FULL, mx[m], o));
+            }
+            cnt += __shfl_xor_sync(FULL, cnt, o);
+        }
+        if (lane == 0) flush_to(a, p);
+        reset();
+    }
+};
+
+template <int M>
+__global__ __launch_bounds__(WARPS * 32) void k_passB(UpdateArgs a)
+{
+    extern __shared__ float s_tf[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint32_t i = tid; i < M * a.T; i += blockDim.x) s_tf[i] = a.tf[i];
+    __syncthreads();
+    const uint64_t chunk = (uint64_t)blockIdx.x * WARPS + warp;
+    const uint64_t base = chunk * CHUNK;
+    if (base >= a.n) return;
+
+    CellConsts<M> cc;
+    cc.load(a.consts, a.T);
+    const UpdateConsts* C = a.consts;
+    const bool linear = C->linear != 0;
+    PixelMap pm{C->F_div_W, C->F_mod_W, C->F, a.W};
+
+    unsigned long long pos = linear ? base : a.chunk_prefix[chunk];
+    uint32_t cur = pm.first_pixel(pos);
+    unsigned long long lo_pos = pm.C(cur), hi_pos = pm.C(cur + 1);
+    Acc<M> acc;
+    acc.reset();
+
+    for (int st = 0; st < STEPS; ++st) {
+        const uint64_t sbase = base + st * STEP;
+        if (sbase >= a.n) break;                        // warp-uniform
+        const uint64_t idx = sbase + lane * 4;
+        const int nvalid = idx < a.n ? (a.n - idx < 4 ? (int)(a.n - idx) : 4) : 0;
+        float t[4][M];
+        unsigned long long q[4] = {0, 0, 0, 0};
+        if (nvalid) {
+            float v[4][M];
+            uint32_t L4;
+            load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                for (int m = 0; m < M; ++m) t[j][m] = norm_t(v[j][m], cc.lo[m], cc.s[m]);
+                if (j < nvalid) {
+                    if (linear) q[j] = 1;
+                    else q[j] = cc.width(cc.importance(cc.variation(t[j], s_tf, a.T), (L4 >> (8 * j)) & 0xFF));
+                }
+            }
+        }
+        const unsigned long long lsum = q[0] + q[1] + q[2] + q[3];
+        const unsigned long long incl = warp_incl_scan_u64(lsum, lane);
+        const unsigned long long total = __shfl_sync(FULL, incl, 31);
+        const unsigned long long I_last = pos + total;
+
+        if (pos >= lo_pos && I_last < hi_pos) {
+            // every cell of the step lies inside pixel `cur`
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j < nvalid) acc.add(t[j]);
+        } else {
+            acc.warp_flush(a, cur, lane);
+            // exact per-cell placement; merge consecutive equal pixels per lane
+            Acc<M> run;
+            run.reset();
+            uint32_t run_p = 0xFFFFFFFFu;
+            unsigned long long E = pos + incl - lsum;
+            for (int j = 0; j < nvalid; ++j) {
+                const unsigned long long I = E + q[j];
+                const uint32_t b1 = pm.first_pixel(E);
+                const uint32_t b2 = I > E ? pm.last_pixel(I) : b1;
+                for (uint32_t p = b1; p <= b2; ++p) {
+                    if (p != run_p) {
+                        run.flush_to(a, run_p);
+                        run.reset();
+                        run_p = p;
+                    }
+                    run.add(t[j]);
+                }
+                E = I;
+            }
+            run.flush_to(a, run_p);
+            cur = pm.first_pixel(I_last);
+            lo_pos = pm.C(cur);
+            hi_pos = pm.C(cur + 1);
+        }
+        pos = I_last;
+    }
+    acc.warp_flush(a, cur, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Finalize: ApplyWeights + ApplyTransFunc (Sec. 4)
+// ---------------------------------------------------------------------------
+
+__global__ void k_finalize(UpdateArgs a)
+{
+    const uint64_t MW = (uint64_t)a.M * a.W;
+    const float Tf = (float)a.T;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < MW;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t m = (uint32_t)(i / a.W), p = (uint32_t)(i % a.W);
+        const uint32_t c = a.count[p];
+        if (c) {
+            const float mean = __double2float_rn(__ddiv_rn(a.sum[i], (double)c));
+            a.mean[i] = mean;
+            a.y[i] = a.tf[m * a.T + tf_entry(mean, Tf, a.T - 1)];
+        } else {
+            a.mean[i] = 0.0f;
+            a.y[i] = 0.0f;
+            a.vmin[i] = 0u;
+            a.vmax[i] = 0u;
+        }
+    }
+}
+
+// Per-cell widths with the constants of the last update (checking aid).
+template <int M>
+__global__ __launch_bounds__(256) void k_widths(UpdateArgs a, unsigned long long* q)
+{
+    extern __shared__ float s_tf[];
+    for (uint32_t i = threadIdx.x; i < M * a.T; i += blockDim.x) s_tf[i] = a.tf[i];
+    __syncthreads();
+    CellConsts<M> cc;
+    cc.load(a.consts, a.T);
+    const bool linear = a.consts->linear != 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        float t[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) t[m] = norm_t(a.val[m * a.pitch + i], cc.lo[m], cc.s[m]);
+        q[i] = linear ? 1ull : cc.width(cc.importance(cc.variation(t, s_tf, a.T), a.lev[i]));
+    }
+}
+
+template <typename K>
+cudaError_t smem_attr(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int grid_cap(uint64_t work, int threads)
+{
+    uint64_t b = (work + threads - 1) / threads;
+    if (b > 148ull * 8) b = 148ull * 8;
+    return b ? (int)b : 1;
+}
+
+template <int M>
+cudaError_t run_update(cudaStream_t s, const UpdateArgs& a)
+{
+    const uint32_t n_tiles = (uint32_t)((a.n + TILE - 1) / TILE);
+    const size_t smem = (size_t)M * a.T * sizeof(float);
+    cudaError_t e;
+    if ((e = smem_attr(k_passA<M>, smem)) != cudaSuccess) return e;
+    if ((e = smem_attr(k_passB<M>, smem)) != cudaSuccess) return e;
+    if ((e = smem_attr(k_vmax_exact<M>, smem)) != cudaSuccess) return e;
+    const uint64_t clear = (uint64_t)a.M * a.W > n_tiles ? (uint64_t)a.M * a.W : n_tiles;
+    if (a.events) cudaEventRecord(a.events[0], s);
+    k_prepare<<<grid_cap(clear, 256), 256, 0, s>>>(a, n_tiles);
+    if (a.prm.vmax_mode == DVL_VMAX_EXACT) {
+        k_vmax_exact<M><<<grid_cap(a.n, 256), 256, smem, s>>>(a);
+        k_consts<<<1, 1, 0, s>>>(a);
+    }
+    if (a.events) cudaEventRecord(a.events[1], s);
+    if (n_tiles) k_passA<M><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles);
+    if (a.events) cudaEventRecord(a.events[2], s);
+    if (n_tiles) k_passB<M><<<n_tiles, WARPS * 32, smem, s>>>(a);
+    if (a.events) cudaEventRecord(a.events[3], s);
+    k_finalize<<<grid_cap((uint64_t)a.M * a.W, 256), 256, 0, s>>>(a);
+    if (a.events) cudaEventRecord(a.events[4], s);
+    return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t run_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* q)
+{
+    const size_t smem = (size_t)M * a.T * sizeof(float);
+    cudaError_t e = smem_attr(k_widths<M>, smem);
+    if (e != cudaSuccess) return e;
+    if (a.n) k_widths<M><<<grid_cap(a.n, 256), 256, smem, s>>>(a, q);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+#define DVL_DISPATCH_M(fn, ...)                   \
+    switch (a.M) {                                \
+        case 1: return fn<1>(__VA_ARGS__);        \
+        case 2: return fn<2>(__VA_ARGS__);        \
+        case 3: return fn<3>(__VA_ARGS__);        \
+        case 4: return fn<4>(__VA_ARGS__);        \
+        case 5: return fn<5>(__VA_ARGS__);        \
+        case 6: return fn<6>(__VA_ARGS__);        \
+        case 7: return fn<7>(__VA_ARGS__);        \
+        case 8: return fn<8>(__VA_ARGS__);        \
+        default: return cudaErrorInvalidValue;    \
+    }
+
+cudaError_t launch_update(cudaStream_t s, const UpdateArgs& a) { DVL_DISPATCH_M(run_update, s, a) }
+
+cudaError_t launch_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* q)
+{
+    DVL_DISPATCH_M(run_widths, s, a, q)
+}
+
+}  // namespace dvl

@@ -172,7 +172,7 @@ CONFIGS = {
     "diff": dict(kind="threshold", base_n=64, n_levels=4, target=20_000_000, seed=4),
 }
 TAU = {"diff": 0.9971523284912109, "paper": 0.7737407684326172,
-       "batched": 1.8879261016845703}
+       "batched": 1.8879261016845703, "large": 2.1677913665771484}
 
 
 def make(name: str, pinned: bool = False, **over) -> AMR:

@@ -1,0 +1,60 @@
+"""The C-ABI library builds, loads and exports every symbol its header
+declares; host-only calls behave without a GPU (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "dvl.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dvl_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ["dvl_create", "dvl_destroy", "dvl_load_amr", "dvl_build_order", "dvl_set_tf",
+              "dvl_update", "dvl_read_bins"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2306_11612_b300 as dvl
+    lib = ctypes.CDLL(dvl._LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(dvl.EXPORTS) == set(_declared())
+
+
+def test_status_strings_and_null_handles():
+    import paper_2306_11612_b300 as dvl
+    L = dvl.lib
+    for code in range(-7, 1):
+        assert L.dvl_status_string(code).decode()
+    assert L.dvl_status_string(99).decode() == "unknown status"
+    assert L.dvl_last_error(None).decode() == ""
+    L.dvl_destroy(None)                      # no-op
+    assert L.dvl_update(None, None) == dvl.ERR_ARG
+    assert L.dvl_sync(None) == dvl.ERR_ARG
+    assert L.dvl_create(None, 0, None) == dvl.ERR_ARG
+
+
+def test_create_fails_loudly_without_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2306_11612_b300 as dvl
+    with pytest.raises(dvl.DVLError) as e:
+        dvl.DVL(0)
+    assert e.value.status == dvl.ERR_CUDA
+
+
+def test_kernels_are_built_for_sm103a():
+    # the build passes only -gencode arch=compute_103a,code=sm_103a
+    from paper_2306_11612_b300 import _build
+    assert "arch=compute_103a,code=sm_103a" in _build.ARCH
+    assert "-fmad=false" in _build.COMMON
