@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""DVL update throughput on B300: cells/s per alpha-TF edit.
+
+One step = one transfer-function edit of the whole data set: the four alpha
+tables change (host -> device, 4 KB) and one DVL update runs over every cell
+(TF alpha per field, variation, importance, fixed-point width, device-wide
+prefix scan, placement into W pixel bins, per-pixel mean and alpha).  The
+once-per-data-set curve order is built before the timed region.
+
+Workload (default): the 6-level synthetic AMR data set of ~414M cells with
+4 float32 fields (128^3 base cells, logical grid 4096^3, Hilbert order),
+W = 4096 pixels, P = 1, minimum importance 0.025, 256-entry TFs.  Inputs are
+seeded and synthetic (they stand in for the paper's Molecular Cloud data).
+The data set (~7 GB per pass) is far larger than L2, so no L2 flush is
+needed between steps.
+
+Output: one JSON line (rank 0).  Under torchrun every rank runs an
+independent replica (the per-edit path needs no exchange on one GPU per data
+set), timing is the max over ranks and ``value`` counts all ranks' cells.
+``--impl reference`` times the CPU oracle instead (rank 0 only, a bounded
+sample of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL_PASS = 4 * 4 + 1      # 4 float32 fields + 1 level byte, read once per pass
+CPU_SAMPLE_BOX = ((0, 0, 0), 32)     # 32^3 of the 128^3 base cells (1/64 of the domain)
+LAUNCHES_PER_UPDATE = 4              # prepare, width+scan pass, placement pass, finalize
+METRIC = "DVL update throughput (cells/s per alpha-TF edit)"
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="large")
+    ap.add_argument("--width", type=int, default=4096)
+    ap.add_argument("--P", type=float, default=1.0)
+    ap.add_argument("--min-importance", type=float, default=0.025)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline budget (rank 0)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region (read only: NVML, else nvidia-smi)
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+            "hw_thermal_slowdown": 0x40, "hw_power_brake_slowdown": 0x80}
+    SMI_COLS = ["clocks.sm", "clocks.max.sm", "clocks_event_reasons.hw_slowdown",
+                "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+                "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, device: int):
+        self.device = device
+        self.samples, self.reasons, self.max_mhz, self.source = [], set(), None, None
+        self._stop = threading.Event()
+        self.proc = None
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self.nv = pynvml
+            self.h = pynvml.nvmlDeviceGetHandleByIndex(device)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+            self.source = "nvml"
+        except Exception:
+            self.nv = None
+
+    def _run_nvml(self):
+        while not self._stop.is_set():
+            try:
+                self.samples.append(self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM))
+                mask = self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                self.reasons.update(k for k, b in self.BITS.items() if mask & b)
+            except Exception:
+                pass
+            time.sleep(0.01)
+
+    def __enter__(self):
+        if self.nv:
+            self.t = threading.Thread(target=self._run_nvml, daemon=True)
+            self.t.start()
+            return self
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + ",".join(self.SMI_COLS),
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.lines = []
+            self.t = threading.Thread(target=lambda: self.lines.extend(iter(self.proc.stdout.readline, "")),
+                                      daemon=True)
+            self.t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:   # first sample before timing
+                time.sleep(0.01)
+            self.skip = len(self.lines)
+            self.source = "nvidia-smi"
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self.nv:
+            self.t.join()
+        elif self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.t.join(timeout=2)
+            for ln in self.lines[max(self.skip - 1, 0):]:
+                f = [x.strip() for x in ln.split(",")]
+                if len(f) < 6:
+                    continue
+                try:
+                    self.samples.append(float(f[0]))
+                    self.max_mhz = float(f[1])
+                except ValueError:
+                    continue
+                for name, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"], f[2:6]):
+                    if v.lower() == "active":
+                        self.reasons.add(name)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0,
+                    "source": self.source}
+        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(self.samples), "source": self.source}
+
+
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def traffic_record():
+    """dram bytes per cell of each update kernel from the committed ncu
+    summary, used only while the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return {}
+    import hashlib
+    with open(p) as f:
+        rec = json.load(f)
+    src = os.path.join(ROOT, "paper_2306_11612_b300", "csrc", "update.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec.get("kernels", {}) if rec.get("update_cu_sha") == sha else {}
+
+
+def workload_desc(amr, args, name=None):
+    return {"workload": name or (f"{args.config}: {amr.meta.get('levels')}-level synthetic AMR, {amr.n} cells, "
+                                 f"4 fp32 fields, Hilbert order, W={args.width}"),
+            "n_cells": amr.n, "levels": amr.meta.get("levels"), "width": args.width, "P": args.P,
+            "min_importance": args.min_importance, "tf_entries": 256, "fields": 4,
+            "l2": "no flush: inputs (17 B/cell per pass) far larger than the 126 MB L2",
+            "step": "4 alpha TFs set from host + one dvl_update"}
+
+
+def tf_sequence(n, seed0=1000):
+    import synth
+    return [synth.random_tfs(seed0 + i) for i in range(n)]
+
+
+def cpu_sample(args):
+    import oracle
+    import synth
+    amr = synth.make(args.config, box=CPU_SAMPLE_BOX) if args.config != "small" else synth.make("small")
+    _, _, lev, fl = oracle.sorted_inputs(amr.lower, amr.level, amr.fields, oracle.SFC_HILBERT)
+    return amr, lev, fl
+
+
+def cpu_baseline(args, seconds):
+    """The oracle, as it stands, on a bounded contiguous piece of the workload."""
+    import oracle
+    amr, lev, fl = cpu_sample(args)
+    tfs = tf_sequence(64, 5000)
+    done, i, t0 = 0, 0, time.perf_counter()
+    while True:
+        oracle.update(fl, lev, tfs[i % len(tfs)], P=args.P, min_importance=args.min_importance, width=args.width)
+        done += amr.n
+        i += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": done / el, "unit": "cells/s", "cores": 1, "kind": "oracle",
+            "sample": f"{amr.n} cells = base cells {CPU_SAMPLE_BOX} of the {args.config} data set "
+                      f"(a contiguous run of its curve order), {i} updates in {el:.1f} s, single thread"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    amr, lev, fl = cpu_sample(args)
+    tfs = tf_sequence(args.steps + args.warmup)
+    kw = dict(P=args.P, min_importance=args.min_importance, width=args.width)
+    for i in range(args.warmup):
+        oracle.update(fl, lev, tfs[i], **kw)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.update(fl, lev, tfs[args.warmup + i], **kw)
+    el = time.perf_counter() - t0
+    value = amr.n * args.steps / el
+    name = f"{args.config} (CPU sample: base cells {CPU_SAMPLE_BOX}, {amr.n} cells), W={args.width}"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64",
+            "data": "synthetic", "config": workload_desc(amr, args, name),
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{amr.n} cells of the {args.config} data set per step"},
+            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2306_11612_b300 as dvl
+    import synth
+
+    t_gen = time.perf_counter()
+    amr = synth.make(args.config, pinned=True)
+    t_gen = time.perf_counter() - t_gen
+    # the library's kernels run on this stream; the timing events go on it too
+    stream = torch.cuda.Stream(local)
+    ctx = dvl.DVL(local, stream)
+    t0 = time.perf_counter()
+    ctx.load_amr(amr.lower, amr.level, amr.fields)
+    t_load = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ctx.build_order(dvl.SFC_HILBERT)
+    ctx.sync()
+    t_build = time.perf_counter() - t0
+    tfs = tf_sequence(args.steps + args.warmup)
+    kw = dict(P=args.P, min_importance=args.min_importance, width=args.width)
+
+    for i in range(args.warmup):
+        ctx.set_tfs(tfs[i])
+        ctx.update(**kw)
+    ctx.sync()
+    ctx.set_option(dvl.OPT_TIMING, 1)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for i in range(args.steps):
+            ctx.set_tfs(tfs[args.warmup + i])
+            ctx.update(**kw)
+        end.record(stream)
+        end.synchronize()
+    barrier()
+    ms = start.elapsed_time(end)
+    stages = ctx.get_timings()
+    ctx.set_option(dvl.OPT_TIMING, 0)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = amr.n * world * args.steps / (ms * 1e-3)
+
+    # end to end through the public API with host buffers: TFs up, bins down
+    e2e = None
+    if not args.no_e2e:
+        W = args.width
+        outs = [{k: torch.empty(W, dtype=dt, pin_memory=True).numpy() for k, dt in
+                 [("mean", torch.float32), ("min", torch.float32), ("max", torch.float32),
+                  ("y", torch.float32), ("sum", torch.float64), ("count", torch.int32)]} for _ in range(4)]
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            ctx.set_tfs(tfs[args.warmup + i])
+            ctx.update(**kw)
+            for m in range(4):
+                ctx.read_bins(m, outs[m])
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": amr.n * world * args.steps / el, "unit": "cells/s",
+               "h2d_bytes_per_step": 4 * 256 * 4 + 2 * 4 * 4, "d2h_bytes_per_step": 4 * W * (4 * 4 + 8 + 4),
+               "ms_per_step": el / args.steps * 1e3}
+
+    peak, peak_kind = measured_peak()
+    traffic = traffic_record()
+    kern = {}
+    for name, key in [("dvl_pass_a", "pass_a"), ("dvl_pass_b", "pass_b")]:
+        t_ms = stages[key]
+        gbs = BYTES_PER_CELL_PASS * amr.n / (t_ms * 1e-3) / 1e9
+        kern[name] = {"ms": t_ms, "achieved_gbs": gbs, "frac": gbs / peak}
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    tr = traffic.get(dom)
+    roofline = {"bound": "hbm", "achieved": kern[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                "frac": kern[dom]["achieved_gbs"] / peak, "kernel": dom,
+                "traffic": None if tr is None else tr["dram_bytes_per_cell"] * amr.n,
+                "algorithmic_bytes": BYTES_PER_CELL_PASS * amr.n,
+                "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json), burst copy" if peak_kind == "measured"
+                else "fallback 6.4 TB/s"}
+    step_gbs = 2 * BYTES_PER_CELL_PASS * amr.n / (ms / args.steps * 1e-3) / 1e9
+
+    line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64", "data": "synthetic",
+            "config": workload_desc(amr, args), "roofline": roofline,
+            "kernels": dict(kern, prepare_ms=stages["prepare"], finalize_ms=stages["finalize"],
+                            edit_gbs_vs_34B_per_cell=step_gbs, edit_frac_of_two_read_floor=step_gbs / peak),
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": LAUNCHES_PER_UPDATE * args.steps,
+            "setup_s": {"generate": t_gen, "load": t_load, "build_order": t_build}}
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -194,12 +194,13 @@ int dvl_read_widths(dvl_ctx* ctx, uint64_t* q, int mem_kind);
  * (DVL_ERR_TIMEOUT, DVL_ERR_RANGE) raised since the last synchronising call. */
 int dvl_sync(dvl_ctx* ctx);
 
-/* Device time of each stage of the last dvl_update, in milliseconds, from
- * CUDA events recorded on the context's stream between the kernels (only when
- * DVL_OPT_TIMING is 1; otherwise DVL_ERR_STATE).  ms[0] = constants and
- * clearing (plus the exact max-V pass if selected), ms[1] = width pass with the
- * prefix scan, ms[2] = placement/reduction pass, ms[3] = finalize.  `n` is
- * the capacity of ms (>= 4).  Synchronises. */
+/* Average device time per stage, in milliseconds, over the dvl_update calls
+ * made with DVL_OPT_TIMING = 1 since the previous dvl_get_timings (CUDA events
+ * recorded on the context's stream between the kernels).  ms[0] = constants
+ * and clearing (plus the exact max-V pass if selected), ms[1] = width pass
+ * with the prefix scan, ms[2] = placement/reduction pass, ms[3] = finalize;
+ * if n >= 5, ms[4] = number of updates averaged.  n >= 4.  Synchronises and
+ * resets the collection.  DVL_ERR_STATE if no timed update is pending. */
 int dvl_get_timings(dvl_ctx* ctx, double* ms, int n);
 
 /* Tuning and fault-injection options (for tests).
@@ -209,8 +210,9 @@ int dvl_get_timings(dvl_ctx* ctx, double* ms, int n);
  *                           scan never publishes its sum, so successors' waits
  *                           run out (tests DVL_ERR_TIMEOUT); reset after one
  *                           update.
- *   DVL_OPT_TIMING          1 = record per-stage CUDA events in dvl_update
- *                           (read with dvl_get_timings); 0 = off (default). */
+ *   DVL_OPT_TIMING          1 = record per-stage CUDA events in every
+ *                           dvl_update (read with dvl_get_timings); 0 = off
+ *                           (default). */
 enum { DVL_OPT_SPIN_LIMIT = 1, DVL_OPT_FAULT_NO_PUBLISH = 2, DVL_OPT_TIMING = 3 };
 int dvl_set_option(dvl_ctx* ctx, int option, int64_t value);
 

@@ -171,7 +171,8 @@ def alpha_grad(fields, level, ctrl, target, T=256, dom_lo=None, dom_hi=None, **k
 
 
 def sorted_inputs(lower, level, fields, sfc):
-    """Keys, permutation and the cells' level/fields gathered into curve order."""
+    """Sorted keys, permutation (perm[k] = input index of the k-th cell in
+    curve order) and the cells' level/fields gathered into curve order."""
     k = keys(lower, level, sfc)
     perm = order(k)
-    return k, perm, np.ascontiguousarray(level[perm]), np.ascontiguousarray(fields[:, perm])
+    return k[perm], perm, np.ascontiguousarray(level[perm]), np.ascontiguousarray(fields[:, perm])

@@ -260,11 +260,12 @@ class DVL:
     set_option = dvl_set_option
 
     def dvl_get_timings(self):
-        """Per-stage device ms of the last update (needs OPT_TIMING=1):
-        prepare, width pass + scan, placement pass, finalize."""
-        ms = (ctypes.c_double * 4)()
-        self._check(lib.dvl_get_timings(self._h, ms, 4))
-        return list(ms)
+        """Average device ms per stage over the updates timed since the last
+        call (needs OPT_TIMING=1): prepare, width pass + scan, placement
+        pass, finalize, and the number of updates."""
+        ms = (ctypes.c_double * 5)()
+        self._check(lib.dvl_get_timings(self._h, ms, 5))
+        return dict(prepare=ms[0], pass_a=ms[1], pass_b=ms[2], finalize=ms[3], updates=int(ms[4]))
 
     get_timings = dvl_get_timings
 

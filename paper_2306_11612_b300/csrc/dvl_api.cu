@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <string>
 #include <vector>
 
@@ -69,8 +70,7 @@ struct dvl_ctx {
     int64_t spin_limit = 1 << 22;
     int fault_no_publish = 0;
     int timing = 0;
-    bool timed_last = false;
-    cudaEvent_t ev[5] = {};
+    std::vector<std::array<cudaEvent_t, 5>> ev;   // one set per timed update
 };
 
 namespace {
@@ -244,8 +244,8 @@ void dvl_destroy(dvl_ctx* c)
     dfree(c->d_hist); dfree(c->d_rs_counters); dfree(c->d_tf); dfree(c->d_dom);
     dfree(c->d_sum); dfree(c->d_vmin); dfree(c->d_vmax); dfree(c->d_count);
     dfree(c->d_mean); dfree(c->d_y);
-    for (auto& e : c->ev)
-        if (e) cudaEventDestroy(e);
+    for (auto& set : c->ev)
+        for (auto e : set) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -263,11 +263,6 @@ int dvl_set_option(dvl_ctx* c, int option, int64_t value)
             return DVL_OK;
         case DVL_OPT_TIMING:
             c->timing = value ? 1 : 0;
-            if (c->timing && !c->ev[0]) {
-                cudaSetDevice(c->device);
-                for (auto& e : c->ev)
-                    if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "event");
-            }
             return DVL_OK;
         default:
             return fail(c, DVL_ERR_ARG, "unknown option %d", option);
@@ -337,8 +332,9 @@ int dvl_build_order(dvl_ctx* c, int sfc)
     CK(dalloc(c->d_keys_alt, n), "alloc keys");
     CK(dalloc(c->d_vals_alt, n), "alloc vals");
     const uint64_t rs_tiles = (n + RS_TILE - 1) / RS_TILE;
-    CK(dalloc(c->d_rs_status, rs_tiles * RS_RADIX), "alloc sort status");
-    CK(cudaMemsetAsync(c->d_rs_status, 0, (rs_tiles ? rs_tiles : 1) * RS_RADIX * 8, c->stream), "clear");
+    const uint64_t rs_words = (rs_tiles ? rs_tiles : 1) * RS_RADIX;
+    CK(dalloc(c->d_rs_status, rs_words), "alloc sort status");
+    CK(cudaMemsetAsync(c->d_rs_status, 0, rs_words * 8, c->stream), "clear");
     CK(cudaMemsetAsync(c->d_hist, 0, 8 * RS_RADIX * 4, c->stream), "clear");
     CK(cudaMemsetAsync(c->d_rs_counters, 0, 8 * 4, c->stream), "clear");
     CK(cudaMemsetAsync(&c->d_meta->key_or, 0, 8, c->stream), "clear");
@@ -354,7 +350,7 @@ int dvl_build_order(dvl_ctx* c, int sfc)
     uint32_t *vin = c->d_perm, *vout = c->d_vals_alt;
     for (int ps = 0; ps < passes; ++ps) {
         if (++c->epoch >= (1u << 24)) {     // tag space exhausted: clear and restart
-            CK(cudaMemsetAsync(c->d_rs_status, 0, rs_tiles * RS_RADIX * 8, c->stream), "clear");
+            CK(cudaMemsetAsync(c->d_rs_status, 0, rs_words * 8, c->stream), "clear");
             c->epoch = 1;
         }
         CK(launch_onesweep(c->stream, n, kin, vin, kout, vout, ps * RS_BITS, c->d_hist + ps * RS_RADIX,
@@ -515,9 +511,13 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
     rc = ensure_update_buffers(c, p->width);
     if (rc) return rc;
     UpdateArgs a = make_args(c, *p);
-    a.events = c->timing ? c->ev : nullptr;
+    if (c->timing) {
+        std::array<cudaEvent_t, 5> set{};
+        for (auto& e : set) CK(cudaEventCreate(&e), "create event");
+        c->ev.push_back(set);
+        a.events = c->ev.back().data();
+    }
     CK(launch_update(c->stream, a), "update kernels");
-    c->timed_last = c->timing != 0;
     c->fault_no_publish = 0;
     c->W_last = p->width;
     c->last_prm = *p;
@@ -619,14 +619,24 @@ int dvl_get_timings(dvl_ctx* c, double* ms, int n)
     if (!c) return DVL_ERR_ARG;
     c->last_error.clear();
     if (!ms || n < 4) return fail(c, DVL_ERR_ARG, "need room for 4 stage times");
-    if (!c->have_update || !c->timed_last) return fail(c, DVL_ERR_STATE, "last update was not timed");
+    if (c->ev.empty()) return fail(c, DVL_ERR_STATE, "no timed update since the last read");
     cudaSetDevice(c->device);
     CK(cudaStreamSynchronize(c->stream), "synchronize");
-    for (int k = 0; k < 4; ++k) {
-        float t = 0.0f;
-        CK(cudaEventElapsedTime(&t, c->ev[k], c->ev[k + 1]), "event time");
-        ms[k] = t;
-    }
+    double acc[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaSuccess;
+    for (auto& set : c->ev)
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+            float t = 0.0f;
+            e = cudaEventElapsedTime(&t, set[k], set[k + 1]);
+            acc[k] += t;
+        }
+    const double cnt = (double)c->ev.size();
+    for (auto& set : c->ev)
+        for (auto ev : set) cudaEventDestroy(ev);
+    c->ev.clear();
+    if (e != cudaSuccess) return cuda_fail(c, e, "event time");
+    for (int k = 0; k < 4; ++k) ms[k] = acc[k] / cnt;
+    if (n >= 5) ms[4] = cnt;
     return take_device_error(c);
 }
 

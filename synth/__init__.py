@@ -43,7 +43,8 @@ class _Cfg(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("base_n", ctypes.c_int32),
                 ("n_levels", ctypes.c_int32), ("brick", ctypes.c_int32),
                 ("n_refined", ctypes.c_int32), ("n_threads", ctypes.c_int32),
-                ("tau", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("tau", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("box_lo", ctypes.c_int32 * 3), ("box_n", ctypes.c_int32)]
 
 
 _lib = None
@@ -122,17 +123,24 @@ def bricks_amr(seed: int = 1, base_n: int = 32, brick: int = 8, n_refined: int =
 
 
 def threshold_amr(base_n: int, n_levels: int, tau: float, seed: int, pinned: bool = False,
-                  n_threads: int = 0) -> AMR:
-    """Threshold-refined AMR: a level-L cell splits while density noise > tau."""
+                  n_threads: int = 0, box=None) -> AMR:
+    """Threshold-refined AMR: a level-L cell splits while density noise > tau.
+
+    ``box = ((x, y, z), n)`` restricts the output to the base cells of that
+    sub-box (the same cells, fields and order as in the full data set)."""
     cfg = _Cfg(0, base_n, n_levels, 0, 0, n_threads, float(tau), seed)
-    nb = base_n ** 3
+    if box is not None:
+        cfg.box_lo[:] = [int(v) for v in box[0]]
+        cfg.box_n = int(box[1])
+    nb = (cfg.box_n or base_n) ** 3
     counts = np.empty(nb, np.uint32)
     n = _L().amrgen_count(ctypes.byref(cfg), counts.ctypes.data)
     offsets = np.zeros(nb, np.int64)
     np.cumsum(counts[:-1], out=offsets[1:])
     lower, level, fields = _alloc(int(n), pinned)
     _L().amrgen_fill(ctypes.byref(cfg), offsets.ctypes.data, *_ptrs(lower, level, fields))
-    meta = dict(kind="threshold", seed=seed, base_n=base_n, levels=n_levels, tau=float(tau))
+    meta = dict(kind="threshold", seed=seed, base_n=base_n, levels=n_levels, tau=float(tau),
+                box=None if box is None else [list(box[0]), int(box[1])])
     return AMR(lower, level, fields, base_n << (n_levels - 1), meta)
 
 
@@ -175,15 +183,16 @@ TAU = {"diff": 0.9971523284912109, "paper": 0.7737407684326172,
        "batched": 1.8879261016845703, "large": 2.1677913665771484}
 
 
-def make(name: str, pinned: bool = False, **over) -> AMR:
-    """Builds a named configuration (see the module docstring)."""
+def make(name: str, pinned: bool = False, box=None, **over) -> AMR:
+    """Builds a named configuration (see the module docstring); ``box``
+    selects a sub-box of base cells (see :func:`threshold_amr`)."""
     c = dict(CONFIGS[name], **over)
     if c["kind"] == "bricks":
         return bricks_amr(seed=c["seed"], pinned=pinned)
     tau = c.get("tau", TAU.get(name))
     if tau is None:
         tau = tau_for_target(c["base_n"], c["n_levels"], c["target"], c["seed"])
-    a = threshold_amr(c["base_n"], c["n_levels"], tau, c["seed"], pinned=pinned)
+    a = threshold_amr(c["base_n"], c["n_levels"], tau, c["seed"], pinned=pinned, box=box)
     a.meta["name"] = name
     return a
 

@@ -60,6 +60,8 @@ typedef struct {
     int32_t n_threads;     /* 0 = all online cores */
     double tau;            /* mode 0: refine when n1 > tau */
     uint64_t seed;
+    int32_t box_lo[3];     /* mode 0: only base cells in [box_lo, box_lo + box_n)^3 */
+    int32_t box_n;         /* 0 = the whole base grid */
 } amrgen_cfg;
 
 static inline uint64_t splitmix64(uint64_t x)
@@ -162,12 +164,21 @@ static void visit(const amrgen_cfg* c, int32_t lx, int32_t ly, int32_t lz, int l
     s->pos++;
 }
 
+/* b-th base cell of the selected box (z slowest, x fastest) */
 static void base_cell(const amrgen_cfg* c, int64_t b, int32_t xyz[3])
 {
-    int64_t n = c->base_n;
+    int64_t n = c->box_n > 0 ? c->box_n : c->base_n;
     xyz[0] = (int32_t)(b % n);
     xyz[1] = (int32_t)((b / n) % n);
     xyz[2] = (int32_t)(b / (n * n));
+    if (c->box_n > 0)
+        for (int d = 0; d < 3; ++d) xyz[d] += c->box_lo[d];
+}
+
+static int64_t n_base(const amrgen_cfg* c)
+{
+    int64_t n = c->box_n > 0 ? c->box_n : c->base_n;
+    return n * n * n;
 }
 
 typedef struct {
@@ -215,7 +226,7 @@ static int threads_for(const amrgen_cfg* c)
 static int64_t run_parallel(const amrgen_cfg* c, int64_t stride, int64_t offset,
                             uint32_t* counts, const int64_t* offsets, const sink* out)
 {
-    int64_t nb = (int64_t)c->base_n * c->base_n * c->base_n;
+    int64_t nb = n_base(c);
     int64_t nsel = nb > offset ? (nb - offset + stride - 1) / stride : 0;
     int T = threads_for(c);
     if (nsel < T) T = nsel > 0 ? (int)nsel : 1;
