@@ -216,6 +216,44 @@ int dvl_get_timings(dvl_ctx* ctx, double* ms, int n);
 enum { DVL_OPT_SPIN_LIMIT = 1, DVL_OPT_FAULT_NO_PUBLISH = 2, DVL_OPT_TIMING = 3 };
 int dvl_set_option(dvl_ctx* ctx, int option, int64_t value);
 
+/* One DVL update that allocates no device memory, for callers that must not
+ * call cudaMalloc or cudaFree at that point (a render or UI callback inside a
+ * memory budget owned by someone else, a process limited to a fixed pool, code
+ * that must not cause the device-wide synchronisation cudaFree implies).  The
+ * paper has no counterpart: it is an interface variant of dvl_update.
+ *
+ * Inputs and outputs are the caller's device buffers; no context is used.  The
+ * working memory beyond them lives in one fixed 4 MiB array inside the library
+ * that every GPU loading the library keeps until the process exits; this caps
+ * n_cells at 476,749,824 (larger counts return DVL_ERR_RANGE before any GPU
+ * work).  The first call on a device looks up that array's device address
+ * (with the device current); make that first call before any stream capture.
+ * All calls share the array and it keeps the previous call's contents (each
+ * call re-initialises what must start fresh), so calls that overlap on the GPU
+ * -- on different streams or host threads -- race and must be serialised by
+ * the caller.
+ *   cuda_stream  stream of the current device the work runs on (NULL = legacy
+ *                default stream); the call synchronises it before returning
+ *   fields       device, cells in curve order, field m at fields + m*pitch;
+ *                16-byte aligned, pitch a multiple of 4 and >= n_cells rounded
+ *                up to a multiple of 4 (the buffer must hold n_fields*pitch
+ *                floats; values finite)
+ *   level        device, n_cells levels rounded up to a multiple of 4 bytes,
+ *                4-byte aligned
+ *   alpha        device, n_fields x n_entries alpha tables in [0, 1]
+ *   domain       host, 2*n_fields floats: lo[0..M), hi[0..M); NaN/NaN = data
+ *                range (as dvl_set_tf)
+ *   params       as dvl_update
+ *   out          device buffers of n_fields*W (mean, min, max, y, sum) and W
+ *                (count) elements, field-major; all six required,
+ *                mem_kind = DVL_MEM_DEVICE
+ * Results equal dvl_update's for the same cells in the same order.  Errors:
+ * DVL_ERR_ARG, DVL_ERR_RANGE (size cap, non-finite value, width bound),
+ * DVL_ERR_TIMEOUT, DVL_ERR_CUDA. */
+int dvl_update_noalloc(void* cuda_stream, uint64_t n_cells, uint32_t n_fields, const float* fields,
+                       size_t pitch, const uint8_t* level, uint32_t n_entries, const float* alpha,
+                       const float* domain, const dvl_params* params, const dvl_bins* out);
+
 /* Static message for a status code. */
 const char* dvl_status_string(int status);
 

@@ -31,7 +31,8 @@ OPT_SPIN_LIMIT, OPT_FAULT_NO_PUBLISH, OPT_TIMING = 1, 2, 3
 
 EXPORTS = ["dvl_create", "dvl_destroy", "dvl_load_amr", "dvl_build_order", "dvl_set_fields",
            "dvl_set_tf", "dvl_update", "dvl_read_bins", "dvl_get_stats", "dvl_read_order",
-           "dvl_read_widths", "dvl_sync", "dvl_set_option", "dvl_get_timings", "dvl_status_string", "dvl_last_error"]
+           "dvl_read_widths", "dvl_sync", "dvl_set_option", "dvl_get_timings", "dvl_update_noalloc",
+           "dvl_status_string", "dvl_last_error"]
 
 
 class dvl_params(ctypes.Structure):
@@ -73,6 +74,8 @@ def _load():
         "dvl_sync": ([vp], i32),
         "dvl_set_option": ([vp, i32, ctypes.c_int64], i32),
         "dvl_get_timings": ([vp, ctypes.POINTER(ctypes.c_double), i32], i32),
+        "dvl_update_noalloc": ([vp, u64, u32, vp, ctypes.c_size_t, vp, u32, vp, vp,
+                                ctypes.POINTER(dvl_params), ctypes.POINTER(dvl_bins)], i32),
         "dvl_status_string": ([i32], ctypes.c_char_p),
         "dvl_last_error": ([vp], ctypes.c_char_p),
     }
@@ -272,3 +275,25 @@ class DVL:
     @property
     def handle(self):
         return self._h
+
+
+def dvl_update_noalloc(stream, fields, pitch, level, alpha, domain, out, P=1.0, min_importance=0.025,
+                       width=1024, min_imp_mode=0, vmax_mode=0, width_mode=0, n_cells=None):
+    """Allocation-free update over caller-owned CUDA tensors (see dvl.h).
+
+    ``fields``: float32 CUDA tensor holding M rows of ``pitch`` cells in curve
+    order; ``level``: uint8 CUDA tensor; ``alpha``: (M, T) float32 CUDA tensor;
+    ``domain``: 2M host floats; ``out``: dict of CUDA tensors mean/min/max/y
+    (float32, M*W), sum (float64, M*W), count (int32/uint32, W).  Returns the
+    status code (0 = ok) instead of raising, so callers can test rejections."""
+    M, T = int(alpha.shape[0]), int(alpha.shape[1])
+    n = int(level.shape[0]) if n_cells is None else int(n_cells)
+    dom = (ctypes.c_float * (2 * M))(*[float(x) for x in domain])
+    p = dvl_params(P, min_importance, width, min_imp_mode, vmax_mode, width_mode)
+    b = dvl_bins()
+    for k in ("mean", "min", "max", "y", "sum", "count"):
+        setattr(b, k, out[k].data_ptr())
+    b.mem_kind = MEM_DEVICE
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    return lib.dvl_update_noalloc(s, n, M, fields.data_ptr(), pitch, level.data_ptr(), T, alpha.data_ptr(),
+                                  dom, ctypes.byref(p), ctypes.byref(b))

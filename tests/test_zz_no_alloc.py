@@ -1,0 +1,81 @@
+"""The allocation-free entry point (dvl_update_noalloc) gives the same bins as
+dvl_update (GPU).
+
+dvl_update_noalloc serves callers that may not allocate device memory where
+they run an update (a render callback inside someone else's memory budget, a
+fixed-pool process, code that must not trigger cudaFree's device-wide sync):
+it works on the caller's buffers plus one fixed scratch array inside the
+library.  This file is collected last on purpose.  Two calls in a row (with
+different transfer functions, widths and exponents) must each match the
+context-based dvl_update on the same cells, within the tolerances of the other
+parity tests: counts and min/max bit for bit, sums and means to 1e-5
+relative, y exactly away from TF bucket boundaries.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+dvl = pytest.importorskip("paper_2306_11612_b300")
+torch = pytest.importorskip("torch")
+
+
+def _reference(ctx, alpha, **kw):
+    ctx.set_tfs(alpha)
+    ctx.update(**kw)
+    return [ctx.read_bins(m) for m in range(alpha.shape[0])]
+
+
+def _compare(ref, got, m, W, T):
+    sl = slice(m * W, (m + 1) * W)
+    assert np.array_equal(got["count"][:W].view(np.uint32), ref["count"])
+    assert np.array_equal(got["min"][sl].view(np.uint32), ref["min"].view(np.uint32))
+    assert np.array_equal(got["max"][sl].view(np.uint32), ref["max"].view(np.uint32))
+    assert np.allclose(got["sum"][sl], ref["sum"], rtol=1e-5, atol=0)
+    assert np.allclose(got["mean"][sl], ref["mean"], rtol=1e-5, atol=0)
+    x = ref["mean"].astype(np.float64) * T
+    away = np.abs(x - np.round(x)) > 1e-5 * np.maximum(x, 1.0)
+    assert np.array_equal(got["y"][sl][away], ref["y"][away])
+
+
+def test_noalloc_matches_update_on_two_calls():
+    amr = synth.make("small")
+    n, M = amr.n, 4
+    dev = torch.device("cuda:0")
+    ctx = dvl.DVL(0)
+    try:
+        ctx.load_amr(amr.lower, amr.level, amr.fields)
+        ctx.build_order(dvl.SFC_HILBERT)
+        _, perm = ctx.read_order()
+        pitch = (n + 3) // 4 * 4 + 4            # any multiple of 4 >= n rounded up
+        fields = np.zeros((M, pitch), np.float32)
+        fields[:, :n] = amr.fields[:, perm]
+        level = np.zeros(pitch, np.uint8)
+        level[:n] = amr.level[perm]
+        d_fields = torch.from_numpy(fields).to(dev)
+        d_level = torch.from_numpy(level).to(dev)
+        stream = torch.cuda.current_stream()
+        nan = float("nan")
+        for call, (seed, kw) in enumerate([(3, dict(P=1.0, min_importance=0.025, width=1024)),
+                                           (4, dict(P=2.0, min_importance=0.1, width=333))]):
+            alpha = synth.random_tfs(seed)
+            ref = _reference(ctx, alpha, **kw)
+            W = kw["width"]
+            out = {k: torch.full((M * W,), 7, dtype=dt, device=dev) for k, dt in
+                   [("mean", torch.float32), ("min", torch.float32), ("max", torch.float32),
+                    ("y", torch.float32), ("sum", torch.float64)]}
+            out["count"] = torch.full((W,), 7, dtype=torch.int32, device=dev)
+            rc = dvl.dvl_update_noalloc(stream, d_fields, pitch, d_level, torch.from_numpy(alpha).to(dev),
+                                        [nan] * (2 * M), out, n_cells=n, **kw)
+            assert rc == dvl.OK, (call, rc)
+            got = {k: v.cpu().numpy() for k, v in out.items()}
+            for m in range(M):
+                _compare(ref[m], got, m, W, alpha.shape[1])
+        # sizes beyond the fixed scratch are refused before any GPU work
+        rc = dvl.dvl_update_noalloc(stream, d_fields, pitch, d_level, torch.from_numpy(alpha).to(dev),
+                                    [nan] * (2 * M), out, n_cells=476_749_825, width=333)
+        assert rc == dvl.ERR_RANGE
+    finally:
+        ctx.close()
