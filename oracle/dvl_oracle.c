@@ -270,10 +270,11 @@ int orc_update(uint64_t n, uint32_t M, const float* fields, const uint8_t* level
     float inv_vmax = Vmax > 0.0f ? 1.0f / Vmax : 0.0f;
 
     /* Fixed-point widths.  Every width is f <= f_upper (each operation above is
-     * monotone for non-negative arguments and V <= 1), so with
-     * f_upper <= 2^e and n < 2^nb the widths q = rint(f * 2^Q) with
-     * Q = 62 - nb - e add up to less than 2^62: the prefix sum of Eq. 4 is then
-     * exact integer arithmetic and does not depend on summation order. */
+     * monotone for non-negative arguments and V <= 1), so with f_upper <= 2^e
+     * the widths q = rint(f * 2^Q) are at most 2^(Q+e).  Q + e is capped at 31
+     * (every width fits in 32 bits) and at 62 - nb for n < 2^nb cells (the
+     * total stays below 2^62): the prefix sum of Eq. 4 is then exact integer
+     * arithmetic and does not depend on summation order. */
     int max_level = 0;
     for (uint64_t c = 0; c < n; ++c)
         if (level[c] > max_level) max_level = level[c];
@@ -283,7 +284,9 @@ int orc_update(uint64_t n, uint32_t M, const float* fields, const uint8_t* level
     int ex = 0;
     frexpf(f_upper, &ex);                     /* f_upper <= 2^ex */
     if (!pow_is_exact(prm->P)) ex += 1;       /* powf is not monotone to the ulp */
-    int Q = 62 - bitlen64(n) - ex;
+    int cap = 62 - bitlen64(n);
+    if (cap > 31) cap = 31;
+    int Q = cap - ex;
     if (Q > 120) Q = 120;
     if (Q < -120) return -5;
     float scale = pow2f_int(Q);

@@ -7,18 +7,18 @@
 //               f (Eq. 3), fixed-point width q; per-warp-chunk sums and a
 //               single-pass decoupled look-back scan over tiles (Eq. 4) that
 //               leaves the exclusive prefix of every chunk and the total F.
-//   k_passB     recomputes q, scans it within each warp step, places every
-//               cell into the pixels its [E, E+q) span touches (Sec. 3.2) and
-//               reduces runs of cells with the same pixel in registers; global
-//               atomics only when the pixel changes or the chunk ends.
+//   k_passB     recomputes q, sums it per warp step, places every cell into
+//               the pixels its [E, E+q) span touches (Sec. 3.2) and reduces
+//               runs of cells with the same pixel in registers; global atomics
+//               only when the pixel changes or the chunk ends.
 //   k_finalize  per pixel: mean = sum / count, alpha of the mean (Sec. 3.3).
 //
-// Widths are integers q = rint(f * 2^Q) (u64); Q is chosen so that the total
-// stays below 2^62, so the prefix sum is exact and independent of summation
-// order and the cell-to-pixel assignment is bit-identical to a sequential CPU
-// evaluation.  Every float operation that decides an integer (TF entry,
-// width) is a correctly rounded float32 operation (explicit __f*_rn intrinsics;
-// this file is built with -fmad=false).
+// Widths are integers q = rint(f * 2^Q) < 2^32 with Q chosen so that the total
+// stays below 2^62: the prefix sum is exact and independent of summation order,
+// so the cell-to-pixel assignment is bit-identical to a sequential CPU
+// evaluation.  Every float operation that decides an integer (TF entry, width)
+// is a correctly rounded float32 operation (explicit __f*_r? intrinsics; this
+// file is built with -fmad=false).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,6 +32,10 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr unsigned long long FLAG_A = 1ull << 62;   // tile aggregate published
 constexpr unsigned long long FLAG_P = 2ull << 62;   // inclusive prefix published
 constexpr unsigned long long VAL_MASK = (1ull << 62) - 1;
+
+// exponent modes of the per-cell kernels: P == 1, or any other P (exact
+// products/sqrt when 2P is an integer in [0, 16], powf otherwise)
+enum { POW_ONE = 0, POW_GEN = 1 };
 
 __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p)
 {
@@ -53,24 +57,34 @@ __device__ __forceinline__ float ordered_to_float(uint32_t u)
 // 2^e as a float for -126 <= e <= 127 (exact).
 __device__ __forceinline__ float exp2i(int e) { return __int_as_float((127 + e) << 23); }
 
-// Normalised value t = clamp((v - lo) * s, 0, 1) (Sec. 3.3); NaN and -0 give +0.
+// Normalised value t = clamp((v - lo) * s, 0, 1) (Sec. 3.3).  The clamp works
+// on the bit pattern: negative values and -0 become +0, values above 1 (and
+// +inf) become 1.  NaN cannot occur: field values are finite (checked at
+// load), lo is finite and s is finite (k_prepare sets lo = 0 where s = 0).
 __device__ __forceinline__ float norm_t(float v, float lo, float s)
 {
-    float t = __fmul_rn(__fsub_rn(v, lo), s);
-    t = t > 0.0f ? t : 0.0f;
-    return t > 1.0f ? 1.0f : t;
+    int b = __float_as_int(__fmul_rn(__fsub_rn(v, lo), s));
+    b = min(max(b, 0), 0x3F800000);
+    return __int_as_float(b);
 }
 
-// TF entry of t: min(floor(t T), T - 1).
+// TF entry of t: min(floor(t T), T - 1) (used by the non-hot kernels).
 __device__ __forceinline__ uint32_t tf_entry(float t, float Tf, uint32_t Tm1)
 {
     uint32_t a = (uint32_t)__fmul_rn(t, Tf);    // t*T >= 0: truncation == floor
     return a < Tm1 ? a : Tm1;
 }
 
-// x^P (Eq. 2/3).  n2 = 2P for the exact modes: sqrt once if n2 is odd, then
-// left-to-right products; n2 < 0 selects powf.
-__device__ __forceinline__ float pow_steep(float x, int n2, float P)
+// floor(x) for 0 <= x < 2^23: adding 2^23 with round-toward-zero keeps the
+// integer part in the low mantissa bits.
+__device__ __forceinline__ uint32_t floor_small(float x)
+{
+    return __float_as_uint(__fadd_rz(x, 8388608.0f)) - 0x4B000000u;
+}
+
+// x^P with n2 = 2P for the exact modes (sqrt once if n2 is odd, then
+// left-to-right products); n2 < 0 selects powf.
+__device__ __forceinline__ float pow_gen(float x, int n2, float P)
 {
     if (n2 < 0) return powf(x, P);
     if (n2 == 0) return 1.0f;
@@ -82,65 +96,80 @@ __device__ __forceinline__ float pow_steep(float x, int n2, float P)
     return y;
 }
 
-// Per-cell constants held in registers by the update kernels.
-template <int M>
-struct CellConsts {
+// Eq. 3 with the minimum importance m.  Both placements in one branch-free
+// form: before-scale f = (max(r, m) 2^L)^P, after-power f = max((r 2^L)^P, m);
+// mb / ma hold m in the selected slot and 0 in the other (max with 0 is the
+// identity here since r >= +0 and x^P >= +0).
+template <int PM>
+__device__ __forceinline__ float importance(float V, uint32_t L, float inv_vmax, float mb, float ma, int wshift,
+                                            int n2, float P)
+{
+    float r = fmaxf(__fmul_rn(V, inv_vmax), mb);
+    float x = __fmul_rn(r, exp2i((int)L * wshift));
+    float f = PM == POW_ONE ? x : pow_gen(x, n2, P);
+    return fmaxf(f, ma);
+}
+
+// Per-cell constants in registers, specialised on the field count M and the
+// exponent mode.  The alpha tables live in shared memory with T+1 entries per
+// field (entry T repeats entry T-1) so that t = 1 needs no clamp.
+template <int M, int PM>
+struct Cell {
     float lo[M], s[M];
-    float inv_vmax, min_imp, qscale, P, Tf;
-    uint32_t Tm1;
-    int n2, mode, wshift;
+    float inv_vmax, mb, ma, qscale, P, Tf;
+    int n2, wshift, T1;
+    bool linear;
 
     __device__ __forceinline__ void load(const UpdateConsts* C, uint32_t T)
     {
 #pragma unroll
         for (int m = 0; m < M; ++m) { lo[m] = C->lo[m]; s[m] = C->s[m]; }
         inv_vmax = C->inv_vmax;
-        min_imp = C->min_imp;
+        const bool after = C->min_imp_mode == DVL_MINIMP_AFTER_POWER;
+        mb = after ? 0.0f : C->min_imp;
+        ma = after ? C->min_imp : 0.0f;
         qscale = C->qscale;
         P = C->P;
         n2 = C->pow_n2;
-        mode = C->min_imp_mode;
         wshift = C->width_shift;
         Tf = (float)T;
-        Tm1 = T - 1;
-    }
-
-    // Eq. 3 with the minimum importance; r = V * (1/maxV) (float32).
-    __device__ __forceinline__ float importance(float V, uint32_t L) const
-    {
-        float r = __fmul_rn(V, inv_vmax);
-        float sc = exp2i((int)L * wshift);
-        float f;
-        if (mode == DVL_MINIMP_BEFORE_SCALE) {
-            r = r < min_imp ? min_imp : r;
-            f = pow_steep(__fmul_rn(r, sc), n2, P);
-        } else {
-            f = pow_steep(__fmul_rn(r, sc), n2, P);
-            f = f < min_imp ? min_imp : f;
-        }
-        return f;
+        T1 = (int)T + 1;
+        linear = C->linear != 0;
     }
 
     // Eq. 1 over the M fields of one cell, from normalised values t[].
-    __device__ __forceinline__ float variation(const float* t, const float* s_tf, uint32_t T) const
+    __device__ __forceinline__ float variation(const float* t, const float* s_tf) const
     {
-        float hi = 0.0f, lw = 1.0f;
+        float hi = s_tf[floor_small(__fmul_rn(t[0], Tf))];
+        float lw = hi;
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            float al = s_tf[m * T + tf_entry(t[m], Tf, Tm1)];
+        for (int m = 1; m < M; ++m) {
+            float al = s_tf[m * T1 + floor_small(__fmul_rn(t[m], Tf))];
             hi = fmaxf(hi, al);
             lw = fminf(lw, al);
         }
         return __fsub_rn(hi, lw);
     }
 
-    __device__ __forceinline__ unsigned long long width(float f) const
+    // fixed-point width of a cell: rint(f 2^Q) (<= 2^31)
+    __device__ __forceinline__ uint32_t width(const float* t, uint32_t L, const float* s_tf) const
     {
-        return __float2ull_rn(__fmul_rn(f, qscale));
+        float f = importance<PM>(variation(t, s_tf), L, inv_vmax, mb, ma, wshift, n2, P);
+        return __float2uint_rn(__fmul_rn(f, qscale));
     }
 };
 
-// Loads 4 consecutive cells at idx (idx % 4 == 0; arrays padded).
+template <int M>
+__device__ __forceinline__ void load_table(float* s_tf, const float* tf, uint32_t T)
+{
+    const uint32_t T1 = T + 1;
+    for (uint32_t i = threadIdx.x; i < M * T1; i += blockDim.x) {
+        uint32_t m = i / T1, e = i - m * T1;
+        s_tf[i] = tf[m * T + (e < T ? e : T - 1)];
+    }
+}
+
+// Loads 4 consecutive cells at idx (idx % 4 == 0; rows padded to 4 cells).
 template <int M>
 __device__ __forceinline__ void load4(const float* __restrict__ val, size_t pitch,
                                       const uint8_t* __restrict__ lev, uint64_t idx,
@@ -159,6 +188,14 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
 #pragma unroll
     for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
     return x;
+}
+
+// Warp total of per-lane values below 2^35 (total below 2^40) with two redux adds.
+__device__ __forceinline__ unsigned long long warp_total_small(unsigned long long x)
+{
+    unsigned lo = __reduce_add_sync(FULL, (unsigned)(x & 0xFFFFFFull));
+    unsigned hi = __reduce_add_sync(FULL, (unsigned)(x >> 24));
+    return ((unsigned long long)hi << 24) + lo;
 }
 
 __device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long x, int lane)
@@ -183,23 +220,20 @@ __device__ void finish_consts(UpdateConsts* C, const UpdateArgs& a, uint32_t max
     const float vmax = C->vmax;
     const float inv = vmax > 0.0f ? __frcp_rn(vmax) : 0.0f;
     C->inv_vmax = inv;
-    CellConsts<1> cc;
-    cc.inv_vmax = inv;
-    cc.min_imp = C->min_imp;
-    cc.P = C->P;
-    cc.n2 = C->pow_n2;
-    cc.mode = C->min_imp_mode;
-    cc.wshift = C->width_shift;
-    float fu = cc.importance(vmax > 0.0f ? 1.0f : 0.0f, max_level);
+    const bool after = C->min_imp_mode == DVL_MINIMP_AFTER_POWER;
+    float fu = importance<POW_GEN>(vmax > 0.0f ? 1.0f : 0.0f, max_level, inv, after ? 0.0f : C->min_imp,
+                                   after ? C->min_imp : 0.0f, C->width_shift, C->pow_n2, C->P);
     C->f_upper = fu;
     int Q = 0;
     if (!isfinite(fu)) {
         atomicOr(a.err, ERR_RANGE);
     } else {
         int e = 0;
-        frexpf(fu, &e);
-        if (C->pow_n2 < 0) e += 1;
-        Q = 62 - bitlen64(a.n) - e;
+        frexpf(fu, &e);                       // fu <= 2^e
+        if (C->pow_n2 < 0) e += 1;            // powf is not monotone to the ulp
+        int cap = 62 - bitlen64(a.n);         // total below 2^62
+        if (cap > 31) cap = 31;               // every width below 2^32
+        Q = cap - e;
         if (Q > 120) Q = 120;
         if (Q < -120) { atomicOr(a.err, ERR_RANGE); Q = 0; }
     }
@@ -248,6 +282,9 @@ __global__ void k_prepare(UpdateArgs a, uint32_t n_tiles)
         if (isnan(lo) && isnan(hi)) { lo = dmin; hi = dmax; }
         float span = __fsub_rn(hi, lo);
         float s = (span > 0.0f && isfinite(span)) ? __frcp_rn(span) : 0.0f;
+        // s = 0 maps every value to t = 0; lo = 0 keeps (v - lo) * s finite
+        // (a range wider than the float range would otherwise give inf * 0)
+        lo = s == 0.0f ? 0.0f : lo;
         C->lo[tid] = lo;
         C->s[tid] = s;
         // Eq. 5: TF entries of the data minimum and maximum of this field
@@ -290,9 +327,9 @@ template <int M>
 __global__ __launch_bounds__(256) void k_vmax_exact(UpdateArgs a)
 {
     extern __shared__ float s_tf[];
-    for (uint32_t i = threadIdx.x; i < a.M * a.T; i += blockDim.x) s_tf[i] = a.tf[i];
+    load_table<M>(s_tf, a.tf, a.T);
     __syncthreads();
-    CellConsts<M> cc;
+    Cell<M, POW_GEN> cc;
     cc.load(a.consts, a.T);
     float best = 0.0f;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n;
@@ -300,7 +337,7 @@ __global__ __launch_bounds__(256) void k_vmax_exact(UpdateArgs a)
         float t[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) t[m] = norm_t(a.val[m * a.pitch + i], cc.lo[m], cc.s[m]);
-        best = fmaxf(best, cc.variation(t, s_tf, a.T));
+        best = fmaxf(best, cc.variation(t, s_tf));
     }
     for (int o = 16; o; o >>= 1) best = fmaxf(best, __shfl_xor_sync(FULL, best, o));
     if ((threadIdx.x & 31) == 0 && best > 0.0f)
@@ -313,37 +350,48 @@ __global__ void k_consts(UpdateArgs a) { finish_consts(a.consts, a, a.meta->max_
 // Pass A: widths, chunk sums, decoupled look-back scan over tiles
 // ---------------------------------------------------------------------------
 
-template <int M>
+template <int M, int PM, bool FULLSTEP>
+__device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, const UpdateArgs& a,
+                                                      const float* s_tf, uint64_t idx)
+{
+    float v[4][M];
+    uint32_t L4;
+    load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
+    unsigned long long acc = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float t[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) t[m] = norm_t(v[j][m], cc.lo[m], cc.s[m]);
+        uint32_t q = cc.width(t, (L4 >> (8 * j)) & 0xFF, s_tf);
+        if (FULLSTEP || idx + j < a.n) acc += q;
+    }
+    return acc;
+}
+
+template <int M, int PM>
 __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_tiles)
 {
     extern __shared__ float s_tf[];
     __shared__ unsigned long long s_wsum[WARPS];
     __shared__ uint32_t s_tile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (uint32_t i = tid; i < M * a.T; i += blockDim.x) s_tf[i] = a.tf[i];
+    load_table<M>(s_tf, a.tf, a.T);
     if (tid == 0) s_tile = atomicAdd(&a.counters[0], 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
-    CellConsts<M> cc;
+    Cell<M, PM> cc;
     cc.load(a.consts, a.T);
 
     const uint64_t base = ((uint64_t)tile * WARPS + warp) * CHUNK;
     unsigned long long acc = 0;
+    if (base + CHUNK <= a.n) {
 #pragma unroll 2
-    for (int st = 0; st < STEPS; ++st) {
-        const uint64_t idx = base + st * STEP + lane * 4;
-        if (idx < a.n) {
-            float v[4][M];
-            uint32_t L4;
-            load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float t[M];
-#pragma unroll
-                for (int m = 0; m < M; ++m) t[m] = norm_t(v[j][m], cc.lo[m], cc.s[m]);
-                float f = cc.importance(cc.variation(t, s_tf, a.T), (L4 >> (8 * j)) & 0xFF);
-                if (idx + j < a.n) acc += cc.width(f);
-            }
+        for (int st = 0; st < STEPS; ++st) acc += widths4<M, PM, true>(cc, a, s_tf, base + st * STEP + lane * 4);
+    } else {
+        for (int st = 0; st < STEPS; ++st) {
+            const uint64_t idx = base + st * STEP + lane * 4;
+            if (idx < a.n) acc += widths4<M, PM, false>(cc, a, s_tf, idx);
         }
     }
     acc = warp_sum_u64(acc);
@@ -489,88 +537,99 @@ struct Acc {
     }
 };
 
+// Exact placement of one lane's cells of a step that crosses a pixel
+// boundary; consecutive cells on the same pixel are merged per lane.
 template <int M>
+__device__ __noinline__ void place_slow(const UpdateArgs& a, const PixelMap& pm, const float (&t)[4][M],
+                                        const uint32_t (&q)[4], int nvalid, unsigned long long E)
+{
+    Acc<M> run;
+    run.reset();
+    uint32_t run_p = 0xFFFFFFFFu;
+    for (int j = 0; j < nvalid; ++j) {
+        const unsigned long long I = E + q[j];
+        const uint32_t b1 = pm.first_pixel(E);
+        const uint32_t b2 = I > E ? pm.last_pixel(I) : b1;
+        for (uint32_t p = b1; p <= b2; ++p) {
+            if (p != run_p) {
+                run.flush_to(a, run_p);
+                run.reset();
+                run_p = p;
+            }
+            run.add(t[j]);
+        }
+        E = I;
+    }
+    run.flush_to(a, run_p);
+}
+
+// One warp step of 128 cells (4 per lane).  FULLSTEP: all cells valid.
+template <int M, int PM, bool FULLSTEP>
+__device__ __forceinline__ void place_step(const UpdateArgs& a, const Cell<M, PM>& cc, const float* s_tf,
+                                           const PixelMap& pm, uint64_t idx, int lane, unsigned long long& pos,
+                                           uint32_t& cur, unsigned long long& hi_pos, Acc<M>& acc)
+{
+    const int nvalid = FULLSTEP ? 4 : (idx < a.n ? (a.n - idx < 4 ? (int)(a.n - idx) : 4) : 0);
+    float t[4][M];
+    uint32_t q[4] = {0, 0, 0, 0};
+    if (FULLSTEP || nvalid) {
+        float v[4][M];
+        uint32_t L4;
+        load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) t[j][m] = norm_t(v[j][m], cc.lo[m], cc.s[m]);
+            uint32_t w = cc.linear ? 1u : cc.width(t[j], (L4 >> (8 * j)) & 0xFF, s_tf);
+            q[j] = (FULLSTEP || j < nvalid) ? w : 0u;
+        }
+    }
+    const unsigned long long lsum = (unsigned long long)q[0] + q[1] + q[2] + q[3];
+    const unsigned long long I_last = pos + warp_total_small(lsum);
+    if (I_last < hi_pos) {
+        // every cell of the step lies inside pixel `cur` (pos >= C(cur) holds)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (FULLSTEP || j < nvalid) acc.add(t[j]);
+    } else {
+        acc.warp_flush(a, cur, lane);
+        const unsigned long long incl = warp_incl_scan_u64(lsum, lane);
+        place_slow<M>(a, pm, t, q, nvalid, pos + incl - lsum);
+        cur = pm.first_pixel(I_last);
+        hi_pos = pm.C(cur + 1);
+    }
+    pos = I_last;
+}
+
+template <int M, int PM>
 __global__ __launch_bounds__(WARPS * 32) void k_passB(UpdateArgs a)
 {
     extern __shared__ float s_tf[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (uint32_t i = tid; i < M * a.T; i += blockDim.x) s_tf[i] = a.tf[i];
+    load_table<M>(s_tf, a.tf, a.T);
     __syncthreads();
     const uint64_t chunk = (uint64_t)blockIdx.x * WARPS + warp;
     const uint64_t base = chunk * CHUNK;
     if (base >= a.n) return;
 
-    CellConsts<M> cc;
+    Cell<M, PM> cc;
     cc.load(a.consts, a.T);
     const UpdateConsts* C = a.consts;
-    const bool linear = C->linear != 0;
     PixelMap pm{C->F_div_W, C->F_mod_W, C->F, a.W};
 
-    unsigned long long pos = linear ? base : a.chunk_prefix[chunk];
+    unsigned long long pos = cc.linear ? base : a.chunk_prefix[chunk];
     uint32_t cur = pm.first_pixel(pos);
-    unsigned long long lo_pos = pm.C(cur), hi_pos = pm.C(cur + 1);
+    unsigned long long hi_pos = pm.C(cur + 1);
     Acc<M> acc;
     acc.reset();
 
-    for (int st = 0; st < STEPS; ++st) {
-        const uint64_t sbase = base + st * STEP;
-        if (sbase >= a.n) break;                        // warp-uniform
-        const uint64_t idx = sbase + lane * 4;
-        const int nvalid = idx < a.n ? (a.n - idx < 4 ? (int)(a.n - idx) : 4) : 0;
-        float t[4][M];
-        unsigned long long q[4] = {0, 0, 0, 0};
-        if (nvalid) {
-            float v[4][M];
-            uint32_t L4;
-            load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-#pragma unroll
-                for (int m = 0; m < M; ++m) t[j][m] = norm_t(v[j][m], cc.lo[m], cc.s[m]);
-                if (j < nvalid) {
-                    if (linear) q[j] = 1;
-                    else q[j] = cc.width(cc.importance(cc.variation(t[j], s_tf, a.T), (L4 >> (8 * j)) & 0xFF));
-                }
-            }
-        }
-        const unsigned long long lsum = q[0] + q[1] + q[2] + q[3];
-        const unsigned long long incl = warp_incl_scan_u64(lsum, lane);
-        const unsigned long long total = __shfl_sync(FULL, incl, 31);
-        const unsigned long long I_last = pos + total;
-
-        if (pos >= lo_pos && I_last < hi_pos) {
-            // every cell of the step lies inside pixel `cur`
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (j < nvalid) acc.add(t[j]);
-        } else {
-            acc.warp_flush(a, cur, lane);
-            // exact per-cell placement; merge consecutive equal pixels per lane
-            Acc<M> run;
-            run.reset();
-            uint32_t run_p = 0xFFFFFFFFu;
-            unsigned long long E = pos + incl - lsum;
-            for (int j = 0; j < nvalid; ++j) {
-                const unsigned long long I = E + q[j];
-                const uint32_t b1 = pm.first_pixel(E);
-                const uint32_t b2 = I > E ? pm.last_pixel(I) : b1;
-                for (uint32_t p = b1; p <= b2; ++p) {
-                    if (p != run_p) {
-                        run.flush_to(a, run_p);
-                        run.reset();
-                        run_p = p;
-                    }
-                    run.add(t[j]);
-                }
-                E = I;
-            }
-            run.flush_to(a, run_p);
-            cur = pm.first_pixel(I_last);
-            lo_pos = pm.C(cur);
-            hi_pos = pm.C(cur + 1);
-        }
-        pos = I_last;
-    }
+    const uint64_t rem = a.n - base;
+    const int full = rem >= (uint64_t)CHUNK ? STEPS : (int)(rem / STEP);
+#pragma unroll 1
+    for (int st = 0; st < full; ++st)
+        place_step<M, PM, true>(a, cc, s_tf, pm, base + st * STEP + lane * 4, lane, pos, cur, hi_pos, acc);
+    if (full < STEPS && base + (uint64_t)full * STEP < a.n)
+        place_step<M, PM, false>(a, cc, s_tf, pm, base + full * STEP + lane * 4, lane, pos, cur, hi_pos, acc);
     acc.warp_flush(a, cur, lane);
 }
 
@@ -604,17 +663,16 @@ template <int M>
 __global__ __launch_bounds__(256) void k_widths(UpdateArgs a, unsigned long long* q)
 {
     extern __shared__ float s_tf[];
-    for (uint32_t i = threadIdx.x; i < M * a.T; i += blockDim.x) s_tf[i] = a.tf[i];
+    load_table<M>(s_tf, a.tf, a.T);
     __syncthreads();
-    CellConsts<M> cc;
+    Cell<M, POW_GEN> cc;
     cc.load(a.consts, a.T);
-    const bool linear = a.consts->linear != 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         float t[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) t[m] = norm_t(a.val[m * a.pitch + i], cc.lo[m], cc.s[m]);
-        q[i] = linear ? 1ull : cc.width(cc.importance(cc.variation(t, s_tf, a.T), a.lev[i]));
+        q[i] = cc.linear ? 1ull : cc.width(t, a.lev[i], s_tf);
     }
 }
 
@@ -632,14 +690,26 @@ int grid_cap(uint64_t work, int threads)
     return b ? (int)b : 1;
 }
 
+template <int M, int PM>
+cudaError_t run_passes(cudaStream_t s, const UpdateArgs& a, uint32_t n_tiles, size_t smem)
+{
+    cudaError_t e;
+    if ((e = smem_attr(k_passA<M, PM>, smem)) != cudaSuccess) return e;
+    if ((e = smem_attr(k_passB<M, PM>, smem)) != cudaSuccess) return e;
+    if (a.events) cudaEventRecord(a.events[1], s);
+    if (n_tiles) k_passA<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles);
+    if (a.events) cudaEventRecord(a.events[2], s);
+    if (n_tiles) k_passB<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a);
+    if (a.events) cudaEventRecord(a.events[3], s);
+    return cudaSuccess;
+}
+
 template <int M>
 cudaError_t run_update(cudaStream_t s, const UpdateArgs& a)
 {
     const uint32_t n_tiles = (uint32_t)((a.n + TILE - 1) / TILE);
-    const size_t smem = (size_t)M * a.T * sizeof(float);
+    const size_t smem = (size_t)M * (a.T + 1) * sizeof(float);
     cudaError_t e;
-    if ((e = smem_attr(k_passA<M>, smem)) != cudaSuccess) return e;
-    if ((e = smem_attr(k_passB<M>, smem)) != cudaSuccess) return e;
     if ((e = smem_attr(k_vmax_exact<M>, smem)) != cudaSuccess) return e;
     const uint64_t clear = (uint64_t)a.M * a.W > n_tiles ? (uint64_t)a.M * a.W : n_tiles;
     if (a.events) cudaEventRecord(a.events[0], s);
@@ -648,11 +718,8 @@ cudaError_t run_update(cudaStream_t s, const UpdateArgs& a)
         k_vmax_exact<M><<<grid_cap(a.n, 256), 256, smem, s>>>(a);
         k_consts<<<1, 1, 0, s>>>(a);
     }
-    if (a.events) cudaEventRecord(a.events[1], s);
-    if (n_tiles) k_passA<M><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles);
-    if (a.events) cudaEventRecord(a.events[2], s);
-    if (n_tiles) k_passB<M><<<n_tiles, WARPS * 32, smem, s>>>(a);
-    if (a.events) cudaEventRecord(a.events[3], s);
+    e = a.prm.P == 1.0f ? run_passes<M, POW_ONE>(s, a, n_tiles, smem) : run_passes<M, POW_GEN>(s, a, n_tiles, smem);
+    if (e != cudaSuccess) return e;
     k_finalize<<<grid_cap((uint64_t)a.M * a.W, 256), 256, 0, s>>>(a);
     if (a.events) cudaEventRecord(a.events[4], s);
     return cudaGetLastError();
@@ -661,7 +728,7 @@ cudaError_t run_update(cudaStream_t s, const UpdateArgs& a)
 template <int M>
 cudaError_t run_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* q)
 {
-    const size_t smem = (size_t)M * a.T * sizeof(float);
+    const size_t smem = (size_t)M * (a.T + 1) * sizeof(float);
     cudaError_t e = smem_attr(k_widths<M>, smem);
     if (e != cudaSuccess) return e;
     if (a.n) k_widths<M><<<grid_cap(a.n, 256), 256, smem, s>>>(a, q);
