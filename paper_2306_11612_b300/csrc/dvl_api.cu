@@ -58,6 +58,7 @@ struct dvl_ctx {
     UpdateConsts* d_consts = nullptr;
     unsigned long long* d_tile_status = nullptr;
     unsigned long long* d_chunk_prefix = nullptr;
+    unsigned long long* d_step_sums = nullptr;
     uint32_t* d_counters = nullptr;
     // bins
     uint32_t W_cap = 0, W_last = 0;
@@ -124,7 +125,7 @@ void free_dataset(dvl_ctx* c)
     dfree(c->d_lower); dfree(c->d_level_in); dfree(c->d_fin);
     dfree(c->d_val); dfree(c->d_lev); dfree(c->d_perm); dfree(c->d_keys);
     dfree(c->d_keys_alt); dfree(c->d_vals_alt); dfree(c->d_rs_status);
-    dfree(c->d_tile_status); dfree(c->d_chunk_prefix);
+    dfree(c->d_tile_status); dfree(c->d_chunk_prefix); dfree(c->d_step_sums);
     c->state = 0;
     c->have_update = false;
 }
@@ -374,6 +375,7 @@ int dvl_build_order(dvl_ctx* c, int sfc)
     const uint64_t tiles = (n + TILE - 1) / TILE;
     CK(dalloc(c->d_tile_status, tiles), "alloc scan state");
     CK(dalloc(c->d_chunk_prefix, tiles * WARPS), "alloc scan state");
+    CK(dalloc(c->d_step_sums, tiles * WARPS * STEPS), "alloc scan state");
     int rc = take_device_error(c);
     if (rc) return rc;
     // the unsorted coordinates are no longer needed; fields stay for set_fields
@@ -483,6 +485,7 @@ static UpdateArgs make_args(dvl_ctx* c, const dvl_params& p)
     a.consts = c->d_consts;
     a.tile_status = c->d_tile_status;
     a.chunk_prefix = c->d_chunk_prefix;
+    a.step_sums = c->d_step_sums;
     a.counters = c->d_counters;
     a.sum = c->d_sum;
     a.vmin = c->d_vmin;

@@ -94,6 +94,8 @@ struct UpdateArgs {
     UpdateConsts* consts;
     unsigned long long* tile_status;   // n_tiles
     unsigned long long* chunk_prefix;  // n_chunks
+    unsigned long long* step_sums;     // n_chunks * STEPS width totals per warp step, or
+                                       // null (then the placement pass recomputes widths)
     uint32_t* counters;        // [0] tile ticket, [1] tiles done
     double* sum;               // M x W
     uint32_t* vmin;            // M x W (float bits)

@@ -7,10 +7,14 @@
 //               f (Eq. 3), fixed-point width q; per-warp-chunk sums and a
 //               single-pass decoupled look-back scan over tiles (Eq. 4) that
 //               leaves the exclusive prefix of every chunk and the total F.
-//   k_passB     recomputes q, sums it per warp step, places every cell into
-//               the pixels its [E, E+q) span touches (Sec. 3.2) and reduces
-//               runs of cells with the same pixel in registers; global atomics
-//               only when the pixel changes or the chunk ends.
+//   k_passB_steps  places every cell into the pixels its [E, E+q) span
+//               touches (Sec. 3.2): pass A's per-step width totals say which
+//               warp steps stay inside one pixel; those only read the field
+//               values and reduce them in registers, the few that cross a pixel
+//               boundary recompute their widths and are placed cell by cell
+//               (global atomics only when the pixel changes or the chunk ends).
+//   k_passB     the same without per-step totals (recomputes every width;
+//               used by the allocation-free entry point).
 //   k_finalize  per pixel: mean = sum / count, alpha of the mean (Sec. 3.3).
 //
 // Widths are integers q = rint(f * 2^Q) < 2^32 with Q chosen so that the total
@@ -350,13 +354,11 @@ __global__ void k_consts(UpdateArgs a) { finish_consts(a.consts, a, a.meta->max_
 // Pass A: widths, chunk sums, decoupled look-back scan over tiles
 // ---------------------------------------------------------------------------
 
+// Sum of the fixed-point widths of one lane's 4 cells (v, L4 already loaded).
 template <int M, int PM, bool FULLSTEP>
-__device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, const UpdateArgs& a,
-                                                      const float* s_tf, uint64_t idx)
+__device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, const UpdateArgs& a, const float* s_tf,
+                                                      uint64_t idx, const float (&v)[4][M], uint32_t L4)
 {
-    float v[4][M];
-    uint32_t L4;
-    load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
     unsigned long long acc = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -383,18 +385,40 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
     Cell<M, PM> cc;
     cc.load(a.consts, a.T);
 
-    const uint64_t base = ((uint64_t)tile * WARPS + warp) * CHUNK;
-    unsigned long long acc = 0;
+    const uint64_t chunk = (uint64_t)tile * WARPS + warp;
+    const uint64_t base = chunk * CHUNK;
+    unsigned long long* ss = a.step_sums ? a.step_sums + chunk * STEPS : nullptr;
+    unsigned long long acc = 0;            // chunk total (warp-uniform)
     if (base + CHUNK <= a.n) {
-#pragma unroll 2
-        for (int st = 0; st < STEPS; ++st) acc += widths4<M, PM, true>(cc, a, s_tf, base + st * STEP + lane * 4);
+        // all 8 steps full: loads of step st+1 are issued before step st is computed
+        float v[2][4][M];
+        uint32_t L4[2];
+        load4<M>(a.val, a.pitch, a.lev, base + lane * 4, v[0], L4[0]);
+#pragma unroll
+        for (int st = 0; st < STEPS; ++st) {
+            if (st + 1 < STEPS)
+                load4<M>(a.val, a.pitch, a.lev, base + (st + 1) * STEP + lane * 4, v[(st + 1) & 1], L4[(st + 1) & 1]);
+            const unsigned long long tot =
+                warp_total_small(widths4<M, PM, true>(cc, a, s_tf, 0, v[st & 1], L4[st & 1]));
+            acc += tot;
+            if (ss && lane == 0) ss[st] = tot;
+        }
     } else {
         for (int st = 0; st < STEPS; ++st) {
+            if (base + (uint64_t)st * STEP >= a.n) break;          // warp-uniform
             const uint64_t idx = base + st * STEP + lane * 4;
-            if (idx < a.n) acc += widths4<M, PM, false>(cc, a, s_tf, idx);
+            unsigned long long l = 0;
+            if (idx < a.n) {
+                float v[4][M];
+                uint32_t L4;
+                load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
+                l = widths4<M, PM, false>(cc, a, s_tf, idx, v, L4);
+            }
+            const unsigned long long tot = warp_total_small(l);
+            acc += tot;
+            if (ss && lane == 0) ss[st] = tot;
         }
     }
-    acc = warp_sum_u64(acc);
     if (lane == 0) s_wsum[warp] = acc;
     __syncthreads();
     if (warp != 0) return;
@@ -633,6 +657,135 @@ __global__ __launch_bounds__(WARPS * 32) void k_passB(UpdateArgs a)
     acc.warp_flush(a, cur, lane);
 }
 
+// Pass B when pass A left the width total of every warp step: a step whose
+// span [s_start, s_end) lies inside the current pixel needs only the cells'
+// normalised values (no levels, no TF lookups, no widths); a step that
+// crosses a pixel boundary is recomputed out of line and placed cell by cell.
+template <int M, int PM>
+__device__ __noinline__ void place_crossing_step(const UpdateArgs& a, const float* s_tf, const PixelMap& pm,
+                                                 uint64_t idx, unsigned long long s_start, int lane)
+{
+    // kept lean (this is the rare path): cells are re-read one at a time from
+    // the cache instead of being held in registers
+    Cell<M, PM> cc;
+    cc.load(a.consts, a.T);
+    const int nvalid = idx < a.n ? (a.n - idx < 4 ? (int)(a.n - idx) : 4) : 0;
+    auto cell = [&](int j, float (&t)[M]) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) t[m] = norm_t(__ldg(a.val + m * a.pitch + idx + j), cc.lo[m], cc.s[m]);
+    };
+    auto width = [&](int j) -> uint32_t {
+        float t[M];
+        cell(j, t);
+        return cc.linear ? 1u : cc.width(t, __ldg(a.lev + idx + j), s_tf);
+    };
+    unsigned long long lsum = 0;
+    for (int j = 0; j < nvalid; ++j) lsum += width(j);
+    unsigned long long E = s_start + warp_incl_scan_u64(lsum, lane) - lsum;
+    Acc<M> run;
+    run.reset();
+    uint32_t run_p = 0xFFFFFFFFu;
+    for (int j = 0; j < nvalid; ++j) {
+        float t[M];
+        cell(j, t);
+        const unsigned long long I = E + (cc.linear ? 1u : cc.width(t, __ldg(a.lev + idx + j), s_tf));
+        const uint32_t b1 = pm.first_pixel(E);
+        const uint32_t b2 = I > E ? pm.last_pixel(I) : b1;
+        for (uint32_t p = b1; p <= b2; ++p) {
+            if (p != run_p) {
+                run.flush_to(a, run_p);
+                run.reset();
+                run_p = p;
+            }
+            run.add(t);
+        }
+        E = I;
+    }
+    run.flush_to(a, run_p);
+}
+
+template <int M, int PM>
+__global__ __launch_bounds__(WARPS * 32, 3) void k_passB_steps(UpdateArgs a)
+{
+    extern __shared__ float s_tf[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    load_table<M>(s_tf, a.tf, a.T);
+    __syncthreads();
+    const uint64_t chunk = (uint64_t)blockIdx.x * WARPS + warp;
+    const uint64_t base = chunk * CHUNK;
+    if (base >= a.n) return;
+
+    const UpdateConsts* C = a.consts;
+    const bool linear = C->linear != 0;
+    PixelMap pm{C->F_div_W, C->F_mod_W, C->F, a.W};
+    float lo[M], sc[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) { lo[m] = C->lo[m]; sc[m] = C->s[m]; }
+
+    // start of the chunk and of each of its steps (lane st holds step st)
+    const unsigned long long pos0 = linear ? base : a.chunk_prefix[chunk];
+    unsigned long long ssum = 0;
+    if (lane < STEPS && base + (uint64_t)lane * STEP < a.n) {
+        const uint64_t left = a.n - (base + (uint64_t)lane * STEP);
+        ssum = linear ? (left < STEP ? left : STEP) : a.step_sums[chunk * STEPS + lane];
+    }
+    const unsigned long long send = pos0 + warp_incl_scan_u64(ssum, lane);   // end of step `lane`
+
+    uint32_t cur = pm.first_pixel(pos0);
+    unsigned long long hi_pos = pm.C(cur + 1);
+    Acc<M> acc;
+    acc.reset();
+
+    const uint64_t rem = a.n - base;
+    const int full = rem >= (uint64_t)CHUNK ? STEPS : (int)(rem / STEP);
+    // two register buffers alternate: step st is reduced from one while the
+    // loads of step st+1 fill the other (issued after the out-of-line call of
+    // a crossing step, so no buffer is live across it)
+    float4 bufA[M], bufB[M];
+    auto load_step = [&](float4 (&dst)[M], int st) {
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+            dst[m] = __ldg(reinterpret_cast<const float4*>(a.val + m * a.pitch + base + st * STEP + lane * 4));
+    };
+    auto do_step = [&](int st, float4 (&x)[M], float4 (&next)[M]) {
+        const unsigned long long s_end = __shfl_sync(FULL, send, st);
+        if (s_end < hi_pos) {
+            if (st + 1 < full) load_step(next, st + 1);
+            // the whole step lies inside pixel `cur` (its start is >= C(cur))
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float t[M];
+#pragma unroll
+                for (int m = 0; m < M; ++m)
+                    t[m] = norm_t(j == 0 ? x[m].x : j == 1 ? x[m].y : j == 2 ? x[m].z : x[m].w, lo[m], sc[m]);
+                acc.add(t);
+            }
+        } else {
+            acc.warp_flush(a, cur, lane);
+            const unsigned long long s_start = s_end - __shfl_sync(FULL, ssum, st);
+            place_crossing_step<M, PM>(a, s_tf, pm, base + st * STEP + lane * 4, s_start, lane);
+            cur = pm.first_pixel(s_end);
+            hi_pos = pm.C(cur + 1);
+            if (st + 1 < full) load_step(next, st + 1);
+        }
+    };
+    if (full > 0) load_step(bufA, 0);
+#pragma unroll 1
+    for (int st = 0; st < full; st += 2) {
+        do_step(st, bufA, bufB);
+        if (st + 1 < full) do_step(st + 1, bufB, bufA);
+    }
+    if (full < STEPS && base + (uint64_t)full * STEP < a.n) {
+        // ragged last step of the data set: place it exactly
+        const unsigned long long s_end = __shfl_sync(FULL, send, full);
+        const unsigned long long s_start = s_end - __shfl_sync(FULL, ssum, full);
+        acc.warp_flush(a, cur, lane);
+        place_crossing_step<M, PM>(a, s_tf, pm, base + full * STEP + lane * 4, s_start, lane);
+        cur = pm.first_pixel(s_end);
+    }
+    acc.warp_flush(a, cur, lane);
+}
+
 // ---------------------------------------------------------------------------
 // Finalize: ApplyWeights + ApplyTransFunc (Sec. 4)
 // ---------------------------------------------------------------------------
@@ -696,10 +849,16 @@ cudaError_t run_passes(cudaStream_t s, const UpdateArgs& a, uint32_t n_tiles, si
     cudaError_t e;
     if ((e = smem_attr(k_passA<M, PM>, smem)) != cudaSuccess) return e;
     if ((e = smem_attr(k_passB<M, PM>, smem)) != cudaSuccess) return e;
+    if ((e = smem_attr(k_passB_steps<M, PM>, smem)) != cudaSuccess) return e;
     if (a.events) cudaEventRecord(a.events[1], s);
     if (n_tiles) k_passA<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles);
     if (a.events) cudaEventRecord(a.events[2], s);
-    if (n_tiles) k_passB<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a);
+    if (n_tiles) {
+        if (a.step_sums)
+            k_passB_steps<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a);
+        else
+            k_passB<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a);
+    }
     if (a.events) cudaEventRecord(a.events[3], s);
     return cudaSuccess;
 }
