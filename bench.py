@@ -34,7 +34,14 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_CELL_PASS = 4 * 4 + 1      # 4 float32 fields + 1 level byte, read once per pass
+# Algorithmic bytes per cell.  Pass A reads the 4 float32 fields and the level
+# byte and writes one u64 width total per warp step (128 cells) and one u64
+# prefix per chunk (1024 cells); pass B reads the fields (levels only at the rare
+# pixel-crossing steps), the step totals and the chunk prefixes.
+SCAN_BYTES = 8 / 128 + 8 / 1024
+BYTES_PASS_A = 4 * 4 + 1 + SCAN_BYTES
+BYTES_PASS_B = 4 * 4 + SCAN_BYTES
+BYTES_EDIT = BYTES_PASS_A + BYTES_PASS_B
 CPU_SAMPLE_BOX = ((0, 0, 0), 32)     # 32^3 of the 128^3 base cells (1/64 of the domain)
 LAUNCHES_PER_UPDATE = 4              # prepare, width+scan pass, placement pass, finalize
 METRIC = "DVL update throughput (cells/s per alpha-TF edit)"
@@ -178,7 +185,7 @@ def workload_desc(amr, args, name=None):
                                  f"4 fp32 fields, Hilbert order, W={args.width}"),
             "n_cells": amr.n, "levels": amr.meta.get("levels"), "width": args.width, "P": args.P,
             "min_importance": args.min_importance, "tf_entries": 256, "fields": 4,
-            "l2": "no flush: inputs (17 B/cell per pass) far larger than the 126 MB L2",
+            "l2": "no flush: inputs (16-17 B/cell per pass, ~7 GB) far larger than the 126 MB L2",
             "step": "4 alpha TFs set from host + one dvl_update"}
 
 
@@ -323,26 +330,26 @@ def run_ours(args):
     peak, peak_kind = measured_peak()
     traffic = traffic_record()
     kern = {}
-    for name, key in [("dvl_pass_a", "pass_a"), ("dvl_pass_b", "pass_b")]:
+    for name, key, bpc in [("dvl_pass_a", "pass_a", BYTES_PASS_A), ("dvl_pass_b", "pass_b", BYTES_PASS_B)]:
         t_ms = stages[key]
-        gbs = BYTES_PER_CELL_PASS * amr.n / (t_ms * 1e-3) / 1e9
+        gbs = bpc * amr.n / (t_ms * 1e-3) / 1e9
         kern[name] = {"ms": t_ms, "achieved_gbs": gbs, "frac": gbs / peak}
     dom = max(kern, key=lambda k: kern[k]["ms"])
     tr = traffic.get(dom)
     roofline = {"bound": "hbm", "achieved": kern[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
                 "frac": kern[dom]["achieved_gbs"] / peak, "kernel": dom,
                 "traffic": None if tr is None else tr["dram_bytes_per_cell"] * amr.n,
-                "algorithmic_bytes": BYTES_PER_CELL_PASS * amr.n,
+                "algorithmic_bytes": (BYTES_PASS_A if dom == "dvl_pass_a" else BYTES_PASS_B) * amr.n,
                 "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json), burst copy" if peak_kind == "measured"
                 else "fallback 6.4 TB/s"}
-    step_gbs = 2 * BYTES_PER_CELL_PASS * amr.n / (ms / args.steps * 1e-3) / 1e9
+    step_gbs = BYTES_EDIT * amr.n / (ms / args.steps * 1e-3) / 1e9
 
     line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64", "data": "synthetic",
             "config": workload_desc(amr, args), "roofline": roofline,
             "kernels": dict(kern, prepare_ms=stages["prepare"], finalize_ms=stages["finalize"],
-                            edit_gbs_vs_34B_per_cell=step_gbs, edit_frac_of_two_read_floor=step_gbs / peak),
+                            edit_bytes_per_cell=BYTES_EDIT, edit_gbs=step_gbs, edit_frac=step_gbs / peak),
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": LAUNCHES_PER_UPDATE * args.steps,
             "setup_s": {"generate": t_gen, "load": t_load, "build_order": t_build}}
     if rank == 0 and not args.no_cpu_baseline and world == 1:

@@ -354,11 +354,14 @@ __global__ void k_consts(UpdateArgs a) { finish_consts(a.consts, a, a.meta->max_
 // Pass A: widths, chunk sums, decoupled look-back scan over tiles
 // ---------------------------------------------------------------------------
 
-// Sum of the fixed-point widths of one lane's 4 cells (v, L4 already loaded).
+// Sum of the fixed-point widths of one lane's 4 cells at idx.
 template <int M, int PM, bool FULLSTEP>
-__device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, const UpdateArgs& a, const float* s_tf,
-                                                      uint64_t idx, const float (&v)[4][M], uint32_t L4)
+__device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, const UpdateArgs& a,
+                                                      const float* s_tf, uint64_t idx)
 {
+    float v[4][M];
+    uint32_t L4;
+    load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
     unsigned long long acc = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -376,6 +379,7 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
 {
     extern __shared__ float s_tf[];
     __shared__ unsigned long long s_wsum[WARPS];
+    __shared__ unsigned long long s_lane[WARPS][STEPS][32];   // per-lane step sums
     __shared__ uint32_t s_tile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     load_table<M>(s_tf, a.tf, a.T);
@@ -387,38 +391,30 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
 
     const uint64_t chunk = (uint64_t)tile * WARPS + warp;
     const uint64_t base = chunk * CHUNK;
-    unsigned long long* ss = a.step_sums ? a.step_sums + chunk * STEPS : nullptr;
-    unsigned long long acc = 0;            // chunk total (warp-uniform)
+    unsigned long long acc = 0;
     if (base + CHUNK <= a.n) {
-        // all 8 steps full: loads of step st+1 are issued before step st is computed
-        float v[2][4][M];
-        uint32_t L4[2];
-        load4<M>(a.val, a.pitch, a.lev, base + lane * 4, v[0], L4[0]);
-#pragma unroll
+#pragma unroll 2
         for (int st = 0; st < STEPS; ++st) {
-            if (st + 1 < STEPS)
-                load4<M>(a.val, a.pitch, a.lev, base + (st + 1) * STEP + lane * 4, v[(st + 1) & 1], L4[(st + 1) & 1]);
-            const unsigned long long tot =
-                warp_total_small(widths4<M, PM, true>(cc, a, s_tf, 0, v[st & 1], L4[st & 1]));
-            acc += tot;
-            if (ss && lane == 0) ss[st] = tot;
+            const unsigned long long l = widths4<M, PM, true>(cc, a, s_tf, base + st * STEP + lane * 4);
+            s_lane[warp][st][lane] = l;
+            acc += l;
         }
     } else {
         for (int st = 0; st < STEPS; ++st) {
-            if (base + (uint64_t)st * STEP >= a.n) break;          // warp-uniform
             const uint64_t idx = base + st * STEP + lane * 4;
-            unsigned long long l = 0;
-            if (idx < a.n) {
-                float v[4][M];
-                uint32_t L4;
-                load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
-                l = widths4<M, PM, false>(cc, a, s_tf, idx, v, L4);
-            }
-            const unsigned long long tot = warp_total_small(l);
-            acc += tot;
-            if (ss && lane == 0) ss[st] = tot;
+            const unsigned long long l = idx < a.n ? widths4<M, PM, false>(cc, a, s_tf, idx) : 0ull;
+            s_lane[warp][st][lane] = l;
+            acc += l;
         }
     }
+    __syncwarp();
+    if (a.step_sums && lane < STEPS) {
+        // lane st adds up step st (rows rotated by lane to spread the banks)
+        unsigned long long tot = 0;
+        for (int k = 0; k < 32; ++k) tot += s_lane[warp][lane][(k + lane) & 31];
+        a.step_sums[chunk * STEPS + lane] = tot;
+    }
+    acc = warp_sum_u64(acc);
     if (lane == 0) s_wsum[warp] = acc;
     __syncthreads();
     if (warp != 0) return;
@@ -705,7 +701,7 @@ __device__ __noinline__ void place_crossing_step(const UpdateArgs& a, const floa
 }
 
 template <int M, int PM>
-__global__ __launch_bounds__(WARPS * 32, 3) void k_passB_steps(UpdateArgs a)
+__global__ __launch_bounds__(WARPS * 32) void k_passB_steps(UpdateArgs a)
 {
     extern __shared__ float s_tf[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -717,73 +713,87 @@ __global__ __launch_bounds__(WARPS * 32, 3) void k_passB_steps(UpdateArgs a)
 
     const UpdateConsts* C = a.consts;
     const bool linear = C->linear != 0;
-    PixelMap pm{C->F_div_W, C->F_mod_W, C->F, a.W};
-    float lo[M], sc[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) { lo[m] = C->lo[m]; sc[m] = C->s[m]; }
+    const PixelMap pm{C->F_div_W, C->F_mod_W, C->F, a.W};
+    const uint64_t rem = a.n - base;
+    const int full = rem >= (uint64_t)CHUNK ? STEPS : (int)(rem / STEP);      // steps with 128 cells
+    const int nsteps = rem >= (uint64_t)CHUNK ? STEPS : (int)((rem + STEP - 1) / STEP);
 
-    // start of the chunk and of each of its steps (lane st holds step st)
+    // Lane st describes step st: its span [s_start, s_end), the pixel of its
+    // start and whether the span leaves that pixel.  Full steps that stay in
+    // one pixel are reduced below without widths; the rest ("crossing" steps
+    // and the ragged last step) are placed exactly afterwards.
     const unsigned long long pos0 = linear ? base : a.chunk_prefix[chunk];
     unsigned long long ssum = 0;
-    if (lane < STEPS && base + (uint64_t)lane * STEP < a.n) {
+    if (lane < nsteps) {
         const uint64_t left = a.n - (base + (uint64_t)lane * STEP);
         ssum = linear ? (left < STEP ? left : STEP) : a.step_sums[chunk * STEPS + lane];
     }
-    const unsigned long long send = pos0 + warp_incl_scan_u64(ssum, lane);   // end of step `lane`
+    const unsigned long long s_end = pos0 + warp_incl_scan_u64(ssum, lane);
+    const unsigned long long s_start = s_end - ssum;
+    uint32_t pix = 0;
+    bool crossing = true;
+    if (lane < nsteps) {
+        pix = pm.first_pixel(s_start);
+        crossing = lane >= full || s_end >= pm.C(pix + 1);
+    }
+    const unsigned exact_mask = __ballot_sync(FULL, crossing) & ((1u << nsteps) - 1u);
 
-    uint32_t cur = pm.first_pixel(pos0);
-    unsigned long long hi_pos = pm.C(cur + 1);
+    float lo[M], sc[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) { lo[m] = C->lo[m]; sc[m] = C->s[m]; }
     Acc<M> acc;
     acc.reset();
+    uint32_t cur = __shfl_sync(FULL, pix, 0);
 
-    const uint64_t rem = a.n - base;
-    const int full = rem >= (uint64_t)CHUNK ? STEPS : (int)(rem / STEP);
-    // two register buffers alternate: step st is reduced from one while the
-    // loads of step st+1 fill the other (issued after the out-of-line call of
-    // a crossing step, so no buffer is live across it)
+    // phase 1: single-pixel steps, register double buffering, no calls
     float4 bufA[M], bufB[M];
     auto load_step = [&](float4 (&dst)[M], int st) {
 #pragma unroll
         for (int m = 0; m < M; ++m)
             dst[m] = __ldg(reinterpret_cast<const float4*>(a.val + m * a.pitch + base + st * STEP + lane * 4));
     };
-    auto do_step = [&](int st, float4 (&x)[M], float4 (&next)[M]) {
-        const unsigned long long s_end = __shfl_sync(FULL, send, st);
-        if (s_end < hi_pos) {
-            if (st + 1 < full) load_step(next, st + 1);
-            // the whole step lies inside pixel `cur` (its start is >= C(cur))
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float t[M];
-#pragma unroll
-                for (int m = 0; m < M; ++m)
-                    t[m] = norm_t(j == 0 ? x[m].x : j == 1 ? x[m].y : j == 2 ? x[m].z : x[m].w, lo[m], sc[m]);
-                acc.add(t);
-            }
-        } else {
+    // next single-pixel step after st (or STEPS)
+    auto next_fast = [&](int st) {
+        const unsigned above = st < 0 ? ~0u : ~((2u << st) - 1u);     // bits > st
+        const unsigned rest = ~exact_mask & ((1u << full) - 1u) & above;
+        return rest ? __ffs(rest) - 1 : STEPS;
+    };
+    auto reduce_step = [&](int st, const float4 (&x)[M]) {
+        const uint32_t p = __shfl_sync(FULL, pix, st);
+        if (p != cur) {                 // warp-uniform
             acc.warp_flush(a, cur, lane);
-            const unsigned long long s_start = s_end - __shfl_sync(FULL, ssum, st);
-            place_crossing_step<M, PM>(a, s_tf, pm, base + st * STEP + lane * 4, s_start, lane);
-            cur = pm.first_pixel(s_end);
-            hi_pos = pm.C(cur + 1);
-            if (st + 1 < full) load_step(next, st + 1);
+            cur = p;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float t[M];
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                t[m] = norm_t(j == 0 ? x[m].x : j == 1 ? x[m].y : j == 2 ? x[m].z : x[m].w, lo[m], sc[m]);
+            acc.add(t);
         }
     };
-    if (full > 0) load_step(bufA, 0);
+    int st = next_fast(-1);
+    if (st < STEPS) load_step(bufA, st);
 #pragma unroll 1
-    for (int st = 0; st < full; st += 2) {
-        do_step(st, bufA, bufB);
-        if (st + 1 < full) do_step(st + 1, bufB, bufA);
-    }
-    if (full < STEPS && base + (uint64_t)full * STEP < a.n) {
-        // ragged last step of the data set: place it exactly
-        const unsigned long long s_end = __shfl_sync(FULL, send, full);
-        const unsigned long long s_start = s_end - __shfl_sync(FULL, ssum, full);
-        acc.warp_flush(a, cur, lane);
-        place_crossing_step<M, PM>(a, s_tf, pm, base + full * STEP + lane * 4, s_start, lane);
-        cur = pm.first_pixel(s_end);
+    while (st < STEPS) {
+        const int s2 = next_fast(st);
+        if (s2 < STEPS) load_step(bufB, s2);
+        reduce_step(st, bufA);
+        if (s2 >= STEPS) break;
+        st = next_fast(s2);
+        if (st < STEPS) load_step(bufA, st);
+        reduce_step(s2, bufB);
     }
     acc.warp_flush(a, cur, lane);
+
+    // phase 2: steps placed cell by cell (rare on large data sets)
+    unsigned m2 = exact_mask;
+    while (m2) {
+        const int k = __ffs(m2) - 1;
+        m2 &= m2 - 1;
+        place_crossing_step<M, PM>(a, s_tf, pm, base + k * STEP + lane * 4, __shfl_sync(FULL, s_start, k), lane);
+    }
 }
 
 // ---------------------------------------------------------------------------
