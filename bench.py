@@ -36,9 +36,9 @@ sys.path.insert(0, ROOT)
 
 # Algorithmic bytes per cell.  Pass A reads the 4 float32 fields and the level
 # byte and writes one u64 width total per warp step (128 cells) and one u64
-# prefix per chunk (1024 cells); pass B reads the fields (levels only at the rare
+# prefix per chunk (2048 cells); pass B reads the fields (levels only at the rare
 # pixel-crossing steps), the step totals and the chunk prefixes.
-SCAN_BYTES = 8 / 128 + 8 / 1024
+SCAN_BYTES = 8 / 128 + 8 / 2048
 BYTES_PASS_A = 4 * 4 + 1 + SCAN_BYTES
 BYTES_PASS_B = 4 * 4 + SCAN_BYTES
 BYTES_EDIT = BYTES_PASS_A + BYTES_PASS_B

@@ -14,11 +14,11 @@ namespace dvl {
 // WARPS warps owns one tile of the device-wide prefix scan.  A lane handles 4
 // consecutive cells per step (one float4 per field, one u32 of levels).
 constexpr int WARPS = 8;
-constexpr int CHUNK = 1024;
+constexpr int CHUNK = 2048;
 constexpr int STEP = 128;                 // cells per warp step (32 lanes x 4)
 constexpr int STEPS = CHUNK / STEP;
-constexpr int TILE = WARPS * CHUNK;       // 8192 cells
-constexpr int PAD = 1024;                 // field/level arrays padded to this
+constexpr int TILE = WARPS * CHUNK;       // 16384 cells
+constexpr int PAD = 2048;                 // field/level arrays padded to a chunk
 
 // ---- radix sort geometry ---------------------------------------------------
 constexpr int RS_THREADS = 256;

@@ -23,13 +23,14 @@ namespace {
 using namespace dvl;
 
 // Fixed scratch: 4 MiB.  Header (constants, data range, counters, TF domain)
-// first, then 8 bytes of tile state and 64 bytes of chunk prefixes per scan
-// tile of TILE cells, which bounds the cell count (see kMaxCells).
+// first, then 8 bytes of tile state and 8 bytes of chunk prefix per warp for
+// every scan tile of TILE cells; kMaxCells is the documented cap, which fits.
 constexpr size_t kScratchBytes = 4u << 20;
 constexpr size_t kHeaderBytes = 4096;
 constexpr size_t kPerTileBytes = 8 + 8 * WARPS;
-constexpr uint64_t kMaxTiles = (kScratchBytes - kHeaderBytes) / kPerTileBytes;
-constexpr uint64_t kMaxCells = kMaxTiles * TILE;
+constexpr uint64_t kMaxCells = 476749824ull;                      // documented in dvl.h
+constexpr uint64_t kMaxTiles = (kMaxCells + TILE - 1) / TILE;
+static_assert(kHeaderBytes + kMaxTiles * kPerTileBytes <= kScratchBytes, "scratch too small for the cap");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 

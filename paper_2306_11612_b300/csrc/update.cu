@@ -839,10 +839,12 @@ __global__ __launch_bounds__(256) void k_widths(UpdateArgs a, unsigned long long
     }
 }
 
+// Opts the kernel in to `bytes` of dynamic shared memory.  Always set: the
+// 48 KB default covers static plus dynamic memory, and pass A has a static
+// array of its own.
 template <typename K>
 cudaError_t smem_attr(K kernel, size_t bytes)
 {
-    if (bytes <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 

@@ -2,7 +2,7 @@
 
 Keys, permutation, fixed-point widths, Q, F, counts and min/max are compared
 bit for bit; sums and means to 1e-5 relative; y exactly away from TF bucket
-boundaries (see tests/_cmp.py).  Sizes span several scan tiles (8192 cells)
+boundaries (see tests/_cmp.py).  Sizes span several scan tiles (16384 cells)
 and ragged tails; the edge cases are N = 0/1, N around tile and chunk sizes,
 W = 1, W > N, one field, eight fields, zero widths and the all-zero fallback.
 """
@@ -87,7 +87,8 @@ def _random_amr(seed, n, M):
     return np.ascontiguousarray(lo), lev, fields
 
 
-@pytest.mark.parametrize("n", [1, 3, 127, 128, 129, 1023, 1024, 1025, 4097, 8191, 8192, 8193, 20000, 70001])
+@pytest.mark.parametrize("n", [1, 3, 127, 128, 129, 1023, 1024, 1025, 2047, 2048, 2049, 4097, 8193,
+                               16383, 16384, 16385, 20000, 70001])
 def test_ragged_sizes(n):
     lo, lev, fields = _random_amr(n, n, 4)
     alpha = synth.random_tfs(n % 97)
