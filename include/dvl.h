@@ -70,7 +70,10 @@ enum { DVL_WIDTH_EDGE = 0, DVL_WIDTH_VOLUME = 1 };
  *                   DVL_MINIMP_AFTER_POWER:  f = max((V/maxV 2^L)^P, m)
  *   vmax_mode       DVL_VMAX_APPROX: max V from the TF entries the data range
  *                   reaches (Sec. 3.4, Eq. 5/6); DVL_VMAX_EXACT: max over cells.
- *   width_mode      DVL_WIDTH_EDGE: scale 2^L; DVL_WIDTH_VOLUME: 8^L (Sec. 3.1). */
+ *   width_mode      DVL_WIDTH_EDGE: scale 2^L; DVL_WIDTH_VOLUME: 8^L (Sec. 3.1).
+ *   want_alpha      1 = also accumulate, per field and pixel, the mean of the
+ *                   cells' TF alpha (read with dvl_read_alpha_means; needed by
+ *                   dvl_backward); 0 = not (default, slightly faster). */
 typedef struct {
     float P;
     float min_importance;
@@ -78,6 +81,7 @@ typedef struct {
     uint32_t min_imp_mode;
     uint32_t vmax_mode;
     uint32_t width_mode;
+    uint32_t want_alpha;
 } dvl_params;
 
 /* Destination of dvl_read_bins for one field.  Each pointer may be NULL
@@ -170,6 +174,40 @@ int dvl_set_tf(dvl_ctx* ctx, uint32_t field, const float* alpha, uint32_t n_entr
  * call. */
 int dvl_update(dvl_ctx* ctx, const dvl_params* params);
 
+/* Sets every field's alpha table from K control points per field
+ * (differentiable parameterisation; not in the paper, whose TFs are edited
+ * directly): control point k sits at k/(K-1), table entry e at e/(T-1) is the
+ * linear interpolation of its two neighbouring control points, evaluated in
+ * float32 as x = e(K-1)/(T-1), k0 = floor(x) (at most K-2), w = x - k0,
+ * A = c[k0] + w (c[k0+1] - c[k0]).
+ *   ctrl     M x K floats in [0, 1] (field-major), host or device per mem_kind
+ *   K        2..1024 control points; T: 2..DVL_MAX_TF_ENTRIES entries
+ *   domain   2*M floats lo[M], hi[M] (host; NaN/NaN = data range) or NULL
+ *            for the data range of every field
+ * The tables stay on the device (no host round trip).  Errors: DVL_ERR_ARG,
+ * DVL_ERR_STATE (no data loaded); control points outside [0, 1] in device
+ * memory are reported as DVL_ERR_RANGE by the next synchronising call. */
+int dvl_set_tf_ctrl(dvl_ctx* ctx, const float* ctrl, uint32_t K, uint32_t T, const float* domain,
+                    int mem_kind);
+
+/* Per-pixel mean of the cells' TF alpha of the last update (which must have
+ * had want_alpha = 1): abar[m][p] = (1/count_p) sum over the cells covering
+ * pixel p of A_m[entry_m(cell)] -- the differentiable counterpart of the bin
+ * mean (the mean of the normalised value has zero gradient with respect to the
+ * TF).  out: M x W floats (field-major), host or device.  Synchronises. */
+int dvl_read_alpha_means(dvl_ctx* ctx, float* out, int mem_kind);
+
+/* Adjoint of dvl_read_alpha_means with the cell-to-pixel assignment and the
+ * cells' TF entries held fixed at the last update: given g[m][p] = dL/dabar,
+ * returns dL/dctrl[m][k] = sum_e (sum over (cell, pixel) pairs with entry e of
+ * g[m][p] / count_p) * dA_m[e]/dctrl[m][k] (the interpolation weights of
+ * dvl_set_tf_ctrl, in float64).  Needs an update with want_alpha = 1 after
+ * dvl_set_tf_ctrl.
+ *   grad_abar   M x W floats, memory kind mem_in
+ *   grad_ctrl   M x K floats (output), memory kind mem_out
+ * Synchronises.  Errors: DVL_ERR_ARG, DVL_ERR_STATE. */
+int dvl_backward(dvl_ctx* ctx, const float* grad_abar, int mem_in, float* grad_ctrl, int mem_out);
+
 /* Copies the bins of one field of the last update into `out` (see dvl_bins).
  * Synchronises the context's stream for host destinations; device
  * destinations are copied on the stream and the call then synchronises too,
@@ -243,7 +281,7 @@ int dvl_set_option(dvl_ctx* ctx, int option, int64_t value);
  *   alpha        device, n_fields x n_entries alpha tables in [0, 1]
  *   domain       host, 2*n_fields floats: lo[0..M), hi[0..M); NaN/NaN = data
  *                range (as dvl_set_tf)
- *   params       as dvl_update
+ *   params       as dvl_update (want_alpha must be 0)
  *   out          device buffers of n_fields*W (mean, min, max, y, sum) and W
  *                (count) elements, field-major; all six required,
  *                mem_kind = DVL_MEM_DEVICE

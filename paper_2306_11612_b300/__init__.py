@@ -31,14 +31,14 @@ OPT_SPIN_LIMIT, OPT_FAULT_NO_PUBLISH, OPT_TIMING = 1, 2, 3
 
 EXPORTS = ["dvl_create", "dvl_destroy", "dvl_load_amr", "dvl_build_order", "dvl_set_fields",
            "dvl_set_tf", "dvl_update", "dvl_read_bins", "dvl_get_stats", "dvl_read_order",
-           "dvl_read_widths", "dvl_sync", "dvl_set_option", "dvl_get_timings", "dvl_update_noalloc",
+           "dvl_read_widths", "dvl_sync", "dvl_set_option", "dvl_get_timings", "dvl_update_noalloc", "dvl_set_tf_ctrl", "dvl_read_alpha_means", "dvl_backward",
            "dvl_status_string", "dvl_last_error"]
 
 
 class dvl_params(ctypes.Structure):
     _fields_ = [("P", ctypes.c_float), ("min_importance", ctypes.c_float), ("width", ctypes.c_uint32),
                 ("min_imp_mode", ctypes.c_uint32), ("vmax_mode", ctypes.c_uint32),
-                ("width_mode", ctypes.c_uint32)]
+                ("width_mode", ctypes.c_uint32), ("want_alpha", ctypes.c_uint32)]
 
 
 class dvl_bins(ctypes.Structure):
@@ -76,6 +76,9 @@ def _load():
         "dvl_get_timings": ([vp, ctypes.POINTER(ctypes.c_double), i32], i32),
         "dvl_update_noalloc": ([vp, u64, u32, vp, ctypes.c_size_t, vp, u32, vp, vp,
                                 ctypes.POINTER(dvl_params), ctypes.POINTER(dvl_bins)], i32),
+        "dvl_set_tf_ctrl": ([vp, vp, u32, u32, vp, i32], i32),
+        "dvl_read_alpha_means": ([vp, vp, i32], i32),
+        "dvl_backward": ([vp, vp, i32, vp, i32], i32),
         "dvl_status_string": ([i32], ctypes.c_char_p),
         "dvl_last_error": ([vp], ctypes.c_char_p),
     }
@@ -198,12 +201,46 @@ class DVL:
         for m in range(len(alphas)):
             self.set_tf(m, alphas[m], math.nan if lo is None else lo[m], math.nan if hi is None else hi[m])
 
-    def dvl_update(self, P=1.0, min_importance=0.025, width=1024, min_imp_mode=0, vmax_mode=0, width_mode=0):
-        p = dvl_params(P, min_importance, width, min_imp_mode, vmax_mode, width_mode)
+    def dvl_update(self, P=1.0, min_importance=0.025, width=1024, min_imp_mode=0, vmax_mode=0, width_mode=0,
+                   want_alpha=0):
+        p = dvl_params(P, min_importance, width, min_imp_mode, vmax_mode, width_mode, want_alpha)
         self._check(lib.dvl_update(self._h, ctypes.byref(p)))
         self.W = width
 
     update = dvl_update
+
+    def dvl_set_tf_ctrl(self, ctrl, n_entries: int = 256, domain=None):
+        """Alpha tables of all fields from (M, K) control points in [0, 1]
+        (numpy / CPU tensor, or CUDA tensor: stays on the device)."""
+        p, kind, keep = _ptr_kind(ctrl)
+        dom = None
+        if domain is not None:
+            dom = (ctypes.c_float * (2 * self.M))(*[float(x) for x in domain])
+        self._K = int(ctrl.shape[1])
+        self._check(lib.dvl_set_tf_ctrl(self._h, p, self._K, n_entries, dom, kind))
+
+    set_tf_ctrl = dvl_set_tf_ctrl
+
+    def dvl_read_alpha_means(self, out=None):
+        """(M, W) per-pixel mean of the cells' alpha (last update with want_alpha=1)."""
+        if out is None:
+            out = np.empty((self.M, self.W), np.float32)
+        p, kind, keep = _ptr_kind(out)
+        self._check(lib.dvl_read_alpha_means(self._h, p, kind))
+        return out
+
+    read_alpha_means = dvl_read_alpha_means
+
+    def dvl_backward(self, grad_abar, out=None):
+        """dL/dctrl (M, K) from dL/dabar (M, W), assignment frozen at the last update."""
+        gp, gkind, gkeep = _ptr_kind(grad_abar)
+        if out is None:
+            out = np.empty((self.M, self._K), np.float32)
+        op, okind, okeep = _ptr_kind(out)
+        self._check(lib.dvl_backward(self._h, gp, gkind, op, okind))
+        return out
+
+    backward = dvl_backward
 
     def dvl_read_bins(self, field: int, out: dict | None = None) -> dict:
         """Bins of one field.  ``out`` may map names (mean, min, max, y, sum,

@@ -51,6 +51,9 @@ struct dvl_ctx {
     std::vector<float> h_tf, h_dom;
     std::vector<char> tf_set;
     bool tf_dirty = false;
+    bool tf_device = false;           // tables built on the device from control points
+    uint32_t K_ctrl = 0;
+    float* d_ctrl = nullptr;          // M x K control points
     float* d_tf = nullptr;
     float* d_dom = nullptr;
     size_t tf_cap = 0;
@@ -66,6 +69,14 @@ struct dvl_ctx {
     double* d_sum = nullptr;
     uint32_t *d_vmin = nullptr, *d_vmax = nullptr, *d_count = nullptr;
     float *d_mean = nullptr, *d_y = nullptr;
+    double* d_asum = nullptr;         // alpha sums / means (want_alpha)
+    float* d_amean = nullptr;
+    uint32_t alpha_cap = 0;
+    double* d_gtab = nullptr;         // adjoint scratch (M x T)
+    float* d_gin = nullptr;           // M x W
+    float* d_gout = nullptr;          // M x K
+    size_t gtab_cap = 0, gin_cap = 0, gout_cap = 0;
+    bool last_alpha = false;
     dvl_params last_prm{};
     // options
     int64_t spin_limit = 1 << 22;
@@ -244,7 +255,8 @@ void dvl_destroy(dvl_ctx* c)
     dfree(c->d_meta); dfree(c->d_err); dfree(c->d_consts); dfree(c->d_counters);
     dfree(c->d_hist); dfree(c->d_rs_counters); dfree(c->d_tf); dfree(c->d_dom);
     dfree(c->d_sum); dfree(c->d_vmin); dfree(c->d_vmax); dfree(c->d_count);
-    dfree(c->d_mean); dfree(c->d_y);
+    dfree(c->d_mean); dfree(c->d_y); dfree(c->d_asum); dfree(c->d_amean); dfree(c->d_ctrl);
+    dfree(c->d_gtab); dfree(c->d_gin); dfree(c->d_gout);
     for (auto& set : c->ev)
         for (auto e : set) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -416,6 +428,11 @@ int dvl_set_tf(dvl_ctx* c, uint32_t field, const float* alpha, uint32_t T, float
     const bool dflt = std::isnan(lo) && std::isnan(hi);
     if (!dflt && !(std::isfinite(lo) && std::isfinite(hi) && lo < hi))
         return fail(c, DVL_ERR_ARG, "domain must be finite with lo < hi, or NaN/NaN");
+    if (c->tf_device) {       // leaving control-point mode: every field needs a host table again
+        c->tf_device = false;
+        c->tf_set.assign(c->M, 0);
+        c->T = 0;
+    }
     if (T != c->T) {          // a new table size invalidates the other fields' tables
         c->T = T;
         c->h_tf.assign((size_t)c->M * T, 0.0f);
@@ -436,7 +453,8 @@ static int check_params(dvl_ctx* c, const dvl_params* p)
     if (!(p->min_importance >= 0.0f) || !std::isfinite(p->min_importance))
         return fail(c, DVL_ERR_ARG, "min_importance must be finite and >= 0");
     if (p->width < 1 || p->width > DVL_MAX_WIDTH) return fail(c, DVL_ERR_ARG, "width must be in [1, %d]", DVL_MAX_WIDTH);
-    if (p->min_imp_mode > 1 || p->vmax_mode > 1 || p->width_mode > 1) return fail(c, DVL_ERR_ARG, "bad mode");
+    if (p->min_imp_mode > 1 || p->vmax_mode > 1 || p->width_mode > 1 || p->want_alpha > 1)
+        return fail(c, DVL_ERR_ARG, "bad mode");
     return DVL_OK;
 }
 
@@ -449,8 +467,9 @@ static int ensure_update_buffers(dvl_ctx* c, uint32_t W)
             CK(dalloc(c->d_dom, 2 * DVL_MAX_FIELDS), "alloc TF domain");
             c->tf_cap = need;
         }
-        CK(cudaMemcpyAsync(c->d_tf, c->h_tf.data(), need * sizeof(float), cudaMemcpyHostToDevice, c->stream),
-           "copy TF");
+        if (!c->tf_device)
+            CK(cudaMemcpyAsync(c->d_tf, c->h_tf.data(), need * sizeof(float), cudaMemcpyHostToDevice, c->stream),
+               "copy TF");
         CK(cudaMemcpyAsync(c->d_dom, c->h_dom.data(), 2 * c->M * sizeof(float), cudaMemcpyHostToDevice,
                            c->stream), "copy TF domain");
         c->tf_dirty = false;
@@ -465,6 +484,17 @@ static int ensure_update_buffers(dvl_ctx* c, uint32_t W)
         CK(dalloc(c->d_y, MW), "alloc bins");
         CK(dalloc(c->d_count, W), "alloc bins");
         c->W_cap = W;
+    }
+    return DVL_OK;
+}
+
+static int ensure_alpha_buffers(dvl_ctx* c, uint32_t W)
+{
+    if (W > c->alpha_cap) {
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        CK(dalloc(c->d_asum, (size_t)c->M * W), "alloc alpha sums");
+        CK(dalloc(c->d_amean, (size_t)c->M * W), "alloc alpha means");
+        c->alpha_cap = W;
     }
     return DVL_OK;
 }
@@ -493,6 +523,8 @@ static UpdateArgs make_args(dvl_ctx* c, const dvl_params& p)
     a.count = c->d_count;
     a.mean = c->d_mean;
     a.y = c->d_y;
+    a.asum = nullptr;
+    a.amean = nullptr;
     a.err = c->d_err;
     a.spin_limit = c->spin_limit;
     a.fault_no_publish = c->fault_no_publish;
@@ -513,7 +545,15 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
     cudaSetDevice(c->device);
     rc = ensure_update_buffers(c, p->width);
     if (rc) return rc;
+    if (p->want_alpha) {
+        rc = ensure_alpha_buffers(c, p->width);
+        if (rc) return rc;
+    }
     UpdateArgs a = make_args(c, *p);
+    if (p->want_alpha) {
+        a.asum = c->d_asum;
+        a.amean = c->d_amean;
+    }
     if (c->timing) {
         std::array<cudaEvent_t, 5> set{};
         for (auto& e : set) CK(cudaEventCreate(&e), "create event");
@@ -524,8 +564,102 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
     c->fault_no_publish = 0;
     c->W_last = p->width;
     c->last_prm = *p;
+    c->last_alpha = p->want_alpha != 0;
     c->have_update = true;
     return DVL_OK;
+}
+
+int dvl_set_tf_ctrl(dvl_ctx* c, const float* ctrl, uint32_t K, uint32_t T, const float* domain, int mem_kind)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (c->state < 1) return fail(c, DVL_ERR_STATE, "no data set loaded");
+    if (!ctrl) return fail(c, DVL_ERR_ARG, "ctrl is NULL");
+    if (K < 2 || K > 1024) return fail(c, DVL_ERR_ARG, "K must be in [2, 1024]");
+    if (T < 2 || T > DVL_MAX_TF_ENTRIES) return fail(c, DVL_ERR_ARG, "n_entries must be in [2, %d]", DVL_MAX_TF_ENTRIES);
+    if (mem_kind != DVL_MEM_HOST && mem_kind != DVL_MEM_DEVICE) return fail(c, DVL_ERR_ARG, "bad mem_kind");
+    const uint32_t M = c->M;
+    if (mem_kind == DVL_MEM_HOST)
+        for (uint32_t i = 0; i < M * K; ++i)
+            if (!(ctrl[i] >= 0.0f && ctrl[i] <= 1.0f)) return fail(c, DVL_ERR_ARG, "ctrl[%u] outside [0, 1]", i);
+    std::vector<float> dom(2 * M, NAN);
+    if (domain) {
+        for (uint32_t m = 0; m < M; ++m) {
+            const float lo = domain[m], hi = domain[M + m];
+            const bool dflt = std::isnan(lo) && std::isnan(hi);
+            if (!dflt && !(std::isfinite(lo) && std::isfinite(hi) && lo < hi))
+                return fail(c, DVL_ERR_ARG, "domain must be finite with lo < hi, or NaN/NaN");
+            dom[m] = lo;
+            dom[M + m] = hi;
+        }
+    }
+    cudaSetDevice(c->device);
+    const size_t need = (size_t)M * T;
+    if (need > c->tf_cap) {
+        CK(dalloc(c->d_tf, need), "alloc TF");
+        CK(dalloc(c->d_dom, 2 * DVL_MAX_FIELDS), "alloc TF domain");
+        c->tf_cap = need;
+    }
+    if (K != c->K_ctrl) {
+        CK(dalloc(c->d_ctrl, (size_t)M * K), "alloc control points");
+        c->K_ctrl = K;
+    }
+    CK(cudaMemcpyAsync(c->d_ctrl, ctrl, (size_t)M * K * sizeof(float), kind_in(mem_kind), c->stream), "copy ctrl");
+    CK(launch_ctrl_table(c->stream, M, K, T, c->d_ctrl, c->d_tf, c->d_err), "control-point tables");
+    c->h_dom = dom;
+    c->T = T;
+    c->tf_set.assign(M, 1);
+    c->tf_device = true;
+    c->tf_dirty = true;                 // uploads the domains (not the tables) at the next update
+    if (mem_kind == DVL_MEM_HOST) CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return DVL_OK;
+}
+
+int dvl_read_alpha_means(dvl_ctx* c, float* out, int mem_kind)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (!out) return fail(c, DVL_ERR_ARG, "out is NULL");
+    if (!c->have_update || !c->last_alpha) return fail(c, DVL_ERR_STATE, "last update had want_alpha = 0");
+    if (mem_kind != DVL_MEM_HOST && mem_kind != DVL_MEM_DEVICE) return fail(c, DVL_ERR_ARG, "bad mem_kind");
+    cudaSetDevice(c->device);
+    int rc = take_device_error(c);
+    if (rc) return rc;
+    const size_t MW = (size_t)c->M * c->W_last;
+    CK(cudaMemcpyAsync(out, c->d_amean, MW * sizeof(float), kind_out(mem_kind), c->stream), "copy alpha means");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return DVL_OK;
+}
+
+int dvl_backward(dvl_ctx* c, const float* grad, int mem_in, float* grad_ctrl, int mem_out)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (!grad || !grad_ctrl) return fail(c, DVL_ERR_ARG, "NULL gradient buffer");
+    if ((mem_in != DVL_MEM_HOST && mem_in != DVL_MEM_DEVICE) || (mem_out != DVL_MEM_HOST && mem_out != DVL_MEM_DEVICE))
+        return fail(c, DVL_ERR_ARG, "bad mem_kind");
+    if (!c->have_update || !c->last_alpha) return fail(c, DVL_ERR_STATE, "last update had want_alpha = 0");
+    if (!c->tf_device) return fail(c, DVL_ERR_STATE, "transfer functions were not set from control points");
+    cudaSetDevice(c->device);
+    const uint32_t M = c->M, W = c->W_last, K = c->K_ctrl, T = c->T;
+    if ((size_t)M * T > c->gtab_cap) { CK(dalloc(c->d_gtab, (size_t)M * T), "alloc adjoint"); c->gtab_cap = (size_t)M * T; }
+    if ((size_t)M * K > c->gout_cap) { CK(dalloc(c->d_gout, (size_t)M * K), "alloc adjoint"); c->gout_cap = (size_t)M * K; }
+    const float* g = grad;
+    if (mem_in == DVL_MEM_HOST) {
+        if ((size_t)M * W > c->gin_cap) { CK(dalloc(c->d_gin, (size_t)M * W), "alloc adjoint"); c->gin_cap = (size_t)M * W; }
+        CK(cudaMemcpyAsync(c->d_gin, grad, (size_t)M * W * sizeof(float), cudaMemcpyHostToDevice, c->stream),
+           "copy gradient");
+        g = c->d_gin;
+    }
+    CK(cudaMemsetAsync(c->d_gtab, 0, (size_t)M * T * sizeof(double), c->stream), "clear adjoint");
+    UpdateArgs a = make_args(c, c->last_prm);
+    float* out = mem_out == DVL_MEM_DEVICE ? grad_ctrl : c->d_gout;
+    CK(launch_backward(c->stream, a, g, c->d_gtab, K, out), "adjoint kernels");
+    if (mem_out == DVL_MEM_HOST)
+        CK(cudaMemcpyAsync(grad_ctrl, c->d_gout, (size_t)M * K * sizeof(float), cudaMemcpyDeviceToHost, c->stream),
+           "copy gradient");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return take_device_error(c);
 }
 
 int dvl_read_bins(dvl_ctx* c, uint32_t field, const dvl_bins* out)

@@ -103,6 +103,8 @@ struct UpdateArgs {
     uint32_t* count;           // W
     float* mean;               // M x W
     float* y;                  // M x W
+    double* asum;              // M x W alpha sums, or null (no alpha means)
+    float* amean;              // M x W alpha means (when asum)
     uint32_t* err;
     int64_t spin_limit;
     int fault_no_publish;
@@ -110,6 +112,14 @@ struct UpdateArgs {
     cudaEvent_t* events;       // 5 events recorded between the stages, or null
 };
 cudaError_t launch_update(cudaStream_t s, const UpdateArgs& a);
+// Alpha tables from control points (M x K -> M x T), flags values outside [0,1].
+cudaError_t launch_ctrl_table(cudaStream_t s, uint32_t M, uint32_t K, uint32_t T, const float* ctrl, float* tf,
+                              uint32_t* err);
+// Adjoint of the alpha means of the last update: gtab (M x T, zeroed by the
+// caller) += per (cell, pixel) g[m][p] / count[p] at the cell's entry; then
+// grad_ctrl (M x K) = gtab through the interpolation weights.
+cudaError_t launch_backward(cudaStream_t s, const UpdateArgs& a, const float* g, double* gtab, uint32_t K,
+                            float* grad_ctrl);
 cudaError_t launch_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* q);
 
 }  // namespace dvl

@@ -89,7 +89,8 @@ extern "C" int dvl_update_noalloc(void* cuda_stream, uint64_t n_cells, uint32_t 
     if (n_entries < 2 || n_entries > DVL_MAX_TF_ENTRIES || !alpha) return DVL_ERR_ARG;
     if (p->width < 1 || p->width > DVL_MAX_WIDTH) return DVL_ERR_ARG;
     if (!(p->P >= 0.0f) || !std::isfinite(p->P) || !(p->min_importance >= 0.0f) ||
-        !std::isfinite(p->min_importance) || p->min_imp_mode > 1 || p->vmax_mode > 1 || p->width_mode > 1)
+        !std::isfinite(p->min_importance) || p->min_imp_mode > 1 || p->vmax_mode > 1 || p->width_mode > 1 ||
+        p->want_alpha)
         return DVL_ERR_ARG;
     if (!out->sum || !out->min || !out->max || !out->count || !out->mean || !out->y ||
         out->mem_kind != DVL_MEM_DEVICE)

@@ -254,6 +254,7 @@ __global__ void k_prepare(UpdateArgs a, uint32_t n_tiles)
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < MW;
          i += (uint64_t)gridDim.x * blockDim.x) {
         a.sum[i] = 0.0;
+        if (a.asum) a.asum[i] = 0.0;
         a.vmin[i] = 0xFFFFFFFFu;
         a.vmax[i] = 0u;
         if (i < a.W) a.count[i] = 0u;
@@ -511,14 +512,19 @@ struct PixelMap {
     }
 };
 
-template <int M>
+template <int M, bool A = false>
 struct Acc {
     float s[M], mn[M], mx[M];
+    float as[A ? M : 1];           // alpha sums (differentiable output)
     uint32_t cnt;
     __device__ __forceinline__ void reset()
     {
 #pragma unroll
         for (int m = 0; m < M; ++m) { s[m] = 0.0f; mn[m] = 2.0f; mx[m] = -1.0f; }
+        if (A) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) as[m] = 0.0f;
+        }
         cnt = 0;
     }
     __device__ __forceinline__ void add(const float* t)
@@ -526,6 +532,13 @@ struct Acc {
 #pragma unroll
         for (int m = 0; m < M; ++m) { s[m] += t[m]; mn[m] = fminf(mn[m], t[m]); mx[m] = fmaxf(mx[m], t[m]); }
         ++cnt;
+    }
+    __device__ __forceinline__ void add_alpha(const float* al)
+    {
+        if (A) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) as[m] += al[m];
+        }
     }
     __device__ __forceinline__ void flush_to(const UpdateArgs& a, uint32_t p) const
     {
@@ -536,6 +549,7 @@ struct Acc {
             atomicAdd(&a.sum[k], (double)s[m]);
             atomicMin(&a.vmin[k], __float_as_uint(mn[m]));   // t >= 0: bit order = value order
             atomicMax(&a.vmax[k], __float_as_uint(mx[m]));
+            if (A) atomicAdd(&a.asum[k], (double)as[m]);
         }
         atomicAdd(&a.count[p], cnt);
     }
@@ -549,6 +563,7 @@ struct Acc {
                 s[m] += __shfl_xor_sync(FULL, s[m], o);
                 mn[m] = fminf(mn[m], __shfl_xor_sync(FULL, mn[m], o));
                 mx[m] = fmaxf(mx[m], __shfl_xor_sync(FULL, mx[m], o));
+                if (A) as[m] += __shfl_xor_sync(FULL, as[m], o);
             }
             cnt += __shfl_xor_sync(FULL, cnt, o);
         }
@@ -556,6 +571,14 @@ struct Acc {
         reset();
     }
 };
+
+// alpha of each field for normalised values t (T+1-entry shared tables)
+template <int M>
+__device__ __forceinline__ void alphas_of(const float* t, const float* s_tf, float Tf, int T1, float* al)
+{
+#pragma unroll
+    for (int m = 0; m < M; ++m) al[m] = s_tf[m * T1 + floor_small(__fmul_rn(t[m], Tf))];
+}
 
 // Exact placement of one lane's cells of a step that crosses a pixel
 // boundary; consecutive cells on the same pixel are merged per lane.
@@ -657,7 +680,7 @@ __global__ __launch_bounds__(WARPS * 32) void k_passB(UpdateArgs a)
 // span [s_start, s_end) lies inside the current pixel needs only the cells'
 // normalised values (no levels, no TF lookups, no widths); a step that
 // crosses a pixel boundary is recomputed out of line and placed cell by cell.
-template <int M, int PM>
+template <int M, int PM, bool ALPHA>
 __device__ __noinline__ void place_crossing_step(const UpdateArgs& a, const float* s_tf, const PixelMap& pm,
                                                  uint64_t idx, unsigned long long s_start, int lane)
 {
@@ -678,7 +701,7 @@ __device__ __noinline__ void place_crossing_step(const UpdateArgs& a, const floa
     unsigned long long lsum = 0;
     for (int j = 0; j < nvalid; ++j) lsum += width(j);
     unsigned long long E = s_start + warp_incl_scan_u64(lsum, lane) - lsum;
-    Acc<M> run;
+    Acc<M, ALPHA> run;
     run.reset();
     uint32_t run_p = 0xFFFFFFFFu;
     for (int j = 0; j < nvalid; ++j) {
@@ -687,6 +710,8 @@ __device__ __noinline__ void place_crossing_step(const UpdateArgs& a, const floa
         const unsigned long long I = E + (cc.linear ? 1u : cc.width(t, __ldg(a.lev + idx + j), s_tf));
         const uint32_t b1 = pm.first_pixel(E);
         const uint32_t b2 = I > E ? pm.last_pixel(I) : b1;
+        float al[ALPHA ? M : 1];
+        if (ALPHA) alphas_of<M>(t, s_tf, cc.Tf, cc.T1, al);
         for (uint32_t p = b1; p <= b2; ++p) {
             if (p != run_p) {
                 run.flush_to(a, run_p);
@@ -694,13 +719,14 @@ __device__ __noinline__ void place_crossing_step(const UpdateArgs& a, const floa
                 run_p = p;
             }
             run.add(t);
+            run.add_alpha(al);
         }
         E = I;
     }
     run.flush_to(a, run_p);
 }
 
-template <int M, int PM>
+template <int M, int PM, bool ALPHA>
 __global__ __launch_bounds__(WARPS * 32) void k_passB_steps(UpdateArgs a)
 {
     extern __shared__ float s_tf[];
@@ -741,9 +767,11 @@ __global__ __launch_bounds__(WARPS * 32) void k_passB_steps(UpdateArgs a)
     float lo[M], sc[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) { lo[m] = C->lo[m]; sc[m] = C->s[m]; }
-    Acc<M> acc;
+    Acc<M, ALPHA> acc;
     acc.reset();
     uint32_t cur = __shfl_sync(FULL, pix, 0);
+    const float Tf = (float)a.T;
+    const int T1 = (int)a.T + 1;
 
     // phase 1: single-pixel steps, register double buffering, no calls
     float4 bufA[M], bufB[M];
@@ -771,6 +799,11 @@ __global__ __launch_bounds__(WARPS * 32) void k_passB_steps(UpdateArgs a)
             for (int m = 0; m < M; ++m)
                 t[m] = norm_t(j == 0 ? x[m].x : j == 1 ? x[m].y : j == 2 ? x[m].z : x[m].w, lo[m], sc[m]);
             acc.add(t);
+            if (ALPHA) {
+                float al[M];
+                alphas_of<M>(t, s_tf, Tf, T1, al);
+                acc.add_alpha(al);
+            }
         }
     };
     int st = next_fast(-1);
@@ -792,7 +825,8 @@ __global__ __launch_bounds__(WARPS * 32) void k_passB_steps(UpdateArgs a)
     while (m2) {
         const int k = __ffs(m2) - 1;
         m2 &= m2 - 1;
-        place_crossing_step<M, PM>(a, s_tf, pm, base + k * STEP + lane * 4, __shfl_sync(FULL, s_start, k), lane);
+        place_crossing_step<M, PM, ALPHA>(a, s_tf, pm, base + k * STEP + lane * 4, __shfl_sync(FULL, s_start, k),
+                                          lane);
     }
 }
 
@@ -808,6 +842,7 @@ __global__ void k_finalize(UpdateArgs a)
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t m = (uint32_t)(i / a.W), p = (uint32_t)(i % a.W);
         const uint32_t c = a.count[p];
+        if (a.asum) a.amean[i] = c ? __double2float_rn(__ddiv_rn(a.asum[i], (double)c)) : 0.0f;
         if (c) {
             const float mean = __double2float_rn(__ddiv_rn(a.sum[i], (double)c));
             a.mean[i] = mean;
@@ -819,6 +854,175 @@ __global__ void k_finalize(UpdateArgs a)
             a.vmax[i] = 0u;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Differentiable path: control points -> alpha tables, and the adjoint of the
+// per-pixel alpha means with the assignment held fixed
+// ---------------------------------------------------------------------------
+
+__global__ void k_ctrl_table(uint32_t M, uint32_t K, uint32_t T, const float* __restrict__ ctrl,
+                             float* __restrict__ tf, uint32_t* err)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (uint64_t)M * K; i += stride)
+        if (!(ctrl[i] >= 0.0f && ctrl[i] <= 1.0f)) atomicOr(err, ERR_RANGE);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (uint64_t)M * T; i += stride) {
+        const uint32_t m = (uint32_t)(i / T), e = (uint32_t)(i % T);
+        const float x = __fdiv_rn((float)(e * (K - 1)), (float)(T - 1));
+        uint32_t k0 = (uint32_t)floorf(x);
+        if (k0 > K - 2) k0 = K - 2;
+        const float w = __fsub_rn(x, (float)k0);
+        const float c0 = ctrl[m * K + k0], c1 = ctrl[m * K + k0 + 1];
+        tf[i] = __fadd_rn(c0, __fmul_rn(w, __fsub_rn(c1, c0)));
+    }
+}
+
+// Adds v at (field m, shared-table entry e) to the CTA's table (or to global).
+__device__ __forceinline__ void gadd(double* sG, double* gtab, uint32_t T, int T1, int m, uint32_t e, double v)
+{
+    if (sG) atomicAdd(&sG[m * T1 + e], v);
+    else atomicAdd(&gtab[(uint64_t)m * T + (e < T ? e : T - 1)], v);
+}
+
+template <int M, int PM>
+__device__ __noinline__ void back_crossing_step(const UpdateArgs& a, const float* s_tf, const PixelMap& pm,
+                                                uint64_t idx, unsigned long long s_start, int lane,
+                                                const float* g, double* sG, double* gtab)
+{
+    Cell<M, PM> cc;
+    cc.load(a.consts, a.T);
+    const int nvalid = idx < a.n ? (a.n - idx < 4 ? (int)(a.n - idx) : 4) : 0;
+    auto cell = [&](int j, float (&t)[M]) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) t[m] = norm_t(__ldg(a.val + m * a.pitch + idx + j), cc.lo[m], cc.s[m]);
+    };
+    unsigned long long lsum = 0;
+    for (int j = 0; j < nvalid; ++j) {
+        float t[M];
+        cell(j, t);
+        lsum += cc.linear ? 1u : cc.width(t, __ldg(a.lev + idx + j), s_tf);
+    }
+    unsigned long long E = s_start + warp_incl_scan_u64(lsum, lane) - lsum;
+    for (int j = 0; j < nvalid; ++j) {
+        float t[M];
+        cell(j, t);
+        const unsigned long long I = E + (cc.linear ? 1u : cc.width(t, __ldg(a.lev + idx + j), s_tf));
+        const uint32_t b1 = pm.first_pixel(E);
+        const uint32_t b2 = I > E ? pm.last_pixel(I) : b1;
+        for (uint32_t p = b1; p <= b2; ++p) {
+            const uint32_t c = a.count[p];
+            if (!c) continue;
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                gadd(sG, gtab, a.T, cc.T1, m, floor_small(__fmul_rn(t[m], cc.Tf)),
+                     (double)g[(uint64_t)m * a.W + p] / (double)c);
+        }
+        E = I;
+    }
+}
+
+template <int M, int PM>
+__global__ __launch_bounds__(WARPS * 32) void k_backward(UpdateArgs a, const float* g, double* gtab, int use_smem)
+{
+    extern __shared__ float s_tf[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    load_table<M>(s_tf, a.tf, a.T);
+    const int T1 = (int)a.T + 1;
+    double* sG = use_smem ? reinterpret_cast<double*>(s_tf + ((M * T1 + 1) & ~1)) : nullptr;
+    if (sG)
+        for (int i = tid; i < M * T1; i += blockDim.x) sG[i] = 0.0;
+    __syncthreads();
+    const uint64_t chunk = (uint64_t)blockIdx.x * WARPS + warp;
+    const uint64_t base = chunk * CHUNK;
+    if (base < a.n) {
+        const UpdateConsts* C = a.consts;
+        const bool linear = C->linear != 0;
+        const PixelMap pm{C->F_div_W, C->F_mod_W, C->F, a.W};
+        const uint64_t rem = a.n - base;
+        const int full = rem >= (uint64_t)CHUNK ? STEPS : (int)(rem / STEP);
+        const int nsteps = rem >= (uint64_t)CHUNK ? STEPS : (int)((rem + STEP - 1) / STEP);
+        const unsigned long long pos0 = linear ? base : a.chunk_prefix[chunk];
+        unsigned long long ssum = 0;
+        if (lane < nsteps) {
+            const uint64_t left = a.n - (base + (uint64_t)lane * STEP);
+            ssum = linear ? (left < STEP ? left : STEP) : a.step_sums[chunk * STEPS + lane];
+        }
+        const unsigned long long s_end = pos0 + warp_incl_scan_u64(ssum, lane);
+        const unsigned long long s_start = s_end - ssum;
+        uint32_t pix = 0;
+        bool crossing = true;
+        if (lane < nsteps) {
+            pix = pm.first_pixel(s_start);
+            crossing = lane >= full || s_end >= pm.C(pix + 1);
+        }
+        const unsigned exact_mask = __ballot_sync(FULL, crossing) & ((1u << nsteps) - 1u);
+        float lo[M], sc[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) { lo[m] = C->lo[m]; sc[m] = C->s[m]; }
+        const float Tf = (float)a.T;
+        const unsigned lt = (1u << lane) - 1u;
+        for (int st = 0; st < full; ++st) {
+            if (exact_mask & (1u << st)) continue;                      // warp-uniform
+            const uint32_t p = __shfl_sync(FULL, pix, st);
+            const uint32_t c = a.count[p];
+            double wm[M];
+#pragma unroll
+            for (int m = 0; m < M; ++m) wm[m] = c ? (double)g[(uint64_t)m * a.W + p] / (double)c : 0.0;
+            float4 x[M];
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                x[m] = __ldg(reinterpret_cast<const float4*>(a.val + m * a.pitch + base + st * STEP + lane * 4));
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    const float v = j == 0 ? x[m].x : j == 1 ? x[m].y : j == 2 ? x[m].z : x[m].w;
+                    const uint32_t e = floor_small(__fmul_rn(norm_t(v, lo[m], sc[m]), Tf));
+                    // lanes with the same entry add their (equal) weights once
+                    const unsigned peers = __match_any_sync(FULL, e);
+                    if ((peers & lt) == 0) gadd(sG, gtab, a.T, T1, m, e, wm[m] * __popc(peers));
+                }
+            }
+        }
+        unsigned m2 = exact_mask;
+        while (m2) {
+            const int k = __ffs(m2) - 1;
+            m2 &= m2 - 1;
+            back_crossing_step<M, PM>(a, s_tf, pm, base + k * STEP + lane * 4, __shfl_sync(FULL, s_start, k), lane,
+                                      g, sG, gtab);
+        }
+    }
+    if (sG) {
+        __syncthreads();
+        for (int i = tid; i < M * T1; i += blockDim.x) {
+            const double v = sG[i];
+            if (v != 0.0) {
+                const int m = i / T1;
+                const uint32_t e = (uint32_t)(i - m * T1);
+                atomicAdd(&gtab[(uint64_t)m * a.T + (e < a.T ? e : a.T - 1)], v);
+            }
+        }
+    }
+}
+
+// dL/dctrl[m][k] = sum_e gtab[m][e] * (interpolation weight of k in entry e)
+__global__ void k_grad_ctrl(uint32_t M, uint32_t K, uint32_t T, const double* __restrict__ gtab,
+                            float* __restrict__ grad)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * K) return;
+    const uint32_t m = i / K, k = i % K;
+    double acc = 0.0;
+    for (uint32_t e = 0; e < T; ++e) {
+        const double x = (double)e * (double)(K - 1) / (double)(T - 1);
+        uint32_t k0 = (uint32_t)floor(x);
+        if (k0 > K - 2) k0 = K - 2;
+        const double w = x - k0, G = gtab[(uint64_t)m * T + e];
+        if (k0 == k) acc += (1.0 - w) * G;
+        if (k0 + 1 == k) acc += w * G;
+    }
+    grad[i] = (float)acc;
 }
 
 // Per-cell widths with the constants of the last update (checking aid).
@@ -861,13 +1065,16 @@ cudaError_t run_passes(cudaStream_t s, const UpdateArgs& a, uint32_t n_tiles, si
     cudaError_t e;
     if ((e = smem_attr(k_passA<M, PM>, smem)) != cudaSuccess) return e;
     if ((e = smem_attr(k_passB<M, PM>, smem)) != cudaSuccess) return e;
-    if ((e = smem_attr(k_passB_steps<M, PM>, smem)) != cudaSuccess) return e;
+    if ((e = smem_attr(k_passB_steps<M, PM, false>, smem)) != cudaSuccess) return e;
+    if ((e = smem_attr(k_passB_steps<M, PM, true>, smem)) != cudaSuccess) return e;
     if (a.events) cudaEventRecord(a.events[1], s);
     if (n_tiles) k_passA<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles);
     if (a.events) cudaEventRecord(a.events[2], s);
     if (n_tiles) {
-        if (a.step_sums)
-            k_passB_steps<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a);
+        if (a.step_sums && a.asum)
+            k_passB_steps<M, PM, true><<<n_tiles, WARPS * 32, smem, s>>>(a);
+        else if (a.step_sums)
+            k_passB_steps<M, PM, false><<<n_tiles, WARPS * 32, smem, s>>>(a);
         else
             k_passB<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a);
     }
@@ -893,6 +1100,31 @@ cudaError_t run_update(cudaStream_t s, const UpdateArgs& a)
     if (e != cudaSuccess) return e;
     k_finalize<<<grid_cap((uint64_t)a.M * a.W, 256), 256, 0, s>>>(a);
     if (a.events) cudaEventRecord(a.events[4], s);
+    return cudaGetLastError();
+}
+
+template <int M, int PM>
+cudaError_t run_backward_pm(cudaStream_t s, const UpdateArgs& a, const float* g, double* gtab)
+{
+    const uint32_t n_tiles = (uint32_t)((a.n + TILE - 1) / TILE);
+    const size_t table = (size_t)((M * (a.T + 1) + 1) & ~1u) * sizeof(float);
+    const size_t gbytes = (size_t)M * (a.T + 1) * sizeof(double);
+    const int use_smem = table + gbytes <= 96 * 1024;
+    const size_t smem = table + (use_smem ? gbytes : 0);
+    cudaError_t e = smem_attr(k_backward<M, PM>, smem);
+    if (e != cudaSuccess) return e;
+    if (n_tiles) k_backward<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a, g, gtab, use_smem);
+    return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t run_backward(cudaStream_t s, const UpdateArgs& a, const float* g, double* gtab, uint32_t K,
+                         float* grad_ctrl)
+{
+    cudaError_t e = a.prm.P == 1.0f ? run_backward_pm<M, POW_ONE>(s, a, g, gtab)
+                                    : run_backward_pm<M, POW_GEN>(s, a, g, gtab);
+    if (e != cudaSuccess) return e;
+    k_grad_ctrl<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(M, K, a.T, gtab, grad_ctrl);
     return cudaGetLastError();
 }
 
@@ -922,6 +1154,19 @@ cudaError_t run_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* 
     }
 
 cudaError_t launch_update(cudaStream_t s, const UpdateArgs& a) { DVL_DISPATCH_M(run_update, s, a) }
+
+cudaError_t launch_ctrl_table(cudaStream_t s, uint32_t M, uint32_t K, uint32_t T, const float* ctrl, float* tf,
+                              uint32_t* err)
+{
+    k_ctrl_table<<<grid_cap((uint64_t)M * T, 256), 256, 0, s>>>(M, K, T, ctrl, tf, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward(cudaStream_t s, const UpdateArgs& a, const float* g, double* gtab, uint32_t K,
+                            float* grad_ctrl)
+{
+    DVL_DISPATCH_M(run_backward, s, a, g, gtab, K, grad_ctrl)
+}
 
 cudaError_t launch_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* q)
 {

@@ -1,0 +1,119 @@
+"""Differentiable pattern on the GPU vs the CPU oracle (GPU).
+
+The per-pixel mean alpha (forward) and its gradient with respect to the
+alpha control points (adjoint kernel, assignment held fixed) are compared
+with oracle.alpha_grad, whose gradient is pinned by float64 central
+differences (tests/test_oracle_grad.py).  Tolerances: alpha means 1e-5
+relative (float32 tables vs float64 in the oracle, sums as in the bins);
+gradients 1e-5 of the largest component (float64 accumulation on both sides).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+dvl = pytest.importorskip("paper_2306_11612_b300")
+torch = pytest.importorskip("torch")
+
+
+def _case(seed, amr, K=64, W=257):
+    rng = np.random.default_rng(seed)
+    ctrl = (rng.integers(0, 1025, (4, K)) / 1024.0).astype(np.float32)
+    target = rng.uniform(0, 1, (4, W))
+    return ctrl, target
+
+
+def _ctx(amr, sfc=dvl.SFC_HILBERT):
+    ctx = dvl.DVL(0)
+    ctx.load_amr(amr.lower, amr.level, amr.fields)
+    ctx.build_order(sfc)
+    return ctx
+
+
+@pytest.mark.parametrize("kw", [dict(P=1.0), dict(P=2.0, min_importance=0.1), dict(P=0.0)])
+def test_alpha_means_and_gradient_match_oracle(kw):
+    amr = synth.make("small")
+    W = 257
+    ctrl, target = _case(1, amr, W=W)
+    _, _, lev, fl = oracle.sorted_inputs(amr.lower, amr.level, amr.fields, oracle.SFC_HILBERT)
+    ref = oracle.alpha_grad(fl, lev, ctrl, target, width=W, **kw)
+    ctx = _ctx(amr)
+    try:
+        ctx.set_tf_ctrl(ctrl, 256)
+        ctx.update(width=W, want_alpha=1, **kw)
+        abar = ctx.read_alpha_means()
+        assert np.allclose(abar, ref["abar"], rtol=1e-5, atol=1e-7)
+        g = (2.0 * (ref["abar"] - target)).astype(np.float32)
+        grad = ctx.backward(g)
+        scale = np.abs(ref["grad"]).max()
+        assert np.max(np.abs(grad - ref["grad"])) <= 1e-5 * scale
+        # the bins of the alpha-means update equal those of a plain update
+        b = ctx.read_bins(2)
+        ctx.update(width=W, **kw)
+        b0 = ctx.read_bins(2)
+        assert np.array_equal(b["count"], b0["count"]) and np.array_equal(b["min"], b0["min"])
+    finally:
+        ctx.close()
+
+
+def test_autograd_function_matches_oracle():
+    from paper_2306_11612_b300.diff import alpha_means
+    amr = synth.make("small")
+    W = 300
+    ctrl, target = _case(2, amr, W=W)
+    _, _, lev, fl = oracle.sorted_inputs(amr.lower, amr.level, amr.fields, oracle.SFC_HILBERT)
+    ref = oracle.alpha_grad(fl, lev, ctrl, target, width=W, P=1.0)
+    ctx = _ctx(amr)
+    try:
+        dev = torch.device("cuda:0")
+        c = torch.tensor(ctrl, device=dev, requires_grad=True)
+        t = torch.tensor(target, device=dev, dtype=torch.float32)
+        abar = alpha_means(ctx, c, width=W, P=1.0)
+        loss = ((abar.double() - t.double()) ** 2).sum()
+        loss.backward()
+        assert abs(loss.item() - ref["loss"]) <= 1e-5 * ref["loss"]
+        grad = c.grad.cpu().numpy()
+        assert np.max(np.abs(grad - ref["grad"])) <= 1e-4 * np.abs(ref["grad"]).max()
+    finally:
+        ctx.close()
+
+
+def test_gradient_at_diff_config_scale():
+    """20M-cell 4-level data set, 64 control points per field, W = 2048."""
+    amr = synth.make("diff")
+    W = 2048
+    ctrl, target = _case(4, amr, W=W)
+    _, _, lev, fl = oracle.sorted_inputs(amr.lower, amr.level, amr.fields, oracle.SFC_HILBERT)
+    ref = oracle.alpha_grad(fl, lev, ctrl, target, width=W, P=1.0)
+    ctx = _ctx(amr)
+    try:
+        ctx.set_tf_ctrl(ctrl, 256)
+        ctx.update(width=W, want_alpha=1, P=1.0)
+        assert np.allclose(ctx.read_alpha_means(), ref["abar"], rtol=1e-5, atol=1e-7)
+        grad = ctx.backward((2.0 * (ref["abar"] - target)).astype(np.float32))
+        assert np.max(np.abs(grad - ref["grad"])) <= 1e-5 * np.abs(ref["grad"]).max()
+    finally:
+        ctx.close()
+
+
+def test_state_errors():
+    amr = synth.make("small")
+    ctx = _ctx(amr)
+    try:
+        ctx.set_tfs(synth.random_tfs(3))
+        ctx.update(width=64)
+        with pytest.raises(dvl.DVLError) as e:
+            ctx.read_alpha_means()
+        assert e.value.status == dvl.ERR_STATE
+        ctx.update(width=64, want_alpha=1)
+        with pytest.raises(dvl.DVLError) as e:
+            ctx._K = 8
+            ctx.backward(np.zeros((4, 64), np.float32))   # tables were not set from control points
+        assert e.value.status == dvl.ERR_STATE
+        with pytest.raises(dvl.DVLError) as e:
+            ctx.set_tf_ctrl(np.full((4, 8), 1.5, np.float32))
+        assert e.value.status == dvl.ERR_ARG
+    finally:
+        ctx.close()
