@@ -14,11 +14,11 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
           "-fmad=false", "-I", INCLUDE]
-SOURCES = ["dvl_api.cu", "sfc_sort.cu", "update.cu", "noalloc.cu"]
+SOURCES = ["dvl_api.cu", "sfc_sort.cu", "update.cu", "bins.cu", "noalloc.cu"]
 
 
 def _deps():
-    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     return hdrs + [os.path.join(INCLUDE, "dvl.h")]
 
 

@@ -78,6 +78,15 @@ struct dvl_ctx {
     size_t gtab_cap = 0, gin_cap = 0, gout_cap = 0;
     bool last_alpha = false;
     dvl_params last_prm{};
+    // value tables for range-query bins (per data set and TF domain)
+    ValueTableArgs vt{};
+    uint64_t* d_vt_tot_lo = nullptr;
+    uint64_t* d_vt_tot_hi = nullptr;
+    bool vt_valid = false;
+    std::vector<float> vt_dom;
+    unsigned long long* d_H = nullptr;
+    uint8_t* d_S = nullptr;
+    uint32_t HS_cap = 0;
     // options
     int64_t spin_limit = 1 << 22;
     int fault_no_publish = 0;
@@ -137,6 +146,10 @@ void free_dataset(dvl_ctx* c)
     dfree(c->d_val); dfree(c->d_lev); dfree(c->d_perm); dfree(c->d_keys);
     dfree(c->d_keys_alt); dfree(c->d_vals_alt); dfree(c->d_rs_status);
     dfree(c->d_tile_status); dfree(c->d_chunk_prefix); dfree(c->d_step_sums);
+    dfree(c->vt.pre_lo); dfree(c->vt.pre_hi); dfree(c->vt.mn); dfree(c->vt.mx);
+    dfree(c->d_vt_tot_lo); dfree(c->d_vt_tot_hi);
+    c->vt = ValueTableArgs{};
+    c->vt_valid = false;
     c->state = 0;
     c->have_update = false;
 }
@@ -256,7 +269,7 @@ void dvl_destroy(dvl_ctx* c)
     dfree(c->d_hist); dfree(c->d_rs_counters); dfree(c->d_tf); dfree(c->d_dom);
     dfree(c->d_sum); dfree(c->d_vmin); dfree(c->d_vmax); dfree(c->d_count);
     dfree(c->d_mean); dfree(c->d_y); dfree(c->d_asum); dfree(c->d_amean); dfree(c->d_ctrl);
-    dfree(c->d_gtab); dfree(c->d_gin); dfree(c->d_gout);
+    dfree(c->d_gtab); dfree(c->d_gin); dfree(c->d_gout); dfree(c->d_H); dfree(c->d_S);
     for (auto& set : c->ev)
         for (auto e : set) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -388,6 +401,23 @@ int dvl_build_order(dvl_ctx* c, int sfc)
     CK(dalloc(c->d_tile_status, tiles), "alloc scan state");
     CK(dalloc(c->d_chunk_prefix, tiles * WARPS), "alloc scan state");
     CK(dalloc(c->d_step_sums, tiles * WARPS * STEPS), "alloc scan state");
+    {
+        ValueTableArgs& v = c->vt;
+        v.n = n;
+        v.val = c->d_val;
+        v.pitch = p;
+        v.consts = c->d_consts;
+        v.n_steps = (n + STEP - 1) / STEP;
+        v.n_levels = (int)value_table_levels(v.n_steps, &v.level_stride);
+        const uint64_t nb = (v.n_steps + 1023) / 1024;
+        CK(dalloc(v.pre_lo, (size_t)c->M * (v.n_steps + 1)), "alloc value tables");
+        CK(dalloc(v.pre_hi, (size_t)c->M * (v.n_steps + 1)), "alloc value tables");
+        CK(dalloc(v.mn, (size_t)c->M * (v.level_stride ? v.level_stride : 1)), "alloc value tables");
+        CK(dalloc(v.mx, (size_t)c->M * (v.level_stride ? v.level_stride : 1)), "alloc value tables");
+        CK(dalloc(c->d_vt_tot_lo, (size_t)c->M * (nb ? nb : 1)), "alloc value tables");
+        CK(dalloc(c->d_vt_tot_hi, (size_t)c->M * (nb ? nb : 1)), "alloc value tables");
+        c->vt_valid = false;
+    }
     int rc = take_device_error(c);
     if (rc) return rc;
     // the unsorted coordinates are no longer needed; fields stay for set_fields
@@ -412,6 +442,7 @@ int dvl_set_fields(dvl_ctx* c, uint32_t M, const float* const* fields, int mem_k
     if (rc) return rc;
     launch_gather(c->stream, c->n, c->d_perm, c->M, c->d_fin, c->pitch, nullptr, c->d_val, c->pitch, nullptr);
     CK(cudaGetLastError(), "gather kernel");
+    c->vt_valid = false;                 // the values changed: rebuild the value tables
     return take_device_error(c);
 }
 
@@ -525,6 +556,12 @@ static UpdateArgs make_args(dvl_ctx* c, const dvl_params& p)
     a.y = c->d_y;
     a.asum = nullptr;
     a.amean = nullptr;
+    a.vt = nullptr;
+    a.vt_build = 0;
+    a.vt_tot_lo = c->d_vt_tot_lo;
+    a.vt_tot_hi = c->d_vt_tot_hi;
+    a.H = c->d_H;
+    a.S = c->d_S;
     a.err = c->d_err;
     a.spin_limit = c->spin_limit;
     a.fault_no_publish = c->fault_no_publish;
@@ -549,10 +586,25 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
         rc = ensure_alpha_buffers(c, p->width);
         if (rc) return rc;
     }
+    bool build_vt = false;
+    if (!p->want_alpha) {
+        // bins from range queries; the value tables depend on the TF domains
+        if (p->width + 1 > c->HS_cap) {
+            CK(cudaStreamSynchronize(c->stream), "synchronize");
+            CK(dalloc(c->d_H, p->width + 1), "alloc pixel bounds");
+            CK(dalloc(c->d_S, p->width + 1), "alloc pixel bounds");
+            c->HS_cap = p->width + 1;
+        }
+        build_vt = !c->vt_valid || c->vt_dom.size() != c->h_dom.size() ||
+                   std::memcmp(c->vt_dom.data(), c->h_dom.data(), c->h_dom.size() * sizeof(float)) != 0;
+    }
     UpdateArgs a = make_args(c, *p);
     if (p->want_alpha) {
         a.asum = c->d_asum;
         a.amean = c->d_amean;
+    } else {
+        a.vt = &c->vt;
+        a.vt_build = build_vt ? 1 : 0;
     }
     if (c->timing) {
         std::array<cudaEvent_t, 5> set{};
@@ -561,6 +613,10 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
         a.events = c->ev.back().data();
     }
     CK(launch_update(c->stream, a), "update kernels");
+    if (build_vt) {
+        c->vt_valid = true;
+        c->vt_dom = c->h_dom;
+    }
     c->fault_no_publish = 0;
     c->W_last = p->width;
     c->last_prm = *p;

@@ -81,6 +81,30 @@ cudaError_t launch_onesweep(cudaStream_t s, uint64_t n, const unsigned long long
 void launch_gather(cudaStream_t s, uint64_t n, const uint32_t* perm, uint32_t M, const float* fin,
                    size_t pitch_in, const uint8_t* lin, float* fout, size_t pitch_out, uint8_t* lout);
 
+// bins.cu: TF-independent value tables (per data set and TF domain) and the
+// per-pixel range queries that replace the placement pass.
+struct ValueTableArgs {
+    uint64_t n;
+    const float* val;          // M x pitch, curve order
+    size_t pitch;
+    const UpdateConsts* consts;   // lo / s of the domains the tables are built for
+    uint64_t n_steps;          // ceil(n / STEP)
+    uint64_t* pre_lo;          // M x (n_steps + 1): exclusive prefix of the per-step
+    uint64_t* pre_hi;          //   sums of floor(t * 2^95) (u128 as two u64)
+    float* mn;                 // M x level_stride: min/max hierarchy (level 0 = steps,
+    float* mx;                 //   each further level covers 16 entries of the last)
+    uint64_t level_stride;
+    int n_levels;
+};
+struct QueryArgs {
+    const UpdateConsts* consts;
+    const unsigned long long* chunk_prefix;
+    const unsigned long long* step_sums;
+    unsigned long long* H;     // W + 1: cells whose span starts before pixel j's first position
+    uint8_t* S;                // W + 1: the last of them also touches pixel j
+};
+uint64_t value_table_levels(uint64_t n_steps, uint64_t* stride);
+
 // update.cu
 struct UpdateArgs {
     uint64_t n;
@@ -110,7 +134,17 @@ struct UpdateArgs {
     int fault_no_publish;
     dvl_params prm;
     cudaEvent_t* events;       // 5 events recorded between the stages, or null
+    // range-query bins (null vt: the placement pass k_passB* is used instead)
+    const ValueTableArgs* vt;
+    int vt_build;              // rebuild the value tables after k_prepare
+    uint64_t* vt_tot_lo;       // scratch of the table scan (M x ceil(n_steps / 1024))
+    uint64_t* vt_tot_hi;
+    unsigned long long* H;
+    uint8_t* S;
 };
+cudaError_t launch_value_tables(cudaStream_t s, uint32_t M, const ValueTableArgs& v, uint64_t* tot_lo,
+                                uint64_t* tot_hi);
+cudaError_t launch_bins(cudaStream_t s, const UpdateArgs& a, const QueryArgs& qa, const ValueTableArgs& v);
 cudaError_t launch_update(cudaStream_t s, const UpdateArgs& a);
 // Alpha tables from control points (M x K -> M x T), flags values outside [0,1].
 cudaError_t launch_ctrl_table(cudaStream_t s, uint32_t M, uint32_t K, uint32_t T, const float* ctrl, float* tf,

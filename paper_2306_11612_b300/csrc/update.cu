@@ -26,192 +26,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "cell_math.cuh"
 #include "dvl_internal.h"
 
 namespace dvl {
 
 namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
-constexpr unsigned long long FLAG_A = 1ull << 62;   // tile aggregate published
-constexpr unsigned long long FLAG_P = 2ull << 62;   // inclusive prefix published
-constexpr unsigned long long VAL_MASK = (1ull << 62) - 1;
-
-// exponent modes of the per-cell kernels: P == 1, or any other P (exact
-// products/sqrt when 2P is an integer in [0, 16], powf otherwise)
-enum { POW_ONE = 0, POW_GEN = 1 };
-
-__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v)
-{
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ float ordered_to_float(uint32_t u)
-{
-    return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
-}
-
-// 2^e as a float for -126 <= e <= 127 (exact).
-__device__ __forceinline__ float exp2i(int e) { return __int_as_float((127 + e) << 23); }
-
-// Normalised value t = clamp((v - lo) * s, 0, 1) (Sec. 3.3).  The clamp works
-// on the bit pattern: negative values and -0 become +0, values above 1 (and
-// +inf) become 1.  NaN cannot occur: field values are finite (checked at
-// load), lo is finite and s is finite (k_prepare sets lo = 0 where s = 0).
-__device__ __forceinline__ float norm_t(float v, float lo, float s)
-{
-    int b = __float_as_int(__fmul_rn(__fsub_rn(v, lo), s));
-    b = min(max(b, 0), 0x3F800000);
-    return __int_as_float(b);
-}
-
-// TF entry of t: min(floor(t T), T - 1) (used by the non-hot kernels).
-__device__ __forceinline__ uint32_t tf_entry(float t, float Tf, uint32_t Tm1)
-{
-    uint32_t a = (uint32_t)__fmul_rn(t, Tf);    // t*T >= 0: truncation == floor
-    return a < Tm1 ? a : Tm1;
-}
-
-// floor(x) for 0 <= x < 2^23: adding 2^23 with round-toward-zero keeps the
-// integer part in the low mantissa bits.
-__device__ __forceinline__ uint32_t floor_small(float x)
-{
-    return __float_as_uint(__fadd_rz(x, 8388608.0f)) - 0x4B000000u;
-}
-
-// x^P with n2 = 2P for the exact modes (sqrt once if n2 is odd, then
-// left-to-right products); n2 < 0 selects powf.
-__device__ __forceinline__ float pow_gen(float x, int n2, float P)
-{
-    if (n2 < 0) return powf(x, P);
-    if (n2 == 0) return 1.0f;
-    float b;
-    int k;
-    if (n2 & 1) { b = __fsqrt_rn(x); k = n2; } else { b = x; k = n2 >> 1; }
-    float y = b;
-    for (int i = 1; i < k; ++i) y = __fmul_rn(y, b);
-    return y;
-}
-
-// Eq. 3 with the minimum importance m.  Both placements in one branch-free
-// form: before-scale f = (max(r, m) 2^L)^P, after-power f = max((r 2^L)^P, m);
-// mb / ma hold m in the selected slot and 0 in the other (max with 0 is the
-// identity here since r >= +0 and x^P >= +0).
-template <int PM>
-__device__ __forceinline__ float importance(float V, uint32_t L, float inv_vmax, float mb, float ma, int wshift,
-                                            int n2, float P)
-{
-    float r = fmaxf(__fmul_rn(V, inv_vmax), mb);
-    float x = __fmul_rn(r, exp2i((int)L * wshift));
-    float f = PM == POW_ONE ? x : pow_gen(x, n2, P);
-    return fmaxf(f, ma);
-}
-
-// Per-cell constants in registers, specialised on the field count M and the
-// exponent mode.  The alpha tables live in shared memory with T+1 entries per
-// field (entry T repeats entry T-1) so that t = 1 needs no clamp.
-template <int M, int PM>
-struct Cell {
-    float lo[M], s[M];
-    float inv_vmax, mb, ma, qscale, P, Tf;
-    int n2, wshift, T1;
-    bool linear;
-
-    __device__ __forceinline__ void load(const UpdateConsts* C, uint32_t T)
-    {
-#pragma unroll
-        for (int m = 0; m < M; ++m) { lo[m] = C->lo[m]; s[m] = C->s[m]; }
-        inv_vmax = C->inv_vmax;
-        const bool after = C->min_imp_mode == DVL_MINIMP_AFTER_POWER;
-        mb = after ? 0.0f : C->min_imp;
-        ma = after ? C->min_imp : 0.0f;
-        qscale = C->qscale;
-        P = C->P;
-        n2 = C->pow_n2;
-        wshift = C->width_shift;
-        Tf = (float)T;
-        T1 = (int)T + 1;
-        linear = C->linear != 0;
-    }
-
-    // Eq. 1 over the M fields of one cell, from normalised values t[].
-    __device__ __forceinline__ float variation(const float* t, const float* s_tf) const
-    {
-        float hi = s_tf[floor_small(__fmul_rn(t[0], Tf))];
-        float lw = hi;
-#pragma unroll
-        for (int m = 1; m < M; ++m) {
-            float al = s_tf[m * T1 + floor_small(__fmul_rn(t[m], Tf))];
-            hi = fmaxf(hi, al);
-            lw = fminf(lw, al);
-        }
-        return __fsub_rn(hi, lw);
-    }
-
-    // fixed-point width of a cell: rint(f 2^Q) (<= 2^31)
-    __device__ __forceinline__ uint32_t width(const float* t, uint32_t L, const float* s_tf) const
-    {
-        float f = importance<PM>(variation(t, s_tf), L, inv_vmax, mb, ma, wshift, n2, P);
-        return __float2uint_rn(__fmul_rn(f, qscale));
-    }
-};
-
-template <int M>
-__device__ __forceinline__ void load_table(float* s_tf, const float* tf, uint32_t T)
-{
-    const uint32_t T1 = T + 1;
-    for (uint32_t i = threadIdx.x; i < M * T1; i += blockDim.x) {
-        uint32_t m = i / T1, e = i - m * T1;
-        s_tf[i] = tf[m * T + (e < T ? e : T - 1)];
-    }
-}
-
-// Loads 4 consecutive cells at idx (idx % 4 == 0; rows padded to 4 cells).
-template <int M>
-__device__ __forceinline__ void load4(const float* __restrict__ val, size_t pitch,
-                                      const uint8_t* __restrict__ lev, uint64_t idx,
-                                      float (&v)[4][M], uint32_t& L4)
-{
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-        float4 x = __ldg(reinterpret_cast<const float4*>(val + m * pitch + idx));
-        v[0][m] = x.x; v[1][m] = x.y; v[2][m] = x.z; v[3][m] = x.w;
-    }
-    L4 = __ldg(reinterpret_cast<const uint32_t*>(lev + idx));
-}
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-    return x;
-}
-
-// Warp total of per-lane values below 2^35 (total below 2^40) with two redux adds.
-__device__ __forceinline__ unsigned long long warp_total_small(unsigned long long x)
-{
-    unsigned lo = __reduce_add_sync(FULL, (unsigned)(x & 0xFFFFFFull));
-    unsigned hi = __reduce_add_sync(FULL, (unsigned)(x >> 24));
-    return ((unsigned long long)hi << 24) + lo;
-}
-
-__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long x, int lane)
-{
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-    }
-    return x;
-}
-
 // ---------------------------------------------------------------------------
 // Constants (Sec. 3.4 and the fixed-point exponent)
 // ---------------------------------------------------------------------------
@@ -473,45 +293,6 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
 // Pass B: placement and per-pixel reduction
 // ---------------------------------------------------------------------------
 
-// Pixel boundaries: C(k) = ceil(k F / W) is the first position of pixel k,
-// D(k) = floor(k F / W); with F = a W + b, k F / W = k a + k b / W.
-struct PixelMap {
-    unsigned long long a, b, F;
-    uint32_t W;
-    __device__ __forceinline__ unsigned long long C(uint32_t k) const
-    {
-        unsigned long long kb = (unsigned long long)k * b;
-        return (unsigned long long)k * a + (kb + W - 1) / W;
-    }
-    __device__ __forceinline__ unsigned long long D(uint32_t k) const
-    {
-        return (unsigned long long)k * a + ((unsigned long long)k * b) / W;
-    }
-    __device__ __forceinline__ uint32_t estimate(unsigned long long x) const
-    {
-        float e = __fmul_rn((float)x, __fdiv_rn((float)W, (float)F));
-        uint32_t k = e > 0.0f ? (uint32_t)e : 0u;
-        return k < W - 1 ? k : W - 1;
-    }
-    // pixel containing start position x: max{k < W : C(k) <= x}
-    __device__ __forceinline__ uint32_t first_pixel(unsigned long long x) const
-    {
-        uint32_t k = estimate(x);
-        while (k + 1 < W && C(k + 1) <= x) ++k;
-        while (k > 0 && C(k) > x) --k;
-        return k;
-    }
-    // last pixel touched by a span ending at I > start: max{k < W : D(k) <= I-1}
-    __device__ __forceinline__ uint32_t last_pixel(unsigned long long I) const
-    {
-        unsigned long long y = I - 1;
-        uint32_t k = estimate(y);
-        while (k + 1 < W && D(k + 1) <= y) ++k;
-        while (k > 0 && D(k) > y) --k;
-        return k;
-    }
-};
-
 template <int M, bool A = false>
 struct Acc {
     float s[M], mn[M], mx[M];
@@ -726,20 +507,16 @@ __device__ __noinline__ void place_crossing_step(const UpdateArgs& a, const floa
     run.flush_to(a, run_p);
 }
 
+// Placement of one warp chunk (two phases, see k_passB_steps).  `a` carries
+// the constants, scan results and bins of one TF and one viewport; s_tf holds
+// that TF's tables.
 template <int M, int PM, bool ALPHA>
-__global__ __launch_bounds__(WARPS * 32) void k_passB_steps(UpdateArgs a)
+__device__ __forceinline__ void place_chunk(const UpdateArgs& a, const float* s_tf, const PixelMap& pm,
+                                            uint64_t chunk, int lane)
 {
-    extern __shared__ float s_tf[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    load_table<M>(s_tf, a.tf, a.T);
-    __syncthreads();
-    const uint64_t chunk = (uint64_t)blockIdx.x * WARPS + warp;
     const uint64_t base = chunk * CHUNK;
-    if (base >= a.n) return;
-
     const UpdateConsts* C = a.consts;
     const bool linear = C->linear != 0;
-    const PixelMap pm{C->F_div_W, C->F_mod_W, C->F, a.W};
     const uint64_t rem = a.n - base;
     const int full = rem >= (uint64_t)CHUNK ? STEPS : (int)(rem / STEP);      // steps with 128 cells
     const int nsteps = rem >= (uint64_t)CHUNK ? STEPS : (int)((rem + STEP - 1) / STEP);
@@ -828,6 +605,20 @@ __global__ __launch_bounds__(WARPS * 32) void k_passB_steps(UpdateArgs a)
         place_crossing_step<M, PM, ALPHA>(a, s_tf, pm, base + k * STEP + lane * 4, __shfl_sync(FULL, s_start, k),
                                           lane);
     }
+}
+
+template <int M, int PM, bool ALPHA>
+__global__ __launch_bounds__(WARPS * 32) void k_passB_steps(UpdateArgs a)
+{
+    extern __shared__ float s_tf[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    load_table<M>(s_tf, a.tf, a.T);
+    __syncthreads();
+    const uint64_t chunk = (uint64_t)blockIdx.x * WARPS + warp;
+    if (chunk * CHUNK >= a.n) return;
+    const UpdateConsts* C = a.consts;
+    const PixelMap pm{C->F_div_W, C->F_mod_W, C->F, a.W};
+    place_chunk<M, PM, ALPHA>(a, s_tf, pm, chunk, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -1070,6 +861,7 @@ cudaError_t run_passes(cudaStream_t s, const UpdateArgs& a, uint32_t n_tiles, si
     if (a.events) cudaEventRecord(a.events[1], s);
     if (n_tiles) k_passA<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles);
     if (a.events) cudaEventRecord(a.events[2], s);
+    if (a.vt) return cudaSuccess;          // bins come from range queries (see run_update)
     if (n_tiles) {
         if (a.step_sums && a.asum)
             k_passB_steps<M, PM, true><<<n_tiles, WARPS * 32, smem, s>>>(a);
@@ -1096,9 +888,19 @@ cudaError_t run_update(cudaStream_t s, const UpdateArgs& a)
         k_vmax_exact<M><<<grid_cap(a.n, 256), 256, smem, s>>>(a);
         k_consts<<<1, 1, 0, s>>>(a);
     }
+    if (a.vt && a.vt_build) {
+        if ((e = launch_value_tables(s, a.M, *a.vt, a.vt_tot_lo, a.vt_tot_hi)) != cudaSuccess) return e;
+    }
     e = a.prm.P == 1.0f ? run_passes<M, POW_ONE>(s, a, n_tiles, smem) : run_passes<M, POW_GEN>(s, a, n_tiles, smem);
     if (e != cudaSuccess) return e;
-    k_finalize<<<grid_cap((uint64_t)a.M * a.W, 256), 256, 0, s>>>(a);
+    if (a.vt) {
+        // bins as range queries over the value tables (writes final bins)
+        const QueryArgs qa{a.consts, a.chunk_prefix, a.step_sums, a.H, a.S};
+        if ((e = launch_bins(s, a, qa, *a.vt)) != cudaSuccess) return e;
+        if (a.events) cudaEventRecord(a.events[3], s);
+    } else {
+        k_finalize<<<grid_cap((uint64_t)a.M * a.W, 256), 256, 0, s>>>(a);
+    }
     if (a.events) cudaEventRecord(a.events[4], s);
     return cudaGetLastError();
 }
