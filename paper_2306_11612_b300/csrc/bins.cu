@@ -215,14 +215,9 @@ __global__ void k_vt_level(ValueTableArgs v, uint64_t off_prev, uint64_t n_prev,
 // whether the last of them (cell H-1) has a positive width reaching past the
 // real boundary j F / W (then it also touches pixel j).
 template <int M, int PM>
-__global__ __launch_bounds__(256) void k_bounds(UpdateArgs a, QueryArgs qa)
+__device__ __forceinline__ void bounds_one(const UpdateArgs& a, const QueryArgs& qa, const float* s_tf, uint32_t j,
+                                           int lane)
 {
-    extern __shared__ float s_tf[];
-    const int lane = threadIdx.x & 31;
-    load_table<M>(s_tf, a.tf, a.T);
-    __syncthreads();
-    const uint32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) + 1;
-    if (j >= a.W) return;
     const UpdateConsts* C = qa.consts;
     const unsigned long long F = C->F;
     const PixelMap pm{F / a.W, F % a.W, F, a.W};
@@ -292,6 +287,17 @@ __global__ __launch_bounds__(256) void k_bounds(UpdateArgs a, QueryArgs qa)
     }
 }
 
+template <int M, int PM>
+__global__ __launch_bounds__(256) void k_bounds(UpdateArgs a, QueryArgs qa)
+{
+    extern __shared__ float s_tf[];
+    load_table<M>(s_tf, a.tf, a.T);
+    __syncthreads();
+    const uint32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) + 1;
+    if (j >= a.W) return;
+    bounds_one<M, PM>(a, qa, s_tf, j, threadIdx.x & 31);
+}
+
 // Range min/max of t over steps [s0, s1) of one field through the hierarchy.
 __device__ __forceinline__ void steps_minmax(const ValueTableArgs& v, uint32_t m, uint64_t s0, uint64_t s1, int lane,
                                              float& mn, float& mx)
@@ -347,11 +353,9 @@ __device__ __forceinline__ void cells_partial(const UpdateArgs& a, const float* 
 
 // One warp per pixel: the bins of cells [lo_p, hi_p].
 template <int M>
-__global__ __launch_bounds__(256) void k_pixels(UpdateArgs a, QueryArgs qa, ValueTableArgs v)
+__device__ __forceinline__ void pixels_one(const UpdateArgs& a, const QueryArgs& qa, const ValueTableArgs& v,
+                                           uint32_t p, int lane)
 {
-    const int lane = threadIdx.x & 31;
-    const uint32_t p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (p >= a.W) return;
     const uint64_t Hn = p + 1 < a.W ? qa.H[p + 1] : a.n;            // cells with E < C(p+1)
     const uint64_t lo_c = p == 0 ? 0 : (qa.S[p] ? qa.H[p] - 1 : qa.H[p]);
     const float Tf = (float)a.T;
@@ -413,6 +417,62 @@ __global__ __launch_bounds__(256) void k_pixels(UpdateArgs a, QueryArgs qa, Valu
     if (lane == 0) a.count[p] = count;
 }
 
+template <int M>
+__global__ __launch_bounds__(256) void k_pixels(UpdateArgs a, QueryArgs qa, ValueTableArgs v)
+{
+    const uint32_t p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (p >= a.W) return;
+    pixels_one<M>(a, qa, v, p, threadIdx.x & 31);
+}
+
+// The arguments of pair y of a batch: one TF's scan, one viewport's bins.
+__device__ __forceinline__ void pair_args(const UpdateArgs& a, const BatchArgs& b, const PairDesc& pd,
+                                          UpdateArgs& ak, QueryArgs& qk)
+{
+    ak = a;
+    ak.W = pd.W;
+    ak.tf = b.tfs + (uint64_t)pd.k * a.M * a.T;
+    ak.sum = b.sum + pd.bin_off;
+    ak.vmin = b.vmin + pd.bin_off;
+    ak.vmax = b.vmax + pd.bin_off;
+    ak.mean = b.mean + pd.bin_off;
+    ak.y = b.y + pd.bin_off;
+    ak.count = b.count + pd.cnt_off;
+    qk.consts = b.consts + pd.k;
+    qk.chunk_prefix = b.chunk_prefix + (uint64_t)pd.k * b.n_chunks;
+    qk.step_sums = b.step_sums + (uint64_t)pd.k * b.n_chunks * STEPS;
+    qk.H = b.H + pd.hs_off;
+    qk.S = b.S + pd.hs_off;
+}
+
+template <int M, int PM>
+__global__ __launch_bounds__(256) void k_bounds_batch(UpdateArgs a, BatchArgs b)
+{
+    extern __shared__ float s_tf[];
+    const PairDesc pd = b.pairs[blockIdx.y];
+    if (blockIdx.x * (blockDim.x >> 5) + 1 >= pd.W) return;          // block-uniform
+    UpdateArgs ak;
+    QueryArgs qk;
+    pair_args(a, b, pd, ak, qk);
+    load_table<M>(s_tf, ak.tf, a.T);
+    __syncthreads();
+    const uint32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) + 1;
+    if (j >= pd.W) return;
+    bounds_one<M, PM>(ak, qk, s_tf, j, threadIdx.x & 31);
+}
+
+template <int M>
+__global__ __launch_bounds__(256) void k_pixels_batch(UpdateArgs a, BatchArgs b, ValueTableArgs v)
+{
+    const PairDesc pd = b.pairs[blockIdx.y];
+    const uint32_t p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (p >= pd.W) return;
+    UpdateArgs ak;
+    QueryArgs qk;
+    pair_args(a, b, pd, ak, qk);
+    pixels_one<M>(ak, qk, v, p, threadIdx.x & 31);
+}
+
 template <int M, int PM>
 cudaError_t run_bins(cudaStream_t s, const UpdateArgs& a, const QueryArgs& qa, const ValueTableArgs& v)
 {
@@ -429,6 +489,29 @@ template <int M>
 cudaError_t run_bins_m(cudaStream_t s, const UpdateArgs& a, const QueryArgs& qa, const ValueTableArgs& v)
 {
     return a.prm.P == 1.0f ? run_bins<M, POW_ONE>(s, a, qa, v) : run_bins<M, POW_GEN>(s, a, qa, v);
+}
+
+template <int M, int PM>
+cudaError_t run_bins_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b, const ValueTableArgs& v)
+{
+    if (a.n == 0 || b.n_pairs == 0) return cudaSuccess;
+    const size_t smem = (size_t)M * (a.T + 1) * sizeof(float);
+    static size_t set_bytes = 0;                 // attribute set once per size (not during capture)
+    if (smem > set_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(k_bounds_batch<M, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        set_bytes = smem;
+    }
+    if (b.max_W > 1) k_bounds_batch<M, PM><<<dim3((b.max_W - 1 + 7) / 8, b.n_pairs), 256, smem, s>>>(a, b);
+    k_pixels_batch<M><<<dim3((b.max_W + 7) / 8, b.n_pairs), 256, 0, s>>>(a, b, v);
+    return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t run_bins_batch_m(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b, const ValueTableArgs& v)
+{
+    return a.prm.P == 1.0f ? run_bins_batch<M, POW_ONE>(s, a, b, v) : run_bins_batch<M, POW_GEN>(s, a, b, v);
 }
 
 template <int M>
@@ -477,6 +560,11 @@ cudaError_t launch_value_tables(cudaStream_t s, uint32_t M, const ValueTableArgs
 cudaError_t launch_bins(cudaStream_t s, const UpdateArgs& a, const QueryArgs& qa, const ValueTableArgs& v)
 {
     DVL_DISPATCH_M2(run_bins_m, a.M, s, a, qa, v)
+}
+
+cudaError_t launch_bins_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b, const ValueTableArgs& v)
+{
+    DVL_DISPATCH_M2(run_bins_batch_m, a.M, s, a, b, v)
 }
 
 uint64_t value_table_levels(uint64_t n_steps, uint64_t* stride)

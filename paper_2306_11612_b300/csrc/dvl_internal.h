@@ -142,6 +142,39 @@ struct UpdateArgs {
     unsigned long long* H;
     uint8_t* S;
 };
+// Batched updates: K transfer functions x V viewports.
+constexpr uint32_t MAX_BATCH_TF = 256;
+struct PairDesc {              // one (TF, viewport) pair of a batch
+    uint32_t k, W;
+    uint64_t bin_off;          // element offset of its M x W bin arrays
+    uint64_t cnt_off;          // element offset of its W counts
+    uint64_t hs_off;           // element offset of its W + 1 pixel bounds
+};
+struct BatchArgs {
+    uint32_t K, G;             // TFs, TFs per shared-memory group of pass A
+    const float* tfs;          // K x M x T alpha tables
+    UpdateConsts* consts;      // K
+    unsigned long long* tile_status;   // K x n_tiles
+    unsigned long long* chunk_prefix;  // K x n_chunks
+    unsigned long long* step_sums;     // K x n_chunks x STEPS
+    uint64_t n_tiles, n_chunks;
+    const PairDesc* pairs;     // device, n_pairs
+    uint32_t n_pairs, max_W;
+    double* sum;
+    uint32_t* vmin;
+    uint32_t* vmax;
+    float* mean;
+    float* y;
+    uint32_t* count;
+    unsigned long long* H;
+    uint8_t* S;
+    int resid;                 // pass A CTAs per SM (persistent grid)
+    int sm_count;
+};
+cudaError_t launch_prepare_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b);
+cudaError_t launch_passA_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b);
+cudaError_t launch_bins_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b, const ValueTableArgs& v);
+
 cudaError_t launch_value_tables(cudaStream_t s, uint32_t M, const ValueTableArgs& v, uint64_t* tot_lo,
                                 uint64_t* tot_hi);
 cudaError_t launch_bins(cudaStream_t s, const UpdateArgs& a, const QueryArgs& qa, const ValueTableArgs& v);

@@ -67,6 +67,8 @@ __device__ void finish_consts(UpdateConsts* C, const UpdateArgs& a, uint32_t max
     C->linear = 0;
 }
 
+__device__ void prepare_consts_block(const UpdateArgs& a);
+
 __global__ void k_prepare(UpdateArgs a, uint32_t n_tiles)
 {
     // clear bins and scan state
@@ -83,15 +85,23 @@ __global__ void k_prepare(UpdateArgs a, uint32_t n_tiles)
          i += (uint64_t)gridDim.x * blockDim.x)
         a.tile_status[i] = 0ull;
     if (blockIdx.x != 0) return;
+    if (threadIdx.x == 0) {
+        a.counters[0] = 0u;
+        a.counters[1] = 0u;
+    }
+    prepare_consts_block(a);
+}
 
+// Per-TF constants (one block of 256 threads): TF domains, Eq. 5 entry range,
+// Eq. 6 max-variation approximation and the fixed-point exponent.
+__device__ void prepare_consts_block(const UpdateArgs& a)
+{
     __shared__ int s_i[DVL_MAX_FIELDS], s_j[DVL_MAX_FIELDS];
     __shared__ float s_spread[256];
     UpdateConsts* C = a.consts;
     const uint32_t M = a.M, T = a.T;
     const int tid = threadIdx.x;
     if (tid == 0) {
-        a.counters[0] = 0u;
-        a.counters[1] = 0u;
         C->P = a.prm.P;
         C->min_imp = a.prm.min_importance;
         C->min_imp_mode = (int)a.prm.min_imp_mode;
@@ -648,6 +658,157 @@ __global__ void k_finalize(UpdateArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// Batched updates: constants of K TFs, and pass A over all of them
+// ---------------------------------------------------------------------------
+
+__global__ void k_prepare_batch(UpdateArgs a, BatchArgs b)
+{
+    UpdateArgs ak = a;
+    ak.tf = b.tfs + (uint64_t)blockIdx.x * a.M * a.T;
+    ak.consts = b.consts + blockIdx.x;
+    prepare_consts_block(ak);
+}
+
+// Persistent pass A for K transfer functions that share the TF domains: a
+// warp step's cells are loaded and normalised once per group of G TFs whose
+// tables sit in shared memory; per TF it writes step totals and, per tile,
+// runs its own decoupled look-back scan.
+template <int M, int PM>
+__global__ __launch_bounds__(WARPS * 32) void k_passA_batch(UpdateArgs a, BatchArgs b)
+{
+    extern __shared__ float s_tf[];                    // G x M x (T+1) tables, then G x 4 params
+    __shared__ unsigned long long s_ct[WARPS][MAX_BATCH_TF];
+    __shared__ uint32_t s_tile;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t T = a.T, T1 = T + 1, K = b.K, G = b.G;
+    float* s_par = s_tf + ((G * M * T1 + 3) & ~3u);
+    const UpdateConsts* C0 = b.consts;
+    float lo[M], sc[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) { lo[m] = C0->lo[m]; sc[m] = C0->s[m]; }
+    const float Tf = (float)T, P = C0->P;
+    const int n2 = C0->pow_n2, wshift = C0->width_shift;
+
+    while (true) {
+        if (tid == 0) s_tile = atomicAdd(&a.counters[0], 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= b.n_tiles) break;                  // block-uniform
+        for (uint32_t k = lane; k < K; k += 32) s_ct[warp][k] = 0ull;
+        const uint64_t chunk = (uint64_t)tile * WARPS + warp;
+        const uint64_t base = chunk * CHUNK;
+        for (uint32_t g0 = 0; g0 < K; g0 += G) {
+            const uint32_t gk = K - g0 < G ? K - g0 : G;
+            __syncthreads();                           // the previous group's tables are free
+            for (uint32_t i = tid; i < gk * M * T1; i += blockDim.x) {
+                const uint32_t kk = i / (M * T1), r = i - kk * M * T1, m = r / T1, e = r - m * T1;
+                s_tf[i] = b.tfs[((uint64_t)(g0 + kk) * M + m) * T + (e < T ? e : T - 1)];
+            }
+            for (uint32_t kk = tid; kk < gk; kk += blockDim.x) {
+                const UpdateConsts* Ck = b.consts + g0 + kk;
+                const bool after = Ck->min_imp_mode == DVL_MINIMP_AFTER_POWER;
+                s_par[kk * 4 + 0] = Ck->inv_vmax;
+                s_par[kk * 4 + 1] = after ? 0.0f : Ck->min_imp;
+                s_par[kk * 4 + 2] = after ? Ck->min_imp : 0.0f;
+                s_par[kk * 4 + 3] = Ck->qscale;
+            }
+            __syncthreads();
+            if (base >= a.n) continue;
+            for (int st = 0; st < STEPS; ++st) {
+                if (base + (uint64_t)st * STEP >= a.n) break;            // warp-uniform
+                const uint64_t idx = base + st * STEP + lane * 4;
+                uint32_t e[4][M], L4 = 0;
+                bool valid[4];
+                if (idx < a.n) {
+                    float v[4][M];
+                    load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+#pragma unroll
+                        for (int m = 0; m < M; ++m) e[j][m] = floor_small(__fmul_rn(norm_t(v[j][m], lo[m], sc[m]), Tf));
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) valid[j] = idx + j < a.n;
+                for (uint32_t kk = 0; kk < gk; ++kk) {
+                    const float* tk = s_tf + kk * M * T1;
+                    const float inv = s_par[kk * 4 + 0], mb = s_par[kk * 4 + 1], ma = s_par[kk * 4 + 2],
+                                qs = s_par[kk * 4 + 3];
+                    unsigned long long l = 0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (!valid[j]) continue;
+                        float hi = tk[e[j][0]], lw = hi;
+#pragma unroll
+                        for (int m = 1; m < M; ++m) {
+                            const float al = tk[m * T1 + e[j][m]];
+                            hi = fmaxf(hi, al);
+                            lw = fminf(lw, al);
+                        }
+                        const float f = importance<PM>(__fsub_rn(hi, lw), (L4 >> (8 * j)) & 0xFF, inv, mb, ma, wshift,
+                                                       n2, P);
+                        l += __float2uint_rn(__fmul_rn(f, qs));
+                    }
+                    const unsigned long long tot = warp_total_small(l);
+                    if (lane == 0) {
+                        b.step_sums[((uint64_t)(g0 + kk) * b.n_chunks + chunk) * STEPS + st] = tot;
+                        s_ct[warp][g0 + kk] += tot;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (uint32_t k = 0; k < K; ++k) {
+                unsigned long long w = lane < WARPS ? s_ct[lane][k] : 0ull;
+                unsigned long long incl = warp_incl_scan_u64(w, lane);
+                const unsigned long long agg = __shfl_sync(FULL, incl, WARPS - 1);
+                unsigned long long* status = b.tile_status + (uint64_t)k * b.n_tiles;
+                if (lane == 0) st_relaxed(status + tile, (tile == 0 ? FLAG_P : FLAG_A) | agg);
+                unsigned long long excl = 0;
+                if (tile > 0) {
+                    int64_t end = (int64_t)tile - 1;
+                    while (true) {
+                        const int64_t jt = end - lane;
+                        unsigned long long sv = FLAG_P;
+                        if (jt >= 0) {
+                            long long spins = 0;
+                            while (true) {
+                                sv = ld_relaxed(status + jt);
+                                if (sv >> 62) break;
+                                if (++spins > a.spin_limit) {
+                                    atomicOr(a.err, ERR_TIMEOUT);
+                                    sv = FLAG_P;
+                                    break;
+                                }
+                                __nanosleep(100);
+                            }
+                        }
+                        const unsigned pmask = __ballot_sync(FULL, (sv & FLAG_P) != 0);
+                        const int first = pmask ? __ffs(pmask) - 1 : 31;
+                        excl += warp_sum_u64(lane <= first ? (sv & VAL_MASK) : 0ull);
+                        if (pmask) break;
+                        end -= 32;
+                    }
+                    if (lane == 0) st_relaxed(status + tile, FLAG_P | (excl + agg));
+                }
+                if (lane < WARPS) b.chunk_prefix[(uint64_t)k * b.n_chunks + (uint64_t)tile * WARPS + lane] = excl + incl - w;
+                if (lane == 0 && tile == b.n_tiles - 1) {
+                    UpdateConsts* Ck = b.consts + k;
+                    unsigned long long F = excl + agg;
+                    int linear = 0;
+                    if (F == 0 && a.n > 0) { F = a.n; linear = 1; }
+                    Ck->F = F;
+                    Ck->linear = linear;
+                    Ck->F_div_W = 0;
+                    Ck->F_mod_W = 0;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Differentiable path: control points -> alpha tables, and the adjoint of the
 // per-pixel alpha means with the assignment held fixed
 // ---------------------------------------------------------------------------
@@ -956,6 +1117,39 @@ cudaError_t run_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* 
     }
 
 cudaError_t launch_update(cudaStream_t s, const UpdateArgs& a) { DVL_DISPATCH_M(run_update, s, a) }
+
+cudaError_t launch_prepare_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
+{
+    k_prepare_batch<<<b.K, 256, 0, s>>>(a, b);
+    return cudaGetLastError();
+}
+
+template <int M, int PM>
+cudaError_t run_passA_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
+{
+    const size_t smem = (size_t)(((b.G * M * (a.T + 1) + 3) & ~3u) + 4 * b.G) * sizeof(float);
+    static size_t set_bytes = 0;                 // attribute set once per size (not during capture)
+    if (smem > set_bytes) {
+        cudaError_t e = smem_attr(k_passA_batch<M, PM>, smem);
+        if (e != cudaSuccess) return e;
+        set_bytes = smem;
+    }
+    uint64_t grid = (uint64_t)b.sm_count * b.resid;
+    if (grid > b.n_tiles) grid = b.n_tiles;
+    if (grid) k_passA_batch<M, PM><<<(unsigned)grid, WARPS * 32, smem, s>>>(a, b);
+    return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t run_passA_batch_m(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
+{
+    return a.prm.P == 1.0f ? run_passA_batch<M, POW_ONE>(s, a, b) : run_passA_batch<M, POW_GEN>(s, a, b);
+}
+
+cudaError_t launch_passA_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
+{
+    DVL_DISPATCH_M(run_passA_batch_m, s, a, b)
+}
 
 cudaError_t launch_ctrl_table(cudaStream_t s, uint32_t M, uint32_t K, uint32_t T, const float* ctrl, float* tf,
                               uint32_t* err)
