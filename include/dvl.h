@@ -254,6 +254,41 @@ int dvl_get_timings(dvl_ctx* ctx, double* ms, int n);
 enum { DVL_OPT_SPIN_LIMIT = 1, DVL_OPT_FAULT_NO_PUBLISH = 2, DVL_OPT_TIMING = 3 };
 int dvl_set_option(dvl_ctx* ctx, int option, int64_t value);
 
+/* Batched update: K transfer functions, each with any number of viewport
+ * widths, over the loaded data set (paper Sec. 3.3-3.4 per (TF, width) pair;
+ * the batching itself is not in the paper -- it serves many clients editing
+ * TFs of one resident data set).  Results equal dvl_update's for the same TF,
+ * domain, params and width, bit for bit.
+ *   alphas      K x n_fields x n_entries alpha tables in [0, 1], TF-major
+ *               (TF k, field m at alphas + (k*n_fields + m)*n_entries);
+ *               host or device per mem_kind
+ *   domain      host, 2*n_fields floats (lo[0..M), hi[0..M)), shared by all K
+ *               TFs; NaN/NaN = the field's data range; NULL = all data ranges
+ *   params      P, min_importance, min_imp_mode, width_mode as dvl_update;
+ *               vmax_mode must be DVL_VMAX_APPROX, want_alpha 0; width ignored
+ *   pair_tf     host, n_pairs TF indices (< K)
+ *   pair_width  host, n_pairs widths in [1, DVL_MAX_WIDTH]
+ * K <= DVL_MAX_BATCH_TF, 1 <= n_pairs <= DVL_MAX_BATCH_PAIRS.  The first call
+ * with a new shape (n_fields, n_entries, K, P == 1, the pair list) times a few
+ * launch configurations and keeps the fastest; later calls of that shape
+ * replay one captured CUDA graph.  Asynchronous on the context's stream.
+ * Errors: DVL_ERR_ARG, DVL_ERR_STATE (no order built), DVL_ERR_NOMEM,
+ * DVL_ERR_CUDA; device-side errors (DVL_ERR_TIMEOUT, DVL_ERR_RANGE) surface in
+ * dvl_read_batch_bins. */
+enum { DVL_MAX_BATCH_TF = 256, DVL_MAX_BATCH_PAIRS = 4096 };
+int dvl_update_batch(dvl_ctx* ctx, const float* alphas, uint32_t K, uint32_t n_entries, int mem_kind,
+                     const float* domain, const dvl_params* params, const uint32_t* pair_tf,
+                     const uint32_t* pair_width, uint32_t n_pairs);
+
+/* Bins of pair `pair` of the last dvl_update_batch (layout as dvl_read_bins
+ * with W = pair_width[pair]).  Synchronises the stream. */
+int dvl_read_batch_bins(dvl_ctx* ctx, uint32_t pair, uint32_t field, const dvl_bins* out);
+
+/* Launch configuration the batch autotuner chose for the last batch shape:
+ * out[0] = TFs per shared-memory group, out[1] = pass-A CTAs per SM,
+ * out[2] = 1 if the last call replayed a captured graph. */
+int dvl_batch_config(dvl_ctx* ctx, int32_t out[3]);
+
 /* One DVL update that allocates no device memory, for callers that must not
  * call cudaMalloc or cudaFree at that point (a render or UI callback inside a
  * memory budget owned by someone else, a process limited to a fixed pool, code

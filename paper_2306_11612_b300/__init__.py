@@ -32,6 +32,7 @@ OPT_SPIN_LIMIT, OPT_FAULT_NO_PUBLISH, OPT_TIMING = 1, 2, 3
 EXPORTS = ["dvl_create", "dvl_destroy", "dvl_load_amr", "dvl_build_order", "dvl_set_fields",
            "dvl_set_tf", "dvl_update", "dvl_read_bins", "dvl_get_stats", "dvl_read_order",
            "dvl_read_widths", "dvl_sync", "dvl_set_option", "dvl_get_timings", "dvl_update_noalloc", "dvl_set_tf_ctrl", "dvl_read_alpha_means", "dvl_backward",
+           "dvl_update_batch", "dvl_read_batch_bins", "dvl_batch_config",
            "dvl_status_string", "dvl_last_error"]
 
 
@@ -79,6 +80,9 @@ def _load():
         "dvl_set_tf_ctrl": ([vp, vp, u32, u32, vp, i32], i32),
         "dvl_read_alpha_means": ([vp, vp, i32], i32),
         "dvl_backward": ([vp, vp, i32, vp, i32], i32),
+        "dvl_update_batch": ([vp, vp, u32, u32, i32, vp, ctypes.POINTER(dvl_params), vp, vp, u32], i32),
+        "dvl_read_batch_bins": ([vp, u32, u32, ctypes.POINTER(dvl_bins)], i32),
+        "dvl_batch_config": ([vp, ctypes.POINTER(ctypes.c_int32)], i32),
         "dvl_status_string": ([i32], ctypes.c_char_p),
         "dvl_last_error": ([vp], ctypes.c_char_p),
     }
@@ -242,11 +246,8 @@ class DVL:
 
     backward = dvl_backward
 
-    def dvl_read_bins(self, field: int, out: dict | None = None) -> dict:
-        """Bins of one field.  ``out`` may map names (mean, min, max, y, sum,
-        count) to preallocated arrays/tensors (all host or all device); by
-        default fresh numpy arrays are returned."""
-        W = self.W
+    @staticmethod
+    def _bins_struct(W, out):
         if out is None:
             out = dict(mean=np.empty(W, np.float32), min=np.empty(W, np.float32), max=np.empty(W, np.float32),
                        y=np.empty(W, np.float32), sum=np.empty(W, np.float64), count=np.empty(W, np.uint32))
@@ -262,8 +263,53 @@ class DVL:
                 keep.append(kk)
                 setattr(b, name, p)
         b.mem_kind = kind if kind is not None else MEM_HOST
+        return out, b, keep
+
+    def dvl_read_bins(self, field: int, out: dict | None = None) -> dict:
+        """Bins of one field.  ``out`` may map names (mean, min, max, y, sum,
+        count) to preallocated arrays/tensors (all host or all device); by
+        default fresh numpy arrays are returned."""
+        out, b, keep = self._bins_struct(self.W, out)
         self._check(lib.dvl_read_bins(self._h, field, ctypes.byref(b)))
         return out
+
+    def dvl_update_batch(self, alphas, pairs, domain=None, P=1.0, min_importance=0.025, min_imp_mode=0,
+                         width_mode=0):
+        """Batched update: ``alphas`` (K, M, T) alpha tables (numpy / CPU
+        tensor, or a CUDA tensor that stays on the device), ``pairs`` a list
+        of (tf_index, width); ``domain`` 2*M floats shared by all TFs (None =
+        data ranges)."""
+        p, kind, keep = _ptr_kind(alphas)
+        K, M, T = (int(x) for x in alphas.shape)
+        if M != self.M:
+            raise ValueError(f"alphas has {M} fields, the data set {self.M}")
+        tf = np.ascontiguousarray([q[0] for q in pairs], np.uint32)
+        wd = np.ascontiguousarray([q[1] for q in pairs], np.uint32)
+        dom = None
+        if domain is not None:
+            dom = (ctypes.c_float * (2 * self.M))(*[float(x) for x in domain])
+        prm = dvl_params(P, min_importance, 1, min_imp_mode, 0, width_mode, 0)
+        self._check(lib.dvl_update_batch(self._h, p, K, T, kind, dom, ctypes.byref(prm), tf.ctypes.data,
+                                         wd.ctypes.data, len(pairs)))
+        self._pairs = [(int(a), int(b)) for a, b in zip(tf, wd)]
+
+    update_batch = dvl_update_batch
+
+    def dvl_read_batch_bins(self, pair: int, field: int, out: dict | None = None) -> dict:
+        """Bins of one field of pair ``pair`` of the last batched update."""
+        out, b, keep = self._bins_struct(self._pairs[pair][1], out)
+        self._check(lib.dvl_read_batch_bins(self._h, pair, field, ctypes.byref(b)))
+        return out
+
+    read_batch_bins = dvl_read_batch_bins
+
+    def dvl_batch_config(self) -> dict:
+        """Launch configuration chosen for the last batch shape."""
+        c = (ctypes.c_int32 * 3)()
+        self._check(lib.dvl_batch_config(self._h, c))
+        return dict(group=c[0], ctas_per_sm=c[1], replayed=bool(c[2]))
+
+    batch_config = dvl_batch_config
 
     read_bins = dvl_read_bins
 

@@ -143,7 +143,7 @@ struct UpdateArgs {
     uint8_t* S;
 };
 // Batched updates: K transfer functions x V viewports.
-constexpr uint32_t MAX_BATCH_TF = 256;
+constexpr uint32_t MAX_BATCH_TF = DVL_MAX_BATCH_TF;
 struct PairDesc {              // one (TF, viewport) pair of a batch
     uint32_t k, W;
     uint64_t bin_off;          // element offset of its M x W bin arrays
@@ -173,6 +173,8 @@ struct BatchArgs {
 };
 cudaError_t launch_prepare_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b);
 cudaError_t launch_passA_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b);
+// Resident pass-A batch CTAs per SM for groups of G tables (0 = does not fit).
+cudaError_t passA_batch_occupancy(const UpdateArgs& a, uint32_t G, int* blocks);
 cudaError_t launch_bins_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b, const ValueTableArgs& v);
 
 cudaError_t launch_value_tables(cudaStream_t s, uint32_t M, const ValueTableArgs& v, uint64_t* tot_lo,

@@ -666,6 +666,8 @@ __global__ void k_prepare_batch(UpdateArgs a, BatchArgs b)
     UpdateArgs ak = a;
     ak.tf = b.tfs + (uint64_t)blockIdx.x * a.M * a.T;
     ak.consts = b.consts + blockIdx.x;
+    for (uint32_t i = threadIdx.x; i < a.M * a.T; i += blockDim.x)
+        if (!(ak.tf[i] >= 0.0f && ak.tf[i] <= 1.0f)) atomicOr(a.err, ERR_RANGE);
     prepare_consts_block(ak);
 }
 
@@ -757,8 +759,9 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA_batch(UpdateArgs a, BatchA
             }
         }
         __syncthreads();
-        if (warp == 0) {
-            for (uint32_t k = 0; k < K; ++k) {
+        {
+            // one look-back per TF; the warps take the TFs in turn
+            for (uint32_t k = warp; k < K; k += WARPS) {
                 unsigned long long w = lane < WARPS ? s_ct[lane][k] : 0ull;
                 unsigned long long incl = warp_incl_scan_u64(w, lane);
                 const unsigned long long agg = __shfl_sync(FULL, incl, WARPS - 1);
@@ -1149,6 +1152,29 @@ cudaError_t run_passA_batch_m(cudaStream_t s, const UpdateArgs& a, const BatchAr
 cudaError_t launch_passA_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
 {
     DVL_DISPATCH_M(run_passA_batch_m, s, a, b)
+}
+
+template <int M, int PM>
+cudaError_t occupancy_passA_batch(const UpdateArgs& a, uint32_t G, int* blocks)
+{
+    const size_t smem = (size_t)(((G * M * (a.T + 1) + 3) & ~3u) + 4 * G) * sizeof(float);
+    *blocks = 0;
+    if (smem + sizeof(unsigned long long) * WARPS * MAX_BATCH_TF + 16 > 227 * 1024) return cudaSuccess;
+    cudaError_t e = smem_attr(k_passA_batch<M, PM>, smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_passA_batch<M, PM>, WARPS * 32, smem);
+}
+
+template <int M>
+cudaError_t occupancy_passA_batch_m(const UpdateArgs& a, uint32_t G, int* blocks)
+{
+    return a.prm.P == 1.0f ? occupancy_passA_batch<M, POW_ONE>(a, G, blocks)
+                           : occupancy_passA_batch<M, POW_GEN>(a, G, blocks);
+}
+
+cudaError_t passA_batch_occupancy(const UpdateArgs& a, uint32_t G, int* blocks)
+{
+    DVL_DISPATCH_M(occupancy_passA_batch_m, a, G, blocks)
 }
 
 cudaError_t launch_ctrl_table(cudaStream_t s, uint32_t M, uint32_t K, uint32_t T, const float* ctrl, float* tf,
