@@ -132,6 +132,7 @@ class DVL:
         self.n = 0
         self.M = 0
         self.W = 0
+        self._pairs = []
 
     def _check(self, rc):
         if rc:
@@ -281,7 +282,7 @@ class DVL:
         data ranges)."""
         p, kind, keep = _ptr_kind(alphas)
         K, M, T = (int(x) for x in alphas.shape)
-        if M != self.M:
+        if self.M and M != self.M:
             raise ValueError(f"alphas has {M} fields, the data set {self.M}")
         tf = np.ascontiguousarray([q[0] for q in pairs], np.uint32)
         wd = np.ascontiguousarray([q[1] for q in pairs], np.uint32)
@@ -297,7 +298,8 @@ class DVL:
 
     def dvl_read_batch_bins(self, pair: int, field: int, out: dict | None = None) -> dict:
         """Bins of one field of pair ``pair`` of the last batched update."""
-        out, b, keep = self._bins_struct(self._pairs[pair][1], out)
+        W = self._pairs[pair][1] if 0 <= pair < len(self._pairs) else 1   # bad index: the library reports it
+        out, b, keep = self._bins_struct(W, out)
         self._check(lib.dvl_read_batch_bins(self._h, pair, field, ctypes.byref(b)))
         return out
 

@@ -972,6 +972,7 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
     c->b_pairs = pairs;
 
     UpdateArgs a = make_args(c, prm);
+    a.T = T;                             // the batch's table size (not the single-TF state's)
     a.W = 0;
     a.tf = nullptr;
     a.dom = c->d_bdom;
