@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline budget (rank 0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", choices=["plain", "batch"], default="plain",
+                    help="plain: one TF edit per step (default); batch: K TFs x 4 viewports per step")
+    ap.add_argument("--batch-tfs", type=int, default=64)
     return ap.parse_args()
 
 
@@ -371,10 +374,203 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# batched mode: K candidate TFs x 4 viewports per step
+# ---------------------------------------------------------------------------
+
+BATCH_WIDTHS = (512, 1024, 2048, 4096)
+BATCH_METRIC = "batched DVL throughput (cells/s per (TF, viewport) bin set)"
+
+
+def batch_tfs(K, seed, n_entries=256):
+    import numpy as np
+    import synth
+    return np.stack([synth.random_tfs(seed * 100_003 + k, n_entries=n_entries) for k in range(K)])
+
+
+def alg_ops_per_cell_tf(M=4):
+    """Algorithmic lane operations per (cell, TF) of batched pass A: M table
+    lookups, 2(M-1) min/max for the spread, the spread subtraction, three for
+    the importance (scale by 1/vmax, minimum importance, level width factor),
+    two for the fixed-point width (scale, round to integer) and one add."""
+    return M + 2 * (M - 1) + 1 + 3 + 2 + 1
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2306_11612_b300 as dvl
+    import synth
+
+    K = args.batch_tfs
+    amr = synth.make("batched", pinned=True)
+    stream = torch.cuda.Stream(local)
+    ctx = dvl.DVL(local, stream)
+    ctx.load_amr(amr.lower, amr.level, amr.fields)
+    ctx.build_order(dvl.SFC_HILBERT)
+    ctx.sync()
+    pairs = [(k, W) for k in range(K) for W in BATCH_WIDTHS]
+    n_sets = 4
+    host = [torch.from_numpy(batch_tfs(K, i)).pin_memory() for i in range(n_sets)]
+    dev = [h.to(f"cuda:{local}") for h in host]
+    kw = dict(P=args.P, min_importance=args.min_importance)
+
+    t0 = time.perf_counter()
+    ctx.update_batch(dev[0], pairs, **kw)          # autotune + value tables + graph capture
+    ctx.sync()
+    t_first = (time.perf_counter() - t0) * 1e3
+    for i in range(1, max(args.warmup, 3)):
+        ctx.update_batch(dev[i % n_sets], pairs, **kw)
+    ctx.sync()
+    cfg = ctx.batch_config()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for i in range(args.steps):
+            ctx.update_batch(dev[i % n_sets], pairs, **kw)
+        end.record(stream)
+        end.synchronize()
+    barrier()
+    ms = start.elapsed_time(end)
+    replayed = ctx.batch_config()["replayed"]
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    step_ms = ms / args.steps
+    value = amr.n * len(pairs) * world / (step_ms * 1e-3)
+
+    # per-stage device times: the same kernels as plain launches with events
+    ctx.set_option(dvl.OPT_TIMING, 1)
+    for i in range(min(args.steps, 20)):
+        ctx.update_batch(dev[i % n_sets], pairs, **kw)
+    stages = ctx.get_timings()
+    ctx.set_option(dvl.OPT_TIMING, 0)
+
+    # the same bin sets from plain single-TF updates, one after another
+    host_np = [h.numpy() for h in host]
+    barrier()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for k in range(K):
+        ctx.set_tfs(host_np[0][k])
+        for W in BATCH_WIDTHS:
+            ctx.update(width=W, **kw)
+    s1.record(stream)
+    s1.synchronize()
+    seq_ms = s0.elapsed_time(s1)
+    s0.record(stream)
+    for k in range(K):
+        ctx.set_tfs(host_np[0][k])
+        ctx.update(width=4096, **kw)
+    s1.record(stream)
+    s1.synchronize()
+    seq64_ms = s0.elapsed_time(s1)
+
+    # end to end: TFs from pinned host memory, every bin set back to the host
+    e2e = None
+    if not args.no_e2e:
+        ctx.update_batch(host[0], pairs, **kw)
+        nb, nc = ctx.batch_sizes()
+        out = {k: torch.empty(nb, dtype=dt, pin_memory=True).numpy() for k, dt in
+               [("mean", torch.float32), ("min", torch.float32), ("max", torch.float32), ("y", torch.float32),
+                ("sum", torch.float64)]}
+        out["count"] = torch.empty(nc, dtype=torch.int32, pin_memory=True).numpy()
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            ctx.update_batch(host[i % n_sets], pairs, **kw)
+            ctx.read_batch_all(out)
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": amr.n * len(pairs) * world * args.steps / el, "unit": "cells/s",
+               "h2d_bytes_per_step": int(host[0].numel() * 4), "d2h_bytes_per_step": int(nb * 24 + nc * 4),
+               "ms_per_step": el / args.steps * 1e3}
+
+    clocks = clk.summary()
+    mhz = clocks["sm_mhz"] or clocks["sm_max_mhz"] or 2032
+    props = torch.cuda.get_device_properties(local)
+    peak_ops = props.multi_processor_count * 4 * 32 * mhz * 1e6 / 1e12     # lane-ops/s, one issue per SMSP/clk
+    ops = alg_ops_per_cell_tf() * amr.n * K
+    t_a = stages["pass_a"]
+    achieved = ops / (t_a * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s", "frac": achieved / peak_ops,
+                "traffic": None, "kernel": "dvl_pass_a_batch",
+                "peak_source": f"{props.multi_processor_count} SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz "
+                               "(one instruction issue per scheduler per clock)",
+                "ops_per_cell_tf": alg_ops_per_cell_tf()}
+    line = {"metric": BATCH_METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+u64", "data": "synthetic",
+            "config": {"workload": f"batched: {amr.meta.get('levels')}-level synthetic AMR, {amr.n} cells, 4 fp32 "
+                                   f"fields, Hilbert order; {K} TFs x W in {list(BATCH_WIDTHS)} = {len(pairs)} "
+                                   "bin sets per step",
+                       "n_cells": amr.n, "tfs": K, "widths": list(BATCH_WIDTHS), "bin_sets": len(pairs),
+                       "P": args.P, "min_importance": args.min_importance,
+                       "l2": "no flush: cells (17 B/cell, ~0.9 GB) far larger than the 126 MB L2",
+                       "step": "one dvl_update_batch (graph replay), TFs already on the device"},
+            "roofline": roofline,
+            "kernels": {"prepare_ms": stages["prepare"], "pass_a_batch_ms": t_a, "bins_batch_ms": stages["pass_b"],
+                        "cell_tf_per_s": amr.n * K / (t_a * 1e-3), "autotuned": cfg,
+                        "graph_replayed": replayed, "first_call_ms_with_tuning_and_tables": t_first},
+            "sequential": {"plain_updates_same_bin_sets_ms": seq_ms,
+                           "value": amr.n * len(pairs) / (seq_ms * 1e-3),
+                           "speedup_batched": seq_ms / step_ms,
+                           "plain_updates_64_tfs_w4096_ms": seq64_ms},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": 4 * args.steps}
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = batch_cpu_baseline(args, K)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def batch_cpu_baseline(args, K, seconds=None):
+    """The oracle on a sub-box of the batched data set: plain updates for
+    (TF, viewport) pairs until the budget is spent."""
+    import oracle
+    import synth
+    seconds = args.cpu_seconds if seconds is None else seconds
+    amr = synth.make("batched", box=CPU_SAMPLE_BOX)
+    _, _, lev, fl = oracle.sorted_inputs(amr.lower, amr.level, amr.fields, oracle.SFC_HILBERT)
+    tfs = batch_tfs(K, 0)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        k, W = divmod(done, len(BATCH_WIDTHS))
+        oracle.update(fl, lev, tfs[k % K], P=args.P, min_importance=args.min_importance, width=BATCH_WIDTHS[W])
+        done += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": amr.n * done / el, "unit": "cells/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} plain (TF, viewport) updates of the {amr.n} cells in base cells {CPU_SAMPLE_BOX} "
+                      "of the batched data set"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -250,7 +250,9 @@ int dvl_get_timings(dvl_ctx* ctx, double* ms, int n);
  *                           update.
  *   DVL_OPT_TIMING          1 = record per-stage CUDA events in every
  *                           dvl_update (read with dvl_get_timings); 0 = off
- *                           (default). */
+ *                           (default).  A timed dvl_update_batch runs its
+ *                           kernels as plain launches instead of the graph
+ *                           (stages: prepare, pass A, bins, -). */
 enum { DVL_OPT_SPIN_LIMIT = 1, DVL_OPT_FAULT_NO_PUBLISH = 2, DVL_OPT_TIMING = 3 };
 int dvl_set_option(dvl_ctx* ctx, int option, int64_t value);
 
@@ -283,6 +285,13 @@ int dvl_update_batch(dvl_ctx* ctx, const float* alphas, uint32_t K, uint32_t n_e
 /* Bins of pair `pair` of the last dvl_update_batch (layout as dvl_read_bins
  * with W = pair_width[pair]).  Synchronises the stream. */
 int dvl_read_batch_bins(dvl_ctx* ctx, uint32_t pair, uint32_t field, const dvl_bins* out);
+
+/* All bins of the last dvl_update_batch in one copy per array: pair q's
+ * field m starts at element bin_off(q) + m*W_q of mean/min/max/y/sum and its
+ * counts at cnt_off(q) of count, where bin_off(q) = sum over earlier pairs of
+ * n_fields*W and cnt_off(q) = sum over earlier pairs of W.  Buffers must hold
+ * the totals.  Synchronises the stream. */
+int dvl_read_batch_all(dvl_ctx* ctx, const dvl_bins* out);
 
 /* Launch configuration the batch autotuner chose for the last batch shape:
  * out[0] = TFs per shared-memory group, out[1] = pass-A CTAs per SM,

@@ -32,7 +32,7 @@ OPT_SPIN_LIMIT, OPT_FAULT_NO_PUBLISH, OPT_TIMING = 1, 2, 3
 EXPORTS = ["dvl_create", "dvl_destroy", "dvl_load_amr", "dvl_build_order", "dvl_set_fields",
            "dvl_set_tf", "dvl_update", "dvl_read_bins", "dvl_get_stats", "dvl_read_order",
            "dvl_read_widths", "dvl_sync", "dvl_set_option", "dvl_get_timings", "dvl_update_noalloc", "dvl_set_tf_ctrl", "dvl_read_alpha_means", "dvl_backward",
-           "dvl_update_batch", "dvl_read_batch_bins", "dvl_batch_config",
+           "dvl_update_batch", "dvl_read_batch_bins", "dvl_read_batch_all", "dvl_batch_config",
            "dvl_status_string", "dvl_last_error"]
 
 
@@ -82,6 +82,7 @@ def _load():
         "dvl_backward": ([vp, vp, i32, vp, i32], i32),
         "dvl_update_batch": ([vp, vp, u32, u32, i32, vp, ctypes.POINTER(dvl_params), vp, vp, u32], i32),
         "dvl_read_batch_bins": ([vp, u32, u32, ctypes.POINTER(dvl_bins)], i32),
+        "dvl_read_batch_all": ([vp, ctypes.POINTER(dvl_bins)], i32),
         "dvl_batch_config": ([vp, ctypes.POINTER(ctypes.c_int32)], i32),
         "dvl_status_string": ([i32], ctypes.c_char_p),
         "dvl_last_error": ([vp], ctypes.c_char_p),
@@ -304,6 +305,23 @@ class DVL:
         return out
 
     read_batch_bins = dvl_read_batch_bins
+
+    def batch_sizes(self):
+        """(bins, counts) element totals of the last batch's layout."""
+        nb = sum(self.M * w for _, w in self._pairs)
+        return nb, sum(w for _, w in self._pairs)
+
+    def dvl_read_batch_all(self, out: dict | None = None) -> dict:
+        """All bins of the last batched update, pair-major (see dvl.h)."""
+        nb, nc = self.batch_sizes()
+        if out is None:
+            out = dict(mean=np.empty(nb, np.float32), min=np.empty(nb, np.float32), max=np.empty(nb, np.float32),
+                       y=np.empty(nb, np.float32), sum=np.empty(nb, np.float64), count=np.empty(nc, np.uint32))
+        out, b, keep = self._bins_struct(0, out)
+        self._check(lib.dvl_read_batch_all(self._h, ctypes.byref(b)))
+        return out
+
+    read_batch_all = dvl_read_batch_all
 
     def dvl_batch_config(self) -> dict:
         """Launch configuration chosen for the last batch shape."""

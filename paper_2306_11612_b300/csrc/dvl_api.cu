@@ -197,11 +197,13 @@ void free_dataset(dvl_ctx* c)
 }
 
 cudaError_t enqueue_batch(dvl_ctx* c, const UpdateArgs& a, const BatchArgs& b, const ValueTableArgs& v,
-                                 bool build_vt)
+                                 bool build_vt, cudaEvent_t* ev = nullptr)
 {
-    // memsets and launches only, so that the sequence can be captured
+    // memsets and launches only, so that the sequence can be captured; ev
+    // (uncaptured runs only): 5 events around prepare, pass A and the bins
     cudaStream_t s = c->stream;
     cudaError_t e;
+    if (ev) cudaEventRecord(ev[0], s);
     if ((e = cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return e;
     if (b.n_tiles &&
         (e = cudaMemsetAsync(c->d_btile, 0, (size_t)b.K * b.n_tiles * sizeof(unsigned long long), s)) != cudaSuccess)
@@ -218,8 +220,15 @@ cudaError_t enqueue_batch(dvl_ctx* c, const UpdateArgs& a, const BatchArgs& b, c
         return cudaMemsetAsync(c->d_bcount, 0, nc * sizeof(uint32_t), s);
     }
     if (build_vt && (e = launch_value_tables(s, a.M, v, c->d_vt_tot_lo, c->d_vt_tot_hi)) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], s);
     if ((e = launch_passA_batch(s, a, b)) != cudaSuccess) return e;
-    return launch_bins_batch(s, a, b, v);
+    if (ev) cudaEventRecord(ev[2], s);
+    if ((e = launch_bins_batch(s, a, b, v)) != cudaSuccess) return e;
+    if (ev) {
+        cudaEventRecord(ev[3], s);
+        cudaEventRecord(ev[4], s);
+    }
+    return cudaSuccess;
 }
 
 // Maps and clears the device error word.
@@ -1075,6 +1084,15 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
     b.resid = tuned->second.second;
     c->b_G = b.G;
     c->b_resid = b.resid;
+    if (c->timing) {
+        // per-stage events need uncaptured launches (same kernels, no graph)
+        std::array<cudaEvent_t, 5> set{};
+        for (auto& e : set) CK(cudaEventCreate(&e), "create event");
+        c->ev.push_back(set);
+        CK(enqueue_batch(c, a, b, v, false, c->ev.back().data()), "batch kernels");
+        c->have_batch = true;
+        return DVL_OK;
+    }
     // one captured graph per launch signature: every value the kernels take
     // by value, and every buffer address
     const std::vector<uint64_t> sig{c->n, M, T, K, P1, b.G, (uint64_t)b.resid, n_pairs, max_W, (uint64_t)sm,
@@ -1137,6 +1155,29 @@ int dvl_read_batch_bins(dvl_ctx* c, uint32_t pair, uint32_t field, const dvl_bin
     if (out->y) CK(cudaMemcpyAsync(out->y, c->d_by + off, W * 4, k, c->stream), "copy y");
     if (out->sum) CK(cudaMemcpyAsync(out->sum, c->d_bsum + off, W * 8, k, c->stream), "copy sum");
     if (out->count) CK(cudaMemcpyAsync(out->count, c->d_bcount + pd.cnt_off, W * 4, k, c->stream), "copy count");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return DVL_OK;
+}
+
+int dvl_read_batch_all(dvl_ctx* c, const dvl_bins* out)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (!out) return fail(c, DVL_ERR_ARG, "out is NULL");
+    if (!c->have_batch) return fail(c, DVL_ERR_STATE, "no batched update has run");
+    if (out->mem_kind != DVL_MEM_HOST && out->mem_kind != DVL_MEM_DEVICE) return fail(c, DVL_ERR_ARG, "bad mem_kind");
+    cudaSetDevice(c->device);
+    int rc = take_device_error(c);
+    if (rc) return rc;
+    const PairDesc& last = c->b_pairs.back();
+    const size_t nb = last.bin_off + (size_t)c->M * last.W, nc = last.cnt_off + last.W;
+    const cudaMemcpyKind k = kind_out(out->mem_kind);
+    if (out->mean) CK(cudaMemcpyAsync(out->mean, c->d_bmean, nb * 4, k, c->stream), "copy mean");
+    if (out->min) CK(cudaMemcpyAsync(out->min, c->d_bvmin, nb * 4, k, c->stream), "copy min");
+    if (out->max) CK(cudaMemcpyAsync(out->max, c->d_bvmax, nb * 4, k, c->stream), "copy max");
+    if (out->y) CK(cudaMemcpyAsync(out->y, c->d_by, nb * 4, k, c->stream), "copy y");
+    if (out->sum) CK(cudaMemcpyAsync(out->sum, c->d_bsum, nb * 8, k, c->stream), "copy sum");
+    if (out->count) CK(cudaMemcpyAsync(out->count, c->d_bcount, nc * 4, k, c->stream), "copy count");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     return DVL_OK;
 }

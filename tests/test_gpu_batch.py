@@ -129,6 +129,14 @@ def test_batch_graph_replay_and_device_tfs():
         ctx.update_batch(alphas, pairs)
         for q in range(K):
             _same(ctx.read_batch_bins(q, 1), first[q])
+        # the bulk read holds every pair's bins in the documented layout
+        allb = ctx.read_batch_all()
+        M = alphas.shape[1]
+        for q in (0, 7, K - 1):
+            off = q * M * 1024 + 1 * 1024
+            for k in ("mean", "min", "max", "y", "sum"):
+                assert np.array_equal(allb[k][off:off + 1024].view(np.uint8), first[q][k].view(np.uint8)), k
+            assert np.array_equal(allb["count"][q * 1024:(q + 1) * 1024], first[q]["count"])
     finally:
         ctx.close()
 
