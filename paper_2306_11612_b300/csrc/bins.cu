@@ -6,16 +6,19 @@
 // is its normalised field value t, which does not depend on the transfer
 // function.  So, once per data set and TF domain, this file builds value
 // tables -- per 128-cell step, the exact fixed-point sum of t and its min/max
-// (plus an exclusive prefix of the sums and a base-16 min/max hierarchy) --
-// and each update then needs only:
+// (an exclusive prefix of the sums, and a sparse table of min/max over every
+// power-of-two run of steps) -- and each update then needs only:
 //   k_bounds  for every pixel boundary j, H(j) = number of cells whose span
 //             starts before the boundary's first position C(j), and whether
 //             the last of them also reaches pixel j ("straddles"); found by a
-//             binary search over the scan's chunk prefixes and an exact
-//             recomputation of the widths of the one step that contains it;
+//             32-way search over the scan's chunk prefixes and an exact
+//             recomputation of the widths of the one step that contains it.
+//             It also records the partial-step sums/min/max of the two pixels
+//             that meet in that step;
 //   k_pixels  for every pixel: count = hi - lo + 1, sums from the prefix
-//             table (with the partial steps at both ends added cell by cell),
-//             min/max from the hierarchy, then mean and the alpha of the mean.
+//             table plus the two recorded partial steps, min/max from two
+//             sparse-table entries and the records, then mean and the alpha of
+//             the mean.
 // Sums are exact integer sums of floor(t * 2^95), so the bins do not depend
 // on any summation order.
 #include <cuda_runtime.h>
@@ -31,16 +34,32 @@ namespace {
 typedef unsigned __int128 u128;
 constexpr int FX_BITS = 95;          // fixed-point fraction bits of t
 
-// floor(t * 2^95) for 0 <= t <= 1 (t a float32)
+// floor(t * 2^95) for 0 <= t <= 1 (t a float32): t = mant * 2^(ex-150), so the
+// value is mant shifted left by ex - 150 + 95 (mant < 2^24, shift at most 72).
 __device__ __forceinline__ u128 fx_of(float t)
 {
     const uint32_t b = __float_as_uint(t);
-    const uint32_t ex = (b >> 23) & 0xFF;
+    const int ex = (int)(b >> 23);                    // t >= +0: no sign bit
     if (ex == 0) return 0;                            // zero or subnormal: below 2^-126
     const uint64_t mant = (b & 0x7FFFFFu) | 0x800000u;
-    const int sh = (int)ex - 150 + FX_BITS;           // t = mant * 2^(ex-150)
-    if (sh >= 0) return (u128)mant << sh;
-    return sh > -24 ? (u128)(mant >> -sh) : (u128)0;
+    const int sh = ex - 150 + FX_BITS;
+    if (sh < 0) return sh > -24 ? (u128)(mant >> -sh) : (u128)0;
+    const uint64_t lo = sh < 64 ? mant << sh : 0ull;
+    const uint64_t hi = sh <= 40 ? 0ull : (sh < 64 ? mant >> (64 - sh) : mant << (sh - 64));
+    return ((u128)hi << 64) | lo;
+}
+
+// Warp sum of per-lane values below 2^120, exact: five 24-bit limbs, each
+// summed by one redux (32 x 2^24 < 2^32), then recombined.
+__device__ __forceinline__ u128 warp_sum_limbs(u128 x)
+{
+    u128 r = 0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const uint32_t limb = (uint32_t)(x >> (24 * k)) & 0xFFFFFFu;
+        r += (u128)__reduce_add_sync(FULL, limb) << (24 * k);
+    }
+    return r;
 }
 
 __device__ __forceinline__ double fx_to_double(u128 x)
@@ -193,27 +212,105 @@ __global__ __launch_bounds__(256) void k_vt_scan3(ValueTableArgs v, const uint64
     }
 }
 
-// Level l of the min/max hierarchy: entry i covers entries 16i..16i+15 of
-// level l-1.
-__global__ void k_vt_level(ValueTableArgs v, uint64_t off_prev, uint64_t n_prev, uint64_t off, uint64_t n)
+// Level l of the min/max sparse table: entry i covers steps [i, i + 2^l)
+// (entries whose range would pass the last step are never read).
+__global__ void k_vt_level(ValueTableArgs v, int l)
 {
     const uint32_t m = blockIdx.y;
+    const uint64_t half = 1ull << (l - 1), n = v.n_steps + 1 - 2 * half;   // i + 2^l <= n_steps
+    float* mn = v.mn + (uint64_t)m * v.level_stride;
+    float* mx = v.mx + (uint64_t)m * v.level_stride;
+    const uint64_t prev = (uint64_t)(l - 1) * v.n_steps, cur = (uint64_t)l * v.n_steps;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        float mn = 3.0f, mx = -1.0f;
-        for (uint64_t c = 16 * i; c < 16 * i + 16 && c < n_prev; ++c) {
-            mn = fminf(mn, v.mn[(uint64_t)m * v.level_stride + off_prev + c]);
-            mx = fmaxf(mx, v.mx[(uint64_t)m * v.level_stride + off_prev + c]);
-        }
-        v.mn[(uint64_t)m * v.level_stride + off + i] = mn;
-        v.mx[(uint64_t)m * v.level_stride + off + i] = mx;
+        mn[cur + i] = fminf(mn[prev + i], mn[prev + i + half]);
+        mx[cur + i] = fmaxf(mx[prev + i], mx[prev + i + half]);
     }
 }
 
 // ---- queries -------------------------------------------------------------------
 
+// Last chunk whose exclusive width prefix is below X (chunk 0 always is, as
+// its prefix is 0 < X): a 32-way search, one probe per lane per round.
+__device__ __forceinline__ uint64_t find_chunk(const unsigned long long* prefix, uint64_t n_chunks,
+                                               unsigned long long X, int lane)
+{
+    uint64_t lo = 0, hi = n_chunks - 1;                  // answer in [lo, hi]
+    while (hi - lo >= 32) {
+        const uint64_t stride = (hi - lo + 32) / 32;     // 32 probes cover [lo, hi]
+        const uint64_t at = lo + (uint64_t)lane * stride;
+        const bool below = at <= hi && prefix[at] < X;
+        const unsigned mask = __ballot_sync(FULL, below);   // lane 0 is always set
+        const int last = 31 - __clz(mask);
+        const uint64_t nlo = lo + (uint64_t)last * stride;
+        const uint64_t nhi = nlo + stride - 1;
+        lo = nlo;
+        hi = nhi < hi ? nhi : hi;
+    }
+    const uint64_t at = lo + lane;
+    const unsigned mask = __ballot_sync(FULL, at <= hi && prefix[at] < X);
+    return lo + (31 - __clz(mask));
+}
+
+// Over the 128-cell step starting at cell stb (cells below ste exist), the
+// sums (fixed point), min and max of t of the cells below H ("tail") and of
+// the cells from `first` on ("head"), reduced over the warp with redux.  Each
+// cell is converted once; min/max work on the bits of t >= 0 (empty: +inf, 0,
+// which are neutral for values in [0, 1]).  Written by lane 0 to the records
+// of boundary j.
+template <int M>
+__device__ __forceinline__ void step_partials(const UpdateArgs& a, const UpdateConsts* C, const QueryArgs& qa,
+                                              uint32_t j, uint64_t stb, uint64_t ste, uint64_t H, uint64_t first,
+                                              int lane)
+{
+    const uint64_t idx = stb + lane * 4;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const float lo = C->lo[m], sc = C->s[m];
+        u128 ts = 0, hs = 0;
+        uint32_t tmn = 0x7F800000u, tmx = 0u, hmn = 0x7F800000u, hmx = 0u;
+        if (idx < ste) {
+            const float4 x = __ldg(reinterpret_cast<const float4*>(a.val + m * a.pitch + idx));
+            const float c[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint64_t cell = idx + k;
+                const float t = norm_t(c[k], lo, sc);
+                const uint32_t tb = __float_as_uint(t);
+                const u128 f = fx_of(t);
+                if (cell < H) {
+                    ts += f;
+                    tmn = min(tmn, tb);
+                    tmx = max(tmx, tb);
+                }
+                if (cell >= first && cell < ste) {
+                    hs += f;
+                    hmn = min(hmn, tb);
+                    hmx = max(hmx, tb);
+                }
+            }
+        }
+        ts = warp_sum_limbs(ts);
+        hs = warp_sum_limbs(hs);
+        tmn = __reduce_min_sync(FULL, tmn);
+        tmx = __reduce_max_sync(FULL, tmx);
+        hmn = __reduce_min_sync(FULL, hmn);
+        hmx = __reduce_max_sync(FULL, hmx);
+        if (lane == 0) {
+            const uint64_t kt = ((uint64_t)j * 2 + 0) * M + m, kh = kt + M;
+            qa.psum[kt] = make_ulonglong2((unsigned long long)(uint64_t)ts, (unsigned long long)(uint64_t)(ts >> 64));
+            qa.pmm[kt] = make_float2(__uint_as_float(tmn), __uint_as_float(tmx));
+            qa.psum[kh] = make_ulonglong2((unsigned long long)(uint64_t)hs, (unsigned long long)(uint64_t)(hs >> 64));
+            qa.pmm[kh] = make_float2(__uint_as_float(hmn), __uint_as_float(hmx));
+        }
+    }
+}
+
 // Pixel boundary j in [1, W-1]: H = #cells with span start E < C(j), and
 // whether the last of them (cell H-1) has a positive width reaching past the
-// real boundary j F / W (then it also touches pixel j).
+// real boundary j F / W (then it also touches pixel j).  Also records, over
+// the step that holds cell H-1, the partial sums/min/max of pixel j-1's last
+// cells and of pixel j's first cells, so that the pixel queries read no
+// cells except where a pixel lies inside one step.
 template <int M, int PM>
 __device__ __forceinline__ void bounds_one(const UpdateArgs& a, const QueryArgs& qa, const float* s_tf, uint32_t j,
                                            int lane)
@@ -223,67 +320,66 @@ __device__ __forceinline__ void bounds_one(const UpdateArgs& a, const QueryArgs&
     const PixelMap pm{F / a.W, F % a.W, F, a.W};
     const unsigned long long X = pm.C(j);
     const u128 jF = (u128)j * F;
+    unsigned long long H;
+    bool S;
     if (C->linear) {                                      // widths 1: E_c = c
-        const unsigned long long H = X < a.n ? X : a.n;
-        if (lane == 0) {
-            qa.H[j] = H;
-            qa.S[j] = H >= 1 && (u128)H * a.W > jF;
+        H = X < a.n ? X : a.n;
+        S = H >= 1 && (u128)H * a.W > jF;
+    } else {
+        const uint64_t n_chunks = (a.n + CHUNK - 1) / CHUNK;
+        const uint64_t chunk = find_chunk(qa.chunk_prefix, n_chunks, X, lane), base = chunk * CHUNK;
+        const uint64_t rem = a.n - base;
+        const int nsteps = rem >= (uint64_t)CHUNK ? STEPS : (int)((rem + STEP - 1) / STEP);
+        unsigned long long ssum = lane < nsteps ? qa.step_sums[chunk * STEPS + lane] : 0ull;
+        const unsigned long long start = qa.chunk_prefix[chunk] + warp_incl_scan_u64(ssum, lane) - ssum;
+        const unsigned before = __ballot_sync(FULL, lane < nsteps && start < X);
+        const int st = 31 - __clz(before);                 // last step starting before X
+        // exact widths of that step's cells
+        Cell<M, PM> cc;
+        cc.load(C, a.T);
+        const uint64_t idx = base + st * STEP + lane * 4;
+        uint32_t q[4] = {0, 0, 0, 0};
+        if (idx < a.n) {
+            float v[4][M];
+            uint32_t L4;
+            load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float t[M];
+#pragma unroll
+                for (int m = 0; m < M; ++m) t[m] = norm_t(v[c][m], cc.lo[m], cc.s[m]);
+                if (idx + c < a.n) q[c] = cc.width(t, (L4 >> (8 * c)) & 0xFF, s_tf);
+            }
         }
-        return;
-    }
-    // last chunk whose first cell starts before X (chunk 0 starts at 0 < X)
-    const uint64_t n_chunks = (a.n + CHUNK - 1) / CHUNK;
-    uint64_t lo = 0, hi = n_chunks - 1;
-    while (lo < hi) {
-        const uint64_t mid = (lo + hi + 1) >> 1;
-        if (qa.chunk_prefix[mid] < X) lo = mid; else hi = mid - 1;
-    }
-    const uint64_t chunk = lo, base = chunk * CHUNK;
-    const uint64_t rem = a.n - base;
-    const int nsteps = rem >= (uint64_t)CHUNK ? STEPS : (int)((rem + STEP - 1) / STEP);
-    unsigned long long ssum = lane < nsteps ? qa.step_sums[chunk * STEPS + lane] : 0ull;
-    const unsigned long long start = qa.chunk_prefix[chunk] + warp_incl_scan_u64(ssum, lane) - ssum;
-    const unsigned before = __ballot_sync(FULL, lane < nsteps && start < X);
-    const int st = 31 - __clz(before);                     // last step starting before X
-    // exact widths of that step's cells
-    Cell<M, PM> cc;
-    cc.load(C, a.T);
-    const uint64_t idx = base + st * STEP + lane * 4;
-    uint32_t q[4] = {0, 0, 0, 0};
-    if (idx < a.n) {
-        float v[4][M];
-        uint32_t L4;
-        load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
+        const unsigned long long lsum = (unsigned long long)q[0] + q[1] + q[2] + q[3];
+        unsigned long long E = __shfl_sync(FULL, start, st) + warp_incl_scan_u64(lsum, lane) - lsum;
+        uint32_t cnt = 0;
+        unsigned long long lastI = 0;
+        bool lastpos = false;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            float t[M];
-#pragma unroll
-            for (int m = 0; m < M; ++m) t[m] = norm_t(v[c][m], cc.lo[m], cc.s[m]);
-            if (idx + c < a.n) q[c] = cc.width(t, (L4 >> (8 * c)) & 0xFF, s_tf);
+            if (idx + c < a.n && E < X) {
+                ++cnt;
+                lastI = E + q[c];
+                lastpos = q[c] > 0;
+            }
+            E += q[c];
         }
+        const uint32_t total = __reduce_add_sync(FULL, cnt);
+        const unsigned has = __ballot_sync(FULL, cnt > 0);
+        const int owner = 31 - __clz(has);                 // lane holding cell H-1
+        const unsigned long long I = __shfl_sync(FULL, lastI, owner);
+        const bool pos = __shfl_sync(FULL, lastpos, owner);
+        H = base + st * STEP + total;
+        S = pos && (u128)I * a.W > jF;
     }
-    const unsigned long long lsum = (unsigned long long)q[0] + q[1] + q[2] + q[3];
-    unsigned long long E = __shfl_sync(FULL, start, st) + warp_incl_scan_u64(lsum, lane) - lsum;
-    uint32_t cnt = 0;
-    unsigned long long lastI = 0;
-    bool lastpos = false;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        if (idx + c < a.n && E < X) {
-            ++cnt;
-            lastI = E + q[c];
-            lastpos = q[c] > 0;
-        }
-        E += q[c];
-    }
-    const uint32_t total = __reduce_add_sync(FULL, cnt);
-    const unsigned has = __ballot_sync(FULL, cnt > 0);
-    const int owner = 31 - __clz(has);                     // lane holding cell H-1
-    const unsigned long long I = __shfl_sync(FULL, lastI, owner);
-    const bool pos = __shfl_sync(FULL, lastpos, owner);
+    // partial terms over the step of cell H-1 (H >= 1: the step's first cell starts before X)
+    const uint64_t stb = (H - 1) / STEP * STEP;
+    const uint64_t ste = stb + STEP < a.n ? stb + STEP : a.n;
+    step_partials<M>(a, C, qa, j, stb, ste, H, S ? H - 1 : H, lane);
     if (lane == 0) {
-        qa.H[j] = base + st * STEP + total;
-        qa.S[j] = pos && (u128)I * a.W > jF;
+        qa.H[j] = H;
+        qa.S[j] = S;
     }
 }
 
@@ -298,131 +394,107 @@ __global__ __launch_bounds__(256) void k_bounds(UpdateArgs a, QueryArgs qa)
     bounds_one<M, PM>(a, qa, s_tf, j, threadIdx.x & 31);
 }
 
-// Range min/max of t over steps [s0, s1) of one field through the hierarchy.
-__device__ __forceinline__ void steps_minmax(const ValueTableArgs& v, uint32_t m, uint64_t s0, uint64_t s1, int lane,
+// Min/max of t over steps [s0, s1) (s0 < s1) of one field: two overlapping
+// power-of-two ranges of the sparse table.
+__device__ __forceinline__ void steps_minmax(const ValueTableArgs& v, uint32_t m, uint64_t s0, uint64_t s1,
                                              float& mn, float& mx)
 {
-    uint64_t off = 0, n = v.n_steps;
-    int l = 0;
-    while (s0 < s1) {
-        const float* bmn = v.mn + (uint64_t)m * v.level_stride + off;
-        const float* bmx = v.mx + (uint64_t)m * v.level_stride + off;
-        if (s1 - s0 <= 32 || l == v.n_levels - 1) {
-            for (uint64_t k = s0 + lane; k < s1; k += 32) { mn = fminf(mn, bmn[k]); mx = fmaxf(mx, bmx[k]); }
-            break;
-        }
-        const uint64_t a = (s0 + 15) & ~15ull, b = s1 & ~15ull;
-        if (a >= b) {                                   // no whole parent block inside
-            for (uint64_t k = s0 + lane; k < s1; k += 32) { mn = fminf(mn, bmn[k]); mx = fmaxf(mx, bmx[k]); }
-            break;
-        }
-        if (lane < (int)(a - s0)) { mn = fminf(mn, bmn[s0 + lane]); mx = fmaxf(mx, bmx[s0 + lane]); }
-        if (lane < (int)(s1 - b)) { mn = fminf(mn, bmn[b + lane]); mx = fmaxf(mx, bmx[b + lane]); }
-        off += n;
-        n = (n + 15) / 16;
-        s0 = a / 16;
-        s1 = b / 16;
-        ++l;
-    }
+    const int k = 63 - __clzll((long long)(s1 - s0));
+    const uint64_t row = (uint64_t)m * v.level_stride + (uint64_t)k * v.n_steps;
+    const uint64_t b = s1 - (1ull << k);
+    mn = fminf(mn, fminf(v.mn[row + s0], v.mn[row + b]));
+    mx = fmaxf(mx, fmaxf(v.mx[row + s0], v.mx[row + b]));
 }
 
-// Sum (fixed point), min and max of t over cells [c0, c1) that lie in one step.
-template <int M>
-__device__ __forceinline__ void cells_partial(const UpdateArgs& a, const float* lo, const float* sc, uint64_t c0,
-                                              uint64_t c1, int lane, u128* sum, float* mn, float* mx)
-{
-    const uint64_t stb = c0 / STEP * STEP;
-    const uint64_t idx = stb + lane * 4;
-    if (c0 >= c1) return;
-    if (idx + 3 < c0 || idx >= c1) return;
-    const float* val = a.val;
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-        const float4 x = __ldg(reinterpret_cast<const float4*>(val + m * a.pitch + idx));
-        const float c[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (idx + j >= c0 && idx + j < c1) {
-                const float t = norm_t(c[j], lo[m], sc[m]);
-                sum[m] += fx_of(t);
-                mn[m] = fminf(mn[m], t);
-                mx[m] = fmaxf(mx[m], t);
-            }
-    }
-}
-
-// One warp per pixel: the bins of cells [lo_p, hi_p].
+// One thread per pixel: the bins of cells [lo_p, hi_p].  With s_p the step of
+// boundary p's cell H(p)-1 and s_q that of boundary p+1, the range is the
+// head recorded at boundary p, the whole steps (s_p, s_q) from the value
+// tables, and the tail recorded at boundary p+1 (the first pixel starts at
+// step 0, the last one ends with the last step).  A pixel inside a single
+// step reads its cells directly.
 template <int M>
 __device__ __forceinline__ void pixels_one(const UpdateArgs& a, const QueryArgs& qa, const ValueTableArgs& v,
-                                           uint32_t p, int lane)
+                                           uint32_t p)
 {
-    const uint64_t Hn = p + 1 < a.W ? qa.H[p + 1] : a.n;            // cells with E < C(p+1)
-    const uint64_t lo_c = p == 0 ? 0 : (qa.S[p] ? qa.H[p] - 1 : qa.H[p]);
+    const bool has_l = p > 0, has_r = p + 1 < a.W;
+    const uint64_t Hn = has_r ? qa.H[p + 1] : a.n;                 // cells with E < C(p+1)
+    const uint64_t Hp = has_l ? qa.H[p] : 0;
+    const uint64_t lo_c = has_l ? (qa.S[p] ? Hp - 1 : Hp) : 0;
     const float Tf = (float)a.T;
     if (Hn == 0 || Hn - 1 < lo_c) {                                  // no cell touches p
-        if (lane < M) {
-            const uint64_t k = (uint64_t)lane * a.W + p;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const uint64_t k = (uint64_t)m * a.W + p;
             a.sum[k] = 0.0;
             a.vmin[k] = 0u;
             a.vmax[k] = 0u;
             a.mean[k] = 0.0f;
             a.y[k] = 0.0f;
         }
-        if (lane == 0) a.count[p] = 0u;
+        a.count[p] = 0u;
         return;
     }
-    const uint64_t hi_c = Hn - 1, c1 = hi_c + 1;
-    const UpdateConsts* C = qa.consts;
-    float lo[M], sc[M], mn[M], mx[M];
-    u128 sum[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) { lo[m] = C->lo[m]; sc[m] = C->s[m]; mn[m] = 3.0f; mx[m] = -1.0f; sum[m] = 0; }
-    const uint64_t s0 = lo_c / STEP, s1 = c1 / STEP;                 // steps of the two ends
-    if (s0 == s1) {
-        cells_partial<M>(a, lo, sc, lo_c, c1, lane, sum, mn, mx);
-    } else {
-        // head [lo_c, end of its step), tail [start of c1's step, c1)
-        cells_partial<M>(a, lo, sc, lo_c, (s0 + 1) * STEP, lane, sum, mn, mx);
-        cells_partial<M>(a, lo, sc, s1 * STEP, c1, lane, sum, mn, mx);
-    }
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-        if (s1 > s0 + 1) steps_minmax(v, m, s0 + 1, s1, lane, mn[m], mx[m]);
-        sum[m] = warp_sum_u128(sum[m]);
-        mn[m] = warp_min(mn[m]);
-        mx[m] = warp_max(mx[m]);
-        if (s1 > s0 + 1) {                                            // whole steps from the prefix table
-            const uint64_t row = (uint64_t)m * (v.n_steps + 1);
-            const u128 pa = ((u128)v.pre_hi[row + s0 + 1] << 64) | v.pre_lo[row + s0 + 1];
-            const u128 pb = ((u128)v.pre_hi[row + s1] << 64) | v.pre_lo[row + s1];
-            sum[m] += pb - pa;
-        }
-    }
+    const uint64_t c1 = Hn;
     const uint32_t count = (uint32_t)(c1 - lo_c);
-    if (lane < M) {
-        // each of the first M lanes writes one field (values are warp-uniform)
-        double s = 0.0;
-        float n_ = 0.0f, x_ = 0.0f;
-#pragma unroll
-        for (int m = 0; m < M; ++m)
-            if (m == lane) { s = fx_to_double(sum[m]); n_ = mn[m]; x_ = mx[m]; }
-        const uint64_t k = (uint64_t)lane * a.W + p;
+    const UpdateConsts* C = qa.consts;
+    const uint64_t sp = has_l ? (Hp - 1) / STEP : 0, sq = has_r ? (Hn - 1) / STEP : 0;
+    const bool one_step = has_l && has_r && sp == sq;
+    const uint64_t w0 = has_l ? sp + 1 : 0, w1 = has_r ? sq : v.n_steps;   // whole steps [w0, w1)
+#pragma unroll 1
+    for (int m = 0; m < M; ++m) {
+        float mn = 3.0f, mx = -1.0f;
+        u128 sum = 0;
+        if (one_step) {
+            const float lo = C->lo[m], sc = C->s[m];
+            for (uint64_t c = lo_c; c < c1; ++c) {
+                const float t = norm_t(__ldg(a.val + m * a.pitch + c), lo, sc);
+                sum += fx_of(t);
+                mn = fminf(mn, t);
+                mx = fmaxf(mx, t);
+            }
+        } else {
+            if (w1 > w0) {
+                steps_minmax(v, m, w0, w1, mn, mx);
+                const uint64_t row = (uint64_t)m * (v.n_steps + 1);
+                const u128 pa = ((u128)v.pre_hi[row + w0] << 64) | v.pre_lo[row + w0];
+                const u128 pb = ((u128)v.pre_hi[row + w1] << 64) | v.pre_lo[row + w1];
+                sum = pb - pa;
+            }
+            if (has_l) {
+                const uint64_t k = ((uint64_t)p * 2 + 1) * M + m;
+                const ulonglong2 ps = qa.psum[k];
+                const float2 mm = qa.pmm[k];
+                sum += ((u128)ps.y << 64) | ps.x;
+                mn = fminf(mn, mm.x);
+                mx = fmaxf(mx, mm.y);
+            }
+            if (has_r) {
+                const uint64_t k = ((uint64_t)(p + 1) * 2 + 0) * M + m;
+                const ulonglong2 ps = qa.psum[k];
+                const float2 mm = qa.pmm[k];
+                sum += ((u128)ps.y << 64) | ps.x;
+                mn = fminf(mn, mm.x);
+                mx = fmaxf(mx, mm.y);
+            }
+        }
+        const double s = fx_to_double(sum);
+        const uint64_t k = (uint64_t)m * a.W + p;
         const float mean = __double2float_rn(__ddiv_rn(s, (double)count));
         a.sum[k] = s;
-        a.vmin[k] = __float_as_uint(n_);
-        a.vmax[k] = __float_as_uint(x_);
+        a.vmin[k] = __float_as_uint(mn);
+        a.vmax[k] = __float_as_uint(mx);
         a.mean[k] = mean;
-        a.y[k] = a.tf[lane * a.T + tf_entry(mean, Tf, a.T - 1)];
+        a.y[k] = a.tf[m * a.T + tf_entry(mean, Tf, a.T - 1)];
     }
-    if (lane == 0) a.count[p] = count;
+    a.count[p] = count;
 }
 
 template <int M>
 __global__ __launch_bounds__(256) void k_pixels(UpdateArgs a, QueryArgs qa, ValueTableArgs v)
 {
-    const uint32_t p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.W) return;
-    pixels_one<M>(a, qa, v, p, threadIdx.x & 31);
+    pixels_one<M>(a, qa, v, p);
 }
 
 // The arguments of pair y of a batch: one TF's scan, one viewport's bins.
@@ -443,6 +515,8 @@ __device__ __forceinline__ void pair_args(const UpdateArgs& a, const BatchArgs& 
     qk.step_sums = b.step_sums + (uint64_t)pd.k * b.n_chunks * STEPS;
     qk.H = b.H + pd.hs_off;
     qk.S = b.S + pd.hs_off;
+    qk.psum = b.psum + pd.hs_off * 2 * a.M;
+    qk.pmm = b.pmm + pd.hs_off * 2 * a.M;
 }
 
 template <int M, int PM>
@@ -465,12 +539,12 @@ template <int M>
 __global__ __launch_bounds__(256) void k_pixels_batch(UpdateArgs a, BatchArgs b, ValueTableArgs v)
 {
     const PairDesc pd = b.pairs[blockIdx.y];
-    const uint32_t p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= pd.W) return;
     UpdateArgs ak;
     QueryArgs qk;
     pair_args(a, b, pd, ak, qk);
-    pixels_one<M>(ak, qk, v, p, threadIdx.x & 31);
+    pixels_one<M>(ak, qk, v, p);
 }
 
 template <int M, int PM>
@@ -481,7 +555,7 @@ cudaError_t run_bins(cudaStream_t s, const UpdateArgs& a, const QueryArgs& qa, c
     cudaError_t e = cudaFuncSetAttribute(k_bounds<M, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (a.W > 1) k_bounds<M, PM><<<(a.W - 1 + 7) / 8, 256, smem, s>>>(a, qa);
-    k_pixels<M><<<(a.W + 7) / 8, 256, 0, s>>>(a, qa, v);
+    k_pixels<M><<<(a.W + 255) / 256, 256, 0, s>>>(a, qa, v);
     return cudaGetLastError();
 }
 
@@ -504,7 +578,7 @@ cudaError_t run_bins_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs&
         set_bytes = smem;
     }
     if (b.max_W > 1) k_bounds_batch<M, PM><<<dim3((b.max_W - 1 + 7) / 8, b.n_pairs), 256, smem, s>>>(a, b);
-    k_pixels_batch<M><<<dim3((b.max_W + 7) / 8, b.n_pairs), 256, 0, s>>>(a, b, v);
+    k_pixels_batch<M><<<dim3((b.max_W + 255) / 256, b.n_pairs), 256, 0, s>>>(a, b, v);
     return cudaGetLastError();
 }
 
@@ -524,14 +598,10 @@ cudaError_t run_tables(cudaStream_t s, const ValueTableArgs& v, uint64_t* tot_lo
     k_vt_scan1<<<dim3(nb, M), 256, 0, s>>>(v, tot_lo, tot_hi);
     k_vt_scan2<<<M, 32, 0, s>>>(v, tot_lo, tot_hi, nb);
     k_vt_scan3<<<dim3(nb, M), 256, 0, s>>>(v, tot_lo, tot_hi);
-    uint64_t off_prev = 0, n_prev = v.n_steps, off = v.n_steps;
     for (int l = 1; l < v.n_levels; ++l) {
-        const uint64_t n = (n_prev + 15) / 16;
+        const uint64_t n = v.n_steps + 1 - (2ull << (l - 1));
         const uint64_t blocks = (n + 255) / 256;
-        k_vt_level<<<dim3((unsigned)(blocks < 4096 ? blocks : 4096), M), 256, 0, s>>>(v, off_prev, n_prev, off, n);
-        off_prev = off;
-        off += n;
-        n_prev = n;
+        k_vt_level<<<dim3((unsigned)(blocks < 4096 ? blocks : 4096), M), 256, 0, s>>>(v, l);
     }
     return cudaGetLastError();
 }
@@ -569,13 +639,9 @@ cudaError_t launch_bins_batch(cudaStream_t s, const UpdateArgs& a, const BatchAr
 
 uint64_t value_table_levels(uint64_t n_steps, uint64_t* stride)
 {
-    uint64_t n = n_steps, total = n_steps, levels = 1;
-    while (n > 32) {
-        n = (n + 15) / 16;
-        total += n;
-        ++levels;
-    }
-    *stride = total;
+    uint64_t levels = 1;                      // sparse table: levels 0 .. floor(log2(n_steps))
+    while ((2ull << (levels - 1)) <= n_steps) ++levels;
+    *stride = n_steps * levels;
     return levels;
 }
 

@@ -88,6 +88,8 @@ struct dvl_ctx {
     std::vector<float> vt_dom;
     unsigned long long* d_H = nullptr;
     uint8_t* d_S = nullptr;
+    ulonglong2* d_psum = nullptr;     // boundary partial terms, 2 x M per boundary
+    float2* d_pmm = nullptr;
     uint32_t HS_cap = 0;
     // batched updates (K TFs x viewports)
     float* d_btf = nullptr;               // K x M x T
@@ -100,6 +102,8 @@ struct dvl_ctx {
     float *d_bmean = nullptr, *d_by = nullptr;
     unsigned long long* d_bH = nullptr;
     uint8_t* d_bS = nullptr;
+    ulonglong2* d_bpsum = nullptr;
+    float2* d_bpmm = nullptr;
     size_t btf_cap = 0, bk_cap = 0, pairs_cap = 0, bbin_cap = 0, bcnt_cap = 0, bhs_cap = 0;
     std::vector<PairDesc> b_pairs;        // of the last batch
     bool have_batch = false;
@@ -174,6 +178,7 @@ void free_batch(dvl_ctx* c)
     dfree(c->d_btf); dfree(c->d_bdom); dfree(c->d_bconsts); dfree(c->d_btile); dfree(c->d_bprefix);
     dfree(c->d_bsteps); dfree(c->d_pairs); dfree(c->d_bsum); dfree(c->d_bvmin); dfree(c->d_bvmax);
     dfree(c->d_bcount); dfree(c->d_bmean); dfree(c->d_by); dfree(c->d_bH); dfree(c->d_bS);
+    dfree(c->d_bpsum); dfree(c->d_bpmm);
     c->btf_cap = c->bk_cap = c->pairs_cap = c->bbin_cap = c->bcnt_cap = c->bhs_cap = 0;
     if (c->b_graph) cudaGraphExecDestroy(c->b_graph);
     c->b_graph = nullptr;
@@ -349,6 +354,7 @@ void dvl_destroy(dvl_ctx* c)
     dfree(c->d_sum); dfree(c->d_vmin); dfree(c->d_vmax); dfree(c->d_count);
     dfree(c->d_mean); dfree(c->d_y); dfree(c->d_asum); dfree(c->d_amean); dfree(c->d_ctrl);
     dfree(c->d_gtab); dfree(c->d_gin); dfree(c->d_gout); dfree(c->d_H); dfree(c->d_S);
+    dfree(c->d_psum); dfree(c->d_pmm);
     for (auto& set : c->ev)
         for (auto e : set) cudaEventDestroy(e);
     free_batch(c);
@@ -642,6 +648,8 @@ static UpdateArgs make_args(dvl_ctx* c, const dvl_params& p)
     a.vt_tot_hi = c->d_vt_tot_hi;
     a.H = c->d_H;
     a.S = c->d_S;
+    a.psum = c->d_psum;
+    a.pmm = c->d_pmm;
     a.err = c->d_err;
     a.spin_limit = c->spin_limit;
     a.fault_no_publish = c->fault_no_publish;
@@ -673,6 +681,8 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
             CK(cudaStreamSynchronize(c->stream), "synchronize");
             CK(dalloc(c->d_H, p->width + 1), "alloc pixel bounds");
             CK(dalloc(c->d_S, p->width + 1), "alloc pixel bounds");
+            CK(dalloc(c->d_psum, (size_t)(p->width + 1) * 2 * DVL_MAX_FIELDS), "alloc pixel bounds");
+            CK(dalloc(c->d_pmm, (size_t)(p->width + 1) * 2 * DVL_MAX_FIELDS), "alloc pixel bounds");
             c->HS_cap = p->width + 1;
         }
         build_vt = !c->vt_valid || c->vt_dom.size() != c->h_dom.size() ||
@@ -970,6 +980,8 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
         if (hs_off > c->bhs_cap) {
             CK(dalloc(c->d_bH, hs_off), "alloc batch bins");
             CK(dalloc(c->d_bS, hs_off), "alloc batch bins");
+            CK(dalloc(c->d_bpsum, hs_off * 2 * M), "alloc batch bins");
+            CK(dalloc(c->d_bpmm, hs_off * 2 * M), "alloc batch bins");
             c->bhs_cap = hs_off;
         }
     }
@@ -991,6 +1003,8 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
     a.step_sums = nullptr;
     a.H = nullptr;
     a.S = nullptr;
+    a.psum = nullptr;
+    a.pmm = nullptr;
     int sm = 0;
     CK(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
     BatchArgs b{};
@@ -1013,6 +1027,8 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
     b.count = c->d_bcount;
     b.H = c->d_bH;
     b.S = c->d_bS;
+    b.psum = c->d_bpsum;
+    b.pmm = c->d_bpmm;
     b.sm_count = sm;
     ValueTableArgs v = c->vt;
     v.consts = c->d_bconsts;             // lo / s are the same for every TF of the batch
@@ -1026,7 +1042,7 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
     if (tuned == c->b_tuned.end()) {
         // autotune: TFs per shared-memory group x resident CTAs per SM, each
         // timed on this data set (all configurations give identical results)
-        b.G = K < 8 ? K : 8;
+        b.G = K <= 4 ? 4 : 8;
         b.resid = 1;
         CK(enqueue_batch(c, a, b, v, build_vt), "batch kernels");
         if (build_vt) {
@@ -1034,14 +1050,11 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
             c->vt_dom = dom;
         }
         std::vector<std::pair<int, int>> cand;
-        for (uint32_t g : {4u, 8u, 16u, 32u, 64u}) {
-            const uint32_t G = g < K ? g : K;
+        for (uint32_t G : {4u, 8u, 16u}) {        // compiled group sizes
             int blocks = 0;
             CK(passA_batch_occupancy(a, G, &blocks), "occupancy");
-            for (int r = 1; r <= blocks && r <= 4; ++r)
-                if (std::find(cand.begin(), cand.end(), std::make_pair((int)G, r)) == cand.end())
-                    cand.push_back({(int)G, r});
-            if (G == K) break;
+            for (int r = 1; r <= blocks && r <= 4; ++r) cand.push_back({(int)G, r});
+            if (G >= K) break;                      // a larger group only adds empty slots
         }
         if (cand.empty()) return fail(c, DVL_ERR_UNSUPPORTED, "TF tables too large for shared memory");
         cudaEvent_t e0, e1;
@@ -1106,6 +1119,7 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
                                     (uint64_t)c->d_bsteps, (uint64_t)c->d_pairs, (uint64_t)c->d_bsum,
                                     (uint64_t)c->d_bvmin, (uint64_t)c->d_bvmax, (uint64_t)c->d_bmean,
                                     (uint64_t)c->d_by, (uint64_t)c->d_bcount, (uint64_t)c->d_bH, (uint64_t)c->d_bS,
+                                    (uint64_t)c->d_bpsum, (uint64_t)c->d_bpmm,
                                     (uint64_t)v.pre_lo, (uint64_t)v.pre_hi, (uint64_t)v.mn, (uint64_t)v.mx};
     if (sig != c->b_graph_sig || !c->b_graph) {
         if (c->b_graph) cudaGraphExecDestroy(c->b_graph);

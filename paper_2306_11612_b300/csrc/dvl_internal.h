@@ -91,8 +91,8 @@ struct ValueTableArgs {
     uint64_t n_steps;          // ceil(n / STEP)
     uint64_t* pre_lo;          // M x (n_steps + 1): exclusive prefix of the per-step
     uint64_t* pre_hi;          //   sums of floor(t * 2^95) (u128 as two u64)
-    float* mn;                 // M x level_stride: min/max hierarchy (level 0 = steps,
-    float* mx;                 //   each further level covers 16 entries of the last)
+    float* mn;                 // M x level_stride: min/max sparse table, level l at
+    float* mx;                 //   l * n_steps, entry i = steps [i, i + 2^l)
     uint64_t level_stride;
     int n_levels;
 };
@@ -102,6 +102,12 @@ struct QueryArgs {
     const unsigned long long* step_sums;
     unsigned long long* H;     // W + 1: cells whose span starts before pixel j's first position
     uint8_t* S;                // W + 1: the last of them also touches pixel j
+    // Per boundary j and field m, the partial-step terms of its two pixels
+    // over the 128-cell step holding cell H(j)-1: side 0 = cells of that step
+    // before H(j) (pixel j-1's tail), side 1 = cells from pixel j's first cell
+    // to the step's end (its head).  Index ((j * 2 + side) * M + m).
+    ulonglong2* psum;          // fixed-point sums of t (lo, hi words)
+    float2* pmm;               // min, max of t (3, -1 if empty)
 };
 uint64_t value_table_levels(uint64_t n_steps, uint64_t* stride);
 
@@ -141,6 +147,8 @@ struct UpdateArgs {
     uint64_t* vt_tot_hi;
     unsigned long long* H;
     uint8_t* S;
+    ulonglong2* psum;          // boundary partial sums (see QueryArgs)
+    float2* pmm;
 };
 // Batched updates: K transfer functions x V viewports.
 constexpr uint32_t MAX_BATCH_TF = DVL_MAX_BATCH_TF;
@@ -168,6 +176,8 @@ struct BatchArgs {
     uint32_t* count;
     unsigned long long* H;
     uint8_t* S;
+    ulonglong2* psum;          // 2 x M per pixel bound (offset hs_off * 2 * M)
+    float2* pmm;
     int resid;                 // pass A CTAs per SM (persistent grid)
     int sm_count;
 };

@@ -674,16 +674,19 @@ __global__ void k_prepare_batch(UpdateArgs a, BatchArgs b)
 // Persistent pass A for K transfer functions that share the TF domains: a
 // warp step's cells are loaded and normalised once per group of G TFs whose
 // tables sit in shared memory; per TF it writes step totals and, per tile,
-// runs its own decoupled look-back scan.
-template <int M, int PM>
+// runs its own decoupled look-back scan.  G is a compile-time constant so the
+// TF loop unrolls; per cell the table offsets (all fields) and the level
+// factor 2^(L w) are computed once and reused by every TF of the group.
+template <int M, int PM, int G>
 __global__ __launch_bounds__(WARPS * 32) void k_passA_batch(UpdateArgs a, BatchArgs b)
 {
-    extern __shared__ float s_tf[];                    // G x M x (T+1) tables, then G x 4 params
+    extern __shared__ float4 s_dyn[];                  // G x 1 params, then G x M x (T+1) tables
     __shared__ unsigned long long s_ct[WARPS][MAX_BATCH_TF];
     __shared__ uint32_t s_tile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t T = a.T, T1 = T + 1, K = b.K, G = b.G;
-    float* s_par = s_tf + ((G * M * T1 + 3) & ~3u);
+    const uint32_t T = a.T, T1 = T + 1, K = b.K, MT1 = M * T1;
+    float4* s_par = s_dyn;                             // inv_vmax, mb, ma, qscale per TF
+    float* s_tf = reinterpret_cast<float*>(s_dyn + G);
     const UpdateConsts* C0 = b.consts;
     float lo[M], sc[M];
 #pragma unroll
@@ -702,53 +705,70 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA_batch(UpdateArgs a, BatchA
         for (uint32_t g0 = 0; g0 < K; g0 += G) {
             const uint32_t gk = K - g0 < G ? K - g0 : G;
             __syncthreads();                           // the previous group's tables are free
-            for (uint32_t i = tid; i < gk * M * T1; i += blockDim.x) {
-                const uint32_t kk = i / (M * T1), r = i - kk * M * T1, m = r / T1, e = r - m * T1;
+            for (uint32_t i = tid; i < gk * MT1; i += blockDim.x) {
+                const uint32_t kk = i / MT1, r = i - kk * MT1, m = r / T1, e = r - m * T1;
                 s_tf[i] = b.tfs[((uint64_t)(g0 + kk) * M + m) * T + (e < T ? e : T - 1)];
             }
-            for (uint32_t kk = tid; kk < gk; kk += blockDim.x) {
-                const UpdateConsts* Ck = b.consts + g0 + kk;
-                const bool after = Ck->min_imp_mode == DVL_MINIMP_AFTER_POWER;
-                s_par[kk * 4 + 0] = Ck->inv_vmax;
-                s_par[kk * 4 + 1] = after ? 0.0f : Ck->min_imp;
-                s_par[kk * 4 + 2] = after ? Ck->min_imp : 0.0f;
-                s_par[kk * 4 + 3] = Ck->qscale;
+            for (uint32_t kk = tid; kk < G; kk += blockDim.x) {
+                float4 pr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (kk < gk) {
+                    const UpdateConsts* Ck = b.consts + g0 + kk;
+                    const bool after = Ck->min_imp_mode == DVL_MINIMP_AFTER_POWER;
+                    pr = make_float4(Ck->inv_vmax, after ? 0.0f : Ck->min_imp, after ? Ck->min_imp : 0.0f,
+                                     Ck->qscale);
+                }
+                s_par[kk] = pr;
             }
             __syncthreads();
             if (base >= a.n) continue;
             for (int st = 0; st < STEPS; ++st) {
                 if (base + (uint64_t)st * STEP >= a.n) break;            // warp-uniform
                 const uint64_t idx = base + st * STEP + lane * 4;
-                uint32_t e[4][M], L4 = 0;
+                uint32_t off[4][M];
+                float lvl[4];
                 bool valid[4];
                 if (idx < a.n) {
                     float v[4][M];
+                    uint32_t L4;
                     load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
+                    for (int j = 0; j < 4; ++j) {
 #pragma unroll
-                        for (int m = 0; m < M; ++m) e[j][m] = floor_small(__fmul_rn(norm_t(v[j][m], lo[m], sc[m]), Tf));
+                        for (int m = 0; m < M; ++m)
+                            off[j][m] = m * T1 + floor_small(__fmul_rn(norm_t(v[j][m], lo[m], sc[m]), Tf));
+                        lvl[j] = exp2i((int)((L4 >> (8 * j)) & 0xFF) * wshift);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                        for (int m = 0; m < M; ++m) off[j][m] = 0;
+                        lvl[j] = 0.0f;
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) valid[j] = idx + j < a.n;
-                for (uint32_t kk = 0; kk < gk; ++kk) {
-                    const float* tk = s_tf + kk * M * T1;
-                    const float inv = s_par[kk * 4 + 0], mb = s_par[kk * 4 + 1], ma = s_par[kk * 4 + 2],
-                                qs = s_par[kk * 4 + 3];
+#pragma unroll
+                for (int kk = 0; kk < G; ++kk) {
+                    if (kk >= (int)gk) break;                              // block-uniform
+                    const float* tk = s_tf + kk * MT1;
+                    const float4 pr = s_par[kk];
                     unsigned long long l = 0;
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        if (!valid[j]) continue;
-                        float hi = tk[e[j][0]], lw = hi;
+                        float hi = tk[off[j][0]], lw = hi;
 #pragma unroll
                         for (int m = 1; m < M; ++m) {
-                            const float al = tk[m * T1 + e[j][m]];
+                            const float al = tk[off[j][m]];
                             hi = fmaxf(hi, al);
                             lw = fminf(lw, al);
                         }
-                        const float f = importance<PM>(__fsub_rn(hi, lw), (L4 >> (8 * j)) & 0xFF, inv, mb, ma, wshift,
-                                                       n2, P);
-                        l += __float2uint_rn(__fmul_rn(f, qs));
+                        // Eq. 3 as importance<PM>, with the level factor precomputed
+                        const float r = fmaxf(__fmul_rn(__fsub_rn(hi, lw), pr.x), pr.y);
+                        const float x = __fmul_rn(r, lvl[j]);
+                        const float f = fmaxf(PM == POW_ONE ? x : pow_gen(x, n2, P), pr.z);
+                        const uint32_t q = __float2uint_rn(__fmul_rn(f, pr.w));
+                        l += valid[j] ? q : 0u;
                     }
                     const unsigned long long tot = warp_total_small(l);
                     if (lane == 0) {
@@ -1059,7 +1079,7 @@ cudaError_t run_update(cudaStream_t s, const UpdateArgs& a)
     if (e != cudaSuccess) return e;
     if (a.vt) {
         // bins as range queries over the value tables (writes final bins)
-        const QueryArgs qa{a.consts, a.chunk_prefix, a.step_sums, a.H, a.S};
+        const QueryArgs qa{a.consts, a.chunk_prefix, a.step_sums, a.H, a.S, a.psum, a.pmm};
         if ((e = launch_bins(s, a, qa, *a.vt)) != cudaSuccess) return e;
         if (a.events) cudaEventRecord(a.events[3], s);
     } else {
@@ -1127,20 +1147,36 @@ cudaError_t launch_prepare_batch(cudaStream_t s, const UpdateArgs& a, const Batc
     return cudaGetLastError();
 }
 
-template <int M, int PM>
-cudaError_t run_passA_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
+size_t passA_batch_smem(uint32_t M, uint32_t T, uint32_t G)
 {
-    const size_t smem = (size_t)(((b.G * M * (a.T + 1) + 3) & ~3u) + 4 * b.G) * sizeof(float);
+    return (size_t)G * sizeof(float4) + (size_t)G * M * (T + 1) * sizeof(float);
+}
+
+template <int M, int PM, int G>
+cudaError_t run_passA_batch_g(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
+{
+    const size_t smem = passA_batch_smem(M, a.T, G);
     static size_t set_bytes = 0;                 // attribute set once per size (not during capture)
     if (smem > set_bytes) {
-        cudaError_t e = smem_attr(k_passA_batch<M, PM>, smem);
+        cudaError_t e = smem_attr(k_passA_batch<M, PM, G>, smem);
         if (e != cudaSuccess) return e;
         set_bytes = smem;
     }
     uint64_t grid = (uint64_t)b.sm_count * b.resid;
     if (grid > b.n_tiles) grid = b.n_tiles;
-    if (grid) k_passA_batch<M, PM><<<(unsigned)grid, WARPS * 32, smem, s>>>(a, b);
+    if (grid) k_passA_batch<M, PM, G><<<(unsigned)grid, WARPS * 32, smem, s>>>(a, b);
     return cudaGetLastError();
+}
+
+template <int M, int PM>
+cudaError_t run_passA_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
+{
+    switch (b.G) {
+        case 4: return run_passA_batch_g<M, PM, 4>(s, a, b);
+        case 8: return run_passA_batch_g<M, PM, 8>(s, a, b);
+        case 16: return run_passA_batch_g<M, PM, 16>(s, a, b);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int M>
@@ -1154,15 +1190,27 @@ cudaError_t launch_passA_batch(cudaStream_t s, const UpdateArgs& a, const BatchA
     DVL_DISPATCH_M(run_passA_batch_m, s, a, b)
 }
 
+template <int M, int PM, int G>
+cudaError_t occupancy_passA_batch_g(const UpdateArgs& a, int* blocks)
+{
+    const size_t smem = passA_batch_smem(M, a.T, G);
+    *blocks = 0;
+    if (smem + sizeof(unsigned long long) * WARPS * MAX_BATCH_TF + 16 > 227 * 1024) return cudaSuccess;
+    cudaError_t e = smem_attr(k_passA_batch<M, PM, G>, smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_passA_batch<M, PM, G>, WARPS * 32, smem);
+}
+
 template <int M, int PM>
 cudaError_t occupancy_passA_batch(const UpdateArgs& a, uint32_t G, int* blocks)
 {
-    const size_t smem = (size_t)(((G * M * (a.T + 1) + 3) & ~3u) + 4 * G) * sizeof(float);
     *blocks = 0;
-    if (smem + sizeof(unsigned long long) * WARPS * MAX_BATCH_TF + 16 > 227 * 1024) return cudaSuccess;
-    cudaError_t e = smem_attr(k_passA_batch<M, PM>, smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_passA_batch<M, PM>, WARPS * 32, smem);
+    switch (G) {
+        case 4: return occupancy_passA_batch_g<M, PM, 4>(a, blocks);
+        case 8: return occupancy_passA_batch_g<M, PM, 8>(a, blocks);
+        case 16: return occupancy_passA_batch_g<M, PM, 16>(a, blocks);
+        default: return cudaSuccess;            // not a compiled group size
+    }
 }
 
 template <int M>
