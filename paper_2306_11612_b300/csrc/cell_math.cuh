@@ -94,6 +94,39 @@ __device__ __forceinline__ float importance(float V, uint32_t L, float inv_vmax,
     return fmaxf(f, ma);
 }
 
+// Three-input float max / min (single instructions on sm_100 and later); the
+// result is one of the inputs, as with fmaxf / fminf on non-NaN values.
+__device__ __forceinline__ float max3f(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// max_m al[m] - min_m al[m] (Eq. 1 for one cell), with three-input steps.
+template <int M>
+__device__ __forceinline__ float spread(const float (&al)[M])
+{
+    float hi = al[0], lw = al[0];
+    int m = 1;
+#pragma unroll
+    for (; m + 1 < M; m += 2) {
+        hi = max3f(hi, al[m], al[m + 1]);
+        lw = min3f(lw, al[m], al[m + 1]);
+    }
+    if (m < M) {
+        hi = fmaxf(hi, al[m]);
+        lw = fminf(lw, al[m]);
+    }
+    return __fsub_rn(hi, lw);
+}
+
 // Per-cell constants in registers, specialised on the field count M and the
 // exponent mode.  The alpha tables live in shared memory with T+1 entries per
 // field (entry T repeats entry T-1) so that t = 1 needs no clamp.
@@ -124,15 +157,10 @@ struct Cell {
     // Eq. 1 over the M fields of one cell, from normalised values t[].
     __device__ __forceinline__ float variation(const float* t, const float* s_tf) const
     {
-        float hi = s_tf[floor_small(__fmul_rn(t[0], Tf))];
-        float lw = hi;
+        float al[M];
 #pragma unroll
-        for (int m = 1; m < M; ++m) {
-            float al = s_tf[m * T1 + floor_small(__fmul_rn(t[m], Tf))];
-            hi = fmaxf(hi, al);
-            lw = fminf(lw, al);
-        }
-        return __fsub_rn(hi, lw);
+        for (int m = 0; m < M; ++m) al[m] = s_tf[m * T1 + floor_small(__fmul_rn(t[m], Tf))];
+        return spread<M>(al);
     }
 
     // fixed-point width of a cell: rint(f 2^Q) (<= 2^31)

@@ -201,4 +201,27 @@ cudaError_t launch_backward(cudaStream_t s, const UpdateArgs& a, const float* g,
                             float* grad_ctrl);
 cudaError_t launch_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* q);
 
+// Opts a kernel in to `bytes` of dynamic shared memory.  Always set: the
+// 48 KB default covers static plus dynamic memory, and several kernels have
+// static arrays of their own.
+template <typename K>
+cudaError_t smem_attr(K kernel, size_t bytes)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Dispatch on the field count of `a` to fn<1..8>(...).
+#define DVL_DISPATCH_M(fn, ...)                   \
+    switch (a.M) {                                \
+        case 1: return fn<1>(__VA_ARGS__);        \
+        case 2: return fn<2>(__VA_ARGS__);        \
+        case 3: return fn<3>(__VA_ARGS__);        \
+        case 4: return fn<4>(__VA_ARGS__);        \
+        case 5: return fn<5>(__VA_ARGS__);        \
+        case 6: return fn<6>(__VA_ARGS__);        \
+        case 7: return fn<7>(__VA_ARGS__);        \
+        case 8: return fn<8>(__VA_ARGS__);        \
+        default: return cudaErrorInvalidValue;    \
+    }
+
 }  // namespace dvl

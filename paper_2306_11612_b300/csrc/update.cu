@@ -27,48 +27,12 @@
 #include <stdint.h>
 
 #include "cell_math.cuh"
+#include "consts.cuh"
 #include "dvl_internal.h"
 
 namespace dvl {
 
 namespace {
-// ---------------------------------------------------------------------------
-// Constants (Sec. 3.4 and the fixed-point exponent)
-// ---------------------------------------------------------------------------
-
-__device__ int bitlen64(uint64_t x) { return x ? 64 - __clzll((long long)x) : 0; }
-
-// f_upper, Q, 2^Q from vmax (after vmax is known).
-__device__ void finish_consts(UpdateConsts* C, const UpdateArgs& a, uint32_t max_level)
-{
-    const float vmax = C->vmax;
-    const float inv = vmax > 0.0f ? __frcp_rn(vmax) : 0.0f;
-    C->inv_vmax = inv;
-    const bool after = C->min_imp_mode == DVL_MINIMP_AFTER_POWER;
-    float fu = importance<POW_GEN>(vmax > 0.0f ? 1.0f : 0.0f, max_level, inv, after ? 0.0f : C->min_imp,
-                                   after ? C->min_imp : 0.0f, C->width_shift, C->pow_n2, C->P);
-    C->f_upper = fu;
-    int Q = 0;
-    if (!isfinite(fu)) {
-        atomicOr(a.err, ERR_RANGE);
-    } else {
-        int e = 0;
-        frexpf(fu, &e);                       // fu <= 2^e
-        if (C->pow_n2 < 0) e += 1;            // powf is not monotone to the ulp
-        int cap = 62 - bitlen64(a.n);         // total below 2^62
-        if (cap > 31) cap = 31;               // every width below 2^32
-        Q = cap - e;
-        if (Q > 120) Q = 120;
-        if (Q < -120) { atomicOr(a.err, ERR_RANGE); Q = 0; }
-    }
-    C->Q = Q;
-    C->qscale = exp2i(Q);
-    C->F = 0;
-    C->linear = 0;
-}
-
-__device__ void prepare_consts_block(const UpdateArgs& a);
-
 __global__ void k_prepare(UpdateArgs a, uint32_t n_tiles)
 {
     // clear bins and scan state
@@ -90,71 +54,6 @@ __global__ void k_prepare(UpdateArgs a, uint32_t n_tiles)
         a.counters[1] = 0u;
     }
     prepare_consts_block(a);
-}
-
-// Per-TF constants (one block of 256 threads): TF domains, Eq. 5 entry range,
-// Eq. 6 max-variation approximation and the fixed-point exponent.
-__device__ void prepare_consts_block(const UpdateArgs& a)
-{
-    __shared__ int s_i[DVL_MAX_FIELDS], s_j[DVL_MAX_FIELDS];
-    __shared__ float s_spread[256];
-    UpdateConsts* C = a.consts;
-    const uint32_t M = a.M, T = a.T;
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        C->P = a.prm.P;
-        C->min_imp = a.prm.min_importance;
-        C->min_imp_mode = (int)a.prm.min_imp_mode;
-        C->width_shift = a.prm.width_mode == DVL_WIDTH_VOLUME ? 3 : 1;
-        float n2 = 2.0f * a.prm.P;
-        C->pow_n2 = (n2 >= 0.0f && n2 <= 16.0f && floorf(n2) == n2) ? (int)n2 : -1;
-    }
-    if (tid < (int)M) {
-        float dmin = ordered_to_float(a.meta->dmin[tid]);
-        float dmax = ordered_to_float(a.meta->dmax[tid]);
-        if (a.n == 0) { dmin = 0.0f; dmax = 0.0f; }
-        float lo = a.dom[tid], hi = a.dom[M + tid];
-        if (isnan(lo) && isnan(hi)) { lo = dmin; hi = dmax; }
-        float span = __fsub_rn(hi, lo);
-        float s = (span > 0.0f && isfinite(span)) ? __frcp_rn(span) : 0.0f;
-        // s = 0 maps every value to t = 0; lo = 0 keeps (v - lo) * s finite
-        // (a range wider than the float range would otherwise give inf * 0)
-        lo = s == 0.0f ? 0.0f : lo;
-        C->lo[tid] = lo;
-        C->s[tid] = s;
-        // Eq. 5: TF entries of the data minimum and maximum of this field
-        s_i[tid] = (int)tf_entry(norm_t(dmin, lo, s), (float)T, T - 1);
-        s_j[tid] = (int)tf_entry(norm_t(dmax, lo, s), (float)T, T - 1);
-    }
-    __syncthreads();
-    int gi = (int)T - 1, gj = 0;
-    for (uint32_t m = 0; m < M; ++m) { gi = min(gi, s_i[m]); gj = max(gj, s_j[m]); }
-    if (gi > gj) { gi = 0; gj = 0; }
-    // Eq. 6: largest spread max_m A(m,a) - min_m A(m,a) over a in [gi, gj]
-    float best = 0.0f;
-    for (int e = gi + tid; e <= gj; e += blockDim.x) {
-        float hi = a.tf[e], lw = a.tf[e];
-        for (uint32_t m = 1; m < M; ++m) {
-            float x = a.tf[m * T + e];
-            hi = fmaxf(hi, x);
-            lw = fminf(lw, x);
-        }
-        best = fmaxf(best, __fsub_rn(hi, lw));
-    }
-    s_spread[tid] = best;
-    __syncthreads();
-    if (tid == 0) {
-        C->i = gi;
-        C->j = gj;
-        if (a.prm.vmax_mode == DVL_VMAX_APPROX) {
-            float v = 0.0f;
-            for (int k = 0; k < (int)blockDim.x; ++k) v = fmaxf(v, s_spread[k]);
-            C->vmax = v;
-            finish_consts(C, a, a.meta->max_level);
-        } else {
-            C->vmax = 0.0f;   // filled by k_vmax_exact, then k_consts
-        }
-    }
 }
 
 // Exact max V over all cells (the reduction Sec. 3.4 avoids; optional mode).
@@ -658,180 +557,6 @@ __global__ void k_finalize(UpdateArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Batched updates: constants of K TFs, and pass A over all of them
-// ---------------------------------------------------------------------------
-
-__global__ void k_prepare_batch(UpdateArgs a, BatchArgs b)
-{
-    UpdateArgs ak = a;
-    ak.tf = b.tfs + (uint64_t)blockIdx.x * a.M * a.T;
-    ak.consts = b.consts + blockIdx.x;
-    for (uint32_t i = threadIdx.x; i < a.M * a.T; i += blockDim.x)
-        if (!(ak.tf[i] >= 0.0f && ak.tf[i] <= 1.0f)) atomicOr(a.err, ERR_RANGE);
-    prepare_consts_block(ak);
-}
-
-// Persistent pass A for K transfer functions that share the TF domains: a
-// warp step's cells are loaded and normalised once per group of G TFs whose
-// tables sit in shared memory; per TF it writes step totals and, per tile,
-// runs its own decoupled look-back scan.  G is a compile-time constant so the
-// TF loop unrolls; per cell the table offsets (all fields) and the level
-// factor 2^(L w) are computed once and reused by every TF of the group.
-template <int M, int PM, int G>
-__global__ __launch_bounds__(WARPS * 32) void k_passA_batch(UpdateArgs a, BatchArgs b)
-{
-    extern __shared__ float4 s_dyn[];                  // G x 1 params, then G x M x (T+1) tables
-    __shared__ unsigned long long s_ct[WARPS][MAX_BATCH_TF];
-    __shared__ uint32_t s_tile;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t T = a.T, T1 = T + 1, K = b.K, MT1 = M * T1;
-    float4* s_par = s_dyn;                             // inv_vmax, mb, ma, qscale per TF
-    float* s_tf = reinterpret_cast<float*>(s_dyn + G);
-    const UpdateConsts* C0 = b.consts;
-    float lo[M], sc[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) { lo[m] = C0->lo[m]; sc[m] = C0->s[m]; }
-    const float Tf = (float)T, P = C0->P;
-    const int n2 = C0->pow_n2, wshift = C0->width_shift;
-
-    while (true) {
-        if (tid == 0) s_tile = atomicAdd(&a.counters[0], 1u);
-        __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= b.n_tiles) break;                  // block-uniform
-        for (uint32_t k = lane; k < K; k += 32) s_ct[warp][k] = 0ull;
-        const uint64_t chunk = (uint64_t)tile * WARPS + warp;
-        const uint64_t base = chunk * CHUNK;
-        for (uint32_t g0 = 0; g0 < K; g0 += G) {
-            const uint32_t gk = K - g0 < G ? K - g0 : G;
-            __syncthreads();                           // the previous group's tables are free
-            for (uint32_t i = tid; i < gk * MT1; i += blockDim.x) {
-                const uint32_t kk = i / MT1, r = i - kk * MT1, m = r / T1, e = r - m * T1;
-                s_tf[i] = b.tfs[((uint64_t)(g0 + kk) * M + m) * T + (e < T ? e : T - 1)];
-            }
-            for (uint32_t kk = tid; kk < G; kk += blockDim.x) {
-                float4 pr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                if (kk < gk) {
-                    const UpdateConsts* Ck = b.consts + g0 + kk;
-                    const bool after = Ck->min_imp_mode == DVL_MINIMP_AFTER_POWER;
-                    pr = make_float4(Ck->inv_vmax, after ? 0.0f : Ck->min_imp, after ? Ck->min_imp : 0.0f,
-                                     Ck->qscale);
-                }
-                s_par[kk] = pr;
-            }
-            __syncthreads();
-            if (base >= a.n) continue;
-            for (int st = 0; st < STEPS; ++st) {
-                if (base + (uint64_t)st * STEP >= a.n) break;            // warp-uniform
-                const uint64_t idx = base + st * STEP + lane * 4;
-                uint32_t off[4][M];
-                float lvl[4];
-                bool valid[4];
-                if (idx < a.n) {
-                    float v[4][M];
-                    uint32_t L4;
-                    load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-#pragma unroll
-                        for (int m = 0; m < M; ++m)
-                            off[j][m] = m * T1 + floor_small(__fmul_rn(norm_t(v[j][m], lo[m], sc[m]), Tf));
-                        lvl[j] = exp2i((int)((L4 >> (8 * j)) & 0xFF) * wshift);
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-#pragma unroll
-                        for (int m = 0; m < M; ++m) off[j][m] = 0;
-                        lvl[j] = 0.0f;
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) valid[j] = idx + j < a.n;
-#pragma unroll
-                for (int kk = 0; kk < G; ++kk) {
-                    if (kk >= (int)gk) break;                              // block-uniform
-                    const float* tk = s_tf + kk * MT1;
-                    const float4 pr = s_par[kk];
-                    unsigned long long l = 0;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        float hi = tk[off[j][0]], lw = hi;
-#pragma unroll
-                        for (int m = 1; m < M; ++m) {
-                            const float al = tk[off[j][m]];
-                            hi = fmaxf(hi, al);
-                            lw = fminf(lw, al);
-                        }
-                        // Eq. 3 as importance<PM>, with the level factor precomputed
-                        const float r = fmaxf(__fmul_rn(__fsub_rn(hi, lw), pr.x), pr.y);
-                        const float x = __fmul_rn(r, lvl[j]);
-                        const float f = fmaxf(PM == POW_ONE ? x : pow_gen(x, n2, P), pr.z);
-                        const uint32_t q = __float2uint_rn(__fmul_rn(f, pr.w));
-                        l += valid[j] ? q : 0u;
-                    }
-                    const unsigned long long tot = warp_total_small(l);
-                    if (lane == 0) {
-                        b.step_sums[((uint64_t)(g0 + kk) * b.n_chunks + chunk) * STEPS + st] = tot;
-                        s_ct[warp][g0 + kk] += tot;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        {
-            // one look-back per TF; the warps take the TFs in turn
-            for (uint32_t k = warp; k < K; k += WARPS) {
-                unsigned long long w = lane < WARPS ? s_ct[lane][k] : 0ull;
-                unsigned long long incl = warp_incl_scan_u64(w, lane);
-                const unsigned long long agg = __shfl_sync(FULL, incl, WARPS - 1);
-                unsigned long long* status = b.tile_status + (uint64_t)k * b.n_tiles;
-                if (lane == 0) st_relaxed(status + tile, (tile == 0 ? FLAG_P : FLAG_A) | agg);
-                unsigned long long excl = 0;
-                if (tile > 0) {
-                    int64_t end = (int64_t)tile - 1;
-                    while (true) {
-                        const int64_t jt = end - lane;
-                        unsigned long long sv = FLAG_P;
-                        if (jt >= 0) {
-                            long long spins = 0;
-                            while (true) {
-                                sv = ld_relaxed(status + jt);
-                                if (sv >> 62) break;
-                                if (++spins > a.spin_limit) {
-                                    atomicOr(a.err, ERR_TIMEOUT);
-                                    sv = FLAG_P;
-                                    break;
-                                }
-                                __nanosleep(100);
-                            }
-                        }
-                        const unsigned pmask = __ballot_sync(FULL, (sv & FLAG_P) != 0);
-                        const int first = pmask ? __ffs(pmask) - 1 : 31;
-                        excl += warp_sum_u64(lane <= first ? (sv & VAL_MASK) : 0ull);
-                        if (pmask) break;
-                        end -= 32;
-                    }
-                    if (lane == 0) st_relaxed(status + tile, FLAG_P | (excl + agg));
-                }
-                if (lane < WARPS) b.chunk_prefix[(uint64_t)k * b.n_chunks + (uint64_t)tile * WARPS + lane] = excl + incl - w;
-                if (lane == 0 && tile == b.n_tiles - 1) {
-                    UpdateConsts* Ck = b.consts + k;
-                    unsigned long long F = excl + agg;
-                    int linear = 0;
-                    if (F == 0 && a.n > 0) { F = a.n; linear = 1; }
-                    Ck->F = F;
-                    Ck->linear = linear;
-                    Ck->F_div_W = 0;
-                    Ck->F_mod_W = 0;
-                }
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Differentiable path: control points -> alpha tables, and the adjoint of the
 // per-pixel alpha means with the assignment held fixed
 // ---------------------------------------------------------------------------
@@ -1018,15 +743,6 @@ __global__ __launch_bounds__(256) void k_widths(UpdateArgs a, unsigned long long
     }
 }
 
-// Opts the kernel in to `bytes` of dynamic shared memory.  Always set: the
-// 48 KB default covers static plus dynamic memory, and pass A has a static
-// array of its own.
-template <typename K>
-cudaError_t smem_attr(K kernel, size_t bytes)
-{
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
 int grid_cap(uint64_t work, int threads)
 {
     uint64_t b = (work + threads - 1) / threads;
@@ -1126,104 +842,7 @@ cudaError_t run_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* 
 
 }  // namespace
 
-#define DVL_DISPATCH_M(fn, ...)                   \
-    switch (a.M) {                                \
-        case 1: return fn<1>(__VA_ARGS__);        \
-        case 2: return fn<2>(__VA_ARGS__);        \
-        case 3: return fn<3>(__VA_ARGS__);        \
-        case 4: return fn<4>(__VA_ARGS__);        \
-        case 5: return fn<5>(__VA_ARGS__);        \
-        case 6: return fn<6>(__VA_ARGS__);        \
-        case 7: return fn<7>(__VA_ARGS__);        \
-        case 8: return fn<8>(__VA_ARGS__);        \
-        default: return cudaErrorInvalidValue;    \
-    }
-
 cudaError_t launch_update(cudaStream_t s, const UpdateArgs& a) { DVL_DISPATCH_M(run_update, s, a) }
-
-cudaError_t launch_prepare_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
-{
-    k_prepare_batch<<<b.K, 256, 0, s>>>(a, b);
-    return cudaGetLastError();
-}
-
-size_t passA_batch_smem(uint32_t M, uint32_t T, uint32_t G)
-{
-    return (size_t)G * sizeof(float4) + (size_t)G * M * (T + 1) * sizeof(float);
-}
-
-template <int M, int PM, int G>
-cudaError_t run_passA_batch_g(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
-{
-    const size_t smem = passA_batch_smem(M, a.T, G);
-    static size_t set_bytes = 0;                 // attribute set once per size (not during capture)
-    if (smem > set_bytes) {
-        cudaError_t e = smem_attr(k_passA_batch<M, PM, G>, smem);
-        if (e != cudaSuccess) return e;
-        set_bytes = smem;
-    }
-    uint64_t grid = (uint64_t)b.sm_count * b.resid;
-    if (grid > b.n_tiles) grid = b.n_tiles;
-    if (grid) k_passA_batch<M, PM, G><<<(unsigned)grid, WARPS * 32, smem, s>>>(a, b);
-    return cudaGetLastError();
-}
-
-template <int M, int PM>
-cudaError_t run_passA_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
-{
-    switch (b.G) {
-        case 4: return run_passA_batch_g<M, PM, 4>(s, a, b);
-        case 8: return run_passA_batch_g<M, PM, 8>(s, a, b);
-        case 16: return run_passA_batch_g<M, PM, 16>(s, a, b);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <int M>
-cudaError_t run_passA_batch_m(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
-{
-    return a.prm.P == 1.0f ? run_passA_batch<M, POW_ONE>(s, a, b) : run_passA_batch<M, POW_GEN>(s, a, b);
-}
-
-cudaError_t launch_passA_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
-{
-    DVL_DISPATCH_M(run_passA_batch_m, s, a, b)
-}
-
-template <int M, int PM, int G>
-cudaError_t occupancy_passA_batch_g(const UpdateArgs& a, int* blocks)
-{
-    const size_t smem = passA_batch_smem(M, a.T, G);
-    *blocks = 0;
-    if (smem + sizeof(unsigned long long) * WARPS * MAX_BATCH_TF + 16 > 227 * 1024) return cudaSuccess;
-    cudaError_t e = smem_attr(k_passA_batch<M, PM, G>, smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_passA_batch<M, PM, G>, WARPS * 32, smem);
-}
-
-template <int M, int PM>
-cudaError_t occupancy_passA_batch(const UpdateArgs& a, uint32_t G, int* blocks)
-{
-    *blocks = 0;
-    switch (G) {
-        case 4: return occupancy_passA_batch_g<M, PM, 4>(a, blocks);
-        case 8: return occupancy_passA_batch_g<M, PM, 8>(a, blocks);
-        case 16: return occupancy_passA_batch_g<M, PM, 16>(a, blocks);
-        default: return cudaSuccess;            // not a compiled group size
-    }
-}
-
-template <int M>
-cudaError_t occupancy_passA_batch_m(const UpdateArgs& a, uint32_t G, int* blocks)
-{
-    return a.prm.P == 1.0f ? occupancy_passA_batch<M, POW_ONE>(a, G, blocks)
-                           : occupancy_passA_batch<M, POW_GEN>(a, G, blocks);
-}
-
-cudaError_t passA_batch_occupancy(const UpdateArgs& a, uint32_t G, int* blocks)
-{
-    DVL_DISPATCH_M(occupancy_passA_batch_m, a, G, blocks)
-}
 
 cudaError_t launch_ctrl_table(cudaStream_t s, uint32_t M, uint32_t K, uint32_t T, const float* ctrl, float* tf,
                               uint32_t* err)
