@@ -61,8 +61,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline budget (rank 0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", choices=["plain", "batch"], default="plain",
-                    help="plain: one TF edit per step (default); batch: K TFs x 4 viewports per step")
+    ap.add_argument("--mode", choices=["plain", "batch", "serve"], default="plain",
+                    help="plain: one TF edit per step (default); batch: K TFs x 4 viewports per step; "
+                         "serve: Poisson TF-edit requests over 8 resident data sets")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean request arrival rate (1/s)")
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="length of the request stream (s)")
     ap.add_argument("--batch-tfs", type=int, default=64)
     return ap.parse_args()
 
@@ -565,12 +568,167 @@ def batch_cpu_baseline(args, K, seconds=None):
                       "of the batched data set"}
 
 
+# ---------------------------------------------------------------------------
+# serving mode: resident data sets, Poisson TF-edit requests
+# ---------------------------------------------------------------------------
+
+SERVE_METRIC = "served DVL throughput (cells/s over TF-edit requests), p50/p99 latency"
+SERVE_WIDTH = 1024
+
+
+def serve_requests(n_req, rate, n_sets, M=4, seed=5):
+    """Arrival times (s), data set and alpha tables of a seeded request
+    stream: Poisson arrivals; each data set keeps a current TF set, 70 % of
+    the requests replace one field's table, 30 % all of them."""
+    import numpy as np
+    import synth
+    rng = np.random.Generator(np.random.PCG64(seed))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    ds = rng.integers(0, n_sets, n_req)
+    state = [synth.random_tfs(900 + d, n_fields=M) for d in range(n_sets)]
+    reqs = []
+    for i in range(n_req):
+        d = int(ds[i])
+        tf = state[d].copy()
+        if rng.random() < 0.7:
+            tf[int(rng.integers(0, M))] = synth.random_tf(rng)
+        else:
+            tf = np.stack([synth.random_tf(rng) for _ in range(M)])
+        state[d] = tf
+        reqs.append((d, tf))
+    return arrivals, reqs
+
+
+def drive(srv, arrivals, reqs, width, open_loop=True):
+    """Submits the stream (at its arrival times, or all at once) from one
+    thread and waits for every result from another; returns wall seconds."""
+    ids = [None] * len(reqs)
+    ready = threading.Semaphore(0)
+
+    def submitter():
+        t0 = time.perf_counter()
+        for i, (d, tf) in enumerate(reqs):
+            if open_loop:
+                dt = arrivals[i] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            ids[i] = srv.submit(d, tf, width)
+            ready.release()
+
+    t0 = time.perf_counter()
+    th = threading.Thread(target=submitter)
+    th.start()
+    for i in range(len(reqs)):
+        ready.acquire()
+        srv.wait(ids[i])
+    th.join()
+    return time.perf_counter() - t0
+
+
+def run_serve(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2306_11612_b300 as dvl
+    from paper_2306_11612_b300.serve import DVLServer
+    import synth
+
+    t0 = time.perf_counter()
+    sets = synth.serving_datasets()
+    t_gen = time.perf_counter() - t0
+    sizes = [a.n for a in sets]
+    n_req = int(args.serve_rate * args.serve_seconds)
+    arrivals, reqs = serve_requests(n_req, args.serve_rate, len(sets))
+    kw = dict(P=args.P, min_importance=args.min_importance)
+
+    def served(max_batch):
+        with DVLServer(local, max_batch=max_batch, max_inflight=len(sets), max_width=SERVE_WIDTH, **kw) as srv:
+            for a in sets:
+                srv.add_dataset(a.lower, a.level, a.fields)
+            srv.warmup()
+            with ClockSampler(local) as clk:
+                wall = drive(srv, arrivals, reqs, SERVE_WIDTH, open_loop=True)
+                st = srv.stats()
+                srv.reset_stats()
+                wall_sat = drive(srv, arrivals, reqs, SERVE_WIDTH, open_loop=False)
+                sat = srv.stats()
+            return st, wall, sat, wall_sat, clk.summary()
+
+    st, wall, sat, wall_sat, clocks = served(64)
+    st1, wall1, sat1, wall_sat1, _ = served(1)
+    # closed-loop plain path: one context per data set, one request at a time
+    ctxs = []
+    for a in sets:
+        c = dvl.DVL(local)
+        c.load_amr(a.lower, a.level, a.fields)
+        c.build_order(dvl.SFC_HILBERT)
+        ctxs.append(c)
+    out = {k: np.empty((4, SERVE_WIDTH), np.float32) for k in ("mean", "min", "max", "y")}
+    out["sum"] = np.empty((4, SERVE_WIDTH), np.float64)
+    out["count"] = np.empty(SERVE_WIDTH, np.uint32)
+    n_plain = min(n_req, 2000)
+    for d, tf in reqs[:8]:                                    # warm-up
+        ctxs[d].set_tfs(tf)
+        ctxs[d].update(width=SERVE_WIDTH, **kw)
+    lat = []
+    t0 = time.perf_counter()
+    for d, tf in reqs[:n_plain]:
+        t1 = time.perf_counter()
+        ctxs[d].set_tfs(tf)
+        ctxs[d].update(width=SERVE_WIDTH, **kw)
+        for m in range(4):
+            ctxs[d].read_bins(m, {k: v[m] if k != "count" else v for k, v in out.items()})
+        lat.append((time.perf_counter() - t1) * 1e3)
+    el = time.perf_counter() - t0
+    plain_cells = sum(sizes[d] for d, _ in reqs[:n_plain])
+    for c in ctxs:
+        c.close()
+
+    def pick(s, wall_s):
+        return {"p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"], "mean_ms": s["mean_ms"], "max_ms": s["max_ms"],
+                "completed": s["completed"], "failed": s["failed"], "batches": s["batches"],
+                "mean_batch": s["mean_batch"], "max_batch": s["max_batch_seen"], "cells_per_s": s["cells_per_s"],
+                "requests_per_s": s["completed"] / wall_s, "wall_s": wall_s}
+
+    line = {"metric": SERVE_METRIC, "value": st["cells_per_s"], "unit": "cells/s", "n_gpus": world,
+            "steps": n_req, "warmup": 1, "ms_per_step": wall / n_req * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64", "data": "synthetic",
+            "config": {"workload": f"serving: {len(sets)} resident sub-boxes of the large synthetic AMR "
+                                   f"({min(sizes)}..{max(sizes)} cells, {sum(sizes)} total), 4 fp32 fields; "
+                                   f"Poisson TF-edit requests at {args.serve_rate:.0f}/s for "
+                                   f"{args.serve_seconds:.0f} s (70 % one field, 30 % all four), W={SERVE_WIDTH}",
+                       "sizes": sizes, "requests": n_req, "rate": args.serve_rate, "width": SERVE_WIDTH,
+                       "max_batch": 64, "max_inflight": len(sets),
+                       "step": "one request, submit to result on the host"},
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "served": pick(st, wall), "saturated": pick(sat, wall_sat),
+            "single_request_server": {"offered": pick(st1, wall1), "saturated": pick(sat1, wall_sat1)},
+            "plain_closed_loop": {"requests": n_plain, "cells_per_s": plain_cells / el,
+                                  "requests_per_s": n_plain / el,
+                                  "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))},
+            "roofline": None, "roofline_note": "kernels as in --mode batch (pass A batch, bins)",
+            "clocks": clocks, "e2e": {"value": st["cells_per_s"], "unit": "cells/s",
+                                      "h2d_bytes_per_step": 4 * 256 * 4,
+                                      "d2h_bytes_per_step": 4 * SERVE_WIDTH * (4 * 4 + 8) + 4 * SERVE_WIDTH},
+            "setup_s": {"generate": t_gen}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "batch":
         run_batch(args)
+    elif args.mode == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -293,6 +293,15 @@ int dvl_read_batch_bins(dvl_ctx* ctx, uint32_t pair, uint32_t field, const dvl_b
  * the totals.  Synchronises the stream. */
 int dvl_read_batch_all(dvl_ctx* ctx, const dvl_bins* out);
 
+/* As dvl_read_batch_all, but only queues the copies on the context's stream
+ * and returns (no synchronisation, no device-error check): host buffers must
+ * be pinned and stay valid until the stream has passed the copies
+ * (dvl_sync, or an event / host callback on dvl_stream). */
+int dvl_read_batch_all_async(dvl_ctx* ctx, const dvl_bins* out);
+
+/* The CUDA stream (cudaStream_t) the context runs its work on. */
+void* dvl_stream(dvl_ctx* ctx);
+
 /* Launch configuration the batch autotuner chose for the last batch shape:
  * out[0] = TFs per shared-memory group, out[1] = pass-A CTAs per SM,
  * out[2] = 1 if the last call replayed a captured graph. */

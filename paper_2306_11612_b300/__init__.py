@@ -33,7 +33,11 @@ EXPORTS = ["dvl_create", "dvl_destroy", "dvl_load_amr", "dvl_build_order", "dvl_
            "dvl_set_tf", "dvl_update", "dvl_read_bins", "dvl_get_stats", "dvl_read_order",
            "dvl_read_widths", "dvl_sync", "dvl_set_option", "dvl_get_timings", "dvl_update_noalloc", "dvl_set_tf_ctrl", "dvl_read_alpha_means", "dvl_backward",
            "dvl_update_batch", "dvl_read_batch_bins", "dvl_read_batch_all", "dvl_batch_config",
-           "dvl_status_string", "dvl_last_error"]
+           "dvl_read_batch_all_async", "dvl_stream",
+           "dvl_status_string", "dvl_last_error",
+           "dvl_server_create", "dvl_server_destroy", "dvl_server_add_dataset", "dvl_server_warmup",
+           "dvl_server_submit", "dvl_server_wait", "dvl_server_get_stats", "dvl_server_reset_stats",
+           "dvl_server_last_error", "dvl_serve_bucket", "dvl_serve_admit"]
 
 
 class dvl_params(ctypes.Structure):
@@ -46,6 +50,19 @@ class dvl_bins(ctypes.Structure):
     _fields_ = [("mean", ctypes.c_void_p), ("min", ctypes.c_void_p), ("max", ctypes.c_void_p),
                 ("y", ctypes.c_void_p), ("sum", ctypes.c_void_p), ("count", ctypes.c_void_p),
                 ("mem_kind", ctypes.c_int)]
+
+
+class dvl_server_config(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_uint64), ("max_batch", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32),
+                ("n_entries", ctypes.c_uint32), ("max_width", ctypes.c_uint32), ("params", dvl_params)]
+
+
+class dvl_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("mean_batch", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("cells_per_s", ctypes.c_double), ("mem_used", ctypes.c_uint64), ("mem_budget", ctypes.c_uint64),
+                ("slot_bytes", ctypes.c_uint64), ("n_datasets", ctypes.c_uint32), ("max_batch_seen", ctypes.c_uint32)]
 
 
 class dvl_stats(ctypes.Structure):
@@ -84,6 +101,19 @@ def _load():
         "dvl_read_batch_bins": ([vp, u32, u32, ctypes.POINTER(dvl_bins)], i32),
         "dvl_read_batch_all": ([vp, ctypes.POINTER(dvl_bins)], i32),
         "dvl_batch_config": ([vp, ctypes.POINTER(ctypes.c_int32)], i32),
+        "dvl_read_batch_all_async": ([vp, ctypes.POINTER(dvl_bins)], i32),
+        "dvl_stream": ([vp], vp),
+        "dvl_server_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(dvl_server_config)], i32),
+        "dvl_server_destroy": ([vp], None),
+        "dvl_server_add_dataset": ([vp, u64, vp, vp, u32, vp, i32, ctypes.POINTER(u32)], i32),
+        "dvl_server_warmup": ([vp], i32),
+        "dvl_server_submit": ([vp, u32, vp, u32, ctypes.POINTER(u64)], i32),
+        "dvl_server_wait": ([vp, u64, ctypes.c_double, ctypes.POINTER(dvl_bins)], i32),
+        "dvl_server_get_stats": ([vp, ctypes.POINTER(dvl_server_stats)], i32),
+        "dvl_server_reset_stats": ([vp], i32),
+        "dvl_server_last_error": ([vp], ctypes.c_char_p),
+        "dvl_serve_bucket": ([u32, u32], u32),
+        "dvl_serve_admit": ([u32, u32, u32, u64, u64, u64], u32),
         "dvl_status_string": ([i32], ctypes.c_char_p),
         "dvl_last_error": ([vp], ctypes.c_char_p),
     }

@@ -14,12 +14,12 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
           "-fmad=false", "-I", INCLUDE]
-SOURCES = ["dvl_api.cu", "sfc_sort.cu", "update.cu", "batch.cu", "bins.cu", "noalloc.cu"]
+SOURCES = ["dvl_api.cu", "sfc_sort.cu", "update.cu", "batch.cu", "bins.cu", "noalloc.cu", "serve.cu"]
 
 
 def _deps():
     hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    return hdrs + [os.path.join(INCLUDE, "dvl.h")]
+    return hdrs + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

@@ -108,8 +108,9 @@ struct dvl_ctx {
     std::vector<PairDesc> b_pairs;        // of the last batch
     bool have_batch = false;
     std::map<std::vector<uint64_t>, std::pair<int, int>> b_tuned;   // shape -> (G, CTAs per SM)
-    std::vector<uint64_t> b_graph_sig;
-    cudaGraphExec_t b_graph = nullptr;
+    // captured graphs by launch signature (least recently used dropped first)
+    std::map<std::vector<uint64_t>, std::pair<cudaGraphExec_t, uint64_t>> b_graphs;
+    uint64_t b_graph_clock = 0;
     int b_G = 0, b_resid = 0, b_replayed = 0;
     // options
     int64_t spin_limit = 1 << 22;
@@ -180,9 +181,8 @@ void free_batch(dvl_ctx* c)
     dfree(c->d_bcount); dfree(c->d_bmean); dfree(c->d_by); dfree(c->d_bH); dfree(c->d_bS);
     dfree(c->d_bpsum); dfree(c->d_bpmm);
     c->btf_cap = c->bk_cap = c->pairs_cap = c->bbin_cap = c->bcnt_cap = c->bhs_cap = 0;
-    if (c->b_graph) cudaGraphExecDestroy(c->b_graph);
-    c->b_graph = nullptr;
-    c->b_graph_sig.clear();
+    for (auto& kv : c->b_graphs) cudaGraphExecDestroy(kv.second.first);
+    c->b_graphs.clear();
     c->have_batch = false;
 }
 
@@ -1121,10 +1121,16 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
                                     (uint64_t)c->d_by, (uint64_t)c->d_bcount, (uint64_t)c->d_bH, (uint64_t)c->d_bS,
                                     (uint64_t)c->d_bpsum, (uint64_t)c->d_bpmm,
                                     (uint64_t)v.pre_lo, (uint64_t)v.pre_hi, (uint64_t)v.mn, (uint64_t)v.mx};
-    if (sig != c->b_graph_sig || !c->b_graph) {
-        if (c->b_graph) cudaGraphExecDestroy(c->b_graph);
-        c->b_graph = nullptr;
-        c->b_graph_sig.clear();
+    constexpr size_t MAX_GRAPHS = 32;
+    auto hit = c->b_graphs.find(sig);
+    if (hit == c->b_graphs.end()) {
+        if (c->b_graphs.size() >= MAX_GRAPHS) {
+            auto lru = c->b_graphs.begin();
+            for (auto it = c->b_graphs.begin(); it != c->b_graphs.end(); ++it)
+                if (it->second.second < lru->second.second) lru = it;
+            cudaGraphExecDestroy(lru->second.first);
+            c->b_graphs.erase(lru);
+        }
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         cudaError_t e1 = enqueue_batch(c, a, b, v, false);
@@ -1133,17 +1139,16 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
             if (g) cudaGraphDestroy(g);
             return cuda_fail(c, e1 != cudaSuccess ? e1 : e2, "capture batch");
         }
-        cudaError_t e3 = cudaGraphInstantiate(&c->b_graph, g, 0);
+        cudaGraphExec_t ge = nullptr;
+        cudaError_t e3 = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
-        if (e3 != cudaSuccess) {
-            c->b_graph = nullptr;
-            return cuda_fail(c, e3, "instantiate batch graph");
-        }
-        c->b_graph_sig = sig;
+        if (e3 != cudaSuccess) return cuda_fail(c, e3, "instantiate batch graph");
+        hit = c->b_graphs.emplace(sig, std::make_pair(ge, 0ull)).first;
     } else {
         c->b_replayed = 1;
     }
-    CK(cudaGraphLaunch(c->b_graph, c->stream), "launch batch graph");
+    hit->second.second = ++c->b_graph_clock;
+    CK(cudaGraphLaunch(hit->second.first, c->stream), "launch batch graph");
     c->have_batch = true;
     return DVL_OK;
 }
@@ -1173,7 +1178,7 @@ int dvl_read_batch_bins(dvl_ctx* c, uint32_t pair, uint32_t field, const dvl_bin
     return DVL_OK;
 }
 
-int dvl_read_batch_all(dvl_ctx* c, const dvl_bins* out)
+static int read_batch_all(dvl_ctx* c, const dvl_bins* out, bool sync)
 {
     if (!c) return DVL_ERR_ARG;
     c->last_error.clear();
@@ -1181,8 +1186,10 @@ int dvl_read_batch_all(dvl_ctx* c, const dvl_bins* out)
     if (!c->have_batch) return fail(c, DVL_ERR_STATE, "no batched update has run");
     if (out->mem_kind != DVL_MEM_HOST && out->mem_kind != DVL_MEM_DEVICE) return fail(c, DVL_ERR_ARG, "bad mem_kind");
     cudaSetDevice(c->device);
-    int rc = take_device_error(c);
-    if (rc) return rc;
+    if (sync) {
+        int rc = take_device_error(c);
+        if (rc) return rc;
+    }
     const PairDesc& last = c->b_pairs.back();
     const size_t nb = last.bin_off + (size_t)c->M * last.W, nc = last.cnt_off + last.W;
     const cudaMemcpyKind k = kind_out(out->mem_kind);
@@ -1192,9 +1199,15 @@ int dvl_read_batch_all(dvl_ctx* c, const dvl_bins* out)
     if (out->y) CK(cudaMemcpyAsync(out->y, c->d_by, nb * 4, k, c->stream), "copy y");
     if (out->sum) CK(cudaMemcpyAsync(out->sum, c->d_bsum, nb * 8, k, c->stream), "copy sum");
     if (out->count) CK(cudaMemcpyAsync(out->count, c->d_bcount, nc * 4, k, c->stream), "copy count");
-    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    if (sync) CK(cudaStreamSynchronize(c->stream), "synchronize");
     return DVL_OK;
 }
+
+int dvl_read_batch_all(dvl_ctx* c, const dvl_bins* out) { return read_batch_all(c, out, true); }
+
+int dvl_read_batch_all_async(dvl_ctx* c, const dvl_bins* out) { return read_batch_all(c, out, false); }
+
+void* dvl_stream(dvl_ctx* c) { return c ? static_cast<void*>(c->stream) : nullptr; }
 
 int dvl_batch_config(dvl_ctx* c, int32_t out[3])
 {

@@ -197,6 +197,56 @@ def make(name: str, pinned: bool = False, box=None, **over) -> AMR:
     return a
 
 
+def box_count(name: str, box) -> int:
+    """Cells of a named threshold configuration inside a sub-box of base
+    cells, counted without generating them."""
+    c = CONFIGS[name]
+    cfg = _Cfg(0, c["base_n"], c["n_levels"], 0, 0, 0, float(TAU[name]), c["seed"])
+    cfg.box_lo[:] = [int(v) for v in box[0]]
+    cfg.box_n = int(box[1])
+    counts = np.empty(int(box[1]) ** 3, np.uint32)
+    return int(_L().amrgen_count(ctypes.byref(cfg), counts.ctypes.data))
+
+
+def serving_boxes(seed: int = 5, n: int = 8, lo: float = 1e6, hi: float = 2e8, name: str = "large"):
+    """Sub-boxes of a named data set whose cell counts follow a log-uniform
+    draw in [lo, hi] (seeded): random box corners, the edge bisected on the
+    count.  Returns [(box, count)], one per serving data set."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    base = CONFIGS[name]["base_n"]
+    out = []
+    for _ in range(n):
+        target = float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        corner = rng.uniform(0.0, 1.0, 3)
+        best = None
+        e_lo, e_hi = 1, base
+        while e_lo <= e_hi:                      # smallest edge reaching the target
+            e = (e_lo + e_hi) // 2
+            x0 = [int(v * (base - e)) for v in corner]
+            cnt = box_count(name, (x0, e))
+            if best is None or abs(np.log(max(cnt, 1) / target)) < abs(np.log(max(best[1], 1) / target)):
+                best = ((x0, e), cnt)
+            if cnt < target:
+                e_lo = e + 1
+            else:
+                e_hi = e - 1
+        out.append(best)
+    return out
+
+
+# The serving data sets: serving_boxes() (seed 5, 8 sets, log-uniform targets
+# in [1e6, 2e8] over the "large" configuration), fixed here with their counts
+# so that generating them needs no search.
+SERVING = [(((68, 43, 24), 43), 74163139), (((31, 33, 3), 47), 1402204), (((90, 59, 21), 37), 2418025),
+           (((74, 68, 64), 52), 8043881), (((33, 46, 4), 60), 6952814), (((13, 43, 3), 78), 22800359),
+           (((67, 17, 69), 50), 37489012), (((0, 23, 0), 95), 102660083)]
+
+
+def serving_datasets(pinned: bool = False):
+    """The 8 serving data sets (sub-boxes of "large", see SERVING)."""
+    return [make("large", pinned=pinned, box=box) for box, _ in SERVING]
+
+
 def random_tf(rng: np.random.Generator, n_entries: int = 256, n_points: int = 8) -> np.ndarray:
     """Random piecewise-linear alpha transfer function sampled into a table.
 

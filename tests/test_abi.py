@@ -10,9 +10,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "dvl.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(dvl_[a-z_]+)\s*\(", src)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, h)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(dvl_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
@@ -58,3 +62,24 @@ def test_kernels_are_built_for_sm103a():
     from paper_2306_11612_b300 import _build
     assert "arch=compute_103a,code=sm_103a" in _build.ARCH
     assert "-fmad=false" in _build.COMMON
+
+
+def test_serving_rules_without_gpu():
+    # batch-size buckets and memory admission are pure host functions
+    import paper_2306_11612_b300 as dvl
+    L = dvl.lib
+    assert [L.dvl_serve_bucket(k, 64) for k in (0, 1, 2, 3, 5, 9, 33, 64, 100)] == [0, 1, 2, 4, 8, 16, 64, 64, 64]
+    assert L.dvl_serve_bucket(40, 48) == 48 and L.dvl_serve_bucket(17, 48) == 32
+    GB = 1 << 30
+    # room for everything: all queued requests up to max_batch
+    assert L.dvl_serve_admit(5, 64, 0, GB, 0, 100 * GB) == 5
+    assert L.dvl_serve_admit(200, 64, 0, GB, 0, 100 * GB) == 64
+    # growth to a bucket of 8 needs 8 GB; only 5 GB left -> bucket 4
+    assert L.dvl_serve_admit(7, 64, 0, GB, 95 * GB, 100 * GB) == 4
+    # buffers already hold 4 slots: a batch of 4 needs no new memory
+    assert L.dvl_serve_admit(7, 64, 4, GB, 100 * GB, 100 * GB) == 4
+    # nothing allocated and not even one slot fits
+    assert L.dvl_serve_admit(3, 64, 0, GB, 100 * GB - 1, 100 * GB) == 0
+    assert L.dvl_serve_admit(0, 64, 0, GB, 0, 100 * GB) == 0
+    assert L.dvl_server_create(None, 0, None) == dvl.ERR_ARG
+    L.dvl_server_destroy(None)
