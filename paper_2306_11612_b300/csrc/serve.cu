@@ -176,10 +176,10 @@ void finish_request(dvl_server* s, Request* r, int status, double t)
     }
 }
 
-// Hands a finished batch's results to its requests (lock held).
-void complete_batch(dvl_server* s, Dataset* d)
+// Hands a finished batch's results to its requests (lock held; no CUDA
+// calls: rc is the data set's dvl_sync status, taken without the lock).
+void complete_batch(dvl_server* s, Dataset* d, int rc)
 {
-    const int rc = dvl_sync(d->ctx);                 // the work is done: returns device-side errors
     const double t = now_s();
     uint64_t bin_off = 0, cnt_off = 0;
     for (size_t i = 0; i < d->batch.size(); ++i) {
@@ -235,8 +235,8 @@ bool launch_batch(dvl_server* s, Dataset* d, std::unique_lock<std::mutex>& lk)
     s->batch_reqs += k;
     s->max_batch_seen = std::max(s->max_batch_seen, k);
     const uint32_t M = d->M, T = s->cfg.n_entries;
-    // tables of the K slots (padding slots repeat the first request's) and one
-    // pair per slot (padding pairs have width 1)
+    // one pair per slot (padding slots repeat the first request's tables and
+    // have width 1)
     uint64_t nb = 0, nc = 0;
     d->pair_tf.resize(K);
     d->pair_w.resize(K);
@@ -246,6 +246,12 @@ bool launch_batch(dvl_server* s, Dataset* d, std::unique_lock<std::mutex>& lk)
         nb += (uint64_t)M * d->pair_w[i];
         nc += d->pair_w[i];
     }
+    dvl_params prm = s->cfg.params;
+    // No CUDA call while the lock is held: pinned allocation, the library
+    // calls and the stream callback may all wait on device work whose host
+    // callbacks take the lock.  The batch's requests stay alive (not done)
+    // and the data set's buffers belong to this thread until it is finished.
+    lk.unlock();
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = d->h_alpha.reserve((size_t)K * M * T);
     if (e == cudaSuccess) e = d->r_mean.reserve(nb);
@@ -256,8 +262,6 @@ bool launch_batch(dvl_server* s, Dataset* d, std::unique_lock<std::mutex>& lk)
     if (e == cudaSuccess) e = d->r_count.reserve(nc);
     for (uint32_t i = 0; i < K && e == cudaSuccess; ++i)
         std::memcpy(d->h_alpha.p + (size_t)i * M * T, d->batch[i < k ? i : 0]->alpha.data(), (size_t)M * T * 4);
-    dvl_params prm = s->cfg.params;
-    lk.unlock();
     int rc = e == cudaSuccess ? DVL_OK : DVL_ERR_NOMEM;
     if (rc == DVL_OK)
         rc = dvl_update_batch(d->ctx, d->h_alpha.p, K, T, DVL_MEM_HOST, nullptr, &prm, d->pair_tf.data(),
@@ -303,14 +307,30 @@ void scheduler(dvl_server* s)
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
-        for (auto& dp : s->ds)
-            if (dp->busy && dp->finished) complete_batch(s, dp.get());
+        // finished batches: sync (device-side errors) without the lock, then
+        // hand out the results
+        std::vector<Dataset*> done;
+        for (size_t i = 0; i < s->ds.size(); ++i) {
+            Dataset* d = s->ds[i].get();
+            if (d->busy && d->finished) {
+                d->finished = false;
+                done.push_back(d);
+            }
+        }
+        if (!done.empty()) {
+            std::vector<int> rc(done.size());
+            lk.unlock();
+            for (size_t i = 0; i < done.size(); ++i) rc[i] = dvl_sync(done[i]->ctx);
+            lk.lock();
+            for (size_t i = 0; i < done.size(); ++i) complete_batch(s, done[i], rc[i]);
+            continue;
+        }
         if (s->stop && s->inflight == 0) break;
         bool launched = false;
         if (!s->stop)
-            for (auto& dp : s->ds) {
+            for (size_t i = 0; i < s->ds.size(); ++i) {       // by index: add_dataset may grow ds
                 if (s->inflight >= (int)s->cfg.max_inflight) break;
-                Dataset* d = dp.get();
+                Dataset* d = s->ds[i].get();
                 if (!d->busy && !d->queue.empty()) launched |= launch_batch(s, d, lk);
             }
         if (launched) continue;
@@ -541,7 +561,7 @@ int dvl_server_warmup(dvl_server* s)
         s->cv_sched.notify_one();
         int rc = DVL_OK;
         for (uint64_t id : ids) {
-            const int r = dvl_server_wait(s, id, -1.0, nullptr);
+            const int r = dvl_server_wait(s, id, 600.0, nullptr);
             if (r != DVL_OK && rc == DVL_OK) rc = r;
         }
         if (rc != DVL_OK) return rc;

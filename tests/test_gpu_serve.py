@@ -53,7 +53,7 @@ def test_result_alone_equals_in_mix_and_plain():
     with DVLServer(0, max_batch=16, max_inflight=4, max_width=2048) as srv:
         for lo, lev, f in data:
             srv.add_dataset(lo, lev, f)
-        alone = srv.wait(srv.submit(*reqs[R]))
+        alone = srv.wait(srv.submit(*reqs[R]), timeout=120)
         srv.reset_stats()
         ids = [None] * len(reqs)
 
@@ -66,7 +66,7 @@ def test_result_alone_equals_in_mix_and_plain():
             t.start()
         for t in th:
             t.join()
-        res = [srv.wait(i) for i in ids]
+        res = [srv.wait(i, timeout=120) for i in ids]
         st = srv.stats()
         assert st["completed"] == len(reqs) and st["failed"] == 0
         assert st["batches"] < len(reqs), "requests that queued together were batched"
@@ -93,7 +93,7 @@ def test_served_request_matches_oracle():
     alpha = synth.random_tfs(77)
     with DVLServer(0, max_batch=4, max_width=1024) as srv:
         srv.add_dataset(a.lower, a.level, a.fields)
-        r = srv.wait(srv.submit(0, alpha, 1000))
+        r = srv.wait(srv.submit(0, alpha, 1000), timeout=120)
     _, _, lev, fl = oracle.sorted_inputs(a.lower, a.level, a.fields, oracle.SFC_HILBERT)
     o = oracle.update(fl, lev, alpha, None, None, width=1000)
     for m in range(4):
@@ -112,20 +112,20 @@ def test_memory_admission_limits_batches():
         srv.add_dataset(lo, lev, f)
         tfs = [synth.random_tfs(i) for i in range(10)]
         ids = [srv.submit(0, t, 1024) for t in tfs]
-        res = [srv.wait(i) for i in ids]
+        res = [srv.wait(i, timeout=120) for i in ids]
         st = srv.stats()
         assert st["completed"] == 10 and st["max_batch_seen"] <= 2
         assert st["mem_used"] <= st["mem_budget"]
-        alone = srv.wait(srv.submit(0, tfs[3], 1024))
+        alone = srv.wait(srv.submit(0, tfs[3], 1024), timeout=120)
         _same(res[3], alone)
     # room for the data set only: requests fail, the server keeps running
     with DVLServer(0, mem_budget=resident + 1, max_batch=16, max_width=1024) as srv:
         srv.add_dataset(lo, lev, f)
         with pytest.raises(dvl.DVLError) as e:
-            srv.wait(srv.submit(0, tfs[0], 1024))
+            srv.wait(srv.submit(0, tfs[0], 1024), timeout=120)
         assert e.value.status == dvl.ERR_NOMEM
         with pytest.raises(dvl.DVLError):
-            srv.wait(srv.submit(0, tfs[1], 1024))
+            srv.wait(srv.submit(0, tfs[1], 1024), timeout=120)
     # not even the data set fits
     with DVLServer(0, mem_budget=resident // 2, max_batch=4, max_width=1024) as srv:
         with pytest.raises(dvl.DVLError) as e:
@@ -148,5 +148,5 @@ def test_server_errors_and_warmup():
         bad[0, 3] = -0.5
         with pytest.raises(dvl.DVLError):
             srv.submit(did, bad, 256)                       # alpha outside [0, 1]
-        r = srv.wait(srv.submit(did, t, 256))
+        r = srv.wait(srv.submit(did, t, 256), timeout=120)
         assert r["count"].sum() >= 3000
