@@ -37,12 +37,18 @@ sys.path.insert(0, ROOT)
 # Algorithmic bytes.  Pass A reads the 4 float32 fields and the level byte of
 # every cell and writes one u64 width total per warp step (128 cells) and one
 # u64 prefix per chunk (2048 cells).  The bins stage then answers one range
-# query per pixel from the value tables: per pixel boundary it re-reads the
-# one 128-cell step that contains the boundary (17 B/cell) and per pixel the
-# two partial steps at its ends (16 B/cell), plus a few table entries.
+# query per pixel from the value tables.  Per pixel boundary (k_bounds): the
+# one 128-cell step that holds it is re-read (128 x 17 B), with its chunk's 16
+# step totals (128 B), about three rounds of 32 chunk-prefix probes (768 B),
+# and it writes H, S and two partial-step records of 4 fields x 24 B (201 B).
+# Per pixel (k_pixels): H and S of both ends (18 B), the two records
+# (192 B), two prefix-sum entries (128 B) and four sparse-table entries
+# (64 B), all over the 4 fields, and the bins written (4 x 24 + 4 B).
 SCAN_BYTES = 8 / 128 + 8 / 2048
 BYTES_PASS_A = 4 * 4 + 1 + SCAN_BYTES
-BYTES_BINS_PER_PIXEL = 128 * 17 + 2 * 128 * 16 + 4 * 64
+BYTES_BOUNDS_PER_PIXEL = 128 * 17 + 16 * 8 + 3 * 32 * 8 + 8 + 1 + 2 * 4 * 24
+BYTES_PIXELS_PER_PIXEL = 2 * 9 + 2 * 4 * 24 + 2 * 4 * 16 + 4 * 4 * 4 + 4 * 24 + 4
+BYTES_BINS_PER_PIXEL = BYTES_BOUNDS_PER_PIXEL + BYTES_PIXELS_PER_PIXEL
 CPU_SAMPLE_BOX = ((0, 0, 0), 32)     # 32^3 of the 128^3 base cells (1/64 of the domain)
 LAUNCHES_PER_UPDATE = 4              # prepare, width+scan pass, pixel bounds, pixel bins
 METRIC = "DVL update throughput (cells/s per alpha-TF edit)"
@@ -61,9 +67,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline budget (rank 0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", choices=["plain", "batch", "serve"], default="plain",
+    ap.add_argument("--mode", choices=["plain", "batch", "serve", "sweep"], default="plain",
                     help="plain: one TF edit per step (default); batch: K TFs x 4 viewports per step; "
-                         "serve: Poisson TF-edit requests over 8 resident data sets")
+                         "serve: Poisson TF-edit requests over 8 resident data sets; "
+                         "sweep: ms/edit over the P x minimum-importance grid of the paper's Fig. 4")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean request arrival rate (1/s)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="length of the request stream (s)")
     ap.add_argument("--batch-tfs", type=int, default=64)
@@ -299,16 +306,23 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
     with ClockSampler(local) as clk:
         start.record(stream)
         for i in range(args.steps):
             ctx.set_tfs(tfs[args.warmup + i])
             ctx.update(**kw)
+            marks[i].record(stream)
         end.record(stream)
         end.synchronize()
     barrier()
     ms = start.elapsed_time(end)
+    per_edit = [start.elapsed_time(marks[0])] + [marks[i - 1].elapsed_time(marks[i]) for i in range(1, args.steps)]
+    tail = per_edit[20:] if len(per_edit) > 40 else per_edit
+    edit_pct = {"p50_ms": statistics.median(tail),
+                "p99_ms": sorted(tail)[min(len(tail) - 1, int(0.99 * len(tail)))],
+                "edits": f"{len(per_edit) - len(tail)}..{len(per_edit) - 1}"}
     stages = ctx.get_timings()
     ctx.set_option(dvl.OPT_TIMING, 0)
     if world > 1:
@@ -366,6 +380,7 @@ def run_ours(args):
             "kernels": dict(kern, prepare_ms=stages["prepare"], finalize_ms=stages["finalize"],
                             edit_bytes_per_cell=edit_bytes / amr.n, edit_gbs=step_gbs, edit_frac=step_gbs / peak,
                             first_update_ms_with_value_tables=t_first),
+            "per_edit": edit_pct,
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": LAUNCHES_PER_UPDATE * args.steps,
             "setup_s": {"generate": t_gen, "load": t_load, "build_order": t_build}}
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -721,6 +736,57 @@ def run_serve(args):
         torch.distributed.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# sweep mode: ms per edit over P and the minimum importance (Fig. 4 settings)
+# ---------------------------------------------------------------------------
+
+SWEEP_P = (0.0, 0.5, 1.0, 2.0, 5.0)
+SWEEP_MIMP = (0.0, 0.025, 0.1, 0.25)
+
+
+def run_sweep(args):
+    import torch
+    import paper_2306_11612_b300 as dvl
+    import synth
+    torch.cuda.set_device(0)
+    amr = synth.make(args.config, pinned=True)
+    stream = torch.cuda.Stream(0)
+    ctx = dvl.DVL(0, stream)
+    ctx.load_amr(amr.lower, amr.level, amr.fields)
+    ctx.build_order(dvl.SFC_HILBERT)
+    tfs = tf_sequence(args.steps + args.warmup)
+    grid = []
+    with ClockSampler(0) as clk:
+        for P in SWEEP_P:
+            for mi in SWEEP_MIMP:
+                kw = dict(P=P, min_importance=mi, width=args.width)
+                for i in range(args.warmup):
+                    ctx.set_tfs(tfs[i])
+                    ctx.update(**kw)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(stream)
+                for i in range(args.steps):
+                    ctx.set_tfs(tfs[args.warmup + i])
+                    ctx.update(**kw)
+                b.record(stream)
+                b.synchronize()
+                ms = a.elapsed_time(b) / args.steps
+                grid.append({"P": P, "min_importance": mi, "ms_per_edit": ms, "cells_per_s": amr.n / (ms * 1e-3),
+                             "Q": ctx.get_stats()["Q"]})
+    ctx.close()
+    best = max(g["cells_per_s"] for g in grid)
+    line = {"metric": METRIC + " over the P x min-importance grid", "value": min(g["cells_per_s"] for g in grid),
+            "unit": "cells/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": max(g["ms_per_edit"] for g in grid), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+u64", "data": "synthetic",
+            "config": dict(workload_desc(amr, args), sweep="value = slowest setting of the grid"),
+            "grid": grid, "fastest_cells_per_s": best, "clocks": clk.summary(), "roofline": None,
+            "roofline_note": "per-kernel roofline in the default mode", "e2e": None,
+            "gpu_launches": LAUNCHES_PER_UPDATE * args.steps * len(grid)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -729,6 +795,8 @@ def main():
         run_batch(args)
     elif args.mode == "serve":
         run_serve(args)
+    elif args.mode == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 
