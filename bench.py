@@ -172,6 +172,25 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The maximum of a per-rank time over all ranks (the job's time): one
+    all-reduce on the process group's backend (NCCL on GPUs, gloo in tests)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the
+    max-over-ranks time (weak scaling: each rank holds its own data set)."""
+    return units_per_rank * world / seconds
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -325,11 +344,8 @@ def run_ours(args):
                 "edits": f"{len(per_edit) - len(tail)}..{len(per_edit) - 1}"}
     stages = ctx.get_timings()
     ctx.set_option(dvl.OPT_TIMING, 0)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = amr.n * world * args.steps / (ms * 1e-3)
+    ms = max_over_ranks(ms, world)
+    value = job_throughput(amr.n * args.steps, world, ms * 1e-3)
 
     # end to end through the public API with host buffers: TFs up, bins down
     e2e = None
@@ -346,10 +362,7 @@ def run_ours(args):
             for m in range(4):
                 ctx.read_bins(m, outs[m])
         el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(el, world)
         e2e = {"value": amr.n * world * args.steps / el, "unit": "cells/s",
                "h2d_bytes_per_step": 4 * 256 * 4 + 2 * 4 * 4, "d2h_bytes_per_step": 4 * W * (4 * 4 + 8 + 4),
                "ms_per_step": el / args.steps * 1e3}
@@ -464,10 +477,7 @@ def run_batch(args):
     barrier()
     ms = start.elapsed_time(end)
     replayed = ctx.batch_config()["replayed"]
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     step_ms = ms / args.steps
     value = amr.n * len(pairs) * world / (step_ms * 1e-3)
 
@@ -513,10 +523,7 @@ def run_batch(args):
             ctx.update_batch(host[i % n_sets], pairs, **kw)
             ctx.read_batch_all(out)
         el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(el, world)
         e2e = {"value": amr.n * len(pairs) * world * args.steps / el, "unit": "cells/s",
                "h2d_bytes_per_step": int(host[0].numel() * 4), "d2h_bytes_per_step": int(nb * 24 + nc * 4),
                "ms_per_step": el / args.steps * 1e3}
