@@ -127,6 +127,33 @@ __device__ __forceinline__ float spread(const float (&al)[M])
     return __fsub_rn(hi, lw);
 }
 
+// Fast TF entry for a power-of-two table size T (then t*T is exact):
+//   t = clamp(fl((v - lo) * s), 0, 1)  one multiply with saturation (NaN -> 0;
+//                                      the sign of a zero t does not matter here),
+//   floor(t * T) + 2^23               one fma rounded toward zero,
+// and the shared-memory address of the entry from that result's bits in one
+// multiply-add: c_m = table address of field m - 4 * bits(2^23) (mod 2^32).
+// The entry equals min(floor(t*T), T) of the general path bit for bit.
+__device__ __forceinline__ float mul_sat(float a, float b)
+{
+    float r;
+    asm("mul.rn.sat.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float fma_rz(float a, float b, float c)
+{
+    float r;
+    asm("fma.rz.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float lds_f32(uint32_t addr)
+{
+    float r;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(r) : "r"(addr));
+    return r;
+}
+constexpr uint32_t BITS_2P23 = 0x4B000000u;         // bits of 2^23
+
 // Per-cell constants in registers, specialised on the field count M and the
 // exponent mode.  The alpha tables live in shared memory with T+1 entries per
 // field (entry T repeats entry T-1) so that t = 1 needs no clamp.
@@ -167,6 +194,20 @@ struct Cell {
     __device__ __forceinline__ uint32_t width(const float* t, uint32_t L, const float* s_tf) const
     {
         float f = importance<PM>(variation(t, s_tf), L, inv_vmax, mb, ma, wshift, n2, P);
+        return __float2uint_rn(__fmul_rn(f, qscale));
+    }
+
+    // the same width from the raw field values, T a power of two (see
+    // mul_sat / fma_rz); cm[m] = shared address of field m's table - 4 bits(2^23)
+    __device__ __forceinline__ uint32_t width_p2(const float* v, uint32_t L, const uint32_t* cm) const
+    {
+        float al[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const float t = mul_sat(__fsub_rn(v[m], lo[m]), s[m]);
+            al[m] = lds_f32(__float_as_uint(fma_rz(t, Tf, 8388608.0f)) * 4u + cm[m]);
+        }
+        float f = importance<PM>(spread<M>(al), L, inv_vmax, mb, ma, wshift, n2, P);
         return __float2uint_rn(__fmul_rn(f, qscale));
     }
 };

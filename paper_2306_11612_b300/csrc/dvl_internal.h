@@ -122,7 +122,7 @@ struct UpdateArgs {
     const float* dom;          // 2*M: lo[M], hi[M]  (NaN,NaN = data range)
     const DataMeta* meta;
     UpdateConsts* consts;
-    unsigned long long* tile_status;   // n_tiles
+    unsigned long long* tile_status;   // n_tiles scan status words
     unsigned long long* chunk_prefix;  // n_chunks
     unsigned long long* step_sums;     // n_chunks * STEPS width totals per warp step, or
                                        // null (then the placement pass recomputes widths)

@@ -33,7 +33,7 @@
 namespace dvl {
 
 namespace {
-__global__ void k_prepare(UpdateArgs a, uint32_t n_tiles)
+__global__ void k_prepare(UpdateArgs a, uint64_t n_status)
 {
     // clear bins and scan state
     const uint64_t MW = (uint64_t)a.M * a.W;
@@ -45,7 +45,7 @@ __global__ void k_prepare(UpdateArgs a, uint32_t n_tiles)
         a.vmax[i] = 0u;
         if (i < a.W) a.count[i] = 0u;
     }
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_tiles;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_status;
          i += (uint64_t)gridDim.x * blockDim.x)
         a.tile_status[i] = 0ull;
     if (blockIdx.x != 0) return;
@@ -85,9 +85,9 @@ __global__ void k_consts(UpdateArgs a) { finish_consts(a.consts, a, a.meta->max_
 // ---------------------------------------------------------------------------
 
 // Sum of the fixed-point widths of one lane's 4 cells at idx.
-template <int M, int PM, bool FULLSTEP>
+template <int M, int PM, bool FULLSTEP, bool P2>
 __device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, const UpdateArgs& a,
-                                                      const float* s_tf, uint64_t idx)
+                                                      const float* s_tf, const uint32_t* cm, uint64_t idx)
 {
     float v[4][M];
     uint32_t L4;
@@ -95,16 +95,22 @@ __device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, con
     unsigned long long acc = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        float t[M];
+        uint32_t q;
+        if (P2) {
+            q = cc.width_p2(v[j], (L4 >> (8 * j)) & 0xFF, cm);
+        } else {
+            float t[M];
 #pragma unroll
-        for (int m = 0; m < M; ++m) t[m] = norm_t(v[j][m], cc.lo[m], cc.s[m]);
-        uint32_t q = cc.width(t, (L4 >> (8 * j)) & 0xFF, s_tf);
+            for (int m = 0; m < M; ++m) t[m] = norm_t(v[j][m], cc.lo[m], cc.s[m]);
+            q = cc.width(t, (L4 >> (8 * j)) & 0xFF, s_tf);
+        }
         if (FULLSTEP || idx + j < a.n) acc += q;
     }
     return acc;
 }
 
-template <int M, int PM>
+// P2: the table size is a power of two (fast TF entries, see width_p2)
+template <int M, int PM, bool P2>
 __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_tiles)
 {
     extern __shared__ float s_tf[];
@@ -118,6 +124,10 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
     const uint32_t tile = s_tile;
     Cell<M, PM> cc;
     cc.load(a.consts, a.T);
+    uint32_t cm[M];
+    const uint32_t sb = (uint32_t)__cvta_generic_to_shared(s_tf);
+#pragma unroll
+    for (int m = 0; m < M; ++m) cm[m] = sb + 4u * (uint32_t)(m * (a.T + 1)) - 4u * BITS_2P23;
 
     const uint64_t chunk = (uint64_t)tile * WARPS + warp;
     const uint64_t base = chunk * CHUNK;
@@ -125,14 +135,14 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
     if (base + CHUNK <= a.n) {
 #pragma unroll 2
         for (int st = 0; st < STEPS; ++st) {
-            const unsigned long long l = widths4<M, PM, true>(cc, a, s_tf, base + st * STEP + lane * 4);
+            const unsigned long long l = widths4<M, PM, true, P2>(cc, a, s_tf, cm, base + st * STEP + lane * 4);
             s_lane[warp][st][lane] = l;
             acc += l;
         }
     } else {
         for (int st = 0; st < STEPS; ++st) {
             const uint64_t idx = base + st * STEP + lane * 4;
-            const unsigned long long l = idx < a.n ? widths4<M, PM, false>(cc, a, s_tf, idx) : 0ull;
+            const unsigned long long l = idx < a.n ? widths4<M, PM, false, P2>(cc, a, s_tf, cm, idx) : 0ull;
             s_lane[warp][st][lane] = l;
             acc += l;
         }
@@ -754,12 +764,17 @@ template <int M, int PM>
 cudaError_t run_passes(cudaStream_t s, const UpdateArgs& a, uint32_t n_tiles, size_t smem)
 {
     cudaError_t e;
-    if ((e = smem_attr(k_passA<M, PM>, smem)) != cudaSuccess) return e;
+    const bool p2 = (a.T & (a.T - 1)) == 0;          // power-of-two table size
+    if ((e = smem_attr(k_passA<M, PM, true>, smem)) != cudaSuccess) return e;
+    if ((e = smem_attr(k_passA<M, PM, false>, smem)) != cudaSuccess) return e;
     if ((e = smem_attr(k_passB<M, PM>, smem)) != cudaSuccess) return e;
     if ((e = smem_attr(k_passB_steps<M, PM, false>, smem)) != cudaSuccess) return e;
     if ((e = smem_attr(k_passB_steps<M, PM, true>, smem)) != cudaSuccess) return e;
     if (a.events) cudaEventRecord(a.events[1], s);
-    if (n_tiles) k_passA<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles);
+    if (n_tiles) {
+        if (p2) k_passA<M, PM, true><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles);
+        else k_passA<M, PM, false><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles);
+    }
     if (a.events) cudaEventRecord(a.events[2], s);
     if (a.vt) return cudaSuccess;          // bins come from range queries (see run_update)
     if (n_tiles) {
@@ -781,9 +796,10 @@ cudaError_t run_update(cudaStream_t s, const UpdateArgs& a)
     const size_t smem = (size_t)M * (a.T + 1) * sizeof(float);
     cudaError_t e;
     if ((e = smem_attr(k_vmax_exact<M>, smem)) != cudaSuccess) return e;
-    const uint64_t clear = (uint64_t)a.M * a.W > n_tiles ? (uint64_t)a.M * a.W : n_tiles;
+    const uint64_t n_status = n_tiles;                 // scan status words, one per tile
+    const uint64_t clear = (uint64_t)a.M * a.W > n_status ? (uint64_t)a.M * a.W : n_status;
     if (a.events) cudaEventRecord(a.events[0], s);
-    k_prepare<<<grid_cap(clear, 256), 256, 0, s>>>(a, n_tiles);
+    k_prepare<<<grid_cap(clear, 256), 256, 0, s>>>(a, n_status);
     if (a.prm.vmax_mode == DVL_VMAX_EXACT) {
         k_vmax_exact<M><<<grid_cap(a.n, 256), 256, smem, s>>>(a);
         k_consts<<<1, 1, 0, s>>>(a);
