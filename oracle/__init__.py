@@ -16,6 +16,9 @@ Parity status per function (see the tests that pin each one):
                     fixtures, and sum/count invariants.
 * ``alpha_grad`` -- pinned: float64 central differences (the loss is quadratic
                     in the control points once the assignment is fixed).
+* ``rasterize``  -- pinned: a hand-worked golden image and the properties that
+                    define the drawing (contiguous columns through the value's
+                    row, 8-connected segments, bar heights).
 """
 from __future__ import annotations
 
@@ -72,6 +75,7 @@ def _L():
         _lib.orc_keys.argtypes = [u64, vp, vp, vp, vp, ctypes.c_int, vp]
         _lib.orc_order.argtypes = [u64, vp, vp]
         _lib.orc_update.argtypes = [u64, u32, vp, vp, u32, vp, vp, vp, ctypes.POINTER(Params)] + [vp] * 10 + [ctypes.POINTER(Stats)]
+        _lib.orc_rasterize.argtypes = [u32, u32, u32, vp, u32, vp, vp]
         _lib.orc_alpha_grad.argtypes = [u64, u32, vp, vp, u32, u32, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp, vp]
         for f in (_lib.orc_keys, _lib.orc_order, _lib.orc_update, _lib.orc_alpha_grad):
             f.restype = ctypes.c_int
@@ -176,3 +180,15 @@ def sorted_inputs(lower, level, fields, sfc):
     k = keys(lower, level, sfc)
     perm = order(k)
     return k[perm], perm, np.ascontiguousarray(level[perm]), np.ascontiguousarray(fields[:, perm])
+
+
+def rasterize(values: np.ndarray, height: int, bar_field: int = 0):
+    """(lines, bars) uint8 images (height, W) of the (M, W) bin values in [0, 1]."""
+    v = np.ascontiguousarray(values, np.float32)
+    M, W = v.shape
+    lines = np.zeros((height, W), np.uint8)
+    bars = np.zeros((height, W), np.uint8)
+    rc = _L().orc_rasterize(M, W, height, _p(v), bar_field, _p(lines), _p(bars))
+    if rc:
+        raise OracleError(f"orc_rasterize failed ({rc})")
+    return lines, bars

@@ -484,3 +484,46 @@ done:
     free(table); free(sum); free(vmn); free(vmx); free(cnt); free(b1); free(b2); free(gtab);
     return rc;
 }
+
+/* ---- line-plot rasterisation (see dvl_oracle.h) ---------------------------- */
+
+static int32_t plot_row(float v, uint32_t H)
+{
+    float d = 1.0f - v;                       /* correctly rounded float32 steps */
+    float x = d * (float)(H - 1);
+    float y = x + 0.5f;
+    int32_t r = (int32_t)floorf(y);
+    if (r < 0) r = 0;
+    if (r > (int32_t)H - 1) r = (int32_t)H - 1;
+    return r;
+}
+
+int orc_rasterize(uint32_t M, uint32_t W, uint32_t H, const float* values, uint32_t bar_field,
+                  uint8_t* lines, uint8_t* bars)
+{
+    if (M < 1 || M > 8 || W < 1 || H < 1 || !values || bar_field >= M) return -1;
+    for (uint64_t i = 0; i < (uint64_t)H * W; ++i) {
+        if (lines) lines[i] = 0;
+        if (bars) bars[i] = 0;
+    }
+    for (uint32_t m = 0; m < M; ++m)
+        for (uint32_t p = 0; p < W; ++p) {
+            const int32_t r = plot_row(values[(uint64_t)m * W + p], H);
+            int32_t lo = r, hi = r;
+            if (p > 0) {                          /* this column's share of the segment from p-1 */
+                const int32_t a = r - (r - plot_row(values[(uint64_t)m * W + p - 1], H)) / 2;
+                if (a < lo) lo = a;
+                if (a > hi) hi = a;
+            }
+            if (p + 1 < W) {                      /* and of the segment to p+1 */
+                const int32_t b = r + (plot_row(values[(uint64_t)m * W + p + 1], H) - r) / 2;
+                if (b < lo) lo = b;
+                if (b > hi) hi = b;
+            }
+            if (lines)
+                for (int32_t row = lo; row <= hi; ++row) lines[(uint64_t)row * W + p] |= (uint8_t)(1u << m);
+            if (bars && m == bar_field)
+                for (int32_t row = r; row < (int32_t)H; ++row) bars[(uint64_t)row * W + p] = 1;
+        }
+    return 0;
+}

@@ -84,6 +84,20 @@ int orc_alpha_grad(uint64_t n, uint32_t M, const float* fields, const uint8_t* l
                    const float* dom_hi, const orc_params* prm, const double* target,
                    double* abar, double* grad, double* loss);
 
+/* Line-plot rasterisation of the bins (the RasterizeLines step after the
+ * update, Sec. 4, Fig. 1): an H x W image, row 0 at the top, column p = bin p.
+ * values[m*W + p] in [0, 1] (the bin means or their alpha) maps to the row
+ *   r = clamp(floor((1 - v) * (H - 1) + 1/2), 0, H - 1)
+ * in correctly rounded float32 steps.  Polyline of field m: consecutive bins
+ * are joined; column p covers the rows between r_p, r_p - trunc((r_p -
+ * r_{p-1}) / 2) (if p > 0) and r_p + trunc((r_{p+1} - r_p) / 2) (if p < W-1),
+ * so that the two columns of a segment split its rise between them; bit m of
+ * lines[row*W + p] is set where field m's line covers the pixel.  Bar plot of
+ * field bar_field: bars[row*W + p] = 1 for rows r_p .. H-1, else 0.  Returns 0,
+ * or -1 for invalid arguments (M in 1..8, W >= 1, H >= 1). */
+int orc_rasterize(uint32_t M, uint32_t W, uint32_t H, const float* values, uint32_t bar_field,
+                  uint8_t* lines, uint8_t* bars);
+
 #ifdef __cplusplus
 }
 #endif
