@@ -51,6 +51,7 @@ BYTES_PIXELS_PER_PIXEL = 2 * 9 + 2 * 4 * 24 + 2 * 4 * 16 + 4 * 4 * 4 + 4 * 24 + 
 BYTES_BINS_PER_PIXEL = BYTES_BOUNDS_PER_PIXEL + BYTES_PIXELS_PER_PIXEL
 CPU_SAMPLE_BOX = ((0, 0, 0), 32)     # 32^3 of the 128^3 base cells (1/64 of the domain)
 LAUNCHES_PER_UPDATE = 4              # prepare, width+scan pass, pixel bounds, pixel bins
+RASTER_H = 512                       # rows of the line-plot image
 METRIC = "DVL update throughput (cells/s per alpha-TF edit)"
 
 
@@ -344,6 +345,17 @@ def run_ours(args):
                 "edits": f"{len(per_edit) - len(tail)}..{len(per_edit) - 1}"}
     stages = ctx.get_timings()
     ctx.set_option(dvl.OPT_TIMING, 0)
+    # the line plot of the last edit (polylines of all fields, bars of one), H = 512
+    img = torch.empty((2, RASTER_H, args.width), dtype=torch.uint8, device=f"cuda:{local}")
+    for i in range(3):
+        ctx.rasterize(RASTER_H, dvl.PLOT_Y, 0, lines=img[0], bars=img[1])
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for i in range(20):
+        ctx.rasterize(RASTER_H, dvl.PLOT_Y, 0, lines=img[0], bars=img[1])
+    r1.record(stream)
+    r1.synchronize()
+    raster_ms = r0.elapsed_time(r1) / 20
     ms = max_over_ranks(ms, world)
     value = job_throughput(amr.n * args.steps, world, ms * 1e-3)
 
@@ -392,7 +404,8 @@ def run_ours(args):
             "config": workload_desc(amr, args), "roofline": roofline,
             "kernels": dict(kern, prepare_ms=stages["prepare"], finalize_ms=stages["finalize"],
                             edit_bytes_per_cell=edit_bytes / amr.n, edit_gbs=step_gbs, edit_frac=step_gbs / peak,
-                            first_update_ms_with_value_tables=t_first),
+                            first_update_ms_with_value_tables=t_first,
+                            rasterize_ms=raster_ms, rasterize_image=f"{RASTER_H} x {args.width}, 4 polylines + bars"),
             "per_edit": edit_pct,
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": LAUNCHES_PER_UPDATE * args.steps,
             "setup_s": {"generate": t_gen, "load": t_load, "build_order": t_build}}

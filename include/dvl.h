@@ -256,6 +256,24 @@ int dvl_get_timings(dvl_ctx* ctx, double* ms, int n);
 enum { DVL_OPT_SPIN_LIMIT = 1, DVL_OPT_FAULT_NO_PUBLISH = 2, DVL_OPT_TIMING = 3 };
 int dvl_set_option(dvl_ctx* ctx, int option, int64_t value);
 
+/* Line-plot image of the bins of the last dvl_update (the RasterizeLines
+ * step after the update, Sec. 4, Fig. 1), headless: an height x W image, row 0
+ * at the top, column p = bin p, row-major bytes.
+ *   value_kind  DVL_PLOT_MEAN (mean of the normalised values) or DVL_PLOT_Y
+ *               (alpha of the mean, the bar heights of Fig. 1)
+ *   lines       bit m set where field m's polyline covers the pixel: a bin
+ *               value v maps to row r = clamp(floor((1 - v)(height - 1) +
+ *               1/2), 0, height - 1) (float32 steps), and column p covers
+ *               the rows between r_p, r_p - trunc((r_p - r_{p-1})/2) and
+ *               r_p + trunc((r_{p+1} - r_p)/2)
+ *   bars        1 from r_p of field bar_field down to the last row, else 0
+ * Either output may be NULL; host or device memory per mem_kind (host: the
+ * call synchronises).  height in [1, 65536].  Errors: DVL_ERR_ARG,
+ * DVL_ERR_STATE (no update has run), DVL_ERR_NOMEM, DVL_ERR_CUDA. */
+enum { DVL_PLOT_MEAN = 0, DVL_PLOT_Y = 1 };
+int dvl_rasterize(dvl_ctx* ctx, uint32_t height, uint32_t value_kind, uint32_t bar_field, uint8_t* lines,
+                  uint8_t* bars, int mem_kind);
+
 /* Batched update: K transfer functions, each with any number of viewport
  * widths, over the loaded data set (paper Sec. 3.3-3.4 per (TF, width) pair;
  * the batching itself is not in the paper -- it serves many clients editing

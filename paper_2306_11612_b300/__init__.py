@@ -28,12 +28,13 @@ MINIMP_BEFORE_SCALE, MINIMP_AFTER_POWER = 0, 1
 VMAX_APPROX, VMAX_EXACT = 0, 1
 WIDTH_EDGE, WIDTH_VOLUME = 0, 1
 OPT_SPIN_LIMIT, OPT_FAULT_NO_PUBLISH, OPT_TIMING = 1, 2, 3
+PLOT_MEAN, PLOT_Y = 0, 1
 
 EXPORTS = ["dvl_create", "dvl_destroy", "dvl_load_amr", "dvl_build_order", "dvl_set_fields",
            "dvl_set_tf", "dvl_update", "dvl_read_bins", "dvl_get_stats", "dvl_read_order",
            "dvl_read_widths", "dvl_sync", "dvl_set_option", "dvl_get_timings", "dvl_update_noalloc", "dvl_set_tf_ctrl", "dvl_read_alpha_means", "dvl_backward",
            "dvl_update_batch", "dvl_read_batch_bins", "dvl_read_batch_all", "dvl_batch_config",
-           "dvl_read_batch_all_async", "dvl_stream",
+           "dvl_read_batch_all_async", "dvl_stream", "dvl_rasterize",
            "dvl_status_string", "dvl_last_error",
            "dvl_server_create", "dvl_server_destroy", "dvl_server_add_dataset", "dvl_server_warmup",
            "dvl_server_submit", "dvl_server_wait", "dvl_server_get_stats", "dvl_server_reset_stats",
@@ -103,6 +104,7 @@ def _load():
         "dvl_batch_config": ([vp, ctypes.POINTER(ctypes.c_int32)], i32),
         "dvl_read_batch_all_async": ([vp, ctypes.POINTER(dvl_bins)], i32),
         "dvl_stream": ([vp], vp),
+        "dvl_rasterize": ([vp, u32, u32, u32, vp, vp, i32], i32),
         "dvl_server_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(dvl_server_config)], i32),
         "dvl_server_destroy": ([vp], None),
         "dvl_server_add_dataset": ([vp, u64, vp, vp, u32, vp, i32, ctypes.POINTER(u32)], i32),
@@ -277,6 +279,22 @@ class DVL:
         return out
 
     backward = dvl_backward
+
+    def dvl_rasterize(self, height: int, value_kind: int = 1, bar_field: int = 0, lines=None, bars=None):
+        """Line-plot image of the last update's bins: (lines, bars) uint8
+        (height, W) arrays (numpy by default; CUDA tensors stay on the device)."""
+        if lines is None and bars is None:
+            lines = np.empty((height, self.W), np.uint8)
+            bars = np.empty((height, self.W), np.uint8)
+        pl, kl, keep_l = _ptr_kind(lines) if lines is not None else (None, None, None)
+        pb, kb, keep_b = _ptr_kind(bars) if bars is not None else (None, None, None)
+        kinds = {k for k in (kl, kb) if k is not None}
+        if len(kinds) != 1:
+            raise ValueError("outputs must be in the same memory")
+        self._check(lib.dvl_rasterize(self._h, height, value_kind, bar_field, pl, pb, kinds.pop()))
+        return lines, bars
+
+    rasterize = dvl_rasterize
 
     @staticmethod
     def _bins_struct(W, out):

@@ -91,6 +91,8 @@ struct dvl_ctx {
     ulonglong2* d_psum = nullptr;     // boundary partial terms, 2 x M per boundary
     float2* d_pmm = nullptr;
     uint32_t HS_cap = 0;
+    uint8_t* d_img = nullptr;         // line-plot images for host outputs (2 x H x W)
+    size_t img_cap = 0;
     // batched updates (K TFs x viewports)
     float* d_btf = nullptr;               // K x M x T
     float* d_bdom = nullptr;              // 2 x DVL_MAX_FIELDS
@@ -354,7 +356,7 @@ void dvl_destroy(dvl_ctx* c)
     dfree(c->d_sum); dfree(c->d_vmin); dfree(c->d_vmax); dfree(c->d_count);
     dfree(c->d_mean); dfree(c->d_y); dfree(c->d_asum); dfree(c->d_amean); dfree(c->d_ctrl);
     dfree(c->d_gtab); dfree(c->d_gin); dfree(c->d_gout); dfree(c->d_H); dfree(c->d_S);
-    dfree(c->d_psum); dfree(c->d_pmm);
+    dfree(c->d_psum); dfree(c->d_pmm); dfree(c->d_img);
     for (auto& set : c->ev)
         for (auto e : set) cudaEventDestroy(e);
     free_batch(c);
@@ -712,6 +714,41 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
     c->last_prm = *p;
     c->last_alpha = p->want_alpha != 0;
     c->have_update = true;
+    return DVL_OK;
+}
+
+int dvl_rasterize(dvl_ctx* c, uint32_t height, uint32_t value_kind, uint32_t bar_field, uint8_t* lines,
+                  uint8_t* bars, int mem_kind)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (!c->have_update) return fail(c, DVL_ERR_STATE, "no update has run");
+    if (height < 1 || height > 65536) return fail(c, DVL_ERR_ARG, "height must be in [1, 65536]");
+    if (value_kind != DVL_PLOT_MEAN && value_kind != DVL_PLOT_Y) return fail(c, DVL_ERR_ARG, "bad value_kind");
+    if (bar_field >= c->M) return fail(c, DVL_ERR_ARG, "bar_field %u out of range", bar_field);
+    if (!lines && !bars) return fail(c, DVL_ERR_ARG, "no output");
+    if (mem_kind != DVL_MEM_HOST && mem_kind != DVL_MEM_DEVICE) return fail(c, DVL_ERR_ARG, "bad mem_kind");
+    cudaSetDevice(c->device);
+    const uint32_t W = c->W_last;
+    const size_t HW = (size_t)height * W;
+    uint8_t *dl = lines, *db = bars;
+    if (mem_kind == DVL_MEM_HOST) {
+        if (2 * HW > c->img_cap) {
+            CK(cudaStreamSynchronize(c->stream), "synchronize");
+            CK(dalloc(c->d_img, 2 * HW), "alloc image");
+            c->img_cap = 2 * HW;
+        }
+        dl = lines ? c->d_img : nullptr;
+        db = bars ? c->d_img + HW : nullptr;
+    }
+    const float* val = value_kind == DVL_PLOT_MEAN ? c->d_mean : c->d_y;
+    CK(launch_raster(c->stream, val, c->M, W, height, bar_field, dl, db), "raster kernel");
+    if (mem_kind == DVL_MEM_HOST) {
+        if (lines) CK(cudaMemcpyAsync(lines, dl, HW, cudaMemcpyDeviceToHost, c->stream), "copy lines");
+        if (bars) CK(cudaMemcpyAsync(bars, db, HW, cudaMemcpyDeviceToHost, c->stream), "copy bars");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        return take_device_error(c);
+    }
     return DVL_OK;
 }
 

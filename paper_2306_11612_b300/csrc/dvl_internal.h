@@ -201,6 +201,11 @@ cudaError_t launch_backward(cudaStream_t s, const UpdateArgs& a, const float* g,
                             float* grad_ctrl);
 cudaError_t launch_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* q);
 
+// raster.cu: line-plot image of M x W bin values (lines: bit m per field,
+// bars of one field), H x W bytes each, row-major; either may be null.
+cudaError_t launch_raster(cudaStream_t s, const float* values, uint32_t M, uint32_t W, uint32_t H,
+                          uint32_t bar_field, uint8_t* lines, uint8_t* bars);
+
 // Opts a kernel in to `bytes` of dynamic shared memory.  Always set: the
 // 48 KB default covers static plus dynamic memory, and several kernels have
 // static arrays of their own.
