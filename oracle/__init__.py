@@ -19,6 +19,8 @@ Parity status per function (see the tests that pin each one):
 * ``rasterize``  -- pinned: a hand-worked golden image and the properties that
                     define the drawing (contiguous columns through the value's
                     row, 8-connected segments, bar heights).
+* ``brush``, ``select_keys`` -- pinned: the exact-rational brute force's bins
+                    give the same selections; hand-built key ranges.
 """
 from __future__ import annotations
 
@@ -76,6 +78,9 @@ def _L():
         _lib.orc_order.argtypes = [u64, vp, vp]
         _lib.orc_update.argtypes = [u64, u32, vp, vp, u32, vp, vp, vp, ctypes.POINTER(Params)] + [vp] * 10 + [ctypes.POINTER(Stats)]
         _lib.orc_rasterize.argtypes = [u32, u32, u32, vp, u32, vp, vp]
+        _lib.orc_brush.argtypes = [u64, vp, vp, u32, u32, vp, vp]
+        _lib.orc_select_keys.argtypes = [u64, vp, u32, vp, vp]
+        _lib.orc_select_keys.restype = None
         _lib.orc_alpha_grad.argtypes = [u64, u32, vp, vp, u32, u32, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp, vp]
         for f in (_lib.orc_keys, _lib.orc_order, _lib.orc_update, _lib.orc_alpha_grad):
             f.restype = ctypes.c_int
@@ -192,3 +197,26 @@ def rasterize(values: np.ndarray, height: int, bar_field: int = 0):
     if rc:
         raise OracleError(f"orc_rasterize failed ({rc})")
     return lines, bars
+
+
+def brush(b1: np.ndarray, b2: np.ndarray, p0: int, p1: int):
+    """(first, last) cell of the pixel ROI [p0, p1] in curve order, or None."""
+    b1 = np.ascontiguousarray(b1, np.uint32)
+    b2 = np.ascontiguousarray(b2, np.uint32)
+    f = np.zeros(1, np.uint64)
+    l = np.zeros(1, np.uint64)
+    rc = _L().orc_brush(b1.size, _p(b1), _p(b2), p0, p1, _p(f), _p(l))
+    if rc == 1:
+        return None
+    if rc:
+        raise OracleError(f"orc_brush failed ({rc})")
+    return int(f[0]), int(l[0])
+
+
+def select_keys(keys: np.ndarray, ranges) -> np.ndarray:
+    """uint8 mask of the cells whose key lies in one of the inclusive ranges."""
+    k = np.ascontiguousarray(keys, np.uint64)
+    r = np.ascontiguousarray(np.asarray(ranges, np.uint64).reshape(-1))
+    mask = np.zeros(k.size, np.uint8)
+    _L().orc_select_keys(k.size, _p(k), r.size // 2, _p(r), _p(mask))
+    return mask

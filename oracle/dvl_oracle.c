@@ -527,3 +527,32 @@ int orc_rasterize(uint32_t M, uint32_t W, uint32_t H, const float* values, uint3
         }
     return 0;
 }
+
+/* ---- brushing and linking (see dvl_oracle.h) ------------------------------- */
+
+int orc_brush(uint64_t n, const uint32_t* b1, const uint32_t* b2, uint32_t p0, uint32_t p1, uint64_t* first,
+              uint64_t* last)
+{
+    if (!b1 || !b2 || !first || !last || p0 > p1) return -1;
+    uint64_t cnt = 0, f = 0, l = 0;
+    for (uint64_t c = 0; c < n; ++c)
+        if (b1[c] <= p1 && b2[c] >= p0) {
+            if (cnt == 0) f = c;
+            l = c;
+            ++cnt;
+        }
+    if (cnt == 0) return 1;
+    *first = f;
+    *last = l;
+    return cnt == l - f + 1 ? 0 : -2;
+}
+
+void orc_select_keys(uint64_t n, const uint64_t* keys, uint32_t R, const uint64_t* ranges, uint8_t* mask)
+{
+    for (uint64_t c = 0; c < n; ++c) {
+        uint8_t sel = 0;
+        for (uint32_t r = 0; r < R; ++r)
+            if (keys[c] >= ranges[2 * r] && keys[c] <= ranges[2 * r + 1]) sel = 1;
+        mask[c] = sel;
+    }
+}

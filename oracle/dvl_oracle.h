@@ -98,6 +98,20 @@ int orc_alpha_grad(uint64_t n, uint32_t M, const float* fields, const uint8_t* l
 int orc_rasterize(uint32_t M, uint32_t W, uint32_t H, const float* values, uint32_t bar_field,
                   uint8_t* lines, uint8_t* bars);
 
+/* Brushing and linking (Sec. 3.5).  The cells of a pixel ROI [p0, p1] of the
+ * plot are those whose span touches a pixel of it: b1[c] <= p1 and b2[c] >= p0
+ * (b1, b2 from orc_update, cells in curve order).  Writes the first and last
+ * such cell; returns 0, 1 if there is none, -1 for invalid arguments, -2 if
+ * the set is not one contiguous run of the curve order (the mapping of Sec.
+ * 3.2 is monotone, so this does not happen). */
+int orc_brush(uint64_t n, const uint32_t* b1, const uint32_t* b2, uint32_t p0, uint32_t p1, uint64_t* first,
+              uint64_t* last);
+
+/* The linked selection in the 3D view (Sec. 3.5): a cell is selected when its
+ * centroid's curve key lies in one of R inclusive key ranges (ranges[2r],
+ * ranges[2r+1]); mask[c] = 1 for selected cells, in the order of `keys`. */
+void orc_select_keys(uint64_t n, const uint64_t* keys, uint32_t R, const uint64_t* ranges, uint8_t* mask);
+
 #ifdef __cplusplus
 }
 #endif
