@@ -274,6 +274,27 @@ enum { DVL_PLOT_MEAN = 0, DVL_PLOT_Y = 1 };
 int dvl_rasterize(dvl_ctx* ctx, uint32_t height, uint32_t value_kind, uint32_t bar_field, uint8_t* lines,
                   uint8_t* bars, int mem_kind);
 
+/* Brushing and linking (Sec. 3.5).  A pixel ROI [p0, p1] (inclusive, < W) of
+ * the last dvl_update's plot selects the cells whose span touches one of its
+ * pixels: one run [first, last] of the curve order (n_cells = 0 when empty),
+ * with its first and last curve keys, the compact ROI the 3D view tests cells
+ * against.  mask (optional, n_cells bytes, host or device per mem_kind):
+ * 1 for the selected cells, 0 otherwise, in the order the cells were loaded.
+ * Needs the last update to have run with want_alpha = 0 (DVL_ERR_STATE
+ * otherwise).  Synchronises the stream. */
+typedef struct dvl_roi {
+    uint64_t first, last, n_cells;        /* curve-order indices, inclusive */
+    uint64_t key_first, key_last;         /* their curve keys */
+} dvl_roi;
+int dvl_brush(dvl_ctx* ctx, uint32_t p0, uint32_t p1, dvl_roi* out, uint8_t* mask, int mem_kind);
+
+/* The linked selection in the 3D view: mask[c] = 1 (input order) when cell
+ * c's curve key lies in one of R inclusive key ranges (host array ranges[2r],
+ * ranges[2r+1]; R <= DVL_MAX_SELECT_RANGES).  mask holds n_cells bytes, host
+ * or device per mem_kind. */
+enum { DVL_MAX_SELECT_RANGES = 1024 };
+int dvl_select_keys(dvl_ctx* ctx, const uint64_t* ranges, uint32_t R, uint8_t* mask, int mem_kind);
+
 /* Batched update: K transfer functions, each with any number of viewport
  * widths, over the loaded data set (paper Sec. 3.3-3.4 per (TF, width) pair;
  * the batching itself is not in the paper -- it serves many clients editing

@@ -34,7 +34,7 @@ EXPORTS = ["dvl_create", "dvl_destroy", "dvl_load_amr", "dvl_build_order", "dvl_
            "dvl_set_tf", "dvl_update", "dvl_read_bins", "dvl_get_stats", "dvl_read_order",
            "dvl_read_widths", "dvl_sync", "dvl_set_option", "dvl_get_timings", "dvl_update_noalloc", "dvl_set_tf_ctrl", "dvl_read_alpha_means", "dvl_backward",
            "dvl_update_batch", "dvl_read_batch_bins", "dvl_read_batch_all", "dvl_batch_config",
-           "dvl_read_batch_all_async", "dvl_stream", "dvl_rasterize",
+           "dvl_read_batch_all_async", "dvl_stream", "dvl_rasterize", "dvl_brush", "dvl_select_keys",
            "dvl_status_string", "dvl_last_error",
            "dvl_server_create", "dvl_server_destroy", "dvl_server_add_dataset", "dvl_server_warmup",
            "dvl_server_submit", "dvl_server_wait", "dvl_server_get_stats", "dvl_server_reset_stats",
@@ -51,6 +51,11 @@ class dvl_bins(ctypes.Structure):
     _fields_ = [("mean", ctypes.c_void_p), ("min", ctypes.c_void_p), ("max", ctypes.c_void_p),
                 ("y", ctypes.c_void_p), ("sum", ctypes.c_void_p), ("count", ctypes.c_void_p),
                 ("mem_kind", ctypes.c_int)]
+
+
+class dvl_roi(ctypes.Structure):
+    _fields_ = [("first", ctypes.c_uint64), ("last", ctypes.c_uint64), ("n_cells", ctypes.c_uint64),
+                ("key_first", ctypes.c_uint64), ("key_last", ctypes.c_uint64)]
 
 
 class dvl_server_config(ctypes.Structure):
@@ -105,6 +110,8 @@ def _load():
         "dvl_read_batch_all_async": ([vp, ctypes.POINTER(dvl_bins)], i32),
         "dvl_stream": ([vp], vp),
         "dvl_rasterize": ([vp, u32, u32, u32, vp, vp, i32], i32),
+        "dvl_brush": ([vp, u32, u32, ctypes.POINTER(dvl_roi), vp, i32], i32),
+        "dvl_select_keys": ([vp, vp, u32, vp, i32], i32),
         "dvl_server_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(dvl_server_config)], i32),
         "dvl_server_destroy": ([vp], None),
         "dvl_server_add_dataset": ([vp, u64, vp, vp, u32, vp, i32, ctypes.POINTER(u32)], i32),
@@ -295,6 +302,34 @@ class DVL:
         return lines, bars
 
     rasterize = dvl_rasterize
+
+    def dvl_brush(self, p0: int, p1: int, mask=None):
+        """Brushing a pixel ROI [p0, p1] of the last update's plot: the run of
+        selected cells in curve order and its key range; ``mask=True`` also
+        returns the per-cell selection (input order) as a numpy array, or pass
+        an n-byte array / CUDA tensor to fill."""
+        r = dvl_roi()
+        if mask is True:
+            mask = np.empty(self.n, np.uint8)
+        pm, km, keep = _ptr_kind(mask) if mask is not None else (None, MEM_HOST, None)
+        self._check(lib.dvl_brush(self._h, p0, p1, ctypes.byref(r), pm, km))
+        out = {k: getattr(r, k) for k, _ in r._fields_}
+        if mask is not None:
+            out["mask"] = mask
+        return out
+
+    brush = dvl_brush
+
+    def dvl_select_keys(self, ranges, mask=None):
+        """Per-cell (input order) selection by inclusive curve-key ranges."""
+        rr = np.ascontiguousarray(np.asarray(ranges, np.uint64).reshape(-1))
+        if mask is None:
+            mask = np.empty(self.n, np.uint8)
+        pm, km, keep = _ptr_kind(mask)
+        self._check(lib.dvl_select_keys(self._h, rr.ctypes.data, rr.size // 2, pm, km))
+        return mask
+
+    select_keys = dvl_select_keys
 
     @staticmethod
     def _bins_struct(W, out):

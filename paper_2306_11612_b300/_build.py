@@ -14,7 +14,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
           "-fmad=false", "-I", INCLUDE]
-SOURCES = ["dvl_api.cu", "sfc_sort.cu", "update.cu", "batch.cu", "bins.cu", "noalloc.cu", "serve.cu", "raster.cu"]
+SOURCES = ["dvl_api.cu", "sfc_sort.cu", "update.cu", "batch.cu", "bins.cu", "noalloc.cu", "serve.cu", "raster.cu", "select.cu"]
 
 
 def _deps():

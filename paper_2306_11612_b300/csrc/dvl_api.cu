@@ -93,6 +93,10 @@ struct dvl_ctx {
     uint32_t HS_cap = 0;
     uint8_t* d_img = nullptr;         // line-plot images for host outputs (2 x H x W)
     size_t img_cap = 0;
+    bool last_rq = false;             // the last update computed pixel bounds (range queries)
+    uint8_t* d_mask = nullptr;        // selection masks for host outputs
+    unsigned long long* d_ranges = nullptr;
+    size_t mask_cap = 0;
     // batched updates (K TFs x viewports)
     float* d_btf = nullptr;               // K x M x T
     float* d_bdom = nullptr;              // 2 x DVL_MAX_FIELDS
@@ -356,7 +360,7 @@ void dvl_destroy(dvl_ctx* c)
     dfree(c->d_sum); dfree(c->d_vmin); dfree(c->d_vmax); dfree(c->d_count);
     dfree(c->d_mean); dfree(c->d_y); dfree(c->d_asum); dfree(c->d_amean); dfree(c->d_ctrl);
     dfree(c->d_gtab); dfree(c->d_gin); dfree(c->d_gout); dfree(c->d_H); dfree(c->d_S);
-    dfree(c->d_psum); dfree(c->d_pmm); dfree(c->d_img);
+    dfree(c->d_psum); dfree(c->d_pmm); dfree(c->d_img); dfree(c->d_mask); dfree(c->d_ranges);
     for (auto& set : c->ev)
         for (auto e : set) cudaEventDestroy(e);
     free_batch(c);
@@ -713,6 +717,7 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
     c->W_last = p->width;
     c->last_prm = *p;
     c->last_alpha = p->want_alpha != 0;
+    c->last_rq = !p->want_alpha;
     c->have_update = true;
     return DVL_OK;
 }
@@ -748,6 +753,93 @@ int dvl_rasterize(dvl_ctx* c, uint32_t height, uint32_t value_kind, uint32_t bar
         if (bars) CK(cudaMemcpyAsync(bars, db, HW, cudaMemcpyDeviceToHost, c->stream), "copy bars");
         CK(cudaStreamSynchronize(c->stream), "synchronize");
         return take_device_error(c);
+    }
+    return DVL_OK;
+}
+
+static int mask_out(dvl_ctx* c, uint8_t* mask, int mem_kind, uint8_t** dev)
+{
+    *dev = mask;
+    if (mem_kind == DVL_MEM_HOST) {
+        if (c->n > c->mask_cap) {
+            CK(cudaStreamSynchronize(c->stream), "synchronize");
+            CK(dalloc(c->d_mask, c->n), "alloc mask");
+            c->mask_cap = c->n;
+        }
+        *dev = c->d_mask;
+    }
+    return DVL_OK;
+}
+
+int dvl_brush(dvl_ctx* c, uint32_t p0, uint32_t p1, dvl_roi* out, uint8_t* mask, int mem_kind)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (!out) return fail(c, DVL_ERR_ARG, "out is NULL");
+    if (!c->have_update || !c->last_rq) return fail(c, DVL_ERR_STATE, "needs a dvl_update with want_alpha = 0");
+    if (p0 > p1 || p1 >= c->W_last) return fail(c, DVL_ERR_ARG, "ROI must satisfy p0 <= p1 < W");
+    if (mask && mem_kind != DVL_MEM_HOST && mem_kind != DVL_MEM_DEVICE) return fail(c, DVL_ERR_ARG, "bad mem_kind");
+    cudaSetDevice(c->device);
+    int rc = take_device_error(c);
+    if (rc) return rc;
+    const uint32_t W = c->W_last;
+    uint64_t first = 0, end = c->n;                   // selected: [first, end)
+    unsigned long long h = 0;
+    uint8_t st = 0;
+    if (p0 > 0) {
+        CK(cudaMemcpyAsync(&h, c->d_H + p0, 8, cudaMemcpyDeviceToHost, c->stream), "copy bound");
+        CK(cudaMemcpyAsync(&st, c->d_S + p0, 1, cudaMemcpyDeviceToHost, c->stream), "copy bound");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        first = st ? h - 1 : h;
+    }
+    if (p1 + 1 < W) {
+        CK(cudaMemcpyAsync(&h, c->d_H + p1 + 1, 8, cudaMemcpyDeviceToHost, c->stream), "copy bound");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        end = h;
+    }
+    dvl_roi r{};
+    if (end > first) {
+        r.first = first;
+        r.last = end - 1;
+        r.n_cells = end - first;
+        unsigned long long k[2] = {0, 0};
+        CK(cudaMemcpyAsync(&k[0], c->d_keys + r.first, 8, cudaMemcpyDeviceToHost, c->stream), "copy key");
+        CK(cudaMemcpyAsync(&k[1], c->d_keys + r.last, 8, cudaMemcpyDeviceToHost, c->stream), "copy key");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        r.key_first = k[0];
+        r.key_last = k[1];
+    }
+    if (mask) {
+        uint8_t* dm = nullptr;
+        if ((rc = mask_out(c, mask, mem_kind, &dm)) != DVL_OK) return rc;
+        const uint64_t f = r.n_cells ? r.first : 1, l = r.n_cells ? r.last : 0;     // empty: l < f
+        CK(launch_roi_mask(c->stream, c->d_perm, c->n, f, l, dm), "mask kernel");
+        if (mem_kind == DVL_MEM_HOST) CK(cudaMemcpyAsync(mask, dm, c->n, cudaMemcpyDeviceToHost, c->stream), "copy mask");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+    }
+    *out = r;
+    return DVL_OK;
+}
+
+int dvl_select_keys(dvl_ctx* c, const uint64_t* ranges, uint32_t R, uint8_t* mask, int mem_kind)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (c->state < 2) return fail(c, DVL_ERR_STATE, "order not built");
+    if (!mask || (R && !ranges)) return fail(c, DVL_ERR_ARG, "NULL argument");
+    if (R > DVL_MAX_SELECT_RANGES) return fail(c, DVL_ERR_ARG, "at most %d ranges", DVL_MAX_SELECT_RANGES);
+    if (mem_kind != DVL_MEM_HOST && mem_kind != DVL_MEM_DEVICE) return fail(c, DVL_ERR_ARG, "bad mem_kind");
+    cudaSetDevice(c->device);
+    if (!c->d_ranges) CK(dalloc(c->d_ranges, 2 * DVL_MAX_SELECT_RANGES), "alloc ranges");
+    uint8_t* dm = nullptr;
+    int rc = mask_out(c, mask, mem_kind, &dm);
+    if (rc) return rc;
+    if (R) CK(cudaMemcpyAsync(c->d_ranges, ranges, 2 * R * sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream),
+              "copy ranges");
+    CK(launch_select_keys(c->stream, c->d_keys, c->d_perm, c->n, c->d_ranges, R, dm), "select kernel");
+    if (mem_kind == DVL_MEM_HOST) {
+        CK(cudaMemcpyAsync(mask, dm, c->n, cudaMemcpyDeviceToHost, c->stream), "copy mask");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
     }
     return DVL_OK;
 }

@@ -206,6 +206,13 @@ cudaError_t launch_widths(cudaStream_t s, const UpdateArgs& a, unsigned long lon
 cudaError_t launch_raster(cudaStream_t s, const float* values, uint32_t M, uint32_t W, uint32_t H,
                           uint32_t bar_field, uint8_t* lines, uint8_t* bars);
 
+// select.cu: brushing and linking masks over the cells in input order.
+constexpr uint32_t MAX_SELECT_RANGES = 1024;
+cudaError_t launch_roi_mask(cudaStream_t s, const uint32_t* perm, uint64_t n, uint64_t first, uint64_t last,
+                            uint8_t* mask);
+cudaError_t launch_select_keys(cudaStream_t s, const unsigned long long* keys, const uint32_t* perm, uint64_t n,
+                               const unsigned long long* ranges, uint32_t R, uint8_t* mask);
+
 // Opts a kernel in to `bytes` of dynamic shared memory.  Always set: the
 // 48 KB default covers static plus dynamic memory, and several kernels have
 // static arrays of their own.
