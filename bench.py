@@ -68,10 +68,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline budget (rank 0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", choices=["plain", "batch", "serve", "sweep"], default="plain",
+    ap.add_argument("--mode", choices=["plain", "batch", "serve", "sweep", "vmax"], default="plain",
                     help="plain: one TF edit per step (default); batch: K TFs x 4 viewports per step; "
                          "serve: Poisson TF-edit requests over 8 resident data sets; "
-                         "sweep: ms/edit over the P x minimum-importance grid of the paper's Fig. 4")
+                         "sweep: ms/edit over the P x minimum-importance grid of the paper's Fig. 4; "
+                         "vmax: exact vs approximated max V over 107 random TFs (Fig. 6)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean request arrival rate (1/s)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="length of the request stream (s)")
     ap.add_argument("--batch-tfs", type=int, default=64)
@@ -807,6 +808,67 @@ def run_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# vmax mode: exact max V over the cells vs the Eq. 5/6 approximation (Fig. 6)
+# ---------------------------------------------------------------------------
+
+VMAX_TFS = 107
+
+
+def run_vmax(args):
+    import numpy as np
+    import torch
+    import paper_2306_11612_b300 as dvl
+    import synth
+    torch.cuda.set_device(0)
+    cfg = "paper" if args.config == "large" else args.config
+    amr = synth.make(cfg, pinned=True)
+    stream = torch.cuda.Stream(0)
+    ctx = dvl.DVL(0, stream)
+    ctx.load_amr(amr.lower, amr.level, amr.fields)
+    ctx.build_order(dvl.SFC_HILBERT)
+    W = 1024
+    tfs = tf_sequence(VMAX_TFS, seed0=5000)
+    rows, t = [], {0: 0.0, 1: 0.0}
+    for i, tf in enumerate(tfs):
+        ctx.set_tfs(tf)
+        row = {}
+        for mode in (0, 1):
+            ctx.update(P=args.P, min_importance=args.min_importance, width=W, vmax_mode=mode)   # warm
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.update(P=args.P, min_importance=args.min_importance, width=W, vmax_mode=mode)
+            b.record(stream)
+            b.synchronize()
+            t[mode] += a.elapsed_time(b)
+            st = ctx.get_stats()
+            row["approx" if mode == 0 else "exact"] = float(st["vmax"])
+            row["Q_" + ("approx" if mode == 0 else "exact")] = st["Q"]
+            if mode == 0:
+                cnt0 = ctx.read_bins(0)["count"].astype(np.float64)
+            else:
+                cnt1 = ctx.read_bins(0)["count"].astype(np.float64)
+        row["count_l1"] = float(np.abs(cnt0 - cnt1).sum() / max(cnt1.sum(), 1.0))
+        rows.append(row)
+    ctx.close()
+    ex = np.array([r["exact"] for r in rows])
+    ap = np.array([r["approx"] for r in rows])
+    rel = (ap - ex) / np.where(ex > 0, ex, 1.0)
+    line = {"metric": "max V: Eq. 5/6 approximation vs exact maximum over cells (107 random TFs)",
+            "value": float(np.median(rel)), "unit": "median relative difference (approx - exact) / exact",
+            "n_gpus": 1, "steps": VMAX_TFS, "warmup": 1, "ms_per_step": (t[0] + t[1]) / VMAX_TFS,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{cfg}: {amr.n} cells, 4 fp32 fields, W={W}, {VMAX_TFS} random 8-point TFs",
+                       "P": args.P, "min_importance": args.min_importance},
+            "summary": {"approx_ge_exact": int((ap >= ex).sum()), "approx_lt_exact": int((ap < ex).sum()),
+                        "rel_diff_min": float(rel.min()), "rel_diff_max": float(rel.max()),
+                        "rel_diff_mean": float(rel.mean()),
+                        "bin_count_l1_mean": float(np.mean([r["count_l1"] for r in rows])),
+                        "ms_per_edit_approx": t[0] / VMAX_TFS, "ms_per_edit_exact": t[1] / VMAX_TFS},
+            "per_tf": rows, "roofline": None, "e2e": None, "gpu_launches": 2 * 2 * 4 * VMAX_TFS}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -817,6 +879,8 @@ def main():
         run_serve(args)
     elif args.mode == "sweep":
         run_sweep(args)
+    elif args.mode == "vmax":
+        run_vmax(args)
     else:
         run_ours(args)
 
