@@ -357,6 +357,24 @@ def run_ours(args):
     r1.record(stream)
     r1.synchronize()
     raster_ms = r0.elapsed_time(r1) / 20
+    # brushing and linking on the last edit: a pixel ROI -> cell run, key range
+    # and per-cell mask (input order); then the key-range test of every cell
+    mask = torch.empty(amr.n, dtype=torch.uint8, device=f"cuda:{local}")
+    roi = ctx.brush(args.width // 4, args.width // 2, mask=mask)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(5):
+        roi = ctx.brush(args.width // 4, args.width // 2, mask=mask)
+    brush_ms = (time.perf_counter() - t0) / 5 * 1e3
+    ranges = [(roi["key_first"], roi["key_last"]), (0, roi["key_first"] // 2)]
+    ctx.select_keys(ranges, mask=mask)
+    r0.record(stream)
+    for i in range(5):
+        ctx.select_keys(ranges, mask=mask)
+    r1.record(stream)
+    r1.synchronize()
+    select_ms = r0.elapsed_time(r1) / 5
+    del mask
     ms = max_over_ranks(ms, world)
     value = job_throughput(amr.n * args.steps, world, ms * 1e-3)
 
@@ -406,7 +424,8 @@ def run_ours(args):
             "kernels": dict(kern, prepare_ms=stages["prepare"], finalize_ms=stages["finalize"],
                             edit_bytes_per_cell=edit_bytes / amr.n, edit_gbs=step_gbs, edit_frac=step_gbs / peak,
                             first_update_ms_with_value_tables=t_first,
-                            rasterize_ms=raster_ms, rasterize_image=f"{RASTER_H} x {args.width}, 4 polylines + bars"),
+                            rasterize_ms=raster_ms, rasterize_image=f"{RASTER_H} x {args.width}, 4 polylines + bars",
+                            brush_ms=brush_ms, brush_cells=roi["n_cells"], select_keys_ms=select_ms),
             "per_edit": edit_pct,
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": LAUNCHES_PER_UPDATE * args.steps,
             "setup_s": {"generate": t_gen, "load": t_load, "build_order": t_build}}
