@@ -19,6 +19,8 @@ Parity status per function (see the tests that pin each one):
 * ``rasterize``  -- pinned: a hand-worked golden image and the properties that
                     define the drawing (contiguous columns through the value's
                     row, 8-connected segments, bar heights).
+* ``widths``     -- pinned: equal to ``update``'s per-cell widths for every
+                    cell of a data set, given that data set's global quantities.
 * ``brush``, ``select_keys`` -- pinned: the exact-rational brute force's bins
                     give the same selections; hand-built key ranges.
 """
@@ -79,6 +81,7 @@ def _L():
         _lib.orc_update.argtypes = [u64, u32, vp, vp, u32, vp, vp, vp, ctypes.POINTER(Params)] + [vp] * 10 + [ctypes.POINTER(Stats)]
         _lib.orc_rasterize.argtypes = [u32, u32, u32, vp, u32, vp, vp]
         _lib.orc_brush.argtypes = [u64, vp, vp, u32, u32, vp, vp]
+        _lib.orc_widths.argtypes = [u64, u32, vp, vp, u32, u32, vp, ctypes.POINTER(Params), u64, vp, vp, vp, vp, vp]
         _lib.orc_select_keys.argtypes = [u64, vp, u32, vp, vp]
         _lib.orc_select_keys.restype = None
         _lib.orc_alpha_grad.argtypes = [u64, u32, vp, vp, u32, u32, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp, vp]
@@ -220,3 +223,25 @@ def select_keys(keys: np.ndarray, ranges) -> np.ndarray:
     mask = np.zeros(k.size, np.uint8)
     _L().orc_select_keys(k.size, _p(k), r.size // 2, _p(r), _p(mask))
     return mask
+
+
+def widths(n_total: int, dmin, dmax, max_level: int, alpha: np.ndarray, values: np.ndarray, level: np.ndarray,
+           **kw):
+    """Widths of sampled cells (values (M, k), level (k,)) of a data set of
+    n_total cells with the given per-field data range and deepest level.
+    Returns (q, Q, vmax)."""
+    v = np.ascontiguousarray(values, np.float32)
+    lv = np.ascontiguousarray(level, np.uint8)
+    a = np.ascontiguousarray(alpha, np.float32)
+    M, k = v.shape
+    lo = np.ascontiguousarray(dmin, np.float32)
+    hi = np.ascontiguousarray(dmax, np.float32)
+    q = np.empty(k, np.uint64)
+    Q = np.zeros(1, np.int32)
+    vm = np.zeros(1, np.float32)
+    p = params(**kw)
+    rc = _L().orc_widths(n_total, M, _p(lo), _p(hi), max_level, a.shape[1], _p(a), ctypes.byref(p), k, _p(v),
+                         _p(lv), _p(q), _p(Q), _p(vm))
+    if rc:
+        raise OracleError(f"orc_widths failed ({rc})")
+    return q, int(Q[0]), float(vm[0])

@@ -202,6 +202,31 @@ static int bitlen64(uint64_t x)
 /* One DVL update                                                            */
 /* ------------------------------------------------------------------------- */
 
+/* Fixed-point widths.  Every width is f <= f_upper (each operation of Eq. 3 is
+ * monotone for non-negative arguments and V <= 1), so with f_upper <= 2^e the
+ * widths q = rint(f * 2^Q) are at most 2^(Q+e).  Q + e is capped at 31 (every
+ * width fits in 32 bits) and at 62 - nb for n < 2^nb cells (the total stays
+ * below 2^62): the prefix sum of Eq. 4 is then exact integer arithmetic and
+ * does not depend on summation order.  Returns -5 when not representable. */
+static int fixed_point(float Vmax, float inv_vmax, int max_level, uint64_t n, const orc_params* prm,
+                       float* f_upper_out, int* Q_out)
+{
+    float f_upper = importance(1.0f, inv_vmax, max_level, prm);
+    if (Vmax == 0.0f) f_upper = importance(0.0f, 0.0f, max_level, prm);
+    if (!isfinite(f_upper)) return -5;
+    int ex = 0;
+    frexpf(f_upper, &ex);                     /* f_upper <= 2^ex */
+    if (!pow_is_exact(prm->P)) ex += 1;       /* powf is not monotone to the ulp */
+    int cap = 62 - bitlen64(n);
+    if (cap > 31) cap = 31;
+    int Q = cap - ex;
+    if (Q > 120) Q = 120;
+    if (Q < -120) return -5;
+    *f_upper_out = f_upper;
+    *Q_out = Q;
+    return 0;
+}
+
 int orc_update(uint64_t n, uint32_t M, const float* fields, const uint8_t* level,
                uint32_t T, const float* alpha, const float* dom_lo, const float* dom_hi,
                const orc_params* prm, double* sum, float* vmin, float* vmax, float* mean,
@@ -269,26 +294,12 @@ int orc_update(uint64_t n, uint32_t M, const float* fields, const uint8_t* level
     }
     float inv_vmax = Vmax > 0.0f ? 1.0f / Vmax : 0.0f;
 
-    /* Fixed-point widths.  Every width is f <= f_upper (each operation above is
-     * monotone for non-negative arguments and V <= 1), so with f_upper <= 2^e
-     * the widths q = rint(f * 2^Q) are at most 2^(Q+e).  Q + e is capped at 31
-     * (every width fits in 32 bits) and at 62 - nb for n < 2^nb cells (the
-     * total stays below 2^62): the prefix sum of Eq. 4 is then exact integer
-     * arithmetic and does not depend on summation order. */
     int max_level = 0;
     for (uint64_t c = 0; c < n; ++c)
         if (level[c] > max_level) max_level = level[c];
-    float f_upper = importance(1.0f, inv_vmax, max_level, prm);
-    if (Vmax == 0.0f) f_upper = importance(0.0f, 0.0f, max_level, prm);
-    if (!isfinite(f_upper)) return -5;
-    int ex = 0;
-    frexpf(f_upper, &ex);                     /* f_upper <= 2^ex */
-    if (!pow_is_exact(prm->P)) ex += 1;       /* powf is not monotone to the ulp */
-    int cap = 62 - bitlen64(n);
-    if (cap > 31) cap = 31;
-    int Q = cap - ex;
-    if (Q > 120) Q = 120;
-    if (Q < -120) return -5;
+    float f_upper = 0.0f;
+    int Q = 0;
+    if (fixed_point(Vmax, inv_vmax, max_level, n, prm, &f_upper, &Q)) return -5;
     float scale = pow2f_int(Q);
 
     uint64_t* q = q_out ? q_out : (uint64_t*)malloc(sizeof(uint64_t) * (n ? n : 1));
@@ -555,4 +566,55 @@ void orc_select_keys(uint64_t n, const uint64_t* keys, uint32_t R, const uint64_
             if (keys[c] >= ranges[2 * r] && keys[c] <= ranges[2 * r + 1]) sel = 1;
         mask[c] = sel;
     }
+}
+
+/* ---- widths of sampled cells (see dvl_oracle.h) ------------------------------ */
+
+int orc_widths(uint64_t n_total, uint32_t M, const float* dmin, const float* dmax, uint32_t max_level, uint32_t T,
+               const float* alpha, const orc_params* prm, uint64_t k, const float* values, const uint8_t* level,
+               uint64_t* q, int32_t* Q_out, float* vmax_out)
+{
+    if (M < 1 || M > 16 || T < 2 || prm->vmax_mode != ORC_VMAX_APPROX) return -1;
+    float lo[16], s[16];
+    for (uint32_t m = 0; m < M; ++m) {                 /* default domain: the data range */
+        lo[m] = dmin[m];
+        s[m] = norm_scale(dmin[m], dmax[m]);
+    }
+    int gi = (int)T - 1, gj = 0;                        /* Eq. 5 */
+    for (uint32_t m = 0; m < M; ++m) {
+        int im = (int)tf_entry(normalise(dmin[m], lo[m], s[m]), T);
+        int jm = (int)tf_entry(normalise(dmax[m], lo[m], s[m]), T);
+        if (im < gi) gi = im;
+        if (jm > gj) gj = jm;
+    }
+    if (gi > gj) { gi = 0; gj = 0; }
+    float Vmax = 0.0f;                                  /* Eq. 6 */
+    for (int a = gi; a <= gj; ++a) {
+        float hi = alpha[a], lw = alpha[a];
+        for (uint32_t m = 1; m < M; ++m) {
+            float x = alpha[(uint64_t)m * T + a];
+            if (x > hi) hi = x;
+            if (x < lw) lw = x;
+        }
+        if (hi - lw > Vmax) Vmax = hi - lw;
+    }
+    float inv_vmax = Vmax > 0.0f ? 1.0f / Vmax : 0.0f;
+    float f_upper = 0.0f;
+    int Q = 0;
+    if (fixed_point(Vmax, inv_vmax, (int)max_level, n_total, prm, &f_upper, &Q)) return -5;
+    float scale = pow2f_int(Q);
+    for (uint64_t c = 0; c < k; ++c) {
+        float hi = 0.0f, lw = 1.0f;
+        for (uint32_t m = 0; m < M; ++m) {
+            float t = normalise(values[(uint64_t)m * k + c], lo[m], s[m]);
+            float al = alpha[(uint64_t)m * T + tf_entry(t, T)];
+            if (al > hi) hi = al;
+            if (al < lw) lw = al;
+        }
+        float f = importance(hi - lw, inv_vmax, level[c], prm);
+        q[c] = (uint64_t)nearbyintf(f * scale);
+    }
+    if (Q_out) *Q_out = Q;
+    if (vmax_out) *vmax_out = Vmax;
+    return 0;
 }

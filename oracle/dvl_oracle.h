@@ -84,6 +84,16 @@ int orc_alpha_grad(uint64_t n, uint32_t M, const float* fields, const uint8_t* l
                    const float* dom_hi, const orc_params* prm, const double* target,
                    double* abar, double* grad, double* loss);
 
+/* Fixed-point widths of k sampled cells of a data set of n_total cells, one
+ * by one, from the data set's global quantities (per-field data minimum and
+ * maximum, deepest level) with the default TF domains and the Eq. 5/6 max V:
+ * the same q as orc_update gives those cells in the whole data set (unless
+ * every width of the data set is 0).  values[m*k + c], level[c]; writes q[k],
+ * Q and max V.  Returns 0, -1 (arguments; exact max V is not supported) or -5. */
+int orc_widths(uint64_t n_total, uint32_t M, const float* dmin, const float* dmax, uint32_t max_level, uint32_t T,
+               const float* alpha, const orc_params* prm, uint64_t k, const float* values, const uint8_t* level,
+               uint64_t* q, int32_t* Q_out, float* vmax_out);
+
 /* Line-plot rasterisation of the bins (the RasterizeLines step after the
  * update, Sec. 4, Fig. 1): an H x W image, row 0 at the top, column p = bin p.
  * values[m*W + p] in [0, 1] (the bin means or their alpha) maps to the row

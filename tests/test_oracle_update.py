@@ -232,3 +232,22 @@ def test_user_domain_clamps():
     # one cell per pixel: min = max = the clamped normalised value
     assert r["min"][0].tolist() == [0.0, 0.0, 0.5, 1.0, 1.0]
     assert r["y"][0].tolist() == [alpha[0, 0], alpha[0, 0], alpha[0, 2], alpha[0, 3], alpha[0, 3]]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_widths_of_sampled_cells_equal_update(seed):
+    # the one-by-one widths (for full-size sampled checks) equal the widths the
+    # whole-data-set update assigns, given the data set's range and deepest level
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(50, 3000))
+    M = int(rng.integers(1, 5))
+    fields = rng.lognormal(0, 1.5, (M, n)).astype(np.float32)
+    level = rng.integers(0, 6, n).astype(np.uint8)
+    alpha = rng.uniform(0, 1, (M, 256)).astype(np.float32)
+    kw = dict(P=float(rng.choice([1.0, 2.0, 0.5])), min_importance=0.025)
+    r = oracle.update(fields, level, alpha, per_cell=True, width=64, **kw)
+    pick = rng.choice(n, min(n, 200), replace=False)
+    q, Q, vmax = oracle.widths(n, fields.min(1), fields.max(1), int(level.max()), alpha, fields[:, pick],
+                               level[pick], **kw)
+    assert Q == r["stats"]["Q"] and np.float32(vmax) == np.float32(r["stats"]["vmax"])
+    assert np.array_equal(q, r["q"][pick])
