@@ -1,0 +1,95 @@
+"""Parity at the full benchmark size (GPU).
+
+The 413,554,163-cell "large" data set in the configuration bench.py times
+(Hilbert order, W = 4096, P = 1, minimum importance 0.025, the benchmark's
+first TF).  The oracle cannot run the whole update in seconds, so:
+
+* order: the permutation is one (every cell appears once), keys strictly
+  increase, and 1M sampled keys equal the oracle's keys of their input cells;
+* widths: 1M sampled cells' fixed-point widths equal the oracle's, computed one
+  by one from the data set's global quantities (data range and deepest level,
+  taken from the input arrays); Q and max V equal the oracle's; F equals the
+  sum of all widths;
+* bins: properties that hold at any size (no empty pixel when F > 0, counts
+  cover every cell, min <= mean <= max within [0, 1], y is the TF at the mean's
+  entry), and agreement with the library's independent placement path (the
+  second pass over the cells used for alpha means): counts, min and max bit
+  for bit, sums to 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+dvl = pytest.importorskip("paper_2306_11612_b300")
+
+W, P, MI, T = 4096, 1.0, 0.025, 256
+
+
+@pytest.fixture(scope="module")
+def full():
+    amr = synth.make("large")
+    tf = synth.random_tfs(1000)                  # bench.py's first TF set
+    ctx = dvl.DVL(0)
+    ctx.load_amr(amr.lower, amr.level, amr.fields)
+    ctx.build_order(dvl.SFC_HILBERT)
+    ctx.set_tfs(tf)
+    ctx.update(P=P, min_importance=MI, width=W)
+    keys, perm = ctx.read_order()
+    yield amr, ctx, tf, keys, perm
+    ctx.close()
+
+
+def test_order_at_full_size(full):
+    amr, ctx, tf, keys, perm = full
+    n = amr.n
+    assert keys.size == n == perm.size
+    seen = np.zeros(n, bool)
+    seen[perm] = True
+    assert seen.all(), "perm is a permutation"
+    assert np.all(keys[1:] > keys[:-1]), "keys strictly increase (non-overlapping cells)"
+    rng = np.random.default_rng(11)
+    k = np.sort(rng.choice(n, 1_000_000, replace=False))
+    c = perm[k]
+    ok = oracle.keys(np.ascontiguousarray(amr.lower[:, c]), np.ascontiguousarray(amr.level[c]), oracle.SFC_HILBERT)
+    assert np.array_equal(ok, keys[k])
+
+
+def test_widths_at_full_size(full):
+    amr, ctx, tf, keys, perm = full
+    q = ctx.read_widths()
+    st = ctx.get_stats()
+    assert st["F"] == int(q.sum(dtype=np.uint64)) and not st["linear"]
+    rng = np.random.default_rng(12)
+    k = rng.choice(amr.n, 1_000_000, replace=False)
+    c = perm[k]
+    qo, Q, vmax = oracle.widths(amr.n, amr.fields.min(1), amr.fields.max(1), int(amr.level.max()), tf,
+                                np.ascontiguousarray(amr.fields[:, c]), np.ascontiguousarray(amr.level[c]),
+                                P=P, min_importance=MI)
+    assert Q == st["Q"] and np.float32(vmax) == np.float32(st["vmax"])
+    assert np.array_equal(qo, q[k])
+
+
+def test_bins_at_full_size(full):
+    amr, ctx, tf, keys, perm = full
+    ctx.update(P=P, min_importance=MI, width=W)
+    rq = [ctx.read_bins(m) for m in range(4)]
+    cnt = rq[0]["count"].astype(np.int64)
+    assert np.all(cnt >= 1) and cnt.sum() >= amr.n
+    for m in range(4):
+        b = rq[m]
+        assert np.all((b["min"] >= 0) & (b["max"] <= 1) & (b["min"] <= b["max"]))
+        mean64 = b["sum"] / cnt
+        assert np.all(mean64 >= b["min"] * (1 - 1e-6)) and np.all(mean64 <= b["max"] * (1 + 1e-6) + 1e-30)
+        e = np.minimum(np.floor(b["mean"].astype(np.float32) * np.float32(T)).astype(np.int64), T - 1)
+        assert np.array_equal(b["y"], tf[m][e])
+    # the independent placement path (second pass over the cells)
+    ctx.update(P=P, min_importance=MI, width=W, want_alpha=1)
+    pl = [ctx.read_bins(m) for m in range(4)]
+    assert np.array_equal(pl[0]["count"], rq[0]["count"])
+    for m in range(4):
+        assert np.array_equal(pl[m]["min"].view(np.uint32), rq[m]["min"].view(np.uint32))
+        assert np.array_equal(pl[m]["max"].view(np.uint32), rq[m]["max"].view(np.uint32))
+        assert np.all(np.abs(pl[m]["sum"] - rq[m]["sum"]) <= 1e-5 * np.abs(rq[m]["sum"]) + 1e-30)
