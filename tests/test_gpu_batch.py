@@ -185,3 +185,34 @@ def test_batch_empty_dataset():
         assert np.all(b["count"] == 0) and np.all(b["sum"] == 0) and np.all(b["y"] == 0)
     finally:
         ctx.close()
+
+
+def test_batch_at_benchmark_size():
+    # the batched workload bench.py times: 50.6M cells, 64 TFs x W in {512,
+    # 1024, 2048, 4096}; sampled pairs equal plain updates bit for bit (the
+    # plain path is checked against the oracle at full size)
+    amr = synth.make("batched")
+    K = 64
+    alphas = np.stack([synth.random_tfs(k * 100_003, n_entries=256) for k in range(K)])
+    widths = (512, 1024, 2048, 4096)
+    pairs = [(k, w) for k in range(K) for w in widths]
+    ctx = _ctx(amr.lower, amr.level, amr.fields)
+    try:
+        ctx.update_batch(alphas, pairs)
+        allb = ctx.read_batch_all()
+        offs, o = [], 0
+        for _, w in pairs:
+            offs.append(o)
+            o += 4 * w
+        rng = np.random.default_rng(3)
+        for q in sorted(rng.choice(len(pairs), 6, replace=False)):
+            k, w = pairs[q]
+            ctx.set_tfs(alphas[k])
+            ctx.update(width=w)
+            for m in range(4):
+                b = ctx.read_bins(m)
+                sl = slice(offs[q] + m * w, offs[q] + (m + 1) * w)
+                for key in ("mean", "min", "max", "y", "sum"):
+                    assert np.array_equal(allb[key][sl].view(np.uint8), b[key].view(np.uint8)), (q, m, key)
+    finally:
+        ctx.close()
