@@ -86,12 +86,10 @@ __global__ void k_consts(UpdateArgs a) { finish_consts(a.consts, a, a.meta->max_
 
 // Sum of the fixed-point widths of one lane's 4 cells at idx.
 template <int M, int PM, bool FULLSTEP, bool P2>
-__device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, const UpdateArgs& a,
-                                                      const float* s_tf, const uint32_t* cm, uint64_t idx)
+__device__ __forceinline__ unsigned long long widths4_of(const Cell<M, PM>& cc, const UpdateArgs& a,
+                                                         const float* s_tf, const uint32_t* cm, uint64_t idx,
+                                                         const float (&v)[4][M], uint32_t L4)
 {
-    float v[4][M];
-    uint32_t L4;
-    load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
     unsigned long long acc = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -109,6 +107,16 @@ __device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, con
     return acc;
 }
 
+template <int M, int PM, bool FULLSTEP, bool P2>
+__device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, const UpdateArgs& a,
+                                                      const float* s_tf, const uint32_t* cm, uint64_t idx)
+{
+    float v[4][M];
+    uint32_t L4;
+    load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
+    return widths4_of<M, PM, FULLSTEP, P2>(cc, a, s_tf, cm, idx, v, L4);
+}
+
 // P2: the table size is a power of two (fast TF entries, see width_p2)
 template <int M, int PM, bool P2>
 __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_tiles)
@@ -118,10 +126,20 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
     __shared__ unsigned long long s_lane[WARPS][STEPS][32];   // per-lane step sums
     __shared__ uint32_t s_tile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // The tile comes from a ticket (the look-back needs tickets in the order
+    // CTAs start), so it is known only after the barrier.  The first step's
+    // cell loads are issued right after it, ahead of the per-thread constants,
+    // so that their latency overlaps the CTA's set-up.
     load_table<M>(s_tf, a.tf, a.T);
     if (tid == 0) s_tile = atomicAdd(&a.counters[0], 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
+    const uint64_t chunk = (uint64_t)tile * WARPS + warp;
+    const uint64_t base = chunk * CHUNK;
+    const bool full = base + CHUNK <= a.n;
+    float v0[4][M];
+    uint32_t L0 = 0;
+    if (full) load4<M>(a.val, a.pitch, a.lev, base + lane * 4, v0, L0);
     Cell<M, PM> cc;
     cc.load(a.consts, a.T);
     uint32_t cm[M];
@@ -129,12 +147,15 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
 #pragma unroll
     for (int m = 0; m < M; ++m) cm[m] = sb + 4u * (uint32_t)(m * (a.T + 1)) - 4u * BITS_2P23;
 
-    const uint64_t chunk = (uint64_t)tile * WARPS + warp;
-    const uint64_t base = chunk * CHUNK;
     unsigned long long acc = 0;
-    if (base + CHUNK <= a.n) {
+    if (full) {
+        {
+            const unsigned long long l = widths4_of<M, PM, true, P2>(cc, a, s_tf, cm, base + lane * 4, v0, L0);
+            s_lane[warp][0][lane] = l;
+            acc += l;
+        }
 #pragma unroll 2
-        for (int st = 0; st < STEPS; ++st) {
+        for (int st = 1; st < STEPS; ++st) {
             const unsigned long long l = widths4<M, PM, true, P2>(cc, a, s_tf, cm, base + st * STEP + lane * 4);
             s_lane[warp][st][lane] = l;
             acc += l;
