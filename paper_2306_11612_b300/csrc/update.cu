@@ -128,8 +128,16 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // The tile comes from a ticket (the look-back needs tickets in the order
     // CTAs start), so it is known only after the barrier.  The first step's
-    // cell loads are issued right after it, ahead of the per-thread constants,
-    // so that their latency overlaps the CTA's set-up.
+    // cell loads are issued before it for the tile a CTA usually gets (its
+    // block index) and redone after it if the ticket differs, so that their
+    // latency overlaps the table load and the CTA's set-up.
+    const uint32_t guess = blockIdx.x;
+    float v0[4][M];
+    uint32_t L0 = 0;
+    {
+        const uint64_t gb = ((uint64_t)guess * WARPS + warp) * CHUNK;
+        if (gb + CHUNK <= a.n) load4<M>(a.val, a.pitch, a.lev, gb + lane * 4, v0, L0);
+    }
     load_table<M>(s_tf, a.tf, a.T);
     if (tid == 0) s_tile = atomicAdd(&a.counters[0], 1u);
     __syncthreads();
@@ -137,9 +145,7 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
     const uint64_t chunk = (uint64_t)tile * WARPS + warp;
     const uint64_t base = chunk * CHUNK;
     const bool full = base + CHUNK <= a.n;
-    float v0[4][M];
-    uint32_t L0 = 0;
-    if (full) load4<M>(a.val, a.pitch, a.lev, base + lane * 4, v0, L0);
+    if (full && tile != guess) load4<M>(a.val, a.pitch, a.lev, base + lane * 4, v0, L0);
     Cell<M, PM> cc;
     cc.load(a.consts, a.T);
     uint32_t cm[M];
