@@ -27,25 +27,30 @@ __global__ void k_prepare_batch(UpdateArgs a, BatchArgs b)
     prepare_consts_block(ak);
 }
 
-// Persistent pass A for K transfer functions that share the TF domains: a
-// warp step's cells are loaded and normalised once per group of G TFs whose
-// tables sit in shared memory; per TF it writes step totals and, per tile,
-// runs its own decoupled look-back scan.  G is a compile-time constant so the
-// TF loop unrolls; per cell the table offsets (all fields) and the level
+// Pass A for one group of G transfer functions (TFs g0 .. g0+G-1 of the
+// batch; all TFs share the TF domains): persistent CTAs load the group's alpha
+// tables into shared memory once, then take tiles from the group's ticket
+// counter; every warp step's cells are loaded and normalised once and
+// evaluated for all G TFs; per TF it writes step totals and, per tile, runs
+// its own decoupled look-back scan.  The batch launches one such kernel per
+// group (the cells are read once per group).  G is a compile-time constant so
+// the TF loop unrolls; per cell the table offsets (all fields) and the level
 // factor 2^(L w) are computed once and reused by every TF of the group.
 template <int M, int PM, int G, int ST>
-__global__ __launch_bounds__(WARPS * 32) void k_passA_batch(UpdateArgs a, BatchArgs b)
+__global__ __launch_bounds__(WARPS * 32) void k_passA_batch(UpdateArgs a, BatchArgs b, uint32_t g0)
 {
     extern __shared__ float4 s_dyn[];                  // G x 1 params, then G x M x T1 tables
-    __shared__ unsigned long long s_ct[WARPS][MAX_BATCH_TF];
+    __shared__ unsigned long long s_ct[WARPS][G];      // chunk totals per warp and TF
     __shared__ uint32_t s_tile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // table stride per field: ST (a compile-time constant >= T + 1, so that
     // the unrolled TF loop addresses its tables with immediate offsets), or
     // T + 1 when ST = 0
     const uint32_t T = a.T, T1 = ST ? (uint32_t)ST : T + 1, K = b.K, MT1 = M * T1;
+    const uint32_t gk = K - g0 < (uint32_t)G ? K - g0 : (uint32_t)G;
     float4* s_par = s_dyn;                             // inv_vmax, mb, ma, qscale per TF
     float* s_tf = reinterpret_cast<float*>(s_dyn + G);
+    uint32_t* ticket = b.tickets + g0 / G;
     const UpdateConsts* C0 = b.consts;
     float lo[M], sc[M];
 #pragma unroll
@@ -53,139 +58,132 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA_batch(UpdateArgs a, BatchA
     const float Tf = (float)T, P = C0->P;
     const int n2 = C0->pow_n2, wshift = C0->width_shift;
 
+    for (uint32_t i = tid; i < gk * MT1; i += blockDim.x) {
+        const uint32_t kk = i / MT1, r = i - kk * MT1, m = r / T1, e = r - m * T1;
+        s_tf[i] = b.tfs[((uint64_t)(g0 + kk) * M + m) * T + (e < T ? e : T - 1)];
+    }
+    for (uint32_t kk = tid; kk < G; kk += blockDim.x) {
+        float4 pr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (kk < gk) {
+            const UpdateConsts* Ck = b.consts + g0 + kk;
+            const bool after = Ck->min_imp_mode == DVL_MINIMP_AFTER_POWER;
+            pr = make_float4(Ck->inv_vmax, after ? 0.0f : Ck->min_imp, after ? Ck->min_imp : 0.0f, Ck->qscale);
+        }
+        s_par[kk] = pr;
+    }
+
     while (true) {
-        if (tid == 0) s_tile = atomicAdd(&a.counters[0], 1u);
-        __syncthreads();
+        if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+        __syncthreads();                               // tables ready; ticket visible
         const uint32_t tile = s_tile;
         if (tile >= b.n_tiles) break;                  // block-uniform
-        for (uint32_t k = lane; k < K; k += 32) s_ct[warp][k] = 0ull;
+        if (lane < G) s_ct[warp][lane] = 0ull;
         const uint64_t chunk = (uint64_t)tile * WARPS + warp;
         const uint64_t base = chunk * CHUNK;
-        for (uint32_t g0 = 0; g0 < K; g0 += G) {
-            const uint32_t gk = K - g0 < G ? K - g0 : G;
-            __syncthreads();                           // the previous group's tables are free
-            for (uint32_t i = tid; i < gk * MT1; i += blockDim.x) {
-                const uint32_t kk = i / MT1, r = i - kk * MT1, m = r / T1, e = r - m * T1;
-                s_tf[i] = b.tfs[((uint64_t)(g0 + kk) * M + m) * T + (e < T ? e : T - 1)];
-            }
-            for (uint32_t kk = tid; kk < G; kk += blockDim.x) {
-                float4 pr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                if (kk < gk) {
-                    const UpdateConsts* Ck = b.consts + g0 + kk;
-                    const bool after = Ck->min_imp_mode == DVL_MINIMP_AFTER_POWER;
-                    pr = make_float4(Ck->inv_vmax, after ? 0.0f : Ck->min_imp, after ? Ck->min_imp : 0.0f,
-                                     Ck->qscale);
+        __syncwarp();
+        for (int st = 0; st < STEPS; ++st) {
+            if (base + (uint64_t)st * STEP >= a.n) break;            // warp-uniform
+            const uint64_t idx = base + st * STEP + lane * 4;
+            uint32_t off[4][M];
+            float lvl[4];
+            bool valid[4];
+            if (idx < a.n) {
+                float v[4][M];
+                uint32_t L4;
+                load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                    for (int m = 0; m < M; ++m)
+                        off[j][m] = m * T1 + floor_small(__fmul_rn(norm_t(v[j][m], lo[m], sc[m]), Tf));
+                    lvl[j] = exp2i((int)((L4 >> (8 * j)) & 0xFF) * wshift);
                 }
-                s_par[kk] = pr;
-            }
-            __syncthreads();
-            if (base >= a.n) continue;
-            for (int st = 0; st < STEPS; ++st) {
-                if (base + (uint64_t)st * STEP >= a.n) break;            // warp-uniform
-                const uint64_t idx = base + st * STEP + lane * 4;
-                uint32_t off[4][M];
-                float lvl[4];
-                bool valid[4];
-                if (idx < a.n) {
-                    float v[4][M];
-                    uint32_t L4;
-                    load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
+            } else {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < 4; ++j) {
 #pragma unroll
-                        for (int m = 0; m < M; ++m)
-                            off[j][m] = m * T1 + floor_small(__fmul_rn(norm_t(v[j][m], lo[m], sc[m]), Tf));
-                        lvl[j] = exp2i((int)((L4 >> (8 * j)) & 0xFF) * wshift);
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-#pragma unroll
-                        for (int m = 0; m < M; ++m) off[j][m] = 0;
-                        lvl[j] = 0.0f;
-                    }
+                    for (int m = 0; m < M; ++m) off[j][m] = 0;
+                    lvl[j] = 0.0f;
                 }
+            }
 #pragma unroll
-                for (int j = 0; j < 4; ++j) valid[j] = idx + j < a.n;
+            for (int j = 0; j < 4; ++j) valid[j] = idx + j < a.n;
 #pragma unroll
-                for (int kk = 0; kk < G; ++kk) {
-                    if (kk >= (int)gk) break;                              // block-uniform
-                    const float* tk = s_tf + kk * MT1;
-                    const float4 pr = s_par[kk];
-                    unsigned long long l = 0;
+            for (int kk = 0; kk < G; ++kk) {
+                if (kk >= (int)gk) break;                              // block-uniform
+                const float* tk = s_tf + kk * MT1;
+                const float4 pr = s_par[kk];
+                unsigned long long l = 0;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        float al[M];
+                for (int j = 0; j < 4; ++j) {
+                    float al[M];
 #pragma unroll
-                        for (int m = 0; m < M; ++m) al[m] = tk[off[j][m]];
-                        // Eq. 3 as importance<PM>, with the level factor precomputed
-                        const float r = fmaxf(__fmul_rn(spread<M>(al), pr.x), pr.y);
-                        const float x = __fmul_rn(r, lvl[j]);
-                        const float f = fmaxf(PM == POW_ONE ? x : pow_gen(x, n2, P), pr.z);
-                        const uint32_t q = __float2uint_rn(__fmul_rn(f, pr.w));
-                        l += valid[j] ? q : 0u;
-                    }
-                    const unsigned long long tot = warp_total_small(l);
-                    if (lane == 0) {
-                        b.step_sums[((uint64_t)(g0 + kk) * b.n_chunks + chunk) * STEPS + st] = tot;
-                        s_ct[warp][g0 + kk] += tot;
-                    }
+                    for (int m = 0; m < M; ++m) al[m] = tk[off[j][m]];
+                    // Eq. 3 as importance<PM>, with the level factor precomputed
+                    const float r = fmaxf(__fmul_rn(spread<M>(al), pr.x), pr.y);
+                    const float x = __fmul_rn(r, lvl[j]);
+                    const float f = fmaxf(PM == POW_ONE ? x : pow_gen(x, n2, P), pr.z);
+                    const uint32_t q = __float2uint_rn(__fmul_rn(f, pr.w));
+                    l += valid[j] ? q : 0u;
+                }
+                const unsigned long long tot = warp_total_small(l);
+                if (lane == 0) {
+                    b.step_sums[((uint64_t)(g0 + kk) * b.n_chunks + chunk) * STEPS + st] = tot;
+                    s_ct[warp][kk] += tot;
                 }
             }
         }
         __syncthreads();
-        {
-            // one look-back per TF; the warps take the TFs in turn
-            for (uint32_t k = warp; k < K; k += WARPS) {
-                unsigned long long w = lane < WARPS ? s_ct[lane][k] : 0ull;
-                unsigned long long incl = warp_incl_scan_u64(w, lane);
-                const unsigned long long agg = __shfl_sync(FULL, incl, WARPS - 1);
-                unsigned long long* status = b.tile_status + (uint64_t)k * b.n_tiles;
-                if (lane == 0) st_relaxed(status + tile, (tile == 0 ? FLAG_P : FLAG_A) | agg);
-                unsigned long long excl = 0;
-                if (tile > 0) {
-                    int64_t end = (int64_t)tile - 1;
-                    while (true) {
-                        const int64_t jt = end - lane;
-                        unsigned long long sv = FLAG_P;
-                        if (jt >= 0) {
-                            long long spins = 0;
-                            while (true) {
-                                sv = ld_relaxed(status + jt);
-                                if (sv >> 62) break;
-                                if (++spins > a.spin_limit) {
-                                    atomicOr(a.err, ERR_TIMEOUT);
-                                    sv = FLAG_P;
-                                    break;
-                                }
-                                __nanosleep(100);
+        // one look-back per TF of the group; the warps take the TFs in turn
+        for (uint32_t kk = warp; kk < gk; kk += WARPS) {
+            const uint32_t k = g0 + kk;
+            unsigned long long w = lane < WARPS ? s_ct[lane][kk] : 0ull;
+            unsigned long long incl = warp_incl_scan_u64(w, lane);
+            const unsigned long long agg = __shfl_sync(FULL, incl, WARPS - 1);
+            unsigned long long* status = b.tile_status + (uint64_t)k * b.n_tiles;
+            if (lane == 0) st_relaxed(status + tile, (tile == 0 ? FLAG_P : FLAG_A) | agg);
+            unsigned long long excl = 0;
+            if (tile > 0) {
+                int64_t end = (int64_t)tile - 1;
+                while (true) {
+                    const int64_t jt = end - lane;
+                    unsigned long long sv = FLAG_P;
+                    if (jt >= 0) {
+                        long long spins = 0;
+                        while (true) {
+                            sv = ld_relaxed(status + jt);
+                            if (sv >> 62) break;
+                            if (++spins > a.spin_limit) {
+                                atomicOr(a.err, ERR_TIMEOUT);
+                                sv = FLAG_P;
+                                break;
                             }
+                            __nanosleep(100);
                         }
-                        const unsigned pmask = __ballot_sync(FULL, (sv & FLAG_P) != 0);
-                        const int first = pmask ? __ffs(pmask) - 1 : 31;
-                        excl += warp_sum_u64(lane <= first ? (sv & VAL_MASK) : 0ull);
-                        if (pmask) break;
-                        end -= 32;
                     }
-                    if (lane == 0) st_relaxed(status + tile, FLAG_P | (excl + agg));
+                    const unsigned pmask = __ballot_sync(FULL, (sv & FLAG_P) != 0);
+                    const int first = pmask ? __ffs(pmask) - 1 : 31;
+                    excl += warp_sum_u64(lane <= first ? (sv & VAL_MASK) : 0ull);
+                    if (pmask) break;
+                    end -= 32;
                 }
-                if (lane < WARPS) b.chunk_prefix[(uint64_t)k * b.n_chunks + (uint64_t)tile * WARPS + lane] = excl + incl - w;
-                if (lane == 0 && tile == b.n_tiles - 1) {
-                    UpdateConsts* Ck = b.consts + k;
-                    unsigned long long F = excl + agg;
-                    int linear = 0;
-                    if (F == 0 && a.n > 0) { F = a.n; linear = 1; }
-                    Ck->F = F;
-                    Ck->linear = linear;
-                    Ck->F_div_W = 0;
-                    Ck->F_mod_W = 0;
-                }
+                if (lane == 0) st_relaxed(status + tile, FLAG_P | (excl + agg));
+            }
+            if (lane < WARPS) b.chunk_prefix[(uint64_t)k * b.n_chunks + (uint64_t)tile * WARPS + lane] = excl + incl - w;
+            if (lane == 0 && tile == b.n_tiles - 1) {
+                UpdateConsts* Ck = b.consts + k;
+                unsigned long long F = excl + agg;
+                int linear = 0;
+                if (F == 0 && a.n > 0) { F = a.n; linear = 1; }
+                Ck->F = F;
+                Ck->linear = linear;
+                Ck->F_div_W = 0;
+                Ck->F_mod_W = 0;
             }
         }
-        __syncthreads();
+        __syncthreads();                               // s_ct and s_tile are reused
     }
 }
-
 
 }  // namespace
 
@@ -215,7 +213,9 @@ cudaError_t run_passA_batch_gs(cudaStream_t s, const UpdateArgs& a, const BatchA
     }
     uint64_t grid = (uint64_t)b.sm_count * b.resid;
     if (grid > b.n_tiles) grid = b.n_tiles;
-    if (grid) k_passA_batch<M, PM, G, ST><<<(unsigned)grid, WARPS * 32, smem, s>>>(a, b);
+    if (grid)
+        for (uint32_t g0 = 0; g0 < b.K; g0 += G)      // one launch per group of G TFs
+            k_passA_batch<M, PM, G, ST><<<(unsigned)grid, WARPS * 32, smem, s>>>(a, b, g0);
     return cudaGetLastError();
 }
 
@@ -253,7 +253,7 @@ cudaError_t occupancy_passA_batch_gs(const UpdateArgs& a, int* blocks)
 {
     const size_t smem = passA_batch_smem(M, a.T, G);
     *blocks = 0;
-    if (smem + sizeof(unsigned long long) * WARPS * MAX_BATCH_TF + 16 > 227 * 1024) return cudaSuccess;
+    if (smem + sizeof(unsigned long long) * WARPS * G + 16 > 227 * 1024) return cudaSuccess;
     cudaError_t e = smem_attr(k_passA_batch<M, PM, G, ST>, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_passA_batch<M, PM, G, ST>, WARPS * 32, smem);

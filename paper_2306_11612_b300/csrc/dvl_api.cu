@@ -101,6 +101,7 @@ struct dvl_ctx {
     float* d_btf = nullptr;               // K x M x T
     float* d_bdom = nullptr;              // 2 x DVL_MAX_FIELDS
     UpdateConsts* d_bconsts = nullptr;    // K
+    uint32_t* d_btickets = nullptr;       // K (one per TF group, at most K groups)
     unsigned long long *d_btile = nullptr, *d_bprefix = nullptr, *d_bsteps = nullptr;
     PairDesc* d_pairs = nullptr;
     double* d_bsum = nullptr;
@@ -182,7 +183,7 @@ size_t pad_to(uint64_t n, size_t q) { return (size_t)((n + q - 1) / q * q); }
 
 void free_batch(dvl_ctx* c)
 {
-    dfree(c->d_btf); dfree(c->d_bdom); dfree(c->d_bconsts); dfree(c->d_btile); dfree(c->d_bprefix);
+    dfree(c->d_btf); dfree(c->d_bdom); dfree(c->d_bconsts); dfree(c->d_btickets); dfree(c->d_btile); dfree(c->d_bprefix);
     dfree(c->d_bsteps); dfree(c->d_pairs); dfree(c->d_bsum); dfree(c->d_bvmin); dfree(c->d_bvmax);
     dfree(c->d_bcount); dfree(c->d_bmean); dfree(c->d_by); dfree(c->d_bH); dfree(c->d_bS);
     dfree(c->d_bpsum); dfree(c->d_bpmm);
@@ -216,6 +217,7 @@ cudaError_t enqueue_batch(dvl_ctx* c, const UpdateArgs& a, const BatchArgs& b, c
     cudaError_t e;
     if (ev) cudaEventRecord(ev[0], s);
     if ((e = cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_btickets, 0, (size_t)b.K * sizeof(uint32_t), s)) != cudaSuccess) return e;
     if (b.n_tiles &&
         (e = cudaMemsetAsync(c->d_btile, 0, (size_t)b.K * b.n_tiles * sizeof(unsigned long long), s)) != cudaSuccess)
         return e;
@@ -1088,6 +1090,7 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
         CK(grow(c->d_btf, c->btf_cap, nTF), "alloc batch TFs");
         if (K > c->bk_cap) {
             CK(dalloc(c->d_bconsts, K), "alloc batch");
+            CK(dalloc(c->d_btickets, K), "alloc batch");
             CK(dalloc(c->d_btile, (size_t)K * n_tiles), "alloc batch scan state");
             CK(dalloc(c->d_bprefix, (size_t)K * n_chunks), "alloc batch scan state");
             CK(dalloc(c->d_bsteps, (size_t)K * n_chunks * STEPS), "alloc batch scan state");
@@ -1140,6 +1143,7 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
     b.K = K;
     b.tfs = c->d_btf;
     b.consts = c->d_bconsts;
+    b.tickets = c->d_btickets;
     b.tile_status = c->d_btile;
     b.chunk_prefix = c->d_bprefix;
     b.step_sums = c->d_bsteps;
@@ -1244,7 +1248,7 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
                                     prm.min_imp_mode, prm.width_mode,
                                     (uint64_t)c->d_val, (uint64_t)c->d_lev, (uint64_t)c->d_meta, (uint64_t)c->d_err,
                                     (uint64_t)c->d_counters, (uint64_t)c->d_btf, (uint64_t)c->d_bdom,
-                                    (uint64_t)c->d_bconsts, (uint64_t)c->d_btile, (uint64_t)c->d_bprefix,
+                                    (uint64_t)c->d_bconsts, (uint64_t)c->d_btickets, (uint64_t)c->d_btile, (uint64_t)c->d_bprefix,
                                     (uint64_t)c->d_bsteps, (uint64_t)c->d_pairs, (uint64_t)c->d_bsum,
                                     (uint64_t)c->d_bvmin, (uint64_t)c->d_bvmax, (uint64_t)c->d_bmean,
                                     (uint64_t)c->d_by, (uint64_t)c->d_bcount, (uint64_t)c->d_bH, (uint64_t)c->d_bS,

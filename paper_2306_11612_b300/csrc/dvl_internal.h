@@ -178,6 +178,7 @@ struct BatchArgs {
     uint8_t* S;
     ulonglong2* psum;          // 2 x M per pixel bound (offset hs_off * 2 * M)
     float2* pmm;
+    uint32_t* tickets;         // tile ticket per TF group (ceil(K / G), zeroed per batch)
     int resid;                 // pass A CTAs per SM (persistent grid)
     int sm_count;
 };
