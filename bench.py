@@ -68,11 +68,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline budget (rank 0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", choices=["plain", "batch", "serve", "sweep", "vmax"], default="plain",
+    ap.add_argument("--mode", choices=["plain", "batch", "serve", "sweep", "vmax", "diff"], default="plain",
                     help="plain: one TF edit per step (default); batch: K TFs x 4 viewports per step; "
                          "serve: Poisson TF-edit requests over 8 resident data sets; "
                          "sweep: ms/edit over the P x minimum-importance grid of the paper's Fig. 4; "
-                         "vmax: exact vs approximated max V over 107 random TFs (Fig. 6)")
+                         "vmax: exact vs approximated max V over 107 random TFs (Fig. 6); "
+                         "diff: forward alpha means + adjoint gradient step of TF tuning")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean request arrival rate (1/s)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="length of the request stream (s)")
     ap.add_argument("--batch-tfs", type=int, default=64)
@@ -888,6 +889,100 @@ def run_vmax(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# diff mode: one gradient step of automatic TF tuning (forward + adjoint)
+# ---------------------------------------------------------------------------
+
+DIFF_W, DIFF_K = 2048, 64
+# algorithmic bytes per cell: the width pass (17 B + scan) and the alpha-means
+# placement pass (17 B: fields, levels for the recomputed widths at pixel
+# crossings, alpha lookups in shared memory) forward; the adjoint reads the
+# cells once more (17 B) with the per-pixel gradients from L2
+DIFF_FWD_BYTES = 2 * 17 + SCAN_BYTES
+DIFF_BWD_BYTES = 17
+
+
+def run_diff(args):
+    import numpy as np
+    import torch
+    import paper_2306_11612_b300 as dvl
+    from paper_2306_11612_b300.diff import alpha_means
+    import synth
+    torch.cuda.set_device(0)
+    amr = synth.make("diff", pinned=True)
+    ctx = dvl.DVL(0, torch.cuda.current_stream())
+    ctx.load_amr(amr.lower, amr.level, amr.fields)
+    ctx.build_order(dvl.SFC_HILBERT)
+    rng = np.random.default_rng(4)
+    dev = torch.device("cuda:0")
+    ctrl = torch.tensor(rng.uniform(0, 1, (4, DIFF_K)), dtype=torch.float32, device=dev, requires_grad=True)
+    target = torch.tensor(rng.uniform(0, 1, (4, DIFF_W)), dtype=torch.float32, device=dev)
+    kw = dict(width=DIFF_W, P=args.P, min_importance=args.min_importance)
+
+    def step():
+        abar = alpha_means(ctx, ctrl, **kw)
+        loss = ((abar - target) ** 2).sum()
+        loss.backward()
+        with torch.no_grad():
+            ctrl -= 1e-3 * ctrl.grad
+            ctrl.clamp_(0.0, 1.0)
+            ctrl.grad = None
+        return loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        a.record()
+        for _ in range(args.steps):
+            loss = step()
+        b.record()
+        b.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    # the parts: forward update with alpha means, adjoint, and a plain update
+    c = ctrl.detach()
+    ctx.set_tf_ctrl(c, 256)
+    torch.cuda.synchronize()
+    parts = {}
+    for name, fn in [("forward_ms", lambda: ctx.update(want_alpha=1, **kw)),
+                     ("plain_update_ms", lambda: ctx.update(**kw))]:
+        fn()
+        a.record()
+        for _ in range(10):
+            fn()
+        b.record()
+        b.synchronize()
+        parts[name] = a.elapsed_time(b) / 10
+    ctx.update(want_alpha=1, **kw)
+    g = torch.ones((4, DIFF_W), dtype=torch.float32, device=dev)
+    gout = torch.empty((4, DIFF_K), dtype=torch.float32, device=dev)
+    ctx.backward(g, gout)
+    a.record()
+    for _ in range(10):
+        ctx.backward(g, gout)
+    b.record()
+    b.synchronize()
+    parts["adjoint_ms"] = a.elapsed_time(b) / 10
+    ctx.close()
+    peak, _ = measured_peak()
+    fwd_gbs = DIFF_FWD_BYTES * amr.n / (parts["forward_ms"] * 1e-3) / 1e9
+    bwd_gbs = DIFF_BWD_BYTES * amr.n / (parts["adjoint_ms"] * 1e-3) / 1e9
+    line = {"metric": "TF-tuning gradient step (forward alpha means + adjoint), cells/s", "value": amr.n / (ms * 1e-3),
+            "unit": "cells/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 gradient sums)",
+            "data": "synthetic",
+            "config": {"workload": f"diff: 4-level synthetic AMR, {amr.n} cells, 4 fp32 fields, {DIFF_K} control "
+                                   f"points per field ({4 * DIFF_K} parameters), W={DIFF_W}, L2 loss vs a seeded target",
+                       "step": "alpha_means forward, loss.backward (adjoint kernel), SGD update of the control points"},
+            "parts": parts, "final_loss": float(loss.item()),
+            "roofline": {"bound": "hbm", "kernel": "forward (width pass + alpha-means placement pass)",
+                         "achieved": fwd_gbs, "peak": peak, "unit": "GB/s", "frac": fwd_gbs / peak,
+                         "traffic": None, "adjoint_gbs": bwd_gbs, "adjoint_frac": bwd_gbs / peak},
+            "clocks": clk.summary(), "e2e": None, "gpu_launches": 8 * args.steps}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -900,6 +995,8 @@ def main():
         run_sweep(args)
     elif args.mode == "vmax":
         run_vmax(args)
+    elif args.mode == "diff":
+        run_diff(args)
     else:
         run_ours(args)
 
