@@ -910,7 +910,9 @@ def run_diff(args):
     import synth
     torch.cuda.set_device(0)
     amr = synth.make("diff", pinned=True)
-    ctx = dvl.DVL(0, torch.cuda.current_stream())
+    stream = torch.cuda.Stream(0)                     # the library and torch share it
+    torch.cuda.set_stream(stream)
+    ctx = dvl.DVL(0, stream)
     ctx.load_amr(amr.lower, amr.level, amr.fields)
     ctx.build_order(dvl.SFC_HILBERT)
     rng = np.random.default_rng(4)
@@ -934,10 +936,10 @@ def run_diff(args):
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
-        a.record()
+        a.record(stream)
         for _ in range(args.steps):
             loss = step()
-        b.record()
+        b.record(stream)
         b.synchronize()
     ms = a.elapsed_time(b) / args.steps
     # the parts: forward update with alpha means, adjoint, and a plain update
@@ -948,20 +950,20 @@ def run_diff(args):
     for name, fn in [("forward_ms", lambda: ctx.update(want_alpha=1, **kw)),
                      ("plain_update_ms", lambda: ctx.update(**kw))]:
         fn()
-        a.record()
+        a.record(stream)
         for _ in range(10):
             fn()
-        b.record()
+        b.record(stream)
         b.synchronize()
         parts[name] = a.elapsed_time(b) / 10
     ctx.update(want_alpha=1, **kw)
     g = torch.ones((4, DIFF_W), dtype=torch.float32, device=dev)
     gout = torch.empty((4, DIFF_K), dtype=torch.float32, device=dev)
     ctx.backward(g, gout)
-    a.record()
+    a.record(stream)
     for _ in range(10):
         ctx.backward(g, gout)
-    b.record()
+    b.record(stream)
     b.synchronize()
     parts["adjoint_ms"] = a.elapsed_time(b) / 10
     ctx.close()
