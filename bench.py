@@ -926,7 +926,7 @@ def run_diff(args):
         loss = ((abar - target) ** 2).sum()
         loss.backward()
         with torch.no_grad():
-            ctrl -= 1e-3 * ctrl.grad
+            ctrl.sub_(1e-3 * ctrl.grad)
             ctrl.clamp_(0.0, 1.0)
             ctrl.grad = None
         return loss
