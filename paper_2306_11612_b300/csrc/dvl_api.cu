@@ -75,6 +75,8 @@ struct dvl_ctx {
     float* d_amean = nullptr;
     uint32_t alpha_cap = 0;
     double* d_gtab = nullptr;         // adjoint scratch (M x T)
+    double* d_gpart = nullptr;        // per-CTA adjoint tables
+    size_t gpart_cap = 0;
     float* d_gin = nullptr;           // M x W
     float* d_gout = nullptr;          // M x K
     size_t gtab_cap = 0, gin_cap = 0, gout_cap = 0;
@@ -361,7 +363,7 @@ void dvl_destroy(dvl_ctx* c)
     dfree(c->d_hist); dfree(c->d_rs_counters); dfree(c->d_tf); dfree(c->d_dom);
     dfree(c->d_sum); dfree(c->d_vmin); dfree(c->d_vmax); dfree(c->d_count);
     dfree(c->d_mean); dfree(c->d_y); dfree(c->d_asum); dfree(c->d_amean); dfree(c->d_ctrl);
-    dfree(c->d_gtab); dfree(c->d_gin); dfree(c->d_gout); dfree(c->d_H); dfree(c->d_S);
+    dfree(c->d_gtab); dfree(c->d_gpart); dfree(c->d_gin); dfree(c->d_gout); dfree(c->d_H); dfree(c->d_S);
     dfree(c->d_psum); dfree(c->d_pmm); dfree(c->d_img); dfree(c->d_mask); dfree(c->d_ranges);
     for (auto& set : c->ev)
         for (auto e : set) cudaEventDestroy(e);
@@ -931,7 +933,13 @@ int dvl_backward(dvl_ctx* c, const float* grad, int mem_in, float* grad_ctrl, in
     CK(cudaMemsetAsync(c->d_gtab, 0, (size_t)M * T * sizeof(double), c->stream), "clear adjoint");
     UpdateArgs a = make_args(c, c->last_prm);
     float* out = mem_out == DVL_MEM_DEVICE ? grad_ctrl : c->d_gout;
-    CK(launch_backward(c->stream, a, g, c->d_gtab, K, out), "adjoint kernels");
+    const size_t np = backward_gpart_elems(M, T, c->n);
+    if (np > c->gpart_cap) {
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        CK(dalloc(c->d_gpart, np), "alloc adjoint");
+        c->gpart_cap = np;
+    }
+    CK(launch_backward(c->stream, a, g, c->d_gtab, K, out, np ? c->d_gpart : nullptr), "adjoint kernels");
     if (mem_out == DVL_MEM_HOST)
         CK(cudaMemcpyAsync(grad_ctrl, c->d_gout, (size_t)M * K * sizeof(float), cudaMemcpyDeviceToHost, c->stream),
            "copy gradient");

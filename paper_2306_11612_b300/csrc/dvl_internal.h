@@ -198,8 +198,11 @@ cudaError_t launch_ctrl_table(cudaStream_t s, uint32_t M, uint32_t K, uint32_t T
 // Adjoint of the alpha means of the last update: gtab (M x T, zeroed by the
 // caller) += per (cell, pixel) g[m][p] / count[p] at the cell's entry; then
 // grad_ctrl (M x K) = gtab through the interpolation weights.
+// gpart: scratch of backward_gpart_elems(M, T, n) doubles for the histogram
+// adjoint (deterministic, no global atomics), or null for the atomic one.
 cudaError_t launch_backward(cudaStream_t s, const UpdateArgs& a, const float* g, double* gtab, uint32_t K,
-                            float* grad_ctrl);
+                            float* grad_ctrl, double* gpart);
+size_t backward_gpart_elems(uint32_t M, uint32_t T, uint64_t n);   // 0: tables too large for it
 cudaError_t launch_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* q);
 
 // raster.cu: line-plot image of M x W bin values (lines: bit m per field,

@@ -743,6 +743,150 @@ __global__ __launch_bounds__(WARPS * 32) void k_backward(UpdateArgs a, const flo
     }
 }
 
+// Adjoint with per-warp entry histograms.  Inside a warp step that stays in
+// one pixel p every cell carries the same weight g[m][p] / count[p], so the
+// step only counts how often each TF entry occurs (u32 shared-memory atomics
+// in the warp's own histogram); when the warp's pixel changes, or its chunk
+// ends, the counts are scaled by the pixel's weights and added to the CTA's
+// float64 table.  Steps that cross a pixel boundary place their cells exactly
+// (back_crossing_step).  Each CTA writes its table to gpart[blockIdx] without
+// atomics; k_gtab_reduce sums the CTAs in a fixed order.
+template <int M, int PM>
+__global__ __launch_bounds__(WARPS * 32) void k_backward_hist(UpdateArgs a, const float* g, double* gpart)
+{
+    extern __shared__ float s_tf[];                    // table | float64 sums | WARPS u32 histograms
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int T1 = (int)a.T + 1, MT1 = M * T1;
+    load_table<M>(s_tf, a.tf, a.T);
+    double* sG = reinterpret_cast<double*>(s_tf + ((MT1 + 1) & ~1));
+    uint32_t* hist = reinterpret_cast<uint32_t*>(sG + MT1);
+    uint32_t* h = hist + warp * MT1;
+    for (int i = tid; i < MT1; i += blockDim.x) sG[i] = 0.0;
+    for (int i = tid; i < WARPS * MT1; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    const uint64_t chunk = (uint64_t)blockIdx.x * WARPS + warp;
+    const uint64_t base = chunk * CHUNK;
+    if (base < a.n) {
+        const UpdateConsts* C = a.consts;
+        const bool linear = C->linear != 0;
+        const PixelMap pm{C->F_div_W, C->F_mod_W, C->F, a.W};
+        const uint64_t rem = a.n - base;
+        const int full = rem >= (uint64_t)CHUNK ? STEPS : (int)(rem / STEP);
+        const int nsteps = rem >= (uint64_t)CHUNK ? STEPS : (int)((rem + STEP - 1) / STEP);
+        const unsigned long long pos0 = linear ? base : a.chunk_prefix[chunk];
+        unsigned long long ssum = 0;
+        if (lane < nsteps) {
+            const uint64_t left = a.n - (base + (uint64_t)lane * STEP);
+            ssum = linear ? (left < STEP ? left : STEP) : a.step_sums[chunk * STEPS + lane];
+        }
+        const unsigned long long s_end = pos0 + warp_incl_scan_u64(ssum, lane);
+        const unsigned long long s_start = s_end - ssum;
+        uint32_t pix = 0;
+        bool crossing = true;
+        if (lane < nsteps) {
+            pix = pm.first_pixel(s_start);
+            crossing = lane >= full || s_end >= pm.C(pix + 1);
+        }
+        const unsigned exact_mask = __ballot_sync(FULL, crossing) & ((1u << nsteps) - 1u);
+        float lo[M], sc[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) { lo[m] = C->lo[m]; sc[m] = C->s[m]; }
+        const float Tf = (float)a.T;
+        uint32_t cur = 0xFFFFFFFFu;
+        double wc[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) wc[m] = 0.0;
+        auto flush = [&]() {
+            if (cur == 0xFFFFFFFFu) return;                        // warp-uniform
+            __syncwarp();
+            for (int i = lane; i < MT1; i += 32) {
+                const uint32_t c = h[i];
+                if (c) {
+                    h[i] = 0u;
+                    const int m = i / T1;
+                    double w = 0.0;
+#pragma unroll
+                    for (int mm = 0; mm < M; ++mm)
+                        if (mm == m) w = wc[mm];
+                    atomicAdd(&sG[i], w * (double)c);
+                }
+            }
+            __syncwarp();
+        };
+        for (int st = 0; st < full; ++st) {
+            if (exact_mask & (1u << st)) continue;                      // warp-uniform
+            const uint32_t p = __shfl_sync(FULL, pix, st);
+            if (p != cur) {
+                flush();
+                cur = p;
+                const uint32_t c = a.count[p];
+#pragma unroll
+                for (int m = 0; m < M; ++m) wc[m] = c ? (double)g[(uint64_t)m * a.W + p] / (double)c : 0.0;
+            }
+            float4 x[M];
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                x[m] = __ldg(reinterpret_cast<const float4*>(a.val + m * a.pitch + base + st * STEP + lane * 4));
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    const float v = j == 0 ? x[m].x : j == 1 ? x[m].y : j == 2 ? x[m].z : x[m].w;
+                    const uint32_t e = floor_small(__fmul_rn(norm_t(v, lo[m], sc[m]), Tf));
+                    atomicAdd(&h[m * T1 + e], 1u);
+                }
+            }
+        }
+        flush();
+        unsigned m2 = exact_mask;
+        while (m2) {
+            const int k = __ffs(m2) - 1;
+            m2 &= m2 - 1;
+            back_crossing_step<M, PM>(a, s_tf, pm, base + k * STEP + lane * 4, __shfl_sync(FULL, s_start, k), lane,
+                                      g, sG, nullptr);
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < MT1; i += blockDim.x) gpart[(uint64_t)blockIdx.x * MT1 + i] = sG[i];
+}
+
+// Sums the CTAs' tables in two fixed-order levels: block (x, y) adds rows y,
+// y + gridDim.y, ... of 32 columns (one per lane; the warps take rows in turn
+// and are combined in warp order) into part2[y]; then k_gtab_final sums the
+// gridDim.y partial rows per entry, folding entry T into entry T-1.
+__global__ __launch_bounds__(256) void k_gtab_reduce(uint32_t MT1, uint64_t rows, const double* __restrict__ gpart,
+                                                     double* __restrict__ part2)
+{
+    __shared__ double s[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t col = blockIdx.x * 32 + lane;
+    double acc = 0.0;
+    if (col < MT1)
+        for (uint64_t r = blockIdx.y + (uint64_t)warp * gridDim.y; r < rows; r += 8ull * gridDim.y)
+            acc += gpart[r * MT1 + col];
+    s[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && col < MT1) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += s[w][lane];
+        part2[(uint64_t)blockIdx.y * MT1 + col] = t;
+    }
+}
+
+__global__ void k_gtab_final(uint32_t M, uint32_t T, uint32_t segs, const double* __restrict__ part2,
+                             double* __restrict__ gtab)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * T) return;
+    const uint32_t m = i / T, e = i - m * T, T1 = T + 1, col = m * T1 + e;
+    double s = 0.0;
+    for (uint32_t y = 0; y < segs; ++y) {
+        s += part2[(uint64_t)y * M * T1 + col];
+        if (e == T - 1) s += part2[(uint64_t)y * M * T1 + col + 1];    // entry T is t = 1: entry T-1
+    }
+    gtab[i] = s;
+}
+
 // dL/dctrl[m][k] = sum_e gtab[m][e] * (interpolation weight of k in entry e)
 __global__ void k_grad_ctrl(uint32_t M, uint32_t K, uint32_t T, const double* __restrict__ gtab,
                             float* __restrict__ grad)
@@ -848,15 +992,36 @@ cudaError_t run_update(cudaStream_t s, const UpdateArgs& a)
     return cudaGetLastError();
 }
 
+constexpr uint32_t GTAB_SEGS = 64;                // row segments of the first reduction level
+
+size_t backward_hist_smem(uint32_t M, uint32_t T)
+{
+    const size_t MT1 = (size_t)M * (T + 1);
+    return ((MT1 + 1) & ~(size_t)1) * sizeof(float) + MT1 * sizeof(double) + WARPS * MT1 * sizeof(uint32_t);
+}
+
 template <int M, int PM>
-cudaError_t run_backward_pm(cudaStream_t s, const UpdateArgs& a, const float* g, double* gtab)
+cudaError_t run_backward_pm(cudaStream_t s, const UpdateArgs& a, const float* g, double* gtab, double* gpart)
 {
     const uint32_t n_tiles = (uint32_t)((a.n + TILE - 1) / TILE);
+    cudaError_t e;
+    if (gpart) {
+        // histogram adjoint: per-CTA tables, then a fixed-order reduction
+        const size_t smem = backward_hist_smem(M, a.T);
+        if ((e = smem_attr(k_backward_hist<M, PM>, smem)) != cudaSuccess) return e;
+        if (!n_tiles) return cudaMemsetAsync(gtab, 0, (size_t)M * a.T * sizeof(double), s);
+        k_backward_hist<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a, g, gpart);
+        const uint32_t MT1 = M * (a.T + 1);
+        double* part2 = gpart + (uint64_t)n_tiles * MT1;
+        k_gtab_reduce<<<dim3((MT1 + 31) / 32, GTAB_SEGS), 256, 0, s>>>(MT1, n_tiles, gpart, part2);
+        k_gtab_final<<<(M * a.T + 255) / 256, 256, 0, s>>>(M, a.T, GTAB_SEGS, part2, gtab);
+        return cudaGetLastError();
+    }
     const size_t table = (size_t)((M * (a.T + 1) + 1) & ~1u) * sizeof(float);
     const size_t gbytes = (size_t)M * (a.T + 1) * sizeof(double);
     const int use_smem = table + gbytes <= 96 * 1024;
     const size_t smem = table + (use_smem ? gbytes : 0);
-    cudaError_t e = smem_attr(k_backward<M, PM>, smem);
+    e = smem_attr(k_backward<M, PM>, smem);
     if (e != cudaSuccess) return e;
     if (n_tiles) k_backward<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a, g, gtab, use_smem);
     return cudaGetLastError();
@@ -864,10 +1029,10 @@ cudaError_t run_backward_pm(cudaStream_t s, const UpdateArgs& a, const float* g,
 
 template <int M>
 cudaError_t run_backward(cudaStream_t s, const UpdateArgs& a, const float* g, double* gtab, uint32_t K,
-                         float* grad_ctrl)
+                         float* grad_ctrl, double* gpart)
 {
-    cudaError_t e = a.prm.P == 1.0f ? run_backward_pm<M, POW_ONE>(s, a, g, gtab)
-                                    : run_backward_pm<M, POW_GEN>(s, a, g, gtab);
+    cudaError_t e = a.prm.P == 1.0f ? run_backward_pm<M, POW_ONE>(s, a, g, gtab, gpart)
+                                    : run_backward_pm<M, POW_GEN>(s, a, g, gtab, gpart);
     if (e != cudaSuccess) return e;
     k_grad_ctrl<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(M, K, a.T, gtab, grad_ctrl);
     return cudaGetLastError();
@@ -895,9 +1060,16 @@ cudaError_t launch_ctrl_table(cudaStream_t s, uint32_t M, uint32_t K, uint32_t T
 }
 
 cudaError_t launch_backward(cudaStream_t s, const UpdateArgs& a, const float* g, double* gtab, uint32_t K,
-                            float* grad_ctrl)
+                            float* grad_ctrl, double* gpart)
 {
-    DVL_DISPATCH_M(run_backward, s, a, g, gtab, K, grad_ctrl)
+    DVL_DISPATCH_M(run_backward, s, a, g, gtab, K, grad_ctrl, gpart)
+}
+
+size_t backward_gpart_elems(uint32_t M, uint32_t T, uint64_t n)
+{
+    if (backward_hist_smem(M, T) > 200 * 1024) return 0;      // tables too large: atomic adjoint
+    const uint64_t n_tiles = (n + TILE - 1) / TILE;
+    return (size_t)(n_tiles + GTAB_SEGS) * M * (T + 1);
 }
 
 cudaError_t launch_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* q)
