@@ -194,7 +194,8 @@ int dvl_set_tf_ctrl(dvl_ctx* ctx, const float* ctrl, uint32_t K, uint32_t T, con
  * had want_alpha = 1): abar[m][p] = (1/count_p) sum over the cells covering
  * pixel p of A_m[entry_m(cell)] -- the differentiable counterpart of the bin
  * mean (the mean of the normalised value has zero gradient with respect to the
- * TF).  out: M x W floats (field-major), host or device.  Synchronises. */
+ * TF).  out: M x W floats (field-major), host or device.  Synchronises for a
+ * host destination; a device copy is ordered on the context's stream. */
 int dvl_read_alpha_means(dvl_ctx* ctx, float* out, int mem_kind);
 
 /* Adjoint of dvl_read_alpha_means with the cell-to-pixel assignment and the
@@ -205,7 +206,9 @@ int dvl_read_alpha_means(dvl_ctx* ctx, float* out, int mem_kind);
  * dvl_set_tf_ctrl.
  *   grad_abar   M x W floats, memory kind mem_in
  *   grad_ctrl   M x K floats (output), memory kind mem_out
- * Synchronises.  Errors: DVL_ERR_ARG, DVL_ERR_STATE. */
+ * Synchronises unless both buffers are device memory (then the work is
+ * ordered on the context's stream and device-side errors surface at the next
+ * synchronising call).  Errors: DVL_ERR_ARG, DVL_ERR_STATE. */
 int dvl_backward(dvl_ctx* ctx, const float* grad_abar, int mem_in, float* grad_ctrl, int mem_out);
 
 /* Copies the bins of one field of the last update into `out` (see dvl_bins).

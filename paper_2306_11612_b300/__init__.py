@@ -178,6 +178,13 @@ class DVL:
         if rc:
             raise DVLError(rc, lib.dvl_last_error(self._h).decode())
 
+    def torch_stream(self):
+        """The library's CUDA stream as a torch stream (for ordering torch work)."""
+        if getattr(self, "_tstream", None) is None:
+            import torch
+            self._tstream = torch.cuda.ExternalStream(lib.dvl_stream(self._h), device=self.device)
+        return self._tstream
+
     def close(self):
         if getattr(self, "_h", None):
             lib.dvl_destroy(self._h)

@@ -902,10 +902,13 @@ int dvl_read_alpha_means(dvl_ctx* c, float* out, int mem_kind)
     if (!c->have_update || !c->last_alpha) return fail(c, DVL_ERR_STATE, "last update had want_alpha = 0");
     if (mem_kind != DVL_MEM_HOST && mem_kind != DVL_MEM_DEVICE) return fail(c, DVL_ERR_ARG, "bad mem_kind");
     cudaSetDevice(c->device);
-    int rc = take_device_error(c);
-    if (rc) return rc;
+    if (mem_kind == DVL_MEM_HOST) {                   // device outputs stay asynchronous
+        int rc = take_device_error(c);
+        if (rc) return rc;
+    }
     const size_t MW = (size_t)c->M * c->W_last;
     CK(cudaMemcpyAsync(out, c->d_amean, MW * sizeof(float), kind_out(mem_kind), c->stream), "copy alpha means");
+    if (mem_kind == DVL_MEM_DEVICE) return DVL_OK;                              // stream-ordered
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     return DVL_OK;
 }
@@ -943,6 +946,7 @@ int dvl_backward(dvl_ctx* c, const float* grad, int mem_in, float* grad_ctrl, in
     if (mem_out == DVL_MEM_HOST)
         CK(cudaMemcpyAsync(grad_ctrl, c->d_gout, (size_t)M * K * sizeof(float), cudaMemcpyDeviceToHost, c->stream),
            "copy gradient");
+    if (mem_in == DVL_MEM_DEVICE && mem_out == DVL_MEM_DEVICE) return DVL_OK;   // stream-ordered, asynchronous
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     return take_device_error(c);
 }

@@ -20,12 +20,16 @@ class AlphaMeans(torch.autograd.Function):
         if not ctrl.is_cuda:
             raise ValueError("ctrl must be a CUDA tensor")
         ctrl = ctrl.detach().float().contiguous()
-        torch.cuda.current_stream().synchronize()     # ctrl is read on the library's stream
+        cur, lib_stream = torch.cuda.current_stream(), dvl.torch_stream()
+        lib_stream.wait_stream(cur)                   # ctrl is read on the library's stream
+        out = torch.empty((dvl.M, width), dtype=torch.float32, device=ctrl.device)
         dvl.set_tf_ctrl(ctrl, n_entries)
         dvl.update(P=P, min_importance=min_importance, width=width, min_imp_mode=min_imp_mode,
                    vmax_mode=vmax_mode, width_mode=width_mode, want_alpha=1)
-        out = torch.empty((dvl.M, width), dtype=torch.float32, device=ctrl.device)
-        dvl.read_alpha_means(out)
+        dvl.read_alpha_means(out)                     # device copy, ordered on the library's stream
+        cur.wait_stream(lib_stream)
+        ctrl.record_stream(lib_stream)
+        out.record_stream(lib_stream)
         ctx.dvl = dvl
         ctx.K = ctrl.shape[1]
         return out
@@ -33,9 +37,13 @@ class AlphaMeans(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         g = grad_out.detach().float().contiguous()
-        torch.cuda.current_stream().synchronize()
+        cur, lib_stream = torch.cuda.current_stream(), ctx.dvl.torch_stream()
+        lib_stream.wait_stream(cur)
         grad = torch.empty((ctx.dvl.M, ctx.K), dtype=torch.float32, device=g.device)
-        ctx.dvl.backward(g, grad)
+        ctx.dvl.backward(g, grad)                     # device in and out: asynchronous
+        cur.wait_stream(lib_stream)
+        g.record_stream(lib_stream)
+        grad.record_stream(lib_stream)
         return (None, grad) + (None,) * 7
 
 
