@@ -894,8 +894,12 @@ __global__ void k_grad_ctrl(uint32_t M, uint32_t K, uint32_t T, const double* __
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M * K) return;
     const uint32_t m = i / K, k = i % K;
+    // only entries with x = e (K-1)/(T-1) in [k-1, k+1] weigh on control point
+    // k; the range is widened by one entry on each side (the test below decides)
+    const uint64_t lo_num = k > 0 ? (uint64_t)(k - 1) * (T - 1) : 0, hi_num = (uint64_t)(k + 1) * (T - 1);
+    const uint64_t e_lo = lo_num / (K - 1), e_hi = hi_num / (K - 1) + 1;
     double acc = 0.0;
-    for (uint32_t e = 0; e < T; ++e) {
+    for (uint32_t e = e_lo > 0 ? (uint32_t)e_lo - 1 : 0; e < T && e <= e_hi; ++e) {
         const double x = (double)e * (double)(K - 1) / (double)(T - 1);
         uint32_t k0 = (uint32_t)floor(x);
         if (k0 > K - 2) k0 = K - 2;

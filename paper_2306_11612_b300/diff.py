@@ -27,9 +27,7 @@ class AlphaMeans(torch.autograd.Function):
         dvl.update(P=P, min_importance=min_importance, width=width, min_imp_mode=min_imp_mode,
                    vmax_mode=vmax_mode, width_mode=width_mode, want_alpha=1)
         dvl.read_alpha_means(out)                     # device copy, ordered on the library's stream
-        cur.wait_stream(lib_stream)
-        ctrl.record_stream(lib_stream)
-        out.record_stream(lib_stream)
+        cur.wait_stream(lib_stream)                   # later uses (and frees) of ctrl / out follow it
         ctx.dvl = dvl
         ctx.K = ctrl.shape[1]
         return out
@@ -42,8 +40,6 @@ class AlphaMeans(torch.autograd.Function):
         grad = torch.empty((ctx.dvl.M, ctx.K), dtype=torch.float32, device=g.device)
         ctx.dvl.backward(g, grad)                     # device in and out: asynchronous
         cur.wait_stream(lib_stream)
-        g.record_stream(lib_stream)
-        grad.record_stream(lib_stream)
         return (None, grad) + (None,) * 7
 
 
