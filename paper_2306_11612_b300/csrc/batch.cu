@@ -205,12 +205,9 @@ template <int M, int PM, int G, int ST>
 cudaError_t run_passA_batch_gs(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
 {
     const size_t smem = passA_batch_smem(M, a.T, G);
-    static size_t set_bytes = 0;                 // attribute set once per size (not during capture)
-    if (smem > set_bytes) {
-        cudaError_t e = smem_attr(k_passA_batch<M, PM, G, ST>, smem);
-        if (e != cudaSuccess) return e;
-        set_bytes = smem;
-    }
+    static std::atomic<size_t> set_bytes[MAX_DEVICES];
+    cudaError_t e = smem_attr_once(k_passA_batch<M, PM, G, ST>, smem, set_bytes);
+    if (e != cudaSuccess) return e;
     uint64_t grid = (uint64_t)b.sm_count * b.resid;
     if (grid > b.n_tiles) grid = b.n_tiles;
     if (grid)

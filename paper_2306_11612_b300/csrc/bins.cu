@@ -570,13 +570,9 @@ cudaError_t run_bins_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs&
 {
     if (a.n == 0 || b.n_pairs == 0) return cudaSuccess;
     const size_t smem = (size_t)M * (a.T + 1) * sizeof(float);
-    static size_t set_bytes = 0;                 // attribute set once per size (not during capture)
-    if (smem > set_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(k_bounds_batch<M, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        set_bytes = smem;
-    }
+    static std::atomic<size_t> set_bytes[MAX_DEVICES];
+    cudaError_t e = smem_attr_once(k_bounds_batch<M, PM>, smem, set_bytes);
+    if (e != cudaSuccess) return e;
     if (b.max_W > 1) k_bounds_batch<M, PM><<<dim3((b.max_W - 1 + 7) / 8, b.n_pairs), 256, smem, s>>>(a, b);
     k_pixels_batch<M><<<dim3((b.max_W + 255) / 256, b.n_pairs), 256, 0, s>>>(a, b, v);
     return cudaGetLastError();

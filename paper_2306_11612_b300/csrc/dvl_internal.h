@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/dvl.h"
 
 namespace dvl {
@@ -224,6 +226,24 @@ template <typename K>
 cudaError_t smem_attr(K kernel, size_t bytes)
 {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Sets a kernel's dynamic shared-memory limit once per device and size: the
+// batched launches are also recorded into CUDA graphs, where the call is
+// avoided by setting the limit on the first uncaptured launch.  `cache` holds
+// the largest size set so far per device (one cache per kernel).
+constexpr int MAX_DEVICES = 64;
+template <typename K>
+cudaError_t smem_attr_once(K kernel, size_t bytes, std::atomic<size_t> (&cache)[MAX_DEVICES])
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return smem_attr(kernel, bytes);
+    if (bytes <= cache[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+    e = smem_attr(kernel, bytes);
+    if (e == cudaSuccess) cache[dev].store(bytes, std::memory_order_relaxed);
+    return e;
 }
 
 // Dispatch on the field count of `a` to fn<1..8>(...).
