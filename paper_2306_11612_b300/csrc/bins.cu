@@ -417,9 +417,10 @@ __device__ __forceinline__ void pixels_one(const UpdateArgs& a, const QueryArgs&
                                            uint32_t p)
 {
     const bool has_l = p > 0, has_r = p + 1 < a.W;
-    const uint64_t Hn = has_r ? qa.H[p + 1] : a.n;                 // cells with E < C(p+1)
-    const uint64_t Hp = has_l ? qa.H[p] : 0;
-    const uint64_t lo_c = has_l ? (qa.S[p] ? Hp - 1 : Hp) : 0;
+    const uint64_t bl = (uint64_t)p * qa.hstride, br = (uint64_t)(p + 1) * qa.hstride;   // boundary entries
+    const uint64_t Hn = has_r ? qa.H[br] : a.n;                    // cells with E < C(p+1)
+    const uint64_t Hp = has_l ? qa.H[bl] : 0;
+    const uint64_t lo_c = has_l ? (qa.S[bl] ? Hp - 1 : Hp) : 0;
     const float Tf = (float)a.T;
     if (Hn == 0 || Hn - 1 < lo_c) {                                  // no cell touches p
 #pragma unroll
@@ -461,7 +462,7 @@ __device__ __forceinline__ void pixels_one(const UpdateArgs& a, const QueryArgs&
                 sum = pb - pa;
             }
             if (has_l) {
-                const uint64_t k = ((uint64_t)p * 2 + 1) * M + m;
+                const uint64_t k = (bl * 2 + 1) * M + m;
                 const ulonglong2 ps = qa.psum[k];
                 const float2 mm = qa.pmm[k];
                 sum += ((u128)ps.y << 64) | ps.x;
@@ -469,7 +470,7 @@ __device__ __forceinline__ void pixels_one(const UpdateArgs& a, const QueryArgs&
                 mx = fmaxf(mx, mm.y);
             }
             if (has_r) {
-                const uint64_t k = ((uint64_t)(p + 1) * 2 + 0) * M + m;
+                const uint64_t k = (br * 2 + 0) * M + m;
                 const ulonglong2 ps = qa.psum[k];
                 const float2 mm = qa.pmm[k];
                 sum += ((u128)ps.y << 64) | ps.x;
@@ -513,10 +514,11 @@ __device__ __forceinline__ void pair_args(const UpdateArgs& a, const BatchArgs& 
     qk.consts = b.consts + pd.k;
     qk.chunk_prefix = b.chunk_prefix + (uint64_t)pd.k * b.n_chunks;
     qk.step_sums = b.step_sums + (uint64_t)pd.k * b.n_chunks * STEPS;
-    qk.H = b.H + pd.hs_off;
-    qk.S = b.S + pd.hs_off;
-    qk.psum = b.psum + pd.hs_off * 2 * a.M;
-    qk.pmm = b.pmm + pd.hs_off * 2 * a.M;
+    qk.H = b.H + pd.src_hs_off;
+    qk.S = b.S + pd.src_hs_off;
+    qk.psum = b.psum + pd.src_hs_off * 2 * a.M;
+    qk.pmm = b.pmm + pd.src_hs_off * 2 * a.M;
+    qk.hstride = pd.hstride;
 }
 
 template <int M, int PM>
@@ -524,7 +526,7 @@ __global__ __launch_bounds__(256) void k_bounds_batch(UpdateArgs a, BatchArgs b)
 {
     extern __shared__ float s_tf[];
     const PairDesc pd = b.pairs[blockIdx.y];
-    if (blockIdx.x * (blockDim.x >> 5) + 1 >= pd.W) return;          // block-uniform
+    if (pd.derived || blockIdx.x * (blockDim.x >> 5) + 1 >= pd.W) return;   // block-uniform
     UpdateArgs ak;
     QueryArgs qk;
     pair_args(a, b, pd, ak, qk);

@@ -1083,12 +1083,32 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
         const uint32_t k = pair_tf[q], W = pair_width[q];
         if (k >= K) return fail(c, DVL_ERR_ARG, "pair %u: TF index %u >= K", q, k);
         if (W < 1 || W > DVL_MAX_WIDTH) return fail(c, DVL_ERR_ARG, "pair %u: width must be in [1, %d]", q, DVL_MAX_WIDTH);
-        pairs[q] = PairDesc{k, W, bin_off, cnt_off, hs_off};
+        pairs[q] = PairDesc{k, W, bin_off, cnt_off, hs_off, hs_off, 1u, 0u};
         bin_off += (uint64_t)M * W;
         cnt_off += W;
         hs_off += W + 1;
         max_W = W > max_W ? W : max_W;
     }
+    // a pair whose width divides a wider (or equal, earlier) pair's of the same
+    // TF reads that pair's pixel bounds instead of computing its own
+    std::vector<std::vector<uint32_t>> by_tf(K);
+    for (uint32_t q = 0; q < n_pairs; ++q) by_tf[pairs[q].k].push_back(q);
+    for (uint32_t q = 0; q < n_pairs; ++q) {
+        int best = -1;
+        for (uint32_t r : by_tf[pairs[q].k]) {
+            if (r == q || pairs[r].W % pairs[q].W) continue;
+            if (pairs[r].W == pairs[q].W && r > q) continue;     // equal widths: the first one computes
+            if (best < 0 || pairs[r].W > pairs[best].W || (pairs[r].W == pairs[best].W && r < (uint32_t)best))
+                best = (int)r;
+        }
+        if (best >= 0 && pairs[best].W >= pairs[q].W) {
+            pairs[q].derived = 1u;
+            pairs[q].hstride = pairs[best].W / pairs[q].W;
+        }
+        pairs[q].src_hs_off = best >= 0 ? (uint64_t)best : (uint64_t)q;   // pair index for now
+    }
+    for (uint32_t q = 0; q < n_pairs; ++q)
+        pairs[q].src_hs_off = pairs[q].derived ? pairs[pairs[q].src_hs_off].hs_off : pairs[q].hs_off;
     if (cnt_off > (1u << 24)) return fail(c, DVL_ERR_ARG, "sum of pair widths above 2^24");
     cudaSetDevice(c->device);
 

@@ -110,6 +110,10 @@ struct QueryArgs {
     // to the step's end (its head).  Index ((j * 2 + side) * M + m).
     ulonglong2* psum;          // fixed-point sums of t (lo, hi words)
     float2* pmm;               // min, max of t (3, -1 if empty)
+    // The pixel queries read boundary j of these arrays at j * hstride: a
+    // width that divides a wider one of the same scan shares its boundaries
+    // (ceil(j F / W) = ceil(r j F / (r W))), so it reads every r-th entry.
+    uint32_t hstride;
 };
 uint64_t value_table_levels(uint64_t n_steps, uint64_t* stride);
 
@@ -159,6 +163,9 @@ struct PairDesc {              // one (TF, viewport) pair of a batch
     uint64_t bin_off;          // element offset of its M x W bin arrays
     uint64_t cnt_off;          // element offset of its W counts
     uint64_t hs_off;           // element offset of its W + 1 pixel bounds
+    uint64_t src_hs_off;       // bounds its pixels read: its own, or those of a
+    uint32_t hstride;          //   wider pair of the same TF (every hstride-th)
+    uint32_t derived;          // 1: its bounds are not computed (src is another pair)
 };
 struct BatchArgs {
     uint32_t K, G;             // TFs, TFs per shared-memory group of pass A

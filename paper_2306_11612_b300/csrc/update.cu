@@ -986,7 +986,7 @@ cudaError_t run_update(cudaStream_t s, const UpdateArgs& a)
     if (e != cudaSuccess) return e;
     if (a.vt) {
         // bins as range queries over the value tables (writes final bins)
-        const QueryArgs qa{a.consts, a.chunk_prefix, a.step_sums, a.H, a.S, a.psum, a.pmm};
+        const QueryArgs qa{a.consts, a.chunk_prefix, a.step_sums, a.H, a.S, a.psum, a.pmm, 1u};
         if ((e = launch_bins(s, a, qa, *a.vt)) != cudaSuccess) return e;
         if (a.events) cudaEventRecord(a.events[3], s);
     } else {

@@ -216,3 +216,18 @@ def test_batch_at_benchmark_size():
                     assert np.array_equal(allb[key][sl].view(np.uint8), b[key].view(np.uint8)), (q, m, key)
     finally:
         ctx.close()
+
+
+def test_batch_shared_bounds_across_widths():
+    # widths of one TF that divide a wider one read its pixel bounds (every
+    # r-th boundary); chains, equal widths and non-divisible widths together
+    amr = synth.make("small")
+    alphas = _tfs(9, 2)
+    widths = [7, 14, 28, 28, 3, 21, 1000, 2000, 1, 4096, 999]
+    pairs = [(0, w) for w in widths] + [(1, w) for w in (512, 2048, 333)]
+    ctx = _ctx(amr.lower, amr.level, amr.fields)
+    try:
+        _check_vs_single(ctx, alphas, pairs, P=1.0)
+        _check_vs_single(ctx, alphas, pairs, P=2.0, min_importance=0.1)
+    finally:
+        ctx.close()
