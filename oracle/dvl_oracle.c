@@ -618,3 +618,52 @@ int orc_widths(uint64_t n_total, uint32_t M, const float* dmin, const float* dma
     if (vmax_out) *vmax_out = Vmax;
     return 0;
 }
+
+/* ---- log10 value scale (see dvl_oracle.h) ----------------------------------- */
+
+float orc_log10f(float x)
+{
+    /* c_k = 2 log10(e) / (2k + 1), k = 0..4, rounded to float32 */
+    const float c0 = 0x1.bcb7b2p-1f, c1 = 0x1.287a76p-2f, c2 = 0x1.63c628p-3f, c3 = 0x1.fc3fa6p-4f,
+                c4 = 0x1.8b4df2p-4f;
+    const float l2_hi = 0x1.344p-2f;        /* log10(2) to 16 bits: e * l2_hi is exact */
+    const float l2_lo = 0x1.3509f8p-18f;    /* float32(log10(2) - l2_hi) */
+    const float s2 = 0x1.6a09e6p+0f;        /* float32(sqrt 2) */
+    int e = 0;
+    if (x < 0x1p-126f) { x = x * 0x1p24f; e = -24; }   /* subnormal: exact rescale */
+    uint32_t b;
+    memcpy(&b, &x, 4);
+    e += (int)(b >> 23) - 127;
+    b = (b & 0x007FFFFFu) | 0x3F800000u;               /* m in [1, 2) */
+    float m;
+    memcpy(&m, &b, 4);
+    if (m >= s2) { m = m * 0.5f; e += 1; }              /* m in [s2/2, s2) */
+    const float num = m - 1.0f;                         /* exact (Sterbenz) */
+    const float den = m + 1.0f;                         /* rounded ... */
+    const float dlo = m - (den - 1.0f);                 /* ... and its exact error: m + 1 = den + dlo */
+    const float z = num / den;
+    /* z's residual against the exact quotient num / (m + 1):
+     * num - z (den + dlo), the first product exact through the fma */
+    float r = fmaf(-z, den, num);
+    r = fmaf(-z, dlo, r);
+    const float dz = r / den;                           /* z + dz = num / (m + 1) to ~2^-48 */
+    const float w = z * z;
+    float p = c4;
+    p = fmaf(p, w, c3);
+    p = fmaf(p, w, c2);
+    p = fmaf(p, w, c1);
+    p = fmaf(p, w, c0);
+    const float lm = fmaf(z, p, dz * c0);               /* log10 m = (z + dz) p */
+    const float ef = (float)e;
+    return fmaf(ef, l2_hi, fmaf(ef, l2_lo, lm));
+}
+
+int orc_log_field(uint64_t n, float* v)
+{
+    float pos = 0.0f;                  /* smallest positive value */
+    for (uint64_t i = 0; i < n; ++i)
+        if (v[i] > 0.0f && (pos == 0.0f || v[i] < pos)) pos = v[i];
+    if (!(pos > 0.0f)) return -5;
+    for (uint64_t i = 0; i < n; ++i) v[i] = orc_log10f(v[i] > 0.0f ? v[i] : pos);
+    return 0;
+}
