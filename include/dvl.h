@@ -152,6 +152,37 @@ int dvl_build_order(dvl_ctx* ctx, int sfc);
  * n_fields must equal the loaded count.  Needs ORDERED. */
 int dvl_set_fields(dvl_ctx* ctx, uint32_t n_fields, const float* const* fields, int mem_kind);
 
+/* Per-field value scale.  Fields spanning many decades (densities,
+ * pressures of astrophysical AMR data) are usually normalised on a log axis:
+ * DVL_SCALE_LOG10 replaces the field's values by their log10 before anything
+ * else of the update sees them, so the domain normalisation of Sec. 3.3 (and
+ * the default TF domain, the field's data range) applies to the log values.
+ * A value <= 0 first takes the field's smallest positive value.  The log10
+ * is a fixed sequence of correctly rounded float32 operations (argument
+ * reduction to [sqrt(2)/2, sqrt(2)), the atanh series, log10(2) split in two
+ * floats), within 1.5 ulp of the exact log10, with the same bits on every
+ * IEEE float32 implementation of the sequence.  The scale holds until the
+ * next dvl_load_amr and is re-applied by dvl_set_fields (a log-scaled field
+ * whose new values have no positive value returns to the linear scale, and
+ * dvl_set_fields returns DVL_ERR_RANGE after setting the values).  Needs
+ * LOADED; once the order is built, the values are re-gathered at once
+ * (synchronising) and the value tables are rebuilt by the next update.
+ * Errors: DVL_ERR_ARG (field, scale), DVL_ERR_STATE, DVL_ERR_RANGE (log
+ * scale for a field without a positive value), DVL_ERR_CUDA. */
+enum { DVL_SCALE_LINEAR = 0, DVL_SCALE_LOG10 = 1 };
+int dvl_set_field_scale(dvl_ctx* ctx, uint32_t field, int scale);
+
+/* Copies the n_cells values of one field in curve order as the update sees
+ * them (after the field's scale).  Host output synchronises; device output
+ * is enqueued on the context's stream.  Needs ORDERED.
+ * Errors: DVL_ERR_ARG, DVL_ERR_STATE, DVL_ERR_CUDA. */
+int dvl_read_values(dvl_ctx* ctx, uint32_t field, float* out, int mem_kind);
+
+/* The data range of every field as the update sees it (after the scales):
+ * lo[n_fields], hi[n_fields], host memory.  Synchronising.  Needs LOADED.
+ * Errors: DVL_ERR_ARG, DVL_ERR_STATE, DVL_ERR_CUDA. */
+int dvl_read_data_range(dvl_ctx* ctx, float* lo, float* hi);
+
 /* Sets the alpha transfer function of one field (paper Sec. 3.3): n_entries
  * alpha values in [0, 1] over the normalised domain, entry a covering
  * t in [a/T, (a+1)/T) (the last entry closed).  The field value v maps to

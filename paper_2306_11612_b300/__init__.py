@@ -29,12 +29,14 @@ VMAX_APPROX, VMAX_EXACT = 0, 1
 WIDTH_EDGE, WIDTH_VOLUME = 0, 1
 OPT_SPIN_LIMIT, OPT_FAULT_NO_PUBLISH, OPT_TIMING = 1, 2, 3
 PLOT_MEAN, PLOT_Y = 0, 1
+SCALE_LINEAR, SCALE_LOG10 = 0, 1
 
 EXPORTS = ["dvl_create", "dvl_destroy", "dvl_load_amr", "dvl_build_order", "dvl_set_fields",
            "dvl_set_tf", "dvl_update", "dvl_read_bins", "dvl_get_stats", "dvl_read_order",
            "dvl_read_widths", "dvl_sync", "dvl_set_option", "dvl_get_timings", "dvl_update_noalloc", "dvl_set_tf_ctrl", "dvl_read_alpha_means", "dvl_backward",
            "dvl_update_batch", "dvl_read_batch_bins", "dvl_read_batch_all", "dvl_batch_config",
            "dvl_read_batch_all_async", "dvl_stream", "dvl_rasterize", "dvl_brush", "dvl_select_keys",
+           "dvl_set_field_scale", "dvl_read_values", "dvl_read_data_range",
            "dvl_status_string", "dvl_last_error",
            "dvl_server_create", "dvl_server_destroy", "dvl_server_add_dataset", "dvl_server_warmup",
            "dvl_server_submit", "dvl_server_wait", "dvl_server_get_stats", "dvl_server_reset_stats",
@@ -112,6 +114,9 @@ def _load():
         "dvl_rasterize": ([vp, u32, u32, u32, vp, vp, i32], i32),
         "dvl_brush": ([vp, u32, u32, ctypes.POINTER(dvl_roi), vp, i32], i32),
         "dvl_select_keys": ([vp, vp, u32, vp, i32], i32),
+        "dvl_set_field_scale": ([vp, u32, i32], i32),
+        "dvl_read_values": ([vp, u32, vp, i32], i32),
+        "dvl_read_data_range": ([vp, vp, vp], i32),
         "dvl_server_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(dvl_server_config)], i32),
         "dvl_server_destroy": ([vp], None),
         "dvl_server_add_dataset": ([vp, u64, vp, vp, u32, vp, i32, ctypes.POINTER(u32)], i32),
@@ -241,6 +246,29 @@ class DVL:
         self._check(lib.dvl_set_fields(self._h, len(fps), arr, kind))
 
     set_fields = dvl_set_fields
+
+    def dvl_set_field_scale(self, field: int, scale: int):
+        self._check(lib.dvl_set_field_scale(self._h, field, scale))
+
+    set_field_scale = dvl_set_field_scale
+
+    def dvl_read_values(self, field: int, out=None):
+        """Field values in curve order as the update sees them (after the scale)."""
+        if out is None:
+            out = np.empty(self.n, np.float32)
+        p, kind, _ = _ptr_kind(out)
+        self._check(lib.dvl_read_values(self._h, field, p, kind))
+        return out
+
+    read_values = dvl_read_values
+
+    def dvl_read_data_range(self):
+        lo = np.empty(self.M, np.float32)
+        hi = np.empty(self.M, np.float32)
+        self._check(lib.dvl_read_data_range(self._h, lo.ctypes.data, hi.ctypes.data))
+        return lo, hi
+
+    read_data_range = dvl_read_data_range
 
     # ---- per edit ----
     def dvl_set_tf(self, field: int, alpha, lo: float = math.nan, hi: float = math.nan):

@@ -52,6 +52,7 @@ struct dvl_ctx {
     uint32_t T = 0;
     std::vector<float> h_tf, h_dom;
     std::vector<char> tf_set;
+    uint32_t log_mask = 0;            // fields on the log10 value scale (bit m)
     bool tf_dirty = false;
     bool tf_device = false;           // tables built on the device from control points
     uint32_t K_ctrl = 0;
@@ -279,15 +280,51 @@ int upload_fields(dvl_ctx* c, const float* const* fields, int mem_kind)
     return DVL_OK;
 }
 
-int compute_ranges(dvl_ctx* c)
+// Resets the per-field min/max words (dmin, dmax lead DataMeta) and, when
+// `positive`, the smallest-positive words, then reduces `vals` into them.
+int reduce_ranges(dvl_ctx* c, const float* vals, bool positive)
 {
-    // reset the per-field min/max words (dmin, dmax lead DataMeta), then reduce
     uint32_t init[2 * DVL_MAX_FIELDS];
     for (int m = 0; m < DVL_MAX_FIELDS; ++m) { init[m] = 0xFFFFFFFFu; init[DVL_MAX_FIELDS + m] = 0u; }
     CK(cudaMemcpyAsync(c->d_meta, init, sizeof init, cudaMemcpyHostToDevice, c->stream), "write meta");
+    if (positive) {
+        uint32_t pos[DVL_MAX_FIELDS];
+        for (int m = 0; m < DVL_MAX_FIELDS; ++m) pos[m] = 0xFFFFFFFFu;
+        CK(cudaMemcpyAsync(c->d_meta->dpos, pos, sizeof pos, cudaMemcpyHostToDevice, c->stream), "write meta");
+    }
     CK(cudaStreamSynchronize(c->stream), "synchronize");
-    launch_field_ranges(c->stream, c->n, c->M, c->d_fin, c->pitch, c->d_meta, c->d_err);
+    launch_field_ranges(c->stream, c->n, c->M, vals, c->pitch, c->d_meta, c->d_err, positive);
     CK(cudaGetLastError(), "field range kernel");
+    return DVL_OK;
+}
+
+int compute_ranges(dvl_ctx* c) { return reduce_ranges(c, c->d_fin, true); }
+
+// Fields flagged in `mask` that have no positive value (synchronises).
+int fields_without_positive(dvl_ctx* c, uint32_t mask, uint32_t* bad)
+{
+    uint32_t pos[DVL_MAX_FIELDS];
+    CK(cudaMemcpyAsync(pos, c->d_meta->dpos, sizeof pos, cudaMemcpyDeviceToHost, c->stream), "read meta");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    *bad = 0;
+    for (uint32_t m = 0; m < c->M; ++m)
+        if ((mask >> m & 1u) && pos[m] == 0xFFFFFFFFu) *bad |= 1u << m;
+    return DVL_OK;
+}
+
+// Gathers the input-order fields into curve order (levels too when lin is
+// given), applying the log scale of the flagged fields; the data ranges are
+// then those of the gathered values.  The value tables must be rebuilt.
+int gather_values(dvl_ctx* c, const uint8_t* lin, uint8_t* lout)
+{
+    launch_gather(c->stream, c->n, c->d_perm, c->M, c->d_fin, c->pitch, lin, c->d_val, c->pitch, lout,
+                  c->log_mask, c->d_meta);
+    CK(cudaGetLastError(), "gather kernel");
+    if (c->log_mask) {
+        int rc = reduce_ranges(c, c->d_val, false);
+        if (rc) return rc;
+    }
+    c->vt_valid = false;
     return DVL_OK;
 }
 
@@ -425,9 +462,10 @@ int dvl_load_amr(dvl_ctx* c, uint64_t n, const int32_t* lower, const uint8_t* le
     init.max_level = 0;
     init.pad = 0;
     init.key_or = 0;
+    for (int m = 0; m < DVL_MAX_FIELDS; ++m) init.dpos[m] = 0xFFFFFFFFu;
     CK(cudaMemcpyAsync(c->d_meta, &init, sizeof init, cudaMemcpyHostToDevice, c->stream), "write meta");
     launch_validate(c->stream, n, c->d_lower, c->d_level_in, M, nullptr, p, c->d_meta, c->d_err);
-    launch_field_ranges(c->stream, n, M, c->d_fin, p, c->d_meta, c->d_err);
+    launch_field_ranges(c->stream, n, M, c->d_fin, p, c->d_meta, c->d_err, true);
     CK(cudaGetLastError(), "validation kernels");
     rc = take_device_error(c);     // synchronises: inputs are consumed on return
     if (rc) { free_dataset(c); return rc; }
@@ -435,6 +473,7 @@ int dvl_load_amr(dvl_ctx* c, uint64_t n, const int32_t* lower, const uint8_t* le
     c->tf_set.assign(M, 0);
     c->h_tf.clear();
     c->h_dom.assign(2 * M, NAN);
+    c->log_mask = 0;
     c->tf_dirty = true;
     c->state = 1;
     return DVL_OK;
@@ -491,8 +530,10 @@ int dvl_build_order(dvl_ctx* c, int sfc)
     CK(dalloc(c->d_lev, p), "alloc sorted levels");
     CK(cudaMemsetAsync(c->d_val, 0, (size_t)c->M * p * sizeof(float), c->stream), "clear");
     CK(cudaMemsetAsync(c->d_lev, 0, p, c->stream), "clear");
-    launch_gather(c->stream, n, c->d_perm, c->M, c->d_fin, p, c->d_level_in, c->d_val, p, c->d_lev);
-    CK(cudaGetLastError(), "gather kernel");
+    {
+        int rc = gather_values(c, c->d_level_in, c->d_lev);
+        if (rc) return rc;
+    }
     const uint64_t tiles = (n + TILE - 1) / TILE;
     CK(dalloc(c->d_tile_status, tiles), "alloc scan state");
     CK(dalloc(c->d_chunk_prefix, tiles * WARPS), "alloc scan state");
@@ -536,10 +577,86 @@ int dvl_set_fields(dvl_ctx* c, uint32_t M, const float* const* fields, int mem_k
     if (rc) return rc;
     rc = compute_ranges(c);
     if (rc) return rc;
-    launch_gather(c->stream, c->n, c->d_perm, c->M, c->d_fin, c->pitch, nullptr, c->d_val, c->pitch, nullptr);
-    CK(cudaGetLastError(), "gather kernel");
-    c->vt_valid = false;                 // the values changed: rebuild the value tables
+    uint32_t bad = 0;
+    if (c->log_mask) {
+        rc = fields_without_positive(c, c->log_mask, &bad);
+        if (rc) return rc;
+        c->log_mask &= ~bad;             // such a field falls back to the linear scale
+    }
+    rc = gather_values(c, nullptr, nullptr);
+    if (rc) return rc;
+    rc = take_device_error(c);
+    if (rc) return rc;
+    if (bad) return fail(c, DVL_ERR_RANGE, "log-scaled fields 0x%x have no positive value; now linear", bad);
+    return DVL_OK;
+}
+
+int dvl_set_field_scale(dvl_ctx* c, uint32_t field, int scale)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (c->state < 1) return fail(c, DVL_ERR_STATE, "no data set loaded");
+    if (field >= c->M) return fail(c, DVL_ERR_ARG, "field %u out of range", field);
+    if (scale != DVL_SCALE_LINEAR && scale != DVL_SCALE_LOG10) return fail(c, DVL_ERR_ARG, "bad scale");
+    cudaSetDevice(c->device);
+    const uint32_t bit = 1u << field;
+    const uint32_t mask = scale == DVL_SCALE_LOG10 ? (c->log_mask | bit) : (c->log_mask & ~bit);
+    if (mask == c->log_mask) return DVL_OK;
+    if (scale == DVL_SCALE_LOG10) {
+        uint32_t bad = 0;
+        int rc = fields_without_positive(c, bit, &bad);
+        if (rc) return rc;
+        if (bad) return fail(c, DVL_ERR_RANGE, "field %u has no positive value", field);
+    }
+    c->log_mask = mask;
+    if (c->state < 2) return DVL_OK;     // applied when the order is built
+    // the ranges of the input values first: a field back on the linear scale
+    // takes its raw range, the others are recomputed after the gather
+    int rc = reduce_ranges(c, c->d_fin, false);
+    if (rc) return rc;
+    rc = gather_values(c, nullptr, nullptr);
+    if (rc) return rc;
     return take_device_error(c);
+}
+
+int dvl_read_values(dvl_ctx* c, uint32_t field, float* out, int mem_kind)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (c->state < 2) return fail(c, DVL_ERR_STATE, "order not built");
+    if (field >= c->M) return fail(c, DVL_ERR_ARG, "field %u out of range", field);
+    if (mem_kind != DVL_MEM_HOST && mem_kind != DVL_MEM_DEVICE) return fail(c, DVL_ERR_ARG, "bad mem_kind");
+    if (c->n && !out) return fail(c, DVL_ERR_ARG, "out is NULL");
+    cudaSetDevice(c->device);
+    if (c->n)
+        CK(cudaMemcpyAsync(out, c->d_val + field * c->pitch, c->n * sizeof(float),
+                           mem_kind == DVL_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream),
+           "copy values");
+    if (mem_kind == DVL_MEM_HOST) return take_device_error(c);
+    return DVL_OK;
+}
+
+int dvl_read_data_range(dvl_ctx* c, float* lo, float* hi)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (c->state < 1) return fail(c, DVL_ERR_STATE, "no data set loaded");
+    if (!lo || !hi) return fail(c, DVL_ERR_ARG, "NULL output");
+    cudaSetDevice(c->device);
+    uint32_t w[2 * DVL_MAX_FIELDS];
+    CK(cudaMemcpyAsync(w, c->d_meta, sizeof w, cudaMemcpyDeviceToHost, c->stream), "read meta");
+    int rc = take_device_error(c);
+    if (rc) return rc;
+    for (uint32_t m = 0; m < c->M; ++m) {
+        for (int k = 0; k < 2; ++k) {
+            uint32_t u = w[k * DVL_MAX_FIELDS + m];
+            u = (u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u;     // order-preserving bits -> float bits
+            float f;
+            std::memcpy(&f, &u, 4);
+            (k ? hi : lo)[m] = f;
+        }
+    }
+    return DVL_OK;
 }
 
 int dvl_set_tf(dvl_ctx* c, uint32_t field, const float* alpha, uint32_t T, float lo, float hi)

@@ -59,6 +59,7 @@ struct DataMeta {
     uint32_t max_level;
     uint32_t pad;
     unsigned long long key_or;       // OR of all keys (significant bits)
+    uint32_t dpos[DVL_MAX_FIELDS];   // bits of the smallest positive value (0xFFFFFFFF: none)
 };
 
 }  // namespace dvl
@@ -69,8 +70,10 @@ namespace dvl {
 // sfc_sort.cu
 void launch_validate(cudaStream_t s, uint64_t n, const int32_t* lower, const uint8_t* level,
                      uint32_t M, float* const* fields, size_t pitch, DataMeta* meta, uint32_t* err);
+// Per-field min/max into meta->dmin/dmax; with `positive` also the smallest
+// positive value into meta->dpos (the clamp of the log scale).
 void launch_field_ranges(cudaStream_t s, uint64_t n, uint32_t M, const float* fields, size_t pitch,
-                         DataMeta* meta, uint32_t* err);
+                         DataMeta* meta, uint32_t* err, bool positive = false);
 void launch_keys(cudaStream_t s, uint64_t n, const int32_t* lower, size_t pitch, const uint8_t* level,
                  int sfc, unsigned long long* keys, uint32_t* vals, uint32_t* hist /*8*256*/,
                  DataMeta* meta);
@@ -80,8 +83,11 @@ cudaError_t launch_onesweep(cudaStream_t s, uint64_t n, const unsigned long long
                             const uint32_t* vin, unsigned long long* kout, uint32_t* vout,
                             int shift, const uint32_t* hist_digit, unsigned long long* status,
                             uint32_t epoch, uint32_t* tile_counter, uint32_t* err, int64_t spin_limit);
+// fout[m][k] = fin[m][perm[k]]; a field whose bit is set in log_mask is
+// stored as its log10 scale (logscale.cuh), values <= 0 taking meta->dpos[m].
 void launch_gather(cudaStream_t s, uint64_t n, const uint32_t* perm, uint32_t M, const float* fin,
-                   size_t pitch_in, const uint8_t* lin, float* fout, size_t pitch_out, uint8_t* lout);
+                   size_t pitch_in, const uint8_t* lin, float* fout, size_t pitch_out, uint8_t* lout,
+                   uint32_t log_mask = 0, const DataMeta* meta = nullptr);
 
 // bins.cu: TF-independent value tables (per data set and TF domain) and the
 // per-pixel range queries that replace the placement pass.

@@ -10,6 +10,7 @@
 #include <stdint.h>
 
 #include "dvl_internal.h"
+#include "logscale.cuh"
 
 namespace dvl {
 
@@ -61,11 +62,11 @@ __global__ void k_validate(uint64_t n, const int32_t* __restrict__ lower, size_t
 }
 
 __global__ void k_field_ranges(uint64_t n, uint32_t M, const float* __restrict__ f, size_t pitch,
-                               DataMeta* meta, uint32_t* err)
+                               DataMeta* meta, uint32_t* err, bool positive)
 {
     uint32_t m = blockIdx.y;
     const float* v = f + m * pitch;
-    uint32_t mn = 0xFFFFFFFFu, mx = 0u, bad = 0;
+    uint32_t mn = 0xFFFFFFFFu, mx = 0u, pos = 0xFFFFFFFFu, bad = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         float x = v[i];
@@ -73,15 +74,18 @@ __global__ void k_field_ranges(uint64_t n, uint32_t M, const float* __restrict__
         uint32_t o = float_to_ordered(x);
         mn = min(mn, o);
         mx = max(mx, o);
+        if (x > 0.0f) pos = min(pos, __float_as_uint(x));   // positive floats order as their bits
     }
     for (int o = 16; o; o >>= 1) {
         mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
         mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        pos = min(pos, __shfl_xor_sync(0xffffffffu, pos, o));
         bad |= __shfl_xor_sync(0xffffffffu, bad, o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicMin(&meta->dmin[m], mn);
         atomicMax(&meta->dmax[m], mx);
+        if (positive && pos != 0xFFFFFFFFu) atomicMin(&meta->dpos[m], pos);
         if (bad) atomicOr(err, bad);
     }
 }
@@ -101,11 +105,11 @@ void launch_validate(cudaStream_t s, uint64_t n, const int32_t* lower, const uin
 }
 
 void launch_field_ranges(cudaStream_t s, uint64_t n, uint32_t M, const float* fields, size_t pitch,
-                         DataMeta* meta, uint32_t* err)
+                         DataMeta* meta, uint32_t* err, bool positive)
 {
     if (!n) return;
     dim3 grid((unsigned)grid_for(n, 256) / M + 1, M);
-    k_field_ranges<<<grid, 256, 0, s>>>(n, M, fields, pitch, meta, err);
+    k_field_ranges<<<grid, 256, 0, s>>>(n, M, fields, pitch, meta, err, positive);
 }
 
 // ---- space-filling-curve keys ----------------------------------------------
@@ -352,22 +356,29 @@ cudaError_t launch_onesweep(cudaStream_t s, uint64_t n, const unsigned long long
 
 __global__ void k_gather(uint64_t n, const uint32_t* __restrict__ perm, uint32_t M,
                          const float* __restrict__ fin, size_t pin, const uint8_t* __restrict__ lin,
-                         float* __restrict__ fout, size_t pout, uint8_t* __restrict__ lout)
+                         float* __restrict__ fout, size_t pout, uint8_t* __restrict__ lout,
+                         uint32_t log_mask, const DataMeta* __restrict__ meta)
 {
     for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n;
          k += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t i = perm[k];
         if (i >= n) continue;        // only after a failed sort (error already raised)
         if (lin) lout[k] = lin[i];
-        for (uint32_t m = 0; m < M; ++m) fout[m * pout + k] = fin[m * pin + i];
+        for (uint32_t m = 0; m < M; ++m) {
+            float x = fin[m * pin + i];
+            if (log_mask >> m & 1u) x = log10_scale(x > 0.0f ? x : __uint_as_float(meta->dpos[m]));
+            fout[m * pout + k] = x;
+        }
     }
 }
 
 void launch_gather(cudaStream_t s, uint64_t n, const uint32_t* perm, uint32_t M, const float* fin,
-                   size_t pitch_in, const uint8_t* lin, float* fout, size_t pitch_out, uint8_t* lout)
+                   size_t pitch_in, const uint8_t* lin, float* fout, size_t pitch_out, uint8_t* lout,
+                   uint32_t log_mask, const DataMeta* meta)
 {
     if (!n) return;
-    k_gather<<<grid_for(n, 256), 256, 0, s>>>(n, perm, M, fin, pitch_in, lin, fout, pitch_out, lout);
+    k_gather<<<grid_for(n, 256), 256, 0, s>>>(n, perm, M, fin, pitch_in, lin, fout, pitch_out, lout,
+                                              log_mask, meta);
 }
 
 }  // namespace dvl
