@@ -51,6 +51,7 @@ BYTES_PIXELS_PER_PIXEL = 2 * 9 + 2 * 4 * 24 + 2 * 4 * 16 + 4 * 4 * 4 + 4 * 24 + 
 BYTES_BINS_PER_PIXEL = BYTES_BOUNDS_PER_PIXEL + BYTES_PIXELS_PER_PIXEL
 CPU_SAMPLE_BOX = ((0, 0, 0), 32)     # 32^3 of the 128^3 base cells (1/64 of the domain)
 LAUNCHES_PER_UPDATE = 4              # prepare, width+scan pass, pixel bounds, pixel bins
+LOG_FIELDS = (0, 2, 3)                   # dens, pres, velmag on the log10 scale
 RASTER_H = 512                       # rows of the line-plot image
 METRIC = "DVL update throughput (cells/s per alpha-TF edit)"
 
@@ -376,6 +377,29 @@ def run_ours(args):
     r1.synchronize()
     select_ms = r0.elapsed_time(r1) / 5
     del mask
+    # per-field log10 scale of dens, pres and velmag: the one-off re-gather of
+    # the values (with the scaled data ranges), the first update after it (value
+    # tables rebuilt), and edits on the scaled fields
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for m in LOG_FIELDS:
+        ctx.set_field_scale(m, dvl.SCALE_LOG10)
+    log_set_ms = (time.perf_counter() - t0) * 1e3 / len(LOG_FIELDS)
+    t0 = time.perf_counter()
+    ctx.update(**kw)
+    ctx.sync()
+    log_first_ms = (time.perf_counter() - t0) * 1e3
+    r0.record(stream)
+    for i in range(10):
+        ctx.set_tfs(tfs[i])
+        ctx.update(**kw)
+    r1.record(stream)
+    r1.synchronize()
+    log_edit_ms = r0.elapsed_time(r1) / 10
+    for m in LOG_FIELDS:
+        ctx.set_field_scale(m, dvl.SCALE_LINEAR)
+    ctx.update(**kw)                     # value tables of the linear fields again
+    ctx.sync()
     ms = max_over_ranks(ms, world)
     value = job_throughput(amr.n * args.steps, world, ms * 1e-3)
 
@@ -426,7 +450,9 @@ def run_ours(args):
                             edit_bytes_per_cell=edit_bytes / amr.n, edit_gbs=step_gbs, edit_frac=step_gbs / peak,
                             first_update_ms_with_value_tables=t_first,
                             rasterize_ms=raster_ms, rasterize_image=f"{RASTER_H} x {args.width}, 4 polylines + bars",
-                            brush_ms=brush_ms, brush_cells=roi["n_cells"], select_keys_ms=select_ms),
+                            brush_ms=brush_ms, brush_cells=roi["n_cells"], select_keys_ms=select_ms,
+                            log_scale={"fields": "dens, pres, velmag", "set_scale_ms_per_field": log_set_ms,
+                                       "first_update_ms": log_first_ms, "ms_per_edit": log_edit_ms}),
             "per_edit": edit_pct,
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": LAUNCHES_PER_UPDATE * args.steps,
             "setup_s": {"generate": t_gen, "load": t_load, "build_order": t_build}}

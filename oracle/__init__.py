@@ -255,10 +255,14 @@ def widths(n_total: int, dmin, dmax, max_level: int, alpha: np.ndarray, values: 
 
 
 def log10f(x) -> np.ndarray:
-    """The log10 of the per-field log scale, element by element (float32)."""
-    v = np.ascontiguousarray(x, np.float32).reshape(-1)
-    f = _L().orc_log10f
-    return np.array([f(float(t)) for t in v], np.float32).reshape(np.shape(x))
+    """The log10 of the per-field log scale, element by element (float32,
+    every value > 0)."""
+    v = np.array(x, np.float32, copy=True).reshape(-1)
+    if not np.all(v > 0):
+        raise OracleError("log10f needs positive values")
+    if v.size:
+        _L().orc_log_field(v.size, _p(v))
+    return v.reshape(np.shape(x))
 
 
 def log_fields(fields: np.ndarray, log_mask: int) -> np.ndarray:

@@ -93,3 +93,54 @@ def test_bins_at_full_size(full):
         assert np.array_equal(pl[m]["min"].view(np.uint32), rq[m]["min"].view(np.uint32))
         assert np.array_equal(pl[m]["max"].view(np.uint32), rq[m]["max"].view(np.uint32))
         assert np.all(np.abs(pl[m]["sum"] - rq[m]["sum"]) <= 1e-5 * np.abs(rq[m]["sum"]) + 1e-30)
+
+
+def test_log_scale_at_full_size(full):
+    """dens, pres and velmag on the log10 scale: 1M sampled scaled values bit
+    for bit against the oracle's log10 of their input cells, the data range
+    equal to the min/max of all scaled values, 1M sampled widths against the
+    oracle given that range, and the bins' properties; then back to linear."""
+    import torch
+    amr, ctx, tf, keys, perm = full
+    n = amr.n
+    logm = (0, 2, 3)
+    for m in logm:
+        ctx.set_field_scale(m, dvl.SCALE_LOG10)
+    try:
+        rng = np.random.default_rng(14)
+        k = np.sort(rng.choice(n, 1_000_000, replace=False))
+        c = perm[k]
+        kd = torch.from_numpy(k.astype(np.int64)).cuda()
+        lo, hi = ctx.read_data_range()
+        sample = np.empty((4, k.size), np.float32)
+        buf = torch.empty(n, dtype=torch.float32, device="cuda")
+        for m in range(4):
+            ctx.read_values(m, out=buf)
+            ctx.sync()
+            assert lo[m] == buf.min().item() and hi[m] == buf.max().item(), m
+            sample[m] = buf[kd].cpu().numpy()
+            raw = np.ascontiguousarray(amr.fields[m, c])
+            if m in logm:
+                pos = amr.fields[m][amr.fields[m] > 0].min()
+                ref = oracle.log10f(np.where(raw > 0, raw, pos).astype(np.float32))
+            else:
+                ref = raw
+            assert np.array_equal(sample[m].view(np.uint32), ref.view(np.uint32)), m
+        del buf
+        ctx.update(P=P, min_importance=MI, width=W)
+        q = ctx.read_widths()
+        st = ctx.get_stats()
+        qo, Q, vmax = oracle.widths(n, lo, hi, int(amr.level.max()), tf, sample,
+                                    np.ascontiguousarray(amr.level[c]), P=P, min_importance=MI)
+        assert Q == st["Q"] and np.float32(vmax) == np.float32(st["vmax"])
+        assert np.array_equal(qo, q[k])
+        cnt = ctx.read_bins(0)["count"].astype(np.int64)
+        assert np.all(cnt >= 1) and cnt.sum() >= n
+        for m in range(4):
+            b = ctx.read_bins(m)
+            assert np.all((b["min"] >= 0) & (b["max"] <= 1) & (b["min"] <= b["max"]))
+            e = np.minimum(np.floor(b["mean"].astype(np.float32) * np.float32(T)).astype(np.int64), T - 1)
+            assert np.array_equal(b["y"], tf[m][e])
+    finally:
+        for m in logm:
+            ctx.set_field_scale(m, dvl.SCALE_LINEAR)
