@@ -391,7 +391,7 @@ def run_ours(args):
     log_first_ms = (time.perf_counter() - t0) * 1e3
     r0.record(stream)
     for i in range(10):
-        ctx.set_tfs(tfs[i])
+        ctx.set_tfs(tfs[i % len(tfs)])
         ctx.update(**kw)
     r1.record(stream)
     r1.synchronize()

@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "bulk.cuh"
 #include "cell_math.cuh"
 #include "consts.cuh"
 #include "dvl_internal.h"
@@ -117,6 +118,60 @@ __device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, con
     return widths4_of<M, PM, FULLSTEP, P2>(cc, a, s_tf, cm, idx, v, L4);
 }
 
+// Warp 0 of a pass-A CTA, after the chunk totals are in s_wsum: chunk
+// offsets within the tile, the tile's exclusive prefix by decoupled look-back
+// (bounded waits), the chunk prefixes, and F after the last tile.
+__device__ __forceinline__ void tile_scan(const UpdateArgs& a, uint32_t tile, uint32_t n_tiles, int lane,
+                                          const unsigned long long* s_wsum)
+{
+    unsigned long long w = lane < WARPS ? s_wsum[lane] : 0ull;
+    unsigned long long incl = warp_incl_scan_u64(w, lane);
+    const unsigned long long agg = __shfl_sync(FULL, incl, WARPS - 1);
+    unsigned long long* status = a.tile_status;
+    const bool skip = a.fault_no_publish && tile == 0;
+    if (lane == 0 && !skip) st_relaxed(status + tile, (tile == 0 ? FLAG_P : FLAG_A) | agg);
+    unsigned long long excl = 0;
+    if (tile > 0) {
+        int64_t end = (int64_t)tile - 1;          // window [end-31, end]
+        while (true) {
+            const int64_t j = end - lane;
+            unsigned long long s = FLAG_P;        // beyond tile 0: neutral
+            if (j >= 0) {
+                long long spins = 0;
+                while (true) {
+                    s = ld_relaxed(status + j);
+                    if (s >> 62) break;
+                    if (++spins > a.spin_limit) {
+                        atomicOr(a.err, ERR_TIMEOUT);
+                        s = FLAG_P;               // give up: count it as 0
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+            }
+            const unsigned pmask = __ballot_sync(FULL, (s & FLAG_P) != 0);
+            // lanes up to and including the nearest inclusive prefix contribute
+            const int first = pmask ? __ffs(pmask) - 1 : 31;
+            unsigned long long contrib = lane <= first ? (s & VAL_MASK) : 0ull;
+            excl += warp_sum_u64(contrib);
+            if (pmask) break;
+            end -= 32;
+        }
+        if (lane == 0 && !skip) st_relaxed(status + tile, FLAG_P | (excl + agg));
+    }
+    if (lane < WARPS) a.chunk_prefix[(uint64_t)tile * WARPS + lane] = excl + incl - w;
+    if (lane == 0 && tile == n_tiles - 1) {
+        UpdateConsts* C = a.consts;
+        unsigned long long F = excl + agg;
+        int linear = 0;
+        if (F == 0 && a.n > 0) { F = a.n; linear = 1; }   // all widths 0: equal widths
+        C->F = F;
+        C->linear = linear;
+        C->F_div_W = F / a.W;
+        C->F_mod_W = F % a.W;
+    }
+}
+
 // P2: the table size is a power of two (fast TF entries, see width_p2)
 template <int M, int PM, bool P2>
 __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_tiles)
@@ -185,54 +240,125 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
     if (lane == 0) s_wsum[warp] = acc;
     __syncthreads();
     if (warp != 0) return;
+    tile_scan(a, tile, n_tiles, lane, s_wsum);
+}
 
-    // warp 0: chunk offsets within the tile, then the tile's exclusive prefix
-    unsigned long long w = lane < WARPS ? s_wsum[lane] : 0ull;
-    unsigned long long incl = warp_incl_scan_u64(w, lane);
-    const unsigned long long agg = __shfl_sync(FULL, incl, WARPS - 1);
-    unsigned long long* status = a.tile_status;
-    const bool skip = a.fault_no_publish && tile == 0;
-    if (lane == 0 && !skip) st_relaxed(status + tile, (tile == 0 ? FLAG_P : FLAG_A) | agg);
-    unsigned long long excl = 0;
-    if (tile > 0) {
-        int64_t end = (int64_t)tile - 1;          // window [end-31, end]
-        while (true) {
-            const int64_t j = end - lane;
-            unsigned long long s = FLAG_P;        // beyond tile 0: neutral
-            if (j >= 0) {
-                long long spins = 0;
-                while (true) {
-                    s = ld_relaxed(status + j);
-                    if (s >> 62) break;
-                    if (++spins > a.spin_limit) {
-                        atomicOr(a.err, ERR_TIMEOUT);
-                        s = FLAG_P;               // give up: count it as 0
-                        break;
-                    }
-                    __nanosleep(100);
-                }
-            }
-            const unsigned pmask = __ballot_sync(FULL, (s & FLAG_P) != 0);
-            // lanes up to and including the nearest inclusive prefix contribute
-            const int first = pmask ? __ffs(pmask) - 1 : 31;
-            unsigned long long contrib = lane <= first ? (s & VAL_MASK) : 0ull;
-            excl += warp_sum_u64(contrib);
-            if (pmask) break;
-            end -= 32;
+// Pass A with the cells streamed into shared memory by bulk copies.  Every
+// warp owns a ring of D slots, one warp step (128 cells: M field rows of 512 B
+// and 128 level bytes) each; its lane 0 keeps D steps in flight, refilling a
+// slot as soon as the warp has read it, so that a warp's loads no longer wait
+// on its own arithmetic and the bytes in flight do not cost registers.  Step
+// totals come from two warp reductions per step (no per-lane table).  The
+// partial last chunk reads global memory directly.  The scan is pass A's.
+constexpr uint32_t RING_WAIT_POLLS = 4096;      // mbarrier polls (<= 1 ms each) before a wait gives up
+
+template <int M>
+__device__ __forceinline__ void ring_issue(uint32_t slot, uint32_t bar, const UpdateArgs& a, uint64_t idx)
+{
+    mbar_arrive_expect_tx(bar, (uint32_t)(M * STEP * 4 + STEP));
+#pragma unroll
+    for (int m = 0; m < M; ++m) bulk_g2s(slot + (uint32_t)(m * STEP * 4), a.val + m * a.pitch + idx, STEP * 4, bar);
+    bulk_g2s(slot + (uint32_t)(M * STEP * 4), a.lev + idx, STEP, bar);
+}
+
+template <int M, int PM, bool P2, int D, int MINB>
+__global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, uint32_t n_tiles, uint32_t tf_bytes)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr uint32_t SLOT = M * STEP * 4 + STEP;
+    float* s_tf = reinterpret_cast<float*>(smem);
+    __shared__ unsigned long long s_wsum[WARPS];
+    __shared__ uint32_t s_tile;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned char* ring = smem + tf_bytes + (size_t)warp * D * SLOT;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t ring_s = sbase + tf_bytes + (uint32_t)warp * D * SLOT;
+    const uint32_t bar_s = sbase + tf_bytes + (uint32_t)(WARPS * D * SLOT) + (uint32_t)warp * D * 8u;
+    // The first D steps of the tile a CTA usually gets (its block index) are
+    // requested before the ticket is known (see k_passA).
+    const uint32_t guess = blockIdx.x;
+    const uint64_t gbase = ((uint64_t)guess * WARPS + warp) * CHUNK;
+    const bool gfull = gbase + CHUNK <= a.n;
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) mbar_init(bar_s + 8u * k, 1);
+        mbar_init_fence();
+        if (gfull) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) ring_issue<M>(ring_s + k * SLOT, bar_s + 8u * k, a, gbase + k * STEP);
         }
-        if (lane == 0 && !skip) st_relaxed(status + tile, FLAG_P | (excl + agg));
     }
-    if (lane < WARPS) a.chunk_prefix[(uint64_t)tile * WARPS + lane] = excl + incl - w;
-    if (lane == 0 && tile == n_tiles - 1) {
-        UpdateConsts* C = a.consts;
-        unsigned long long F = excl + agg;
-        int linear = 0;
-        if (F == 0 && a.n > 0) { F = a.n; linear = 1; }   // all widths 0: equal widths
-        C->F = F;
-        C->linear = linear;
-        C->F_div_W = F / a.W;
-        C->F_mod_W = F % a.W;
+    __syncwarp();
+    load_table<M>(s_tf, a.tf, a.T);
+    if (tid == 0) s_tile = atomicAdd(&a.counters[0], 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t chunk = (uint64_t)tile * WARPS + warp;
+    const uint64_t base = chunk * CHUNK;
+    const bool full = base + CHUNK <= a.n;
+    uint32_t phase = 0;           // parity of the slots' next phase
+    bool late = false;            // a wait gave up
+    if (tile != guess) {
+        if (gfull) {              // the early copies belong to another tile: let them land
+#pragma unroll
+            for (int k = 0; k < D; ++k) late |= !mbar_wait(bar_s + 8u * k, 0, RING_WAIT_POLLS);
+            phase = 1;
+            __syncwarp();
+        }
+        if (full && lane == 0) {
+            proxy_fence_shared();
+#pragma unroll
+            for (int k = 0; k < D; ++k) ring_issue<M>(ring_s + k * SLOT, bar_s + 8u * k, a, base + k * STEP);
+        }
     }
+    Cell<M, PM> cc;
+    cc.load(a.consts, a.T);
+    uint32_t cm[M];
+    const uint32_t sb = (uint32_t)__cvta_generic_to_shared(s_tf);
+#pragma unroll
+    for (int m = 0; m < M; ++m) cm[m] = sb + 4u * (uint32_t)(m * (a.T + 1)) - 4u * BITS_2P23;
+
+    unsigned long long acc = 0, mine = 0;
+    if (full) {
+        int k = 0;
+#pragma unroll 1
+        for (int st = 0; st < STEPS; ++st) {
+            late |= !mbar_wait(bar_s + 8u * k, phase, RING_WAIT_POLLS);
+            float v[4][M];
+            const float4* f4 = reinterpret_cast<const float4*>(ring + k * SLOT);
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const float4 x = f4[m * 32 + lane];
+                v[0][m] = x.x; v[1][m] = x.y; v[2][m] = x.z; v[3][m] = x.w;
+            }
+            const uint32_t L4 = reinterpret_cast<const uint32_t*>(ring + k * SLOT + M * STEP * 4)[lane];
+            __syncwarp();             // every lane has read the slot
+            if (lane == 0 && st + D < STEPS) {
+                proxy_fence_shared();
+                ring_issue<M>(ring_s + k * SLOT, bar_s + 8u * k, a, base + (st + D) * STEP);
+            }
+            const unsigned long long l =
+                widths4_of<M, PM, true, P2>(cc, a, s_tf, cm, base + st * STEP + lane * 4, v, L4);
+            const unsigned long long tot = warp_total_small(l);
+            if (lane == st) mine = tot;
+            acc += tot;
+            if (++k == D) { k = 0; phase ^= 1u; }
+        }
+    } else {
+        for (int st = 0; st < STEPS; ++st) {
+            const uint64_t idx = base + st * STEP + lane * 4;
+            const unsigned long long l = idx < a.n ? widths4<M, PM, false, P2>(cc, a, s_tf, cm, idx) : 0ull;
+            const unsigned long long tot = warp_total_small(l);
+            if (lane == st) mine = tot;
+            acc += tot;
+        }
+    }
+    if (late && lane == 0) atomicOr(a.err, ERR_TIMEOUT);
+    if (a.step_sums && lane < STEPS) a.step_sums[chunk * STEPS + lane] = mine;
+    if (lane == 0) s_wsum[warp] = acc;
+    __syncthreads();
+    if (warp != 0) return;
+    tile_scan(a, tile, n_tiles, lane, s_wsum);
 }
 
 // ---------------------------------------------------------------------------
@@ -935,6 +1061,36 @@ int grid_cap(uint64_t work, int threads)
     return b ? (int)b : 1;
 }
 
+// Ring depth and register cap: D = 3 steps per warp with 4 CTAs per SM
+// (64 registers, 57 KB of shared memory with 256-entry tables) for up to 4
+// fields; wider cells keep 2 steps and 2 CTAs.
+template <int M> constexpr int ring_depth() { return M <= 4 ? 3 : 2; }
+template <int M> constexpr int ring_min_blocks() { return M <= 4 ? 4 : 2; }
+
+template <int M>
+size_t ring_smem(uint32_t T, uint32_t* tf_bytes)
+{
+    *tf_bytes = (uint32_t)(((size_t)M * (T + 1) * sizeof(float) + 127) & ~(size_t)127);
+    return *tf_bytes + (size_t)WARPS * ring_depth<M>() * (M * STEP * 4 + STEP + 8);
+}
+
+template <int M, int PM>
+cudaError_t launch_passA_ring(cudaStream_t s, const UpdateArgs& a, uint32_t n_tiles, bool p2)
+{
+    constexpr int D = ring_depth<M>(), MB = ring_min_blocks<M>();
+    uint32_t tf_bytes;
+    const size_t smem = ring_smem<M>(a.T, &tf_bytes);
+    cudaError_t e;
+    if (p2) {
+        if ((e = smem_attr(k_passA_ring<M, PM, true, D, MB>, smem)) != cudaSuccess) return e;
+        k_passA_ring<M, PM, true, D, MB><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles, tf_bytes);
+    } else {
+        if ((e = smem_attr(k_passA_ring<M, PM, false, D, MB>, smem)) != cudaSuccess) return e;
+        k_passA_ring<M, PM, false, D, MB><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles, tf_bytes);
+    }
+    return cudaSuccess;
+}
+
 template <int M, int PM>
 cudaError_t run_passes(cudaStream_t s, const UpdateArgs& a, uint32_t n_tiles, size_t smem)
 {
@@ -945,10 +1101,17 @@ cudaError_t run_passes(cudaStream_t s, const UpdateArgs& a, uint32_t n_tiles, si
     if ((e = smem_attr(k_passB<M, PM>, smem)) != cudaSuccess) return e;
     if ((e = smem_attr(k_passB_steps<M, PM, false>, smem)) != cudaSuccess) return e;
     if ((e = smem_attr(k_passB_steps<M, PM, true>, smem)) != cudaSuccess) return e;
+    // the bulk copies need 16-byte aligned rows (they read whole chunks only)
+    const bool ring = ((uintptr_t)a.val % 16 == 0) && ((uintptr_t)a.lev % 16 == 0) && (a.pitch % 4 == 0);
     if (a.events) cudaEventRecord(a.events[1], s);
     if (n_tiles) {
-        if (p2) k_passA<M, PM, true><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles);
-        else k_passA<M, PM, false><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles);
+        if (ring) {
+            if ((e = launch_passA_ring<M, PM>(s, a, n_tiles, p2)) != cudaSuccess) return e;
+        } else if (p2) {
+            k_passA<M, PM, true><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles);
+        } else {
+            k_passA<M, PM, false><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles);
+        }
     }
     if (a.events) cudaEventRecord(a.events[2], s);
     if (a.vt) return cudaSuccess;          // bins come from range queries (see run_update)

@@ -73,6 +73,25 @@ def test_noalloc_matches_update_on_two_calls():
             got = {k: v.cpu().numpy() for k, v in out.items()}
             for m in range(M):
                 _compare(ref[m], got, m, W, alpha.shape[1])
+        # levels only 4-byte aligned: pass A reads the cells directly instead
+        # of through bulk copies (which need 16-byte aligned rows)
+        lev_store = torch.zeros(pitch + 16, dtype=torch.uint8, device=dev)
+        d_level4 = lev_store[4:4 + pitch]
+        d_level4.copy_(d_level)
+        kw = dict(P=1.0, min_importance=0.025, width=700)
+        alpha = synth.random_tfs(5)
+        ref = _reference(ctx, alpha, **kw)
+        out = {k: torch.full((M * 700,), 7, dtype=dt, device=dev) for k, dt in
+               [("mean", torch.float32), ("min", torch.float32), ("max", torch.float32),
+                ("y", torch.float32), ("sum", torch.float64)]}
+        out["count"] = torch.full((700,), 7, dtype=torch.int32, device=dev)
+        assert d_level4.data_ptr() % 16 == 4
+        rc = dvl.dvl_update_noalloc(stream, d_fields, pitch, d_level4, torch.from_numpy(alpha).to(dev),
+                                    [nan] * (2 * M), out, n_cells=n, **kw)
+        assert rc == dvl.OK
+        got = {k: v.cpu().numpy() for k, v in out.items()}
+        for m in range(M):
+            _compare(ref[m], got, m, 700, alpha.shape[1])
         # sizes beyond the fixed scratch are refused before any GPU work
         rc = dvl.dvl_update_noalloc(stream, d_fields, pitch, d_level, torch.from_numpy(alpha).to(dev),
                                     [nan] * (2 * M), out, n_cells=476_749_825, width=333)
