@@ -278,10 +278,13 @@ int dvl_get_timings(dvl_ctx* ctx, double* ms, int n);
 /* Tuning and fault-injection options (for tests).
  *   DVL_OPT_SPIN_LIMIT      iteration limit of every device-side wait
  *                           (default 1<<22; each iteration sleeps ~100 ns)
- *   DVL_OPT_FAULT_NO_PUBLISH  1 = the first tile of the next update's prefix
- *                           scan never publishes its sum, so successors' waits
- *                           run out (tests DVL_ERR_TIMEOUT); reset after one
- *                           update.
+ *   DVL_OPT_FAULT_NO_PUBLISH  1 = in the next update's width pass, a bounded
+ *                           device-side wait is made to run out (tests
+ *                           DVL_ERR_TIMEOUT): the first warp waits on a signal
+ *                           that nothing sends or, where that pass reads the
+ *                           cells directly (rows not 16-byte aligned), the
+ *                           first tile of its look-back scan never publishes
+ *                           its sum; reset after one update.
  *   DVL_OPT_TIMING          1 = record per-stage CUDA events in every
  *                           dvl_update (read with dvl_get_timings); 0 = off
  *                           (default).  A timed dvl_update_batch runs its

@@ -35,6 +35,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+// Plain arrival (release at CTA scope): completes the phase of a barrier
+// initialised with count 1.
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // dst (shared), src (global) 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
 {
@@ -59,11 +66,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity, uin
 constexpr uint32_t MBAR_SUSPEND_NS = 1000000;   // 1 ms per poll at most
 
 // Waits for the phase with the given parity, at most `limit` polls of at
-// most MBAR_SUSPEND_NS each.  Returns false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit)
+// most `suspend_ns` each.  Returns false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit,
+                                          uint32_t suspend_ns = MBAR_SUSPEND_NS)
 {
     for (uint32_t i = 0; i < limit; ++i)
-        if (mbar_try_wait(bar, parity, MBAR_SUSPEND_NS)) return true;
+        if (mbar_try_wait(bar, parity, suspend_ns)) return true;
     return false;
 }
 

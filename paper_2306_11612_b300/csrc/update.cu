@@ -118,13 +118,12 @@ __device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, con
     return widths4_of<M, PM, FULLSTEP, P2>(cc, a, s_tf, cm, idx, v, L4);
 }
 
-// Warp 0 of a pass-A CTA, after the chunk totals are in s_wsum: chunk
+// One warp of a pass-A CTA, with the tile's chunk totals in lanes 0..7: chunk
 // offsets within the tile, the tile's exclusive prefix by decoupled look-back
 // (bounded waits), the chunk prefixes, and F after the last tile.
 __device__ __forceinline__ void tile_scan(const UpdateArgs& a, uint32_t tile, uint32_t n_tiles, int lane,
-                                          const unsigned long long* s_wsum)
+                                          unsigned long long w /* lane < WARPS: chunk total of warp lane */)
 {
-    unsigned long long w = lane < WARPS ? s_wsum[lane] : 0ull;
     unsigned long long incl = warp_incl_scan_u64(w, lane);
     const unsigned long long agg = __shfl_sync(FULL, incl, WARPS - 1);
     unsigned long long* status = a.tile_status;
@@ -240,77 +239,74 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
     if (lane == 0) s_wsum[warp] = acc;
     __syncthreads();
     if (warp != 0) return;
-    tile_scan(a, tile, n_tiles, lane, s_wsum);
+    tile_scan(a, tile, n_tiles, lane, lane < WARPS ? s_wsum[lane] : 0ull);
 }
 
-// Pass A with the cells streamed into shared memory by bulk copies.  Every
-// warp owns a ring of D slots, one warp step (128 cells: M field rows of 512 B
-// and 128 level bytes) each; its lane 0 keeps D steps in flight, refilling a
-// slot as soon as the warp has read it, so that a warp's loads no longer wait
-// on its own arithmetic and the bytes in flight do not cost registers.  Step
-// totals come from two warp reductions per step (no per-lane table).  The
-// partial last chunk reads global memory directly.  The scan is pass A's.
+// Pass A with the cells streamed into shared memory by bulk copies, in a
+// persistent grid (as many CTAs as fit on the GPU at once) whose warps run
+// independently: global warp g handles chunks g, g + G, g + 2G, ... (G warps
+// in the grid) and writes each chunk's width total; k_chunk_reduce and
+// k_chunk_scan then turn the totals into the exclusive chunk prefixes and F.
+// No warp ever waits for another (no tile barrier, no look-back), so the
+// stream of copies never stalls on the scan's chain of tiles.
+//
+// Every warp owns a ring of D slots, one warp step (128 cells: M field rows of
+// 512 B and 128 level bytes) each.  Its lane 0 keeps D steps in flight,
+// refilling a slot as soon as the warp has read it and running on into the
+// warp's next chunk, so a warp's loads never wait on its own arithmetic and
+// the bytes in flight cost no registers.  Step totals come from two warp
+// reductions per step.  Partial chunks (the data set's end) read global
+// memory directly.
 constexpr uint32_t RING_WAIT_POLLS = 4096;      // mbarrier polls (<= 1 ms each) before a wait gives up
 
+// Requests warp step idx into a slot: lanes 0..M-1 copy one field row each,
+// lane M the levels, lane 0 arms the barrier with the step's byte count (a
+// copy may complete first: the phase cannot end before that arrival).  Called
+// by the whole warp after every lane has finished reading the slot.
 template <int M>
-__device__ __forceinline__ void ring_issue(uint32_t slot, uint32_t bar, const UpdateArgs& a, uint64_t idx)
+__device__ __forceinline__ void ring_issue(int lane, uint32_t slot, uint32_t bar, const UpdateArgs& a, uint64_t idx)
 {
-    mbar_arrive_expect_tx(bar, (uint32_t)(M * STEP * 4 + STEP));
-#pragma unroll
-    for (int m = 0; m < M; ++m) bulk_g2s(slot + (uint32_t)(m * STEP * 4), a.val + m * a.pitch + idx, STEP * 4, bar);
-    bulk_g2s(slot + (uint32_t)(M * STEP * 4), a.lev + idx, STEP, bar);
+    if (lane <= M) {
+        proxy_fence_shared();          // the warp's reads of the slot before the copy's writes
+        if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(M * STEP * 4 + STEP));
+        if (lane < M) bulk_g2s(slot + (uint32_t)(lane * STEP * 4), a.val + lane * a.pitch + idx, STEP * 4, bar);
+        else bulk_g2s(slot + (uint32_t)(M * STEP * 4), a.lev + idx, STEP, bar);
+    }
 }
 
+// chunk totals go to chunk_prefix (turned into prefixes by k_chunk_scan)
 template <int M, int PM, bool P2, int D, int MINB>
-__global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, uint32_t n_tiles, uint32_t tf_bytes)
+__global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, uint64_t n_chunks, uint32_t tf_bytes)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr uint32_t SLOT = M * STEP * 4 + STEP;
     float* s_tf = reinterpret_cast<float*>(smem);
-    __shared__ unsigned long long s_wsum[WARPS];
-    __shared__ uint32_t s_tile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned char* ring = smem + tf_bytes + (size_t)warp * D * SLOT;
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const uint32_t ring_s = sbase + tf_bytes + (uint32_t)warp * D * SLOT;
     const uint32_t bar_s = sbase + tf_bytes + (uint32_t)(WARPS * D * SLOT) + (uint32_t)warp * D * 8u;
-    // The first D steps of the tile a CTA usually gets (its block index) are
-    // requested before the ticket is known (see k_passA).
-    const uint32_t guess = blockIdx.x;
-    const uint64_t gbase = ((uint64_t)guess * WARPS + warp) * CHUNK;
-    const bool gfull = gbase + CHUNK <= a.n;
+    const uint64_t G = (uint64_t)gridDim.x * WARPS;
+    uint64_t chunk = (uint64_t)blockIdx.x * WARPS + warp;
+    auto full = [&](uint64_t c) { return c < n_chunks && (c + 1) * CHUNK <= a.n; };
+    bool cur_full = full(chunk);
+    // fault injection (tests): the first warp also waits on a barrier that
+    // nothing completes, so its bounded wait runs out
+    const uint32_t never_s = sbase + tf_bytes + (uint32_t)(WARPS * D * SLOT) + (uint32_t)(WARPS * D * 8);
+    const bool inject = a.fault_no_publish && blockIdx.x == 0 && warp == 0;
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < D; ++k) mbar_init(bar_s + 8u * k, 1);
+        if (tid == 0) mbar_init(never_s, 1);
         mbar_init_fence();
-        if (gfull) {
-#pragma unroll
-            for (int k = 0; k < D; ++k) ring_issue<M>(ring_s + k * SLOT, bar_s + 8u * k, a, gbase + k * STEP);
-        }
     }
     __syncwarp();
-    load_table<M>(s_tf, a.tf, a.T);
-    if (tid == 0) s_tile = atomicAdd(&a.counters[0], 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    const uint64_t chunk = (uint64_t)tile * WARPS + warp;
-    const uint64_t base = chunk * CHUNK;
-    const bool full = base + CHUNK <= a.n;
-    uint32_t phase = 0;           // parity of the slots' next phase
-    bool late = false;            // a wait gave up
-    if (tile != guess) {
-        if (gfull) {              // the early copies belong to another tile: let them land
+    if (cur_full) {
 #pragma unroll
-            for (int k = 0; k < D; ++k) late |= !mbar_wait(bar_s + 8u * k, 0, RING_WAIT_POLLS);
-            phase = 1;
-            __syncwarp();
-        }
-        if (full && lane == 0) {
-            proxy_fence_shared();
-#pragma unroll
-            for (int k = 0; k < D; ++k) ring_issue<M>(ring_s + k * SLOT, bar_s + 8u * k, a, base + k * STEP);
-        }
+        for (int k = 0; k < D; ++k) ring_issue<M>(lane, ring_s + k * SLOT, bar_s + 8u * k, a, chunk * CHUNK + k * STEP);
     }
+    load_table<M>(s_tf, a.tf, a.T);
+    __syncthreads();
     Cell<M, PM> cc;
     cc.load(a.consts, a.T);
     uint32_t cm[M];
@@ -318,47 +314,139 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
 #pragma unroll
     for (int m = 0; m < M; ++m) cm[m] = sb + 4u * (uint32_t)(m * (a.T + 1)) - 4u * BITS_2P23;
 
-    unsigned long long acc = 0, mine = 0;
-    if (full) {
-        int k = 0;
+    int k = 0;                         // next slot to consume
+    uint32_t phase = 0;                // its parity
+    bool late = false;                 // a wait gave up
+    const bool injected = inject && !mbar_wait(never_s, 0, (uint32_t)min((int64_t)RING_WAIT_POLLS, a.spin_limit),
+                                               1000u);
+    for (; chunk < n_chunks; chunk += G) {
+        const uint64_t base = chunk * CHUNK;
+        const uint64_t nxt = chunk + G;
+        const bool nxt_full = full(nxt);
+        unsigned long long acc = 0, mine = 0;
+        if (cur_full) {
 #pragma unroll 1
-        for (int st = 0; st < STEPS; ++st) {
-            late |= !mbar_wait(bar_s + 8u * k, phase, RING_WAIT_POLLS);
-            float v[4][M];
-            const float4* f4 = reinterpret_cast<const float4*>(ring + k * SLOT);
+            for (int st = 0; st < STEPS; ++st) {
+                if (!late) late = !mbar_wait(bar_s + 8u * k, phase, RING_WAIT_POLLS);   // after one
+                float v[4][M];                                                         // give-up: no more waits
+                const float4* f4 = reinterpret_cast<const float4*>(ring + k * SLOT);
 #pragma unroll
-            for (int m = 0; m < M; ++m) {
-                const float4 x = f4[m * 32 + lane];
-                v[0][m] = x.x; v[1][m] = x.y; v[2][m] = x.z; v[3][m] = x.w;
+                for (int m = 0; m < M; ++m) {
+                    const float4 x = f4[m * 32 + lane];
+                    v[0][m] = x.x; v[1][m] = x.y; v[2][m] = x.z; v[3][m] = x.w;
+                }
+                const uint32_t L4 = reinterpret_cast<const uint32_t*>(ring + k * SLOT + M * STEP * 4)[lane];
+                __syncwarp();             // every lane has read the slot
+                {
+                    const int s2 = st + D;
+                    if (s2 < STEPS)
+                        ring_issue<M>(lane, ring_s + k * SLOT, bar_s + 8u * k, a, base + s2 * STEP);
+                    else if (nxt_full)
+                        ring_issue<M>(lane, ring_s + k * SLOT, bar_s + 8u * k, a, nxt * CHUNK + (s2 - STEPS) * STEP);
+                }
+                const unsigned long long l =
+                    widths4_of<M, PM, true, P2>(cc, a, s_tf, cm, base + st * STEP + lane * 4, v, L4);
+                const unsigned long long tot = warp_total_small(l);
+                if (lane == st) mine = tot;
+                acc += tot;
+                if (++k == D) { k = 0; phase ^= 1u; }
             }
-            const uint32_t L4 = reinterpret_cast<const uint32_t*>(ring + k * SLOT + M * STEP * 4)[lane];
-            __syncwarp();             // every lane has read the slot
-            if (lane == 0 && st + D < STEPS) {
-                proxy_fence_shared();
-                ring_issue<M>(ring_s + k * SLOT, bar_s + 8u * k, a, base + (st + D) * STEP);
+        } else {
+            if (nxt_full) {
+                // nothing of this chunk is in flight: the next one's first steps
+                int kk = k;
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    ring_issue<M>(lane, ring_s + kk * SLOT, bar_s + 8u * kk, a, nxt * CHUNK + j * STEP);
+                    if (++kk == D) kk = 0;
+                }
             }
-            const unsigned long long l =
-                widths4_of<M, PM, true, P2>(cc, a, s_tf, cm, base + st * STEP + lane * 4, v, L4);
-            const unsigned long long tot = warp_total_small(l);
-            if (lane == st) mine = tot;
-            acc += tot;
-            if (++k == D) { k = 0; phase ^= 1u; }
+            for (int st = 0; st < STEPS; ++st) {
+                const uint64_t idx = base + st * STEP + lane * 4;
+                const unsigned long long l = idx < a.n ? widths4<M, PM, false, P2>(cc, a, s_tf, cm, idx) : 0ull;
+                const unsigned long long tot = warp_total_small(l);
+                if (lane == st) mine = tot;
+                acc += tot;
+            }
         }
-    } else {
-        for (int st = 0; st < STEPS; ++st) {
-            const uint64_t idx = base + st * STEP + lane * 4;
-            const unsigned long long l = idx < a.n ? widths4<M, PM, false, P2>(cc, a, s_tf, cm, idx) : 0ull;
-            const unsigned long long tot = warp_total_small(l);
-            if (lane == st) mine = tot;
-            acc += tot;
-        }
+        if (a.step_sums && lane < STEPS) a.step_sums[chunk * STEPS + lane] = mine;
+        if (lane == 0) a.chunk_prefix[chunk] = acc;
+        cur_full = nxt_full;
     }
-    if (late && lane == 0) atomicOr(a.err, ERR_TIMEOUT);
-    if (a.step_sums && lane < STEPS) a.step_sums[chunk * STEPS + lane] = mine;
-    if (lane == 0) s_wsum[warp] = acc;
+    if ((late || injected) && lane == 0) atomicOr(a.err, ERR_TIMEOUT);
+}
+
+// The chunk totals (in chunk_prefix) become exclusive prefixes, in two small
+// launches over blocks of SCAN_SPAN chunks: block sums, then per block the sum
+// of the earlier blocks' sums plus a block-local scan.  The last block also
+// writes F (Eq. 4's total) and the all-zero fallback, as tile_scan does.
+constexpr int SCAN_THREADS = 256, SCAN_PER_THREAD = 8, SCAN_SPAN = SCAN_THREADS * SCAN_PER_THREAD;
+
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x, unsigned long long* s_red)
+{
+    x = warp_sum_u64(x);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_red[warp] = x;
     __syncthreads();
-    if (warp != 0) return;
-    tile_scan(a, tile, n_tiles, lane, s_wsum);
+    unsigned long long t = lane < (int)(blockDim.x >> 5) ? s_red[lane] : 0ull;
+    t = warp_sum_u64(t);
+    __syncthreads();
+    return t;
+}
+
+__global__ __launch_bounds__(SCAN_THREADS) void k_chunk_reduce(const unsigned long long* __restrict__ tot,
+                                                               uint64_t n_chunks, unsigned long long* blk)
+{
+    __shared__ unsigned long long s_red[SCAN_THREADS / 32];
+    const uint64_t b0 = (uint64_t)blockIdx.x * SCAN_SPAN;
+    unsigned long long x = 0;
+    for (int j = 0; j < SCAN_PER_THREAD; ++j) {
+        const uint64_t c = b0 + (uint64_t)j * SCAN_THREADS + threadIdx.x;
+        if (c < n_chunks) x += tot[c];
+    }
+    x = block_sum_u64(x, s_red);
+    if (threadIdx.x == 0) blk[blockIdx.x] = x;
+}
+
+__global__ __launch_bounds__(SCAN_THREADS) void k_chunk_scan(UpdateArgs a, uint64_t n_chunks,
+                                                             const unsigned long long* __restrict__ blk)
+{
+    __shared__ unsigned long long s_red[SCAN_THREADS / 32];
+    __shared__ unsigned long long s_warp[SCAN_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // sum of the earlier blocks
+    unsigned long long pre = 0;
+    for (uint32_t b = tid; b < blockIdx.x; b += SCAN_THREADS) pre += blk[b];
+    pre = block_sum_u64(pre, s_red);
+    // block-local exclusive scan: thread tid holds chunks b0 + tid*8 .. +8
+    const uint64_t c0 = (uint64_t)blockIdx.x * SCAN_SPAN + (uint64_t)tid * SCAN_PER_THREAD;
+    unsigned long long v[SCAN_PER_THREAD], t = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_PER_THREAD; ++j) {
+        v[j] = c0 + j < n_chunks ? a.chunk_prefix[c0 + j] : 0ull;
+        t += v[j];
+    }
+    const unsigned long long incl = warp_incl_scan_u64(t, lane);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    unsigned long long wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += s_warp[w];
+    unsigned long long run = pre + wpre + incl - t;
+#pragma unroll
+    for (int j = 0; j < SCAN_PER_THREAD; ++j) {
+        if (c0 + j < n_chunks) a.chunk_prefix[c0 + j] = run;
+        run += v[j];
+    }
+    if (blockIdx.x == gridDim.x - 1 && tid == SCAN_THREADS - 1) {
+        UpdateConsts* C = a.consts;
+        unsigned long long F = run;       // the last thread's running sum is the total
+        int linear = 0;
+        if (F == 0 && a.n > 0) { F = a.n; linear = 1; }   // all widths 0: equal widths
+        C->F = F;
+        C->linear = linear;
+        C->F_div_W = F / a.W;
+        C->F_mod_W = F % a.W;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1061,17 +1149,43 @@ int grid_cap(uint64_t work, int threads)
     return b ? (int)b : 1;
 }
 
-// Ring depth and register cap: D = 3 steps per warp with 4 CTAs per SM
-// (64 registers, 57 KB of shared memory with 256-entry tables) for up to 4
-// fields; wider cells keep 2 steps and 2 CTAs.
-template <int M> constexpr int ring_depth() { return M <= 4 ? 3 : 2; }
+// Ring depth and register cap: D = 2 steps per warp, 4 CTAs per SM (64
+// registers, 40 KB of shared memory with 256-entry tables) for up to 4 fields,
+// 2 CTAs for wider cells.  (Measured on the 413.6M-cell case: depth 3 or 4
+// and 5 CTAs with a 48-register cap were 0.5-1.5 % slower.)
+template <int M> constexpr int ring_depth() { return 2; }
 template <int M> constexpr int ring_min_blocks() { return M <= 4 ? 4 : 2; }
 
 template <int M>
 size_t ring_smem(uint32_t T, uint32_t* tf_bytes)
 {
     *tf_bytes = (uint32_t)(((size_t)M * (T + 1) * sizeof(float) + 127) & ~(size_t)127);
-    return *tf_bytes + (size_t)WARPS * ring_depth<M>() * (M * STEP * 4 + STEP + 8);
+    return *tf_bytes + (size_t)WARPS * ring_depth<M>() * (M * STEP * 4 + STEP + 8) + 8;
+}
+
+// The persistent grid: as many CTAs as are resident at once (the occupancy of
+// the kernel at this shared-memory size, cached per thread for the last key).
+template <typename K>
+cudaError_t resident_ctas(K kernel, size_t smem, int* out)
+{
+    thread_local const void* last_k = nullptr;
+    thread_local size_t last_smem = 0;
+    thread_local int last_dev = -1, last_n = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (last_k != (const void*)kernel || last_smem != smem || last_dev != dev) {
+        int per_sm = 0, sms = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, WARPS * 32, smem)) != cudaSuccess)
+            return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        last_k = (const void*)kernel;
+        last_smem = smem;
+        last_dev = dev;
+        last_n = (per_sm > 0 ? per_sm : 1) * sms;
+    }
+    *out = last_n;
+    return cudaSuccess;
 }
 
 template <int M, int PM>
@@ -1080,14 +1194,18 @@ cudaError_t launch_passA_ring(cudaStream_t s, const UpdateArgs& a, uint32_t n_ti
     constexpr int D = ring_depth<M>(), MB = ring_min_blocks<M>();
     uint32_t tf_bytes;
     const size_t smem = ring_smem<M>(a.T, &tf_bytes);
+    auto kernel = p2 ? k_passA_ring<M, PM, true, D, MB> : k_passA_ring<M, PM, false, D, MB>;
     cudaError_t e;
-    if (p2) {
-        if ((e = smem_attr(k_passA_ring<M, PM, true, D, MB>, smem)) != cudaSuccess) return e;
-        k_passA_ring<M, PM, true, D, MB><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles, tf_bytes);
-    } else {
-        if ((e = smem_attr(k_passA_ring<M, PM, false, D, MB>, smem)) != cudaSuccess) return e;
-        k_passA_ring<M, PM, false, D, MB><<<n_tiles, WARPS * 32, smem, s>>>(a, n_tiles, tf_bytes);
-    }
+    if ((e = smem_attr(kernel, smem)) != cudaSuccess) return e;
+    int grid = 0;
+    if ((e = resident_ctas(kernel, smem, &grid)) != cudaSuccess) return e;
+    if ((uint32_t)grid > n_tiles) grid = (int)n_tiles;
+    const uint64_t n_chunks = (uint64_t)n_tiles * WARPS;
+    kernel<<<grid, WARPS * 32, smem, s>>>(a, n_chunks, tf_bytes);
+    // block sums into the (here unused) tile status words, then the scan
+    const uint32_t blocks = (uint32_t)((n_chunks + SCAN_SPAN - 1) / SCAN_SPAN);
+    k_chunk_reduce<<<blocks, SCAN_THREADS, 0, s>>>(a.chunk_prefix, n_chunks, a.tile_status);
+    k_chunk_scan<<<blocks, SCAN_THREADS, 0, s>>>(a, n_chunks, a.tile_status);
     return cudaSuccess;
 }
 
