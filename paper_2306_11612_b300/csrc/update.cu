@@ -244,8 +244,9 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
 
 // Pass A with the cells streamed into shared memory by bulk copies, in a
 // persistent grid (as many CTAs as fit on the GPU at once) whose warps run
-// independently: global warp g handles chunks g, g + G, g + 2G, ... (G warps
-// in the grid) and writes each chunk's width total; k_chunk_reduce and
+// independently: global warp g starts with chunk g and claims each next chunk
+// from a counter when it starts the previous one (G warps in the grid: the
+// claims start at G), writing each chunk's width total; k_chunk_reduce and
 // k_chunk_scan then turn the totals into the exclusive chunk prefixes and F.
 // No warp ever waits for another (no tile barrier, no look-back), so the
 // stream of copies never stalls on the scan's chain of tiles.
@@ -286,8 +287,15 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const uint32_t ring_s = sbase + tf_bytes + (uint32_t)warp * D * SLOT;
     const uint32_t bar_s = sbase + tf_bytes + (uint32_t)(WARPS * D * SLOT) + (uint32_t)warp * D * 8u;
+    // first chunk by position, then the next unclaimed one from a counter
+    // (dynamic: the grid's last chunks end together whatever the chunk count)
     const uint64_t G = (uint64_t)gridDim.x * WARPS;
     uint64_t chunk = (uint64_t)blockIdx.x * WARPS + warp;
+    auto claim = [&]() {
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(&a.counters[0], 1u);
+        return G + __shfl_sync(FULL, c, 0);
+    };
     auto full = [&](uint64_t c) { return c < n_chunks && (c + 1) * CHUNK <= a.n; };
     bool cur_full = full(chunk);
     // fault injection (tests): the first warp also waits on a barrier that
@@ -319,9 +327,9 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
     bool late = false;                 // a wait gave up
     const bool injected = inject && !mbar_wait(never_s, 0, (uint32_t)min((int64_t)RING_WAIT_POLLS, a.spin_limit),
                                                1000u);
-    for (; chunk < n_chunks; chunk += G) {
+    while (chunk < n_chunks) {
         const uint64_t base = chunk * CHUNK;
-        const uint64_t nxt = chunk + G;
+        const uint64_t nxt = claim();
         const bool nxt_full = full(nxt);
         unsigned long long acc = 0, mine = 0;
         if (cur_full) {
@@ -371,6 +379,7 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
         }
         if (a.step_sums && lane < STEPS) a.step_sums[chunk * STEPS + lane] = mine;
         if (lane == 0) a.chunk_prefix[chunk] = acc;
+        chunk = nxt;
         cur_full = nxt_full;
     }
     if ((late || injected) && lane == 0) atomicOr(a.err, ERR_TIMEOUT);
