@@ -50,7 +50,7 @@ BYTES_BOUNDS_PER_PIXEL = 128 * 17 + 16 * 8 + 3 * 32 * 8 + 8 + 1 + 2 * 4 * 24
 BYTES_PIXELS_PER_PIXEL = 2 * 9 + 2 * 4 * 24 + 2 * 4 * 16 + 4 * 4 * 4 + 4 * 24 + 4
 BYTES_BINS_PER_PIXEL = BYTES_BOUNDS_PER_PIXEL + BYTES_PIXELS_PER_PIXEL
 CPU_SAMPLE_BOX = ((0, 0, 0), 32)     # 32^3 of the 128^3 base cells (1/64 of the domain)
-LAUNCHES_PER_UPDATE = 6              # prepare, width pass, chunk sums, chunk scan, pixel bounds, pixel bins
+LAUNCHES_PER_UPDATE = 5              # prepare, width pass, chunk scan, pixel bounds, pixel bins
 LOG_FIELDS = (0, 2, 3)                   # dens, pres, velmag on the log10 scale
 RASTER_H = 512                       # rows of the line-plot image
 METRIC = "DVL update throughput (cells/s per alpha-TF edit)"
@@ -1008,9 +1008,9 @@ def run_diff(args):
                          "achieved": fwd_gbs, "peak": peak, "unit": "GB/s", "frac": fwd_gbs / peak,
                          "traffic": None, "adjoint_gbs": bwd_gbs, "adjoint_frac": bwd_gbs / peak},
             "clocks": clk.summary(), "e2e": None,
-            # forward: control-point tables, prepare, width pass, chunk sums, chunk scan, alpha-means
-            # placement, finalize; adjoint: histograms, two reduction levels, chain rule
-            "gpu_launches": 11 * args.steps}
+            # forward: control-point tables, prepare, width pass, chunk scan, alpha-means placement,
+            # finalize; adjoint: histograms, two reduction levels, chain rule
+            "gpu_launches": 10 * args.steps}
     print(json.dumps(line), flush=True)
 
 

@@ -413,26 +413,22 @@ __device__ __forceinline__ void steps_minmax(const ValueTableArgs& v, uint32_t m
 // step 0, the last one ends with the last step).  A pixel inside a single
 // step reads its cells directly.
 template <int M>
-__device__ __forceinline__ void pixels_one(const UpdateArgs& a, const QueryArgs& qa, const ValueTableArgs& v,
-                                           uint32_t p)
+__device__ __forceinline__ void pixels_field(const UpdateArgs& a, const QueryArgs& qa, const ValueTableArgs& v,
+                                             uint32_t p, int m)
 {
     const bool has_l = p > 0, has_r = p + 1 < a.W;
     const uint64_t bl = (uint64_t)p * qa.hstride, br = (uint64_t)(p + 1) * qa.hstride;   // boundary entries
     const uint64_t Hn = has_r ? qa.H[br] : a.n;                    // cells with E < C(p+1)
     const uint64_t Hp = has_l ? qa.H[bl] : 0;
     const uint64_t lo_c = has_l ? (qa.S[bl] ? Hp - 1 : Hp) : 0;
-    const float Tf = (float)a.T;
+    const uint64_t k = (uint64_t)m * a.W + p;
     if (Hn == 0 || Hn - 1 < lo_c) {                                  // no cell touches p
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const uint64_t k = (uint64_t)m * a.W + p;
-            a.sum[k] = 0.0;
-            a.vmin[k] = 0u;
-            a.vmax[k] = 0u;
-            a.mean[k] = 0.0f;
-            a.y[k] = 0.0f;
-        }
-        a.count[p] = 0u;
+        a.sum[k] = 0.0;
+        a.vmin[k] = 0u;
+        a.vmax[k] = 0u;
+        a.mean[k] = 0.0f;
+        a.y[k] = 0.0f;
+        if (m == 0) a.count[p] = 0u;
         return;
     }
     const uint64_t c1 = Hn;
@@ -441,61 +437,69 @@ __device__ __forceinline__ void pixels_one(const UpdateArgs& a, const QueryArgs&
     const uint64_t sp = has_l ? (Hp - 1) / STEP : 0, sq = has_r ? (Hn - 1) / STEP : 0;
     const bool one_step = has_l && has_r && sp == sq;
     const uint64_t w0 = has_l ? sp + 1 : 0, w1 = has_r ? sq : v.n_steps;   // whole steps [w0, w1)
-#pragma unroll 1
-    for (int m = 0; m < M; ++m) {
-        float mn = 3.0f, mx = -1.0f;
-        u128 sum = 0;
-        if (one_step) {
-            const float lo = C->lo[m], sc = C->s[m];
-            for (uint64_t c = lo_c; c < c1; ++c) {
-                const float t = norm_t(__ldg(a.val + m * a.pitch + c), lo, sc);
-                sum += fx_of(t);
-                mn = fminf(mn, t);
-                mx = fmaxf(mx, t);
-            }
-        } else {
-            if (w1 > w0) {
-                steps_minmax(v, m, w0, w1, mn, mx);
-                const uint64_t row = (uint64_t)m * (v.n_steps + 1);
-                const u128 pa = ((u128)v.pre_hi[row + w0] << 64) | v.pre_lo[row + w0];
-                const u128 pb = ((u128)v.pre_hi[row + w1] << 64) | v.pre_lo[row + w1];
-                sum = pb - pa;
-            }
-            if (has_l) {
-                const uint64_t k = (bl * 2 + 1) * M + m;
-                const ulonglong2 ps = qa.psum[k];
-                const float2 mm = qa.pmm[k];
-                sum += ((u128)ps.y << 64) | ps.x;
-                mn = fminf(mn, mm.x);
-                mx = fmaxf(mx, mm.y);
-            }
-            if (has_r) {
-                const uint64_t k = (br * 2 + 0) * M + m;
-                const ulonglong2 ps = qa.psum[k];
-                const float2 mm = qa.pmm[k];
-                sum += ((u128)ps.y << 64) | ps.x;
-                mn = fminf(mn, mm.x);
-                mx = fmaxf(mx, mm.y);
-            }
+    float mn = 3.0f, mx = -1.0f;
+    u128 sum = 0;
+    if (one_step) {
+        const float lo = C->lo[m], sc = C->s[m];
+        for (uint64_t c = lo_c; c < c1; ++c) {
+            const float t = norm_t(__ldg(a.val + m * a.pitch + c), lo, sc);
+            sum += fx_of(t);
+            mn = fminf(mn, t);
+            mx = fmaxf(mx, t);
         }
-        const double s = fx_to_double(sum);
-        const uint64_t k = (uint64_t)m * a.W + p;
-        const float mean = __double2float_rn(__ddiv_rn(s, (double)count));
-        a.sum[k] = s;
-        a.vmin[k] = __float_as_uint(mn);
-        a.vmax[k] = __float_as_uint(mx);
-        a.mean[k] = mean;
-        a.y[k] = a.tf[m * a.T + tf_entry(mean, Tf, a.T - 1)];
+    } else {
+        if (w1 > w0) {
+            steps_minmax(v, m, w0, w1, mn, mx);
+            const uint64_t row = (uint64_t)m * (v.n_steps + 1);
+            const u128 pa = ((u128)v.pre_hi[row + w0] << 64) | v.pre_lo[row + w0];
+            const u128 pb = ((u128)v.pre_hi[row + w1] << 64) | v.pre_lo[row + w1];
+            sum = pb - pa;
+        }
+        if (has_l) {
+            const uint64_t q = (bl * 2 + 1) * M + m;
+            const ulonglong2 ps = qa.psum[q];
+            const float2 mm = qa.pmm[q];
+            sum += ((u128)ps.y << 64) | ps.x;
+            mn = fminf(mn, mm.x);
+            mx = fmaxf(mx, mm.y);
+        }
+        if (has_r) {
+            const uint64_t q = (br * 2 + 0) * M + m;
+            const ulonglong2 ps = qa.psum[q];
+            const float2 mm = qa.pmm[q];
+            sum += ((u128)ps.y << 64) | ps.x;
+            mn = fminf(mn, mm.x);
+            mx = fmaxf(mx, mm.y);
+        }
     }
-    a.count[p] = count;
+    const double sd = fx_to_double(sum);
+    const float mean = __double2float_rn(__ddiv_rn(sd, (double)count));
+    a.sum[k] = sd;
+    a.vmin[k] = __float_as_uint(mn);
+    a.vmax[k] = __float_as_uint(mx);
+    a.mean[k] = mean;
+    a.y[k] = a.tf[m * a.T + tf_entry(mean, (float)a.T, a.T - 1)];
+    if (m == 0) a.count[p] = count;
 }
 
+// All fields of pixel p by one thread (the batched queries, which have many
+// pixels over all pairs).
+template <int M>
+__device__ __forceinline__ void pixels_one(const UpdateArgs& a, const QueryArgs& qa, const ValueTableArgs& v,
+                                           uint32_t p)
+{
+#pragma unroll 1
+    for (int m = 0; m < M; ++m) pixels_field<M>(a, qa, v, p, m);
+}
+
+// One thread per (pixel, field): a pixel's fields are independent chains of
+// table loads, run side by side (grid.y = field).
 template <int M>
 __global__ __launch_bounds__(256) void k_pixels(UpdateArgs a, QueryArgs qa, ValueTableArgs v)
 {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.W) return;
-    pixels_one<M>(a, qa, v, p);
+    pixels_field<M>(a, qa, v, p, (int)blockIdx.y);
 }
 
 // The arguments of pair y of a batch: one TF's scan, one viewport's bins.
@@ -557,7 +561,7 @@ cudaError_t run_bins(cudaStream_t s, const UpdateArgs& a, const QueryArgs& qa, c
     cudaError_t e = cudaFuncSetAttribute(k_bounds<M, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (a.W > 1) k_bounds<M, PM><<<(a.W - 1 + 7) / 8, 256, smem, s>>>(a, qa);
-    k_pixels<M><<<(a.W + 255) / 256, 256, 0, s>>>(a, qa, v);
+    k_pixels<M><<<dim3((a.W + 255) / 256, M), 256, 0, s>>>(a, qa, v);
     return cudaGetLastError();
 }
 

@@ -121,6 +121,41 @@ __device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, con
 // One warp of a pass-A CTA, with the tile's chunk totals in lanes 0..7: chunk
 // offsets within the tile, the tile's exclusive prefix by decoupled look-back
 // (bounded waits), the chunk prefixes, and F after the last tile.
+// Decoupled look-back of scan unit `unit` > 0 by one warp: the sum of the
+// units before it, from their published aggregates (FLAG_A) back to the
+// nearest inclusive prefix (FLAG_P), 32 units per round.  Waits are bounded
+// (spin_limit polls, then the unit counts as 0 and ERR_TIMEOUT is raised).
+__device__ __forceinline__ unsigned long long look_back(const UpdateArgs& a, const unsigned long long* status,
+                                                        uint64_t unit, int lane)
+{
+    unsigned long long excl = 0;
+    int64_t end = (int64_t)unit - 1;              // window [end-31, end]
+    while (true) {
+        const int64_t j = end - lane;
+        unsigned long long s = FLAG_P;            // before unit 0: neutral
+        if (j >= 0) {
+            long long spins = 0;
+            while (true) {
+                s = ld_relaxed(status + j);
+                if (s >> 62) break;
+                if (++spins > a.spin_limit) {
+                    atomicOr(a.err, ERR_TIMEOUT);
+                    s = FLAG_P;                   // give up: count it as 0
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        const unsigned pmask = __ballot_sync(FULL, (s & FLAG_P) != 0);
+        // lanes up to and including the nearest inclusive prefix contribute
+        const int first = pmask ? __ffs(pmask) - 1 : 31;
+        const unsigned long long contrib = lane <= first ? (s & VAL_MASK) : 0ull;
+        excl += warp_sum_u64(contrib);
+        if (pmask) return excl;
+        end -= 32;
+    }
+}
+
 __device__ __forceinline__ void tile_scan(const UpdateArgs& a, uint32_t tile, uint32_t n_tiles, int lane,
                                           unsigned long long w /* lane < WARPS: chunk total of warp lane */)
 {
@@ -131,31 +166,7 @@ __device__ __forceinline__ void tile_scan(const UpdateArgs& a, uint32_t tile, ui
     if (lane == 0 && !skip) st_relaxed(status + tile, (tile == 0 ? FLAG_P : FLAG_A) | agg);
     unsigned long long excl = 0;
     if (tile > 0) {
-        int64_t end = (int64_t)tile - 1;          // window [end-31, end]
-        while (true) {
-            const int64_t j = end - lane;
-            unsigned long long s = FLAG_P;        // beyond tile 0: neutral
-            if (j >= 0) {
-                long long spins = 0;
-                while (true) {
-                    s = ld_relaxed(status + j);
-                    if (s >> 62) break;
-                    if (++spins > a.spin_limit) {
-                        atomicOr(a.err, ERR_TIMEOUT);
-                        s = FLAG_P;               // give up: count it as 0
-                        break;
-                    }
-                    __nanosleep(100);
-                }
-            }
-            const unsigned pmask = __ballot_sync(FULL, (s & FLAG_P) != 0);
-            // lanes up to and including the nearest inclusive prefix contribute
-            const int first = pmask ? __ffs(pmask) - 1 : 31;
-            unsigned long long contrib = lane <= first ? (s & VAL_MASK) : 0ull;
-            excl += warp_sum_u64(contrib);
-            if (pmask) break;
-            end -= 32;
-        }
+        excl = look_back(a, status, tile, lane);
         if (lane == 0 && !skip) st_relaxed(status + tile, FLAG_P | (excl + agg));
     }
     if (lane < WARPS) a.chunk_prefix[(uint64_t)tile * WARPS + lane] = excl + incl - w;
@@ -246,8 +257,8 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
 // persistent grid (as many CTAs as fit on the GPU at once) whose warps run
 // independently: global warp g starts with chunk g and claims each next chunk
 // from a counter when it starts the previous one (G warps in the grid: the
-// claims start at G), writing each chunk's width total; k_chunk_reduce and
-// k_chunk_scan then turn the totals into the exclusive chunk prefixes and F.
+// claims start at G), writing each chunk's width total; k_chunk_scan then
+// turns the totals into the exclusive chunk prefixes and F.
 // No warp ever waits for another (no tile barrier, no look-back), so the
 // stream of copies never stalls on the scan's chain of tiles.
 //
@@ -385,50 +396,26 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
     if ((late || injected) && lane == 0) atomicOr(a.err, ERR_TIMEOUT);
 }
 
-// The chunk totals (in chunk_prefix) become exclusive prefixes, in two small
-// launches over blocks of SCAN_SPAN chunks: block sums, then per block the sum
-// of the earlier blocks' sums plus a block-local scan.  The last block also
-// writes F (Eq. 4's total) and the all-zero fallback, as tile_scan does.
+// The chunk totals (in chunk_prefix) become exclusive prefixes in one launch
+// over blocks of SCAN_SPAN chunks, taken by tickets (counters[1]): a block scans
+// its chunks, publishes its total and looks back over the earlier blocks'
+// (decoupled look-back; all blocks are resident at once, so the chain is
+// short).  The last block also writes F (Eq. 4's total) and the all-zero
+// fallback, as tile_scan does.
 constexpr int SCAN_THREADS = 256, SCAN_PER_THREAD = 8, SCAN_SPAN = SCAN_THREADS * SCAN_PER_THREAD;
 
-__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x, unsigned long long* s_red)
-{
-    x = warp_sum_u64(x);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_red[warp] = x;
-    __syncthreads();
-    unsigned long long t = lane < (int)(blockDim.x >> 5) ? s_red[lane] : 0ull;
-    t = warp_sum_u64(t);
-    __syncthreads();
-    return t;
-}
-
-__global__ __launch_bounds__(SCAN_THREADS) void k_chunk_reduce(const unsigned long long* __restrict__ tot,
-                                                               uint64_t n_chunks, unsigned long long* blk)
-{
-    __shared__ unsigned long long s_red[SCAN_THREADS / 32];
-    const uint64_t b0 = (uint64_t)blockIdx.x * SCAN_SPAN;
-    unsigned long long x = 0;
-    for (int j = 0; j < SCAN_PER_THREAD; ++j) {
-        const uint64_t c = b0 + (uint64_t)j * SCAN_THREADS + threadIdx.x;
-        if (c < n_chunks) x += tot[c];
-    }
-    x = block_sum_u64(x, s_red);
-    if (threadIdx.x == 0) blk[blockIdx.x] = x;
-}
-
 __global__ __launch_bounds__(SCAN_THREADS) void k_chunk_scan(UpdateArgs a, uint64_t n_chunks,
-                                                             const unsigned long long* __restrict__ blk)
+                                                             unsigned long long* status)
 {
-    __shared__ unsigned long long s_red[SCAN_THREADS / 32];
     __shared__ unsigned long long s_warp[SCAN_THREADS / 32];
+    __shared__ unsigned long long s_excl;
+    __shared__ uint32_t s_b;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // sum of the earlier blocks
-    unsigned long long pre = 0;
-    for (uint32_t b = tid; b < blockIdx.x; b += SCAN_THREADS) pre += blk[b];
-    pre = block_sum_u64(pre, s_red);
-    // block-local exclusive scan: thread tid holds chunks b0 + tid*8 .. +8
-    const uint64_t c0 = (uint64_t)blockIdx.x * SCAN_SPAN + (uint64_t)tid * SCAN_PER_THREAD;
+    if (tid == 0) s_b = atomicAdd(&a.counters[1], 1u);
+    __syncthreads();
+    const uint32_t b = s_b;
+    // block-local scan: thread tid holds chunks b0 + tid*8 .. +8
+    const uint64_t c0 = (uint64_t)b * SCAN_SPAN + (uint64_t)tid * SCAN_PER_THREAD;
     unsigned long long v[SCAN_PER_THREAD], t = 0;
 #pragma unroll
     for (int j = 0; j < SCAN_PER_THREAD; ++j) {
@@ -438,17 +425,31 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_chunk_scan(UpdateArgs a, uint6
     const unsigned long long incl = warp_incl_scan_u64(t, lane);
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
-    unsigned long long wpre = 0;
-    for (int w = 0; w < warp; ++w) wpre += s_warp[w];
-    unsigned long long run = pre + wpre + incl - t;
+    unsigned long long wpre = 0, agg = 0;
+#pragma unroll
+    for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+        if (w < warp) wpre += s_warp[w];
+        agg += s_warp[w];
+    }
+    if (warp == 0) {
+        if (lane == 0) st_relaxed(status + b, (b == 0 ? FLAG_P : FLAG_A) | agg);
+        unsigned long long excl = 0;
+        if (b > 0) {
+            excl = look_back(a, status, b, lane);
+            if (lane == 0) st_relaxed(status + b, FLAG_P | (excl + agg));
+        }
+        if (lane == 0) s_excl = excl;
+    }
+    __syncthreads();
+    unsigned long long run = s_excl + wpre + incl - t;
 #pragma unroll
     for (int j = 0; j < SCAN_PER_THREAD; ++j) {
         if (c0 + j < n_chunks) a.chunk_prefix[c0 + j] = run;
         run += v[j];
     }
-    if (blockIdx.x == gridDim.x - 1 && tid == SCAN_THREADS - 1) {
+    if (b == gridDim.x - 1 && tid == 0) {
         UpdateConsts* C = a.consts;
-        unsigned long long F = run;       // the last thread's running sum is the total
+        unsigned long long F = s_excl + agg;
         int linear = 0;
         if (F == 0 && a.n > 0) { F = a.n; linear = 1; }   // all widths 0: equal widths
         C->F = F;
@@ -1211,9 +1212,8 @@ cudaError_t launch_passA_ring(cudaStream_t s, const UpdateArgs& a, uint32_t n_ti
     if ((uint32_t)grid > n_tiles) grid = (int)n_tiles;
     const uint64_t n_chunks = (uint64_t)n_tiles * WARPS;
     kernel<<<grid, WARPS * 32, smem, s>>>(a, n_chunks, tf_bytes);
-    // block sums into the (here unused) tile status words, then the scan
+    // the scan's block states use the (here unused) tile status words
     const uint32_t blocks = (uint32_t)((n_chunks + SCAN_SPAN - 1) / SCAN_SPAN);
-    k_chunk_reduce<<<blocks, SCAN_THREADS, 0, s>>>(a.chunk_prefix, n_chunks, a.tile_status);
     k_chunk_scan<<<blocks, SCAN_THREADS, 0, s>>>(a, n_chunks, a.tile_status);
     return cudaSuccess;
 }
