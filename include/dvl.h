@@ -248,6 +248,17 @@ int dvl_backward(dvl_ctx* ctx, const float* grad_abar, int mem_in, float* grad_c
  * so device-side errors of the update are reported here. */
 int dvl_read_bins(dvl_ctx* ctx, uint32_t field, const dvl_bins* out);
 
+/* The bins of every field of the last update in one call: mean, min, max, y
+ * and sum hold n_fields*W elements, field m's row starting at element m*W
+ * (the layout dvl_read_bins fills one row of); count holds W (shared by the
+ * fields).  NULL members are skipped.  One copy per array and one
+ * synchronisation of the context's stream, whatever the number of fields;
+ * device-side errors of the update are reported here (the buffers' contents
+ * are then unspecified).  Errors: DVL_ERR_ARG,
+ * DVL_ERR_STATE, DVL_ERR_CUDA, and the device-side DVL_ERR_TIMEOUT and
+ * DVL_ERR_RANGE. */
+int dvl_read_bins_all(dvl_ctx* ctx, const dvl_bins* out);
+
 /* Scalars of the last update (synchronises). */
 int dvl_get_stats(dvl_ctx* ctx, dvl_stats* out);
 

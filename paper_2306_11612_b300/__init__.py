@@ -32,7 +32,7 @@ PLOT_MEAN, PLOT_Y = 0, 1
 SCALE_LINEAR, SCALE_LOG10 = 0, 1
 
 EXPORTS = ["dvl_create", "dvl_destroy", "dvl_load_amr", "dvl_build_order", "dvl_set_fields",
-           "dvl_set_tf", "dvl_update", "dvl_read_bins", "dvl_get_stats", "dvl_read_order",
+           "dvl_set_tf", "dvl_update", "dvl_read_bins", "dvl_read_bins_all", "dvl_get_stats", "dvl_read_order",
            "dvl_read_widths", "dvl_sync", "dvl_set_option", "dvl_get_timings", "dvl_update_noalloc", "dvl_set_tf_ctrl", "dvl_read_alpha_means", "dvl_backward",
            "dvl_update_batch", "dvl_read_batch_bins", "dvl_read_batch_all", "dvl_batch_config",
            "dvl_read_batch_all_async", "dvl_stream", "dvl_rasterize", "dvl_brush", "dvl_select_keys",
@@ -94,6 +94,7 @@ def _load():
         "dvl_set_tf": ([vp, u32, vp, u32, f32, f32], i32),
         "dvl_update": ([vp, ctypes.POINTER(dvl_params)], i32),
         "dvl_read_bins": ([vp, u32, ctypes.POINTER(dvl_bins)], i32),
+        "dvl_read_bins_all": ([vp, ctypes.POINTER(dvl_bins)], i32),
         "dvl_get_stats": ([vp, ctypes.POINTER(dvl_stats)], i32),
         "dvl_read_order": ([vp, vp, vp, i32], i32),
         "dvl_read_widths": ([vp, vp, i32], i32),
@@ -392,6 +393,28 @@ class DVL:
         out, b, keep = self._bins_struct(self.W, out)
         self._check(lib.dvl_read_bins(self._h, field, ctypes.byref(b)))
         return out
+
+    def dvl_read_bins_all(self, out: dict | None = None) -> dict:
+        """Bins of every field in one call: mean/min/max/y/sum of shape
+        (M, W) (or M*W elements), count of W; one copy per array and one
+        synchronisation.  ``out`` as for read_bins."""
+        M, W = self.M, self.W
+        if out is None:
+            out = dict(mean=np.empty((M, W), np.float32), min=np.empty((M, W), np.float32),
+                       max=np.empty((M, W), np.float32), y=np.empty((M, W), np.float32),
+                       sum=np.empty((M, W), np.float64), count=np.empty(W, np.uint32))
+        for name, x in out.items():
+            if x is None:
+                continue
+            need = (W if name == "count" else M * W) * (8 if name == "sum" else 4)
+            have = (x.numel() * x.element_size()) if hasattr(x, "numel") else x.nbytes
+            if have < need:
+                raise ValueError(f"out[{name!r}] holds {have} bytes, needs {need}")
+        out, b, keep = self._bins_struct(0, out)
+        self._check(lib.dvl_read_bins_all(self._h, ctypes.byref(b)))
+        return out
+
+    read_bins_all = dvl_read_bins_all
 
     def dvl_update_batch(self, alphas, pairs, domain=None, P=1.0, min_importance=0.025, min_imp_mode=0,
                          width_mode=0):

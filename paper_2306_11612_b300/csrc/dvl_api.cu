@@ -1091,6 +1091,30 @@ int dvl_read_bins(dvl_ctx* c, uint32_t field, const dvl_bins* out)
     return DVL_OK;
 }
 
+int dvl_read_bins_all(dvl_ctx* c, const dvl_bins* out)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (!out) return fail(c, DVL_ERR_ARG, "out is NULL");
+    if (!c->have_update) return fail(c, DVL_ERR_STATE, "no update has run");
+    if (out->mem_kind != DVL_MEM_HOST && out->mem_kind != DVL_MEM_DEVICE) return fail(c, DVL_ERR_ARG, "bad mem_kind");
+    cudaSetDevice(c->device);
+    // the per-field rows are adjacent on the device: one copy per array, and
+    // the device error word read with them (one synchronisation in all)
+    const size_t W = c->W_last, nb = (size_t)c->M * W;
+    const cudaMemcpyKind k = kind_out(out->mem_kind);
+    if (out->mean) CK(cudaMemcpyAsync(out->mean, c->d_mean, nb * 4, k, c->stream), "copy mean");
+    if (out->min) CK(cudaMemcpyAsync(out->min, c->d_vmin, nb * 4, k, c->stream), "copy min");
+    if (out->max) CK(cudaMemcpyAsync(out->max, c->d_vmax, nb * 4, k, c->stream), "copy max");
+    if (out->y) CK(cudaMemcpyAsync(out->y, c->d_y, nb * 4, k, c->stream), "copy y");
+    if (out->sum) CK(cudaMemcpyAsync(out->sum, c->d_sum, nb * 8, k, c->stream), "copy sum");
+    if (out->count) CK(cudaMemcpyAsync(out->count, c->d_count, W * 4, k, c->stream), "copy count");
+    uint32_t e = 0;
+    CK(cudaMemcpyAsync(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost, c->stream), "read error word");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return e ? take_device_error(c) : DVL_OK;
+}
+
 int dvl_get_stats(dvl_ctx* c, dvl_stats* out)
 {
     if (!c || !out) return fail(c, DVL_ERR_ARG, "NULL argument");

@@ -198,6 +198,45 @@ def test_device_inputs_and_outputs(small):
         ctx.close()
 
 
+def test_read_bins_all_equals_per_field_reads(small):
+    """dvl_read_bins_all: every field's row, bit for bit what dvl_read_bins
+    gives, into host and device buffers; the oracle agrees; refused before
+    the first update and for short buffers."""
+    torch = pytest.importorskip("torch")
+    alpha = synth.random_tfs(37)
+    W, M = 1000, small.fields.shape[0]
+    keys, perm, lev_s, fl_s = oracle.sorted_inputs(small.lower, small.level, small.fields, oracle.SFC_HILBERT)
+    o = oracle.update(fl_s, lev_s, alpha, per_cell=True, P=1.0, min_importance=0.025, width=W)
+    ctx = dvl.DVL(0)
+    try:
+        ctx.load_amr(small.lower, small.level, small.fields)
+        ctx.build_order(oracle.SFC_HILBERT)
+        with pytest.raises(dvl.DVLError) as e:
+            ctx.read_bins_all()
+        assert e.value.status == dvl.ERR_STATE
+        ctx.set_tfs(alpha)
+        ctx.update(P=1.0, min_importance=0.025, width=W)
+        allb = ctx.read_bins_all()
+        dev = torch.device("cuda:0")
+        outd = {k: torch.empty(W if k == "count" else M * W, dtype=dt, device=dev) for k, dt in
+                [("mean", torch.float32), ("min", torch.float32), ("max", torch.float32),
+                 ("y", torch.float32), ("sum", torch.float64), ("count", torch.int32)]}
+        ctx.read_bins_all(outd)
+        for m in range(M):
+            one = ctx.read_bins(m)
+            row = {k: (allb[k] if k == "count" else allb[k][m]) for k in one}
+            for k in one:
+                assert np.array_equal(row[k], one[k]), (m, k)
+                d = outd[k].cpu().numpy()
+                d = d if k == "count" else d.reshape(M, W)[m]
+                assert np.array_equal(d.view(one[k].dtype), one[k]), (m, k, "device")
+            assert_bins_match(row, o, m, alpha.shape[1], alpha[m])
+        with pytest.raises(ValueError):
+            ctx.read_bins_all({"mean": np.empty(M * W - 1, np.float32)})
+    finally:
+        ctx.close()
+
+
 def test_timeout_is_reported_and_context_survives(small):
     """The first scan tile withholds its sum: the waits of its successors run
     out (bounded), the update reports DVL_ERR_TIMEOUT, and the next update on
