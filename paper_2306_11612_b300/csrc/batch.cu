@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "cell_math.cuh"
 #include "consts.cuh"
 #include "dvl_internal.h"
@@ -77,20 +79,34 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA_batch(UpdateArgs a, BatchA
         __syncthreads();                               // tables ready; ticket visible
         const uint32_t tile = s_tile;
         if (tile >= b.n_tiles) break;                  // block-uniform
-        if (lane < G) s_ct[warp][lane] = 0ull;
+        unsigned long long ct = 0;                     // lane kk: TF kk's chunk total
         const uint64_t chunk = (uint64_t)tile * WARPS + warp;
         const uint64_t base = chunk * CHUNK;
         __syncwarp();
+        // the next step's cells are loaded while this step's TFs run (the
+        // same addresses as the step itself reads, one step earlier)
+        float vn[4][M];
+        uint32_t Ln = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int m = 0; m < M; ++m) vn[j][m] = 0.0f;
+        if (base + lane * 4 < a.n) load4<M>(a.val, a.pitch, a.lev, base + lane * 4, vn, Ln);
         for (int st = 0; st < STEPS; ++st) {
             if (base + (uint64_t)st * STEP >= a.n) break;            // warp-uniform
             const uint64_t idx = base + st * STEP + lane * 4;
             uint32_t off[4][M];
             float lvl[4];
             bool valid[4];
+            float v[4][M];
+            const uint32_t L4 = Ln;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int m = 0; m < M; ++m) v[j][m] = vn[j][m];
+            const uint64_t nidx = idx + STEP;
+            if (st + 1 < STEPS && nidx < a.n) load4<M>(a.val, a.pitch, a.lev, nidx, vn, Ln);
             if (idx < a.n) {
-                float v[4][M];
-                uint32_t L4;
-                load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
 #pragma unroll
@@ -108,31 +124,44 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA_batch(UpdateArgs a, BatchA
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) valid[j] = idx + j < a.n;
+            // lane kk keeps TF kk's step total; a step with all 128 cells
+            // present (every step but the data set's last) needs no masks
+            unsigned long long mine = 0;
+            auto tf_loop = [&](auto full_tag) {
+                constexpr bool ALL = decltype(full_tag)::value;     // every cell present
 #pragma unroll
-            for (int kk = 0; kk < G; ++kk) {
-                if (kk >= (int)gk) break;                              // block-uniform
-                const float* tk = s_tf + kk * MT1;
-                const float4 pr = s_par[kk];
-                unsigned long long l = 0;
+                for (int kk = 0; kk < G; ++kk) {
+                    if (kk >= (int)gk) break;                          // block-uniform
+                    const float* tk = s_tf + kk * MT1;
+                    const float4 pr = s_par[kk];
+                    uint32_t q[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float al[M];
+                    for (int j = 0; j < 4; ++j) {
+                        float al[M];
 #pragma unroll
-                    for (int m = 0; m < M; ++m) al[m] = tk[off[j][m]];
-                    // Eq. 3 as importance<PM>, with the level factor precomputed
-                    const float r = fmaxf(__fmul_rn(spread<M>(al), pr.x), pr.y);
-                    const float x = __fmul_rn(r, lvl[j]);
-                    const float f = fmaxf(PM == POW_ONE ? x : pow_gen(x, n2, P), pr.z);
-                    const uint32_t q = __float2uint_rn(__fmul_rn(f, pr.w));
-                    l += valid[j] ? q : 0u;
+                        for (int m = 0; m < M; ++m) al[m] = tk[off[j][m]];
+                        // Eq. 3 as importance<PM>, with the level factor precomputed
+                        const float r = fmaxf(__fmul_rn(spread<M>(al), pr.x), pr.y);
+                        const float x = __fmul_rn(r, lvl[j]);
+                        const float f = fmaxf(PM == POW_ONE ? x : pow_gen(x, n2, P), pr.z);
+                        q[j] = __float2uint_rn(__fmul_rn(f, pr.w));
+                        if (!ALL) q[j] = valid[j] ? q[j] : 0u;
+                    }
+                    const unsigned long long l = ((unsigned long long)q[0] + q[1]) + ((unsigned long long)q[2] + q[3]);
+                    const unsigned long long tot = warp_total_small(l);
+                    mine = lane == kk ? tot : mine;
                 }
-                const unsigned long long tot = warp_total_small(l);
-                if (lane == 0) {
-                    b.step_sums[((uint64_t)(g0 + kk) * b.n_chunks + chunk) * STEPS + st] = tot;
-                    s_ct[warp][kk] += tot;
-                }
+            };
+            if (base + (uint64_t)(st + 1) * STEP <= a.n)                // warp-uniform
+                tf_loop(std::true_type{});
+            else
+                tf_loop(std::false_type{});
+            if (lane < (int)gk) {
+                b.step_sums[((uint64_t)(g0 + lane) * b.n_chunks + chunk) * STEPS + st] = mine;
+                ct += mine;
             }
         }
+        if (lane < G) s_ct[warp][lane] = ct;
         __syncthreads();
         // one look-back per TF of the group; the warps take the TFs in turn
         for (uint32_t kk = warp; kk < gk; kk += WARPS) {
