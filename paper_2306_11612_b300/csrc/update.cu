@@ -883,6 +883,108 @@ __device__ __noinline__ void back_crossing_step(const UpdateArgs& a, const float
     }
 }
 
+// The histogram adjoint's form of back_crossing_step, for a step whose cells
+// fall in more than one pixel.  A cell that covers several pixels adds its
+// weight once per pixel as before (float64 shared atomics; at most a few per
+// boundary).  The cells that lie inside one pixel (nearly all) are counted per
+// TF entry in the warp's own histogram h, pixel by pixel, and each pixel's
+// counts are scaled by its weights g[m][p] / count[p] once, as the
+// non-crossing steps are.  h is clear on entry and on return.
+template <int M, int PM>
+__device__ __noinline__ void back_crossing_step_hist(const UpdateArgs& a, const float* s_tf, const PixelMap& pm,
+                                                     uint64_t idx, unsigned long long s_start, int lane,
+                                                     const float* g, double* sG, uint32_t* h)
+{
+    Cell<M, PM> cc;
+    cc.load(a.consts, a.T);
+    const int T1 = cc.T1, MT1 = M * T1;
+    const int nvalid = idx < a.n ? (a.n - idx < 4 ? (int)(a.n - idx) : 4) : 0;
+    uint32_t e[4][M], q[4];
+    unsigned long long lsum = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        q[j] = 0;
+        float t[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            t[m] = j < nvalid ? norm_t(__ldg(a.val + m * a.pitch + idx + j), cc.lo[m], cc.s[m]) : 0.0f;
+            e[j][m] = floor_small(__fmul_rn(t[m], cc.Tf));
+        }
+        if (j < nvalid) q[j] = cc.linear ? 1u : cc.width(t, __ldg(a.lev + idx + j), s_tf);
+        lsum += q[j];
+    }
+    unsigned long long E = s_start + warp_incl_scan_u64(lsum, lane) - lsum;
+    uint32_t pix[4];
+    bool single[4];
+    uint32_t plo = 0xFFFFFFFFu, phi = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        single[j] = false;
+        pix[j] = 0;
+        if (j < nvalid) {
+            const unsigned long long I = E + q[j];
+            const uint32_t b1 = pm.first_pixel(E);
+            const uint32_t b2 = I > E ? pm.last_pixel(I) : b1;
+            if (b1 == b2) {
+                single[j] = true;
+                pix[j] = b1;
+                plo = min(plo, b1);
+                phi = max(phi, b1);
+            } else {
+                for (uint32_t p = b1; p <= b2; ++p) {
+                    const uint32_t c = a.count[p];
+                    if (!c) continue;
+#pragma unroll
+                    for (int m = 0; m < M; ++m)
+                        atomicAdd(&sG[m * T1 + e[j][m]], (double)g[(uint64_t)m * a.W + p] / (double)c);
+                }
+            }
+            E = I;
+        }
+    }
+    plo = __reduce_min_sync(FULL, plo);
+    phi = __reduce_max_sync(FULL, phi);
+    if (plo > phi) return;                                      // warp-uniform: no single-pixel cell
+    if (phi - plo > 8) {                                        // many narrow pixels: per-cell adds
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!single[j]) continue;
+            const uint32_t c = a.count[pix[j]];
+            if (!c) continue;
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                atomicAdd(&sG[m * T1 + e[j][m]], (double)g[(uint64_t)m * a.W + pix[j]] / (double)c);
+        }
+        return;
+    }
+    for (uint32_t p = plo; p <= phi; ++p) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (single[j] && pix[j] == p) {
+#pragma unroll
+                for (int m = 0; m < M; ++m) atomicAdd(&h[m * T1 + e[j][m]], 1u);
+            }
+        __syncwarp();
+        const uint32_t c = a.count[p];
+        double wc[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) wc[m] = c ? (double)g[(uint64_t)m * a.W + p] / (double)c : 0.0;
+        for (int i = lane; i < MT1; i += 32) {
+            const uint32_t n = h[i];
+            if (n) {
+                h[i] = 0u;
+                const int m = i / T1;
+                double w = 0.0;
+#pragma unroll
+                for (int mm = 0; mm < M; ++mm)
+                    if (mm == m) w = wc[mm];
+                if (w != 0.0) atomicAdd(&sG[i], w * (double)n);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 template <int M, int PM>
 __global__ __launch_bounds__(WARPS * 32) void k_backward(UpdateArgs a, const float* g, double* gtab, int use_smem)
 {
@@ -973,10 +1075,10 @@ __global__ __launch_bounds__(WARPS * 32) void k_backward(UpdateArgs a, const flo
 // in the warp's own histogram); when the warp's pixel changes, or its chunk
 // ends, the counts are scaled by the pixel's weights and added to the CTA's
 // float64 table.  Steps that cross a pixel boundary place their cells exactly
-// (back_crossing_step).  Each CTA writes its table to gpart[blockIdx] without
+// (back_crossing_step_hist).  Each CTA writes its table to gpart[blockIdx] without
 // atomics; k_gtab_reduce sums the CTAs in a fixed order.
 template <int M, int PM>
-__global__ __launch_bounds__(WARPS * 32) void k_backward_hist(UpdateArgs a, const float* g, double* gpart)
+__global__ __launch_bounds__(WARPS * 32, 3) void k_backward_hist(UpdateArgs a, const float* g, double* gpart)
 {
     extern __shared__ float s_tf[];                    // table | float64 sums | WARPS u32 histograms
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1066,8 +1168,8 @@ __global__ __launch_bounds__(WARPS * 32) void k_backward_hist(UpdateArgs a, cons
         while (m2) {
             const int k = __ffs(m2) - 1;
             m2 &= m2 - 1;
-            back_crossing_step<M, PM>(a, s_tf, pm, base + k * STEP + lane * 4, __shfl_sync(FULL, s_start, k), lane,
-                                      g, sG, nullptr);
+            back_crossing_step_hist<M, PM>(a, s_tf, pm, base + k * STEP + lane * 4, __shfl_sync(FULL, s_start, k),
+                                           lane, g, sG, h);
         }
     }
     __syncthreads();
