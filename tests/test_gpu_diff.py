@@ -58,6 +58,41 @@ def test_alpha_means_and_gradient_match_oracle(kw):
         ctx.close()
 
 
+@pytest.mark.parametrize("W,M,n", [(2048, 4, 0), (16384, 4, 0), (65536, 4, 0), (5000, 3, 70001), (777, 1, 4097),
+                                   (3000, 8, 33333)])
+def test_gradient_wide_plots_and_field_counts(W, M, n):
+    """Steps that cross pixel boundaries in every form: a few pixels per step
+    (entry counts per pixel), many narrow pixels per step (per-cell adds) and
+    cells wider than a pixel; 1, 3, 4 and 8 fields, ragged sizes."""
+    if n == 0:
+        amr = synth.make("small")
+        lower, level, fields = amr.lower, amr.level, amr.fields
+    else:
+        rng = np.random.default_rng(n)
+        level = rng.integers(0, 6, n).astype(np.uint8)
+        g = 1 << 10
+        lo = rng.integers(0, g, (3, n)) >> level << level
+        lower = np.ascontiguousarray(np.minimum(lo, g - (1 << level.astype(np.int64))).astype(np.int32))
+        fields = rng.lognormal(0, 1.5, (M, n)).astype(np.float32)
+    rng = np.random.default_rng(W + M)
+    K = 16
+    ctrl = (rng.integers(0, 1025, (M, K)) / 1024.0).astype(np.float32)
+    target = rng.uniform(0, 1, (M, W))
+    _, _, lev, fl = oracle.sorted_inputs(lower, level, fields, oracle.SFC_HILBERT)
+    ref = oracle.alpha_grad(fl, lev, ctrl, target, width=W, P=1.0)
+    ctx = dvl.DVL(0)
+    try:
+        ctx.load_amr(lower, level, fields)
+        ctx.build_order(dvl.SFC_HILBERT)
+        ctx.set_tf_ctrl(ctrl, 256)
+        ctx.update(width=W, want_alpha=1, P=1.0)
+        assert np.allclose(ctx.read_alpha_means(), ref["abar"], rtol=1e-5, atol=1e-7)
+        grad = ctx.backward((2.0 * (ref["abar"] - target)).astype(np.float32))
+        assert np.max(np.abs(grad - ref["grad"])) <= 1e-5 * np.abs(ref["grad"]).max()
+    finally:
+        ctx.close()
+
+
 def test_autograd_function_matches_oracle():
     from paper_2306_11612_b300.diff import alpha_means
     amr = synth.make("small")
