@@ -778,7 +778,7 @@ __device__ __forceinline__ void place_chunk(const UpdateArgs& a, const float* s_
 }
 
 template <int M, int PM, bool ALPHA>
-__global__ __launch_bounds__(WARPS * 32) void k_passB_steps(UpdateArgs a)
+__global__ __launch_bounds__(WARPS * 32, 3) void k_passB_steps(UpdateArgs a)
 {
     extern __shared__ float s_tf[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
