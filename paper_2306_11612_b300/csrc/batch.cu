@@ -39,7 +39,7 @@ __global__ void k_prepare_batch(UpdateArgs a, BatchArgs b)
 // the TF loop unrolls; per cell the table offsets (all fields) and the level
 // factor 2^(L w) are computed once and reused by every TF of the group.
 template <int M, int PM, int G, int ST>
-__global__ __launch_bounds__(WARPS * 32) void k_passA_batch(UpdateArgs a, BatchArgs b, uint32_t g0)
+__global__ __launch_bounds__(WARPS * 32, M <= 4 ? 3 : 1) void k_passA_batch(UpdateArgs a, BatchArgs b, uint32_t g0)
 {
     extern __shared__ float4 s_dyn[];                  // G x 1 params, then G x M x T1 tables
     __shared__ unsigned long long s_ct[WARPS][G];      // chunk totals per warp and TF
