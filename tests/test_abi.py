@@ -84,3 +84,16 @@ def test_serving_rules_without_gpu():
     assert L.dvl_serve_admit(0, 64, 0, GB, 0, 100 * GB) == 0
     assert L.dvl_server_create(None, 0, None) == dvl.ERR_ARG
     L.dvl_server_destroy(None)
+
+
+def test_read_bins_all_checks_buffer_sizes_on_the_host():
+    """The binding refuses buffers smaller than n_fields x W (W for count)
+    before it calls into the library."""
+    import numpy as np
+    import paper_2306_11612_b300 as dvl
+    ctx = object.__new__(dvl.DVL)          # no device context: the check runs first
+    ctx.M, ctx.W, ctx._h = 4, 100, None
+    for name, arr in [("mean", np.empty(399, np.float32)), ("sum", np.empty(399, np.float64)),
+                      ("count", np.empty(99, np.uint32)), ("y", np.empty(200, np.float64)[:199])]:
+        with pytest.raises(ValueError):
+            ctx.read_bins_all({name: arr})
