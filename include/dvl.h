@@ -194,6 +194,15 @@ int dvl_read_data_range(dvl_ctx* ctx, float* lo, float* hi);
 int dvl_set_tf(dvl_ctx* ctx, uint32_t field, const float* alpha, uint32_t n_entries,
                float domain_lo, float domain_hi);
 
+/* Sets the alpha transfer functions of all fields in one call, as
+ * dvl_set_tf does for each field m with alpha + m*n_entries (field-major,
+ * n_fields x n_entries host floats) and the domain (domain[m],
+ * domain[n_fields + m]); domain may be NULL for every field's data range.
+ * n_fields must equal the data set's field count.  Every argument is checked
+ * before any table changes, so a refused call leaves the tables as they were.
+ * Errors: DVL_ERR_ARG, DVL_ERR_STATE (no data loaded). */
+int dvl_set_tfs(dvl_ctx* ctx, uint32_t n_fields, const float* alpha, uint32_t n_entries, const float* domain);
+
 /* Enqueues one DVL update (paper Sec. 3-4): per cell and field the TF alpha,
  * the local variation V (Eq. 1), the importance (Eq. 3), a fixed-point width,
  * the device-wide prefix sum (Eq. 4), the projection of every cell into the

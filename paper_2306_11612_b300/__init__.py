@@ -32,7 +32,7 @@ PLOT_MEAN, PLOT_Y = 0, 1
 SCALE_LINEAR, SCALE_LOG10 = 0, 1
 
 EXPORTS = ["dvl_create", "dvl_destroy", "dvl_load_amr", "dvl_build_order", "dvl_set_fields",
-           "dvl_set_tf", "dvl_update", "dvl_read_bins", "dvl_read_bins_all", "dvl_get_stats", "dvl_read_order",
+           "dvl_set_tf", "dvl_set_tfs", "dvl_update", "dvl_read_bins", "dvl_read_bins_all", "dvl_get_stats", "dvl_read_order",
            "dvl_read_widths", "dvl_sync", "dvl_set_option", "dvl_get_timings", "dvl_update_noalloc", "dvl_set_tf_ctrl", "dvl_read_alpha_means", "dvl_backward",
            "dvl_update_batch", "dvl_read_batch_bins", "dvl_read_batch_all", "dvl_batch_config",
            "dvl_read_batch_all_async", "dvl_stream", "dvl_rasterize", "dvl_brush", "dvl_select_keys",
@@ -94,6 +94,7 @@ def _load():
         "dvl_set_tf": ([vp, u32, vp, u32, f32, f32], i32),
         "dvl_update": ([vp, ctypes.POINTER(dvl_params)], i32),
         "dvl_read_bins": ([vp, u32, ctypes.POINTER(dvl_bins)], i32),
+        "dvl_set_tfs": ([vp, u32, vp, u32, vp], i32),
         "dvl_read_bins_all": ([vp, ctypes.POINTER(dvl_bins)], i32),
         "dvl_get_stats": ([vp, ctypes.POINTER(dvl_stats)], i32),
         "dvl_read_order": ([vp, vp, vp, i32], i32),
@@ -278,9 +279,21 @@ class DVL:
 
     set_tf = dvl_set_tf
 
-    def set_tfs(self, alphas, lo=None, hi=None):
-        for m in range(len(alphas)):
-            self.set_tf(m, alphas[m], math.nan if lo is None else lo[m], math.nan if hi is None else hi[m])
+    def dvl_set_tfs(self, alphas, lo=None, hi=None):
+        """Alpha tables of all fields in one call: ``alphas`` (M, T) host
+        floats; ``lo``/``hi`` per-field domains (None: data ranges)."""
+        a = np.ascontiguousarray(alphas, dtype=np.float32)
+        if a.ndim != 2:
+            raise ValueError("alphas must be (n_fields, n_entries)")
+        dom = None
+        if lo is not None or hi is not None:
+            M = a.shape[0]
+            lo = [math.nan] * M if lo is None else lo
+            hi = [math.nan] * M if hi is None else hi
+            dom = (ctypes.c_float * (2 * M))(*[float(x) for x in list(lo) + list(hi)])
+        self._check(lib.dvl_set_tfs(self._h, a.shape[0], a.ctypes.data, a.shape[1], dom))
+
+    set_tfs = dvl_set_tfs
 
     def dvl_update(self, P=1.0, min_importance=0.025, width=1024, min_imp_mode=0, vmax_mode=0, width_mode=0,
                    want_alpha=0):

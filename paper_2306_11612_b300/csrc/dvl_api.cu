@@ -690,6 +690,32 @@ int dvl_set_tf(dvl_ctx* c, uint32_t field, const float* alpha, uint32_t T, float
     return DVL_OK;
 }
 
+int dvl_set_tfs(dvl_ctx* c, uint32_t n_fields, const float* alpha, uint32_t T, const float* domain)
+{
+    if (!c) return DVL_ERR_ARG;
+    c->last_error.clear();
+    if (c->state < 1) return fail(c, DVL_ERR_STATE, "no data set loaded");
+    if (n_fields != c->M) return fail(c, DVL_ERR_ARG, "n_fields is %u, the data set has %u fields", n_fields, c->M);
+    if (!alpha) return fail(c, DVL_ERR_ARG, "alpha is NULL");
+    if (T < 2 || T > DVL_MAX_TF_ENTRIES) return fail(c, DVL_ERR_ARG, "n_entries must be in [2, %d]", DVL_MAX_TF_ENTRIES);
+    // everything is checked before any field changes: a refused call leaves
+    // the tables as they were
+    const uint32_t M = c->M;
+    for (size_t i = 0; i < (size_t)M * T; ++i)
+        if (!(alpha[i] >= 0.0f && alpha[i] <= 1.0f))
+            return fail(c, DVL_ERR_ARG, "alpha[%u][%u] outside [0, 1]", (unsigned)(i / T), (unsigned)(i % T));
+    for (uint32_t m = 0; domain && m < M; ++m) {
+        const float lo = domain[m], hi = domain[M + m];
+        if (!(std::isnan(lo) && std::isnan(hi)) && !(std::isfinite(lo) && std::isfinite(hi) && lo < hi))
+            return fail(c, DVL_ERR_ARG, "domain must be finite with lo < hi, or NaN/NaN");
+    }
+    for (uint32_t m = 0; m < M; ++m) {
+        const int rc = dvl_set_tf(c, m, alpha + (size_t)m * T, T, domain ? domain[m] : NAN, domain ? domain[M + m] : NAN);
+        if (rc) return rc;
+    }
+    return DVL_OK;
+}
+
 static int check_params(dvl_ctx* c, const dvl_params* p)
 {
     if (!p) return fail(c, DVL_ERR_ARG, "params is NULL");

@@ -45,6 +45,7 @@ def test_status_strings_and_null_handles():
     assert L.dvl_update(None, None) == dvl.ERR_ARG
     assert L.dvl_sync(None) == dvl.ERR_ARG
     assert L.dvl_read_bins_all(None, None) == dvl.ERR_ARG
+    assert L.dvl_set_tfs(None, 4, None, 256, None) == dvl.ERR_ARG
     assert L.dvl_create(None, 0, None) == dvl.ERR_ARG
 
 

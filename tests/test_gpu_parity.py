@@ -198,6 +198,48 @@ def test_device_inputs_and_outputs(small):
         ctx.close()
 
 
+def test_set_tfs_equals_per_field_tables(small):
+    """dvl_set_tfs: the same update as one dvl_set_tf per field (bit for bit),
+    with and without user domains; a refused call leaves the tables as they
+    were."""
+    alpha = synth.random_tfs(41)
+    M = small.fields.shape[0]
+    lo = [float(np.percentile(small.fields[m], 10)) for m in range(M)]
+    hi = [float(np.percentile(small.fields[m], 90)) for m in range(M)]
+    lo[1], hi[1] = math.nan, math.nan                  # field 1 keeps its data range
+    ctx = dvl.DVL(0)
+    try:
+        ctx.load_amr(small.lower, small.level, small.fields)
+        ctx.build_order(oracle.SFC_HILBERT)
+        for dom in (None, (lo, hi)):
+            for m in range(M):
+                ctx.set_tf(m, alpha[m], math.nan if dom is None else lo[m], math.nan if dom is None else hi[m])
+            ctx.update(P=1.0, width=777)
+            one = ctx.read_bins_all()
+            if dom is None:
+                ctx.set_tfs(alpha)
+            else:
+                ctx.set_tfs(alpha, lo, hi)
+            ctx.update(P=1.0, width=777)
+            allb = ctx.read_bins_all()
+            for k in one:
+                assert np.array_equal(one[k], allb[k]), (dom is None, k)
+        bad = alpha.copy()
+        bad[3, 7] = 1.5
+        with pytest.raises(dvl.DVLError) as e:
+            ctx.set_tfs(bad)
+        assert e.value.status == dvl.ERR_ARG
+        with pytest.raises(dvl.DVLError) as e:
+            ctx.set_tfs(alpha[:2])
+        assert e.value.status == dvl.ERR_ARG
+        ctx.update(P=1.0, width=777)                   # the last accepted tables
+        again = ctx.read_bins_all()
+        for k in again:
+            assert np.array_equal(again[k], allb[k]), k
+    finally:
+        ctx.close()
+
+
 def test_read_bins_all_equals_per_field_reads(small):
     """dvl_read_bins_all: every field's row, bit for bit what dvl_read_bins
     gives, into host and device buffers; the oracle agrees; refused before
