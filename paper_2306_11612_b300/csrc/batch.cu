@@ -127,35 +127,37 @@ __global__ __launch_bounds__(WARPS * 32, M <= 4 ? 3 : 1) void k_passA_batch(Upda
             // lane kk keeps TF kk's step total; a step with all 128 cells
             // present (every step but the data set's last) needs no masks
             unsigned long long mine = 0;
-            auto tf_loop = [&](auto full_tag) {
+            auto one_tf = [&](int kk, auto full_tag) {
                 constexpr bool ALL = decltype(full_tag)::value;     // every cell present
+                const float* tk = s_tf + kk * MT1;
+                const float4 pr = s_par[kk];
+                uint32_t q[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float al[M];
+#pragma unroll
+                    for (int m = 0; m < M; ++m) al[m] = tk[off[j][m]];
+                    // Eq. 3 as importance<PM>, with the level factor precomputed
+                    const float r = fmaxf(__fmul_rn(spread<M>(al), pr.x), pr.y);
+                    const float x = __fmul_rn(r, lvl[j]);
+                    const float f = fmaxf(PM == POW_ONE ? x : pow_gen(x, n2, P), pr.z);
+                    q[j] = __float2uint_rn(__fmul_rn(f, pr.w));
+                    if (!ALL) q[j] = valid[j] ? q[j] : 0u;
+                }
+                const unsigned long long l = ((unsigned long long)q[0] + q[1]) + ((unsigned long long)q[2] + q[3]);
+                const unsigned long long tot = warp_total_small(l);
+                mine = lane == kk ? tot : mine;
+            };
+            if (base + (uint64_t)(st + 1) * STEP <= a.n) {             // warp-uniform
 #pragma unroll
                 for (int kk = 0; kk < G; ++kk) {
                     if (kk >= (int)gk) break;                          // block-uniform
-                    const float* tk = s_tf + kk * MT1;
-                    const float4 pr = s_par[kk];
-                    uint32_t q[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        float al[M];
-#pragma unroll
-                        for (int m = 0; m < M; ++m) al[m] = tk[off[j][m]];
-                        // Eq. 3 as importance<PM>, with the level factor precomputed
-                        const float r = fmaxf(__fmul_rn(spread<M>(al), pr.x), pr.y);
-                        const float x = __fmul_rn(r, lvl[j]);
-                        const float f = fmaxf(PM == POW_ONE ? x : pow_gen(x, n2, P), pr.z);
-                        q[j] = __float2uint_rn(__fmul_rn(f, pr.w));
-                        if (!ALL) q[j] = valid[j] ? q[j] : 0u;
-                    }
-                    const unsigned long long l = ((unsigned long long)q[0] + q[1]) + ((unsigned long long)q[2] + q[3]);
-                    const unsigned long long tot = warp_total_small(l);
-                    mine = lane == kk ? tot : mine;
+                    one_tf(kk, std::true_type{});
                 }
-            };
-            if (base + (uint64_t)(st + 1) * STEP <= a.n)                // warp-uniform
-                tf_loop(std::true_type{});
-            else
-                tf_loop(std::false_type{});
+            } else {                                                   // the data set's last step:
+#pragma unroll 1                                                       // not unrolled (compile time)
+                for (int kk = 0; kk < (int)gk; ++kk) one_tf(kk, std::false_type{});
+            }
             if (lane < (int)gk) {
                 b.step_sums[((uint64_t)(g0 + lane) * b.n_chunks + chunk) * STEPS + st] = mine;
                 ct += mine;
