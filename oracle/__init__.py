@@ -13,9 +13,12 @@ Parity status per function (see the tests that pin each one):
 * ``order``      -- pinned: against numpy's stable argsort.
 * ``update``     -- pinned: exact-rational brute force (``brute.py``), the P = 0
                     closed form, constant-field closed forms, hand-worked golden
-                    fixtures, and sum/count invariants.
+                    fixtures, and sum/count invariants.  Its threaded form
+                    (``threads`` > 1, ``orc_update_mt``) is pinned to the
+                    sequential one bit for bit; ``keys(threads=)`` likewise.
 * ``alpha_grad`` -- pinned: float64 central differences (the loss is quadratic
-                    in the control points once the assignment is fixed).
+                    in the control points once the assignment is fixed; with
+                    given pixel weights ``g`` the functional is linear).
 * ``rasterize``  -- pinned: a hand-worked golden image and the properties that
                     define the drawing (contiguous columns through the value's
                     row, 8-connected segments, bar heights).
@@ -51,7 +54,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle with strict IEEE semantics (no contraction)."""
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
                                "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
     return _LIB
 
@@ -83,16 +86,20 @@ def _L():
         _lib.orc_keys.argtypes = [u64, vp, vp, vp, vp, ctypes.c_int, vp]
         _lib.orc_order.argtypes = [u64, vp, vp]
         _lib.orc_update.argtypes = [u64, u32, vp, vp, u32, vp, vp, vp, ctypes.POINTER(Params)] + [vp] * 10 + [ctypes.POINTER(Stats)]
+        _lib.orc_update_mt.argtypes = _lib.orc_update.argtypes + [ctypes.c_int]
+        _lib.orc_keys_mt.argtypes = [u64, vp, vp, vp, vp, ctypes.c_int, vp, ctypes.c_int]
         _lib.orc_rasterize.argtypes = [u32, u32, u32, vp, u32, vp, vp]
         _lib.orc_brush.argtypes = [u64, vp, vp, u32, u32, vp, vp]
         _lib.orc_widths.argtypes = [u64, u32, vp, vp, u32, u32, vp, ctypes.POINTER(Params), u64, vp, vp, vp, vp, vp]
         _lib.orc_select_keys.argtypes = [u64, vp, u32, vp, vp]
         _lib.orc_select_keys.restype = None
-        _lib.orc_alpha_grad.argtypes = [u64, u32, vp, vp, u32, u32, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp, vp]
+        _lib.orc_alpha_grad.argtypes = [u64, u32, vp, vp, u32, u32, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp,
+                                        vp, vp]
         _lib.orc_log10f.argtypes = [ctypes.c_float]
         _lib.orc_log10f.restype = ctypes.c_float
         _lib.orc_log_field.argtypes = [u64, vp]
-        for f in (_lib.orc_keys, _lib.orc_order, _lib.orc_update, _lib.orc_alpha_grad, _lib.orc_log_field):
+        for f in (_lib.orc_keys, _lib.orc_keys_mt, _lib.orc_order, _lib.orc_update, _lib.orc_update_mt,
+                  _lib.orc_alpha_grad, _lib.orc_log_field):
             f.restype = ctypes.c_int
     return _lib
 
@@ -105,14 +112,18 @@ class OracleError(RuntimeError):
     pass
 
 
-def keys(lower: np.ndarray, level: np.ndarray, sfc: int) -> np.ndarray:
+def keys(lower: np.ndarray, level: np.ndarray, sfc: int, threads: int = 1) -> np.ndarray:
     """u64 space-filling-curve key per cell (Morton or Hilbert of the exact
-    centroid 2*lower + 2^level, 21 bits per axis)."""
+    centroid 2*lower + 2^level, 21 bits per axis).  ``threads`` > 1 computes
+    contiguous ranges of the cells at once (same keys)."""
     lower = np.ascontiguousarray(lower, np.int32)
     level = np.ascontiguousarray(level, np.uint8)
     n = level.shape[0]
     out = np.empty(n, np.uint64)
-    rc = _L().orc_keys(n, _p(lower[0]), _p(lower[1]), _p(lower[2]), _p(level), sfc, _p(out))
+    if threads > 1:
+        rc = _L().orc_keys_mt(n, _p(lower[0]), _p(lower[1]), _p(lower[2]), _p(level), sfc, _p(out), threads)
+    else:
+        rc = _L().orc_keys(n, _p(lower[0]), _p(lower[1]), _p(lower[2]), _p(level), sfc, _p(out))
     if rc:
         raise OracleError(f"orc_keys failed: {rc}")
     return out
@@ -133,13 +144,15 @@ def params(P=1.0, min_importance=0.025, width=1024, min_imp_mode=0, vmax_mode=0,
 
 
 def update(fields: np.ndarray, level: np.ndarray, alpha: np.ndarray, dom_lo=None, dom_hi=None,
-           per_cell: bool = False, **kw) -> dict:
+           per_cell: bool = False, threads: int = 1, **kw) -> dict:
     """One DVL update over cells already in curve order.
 
     ``fields`` (M, N) float32, ``level`` (N,) uint8, ``alpha`` (M, T) float32.
     ``dom_lo``/``dom_hi`` per field (NaN = data range).  Keyword arguments are
     :func:`params`.  Returns bins (sum/min/max/mean/mean64/y per field and the
     shared count), stats, and with ``per_cell`` the widths q and bins b1, b2.
+    ``threads`` > 1 runs ``orc_update_mt``, which gives the same results bit
+    for bit on that many host threads.
     """
     prm = params(**kw)
     fields = np.ascontiguousarray(fields, np.float32)
@@ -157,23 +170,28 @@ def update(fields: np.ndarray, level: np.ndarray, alpha: np.ndarray, dom_lo=None
     if per_cell:
         out.update(q=np.empty(n, np.uint64), b1=np.empty(n, np.uint32), b2=np.empty(n, np.uint32))
     st = Stats()
-    rc = _L().orc_update(n, M, _p(fields), _p(level), T, _p(alpha), _p(lo), _p(hi), ctypes.byref(prm),
-                         _p(out["sum"]), _p(out["min"]), _p(out["max"]), _p(out["mean"]),
-                         _p(out["mean64"]), _p(out["y"]), _p(out["count"]), _p(out.get("q")),
-                         _p(out.get("b1")), _p(out.get("b2")), ctypes.byref(st))
+    args = (n, M, _p(fields), _p(level), T, _p(alpha), _p(lo), _p(hi), ctypes.byref(prm),
+            _p(out["sum"]), _p(out["min"]), _p(out["max"]), _p(out["mean"]),
+            _p(out["mean64"]), _p(out["y"]), _p(out["count"]), _p(out.get("q")),
+            _p(out.get("b1")), _p(out.get("b2")), ctypes.byref(st))
+    rc = _L().orc_update_mt(*args, int(threads)) if threads > 1 else _L().orc_update(*args)
     if rc:
         raise OracleError(f"orc_update failed: {rc}")
     out["stats"] = st.as_dict()
     return out
 
 
-def alpha_grad(fields, level, ctrl, target, T=256, dom_lo=None, dom_hi=None, **kw) -> dict:
-    """Loss, per-pixel mean alpha and its gradient w.r.t. the control points."""
+def alpha_grad(fields, level, ctrl, target, T=256, dom_lo=None, dom_hi=None, g=None, **kw) -> dict:
+    """Loss, per-pixel mean alpha and its gradient w.r.t. the control points.
+
+    With ``g`` (M, W), the gradient is that of sum(g * abar) instead (g takes
+    the place of dL/dabar = 2 (abar - target))."""
     prm = params(**kw)
     fields = np.ascontiguousarray(fields, np.float32)
     level = np.ascontiguousarray(level, np.uint8)
     ctrl = np.ascontiguousarray(ctrl, np.float32)
     target = np.ascontiguousarray(target, np.float64)
+    g = None if g is None else np.ascontiguousarray(g, np.float64)
     M, n = fields.shape
     K = ctrl.shape[1]
     W = prm.width
@@ -183,7 +201,7 @@ def alpha_grad(fields, level, ctrl, target, T=256, dom_lo=None, dom_hi=None, **k
     grad = np.empty((M, K), np.float64)
     loss = np.zeros(1, np.float64)
     rc = _L().orc_alpha_grad(n, M, _p(fields), _p(level), T, K, _p(ctrl), _p(lo), _p(hi),
-                             ctypes.byref(prm), _p(target), _p(abar), _p(grad), _p(loss))
+                             ctypes.byref(prm), _p(target), _p(g), _p(abar), _p(grad), _p(loss))
     if rc:
         raise OracleError(f"orc_alpha_grad failed: {rc}")
     return dict(loss=float(loss[0]), abar=abar, grad=grad)

@@ -9,6 +9,9 @@
  * one correctly rounded IEEE operation.
  *
  * Readings of points the paper leaves open are stated where they are used.
+ * orc_update_mt and orc_keys_mt spread the same per-cell arithmetic over host
+ * threads (OpenMP) for the all-cores CPU baseline and for oracle runs at
+ * benchmark sizes; their results equal the sequential functions' bit for bit.
  */
 #include "dvl_oracle.h"
 
@@ -387,6 +390,273 @@ int orc_update(uint64_t n, uint32_t M, const float* fields, const uint8_t* level
 }
 
 /* ------------------------------------------------------------------------- */
+/* The same update spread over host threads (OpenMP)                         */
+/* ------------------------------------------------------------------------- */
+
+/* Contiguous share [*b, *e) of n items for thread t of nt. */
+static void share(uint64_t n, int nt, int t, uint64_t* b, uint64_t* e)
+{
+    *b = n / (uint64_t)nt * (uint64_t)t + (n % (uint64_t)nt < (uint64_t)t ? n % (uint64_t)nt : (uint64_t)t);
+    *e = *b + n / (uint64_t)nt + ((uint64_t)t < n % (uint64_t)nt ? 1 : 0);
+}
+
+/* orc_keys over n_threads contiguous ranges of the cells at once; every key
+ * is orc_keys' own, so the output is identical. */
+int orc_keys_mt(uint64_t n, const int32_t* lx, const int32_t* ly, const int32_t* lz,
+                const uint8_t* level, int sfc, uint64_t* keys, int n_threads)
+{
+    if (n_threads < 1) return -1;
+    int rc = 0;
+#pragma omp parallel for num_threads(n_threads) schedule(static, 1) reduction(min : rc)
+    for (int t = 0; t < n_threads; ++t) {
+        uint64_t b, e;
+        share(n, n_threads, t, &b, &e);
+        int r = orc_keys(e - b, lx + b, ly + b, lz + b, level + b, sfc, keys + b);
+        if (r < rc) rc = r;
+    }
+    return rc;
+}
+
+/* orc_update's result, bit for bit, computed by n_threads threads.  Only the
+ * distribution of the work differs:
+ *  - per-field data range and deepest level: each thread scans one contiguous
+ *    range of cells; the partial results are combined in range order with the
+ *    same comparisons, so the first occurrence of an extreme wins as in the
+ *    sequential scan;
+ *  - widths (Eq. 1, 3 and the fixed point): independent per cell; F is an
+ *    exact integer sum, independent of order;
+ *  - prefix of Eq. 4: per-range integer totals, their exclusive prefix in
+ *    range order, then each range's cells in order (exact integers);
+ *  - bins: each thread owns a contiguous run of pixels and visits, in curve
+ *    order, the cells whose span touches them, so every pixel receives its
+ *    cells' values in the same order as in orc_update (b1 and b2 are
+ *    non-decreasing in curve order, so those cells are one run).
+ * Setup steps of O(M T) work are the same code as in orc_update. */
+int orc_update_mt(uint64_t n, uint32_t M, const float* fields, const uint8_t* level,
+                  uint32_t T, const float* alpha, const float* dom_lo, const float* dom_hi,
+                  const orc_params* prm, double* sum, float* vmin, float* vmax, float* mean,
+                  double* mean64, float* y, uint32_t* count, uint64_t* q_out, uint32_t* b1_out,
+                  uint32_t* b2_out, orc_stats* st, int n_threads)
+{
+    const uint32_t W = prm->width;
+    const int nt = n_threads;
+    if (nt < 1 || nt > 4096) return -1;
+    if (M < 1 || M > 16 || T < 2 || W < 1 || !sum || !vmin || !vmax || !count) return -1;
+    for (uint64_t e = 0; e < (uint64_t)M * T; ++e)
+        if (!(alpha[e] >= 0.0f && alpha[e] <= 1.0f)) return -1;
+
+    /* data range per field: per-range first extremes, combined in range order */
+    float* part = (float*)malloc(sizeof(float) * 2 * 16 * (size_t)nt);
+    int* plev = (int*)malloc(sizeof(int) * (size_t)nt);
+    if (!part || !plev) { free(part); free(plev); return -3; }
+#pragma omp parallel for num_threads(nt) schedule(static, 1)
+    for (int t = 0; t < nt; ++t) {
+        uint64_t b, e;
+        share(n, nt, t, &b, &e);
+        for (uint32_t m = 0; m < M; ++m) {
+            const float* v = fields + (uint64_t)m * n;
+            float a = INFINITY, hb = -INFINITY;
+            for (uint64_t c = b; c < e; ++c) {
+                if (v[c] < a) a = v[c];
+                if (v[c] > hb) hb = v[c];
+            }
+            part[(size_t)t * 32 + m] = a;
+            part[(size_t)t * 32 + 16 + m] = hb;
+        }
+        int ml = 0;
+        for (uint64_t c = b; c < e; ++c)
+            if (level[c] > ml) ml = level[c];
+        plev[t] = ml;
+    }
+    float lo[16], s[16], dmin[16], dmax[16];
+    int max_level = 0;
+    for (uint32_t m = 0; m < M; ++m) {
+        float a = INFINITY, hb = -INFINITY;
+        for (int t = 0; t < nt; ++t) {
+            if (part[(size_t)t * 32 + m] < a) a = part[(size_t)t * 32 + m];
+            if (part[(size_t)t * 32 + 16 + m] > hb) hb = part[(size_t)t * 32 + 16 + m];
+        }
+        if (n == 0) { a = 0.0f; hb = 0.0f; }
+        dmin[m] = a;
+        dmax[m] = hb;
+        float l = dom_lo[m], h = dom_hi[m];
+        if (isnan(l) && isnan(h)) { l = a; h = hb; }
+        lo[m] = l;
+        s[m] = norm_scale(l, h);
+    }
+    for (int t = 0; t < nt; ++t)
+        if (plev[t] > max_level) max_level = plev[t];
+
+    /* max V: Eq. 5/6 as in orc_update, or the exact maximum over the cells */
+    int gi = (int)T - 1, gj = 0;
+    for (uint32_t m = 0; m < M; ++m) {
+        int im = (int)tf_entry(normalise(dmin[m], lo[m], s[m]), T);
+        int jm = (int)tf_entry(normalise(dmax[m], lo[m], s[m]), T);
+        if (im < gi) gi = im;
+        if (jm > gj) gj = jm;
+    }
+    if (gi > gj) { gi = 0; gj = 0; }
+    float Vmax = 0.0f;
+    if (prm->vmax_mode == ORC_VMAX_APPROX) {
+        for (int a = gi; a <= gj; ++a) {
+            float hi = alpha[a], lw = alpha[a];
+            for (uint32_t m = 1; m < M; ++m) {
+                float x = alpha[(uint64_t)m * T + a];
+                if (x > hi) hi = x;
+                if (x < lw) lw = x;
+            }
+            if (hi - lw > Vmax) Vmax = hi - lw;
+        }
+    } else {
+#pragma omp parallel for num_threads(nt) schedule(static, 1)
+        for (int t = 0; t < nt; ++t) {
+            uint64_t b, e;
+            share(n, nt, t, &b, &e);
+            float vm = 0.0f;
+            for (uint64_t c = b; c < e; ++c) {
+                float hi = 0.0f, lw = 1.0f;
+                for (uint32_t m = 0; m < M; ++m) {
+                    float al = alpha[(uint64_t)m * T + tf_entry(normalise(fields[(uint64_t)m * n + c], lo[m], s[m]), T)];
+                    if (al > hi) hi = al;
+                    if (al < lw) lw = al;
+                }
+                if (hi - lw > vm) vm = hi - lw;
+            }
+            part[(size_t)t * 32] = vm;
+        }
+        for (int t = 0; t < nt; ++t)
+            if (part[(size_t)t * 32] > Vmax) Vmax = part[(size_t)t * 32];
+    }
+    free(part);
+    free(plev);
+    float inv_vmax = Vmax > 0.0f ? 1.0f / Vmax : 0.0f;
+    float f_upper = 0.0f;
+    int Q = 0;
+    if (fixed_point(Vmax, inv_vmax, max_level, n, prm, &f_upper, &Q)) return -5;
+    float scale = pow2f_int(Q);
+
+    uint64_t* q = q_out ? q_out : (uint64_t*)malloc(sizeof(uint64_t) * (n ? n : 1));
+    uint32_t* b1 = b1_out ? b1_out : (uint32_t*)malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint32_t* b2 = b2_out ? b2_out : (uint32_t*)malloc(sizeof(uint32_t) * (n ? n : 1));
+    u128* tot = (u128*)malloc(sizeof(u128) * (size_t)nt);
+    int rc = -3;
+    if (!q || !b1 || !b2 || !tot) goto done;
+
+    /* widths (Eq. 1, Eq. 3, fixed point) and per-range totals */
+#pragma omp parallel for num_threads(nt) schedule(static, 1)
+    for (int t = 0; t < nt; ++t) {
+        uint64_t b, e;
+        share(n, nt, t, &b, &e);
+        u128 acc = 0;
+        for (uint64_t c = b; c < e; ++c) {
+            float hi = 0.0f, lw = 1.0f;
+            for (uint32_t m = 0; m < M; ++m) {
+                float tv = normalise(fields[(uint64_t)m * n + c], lo[m], s[m]);
+                float al = alpha[(uint64_t)m * T + tf_entry(tv, T)];
+                if (al > hi) hi = al;
+                if (al < lw) lw = al;
+            }
+            float f = importance(hi - lw, inv_vmax, level[c], prm);
+            q[c] = (uint64_t)nearbyintf(f * scale);
+            acc += q[c];
+        }
+        tot[t] = acc;
+    }
+    u128 F = 0;
+    for (int t = 0; t < nt; ++t) F += tot[t];
+    int linear = 0;
+    if (F == 0 && n > 0) {
+        linear = 1;
+#pragma omp parallel for num_threads(nt) schedule(static)
+        for (uint64_t c = 0; c < n; ++c) q[c] = 1;
+        F = n;
+        for (int t = 0; t < nt; ++t) {
+            uint64_t b, e;
+            share(n, nt, t, &b, &e);
+            tot[t] = e - b;
+        }
+    }
+    /* Eq. 4 prefix: exclusive prefix of the range totals, then b1/b2 per cell */
+    {
+        u128 run = 0;
+        for (int t = 0; t < nt; ++t) { u128 x = tot[t]; tot[t] = run; run += x; }
+    }
+#pragma omp parallel for num_threads(nt) schedule(static, 1)
+    for (int t = 0; t < nt; ++t) {
+        uint64_t b, e;
+        share(n, nt, t, &b, &e);
+        u128 E = tot[t];
+        for (uint64_t c = b; c < e; ++c) {
+            u128 I = E + q[c];
+            u128 x1 = E * W / F;
+            u128 x2 = I > E ? (I * W + F - 1) / F - 1 : x1;
+            if (x1 > W - 1) x1 = W - 1;
+            if (x2 > W - 1) x2 = W - 1;
+            b1[c] = (uint32_t)x1;
+            b2[c] = (uint32_t)x2;
+            E = I;
+        }
+    }
+
+    /* bins: thread t owns pixels [p0, p1) and the run of cells touching them */
+    for (uint64_t k = 0; k < (uint64_t)M * W; ++k) { sum[k] = 0.0; vmin[k] = INFINITY; vmax[k] = -INFINITY; }
+    for (uint32_t k = 0; k < W; ++k) count[k] = 0;
+#pragma omp parallel for num_threads(nt) schedule(static, 1)
+    for (int t = 0; t < nt; ++t) {
+        uint64_t pb, pe;
+        share(W, nt, t, &pb, &pe);
+        if (pb == pe) continue;
+        uint64_t lo_c = 0, hi_c = n;             /* first cell with b2 >= pb */
+        while (lo_c < hi_c) {
+            uint64_t mid = lo_c + (hi_c - lo_c) / 2;
+            if (b2[mid] < pb) lo_c = mid + 1; else hi_c = mid;
+        }
+        for (uint64_t c = lo_c; c < n && b1[c] < pe; ++c) {
+            uint32_t p0 = b1[c] > pb ? b1[c] : (uint32_t)pb;
+            uint32_t p1 = b2[c] < pe - 1 ? b2[c] : (uint32_t)(pe - 1);
+            for (uint32_t p = p0; p <= p1; ++p) {
+                count[p] += 1;
+                for (uint32_t m = 0; m < M; ++m) {
+                    float tv = normalise(fields[(uint64_t)m * n + c], lo[m], s[m]);
+                    uint64_t k = (uint64_t)m * W + p;
+                    sum[k] += (double)tv;
+                    if (tv < vmin[k]) vmin[k] = tv;
+                    if (tv > vmax[k]) vmax[k] = tv;
+                }
+            }
+        }
+    }
+    for (uint32_t m = 0; m < M; ++m)
+        for (uint32_t p = 0; p < W; ++p) {
+            uint64_t k = (uint64_t)m * W + p;
+            double mu = count[p] ? sum[k] / (double)count[p] : 0.0;
+            float mf = (float)mu;
+            if (mean64) mean64[k] = mu;
+            if (mean) mean[k] = mf;
+            if (y) y[k] = count[p] ? alpha[(uint64_t)m * T + tf_entry(mf, T)] : 0.0f;
+            if (!count[p]) { vmin[k] = 0.0f; vmax[k] = 0.0f; }
+        }
+    if (st) {
+        st->vmax = Vmax;
+        st->inv_vmax = inv_vmax;
+        st->f_upper = f_upper;
+        st->Q = Q;
+        st->i = gi;
+        st->j = gj;
+        st->linear = linear;
+        st->pow_exact = pow_is_exact(prm->P);
+        st->F = (uint64_t)F;
+    }
+    rc = 0;
+done:
+    if (!q_out) free(q);
+    if (!b1_out) free(b1);
+    if (!b2_out) free(b2);
+    free(tot);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Gradient of the per-pixel mean alpha w.r.t. alpha control points          */
 /* ------------------------------------------------------------------------- */
 
@@ -409,7 +679,7 @@ static void ctrl_to_table(uint32_t T, uint32_t K, const float* ctrl, float* tabl
 int orc_alpha_grad(uint64_t n, uint32_t M, const float* fields, const uint8_t* level,
                    uint32_t T, uint32_t K, const float* ctrl, const float* dom_lo,
                    const float* dom_hi, const orc_params* prm, const double* target,
-                   double* abar, double* grad, double* loss)
+                   const double* g_in, double* abar, double* grad, double* loss)
 {
     const uint32_t W = prm->width;
     if (K < 2 || M < 1 || M > 16 || T < 2) return -1;
@@ -469,13 +739,15 @@ int orc_alpha_grad(uint64_t n, uint32_t M, const float* fields, const uint8_t* l
             double d = abar[k] - target[k];
             L += d * d;
         }
-    /* adjoint: dL/dA_m[e] = sum over covering (cell, pixel) of 2 (abar-target)/count */
+    /* adjoint: dL/dA_m[e] = sum over covering (cell, pixel) of g/count, with
+     * g = dL/dabar = 2 (abar - target), or the caller's g_in when given */
     for (uint64_t c = 0; c < n; ++c)
         for (uint32_t p = b1[c]; p <= b2[c]; ++p)
             for (uint32_t m = 0; m < M; ++m) {
                 uint32_t e = tf_entry(normalise(fields[(uint64_t)m * n + c], lo[m], s[m]), T);
                 uint64_t k = (uint64_t)m * W + p;
-                gtab[(uint64_t)m * T + e] += 2.0 * (abar[k] - target[k]) / cnt[p];
+                double gk = g_in ? g_in[k] : 2.0 * (abar[k] - target[k]);
+                gtab[(uint64_t)m * T + e] += gk / cnt[p];
             }
     /* chain rule through the linear interpolation of the control points */
     for (uint64_t k = 0; k < (uint64_t)M * K; ++k) grad[k] = 0.0;

@@ -71,6 +71,20 @@ int orc_update(uint64_t n, uint32_t M, const float* fields, const uint8_t* level
                double* mean64, float* y, uint32_t* count, uint64_t* q, uint32_t* b1,
                uint32_t* b2, orc_stats* stats);
 
+/* orc_update's results, bit for bit, computed on n_threads host threads
+ * (OpenMP): the per-cell work is split into contiguous ranges, the Eq. 4
+ * prefix is exact integer arithmetic, and each pixel is filled by one thread
+ * with its cells in curve order, so no floating-point sum changes order. */
+int orc_update_mt(uint64_t n, uint32_t M, const float* fields, const uint8_t* level,
+                  uint32_t T, const float* alpha, const float* dom_lo, const float* dom_hi,
+                  const orc_params* prm, double* sum, float* vmin, float* vmax, float* mean,
+                  double* mean64, float* y, uint32_t* count, uint64_t* q, uint32_t* b1,
+                  uint32_t* b2, orc_stats* stats, int n_threads);
+
+/* orc_keys over n_threads contiguous ranges of the cells at once. */
+int orc_keys_mt(uint64_t n, const int32_t* lx, const int32_t* ly, const int32_t* lz,
+                const uint8_t* level, int sfc, uint64_t* keys, int n_threads);
+
 /* Gradient of L = sum_{m,p} (abar[m][p] - target[m][p])^2 with respect to K
  * uniformly spaced alpha control points per field, where abar[m][p] is the
  * mean over the cells covering bin p of the per-cell alpha of field m, and the
@@ -78,11 +92,13 @@ int orc_update(uint64_t n, uint32_t M, const float* fields, const uint8_t* level
  * e/(T-1).  Bin assignment and entry indices are held fixed at the values
  * of a forward update with the same inputs.  ctrl[M*K] are the parameters.
  * Writes abar[M*W] (double), grad[M*K] (double), *loss.  See orc_update for
- * the other arguments (the alpha table is built from ctrl). */
+ * the other arguments (the alpha table is built from ctrl).  With g_in
+ * (M*W doubles) not NULL, grad is instead the gradient of the linear
+ * functional sum_{m,p} g_in[m][p] * abar[m][p] (g_in replaces dL/dabar). */
 int orc_alpha_grad(uint64_t n, uint32_t M, const float* fields, const uint8_t* level,
                    uint32_t T, uint32_t K, const float* ctrl, const float* dom_lo,
                    const float* dom_hi, const orc_params* prm, const double* target,
-                   double* abar, double* grad, double* loss);
+                   const double* g_in, double* abar, double* grad, double* loss);
 
 /* Fixed-point widths of k sampled cells of a data set of n_total cells, one
  * by one, from the data set's global quantities (per-field data minimum and

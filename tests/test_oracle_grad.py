@@ -64,3 +64,29 @@ def test_abar_is_mean_of_table_alpha():
             expect[:, p] += a[:, c]
     expect /= u["count"][None, :]
     assert np.allclose(r["abar"], expect, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("kw", [dict(P=0.0), dict(P=1.0, min_importance=1.0, vmax_mode=1)])
+def test_gradient_of_given_pixel_weights_matches_central_differences(kw):
+    """With pixel weights g in place of dL/dabar, the gradient is that of the
+    linear functional sum(g * abar); central differences of that functional
+    (linear in the control points) equal it up to rounding."""
+    fl, lev, ctrl, target = _setup(4)
+    W = target.shape[1]
+    rng = np.random.default_rng(2)
+    g = rng.normal(size=(4, W)).astype(np.float32).astype(np.float64)
+    base = oracle.alpha_grad(fl, lev, ctrl, target, width=W, g=g, **kw)
+    h = 2.0 ** -6
+    for flat in rng.choice(ctrl.size, 32, replace=False):
+        m, k = divmod(int(flat), ctrl.shape[1])
+        cp, cm = ctrl.copy(), ctrl.copy()
+        cp[m, k] += h
+        cm[m, k] -= h
+        fp = float(np.sum(g * oracle.alpha_grad(fl, lev, cp, target, width=W, **kw)["abar"]))
+        fm = float(np.sum(g * oracle.alpha_grad(fl, lev, cm, target, width=W, **kw)["abar"]))
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - base["grad"][m, k]) <= 1e-9 * max(1.0, abs(fd)), (m, k, fd, base["grad"][m, k])
+    # g = 2 (abar - target) gives the loss gradient
+    lg = oracle.alpha_grad(fl, lev, ctrl, target, width=W, **kw)
+    gg = oracle.alpha_grad(fl, lev, ctrl, target, width=W, g=2.0 * (lg["abar"] - target), **kw)
+    assert np.array_equal(lg["grad"], gg["grad"])

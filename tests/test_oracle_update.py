@@ -220,8 +220,22 @@ def test_vmax_exact_mode_is_max_of_variation():
     # with P = 1, no minimum and one level, q is proportional to V / max V:
     # the largest width is exactly rint(1 * 2^Q)
     assert int(r["q"].max()) == 2 ** r["stats"]["Q"]
-    ra = oracle.update(fields, level, alpha, P=1, min_importance=0.0, width=10, vmax_mode=0)
-    assert ra["stats"]["vmax"] >= r["stats"]["vmax"] - 1e-7 or True  # approximation may differ either way
+    # brute force over the cells: the largest spread of the looked-up alphas
+    lo, hi = fields.min(1), fields.max(1)
+    s = (np.float32(1) / (hi - lo)).astype(np.float32)
+    t = np.clip(((fields - lo[:, None]).astype(np.float32) * s[:, None]).astype(np.float32), 0, 1)
+    e = np.minimum(np.floor(t * np.float32(64)).astype(np.int64), 63)
+    a = np.take_along_axis(alpha, e, 1)
+    assert np.float32(r["stats"]["vmax"]) == np.max(a.max(0) - a.min(0))
+    # Eq. 6 pairs the fields' entries by index: when every field has the same
+    # values (so every cell looks up one entry index in all tables) and all
+    # entries between the data minimum's and maximum's are reached, the
+    # approximation equals the exact maximum
+    same = np.repeat(np.linspace(-1, 1, 64 * 8, dtype=np.float32)[None], 3, axis=0)
+    lv = np.zeros(same.shape[1], np.uint8)
+    ex = oracle.update(same, lv, alpha, P=1, min_importance=0.0, width=10, vmax_mode=1)["stats"]
+    ap = oracle.update(same, lv, alpha, P=1, min_importance=0.0, width=10, vmax_mode=0)["stats"]
+    assert (ap["i"], ap["j"]) == (0, 63) and ap["vmax"] == ex["vmax"] == np.max(alpha.max(0) - alpha.min(0))
 
 
 def test_user_domain_clamps():
