@@ -414,13 +414,17 @@ int dvl_batch_config(dvl_ctx* ctx, int32_t out[3]);
  * that every GPU loading the library keeps until the process exits; this caps
  * n_cells at 476,749,824 (larger counts return DVL_ERR_RANGE before any GPU
  * work).  The first call on a device looks up that array's device address
- * (with the device current); make that first call before any stream capture.
+ * (with the device current) and keeps it for the life of the process; make
+ * that first call before any stream capture.  A cudaDeviceReset destroys the
+ * array's memory with the context, so the kept address is then stale: do not
+ * use this entry point on a device after resetting it.
  * All calls share the array and it keeps the previous call's contents (each
  * call re-initialises what must start fresh), so calls that overlap on the GPU
  * -- on different streams or host threads -- race and must be serialised by
  * the caller.
  *   cuda_stream  stream of the current device the work runs on (NULL = legacy
- *                default stream); the call synchronises it before returning
+ *                default stream); the call waits for that stream to finish
+ *                its work before returning (it reads back an error word)
  *   fields       device, cells in curve order, field m at fields + m*pitch;
  *                16-byte aligned, pitch a multiple of 4 and >= n_cells rounded
  *                up to a multiple of 4 (the buffer must hold n_fields*pitch
@@ -434,7 +438,11 @@ int dvl_batch_config(dvl_ctx* ctx, int32_t out[3]);
  *   out          device buffers of n_fields*W (mean, min, max, y, sum) and W
  *                (count) elements, field-major; all six required,
  *                mem_kind = DVL_MEM_DEVICE
- * Results equal dvl_update's for the same cells in the same order.  Errors:
+ * Results, for the same cells in the same order, against dvl_update's:
+ * counts, min and max bit-identical; sums and means within 1e-5 relative
+ * (this call places the cells with a second pass over them instead of
+ * dvl_update's prefix tables, so sums are added in another order); y the
+ * same except where a mean lies that close to a TF bucket boundary.  Errors:
  * DVL_ERR_ARG, DVL_ERR_RANGE (size cap, non-finite value, width bound),
  * DVL_ERR_TIMEOUT, DVL_ERR_CUDA. */
 int dvl_update_noalloc(void* cuda_stream, uint64_t n_cells, uint32_t n_fields, const float* fields,

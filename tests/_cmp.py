@@ -16,6 +16,8 @@ float32 values of t) must match bit for bit.
 """
 import numpy as np
 
+import oracle
+
 REL = 1e-5
 
 
@@ -44,3 +46,26 @@ def assert_bins_match(g: dict, o: dict, m: int, T: int, alpha_row: np.ndarray):
         k = int(np.round(x[p]))
         cands = {float(alpha_row[min(max(k + d, 0), T - 1)]) for d in (-1, 0)}
         assert float(g["y"][p]) in cands
+
+
+def assert_grad_match(grad, fields, level, ctrl, g32, width, **kw):
+    """Element-wise check of a GPU control-point gradient (float32, M x K)
+    computed from the float32 pixel weights g32 (M x W) against the oracle's
+    gradient for the same weights.
+
+    Both sides add per (cell, pixel) terms g/count in float64 (in different
+    orders), then the GPU rounds to float32.  So for every component k:
+    |gpu - ref| <= 2^-24 |ref| + (n + W + 16) 2^-53 S_k, where S_k is the
+    same gradient computed with |g| (the sum of the terms' magnitudes; the
+    interpolation weights are non-negative) and n + W bounds the number of
+    (cell, pixel) terms.
+    """
+    g = np.asarray(g32, np.float32).astype(np.float64)
+    target = np.zeros_like(g)
+    ref = oracle.alpha_grad(fields, level, ctrl, target, width=width, g=g, **kw)["grad"]
+    mag = oracle.alpha_grad(fields, level, ctrl, target, width=width, g=np.abs(g), **kw)["grad"]
+    n = fields.shape[1]
+    bound = 2.0 ** -24 * np.abs(ref) + (n + width + 16) * 2.0 ** -53 * mag + 1e-300
+    err = np.abs(np.asarray(grad, np.float64) - ref)
+    bad = err > bound
+    assert not np.any(bad), f"{int(bad.sum())} components off, worst ratio {np.max(err / bound):.3g}"

@@ -14,13 +14,22 @@ first TF).  The oracle cannot run the whole update in seconds, so:
   cover every cell, min <= mean <= max within [0, 1], y is the TF at the mean's
   entry), and agreement with the library's independent placement path (the
   second pass over the cells used for alpha means): counts, min and max bit
-  for bit, sums to 1e-5 relative.
+  for bit, sums to 1e-5 relative;
+* and the whole update against the oracle: the oracle's key of every cell
+  (threaded orc_keys), which the library's permutation must put in strictly
+  increasing order -- with distinct keys that is the one stable order -- then
+  the oracle's update of all 413.6M cells in that order (threaded
+  orc_update_mt, bit-identical to the sequential oracle): Q, F, max V, and
+  every pixel of every field (tests/_cmp.py).
 """
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 import synth
+from tests._cmp import assert_bins_match
 
 pytestmark = pytest.mark.gpu
 dvl = pytest.importorskip("paper_2306_11612_b300")
@@ -144,3 +153,27 @@ def test_log_scale_at_full_size(full):
     finally:
         for m in logm:
             ctx.set_field_scale(m, dvl.SCALE_LINEAR)
+
+
+def test_update_matches_oracle_at_full_size(full):
+    amr, ctx, tf, keys, perm = full
+    threads = max(1, min(os.cpu_count() or 1, 64))
+    ko = oracle.keys(amr.lower, amr.level, oracle.SFC_HILBERT, threads=threads)
+    ko = ko[perm]
+    assert np.array_equal(ko, keys), "library keys differ from the oracle's"
+    assert np.all(ko[1:] > ko[:-1]), "the permutation does not sort the oracle's keys"
+    del ko
+    lev = np.ascontiguousarray(amr.level[perm])
+    fl = np.empty((4, amr.n), np.float32)
+    for m in range(4):
+        np.take(amr.fields[m], perm, out=fl[m])
+    o = oracle.update(fl, lev, tf, P=P, min_importance=MI, width=W, threads=threads)
+    del fl, lev
+    ctx.set_tfs(tf)
+    ctx.update(P=P, min_importance=MI, width=W)
+    st = ctx.get_stats()
+    for k in ("Q", "F", "i", "j", "linear"):
+        assert st[k] == o["stats"][k], (k, st[k], o["stats"][k])
+    assert np.float32(st["vmax"]) == np.float32(o["stats"]["vmax"])
+    for m in range(4):
+        assert_bins_match(ctx.read_bins(m), o, m, T, tf[m])

@@ -9,7 +9,11 @@ library.  This file is collected last on purpose.  Two calls in a row (with
 different transfer functions, widths and exponents) must each match the
 context-based dvl_update on the same cells, within the tolerances of the other
 parity tests: counts and min/max bit for bit, sums and means to 1e-5
-relative, y exactly away from TF bucket boundaries.
+relative, y exactly away from TF bucket boundaries.  And the calls must leave
+device memory as they found it: the free memory the driver reports and the
+bytes torch holds are the same before and after a repeat of the same calls
+(the first round of calls may load the library's kernels and its fixed
+scratch array, which the driver does on first use).
 """
 import numpy as np
 import pytest
@@ -58,21 +62,32 @@ def test_noalloc_matches_update_on_two_calls():
         d_level = torch.from_numpy(level).to(dev)
         stream = torch.cuda.current_stream()
         nan = float("nan")
-        for call, (seed, kw) in enumerate([(3, dict(P=1.0, min_importance=0.025, width=1024)),
-                                           (4, dict(P=2.0, min_importance=0.1, width=333))]):
+        calls = []
+        for seed, kw in [(3, dict(P=1.0, min_importance=0.025, width=1024)),
+                         (4, dict(P=2.0, min_importance=0.1, width=333))]:
             alpha = synth.random_tfs(seed)
-            ref = _reference(ctx, alpha, **kw)
             W = kw["width"]
             out = {k: torch.full((M * W,), 7, dtype=dt, device=dev) for k, dt in
                    [("mean", torch.float32), ("min", torch.float32), ("max", torch.float32),
                     ("y", torch.float32), ("sum", torch.float64)]}
             out["count"] = torch.full((W,), 7, dtype=torch.int32, device=dev)
-            rc = dvl.dvl_update_noalloc(stream, d_fields, pitch, d_level, torch.from_numpy(alpha).to(dev),
-                                        [nan] * (2 * M), out, n_cells=n, **kw)
-            assert rc == dvl.OK, (call, rc)
-            got = {k: v.cpu().numpy() for k, v in out.items()}
-            for m in range(M):
-                _compare(ref[m], got, m, W, alpha.shape[1])
+            calls.append((alpha, torch.from_numpy(alpha).to(dev), kw, out, _reference(ctx, alpha, **kw)))
+        torch.cuda.synchronize()
+        for rnd in range(2):
+            if rnd == 1:
+                free0, held0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+            for call, (alpha, d_alpha, kw, out, ref) in enumerate(calls):
+                for v in out.values():
+                    v.fill_(7)
+                rc = dvl.dvl_update_noalloc(stream, d_fields, pitch, d_level, d_alpha, [nan] * (2 * M), out,
+                                            n_cells=n, **kw)
+                assert rc == dvl.OK, (rnd, call, rc)
+                got = {k: v.cpu().numpy() for k, v in out.items()}
+                for m in range(M):
+                    _compare(ref[m], got, m, kw["width"], alpha.shape[1])
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0, "device memory changed across allocation-free calls"
+        assert torch.cuda.memory_allocated() == held0
         # levels only 4-byte aligned: pass A reads the cells directly instead
         # of through bulk copies (which need 16-byte aligned rows)
         lev_store = torch.zeros(pitch + 16, dtype=torch.uint8, device=dev)
