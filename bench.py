@@ -49,6 +49,11 @@ BYTES_PASS_A = 4 * 4 + 1 + SCAN_BYTES
 BYTES_BOUNDS_PER_PIXEL = 128 * 17 + 16 * 8 + 3 * 32 * 8 + 8 + 1 + 2 * 4 * 24
 BYTES_PIXELS_PER_PIXEL = 2 * 9 + 2 * 4 * 24 + 2 * 4 * 16 + 4 * 4 * 4 + 4 * 24 + 4
 BYTES_BINS_PER_PIXEL = BYTES_BOUNDS_PER_PIXEL + BYTES_PIXELS_PER_PIXEL
+# Value tables (once per data set and TF domain): the 4 fields read once
+# (16 B/cell); per 128-cell step and field a 16-B in-block prefix and three
+# 8-B (min, max) pairs written (4 x 40 / 128 B/cell); block arrays are
+# 1/32 of that.
+BYTES_TABLES = 4 * 4 + 4 * 40 / 128 * (1 + 1 / 32)
 CPU_SAMPLE_BOX = ((0, 0, 0), 32)     # 32^3 of the 128^3 base cells (1/64 of the domain)
 LAUNCHES_PER_UPDATE = 5              # prepare, width pass, chunk scan, pixel bounds, pixel bins
 LOG_FIELDS = (0, 2, 3)                   # dens, pres, velmag on the log10 scale
@@ -69,6 +74,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline budget (rank 0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-patterns", action="store_true",
+                    help="default mode: skip the batched, served and differentiated records")
     ap.add_argument("--mode", choices=["plain", "batch", "serve", "sweep", "vmax", "diff"], default="plain",
                     help="plain: one TF edit per step (default); batch: K TFs x 4 viewports per step; "
                          "serve: Poisson TF-edit requests over 8 resident data sets; "
@@ -239,22 +246,44 @@ def cpu_sample(args):
     return amr, lev, fl
 
 
-def cpu_baseline(args, seconds):
-    """The oracle, as it stands, on a bounded contiguous piece of the workload."""
+def host_cores():
+    """Host threads this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def time_oracle(amr, lev, fl, args, seconds, threads):
+    """Updates of the CPU sample by the oracle on `threads` host threads
+    until `seconds` have passed: (cells/s, updates, seconds)."""
     import oracle
-    amr, lev, fl = cpu_sample(args)
     tfs = tf_sequence(64, 5000)
     done, i, t0 = 0, 0, time.perf_counter()
     while True:
-        oracle.update(fl, lev, tfs[i % len(tfs)], P=args.P, min_importance=args.min_importance, width=args.width)
+        oracle.update(fl, lev, tfs[i % len(tfs)], P=args.P, min_importance=args.min_importance, width=args.width,
+                      threads=threads)
         done += amr.n
         i += 1
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    return {"value": done / el, "unit": "cells/s", "cores": 1, "kind": "oracle",
+    return done / el, i, el
+
+
+def cpu_baseline(args, seconds):
+    """The oracle, as it stands, on a bounded contiguous piece of the
+    workload: on every host core (its threaded form, bit-identical to the
+    sequential one) and on one core."""
+    amr, lev, fl = cpu_sample(args)
+    cores = host_cores()
+    v_all, n_all, t_all = time_oracle(amr, lev, fl, args, seconds / 2, cores)
+    v_one, n_one, t_one = time_oracle(amr, lev, fl, args, seconds / 2, 1)
+    return {"value": v_all, "unit": "cells/s", "cores": cores, "kind": "oracle",
             "sample": f"{amr.n} cells = base cells {CPU_SAMPLE_BOX} of the {args.config} data set "
-                      f"(a contiguous run of its curve order), {i} updates in {el:.1f} s, single thread"}
+                      f"(a contiguous run of its curve order); {n_all} updates in {t_all:.1f} s on {cores} threads "
+                      f"(orc_update_mt), {n_one} in {t_one:.1f} s on one (orc_update)",
+            "one_core": {"value": v_one, "unit": "cells/s", "cores": 1}}
 
 
 def run_reference(args):
@@ -264,7 +293,8 @@ def run_reference(args):
     import oracle
     amr, lev, fl = cpu_sample(args)
     tfs = tf_sequence(args.steps + args.warmup)
-    kw = dict(P=args.P, min_importance=args.min_importance, width=args.width)
+    cores = host_cores()
+    kw = dict(P=args.P, min_importance=args.min_importance, width=args.width, threads=cores)
     for i in range(args.warmup):
         oracle.update(fl, lev, tfs[i], **kw)
     t0 = time.perf_counter()
@@ -277,8 +307,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64",
             "data": "synthetic", "config": workload_desc(amr, args, name),
-            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{amr.n} cells of the {args.config} data set per step"},
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{amr.n} cells of the {args.config} data set per step, oracle on "
+                                       f"{cores} host threads (orc_update_mt)"},
             "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
@@ -347,6 +378,33 @@ def run_ours(args):
                 "p99_ms": sorted(tail)[min(len(tail) - 1, int(0.99 * len(tail)))],
                 "edits": f"{len(per_edit) - len(tail)}..{len(per_edit) - 1}"}
     stages = ctx.get_timings()
+    # TF-domain edits: every field's [lo, hi] moves, so each update first
+    # rebuilds the value tables (once per domain) and then runs as usual
+    dlo, dhi = ctx.read_data_range()
+    n_dom = 10
+    doms = []
+    for i in range(n_dom + 2):
+        f = 0.002 * (i + 1)
+        doms.append(([float(a + f * (b - a)) for a, b in zip(dlo, dhi)],
+                     [float(b - f * (b - a)) for a, b in zip(dlo, dhi)]))
+    for i in range(2):                                  # warm (first use of the table kernels)
+        ctx.set_tfs(tfs[i], lo=doms[i][0], hi=doms[i][1])
+        ctx.update(**kw)
+    torch.cuda.synchronize()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    d0.record(stream)
+    for i in range(n_dom):
+        ctx.set_tfs(tfs[i], lo=doms[2 + i][0], hi=doms[2 + i][1])
+        ctx.update(**kw)
+    d1.record(stream)
+    d1.synchronize()
+    dom_wall_ms = (time.perf_counter() - t0) * 1e3 / n_dom
+    dom_ms = d0.elapsed_time(d1) / n_dom
+    dom_stages = ctx.get_timings()
+    ctx.set_tfs(tfs[0])                                 # data-range domains again
+    ctx.update(**kw)
+    ctx.sync()
     ctx.set_option(dvl.OPT_TIMING, 0)
     # the line plot of the last edit (polylines of all fields, bars of one), H = 512
     img = torch.empty((2, RASTER_H, args.width), dtype=torch.uint8, device=f"cuda:{local}")
@@ -449,6 +507,14 @@ def run_ours(args):
             "kernels": dict(kern, prepare_ms=stages["prepare"], finalize_ms=stages["finalize"],
                             edit_bytes_per_cell=edit_bytes / amr.n, edit_gbs=step_gbs, edit_frac=step_gbs / peak,
                             first_update_ms_with_value_tables=t_first,
+                            domain_change=dict(
+                                ms_per_edit=dom_ms, wall_ms_per_edit=dom_wall_ms, edits=n_dom,
+                                value_tables_ms=dom_stages["prepare"] - stages["prepare"],
+                                tables_gbs=BYTES_TABLES * amr.n / ((dom_stages["prepare"] - stages["prepare"]) * 1e-3) / 1e9,
+                                tables_frac=BYTES_TABLES * amr.n / ((dom_stages["prepare"] - stages["prepare"]) * 1e-3)
+                                / 1e9 / peak,
+                                note="set_tfs with new [lo, hi] for every field + dvl_update (value tables rebuilt "
+                                     "inside the update); device time by CUDA events, wall time on the host"),
                             rasterize_ms=raster_ms, rasterize_image=f"{RASTER_H} x {args.width}, 4 polylines + bars",
                             brush_ms=brush_ms, brush_cells=roi["n_cells"], select_keys_ms=select_ms,
                             log_scale={"fields": "dens, pres, velmag", "set_scale_ms_per_field": log_set_ms,
@@ -458,11 +524,48 @@ def run_ours(args):
             "setup_s": {"generate": t_gen, "load": t_load, "build_order": t_build}}
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args, args.cpu_seconds)
+    ctx.close()
+    if world == 1 and not args.no_patterns and args.config == "large":
+        line.update(pattern_records(args, amr))
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def pattern_records(args, full):
+    """The batched, served and differentiated forms, each on its own
+    configuration and next to the plain single-edit path on the same GPU, as
+    compact records for the default run's line (the --mode runs print the
+    full records)."""
+    import copy
+    import torch
+    out = {}
+    a = copy.copy(args)
+    a.steps, a.warmup, a.no_e2e, a.no_cpu_baseline = 10, 3, True, True
+    b = run_batch(a, emit=False)
+    out["batch"] = {"metric": b["metric"], "value": b["value"], "unit": b["unit"], "ms_per_step": b["ms_per_step"],
+                    "steps": a.steps, "config": b["config"], "roofline": b["roofline"],
+                    "kernels": b["kernels"], "plain_same_gpu": b["sequential"], "clocks": b["clocks"]}
+    torch.cuda.empty_cache()
+    a = copy.copy(args)
+    a.serve_seconds, a.warmup = 2.0, 1
+    v = run_serve(a, emit=False, full=full, compare_unbatched=False)
+    out["serve"] = {"metric": v["metric"], "value": v["value"], "unit": v["unit"], "p50_ms": v["p50_ms"],
+                    "p99_ms": v["p99_ms"], "resident_gb": v["resident_gb"], "config": v["config"],
+                    "served": v["served"], "saturated": v["saturated"], "plain_same_gpu": v["plain_closed_loop"],
+                    "clocks": v["clocks"]}
+    torch.cuda.empty_cache()
+    a = copy.copy(args)
+    a.steps, a.warmup = 20, 3
+    d = run_diff(a, emit=False)
+    out["diff"] = {"metric": d["metric"], "value": d["value"], "unit": d["unit"], "ms_per_step": d["ms_per_step"],
+                   "steps": a.steps, "config": d["config"], "parts": d["parts"], "roofline": d["roofline"],
+                   "plain_same_gpu": {"plain_update_ms": d["parts"]["plain_update_ms"],
+                                      "forward_over_plain": d["parts"]["forward_ms"] / d["parts"]["plain_update_ms"]},
+                   "clocks": d["clocks"]}
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -487,12 +590,12 @@ def alg_ops_per_cell_tf(M=4):
     return M + 2 * (M - 1) + 1 + 3 + 2 + 1
 
 
-def run_batch(args):
+def run_batch(args, emit=True):
     import numpy as np
     import torch
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
+    if world > 1 and emit:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2306_11612_b300 as dvl
@@ -621,11 +724,12 @@ def run_batch(args):
             "clocks": clocks, "e2e": e2e, "gpu_launches": 4 * args.steps}
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = batch_cpu_baseline(args, K)
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
     ctx.close()
-    if world > 1:
+    if world > 1 and emit:
         torch.distributed.destroy_process_group()
+    return line
 
 
 def batch_cpu_baseline(args, K, seconds=None):
@@ -707,12 +811,31 @@ def drive(srv, arrivals, reqs, width, open_loop=True):
     return time.perf_counter() - t0
 
 
-def run_serve(args):
+def overlap_ms(tl, a="run_start_ms", b="run_end_ms"):
+    """From a server timeline: device time during which batches of two or
+    more data sets ran at once, and the time at least one batch ran."""
+    ev = []
+    for r in tl:
+        ev.append((float(r[a]), 1, int(r["dataset"])))
+        ev.append((float(r[b]), -1, int(r["dataset"])))
+    ev.sort(key=lambda e: (e[0], e[1]))
+    active, last, both, busy = {}, None, 0.0, 0.0
+    for t, d, ds in ev:
+        if last is not None:
+            live = sum(1 for c in active.values() if c > 0)
+            busy += (t - last) if live >= 1 else 0.0
+            both += (t - last) if live >= 2 else 0.0
+        active[ds] = active.get(ds, 0) + d
+        last = t
+    return both, busy
+
+
+def run_serve(args, emit=True, full=None, compare_unbatched=True):
     import numpy as np
     import torch
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
+    if world > 1 and emit:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2306_11612_b300 as dvl
@@ -720,7 +843,7 @@ def run_serve(args):
     import synth
 
     t0 = time.perf_counter()
-    sets = synth.serving_datasets()
+    sets = synth.serving_datasets(full=full)
     t_gen = time.perf_counter() - t0
     sizes = [a.n for a in sets]
     n_req = int(args.serve_rate * args.serve_seconds)
@@ -728,20 +851,41 @@ def run_serve(args):
     kw = dict(P=args.P, min_importance=args.min_importance)
 
     def served(max_batch):
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info(local)[0]
         with DVLServer(local, max_batch=max_batch, max_inflight=len(sets), max_width=SERVE_WIDTH, **kw) as srv:
             for a in sets:
                 srv.add_dataset(a.lower, a.level, a.fields)
             srv.warmup()
+            torch.cuda.synchronize()
+            resident = free0 - torch.cuda.mem_get_info(local)[0]
             with ClockSampler(local) as clk:
+                srv.reset_stats()
                 wall = drive(srv, arrivals, reqs, SERVE_WIDTH, open_loop=True)
                 st = srv.stats()
+                tl = srv.timeline()
                 srv.reset_stats()
                 wall_sat = drive(srv, arrivals, reqs, SERVE_WIDTH, open_loop=False)
                 sat = srv.stats()
+                tl_sat = srv.timeline()
+            st["resident_gb"] = resident / 1e9
+            st["overlap"] = overlap_record(tl)
+            sat["overlap"] = overlap_record(tl_sat)
             return st, wall, sat, wall_sat, clk.summary()
 
+    def overlap_record(tl):
+        both, busy = overlap_ms(tl)
+        ev_both, ev_busy = overlap_ms(tl, "start_ms", "end_ms")
+        return {"batches": int(len(tl)), "datasets": int(len(set(tl["dataset"].tolist()))),
+                "run_busy_ms": busy, "run_two_or_more_datasets_ms": both,
+                "run_overlap_frac": both / busy if busy > 0 else 0.0,
+                "stream_busy_ms": ev_busy, "stream_two_or_more_datasets_ms": ev_both,
+                "how": "run: device clock (%globaltimer) read by each batch's first kernel at start and its last "
+                       "kernel's blocks at end; stream: CUDA events around the batch's kernels on its stream"}
+
     st, wall, sat, wall_sat, clocks = served(64)
-    st1, wall1, sat1, wall_sat1, _ = served(1)
+    if compare_unbatched:
+        st1, wall1, sat1, wall_sat1, _ = served(1)
     # closed-loop plain path: one context per data set, one request at a time
     ctxs = []
     for a in sets:
@@ -776,6 +920,7 @@ def run_serve(args):
                 "mean_batch": s["mean_batch"], "max_batch": s["max_batch_seen"], "cells_per_s": s["cells_per_s"],
                 "requests_per_s": s["completed"] / wall_s, "wall_s": wall_s}
 
+    pk = lambda s_, w_: dict(pick(s_, w_), overlap=s_["overlap"])
     line = {"metric": SERVE_METRIC, "value": st["cells_per_s"], "unit": "cells/s", "n_gpus": world,
             "steps": n_req, "warmup": 1, "ms_per_step": wall / n_req * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64", "data": "synthetic",
@@ -786,9 +931,10 @@ def run_serve(args):
                        "sizes": sizes, "requests": n_req, "rate": args.serve_rate, "width": SERVE_WIDTH,
                        "max_batch": 64, "max_inflight": len(sets),
                        "step": "one request, submit to result on the host"},
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-            "served": pick(st, wall), "saturated": pick(sat, wall_sat),
-            "single_request_server": {"offered": pick(st1, wall1), "saturated": pick(sat1, wall_sat1)},
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "resident_gb": st["resident_gb"],
+            "served": pk(st, wall), "saturated": pk(sat, wall_sat),
+            "single_request_server": ({"offered": pick(st1, wall1), "saturated": pick(sat1, wall_sat1)}
+                                      if compare_unbatched else None),
             "plain_closed_loop": {"requests": n_plain, "cells_per_s": plain_cells / el,
                                   "requests_per_s": n_plain / el,
                                   "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))},
@@ -797,10 +943,11 @@ def run_serve(args):
                                       "h2d_bytes_per_step": 4 * 256 * 4,
                                       "d2h_bytes_per_step": 4 * SERVE_WIDTH * (4 * 4 + 8) + 4 * SERVE_WIDTH},
             "setup_s": {"generate": t_gen}}
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
-    if world > 1:
+    if world > 1 and emit:
         torch.distributed.destroy_process_group()
+    return line
 
 
 # ---------------------------------------------------------------------------
@@ -920,15 +1067,16 @@ def run_vmax(args):
 # ---------------------------------------------------------------------------
 
 DIFF_W, DIFF_K = 2048, 64
-# algorithmic bytes per cell: the width pass (17 B + scan) and the alpha-means
-# placement pass (17 B: fields, levels for the recomputed widths at pixel
-# crossings, alpha lookups in shared memory) forward; the adjoint reads the
-# cells once more (17 B) with the per-pixel gradients from L2
-DIFF_FWD_BYTES = 2 * 17 + SCAN_BYTES
-DIFF_BWD_BYTES = 17
+# algorithmic bytes per cell: the forward is one read of the cells (17 B) by
+# pass A, which writes the width totals (SCAN_BYTES) and the fixed-point alpha
+# sums of the 4 fields per step and per chunk; the bins come from range
+# queries.  The adjoint reads the fields once more (16 B; the levels only at
+# pixel crossings) with the per-pixel gradients from L2.
+DIFF_FWD_BYTES = 17 + SCAN_BYTES + 4 * 8 / 128 + 4 * 8 / 2048
+DIFF_BWD_BYTES = 16
 
 
-def run_diff(args):
+def run_diff(args, emit=True):
     import numpy as np
     import torch
     import paper_2306_11612_b300 as dvl
@@ -1004,14 +1152,17 @@ def run_diff(args):
                                    f"points per field ({4 * DIFF_K} parameters), W={DIFF_W}, L2 loss vs a seeded target",
                        "step": "alpha_means forward, loss.backward (adjoint kernel), SGD update of the control points"},
             "parts": parts, "final_loss": float(loss.item()),
-            "roofline": {"bound": "hbm", "kernel": "forward (width pass + alpha-means placement pass)",
+            "roofline": {"bound": "hbm", "kernel": "forward (pass A with alpha sums, range-query bins)",
                          "achieved": fwd_gbs, "peak": peak, "unit": "GB/s", "frac": fwd_gbs / peak,
                          "traffic": None, "adjoint_gbs": bwd_gbs, "adjoint_frac": bwd_gbs / peak},
             "clocks": clk.summary(), "e2e": None,
             # forward: control-point tables, prepare, width pass, chunk scan, alpha-means placement,
             # finalize; adjoint: histograms, two reduction levels, chain rule
             "gpu_launches": 10 * args.steps}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    torch.cuda.set_stream(torch.cuda.default_stream(0))
+    return line
 
 
 def main():

@@ -88,6 +88,29 @@ typedef struct dvl_server_stats {
 int dvl_server_get_stats(dvl_server* srv, dvl_server_stats* out);
 int dvl_server_reset_stats(dvl_server* srv);
 
+/* One finished batch on the device timeline. */
+typedef struct dvl_batch_span {
+    uint32_t dataset;         /* data-set index */
+    uint32_t requests;        /* real requests in the batch */
+    double start_ms, end_ms;  /* CUDA events recorded on the data set's stream
+                                 before and after the batch's kernels, in ms
+                                 from the earliest start of the listed
+                                 batches (a start event completes when the
+                                 stream reaches it, which may be before its
+                                 kernels get SMs) */
+    double run_start_ms, run_end_ms;   /* the device clock read by the batch's
+                                 first kernel when it starts and by its last
+                                 kernel's blocks when they end, in ms from the
+                                 earliest such start (end -1: not recorded) */
+} dvl_batch_span;
+
+/* The batches finished since create or the last reset (at most 2^20), in
+ * order of completion: up to `cap` spans into out, their number into *n
+ * (cap = 0 only counts).  Batches of different data sets whose run
+ * intervals intersect executed on the device at the same time.  Call it while
+ * no dvl_server_reset_stats runs (that recycles the events). */
+int dvl_server_timeline(dvl_server* srv, dvl_batch_span* out, uint32_t cap, uint32_t* n);
+
 /* Message of the last failing call on srv (empty if none); never NULL. */
 const char* dvl_server_last_error(dvl_server* srv);
 

@@ -40,7 +40,7 @@ EXPORTS = ["dvl_create", "dvl_destroy", "dvl_load_amr", "dvl_build_order", "dvl_
            "dvl_status_string", "dvl_last_error",
            "dvl_server_create", "dvl_server_destroy", "dvl_server_add_dataset", "dvl_server_warmup",
            "dvl_server_submit", "dvl_server_wait", "dvl_server_get_stats", "dvl_server_reset_stats",
-           "dvl_server_last_error", "dvl_serve_bucket", "dvl_serve_admit"]
+           "dvl_server_timeline", "dvl_server_last_error", "dvl_serve_bucket", "dvl_serve_admit"]
 
 
 class dvl_params(ctypes.Structure):
@@ -71,6 +71,11 @@ class dvl_server_stats(ctypes.Structure):
                 ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("cells_per_s", ctypes.c_double), ("mem_used", ctypes.c_uint64), ("mem_budget", ctypes.c_uint64),
                 ("slot_bytes", ctypes.c_uint64), ("n_datasets", ctypes.c_uint32), ("max_batch_seen", ctypes.c_uint32)]
+
+
+class dvl_batch_span(ctypes.Structure):
+    _fields_ = [("dataset", ctypes.c_uint32), ("requests", ctypes.c_uint32), ("start_ms", ctypes.c_double),
+                ("end_ms", ctypes.c_double), ("run_start_ms", ctypes.c_double), ("run_end_ms", ctypes.c_double)]
 
 
 class dvl_stats(ctypes.Structure):
@@ -127,6 +132,7 @@ def _load():
         "dvl_server_wait": ([vp, u64, ctypes.c_double, ctypes.POINTER(dvl_bins)], i32),
         "dvl_server_get_stats": ([vp, ctypes.POINTER(dvl_server_stats)], i32),
         "dvl_server_reset_stats": ([vp], i32),
+        "dvl_server_timeline": ([vp, vp, u32, vp], i32),
         "dvl_server_last_error": ([vp], ctypes.c_char_p),
         "dvl_serve_bucket": ([u32, u32], u32),
         "dvl_serve_admit": ([u32, u32, u32, u64, u64, u64], u32),

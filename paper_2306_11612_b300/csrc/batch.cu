@@ -21,6 +21,10 @@ namespace {
 
 __global__ void k_prepare_batch(UpdateArgs a, BatchArgs b)
 {
+    if (b.stamps && blockIdx.x == 0 && threadIdx.x == 0) {
+        b.stamps[0] = global_ns();
+        b.stamps[1] = 0ull;
+    }
     UpdateArgs ak = a;
     ak.tf = b.tfs + (uint64_t)blockIdx.x * a.M * a.T;
     ak.consts = b.consts + blockIdx.x;
@@ -29,17 +33,21 @@ __global__ void k_prepare_batch(UpdateArgs a, BatchArgs b)
     prepare_consts_block(ak);
 }
 
-// Pass A for one group of G transfer functions (TFs g0 .. g0+G-1 of the
-// batch; all TFs share the TF domains): persistent CTAs load the group's alpha
-// tables into shared memory once, then take tiles from the group's ticket
-// counter; every warp step's cells are loaded and normalised once and
-// evaluated for all G TFs; per TF it writes step totals and, per tile, runs
-// its own decoupled look-back scan.  The batch launches one such kernel per
-// group (the cells are read once per group).  G is a compile-time constant so
-// the TF loop unrolls; per cell the table offsets (all fields) and the level
-// factor 2^(L w) are computed once and reused by every TF of the group.
+// Pass A for all K transfer functions of a batch (all TFs share the TF
+// domains), in one persistent launch: the TFs form groups of G whose alpha
+// tables fit in shared memory together, and CTAs take (group, tile) tickets
+// from one counter, group by group; a CTA loads a group's tables when its
+// ticket moves to a new group (once or twice per CTA).  Every warp step's
+// cells are loaded and normalised once per group and evaluated for all G TFs;
+// per TF it writes step totals and, per tile, runs its own decoupled
+// look-back scan.  G is a compile-time constant so the TF loop unrolls; per
+// cell the table offsets (all fields) and the level factor 2^(L w) are
+// computed once and reused by every TF of the group.  With P = 1 the
+// fixed-point scale 2^Q of each TF is folded into its constants: scaling by a
+// power of two is exact, so rint(max(max(V/maxV, m_b) 2^L, m_a) 2^Q) equals
+// rint(max(max(V (2^Q/maxV), m_b 2^Q) 2^L, m_a 2^Q)) bit for bit.
 template <int M, int PM, int G, int ST>
-__global__ __launch_bounds__(WARPS * 32, M <= 4 ? 3 : 1) void k_passA_batch(UpdateArgs a, BatchArgs b, uint32_t g0)
+__global__ __launch_bounds__(WARPS * 32, M <= 4 ? 3 : 1) void k_passA_batch(UpdateArgs a, BatchArgs b)
 {
     extern __shared__ float4 s_dyn[];                  // G x 1 params, then G x M x T1 tables
     __shared__ unsigned long long s_ct[WARPS][G];      // chunk totals per warp and TF
@@ -49,36 +57,49 @@ __global__ __launch_bounds__(WARPS * 32, M <= 4 ? 3 : 1) void k_passA_batch(Upda
     // the unrolled TF loop addresses its tables with immediate offsets), or
     // T + 1 when ST = 0
     const uint32_t T = a.T, T1 = ST ? (uint32_t)ST : T + 1, K = b.K, MT1 = M * T1;
-    const uint32_t gk = K - g0 < (uint32_t)G ? K - g0 : (uint32_t)G;
-    float4* s_par = s_dyn;                             // inv_vmax, mb, ma, qscale per TF
+    const uint32_t n_tiles = (uint32_t)b.n_tiles, n_groups = (K + G - 1) / G;
+    float4* s_par = s_dyn;                             // per TF: (1/maxV, m_b, m_a, 2^Q), see above
     float* s_tf = reinterpret_cast<float*>(s_dyn + G);
-    uint32_t* ticket = b.tickets + g0 / G;
     const UpdateConsts* C0 = b.consts;
     float lo[M], sc[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) { lo[m] = C0->lo[m]; sc[m] = C0->s[m]; }
     const float Tf = (float)T, P = C0->P;
     const int n2 = C0->pow_n2, wshift = C0->width_shift;
+    uint32_t g0 = 0xFFFFFFFFu, gk = 0;                 // the group whose tables are loaded
 
-    for (uint32_t i = tid; i < gk * MT1; i += blockDim.x) {
-        const uint32_t kk = i / MT1, r = i - kk * MT1, m = r / T1, e = r - m * T1;
-        s_tf[i] = b.tfs[((uint64_t)(g0 + kk) * M + m) * T + (e < T ? e : T - 1)];
-    }
-    for (uint32_t kk = tid; kk < G; kk += blockDim.x) {
-        float4 pr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (kk < gk) {
-            const UpdateConsts* Ck = b.consts + g0 + kk;
-            const bool after = Ck->min_imp_mode == DVL_MINIMP_AFTER_POWER;
-            pr = make_float4(Ck->inv_vmax, after ? 0.0f : Ck->min_imp, after ? Ck->min_imp : 0.0f, Ck->qscale);
+    auto load_group = [&](uint32_t first) {
+        g0 = first;
+        gk = K - g0 < (uint32_t)G ? K - g0 : (uint32_t)G;
+        for (uint32_t i = tid; i < gk * MT1; i += blockDim.x) {
+            const uint32_t kk = i / MT1, r = i - kk * MT1, m = r / T1, e = r - m * T1;
+            s_tf[i] = b.tfs[((uint64_t)(g0 + kk) * M + m) * T + (e < T ? e : T - 1)];
         }
-        s_par[kk] = pr;
-    }
+        for (uint32_t kk = tid; kk < G; kk += blockDim.x) {
+            float4 pr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (kk < gk) {
+                const UpdateConsts* Ck = b.consts + g0 + kk;
+                const bool after = Ck->min_imp_mode == DVL_MINIMP_AFTER_POWER;
+                const float mb = after ? 0.0f : Ck->min_imp, ma = after ? Ck->min_imp : 0.0f;
+                const float qs = Ck->qscale;
+                pr = PM == POW_ONE ? make_float4(__fmul_rn(Ck->inv_vmax, qs), __fmul_rn(mb, qs), __fmul_rn(ma, qs), qs)
+                                   : make_float4(Ck->inv_vmax, mb, ma, qs);
+            }
+            s_par[kk] = pr;
+        }
+    };
 
     while (true) {
-        if (tid == 0) s_tile = atomicAdd(ticket, 1u);
-        __syncthreads();                               // tables ready; ticket visible
-        const uint32_t tile = s_tile;
-        if (tile >= b.n_tiles) break;                  // block-uniform
+        if (tid == 0) s_tile = atomicAdd(b.tickets, 1u);
+        __syncthreads();                               // ticket visible; the last tile's work done
+        const uint32_t ticket = s_tile;
+        const uint32_t gi = ticket / n_tiles;          // block-uniform
+        if (gi >= n_groups) break;
+        const uint32_t tile = ticket - gi * n_tiles;
+        if (gi * G != g0) {
+            load_group(gi * G);
+            __syncthreads();                           // tables ready
+        }
         unsigned long long ct = 0;                     // lane kk: TF kk's chunk total
         const uint64_t chunk = (uint64_t)tile * WARPS + warp;
         const uint64_t base = chunk * CHUNK;
@@ -138,10 +159,15 @@ __global__ __launch_bounds__(WARPS * 32, M <= 4 ? 3 : 1) void k_passA_batch(Upda
 #pragma unroll
                     for (int m = 0; m < M; ++m) al[m] = tk[off[j][m]];
                     // Eq. 3 as importance<PM>, with the level factor precomputed
+                    // (and, with P = 1, 2^Q folded into the constants)
                     const float r = fmaxf(__fmul_rn(spread<M>(al), pr.x), pr.y);
                     const float x = __fmul_rn(r, lvl[j]);
-                    const float f = fmaxf(PM == POW_ONE ? x : pow_gen(x, n2, P), pr.z);
-                    q[j] = __float2uint_rn(__fmul_rn(f, pr.w));
+                    if (PM == POW_ONE) {
+                        q[j] = __float2uint_rn(fmaxf(x, pr.z));
+                    } else {
+                        const float f = fmaxf(pow_gen(x, n2, P), pr.z);
+                        q[j] = __float2uint_rn(__fmul_rn(f, pr.w));
+                    }
                     if (!ALL) q[j] = valid[j] ? q[j] : 0u;
                 }
                 const unsigned long long l = ((unsigned long long)q[0] + q[1]) + ((unsigned long long)q[2] + q[3]);
@@ -239,11 +265,10 @@ cudaError_t run_passA_batch_gs(cudaStream_t s, const UpdateArgs& a, const BatchA
     static std::atomic<size_t> set_bytes[MAX_DEVICES];
     cudaError_t e = smem_attr_once(k_passA_batch<M, PM, G, ST>, smem, set_bytes);
     if (e != cudaSuccess) return e;
+    const uint64_t work = b.n_tiles * ((b.K + G - 1) / G);    // (group, tile) tickets
     uint64_t grid = (uint64_t)b.sm_count * b.resid;
-    if (grid > b.n_tiles) grid = b.n_tiles;
-    if (grid)
-        for (uint32_t g0 = 0; g0 < b.K; g0 += G)      // one launch per group of G TFs
-            k_passA_batch<M, PM, G, ST><<<(unsigned)grid, WARPS * 32, smem, s>>>(a, b, g0);
+    if (grid > work) grid = work;
+    if (grid) k_passA_batch<M, PM, G, ST><<<(unsigned)grid, WARPS * 32, smem, s>>>(a, b);
     return cudaGetLastError();
 }
 

@@ -5,9 +5,10 @@
 // non-decreasing in the cell index).  The value a cell contributes to the bins
 // is its normalised field value t, which does not depend on the transfer
 // function.  So, once per data set and TF domain, this file builds value
-// tables -- per 128-cell step, the exact fixed-point sum of t and its min/max
-// (an exclusive prefix of the sums, and a sparse table of min/max over every
-// power-of-two run of steps) -- and each update then needs only:
+// tables -- per 128-cell step, the exact fixed-point sum of t and its min/max,
+// kept as prefixes within blocks of 32 steps plus a prefix of the block sums
+// and a min/max sparse table over power-of-two runs of blocks -- and each
+// update then needs only:
 //   k_bounds  for every pixel boundary j, H(j) = number of cells whose span
 //             starts before the boundary's first position C(j), and whether
 //             the last of them also reaches pixel j ("straddles"); found by a
@@ -16,9 +17,9 @@
 //             It also records the partial-step sums/min/max of the two pixels
 //             that meet in that step;
 //   k_pixels  for every pixel: count = hi - lo + 1, sums from the prefix
-//             table plus the two recorded partial steps, min/max from two
-//             sparse-table entries and the records, then mean and the alpha of
-//             the mean.
+//             tables plus the two recorded partial steps, min/max from the
+//             block prefix/suffix entries, two sparse-table entries and the
+//             records, then mean and the alpha of the mean.
 // Sums are exact integer sums of floor(t * 2^95), so the bins do not depend
 // on any summation order.
 #include <cuda_runtime.h>
@@ -68,162 +69,158 @@ __device__ __forceinline__ double fx_to_double(u128 x)
     return (hi * 18446744073709551616.0 + lo) * 0x1.0p-95;
 }
 
-__device__ __forceinline__ u128 shfl_xor_u128(u128 x, int o)
+// ---- value tables ------------------------------------------------------------
+
+__device__ __forceinline__ u128 shfl_up_u128(u128 x, int o)
 {
-    const uint64_t lo = __shfl_xor_sync(FULL, (unsigned long long)(uint64_t)x, o);
-    const uint64_t hi = __shfl_xor_sync(FULL, (unsigned long long)(uint64_t)(x >> 64), o);
+    const uint64_t lo = __shfl_up_sync(FULL, (unsigned long long)(uint64_t)x, o);
+    const uint64_t hi = __shfl_up_sync(FULL, (unsigned long long)(uint64_t)(x >> 64), o);
     return ((u128)hi << 64) | lo;
 }
 
-__device__ __forceinline__ u128 warp_sum_u128(u128 x)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) x += shfl_xor_u128(x, o);
-    return x;
-}
-
-__device__ __forceinline__ float warp_min(float x)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) x = fminf(x, __shfl_xor_sync(FULL, x, o));
-    return x;
-}
-
-__device__ __forceinline__ float warp_max(float x)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) x = fmaxf(x, __shfl_xor_sync(FULL, x, o));
-    return x;
-}
-
-// ---- value tables ------------------------------------------------------------
-
-// One warp per 128-cell step: fixed-point sum, min and max of t per field.
+// One warp per block of VT_BLOCK = 32 steps (4096 cells).  Step by step the
+// warp reads the step's cells (lane: 4 consecutive cells, one float4 per
+// field) and reduces the sum of floor(t 2^95), min and max of t over the
+// step with redux (sums exact in five 24-bit limbs; min/max on the bits of
+// t >= 0, so that empty lanes hold +inf / 0); lane k keeps step k.  Then the
+// lanes scan across the block's steps: the exclusive prefix of the sums, the
+// inclusive prefix and suffix min/max; lane 31's inclusive values are the
+// block's total and (min, max).  Every table row is written once, coalesced.
 template <int M>
-__global__ __launch_bounds__(256) void k_vt_steps(ValueTableArgs v)
+__global__ __launch_bounds__(256) void k_vt_block(ValueTableArgs v)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     float lo[M], sc[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) { lo[m] = v.consts->lo[m]; sc[m] = v.consts->s[m]; }
-    for (uint64_t st = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); st < v.n_steps; st += warps) {
-        const uint64_t idx = st * STEP + lane * 4;
+    if (blockIdx.x == 0 && threadIdx.x < M && v.n_steps % VT_BLOCK == 0)
+        v.loc[(uint64_t)threadIdx.x * (v.n_steps + 1) + v.n_steps] = make_ulonglong2(0ull, 0ull);
+    for (uint64_t b = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); b < v.n_blocks; b += warps) {
+        const uint64_t s0 = b * VT_BLOCK;
+        const int nst = v.n_steps - s0 < (uint64_t)VT_BLOCK ? (int)(v.n_steps - s0) : VT_BLOCK;
+        u128 my_sum[M];
+        uint32_t my_mn[M], my_mx[M];
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            u128 sum = 0;
-            float mn = 3.0f, mx = -1.0f;
-            if (idx < v.n) {
-                const float4 x = __ldg(reinterpret_cast<const float4*>(v.val + m * v.pitch + idx));
-                const float c[4] = {x.x, x.y, x.z, x.w};
+        for (int m = 0; m < M; ++m) { my_sum[m] = 0; my_mn[m] = 0x7F800000u; my_mx[m] = 0u; }
+        // the next step's cells are loaded before this step's reductions
+        float4 xn[M];
+        {
+            const uint64_t idx = s0 * STEP + lane * 4;
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                xn[m] = idx < v.n ? __ldg(reinterpret_cast<const float4*>(v.val + m * v.pitch + idx))
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll 1
+        for (int st = 0; st < nst; ++st) {
+            const uint64_t idx = (s0 + st) * STEP + lane * 4;
+            float4 x[M];
+#pragma unroll
+            for (int m = 0; m < M; ++m) x[m] = xn[m];
+            if (st + 1 < nst) {
+                const uint64_t nidx = idx + STEP;
+#pragma unroll
+                for (int m = 0; m < M; ++m)
+                    if (nidx < v.n) xn[m] = __ldg(reinterpret_cast<const float4*>(v.val + m * v.pitch + nidx));
+            }
+            const int valid = idx < v.n ? (v.n - idx < 4 ? (int)(v.n - idx) : 4) : 0;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const float c[4] = {x[m].x, x[m].y, x[m].z, x[m].w};
+                u128 sum = 0;
+                uint32_t mn = 0x7F800000u, mx = 0u;
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (idx + j < v.n) {
+                    if (j < valid) {
                         const float t = norm_t(c[j], lo[m], sc[m]);
                         sum += fx_of(t);
-                        mn = fminf(mn, t);
-                        mx = fmaxf(mx, t);
+                        mn = min(mn, __float_as_uint(t));
+                        mx = max(mx, __float_as_uint(t));
                     }
+                sum = warp_sum_limbs(sum);
+                mn = __reduce_min_sync(FULL, mn);
+                mx = __reduce_max_sync(FULL, mx);
+                if (lane == st) { my_sum[m] = sum; my_mn[m] = mn; my_mx[m] = mx; }
             }
-            sum = warp_sum_u128(sum);
-            mn = warp_min(mn);
-            mx = warp_max(mx);
-            if (lane == 0) {
-                const uint64_t k = (uint64_t)m * (v.n_steps + 1) + st;
-                v.pre_lo[k] = (uint64_t)sum;
-                v.pre_hi[k] = (uint64_t)(sum >> 64);
-                v.mn[(uint64_t)m * v.level_stride + st] = mn;
-                v.mx[(uint64_t)m * v.level_stride + st] = mx;
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            // lanes >= nst hold the neutral values
+            u128 incl = my_sum[m];
+            uint32_t pmn = my_mn[m], pmx = my_mx[m], smn = my_mn[m], smx = my_mx[m];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const u128 y = shfl_up_u128(incl, o);
+                const uint32_t a = __shfl_up_sync(FULL, pmn, o), bb = __shfl_up_sync(FULL, pmx, o);
+                const uint32_t c = __shfl_down_sync(FULL, smn, o), d = __shfl_down_sync(FULL, smx, o);
+                if (lane >= o) { incl += y; pmn = min(pmn, a); pmx = max(pmx, bb); }
+                if (lane + o < 32) { smn = min(smn, c); smx = max(smx, d); }
+            }
+            const u128 excl = incl - my_sum[m];
+            const uint64_t row = (uint64_t)m * v.n_steps, s = s0 + lane;
+            if (lane <= nst && s <= v.n_steps)      // entry n_steps: the prefix at the data set's end
+                v.loc[(uint64_t)m * (v.n_steps + 1) + s] =
+                    make_ulonglong2((unsigned long long)(uint64_t)excl, (unsigned long long)(uint64_t)(excl >> 64));
+            if (lane < nst) {
+                v.raw[row + s] = make_float2(__uint_as_float(my_mn[m]), __uint_as_float(my_mx[m]));
+                v.pre[row + s] = make_float2(__uint_as_float(pmn), __uint_as_float(pmx));
+                v.suf[row + s] = make_float2(__uint_as_float(smn), __uint_as_float(smx));
+            }
+            if (lane == 31) {
+                // block total into blk (turned into the exclusive prefix by k_vt_top),
+                // block (min, max) into level 0 of the sparse table
+                v.blk[(uint64_t)m * (v.n_blocks + 1) + b] =
+                    make_ulonglong2((unsigned long long)(uint64_t)incl, (unsigned long long)(uint64_t)(incl >> 64));
+                v.bmm[(uint64_t)m * v.b_levels * v.n_blocks + b] = make_float2(__uint_as_float(pmn), __uint_as_float(pmx));
             }
         }
     }
 }
 
-// Exclusive scan of the step sums of every field, in blocks of 1024 steps
-// (phase 1: in-block scan and block totals; phase 2: scan of the totals;
-// phase 3: add the block offsets).  u128 adds are exact and associative.
-__global__ __launch_bounds__(256) void k_vt_scan1(ValueTableArgs v, uint64_t* tot_lo, uint64_t* tot_hi)
+// One CTA per field: the block totals become their exclusive prefix (entry
+// n_blocks: the field's total).  Thread t takes a contiguous run of blocks.
+constexpr int VT_TOP_THREADS = 1024;
+__global__ __launch_bounds__(VT_TOP_THREADS) void k_vt_top(ValueTableArgs v)
 {
-    __shared__ u128 s[256];
-    const uint32_t m = blockIdx.y;
-    const uint64_t b0 = (uint64_t)blockIdx.x * 1024;
-    const uint64_t row = (uint64_t)m * (v.n_steps + 1);
-    u128 x[4], acc = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const uint64_t k = b0 + threadIdx.x * 4 + i;
-        x[i] = k < v.n_steps ? (((u128)v.pre_hi[row + k] << 64) | v.pre_lo[row + k]) : (u128)0;
-        acc += x[i];
-    }
-    s[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = 1; o < 256; o <<= 1) {            // Hillis-Steele inclusive scan of thread sums
-        u128 y = threadIdx.x >= o ? s[threadIdx.x - o] : (u128)0;
-        __syncthreads();
-        s[threadIdx.x] += y;
-        __syncthreads();
-    }
-    u128 run = s[threadIdx.x] - acc;               // exclusive prefix of this thread
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const uint64_t k = b0 + threadIdx.x * 4 + i;
-        if (k < v.n_steps) {
-            v.pre_lo[row + k] = (uint64_t)run;
-            v.pre_hi[row + k] = (uint64_t)(run >> 64);
-        }
-        run += x[i];
-    }
-    if (threadIdx.x == 255) {
-        const uint64_t nb = gridDim.x;
-        tot_lo[m * nb + blockIdx.x] = (uint64_t)s[255];
-        tot_hi[m * nb + blockIdx.x] = (uint64_t)(s[255] >> 64);
-    }
-}
-
-__global__ void k_vt_scan2(ValueTableArgs v, uint64_t* tot_lo, uint64_t* tot_hi, uint32_t nb)
-{
-    if (threadIdx.x != 0) return;
+    __shared__ u128 s_part[VT_TOP_THREADS];
     const uint32_t m = blockIdx.x;
-    u128 run = 0;
-    for (uint32_t b = 0; b < nb; ++b) {
-        const u128 t = ((u128)tot_hi[m * nb + b] << 64) | tot_lo[m * nb + b];
-        tot_lo[m * nb + b] = (uint64_t)run;
-        tot_hi[m * nb + b] = (uint64_t)(run >> 64);
-        run += t;
+    ulonglong2* blk = v.blk + (uint64_t)m * (v.n_blocks + 1);
+    const uint64_t per = (v.n_blocks + VT_TOP_THREADS - 1) / VT_TOP_THREADS;
+    const uint64_t b0 = threadIdx.x * per, b1 = b0 + per < v.n_blocks ? b0 + per : v.n_blocks;
+    u128 t = 0;
+    for (uint64_t b = b0; b < b1; ++b) t += ((u128)blk[b].y << 64) | blk[b].x;
+    s_part[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = 1; o < VT_TOP_THREADS; o <<= 1) {          // inclusive scan of the thread totals
+        const u128 y = threadIdx.x >= (unsigned)o ? s_part[threadIdx.x - o] : (u128)0;
+        __syncthreads();
+        s_part[threadIdx.x] += y;
+        __syncthreads();
     }
-    const uint64_t row = (uint64_t)m * (v.n_steps + 1);
-    v.pre_lo[row + v.n_steps] = (uint64_t)run;           // prefix up to the end
-    v.pre_hi[row + v.n_steps] = (uint64_t)(run >> 64);
-}
-
-__global__ __launch_bounds__(256) void k_vt_scan3(ValueTableArgs v, const uint64_t* tot_lo, const uint64_t* tot_hi)
-{
-    const uint32_t m = blockIdx.y;
-    const uint64_t nb = gridDim.x;
-    const u128 off = ((u128)tot_hi[m * nb + blockIdx.x] << 64) | tot_lo[m * nb + blockIdx.x];
-    const uint64_t row = (uint64_t)m * (v.n_steps + 1);
-    for (int i = 0; i < 4; ++i) {
-        const uint64_t k = (uint64_t)blockIdx.x * 1024 + threadIdx.x * 4 + i;
-        if (k < v.n_steps) {
-            const u128 x = (((u128)v.pre_hi[row + k] << 64) | v.pre_lo[row + k]) + off;
-            v.pre_lo[row + k] = (uint64_t)x;
-            v.pre_hi[row + k] = (uint64_t)(x >> 64);
-        }
+    u128 run = s_part[threadIdx.x] - t;
+    for (uint64_t b = b0; b < b1; ++b) {
+        const u128 x = ((u128)blk[b].y << 64) | blk[b].x;
+        blk[b] = make_ulonglong2((unsigned long long)(uint64_t)run, (unsigned long long)(uint64_t)(run >> 64));
+        run += x;
+    }
+    if (threadIdx.x == VT_TOP_THREADS - 1) {
+        const u128 tot = s_part[VT_TOP_THREADS - 1];
+        blk[v.n_blocks] = make_ulonglong2((unsigned long long)(uint64_t)tot, (unsigned long long)(uint64_t)(tot >> 64));
     }
 }
 
-// Level l of the min/max sparse table: entry i covers steps [i, i + 2^l)
-// (entries whose range would pass the last step are never read).
+// Level l of the blocks' sparse table: entry i covers blocks [i, i + 2^l)
+// (entries whose run would pass the last block are never read).
 __global__ void k_vt_level(ValueTableArgs v, int l)
 {
     const uint32_t m = blockIdx.y;
-    const uint64_t half = 1ull << (l - 1), n = v.n_steps + 1 - 2 * half;   // i + 2^l <= n_steps
-    float* mn = v.mn + (uint64_t)m * v.level_stride;
-    float* mx = v.mx + (uint64_t)m * v.level_stride;
-    const uint64_t prev = (uint64_t)(l - 1) * v.n_steps, cur = (uint64_t)l * v.n_steps;
+    const uint64_t half = 1ull << (l - 1), n = v.n_blocks + 1 - 2 * half;   // i + 2^l <= n_blocks
+    float2* t = v.bmm + (uint64_t)m * v.b_levels * v.n_blocks;
+    const uint64_t prev = (uint64_t)(l - 1) * v.n_blocks, cur = (uint64_t)l * v.n_blocks;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        mn[cur + i] = fminf(mn[prev + i], mn[prev + i + half]);
-        mx[cur + i] = fmaxf(mx[prev + i], mx[prev + i + half]);
+        const float2 a = t[prev + i], b = t[prev + i + half];
+        t[cur + i] = make_float2(fminf(a.x, b.x), fmaxf(a.y, b.y));
     }
 }
 
@@ -257,16 +254,22 @@ __device__ __forceinline__ uint64_t find_chunk(const unsigned long long* prefix,
 // cell is converted once; min/max work on the bits of t >= 0 (empty: +inf, 0,
 // which are neutral for values in [0, 1]).  Written by lane 0 to the records
 // of boundary j.
+// With alpha sums (qa.apart), also the fixed-point alpha sums of the same two
+// cell sets, the alpha of a cell from the CTA's shared tables s_tf (T + 1
+// entries per field).
 template <int M>
 __device__ __forceinline__ void step_partials(const UpdateArgs& a, const UpdateConsts* C, const QueryArgs& qa,
                                               uint32_t j, uint64_t stb, uint64_t ste, uint64_t H, uint64_t first,
-                                              int lane)
+                                              int lane, const float* s_tf)
 {
     const uint64_t idx = stb + lane * 4;
+    const float Tf = (float)a.T;
+    const uint32_t T1 = a.T + 1;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
         const float lo = C->lo[m], sc = C->s[m];
         u128 ts = 0, hs = 0;
+        unsigned long long ta = 0, ha = 0;
         uint32_t tmn = 0x7F800000u, tmx = 0u, hmn = 0x7F800000u, hmx = 0u;
         if (idx < ste) {
             const float4 x = __ldg(reinterpret_cast<const float4*>(a.val + m * a.pitch + idx));
@@ -277,13 +280,16 @@ __device__ __forceinline__ void step_partials(const UpdateArgs& a, const UpdateC
                 const float t = norm_t(c[k], lo, sc);
                 const uint32_t tb = __float_as_uint(t);
                 const u128 f = fx_of(t);
+                const uint32_t af = qa.apart ? alpha_fx(s_tf[m * T1 + floor_small(__fmul_rn(t, Tf))]) : 0u;
                 if (cell < H) {
                     ts += f;
+                    ta += af;
                     tmn = min(tmn, tb);
                     tmx = max(tmx, tb);
                 }
                 if (cell >= first && cell < ste) {
                     hs += f;
+                    ha += af;
                     hmn = min(hmn, tb);
                     hmx = max(hmx, tb);
                 }
@@ -295,12 +301,20 @@ __device__ __forceinline__ void step_partials(const UpdateArgs& a, const UpdateC
         tmx = __reduce_max_sync(FULL, tmx);
         hmn = __reduce_min_sync(FULL, hmn);
         hmx = __reduce_max_sync(FULL, hmx);
+        if (qa.apart) {                                            // uniform over the launch
+            ta = warp_total_small(ta);
+            ha = warp_total_small(ha);
+        }
         if (lane == 0) {
             const uint64_t kt = ((uint64_t)j * 2 + 0) * M + m, kh = kt + M;
             qa.psum[kt] = make_ulonglong2((unsigned long long)(uint64_t)ts, (unsigned long long)(uint64_t)(ts >> 64));
             qa.pmm[kt] = make_float2(__uint_as_float(tmn), __uint_as_float(tmx));
             qa.psum[kh] = make_ulonglong2((unsigned long long)(uint64_t)hs, (unsigned long long)(uint64_t)(hs >> 64));
             qa.pmm[kh] = make_float2(__uint_as_float(hmn), __uint_as_float(hmx));
+            if (qa.apart) {
+                qa.apart[kt] = ta;
+                qa.apart[kh] = ha;
+            }
         }
     }
 }
@@ -376,7 +390,7 @@ __device__ __forceinline__ void bounds_one(const UpdateArgs& a, const QueryArgs&
     // partial terms over the step of cell H-1 (H >= 1: the step's first cell starts before X)
     const uint64_t stb = (H - 1) / STEP * STEP;
     const uint64_t ste = stb + STEP < a.n ? stb + STEP : a.n;
-    step_partials<M>(a, C, qa, j, stb, ste, H, S ? H - 1 : H, lane);
+    step_partials<M>(a, C, qa, j, stb, ste, H, S ? H - 1 : H, lane, s_tf);
     if (lane == 0) {
         qa.H[j] = H;
         qa.S[j] = S;
@@ -394,16 +408,53 @@ __global__ __launch_bounds__(256) void k_bounds(UpdateArgs a, QueryArgs qa)
     bounds_one<M, PM>(a, qa, s_tf, j, threadIdx.x & 31);
 }
 
-// Min/max of t over steps [s0, s1) (s0 < s1) of one field: two overlapping
-// power-of-two ranges of the sparse table.
+// Prefix of the step sums of field m up to step s (steps [0, s)).
+__device__ __forceinline__ u128 steps_prefix(const ValueTableArgs& v, uint32_t m, uint64_t s)
+{
+    const ulonglong2 a = v.blk[(uint64_t)m * (v.n_blocks + 1) + s / VT_BLOCK];
+    const ulonglong2 b = v.loc[(uint64_t)m * (v.n_steps + 1) + s];
+    return (((u128)a.y << 64) | a.x) + (((u128)b.y << 64) | b.x);
+}
+
+// Min/max of t over steps [s0, s1) (s0 < s1) of one field: inside one block
+// the steps' own entries; across blocks the suffix of the first block, the
+// prefix of the last one and, between them, two overlapping power-of-two
+// runs of the blocks' sparse table.
 __device__ __forceinline__ void steps_minmax(const ValueTableArgs& v, uint32_t m, uint64_t s0, uint64_t s1,
                                              float& mn, float& mx)
 {
-    const int k = 63 - __clzll((long long)(s1 - s0));
-    const uint64_t row = (uint64_t)m * v.level_stride + (uint64_t)k * v.n_steps;
-    const uint64_t b = s1 - (1ull << k);
-    mn = fminf(mn, fminf(v.mn[row + s0], v.mn[row + b]));
-    mx = fmaxf(mx, fmaxf(v.mx[row + s0], v.mx[row + b]));
+    const uint64_t row = (uint64_t)m * v.n_steps;
+    const uint64_t b0 = s0 / VT_BLOCK, b1 = (s1 - 1) / VT_BLOCK;
+    if (b0 == b1) {
+        for (uint64_t s = s0; s < s1; ++s) {
+            const float2 r = v.raw[row + s];
+            mn = fminf(mn, r.x);
+            mx = fmaxf(mx, r.y);
+        }
+        return;
+    }
+    const float2 a = v.suf[row + s0], b = v.pre[row + s1 - 1];
+    mn = fminf(mn, fminf(a.x, b.x));
+    mx = fmaxf(mx, fmaxf(a.y, b.y));
+    if (b1 > b0 + 1) {
+        const uint64_t c0 = b0 + 1, c1 = b1;                   // whole blocks [c0, c1)
+        const int k = 63 - __clzll((long long)(c1 - c0));
+        const float2* t = v.bmm + ((uint64_t)m * v.b_levels + (uint64_t)k) * v.n_blocks;
+        const float2 x = t[c0], y = t[c1 - (1ull << k)];
+        mn = fminf(mn, fminf(x.x, y.x));
+        mx = fmaxf(mx, fmaxf(x.y, y.y));
+    }
+}
+
+// Prefix of the fixed-point alpha sums of field m over steps [0, s): the
+// exclusive prefix of s's chunk plus the steps of that chunk before s.
+__device__ __forceinline__ unsigned long long alpha_prefix(const QueryArgs& qa, uint32_t m, uint64_t s)
+{
+    const uint64_t c = s / STEPS, r = s - c * STEPS;
+    unsigned long long x = qa.achunk[(uint64_t)m * (qa.a_chunks + 1) + c];
+    const unsigned long long* st = qa.astep + (uint64_t)m * qa.a_chunks * STEPS + c * STEPS;
+    for (uint64_t i = 0; i < r; ++i) x += st[i];
+    return x;
 }
 
 // One thread per pixel: the bins of cells [lo_p, hi_p].  With s_p the step of
@@ -429,6 +480,10 @@ __device__ __forceinline__ void pixels_field(const UpdateArgs& a, const QueryArg
         a.mean[k] = 0.0f;
         a.y[k] = 0.0f;
         if (m == 0) a.count[p] = 0u;
+        if (qa.apart) {
+            a.asum[k] = 0.0;
+            a.amean[k] = 0.0f;
+        }
         return;
     }
     const uint64_t c1 = Hn;
@@ -439,6 +494,7 @@ __device__ __forceinline__ void pixels_field(const UpdateArgs& a, const QueryArg
     const uint64_t w0 = has_l ? sp + 1 : 0, w1 = has_r ? sq : v.n_steps;   // whole steps [w0, w1)
     float mn = 3.0f, mx = -1.0f;
     u128 sum = 0;
+    unsigned long long asum = 0;                                     // fixed-point alpha sum
     if (one_step) {
         const float lo = C->lo[m], sc = C->s[m];
         for (uint64_t c = lo_c; c < c1; ++c) {
@@ -446,14 +502,20 @@ __device__ __forceinline__ void pixels_field(const UpdateArgs& a, const QueryArg
             sum += fx_of(t);
             mn = fminf(mn, t);
             mx = fmaxf(mx, t);
+            if (qa.apart) {
+                const uint32_t e = floor_small(__fmul_rn(t, (float)a.T));
+                asum += alpha_fx(a.tf[m * a.T + (e < a.T ? e : a.T - 1)]);
+            }
         }
     } else {
+        if (qa.apart) {
+            if (w1 > w0) asum = alpha_prefix(qa, m, w1) - alpha_prefix(qa, m, w0);
+            if (has_l) asum += qa.apart[(bl * 2 + 1) * M + m];
+            if (has_r) asum += qa.apart[(br * 2 + 0) * M + m];
+        }
         if (w1 > w0) {
             steps_minmax(v, m, w0, w1, mn, mx);
-            const uint64_t row = (uint64_t)m * (v.n_steps + 1);
-            const u128 pa = ((u128)v.pre_hi[row + w0] << 64) | v.pre_lo[row + w0];
-            const u128 pb = ((u128)v.pre_hi[row + w1] << 64) | v.pre_lo[row + w1];
-            sum = pb - pa;
+            sum = steps_prefix(v, m, w1) - steps_prefix(v, m, w0);
         }
         if (has_l) {
             const uint64_t q = (bl * 2 + 1) * M + m;
@@ -480,6 +542,11 @@ __device__ __forceinline__ void pixels_field(const UpdateArgs& a, const QueryArg
     a.mean[k] = mean;
     a.y[k] = a.tf[m * a.T + tf_entry(mean, (float)a.T, a.T - 1)];
     if (m == 0) a.count[p] = count;
+    if (qa.apart) {
+        const double as = (double)asum * (1.0 / 2147483648.0);           // one rounding to double
+        a.asum[k] = as;
+        a.amean[k] = __double2float_rn(__ddiv_rn(as, (double)count));
+    }
 }
 
 // All fields of pixel p by one thread (the batched queries, which have many
@@ -523,6 +590,10 @@ __device__ __forceinline__ void pair_args(const UpdateArgs& a, const BatchArgs& 
     qk.psum = b.psum + pd.src_hs_off * 2 * a.M;
     qk.pmm = b.pmm + pd.src_hs_off * 2 * a.M;
     qk.hstride = pd.hstride;
+    qk.astep = nullptr;                      // batches have no alpha means
+    qk.achunk = nullptr;
+    qk.apart = nullptr;
+    qk.a_chunks = 0;
 }
 
 template <int M, int PM>
@@ -546,11 +617,16 @@ __global__ __launch_bounds__(256) void k_pixels_batch(UpdateArgs a, BatchArgs b,
 {
     const PairDesc pd = b.pairs[blockIdx.y];
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= pd.W) return;
-    UpdateArgs ak;
-    QueryArgs qk;
-    pair_args(a, b, pd, ak, qk);
-    pixels_one<M>(ak, qk, v, p);
+    if (p < pd.W) {
+        UpdateArgs ak;
+        QueryArgs qk;
+        pair_args(a, b, pd, ak, qk);
+        pixels_one<M>(ak, qk, v, p);
+    }
+    if (b.stamps && blockIdx.x * blockDim.x < pd.W) {      // blocks with pixels: when they end
+        __syncthreads();
+        if (threadIdx.x == 0) atomicMax(&b.stamps[1], global_ns());
+    }
 }
 
 template <int M, int PM>
@@ -591,19 +667,16 @@ cudaError_t run_bins_batch_m(cudaStream_t s, const UpdateArgs& a, const BatchArg
 }
 
 template <int M>
-cudaError_t run_tables(cudaStream_t s, const ValueTableArgs& v, uint64_t* tot_lo, uint64_t* tot_hi)
+cudaError_t run_tables(cudaStream_t s, const ValueTableArgs& v)
 {
-    if (v.n_steps == 0) return cudaSuccess;
-    const uint64_t warps_blocks = (v.n_steps + 7) / 8;
-    k_vt_steps<M><<<(unsigned)(warps_blocks < 148ull * 16 ? warps_blocks : 148ull * 16), 256, 0, s>>>(v);
-    const uint32_t nb = (uint32_t)((v.n_steps + 1023) / 1024);
-    k_vt_scan1<<<dim3(nb, M), 256, 0, s>>>(v, tot_lo, tot_hi);
-    k_vt_scan2<<<M, 32, 0, s>>>(v, tot_lo, tot_hi, nb);
-    k_vt_scan3<<<dim3(nb, M), 256, 0, s>>>(v, tot_lo, tot_hi);
-    for (int l = 1; l < v.n_levels; ++l) {
-        const uint64_t n = v.n_steps + 1 - (2ull << (l - 1));
+    if (v.n_blocks == 0) return cudaSuccess;
+    const uint64_t cta = (v.n_blocks + 7) / 8;                 // 8 warps (blocks of steps) per CTA
+    k_vt_block<M><<<(unsigned)(cta < 148ull * 4 ? cta : 148ull * 4), 256, 0, s>>>(v);
+    k_vt_top<<<M, VT_TOP_THREADS, 0, s>>>(v);
+    for (int l = 1; l < v.b_levels; ++l) {
+        const uint64_t n = v.n_blocks + 1 - (2ull << (l - 1));
         const uint64_t blocks = (n + 255) / 256;
-        k_vt_level<<<dim3((unsigned)(blocks < 4096 ? blocks : 4096), M), 256, 0, s>>>(v, l);
+        k_vt_level<<<dim3((unsigned)(blocks < 1024 ? blocks : 1024), M), 256, 0, s>>>(v, l);
     }
     return cudaGetLastError();
 }
@@ -623,10 +696,9 @@ cudaError_t run_tables(cudaStream_t s, const ValueTableArgs& v, uint64_t* tot_lo
         default: return cudaErrorInvalidValue;    \
     }
 
-cudaError_t launch_value_tables(cudaStream_t s, uint32_t M, const ValueTableArgs& v, uint64_t* tot_lo,
-                                uint64_t* tot_hi)
+cudaError_t launch_value_tables(cudaStream_t s, uint32_t M, const ValueTableArgs& v)
 {
-    DVL_DISPATCH_M2(run_tables, M, s, v, tot_lo, tot_hi)
+    DVL_DISPATCH_M2(run_tables, M, s, v)
 }
 
 cudaError_t launch_bins(cudaStream_t s, const UpdateArgs& a, const QueryArgs& qa, const ValueTableArgs& v)
@@ -639,11 +711,10 @@ cudaError_t launch_bins_batch(cudaStream_t s, const UpdateArgs& a, const BatchAr
     DVL_DISPATCH_M2(run_bins_batch_m, a.M, s, a, b, v)
 }
 
-uint64_t value_table_levels(uint64_t n_steps, uint64_t* stride)
+int value_table_levels(uint64_t n_blocks)
 {
-    uint64_t levels = 1;                      // sparse table: levels 0 .. floor(log2(n_steps))
-    while ((2ull << (levels - 1)) <= n_steps) ++levels;
-    *stride = n_steps * levels;
+    int levels = 0;                           // sparse table: levels 0 .. floor(log2(n_blocks))
+    while (n_blocks >> levels) ++levels;
     return levels;
 }
 

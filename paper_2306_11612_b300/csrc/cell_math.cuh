@@ -33,6 +33,14 @@ __device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long 
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// The device's global nanosecond clock.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ float ordered_to_float(uint32_t u)
 {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
@@ -154,6 +162,20 @@ __device__ __forceinline__ float lds_f32(uint32_t addr)
 }
 constexpr uint32_t BITS_2P23 = 0x4B000000u;         // bits of 2^23
 
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr)
+{
+    uint32_t r;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r) : "r"(addr));
+    return r;
+}
+
+// A cell's alpha in the fixed point of the alpha-mean sums: rint(alpha 2^31)
+// (alpha in [0, 1], so at most 2^31; the scaling is exact).  Every kernel
+// that adds alphas converts with this one function, so the sums are exact
+// integers and independent of the order of addition.
+constexpr float ALPHA_FX_ONE = 2147483648.0f;        // 2^31
+__device__ __forceinline__ uint32_t alpha_fx(float A) { return __float2uint_rn(__fmul_rn(A, ALPHA_FX_ONE)); }
+
 // Per-cell constants in registers, specialised on the field count M and the
 // exponent mode.  The alpha tables live in shared memory with T+1 entries per
 // field (entry T repeats entry T-1) so that t = 1 needs no clamp.
@@ -210,6 +232,39 @@ struct Cell {
         float f = importance<PM>(spread<M>(al), L, inv_vmax, mb, ma, wshift, n2, P);
         return __float2uint_rn(__fmul_rn(f, qscale));
     }
+
+    // width_p2, also adding each field's fixed-point alpha (alpha_fx of the
+    // same entry, from a second table `aoff` bytes after the first) to ax[m]
+    __device__ __forceinline__ uint32_t width_p2_alpha(const float* v, uint32_t L, const uint32_t* cm, uint32_t aoff,
+                                                       unsigned long long (&ax)[M]) const
+    {
+        float al[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const float t = mul_sat(__fsub_rn(v[m], lo[m]), s[m]);
+            const uint32_t addr = __float_as_uint(fma_rz(t, Tf, 8388608.0f)) * 4u + cm[m];
+            al[m] = lds_f32(addr);
+            ax[m] += lds_u32(addr + aoff);
+        }
+        float f = importance<PM>(spread<M>(al), L, inv_vmax, mb, ma, wshift, n2, P);
+        return __float2uint_rn(__fmul_rn(f, qscale));
+    }
+
+    // width from normalised values, also adding the fixed-point alphas
+    // (s_ax: the u32 twin of the table s_tf)
+    __device__ __forceinline__ uint32_t width_alpha(const float* t, uint32_t L, const float* s_tf,
+                                                    const uint32_t* s_ax, unsigned long long (&ax)[M]) const
+    {
+        float al[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const uint32_t e = m * T1 + floor_small(__fmul_rn(t[m], Tf));
+            al[m] = s_tf[e];
+            ax[m] += s_ax[e];
+        }
+        float f = importance<PM>(spread<M>(al), L, inv_vmax, mb, ma, wshift, n2, P);
+        return __float2uint_rn(__fmul_rn(f, qscale));
+    }
 };
 
 template <int M>
@@ -219,6 +274,17 @@ __device__ __forceinline__ void load_table(float* s_tf, const float* tf, uint32_
     for (uint32_t i = threadIdx.x; i < M * T1; i += blockDim.x) {
         uint32_t m = i / T1, e = i - m * T1;
         s_tf[i] = tf[m * T + (e < T ? e : T - 1)];
+    }
+}
+
+// The fixed-point twin of load_table: s_ax[i] = alpha_fx(s_tf[i]).
+template <int M>
+__device__ __forceinline__ void load_table_fx(uint32_t* s_ax, const float* tf, uint32_t T)
+{
+    const uint32_t T1 = T + 1;
+    for (uint32_t i = threadIdx.x; i < M * T1; i += blockDim.x) {
+        uint32_t m = i / T1, e = i - m * T1;
+        s_ax[i] = alpha_fx(tf[m * T + (e < T ? e : T - 1)]);
     }
 }
 

@@ -74,6 +74,10 @@ struct dvl_ctx {
     float *d_mean = nullptr, *d_y = nullptr;
     double* d_asum = nullptr;         // alpha sums / means (want_alpha)
     float* d_amean = nullptr;
+    unsigned long long* d_astep = nullptr;    // pass A's per-step / per-chunk alpha sums (want_alpha)
+    unsigned long long* d_achunk = nullptr;
+    unsigned long long* d_apart = nullptr;    // boundary partial alpha sums, (W + 1) x 2 x DVL_MAX_FIELDS
+    uint64_t astep_chunks = 0;                // chunks the alpha step arrays were sized for
     uint32_t alpha_cap = 0;
     double* d_gtab = nullptr;         // adjoint scratch (M x T)
     double* d_gpart = nullptr;        // per-CTA adjoint tables
@@ -85,8 +89,6 @@ struct dvl_ctx {
     dvl_params last_prm{};
     // value tables for range-query bins (per data set and TF domain)
     ValueTableArgs vt{};
-    uint64_t* d_vt_tot_lo = nullptr;
-    uint64_t* d_vt_tot_hi = nullptr;
     bool vt_valid = false;
     std::vector<float> vt_dom;
     unsigned long long* d_H = nullptr;
@@ -114,6 +116,7 @@ struct dvl_ctx {
     uint8_t* d_bS = nullptr;
     ulonglong2* d_bpsum = nullptr;
     float2* d_bpmm = nullptr;
+    unsigned long long* d_bstamps = nullptr;   // 2 words: device clock at batch start / end
     size_t btf_cap = 0, bk_cap = 0, pairs_cap = 0, bbin_cap = 0, bcnt_cap = 0, bhs_cap = 0;
     std::vector<PairDesc> b_pairs;        // of the last batch
     bool have_batch = false;
@@ -189,7 +192,7 @@ void free_batch(dvl_ctx* c)
     dfree(c->d_btf); dfree(c->d_bdom); dfree(c->d_bconsts); dfree(c->d_btickets); dfree(c->d_btile); dfree(c->d_bprefix);
     dfree(c->d_bsteps); dfree(c->d_pairs); dfree(c->d_bsum); dfree(c->d_bvmin); dfree(c->d_bvmax);
     dfree(c->d_bcount); dfree(c->d_bmean); dfree(c->d_by); dfree(c->d_bH); dfree(c->d_bS);
-    dfree(c->d_bpsum); dfree(c->d_bpmm);
+    dfree(c->d_bpsum); dfree(c->d_bpmm); dfree(c->d_bstamps);
     c->btf_cap = c->bk_cap = c->pairs_cap = c->bbin_cap = c->bcnt_cap = c->bhs_cap = 0;
     for (auto& kv : c->b_graphs) cudaGraphExecDestroy(kv.second.first);
     c->b_graphs.clear();
@@ -202,8 +205,7 @@ void free_dataset(dvl_ctx* c)
     dfree(c->d_val); dfree(c->d_lev); dfree(c->d_perm); dfree(c->d_keys);
     dfree(c->d_keys_alt); dfree(c->d_vals_alt); dfree(c->d_rs_status);
     dfree(c->d_tile_status); dfree(c->d_chunk_prefix); dfree(c->d_step_sums);
-    dfree(c->vt.pre_lo); dfree(c->vt.pre_hi); dfree(c->vt.mn); dfree(c->vt.mx);
-    dfree(c->d_vt_tot_lo); dfree(c->d_vt_tot_hi);
+    dfree(c->vt.loc); dfree(c->vt.blk); dfree(c->vt.raw); dfree(c->vt.pre); dfree(c->vt.suf); dfree(c->vt.bmm);
     c->vt = ValueTableArgs{};
     c->vt_valid = false;
     free_batch(c);
@@ -235,7 +237,7 @@ cudaError_t enqueue_batch(dvl_ctx* c, const UpdateArgs& a, const BatchArgs& b, c
         if ((e = cudaMemsetAsync(c->d_by, 0, nb * sizeof(float), s)) != cudaSuccess) return e;
         return cudaMemsetAsync(c->d_bcount, 0, nc * sizeof(uint32_t), s);
     }
-    if (build_vt && (e = launch_value_tables(s, a.M, v, c->d_vt_tot_lo, c->d_vt_tot_hi)) != cudaSuccess) return e;
+    if (build_vt && (e = launch_value_tables(s, a.M, v)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
     if ((e = launch_passA_batch(s, a, b)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], s);
@@ -330,6 +332,8 @@ int gather_values(dvl_ctx* c, const uint8_t* lin, uint8_t* lout)
 
 }  // namespace
 
+const unsigned long long* dvl::batch_stamps(const dvl_ctx* c) { return c ? c->d_bstamps : nullptr; }
+
 extern "C" {
 
 const char* dvl_status_string(int s)
@@ -400,6 +404,8 @@ void dvl_destroy(dvl_ctx* c)
     dfree(c->d_hist); dfree(c->d_rs_counters); dfree(c->d_tf); dfree(c->d_dom);
     dfree(c->d_sum); dfree(c->d_vmin); dfree(c->d_vmax); dfree(c->d_count);
     dfree(c->d_mean); dfree(c->d_y); dfree(c->d_asum); dfree(c->d_amean); dfree(c->d_ctrl);
+    dfree(c->d_astep); dfree(c->d_achunk); dfree(c->d_apart);
+    c->astep_chunks = 0;
     dfree(c->d_gtab); dfree(c->d_gpart); dfree(c->d_gin); dfree(c->d_gout); dfree(c->d_H); dfree(c->d_S);
     dfree(c->d_psum); dfree(c->d_pmm); dfree(c->d_img); dfree(c->d_mask); dfree(c->d_ranges);
     for (auto& set : c->ev)
@@ -535,7 +541,10 @@ int dvl_build_order(dvl_ctx* c, int sfc)
         if (rc) return rc;
     }
     const uint64_t tiles = (n + TILE - 1) / TILE;
-    CK(dalloc(c->d_tile_status, tiles), "alloc scan state");
+    // one status word per tile, and at least one per chunk-scan block and
+    // quantity (the widths and each field's alpha sums)
+    const uint64_t scan_blocks = (tiles * WARPS + 2047) / 2048;
+    CK(dalloc(c->d_tile_status, std::max<uint64_t>(tiles, (1 + DVL_MAX_FIELDS) * scan_blocks)), "alloc scan state");
     CK(dalloc(c->d_chunk_prefix, tiles * WARPS), "alloc scan state");
     CK(dalloc(c->d_step_sums, tiles * WARPS * STEPS), "alloc scan state");
     {
@@ -545,14 +554,15 @@ int dvl_build_order(dvl_ctx* c, int sfc)
         v.pitch = p;
         v.consts = c->d_consts;
         v.n_steps = (n + STEP - 1) / STEP;
-        v.n_levels = (int)value_table_levels(v.n_steps, &v.level_stride);
-        const uint64_t nb = (v.n_steps + 1023) / 1024;
-        CK(dalloc(v.pre_lo, (size_t)c->M * (v.n_steps + 1)), "alloc value tables");
-        CK(dalloc(v.pre_hi, (size_t)c->M * (v.n_steps + 1)), "alloc value tables");
-        CK(dalloc(v.mn, (size_t)c->M * (v.level_stride ? v.level_stride : 1)), "alloc value tables");
-        CK(dalloc(v.mx, (size_t)c->M * (v.level_stride ? v.level_stride : 1)), "alloc value tables");
-        CK(dalloc(c->d_vt_tot_lo, (size_t)c->M * (nb ? nb : 1)), "alloc value tables");
-        CK(dalloc(c->d_vt_tot_hi, (size_t)c->M * (nb ? nb : 1)), "alloc value tables");
+        v.n_blocks = (v.n_steps + VT_BLOCK - 1) / VT_BLOCK;
+        v.b_levels = value_table_levels(v.n_blocks);
+        const size_t M = c->M, ns = v.n_steps ? v.n_steps : 1;
+        CK(dalloc(v.loc, M * (v.n_steps + 1)), "alloc value tables");
+        CK(dalloc(v.blk, M * (v.n_blocks + 1)), "alloc value tables");
+        CK(dalloc(v.raw, M * ns), "alloc value tables");
+        CK(dalloc(v.pre, M * ns), "alloc value tables");
+        CK(dalloc(v.suf, M * ns), "alloc value tables");
+        CK(dalloc(v.bmm, M * (v.b_levels ? (size_t)v.b_levels * v.n_blocks : 1)), "alloc value tables");
         c->vt_valid = false;
     }
     int rc = take_device_error(c);
@@ -764,7 +774,15 @@ static int ensure_alpha_buffers(dvl_ctx* c, uint32_t W)
         CK(cudaStreamSynchronize(c->stream), "synchronize");
         CK(dalloc(c->d_asum, (size_t)c->M * W), "alloc alpha sums");
         CK(dalloc(c->d_amean, (size_t)c->M * W), "alloc alpha means");
+        CK(dalloc(c->d_apart, (size_t)(W + 1) * 2 * DVL_MAX_FIELDS), "alloc alpha sums");
         c->alpha_cap = W;
+    }
+    const uint64_t chunks = (c->n + TILE - 1) / TILE * WARPS;   // pass A's chunk count
+    if (chunks != c->astep_chunks || !c->d_astep) {
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        CK(dalloc(c->d_astep, (size_t)c->M * chunks * STEPS), "alloc alpha sums");
+        CK(dalloc(c->d_achunk, (size_t)c->M * (chunks + 1)), "alloc alpha sums");
+        c->astep_chunks = chunks;
     }
     return DVL_OK;
 }
@@ -795,10 +813,11 @@ static UpdateArgs make_args(dvl_ctx* c, const dvl_params& p)
     a.y = c->d_y;
     a.asum = nullptr;
     a.amean = nullptr;
+    a.astep = nullptr;
+    a.achunk = nullptr;
+    a.apart = nullptr;
     a.vt = nullptr;
     a.vt_build = 0;
-    a.vt_tot_lo = c->d_vt_tot_lo;
-    a.vt_tot_hi = c->d_vt_tot_hi;
     a.H = c->d_H;
     a.S = c->d_S;
     a.psum = c->d_psum;
@@ -827,27 +846,28 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
         rc = ensure_alpha_buffers(c, p->width);
         if (rc) return rc;
     }
-    bool build_vt = false;
-    if (!p->want_alpha) {
-        // bins from range queries; the value tables depend on the TF domains
-        if (p->width + 1 > c->HS_cap) {
-            CK(cudaStreamSynchronize(c->stream), "synchronize");
-            CK(dalloc(c->d_H, p->width + 1), "alloc pixel bounds");
-            CK(dalloc(c->d_S, p->width + 1), "alloc pixel bounds");
-            CK(dalloc(c->d_psum, (size_t)(p->width + 1) * 2 * DVL_MAX_FIELDS), "alloc pixel bounds");
-            CK(dalloc(c->d_pmm, (size_t)(p->width + 1) * 2 * DVL_MAX_FIELDS), "alloc pixel bounds");
-            c->HS_cap = p->width + 1;
-        }
-        build_vt = !c->vt_valid || c->vt_dom.size() != c->h_dom.size() ||
-                   std::memcmp(c->vt_dom.data(), c->h_dom.data(), c->h_dom.size() * sizeof(float)) != 0;
+    // bins from range queries over the value tables (which depend on the TF
+    // domains); alpha means from pass A's per-step alpha sums, in the same
+    // read of the cells
+    if (p->width + 1 > c->HS_cap) {
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        CK(dalloc(c->d_H, p->width + 1), "alloc pixel bounds");
+        CK(dalloc(c->d_S, p->width + 1), "alloc pixel bounds");
+        CK(dalloc(c->d_psum, (size_t)(p->width + 1) * 2 * DVL_MAX_FIELDS), "alloc pixel bounds");
+        CK(dalloc(c->d_pmm, (size_t)(p->width + 1) * 2 * DVL_MAX_FIELDS), "alloc pixel bounds");
+        c->HS_cap = p->width + 1;
     }
+    const bool build_vt = !c->vt_valid || c->vt_dom.size() != c->h_dom.size() ||
+                          std::memcmp(c->vt_dom.data(), c->h_dom.data(), c->h_dom.size() * sizeof(float)) != 0;
     UpdateArgs a = make_args(c, *p);
+    a.vt = &c->vt;
+    a.vt_build = build_vt ? 1 : 0;
     if (p->want_alpha) {
         a.asum = c->d_asum;
         a.amean = c->d_amean;
-    } else {
-        a.vt = &c->vt;
-        a.vt_build = build_vt ? 1 : 0;
+        a.astep = c->d_astep;
+        a.achunk = c->d_achunk;
+        a.apart = c->d_apart;
     }
     if (c->timing) {
         std::array<cudaEvent_t, 5> set{};
@@ -864,7 +884,7 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
     c->W_last = p->width;
     c->last_prm = *p;
     c->last_alpha = p->want_alpha != 0;
-    c->last_rq = !p->want_alpha;
+    c->last_rq = true;
     c->have_update = true;
     return DVL_OK;
 }
@@ -1362,6 +1382,11 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
     b.psum = c->d_bpsum;
     b.pmm = c->d_bpmm;
     b.sm_count = sm;
+    if (!c->d_bstamps) {
+        CK(dalloc(c->d_bstamps, 2), "alloc batch stamps");
+        CK(cudaMemsetAsync(c->d_bstamps, 0, 2 * sizeof(unsigned long long), c->stream), "clear");
+    }
+    b.stamps = c->d_bstamps;
     ValueTableArgs v = c->vt;
     v.consts = c->d_bconsts;             // lo / s are the same for every TF of the batch
 
@@ -1451,8 +1476,9 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
                                     (uint64_t)c->d_bsteps, (uint64_t)c->d_pairs, (uint64_t)c->d_bsum,
                                     (uint64_t)c->d_bvmin, (uint64_t)c->d_bvmax, (uint64_t)c->d_bmean,
                                     (uint64_t)c->d_by, (uint64_t)c->d_bcount, (uint64_t)c->d_bH, (uint64_t)c->d_bS,
-                                    (uint64_t)c->d_bpsum, (uint64_t)c->d_bpmm,
-                                    (uint64_t)v.pre_lo, (uint64_t)v.pre_hi, (uint64_t)v.mn, (uint64_t)v.mx};
+                                    (uint64_t)c->d_bpsum, (uint64_t)c->d_bpmm, (uint64_t)c->d_bstamps,
+                                    (uint64_t)v.loc, (uint64_t)v.blk, (uint64_t)v.raw, (uint64_t)v.pre,
+                                    (uint64_t)v.suf, (uint64_t)v.bmm};
     constexpr size_t MAX_GRAPHS = 32;
     auto hit = c->b_graphs.find(sig);
     if (hit == c->b_graphs.end()) {

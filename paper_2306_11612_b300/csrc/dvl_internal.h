@@ -91,18 +91,29 @@ void launch_gather(cudaStream_t s, uint64_t n, const uint32_t* perm, uint32_t M,
 
 // bins.cu: TF-independent value tables (per data set and TF domain) and the
 // per-pixel range queries that replace the placement pass.
+//
+// Per field, over steps of STEP cells grouped in blocks of VT_BLOCK steps:
+// the fixed-point sum of t = floor(t * 2^95) of every step as an exclusive
+// prefix within its block (loc) plus an exclusive prefix over the blocks
+// (blk), so the prefix up to step s is blk[s / VT_BLOCK] + loc[s]; and the
+// (min, max) of t per step (raw), over the block's steps up to and including
+// it (pre) and from it to the block's end (suf), with a sparse table of the
+// blocks' (min, max) over power-of-two runs of blocks (bmm).
+constexpr int VT_BLOCK = 32;
 struct ValueTableArgs {
     uint64_t n;
     const float* val;          // M x pitch, curve order
     size_t pitch;
     const UpdateConsts* consts;   // lo / s of the domains the tables are built for
     uint64_t n_steps;          // ceil(n / STEP)
-    uint64_t* pre_lo;          // M x (n_steps + 1): exclusive prefix of the per-step
-    uint64_t* pre_hi;          //   sums of floor(t * 2^95) (u128 as two u64)
-    float* mn;                 // M x level_stride: min/max sparse table, level l at
-    float* mx;                 //   l * n_steps, entry i = steps [i, i + 2^l)
-    uint64_t level_stride;
-    int n_levels;
+    uint64_t n_blocks;         // ceil(n_steps / VT_BLOCK)
+    ulonglong2* loc;           // M x (n_steps + 1), u128 as (lo, hi)
+    ulonglong2* blk;           // M x (n_blocks + 1), u128 as (lo, hi)
+    float2* raw;               // M x n_steps
+    float2* pre;               // M x n_steps
+    float2* suf;               // M x n_steps
+    float2* bmm;               // M x b_levels x n_blocks: level l, entry i = blocks [i, i + 2^l)
+    int b_levels;              // floor(log2(n_blocks)) + 1 (0 when there are no blocks)
 };
 struct QueryArgs {
     const UpdateConsts* consts;
@@ -120,8 +131,16 @@ struct QueryArgs {
     // width that divides a wider one of the same scan shares its boundaries
     // (ceil(j F / W) = ceil(r j F / (r W))), so it reads every r-th entry.
     uint32_t hstride;
+    // Alpha means (null when not asked for): pass A's per-step and per-chunk
+    // sums of the cells' fixed-point alpha (see UpdateArgs::astep) and, per
+    // boundary, the two partial-step sums (index as psum).
+    const unsigned long long* astep;
+    const unsigned long long* achunk;
+    unsigned long long* apart;
+    uint64_t a_chunks;         // chunks per field row of astep / achunk (pass A's count)
 };
-uint64_t value_table_levels(uint64_t n_steps, uint64_t* stride);
+// Sparse-table levels over n_blocks blocks: floor(log2(n_blocks)) + 1.
+int value_table_levels(uint64_t n_blocks);
 
 // update.cu
 struct UpdateArgs {
@@ -147,6 +166,15 @@ struct UpdateArgs {
     float* y;                  // M x W
     double* asum;              // M x W alpha sums, or null (no alpha means)
     float* amean;              // M x W alpha means (when asum)
+    // Alpha means in the same read of the cells as the widths: pass A adds the
+    // cells' alpha per field in fixed point, a_fx = rint(alpha 2^31), per warp
+    // step (astep: M x n_chunks * STEPS) and per chunk (achunk: M x (n_chunks
+    // + 1), turned into the exclusive prefix over chunks); apart holds the
+    // pixel boundaries' partial-step sums ((W + 1) x 2 x M).  Null: no alpha
+    // sums in pass A (the placement pass computes them, or none are asked for).
+    unsigned long long* astep;
+    unsigned long long* achunk;
+    unsigned long long* apart;
     uint32_t* err;
     int64_t spin_limit;
     int fault_no_publish;
@@ -155,8 +183,6 @@ struct UpdateArgs {
     // range-query bins (null vt: the placement pass k_passB* is used instead)
     const ValueTableArgs* vt;
     int vt_build;              // rebuild the value tables after k_prepare
-    uint64_t* vt_tot_lo;       // scratch of the table scan (M x ceil(n_steps / 1024))
-    uint64_t* vt_tot_hi;
     unsigned long long* H;
     uint8_t* S;
     ulonglong2* psum;          // boundary partial sums (see QueryArgs)
@@ -193,18 +219,22 @@ struct BatchArgs {
     uint8_t* S;
     ulonglong2* psum;          // 2 x M per pixel bound (offset hs_off * 2 * M)
     float2* pmm;
-    uint32_t* tickets;         // tile ticket per TF group (ceil(K / G), zeroed per batch)
+    uint32_t* tickets;         // [0]: the (group, tile) ticket counter of pass A (zeroed per batch)
     int resid;                 // pass A CTAs per SM (persistent grid)
     int sm_count;
+    // Device clock (%globaltimer, ns) of the batch's execution: [0] when the
+    // first kernel started, [1] when the last of its pixel-query blocks ended.
+    unsigned long long* stamps;
 };
+// The stamps of the last batch of a context (device memory, 2 words).
+const unsigned long long* batch_stamps(const dvl_ctx* c);
 cudaError_t launch_prepare_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b);
 cudaError_t launch_passA_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b);
 // Resident pass-A batch CTAs per SM for groups of G tables (0 = does not fit).
 cudaError_t passA_batch_occupancy(const UpdateArgs& a, uint32_t G, int* blocks);
 cudaError_t launch_bins_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b, const ValueTableArgs& v);
 
-cudaError_t launch_value_tables(cudaStream_t s, uint32_t M, const ValueTableArgs& v, uint64_t* tot_lo,
-                                uint64_t* tot_hi);
+cudaError_t launch_value_tables(cudaStream_t s, uint32_t M, const ValueTableArgs& v);
 cudaError_t launch_bins(cudaStream_t s, const UpdateArgs& a, const QueryArgs& qa, const ValueTableArgs& v);
 cudaError_t launch_update(cudaStream_t s, const UpdateArgs& a);
 // Alpha tables from control points (M x K -> M x T), flags values outside [0,1].

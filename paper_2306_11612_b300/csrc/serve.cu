@@ -94,7 +94,19 @@ struct Dataset {
     Pinned<double> r_sum;
     Pinned<uint32_t> r_count;
     std::vector<uint32_t> pair_tf, pair_w;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // the batch's kernels: before and after, on its stream
+    Pinned<unsigned long long> r_stamps;        // device clock at its first kernel's start, last kernel's end
 };
+
+// One finished batch on the device timeline: its data set, real requests,
+// the events around its kernels and the device-clock stamps of their run.
+struct Span {
+    uint32_t ds, k;
+    cudaEvent_t ev0, ev1;
+    unsigned long long ns0, ns1;
+};
+
+constexpr size_t MAX_SPANS = 1u << 20;
 
 }  // namespace
 
@@ -116,6 +128,9 @@ struct dvl_server {
     uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batch_reqs = 0, cells = 0;
     uint32_t max_batch_seen = 0;
     double t_first = 0, t_last = 0;
+    // device timeline of the finished batches (events are recycled through `free_ev`)
+    std::vector<Span> spans;
+    std::vector<cudaEvent_t> free_ev;
 };
 
 namespace {
@@ -133,16 +148,17 @@ int sfail(dvl_server* s, int code, const char* fmt, ...)
 }
 
 // Estimated device bytes of one resident data set: input and sorted fields,
-// levels, order and sort scratch, the value tables (prefix sums and the
-// min/max sparse table) and the single-update scan state.
+// levels, order and sort scratch, the value tables (prefix sums within and
+// over blocks of steps, per-step and in-block min/max, the blocks' sparse
+// table) and the single-update scan state.
 uint64_t resident_bytes(uint64_t n, uint32_t M)
 {
     const uint64_t pad = (n + PAD - 1) / PAD * PAD;
     const uint64_t steps = (n + STEP - 1) / STEP, tiles = (n + TILE - 1) / TILE, chunks = tiles * WARPS;
-    uint64_t stride = 0;
-    value_table_levels(steps, &stride);
-    return pad * (8ull * M + 1) + n * (4 + 8 + 8 + 4) + (uint64_t)M * (steps + 1) * 16 + (uint64_t)M * stride * 8 +
-           tiles * 8 + chunks * 8 + chunks * STEPS * 8;
+    const uint64_t blocks = (steps + VT_BLOCK - 1) / VT_BLOCK;
+    const uint64_t tables = (uint64_t)M * ((steps + 1) * 16 + (blocks + 1) * 16 + steps * 3 * 8 +
+                                           (uint64_t)value_table_levels(blocks) * blocks * 8);
+    return pad * (8ull * M + 1) + n * (4 + 8 + 8 + 4) + tables + tiles * 8 + chunks * 8 + chunks * STEPS * 8;
 }
 
 // Estimated batch-buffer bytes per TF slot (one pair of width W per slot).
@@ -197,6 +213,19 @@ void complete_batch(dvl_server* s, Dataset* d, int rc)
         bin_off += MW;
         cnt_off += r->W;
     }
+    if (d->ev0 && d->ev1) {
+        if (rc == DVL_OK && s->spans.size() < MAX_SPANS) {
+            uint32_t idx = 0;
+            for (size_t i = 0; i < s->ds.size(); ++i)
+                if (s->ds[i].get() == d) idx = (uint32_t)i;
+            s->spans.push_back(Span{idx, (uint32_t)d->batch.size(), d->ev0, d->ev1, d->r_stamps.p[0],
+                                    d->r_stamps.p[1]});
+        } else {
+            s->free_ev.push_back(d->ev0);
+            s->free_ev.push_back(d->ev1);
+        }
+        d->ev0 = d->ev1 = nullptr;
+    }
     d->batch.clear();
     d->busy = false;
     d->finished = false;
@@ -247,12 +276,24 @@ bool launch_batch(dvl_server* s, Dataset* d, std::unique_lock<std::mutex>& lk)
         nc += d->pair_w[i];
     }
     dvl_params prm = s->cfg.params;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    for (int i = 0; i < 2 && !s->free_ev.empty(); ++i) {
+        ev[i] = s->free_ev.back();
+        s->free_ev.pop_back();
+    }
     // No CUDA call while the lock is held: pinned allocation, the library
     // calls and the stream callback may all wait on device work whose host
     // callbacks take the lock.  The batch's requests stay alive (not done)
     // and the data set's buffers belong to this thread until it is finished.
     lk.unlock();
     cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2; ++i)
+        if (!ev[i] && cudaEventCreate(&ev[i]) != cudaSuccess) {
+            cudaGetLastError();
+            ev[i] = nullptr;
+        }
+    cudaStream_t st = static_cast<cudaStream_t>(dvl_stream(d->ctx));
+    const bool timed = ev[0] && ev[1] && cudaEventRecord(ev[0], st) == cudaSuccess;
     if (e == cudaSuccess) e = d->h_alpha.reserve((size_t)K * M * T);
     if (e == cudaSuccess) e = d->r_mean.reserve(nb);
     if (e == cudaSuccess) e = d->r_mn.reserve(nb);
@@ -260,24 +301,38 @@ bool launch_batch(dvl_server* s, Dataset* d, std::unique_lock<std::mutex>& lk)
     if (e == cudaSuccess) e = d->r_y.reserve(nb);
     if (e == cudaSuccess) e = d->r_sum.reserve(nb);
     if (e == cudaSuccess) e = d->r_count.reserve(nc);
+    if (e == cudaSuccess) e = d->r_stamps.reserve(2);
     for (uint32_t i = 0; i < K && e == cudaSuccess; ++i)
         std::memcpy(d->h_alpha.p + (size_t)i * M * T, d->batch[i < k ? i : 0]->alpha.data(), (size_t)M * T * 4);
     int rc = e == cudaSuccess ? DVL_OK : DVL_ERR_NOMEM;
     if (rc == DVL_OK)
         rc = dvl_update_batch(d->ctx, d->h_alpha.p, K, T, DVL_MEM_HOST, nullptr, &prm, d->pair_tf.data(),
                               d->pair_w.data(), K);
+    const bool timed1 = timed && rc == DVL_OK && cudaEventRecord(ev[1], st) == cudaSuccess;
     if (rc == DVL_OK) {
         dvl_bins out{d->r_mean.p, d->r_mn.p, d->r_mx.p, d->r_y.p, d->r_sum.p, d->r_count.p, DVL_MEM_HOST};
         rc = dvl_read_batch_all_async(d->ctx, &out);
     }
+    if (rc == DVL_OK && cudaMemcpyAsync(d->r_stamps.p, batch_stamps(d->ctx), 2 * sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+        cudaGetLastError();
+        rc = DVL_ERR_CUDA;
+    }
     if (rc == DVL_OK) {
         auto* arg = new CallbackArg{s, d};
-        if (cudaLaunchHostFunc(static_cast<cudaStream_t>(dvl_stream(d->ctx)), on_batch_done, arg) != cudaSuccess) {
+        if (cudaLaunchHostFunc(st, on_batch_done, arg) != cudaSuccess) {
             delete arg;
             rc = DVL_ERR_CUDA;
         }
     }
     lk.lock();
+    if (timed1 && rc == DVL_OK) {
+        d->ev0 = ev[0];
+        d->ev1 = ev[1];
+    } else {
+        for (cudaEvent_t x : ev)
+            if (x) s->free_ev.push_back(x);
+    }
     if (rc != DVL_OK) {
         const double t = now_s();
         for (Request* r : d->batch) finish_request(s, r, rc, t);
@@ -422,6 +477,11 @@ void dvl_server_destroy(dvl_server* s)
     if (s->th.joinable()) s->th.join();
     for (auto& kv : s->reqs) delete kv.second;
     for (auto& dp : s->ds) dvl_destroy(dp->ctx);
+    for (const Span& sp : s->spans) {
+        cudaEventDestroy(sp.ev0);
+        cudaEventDestroy(sp.ev1);
+    }
+    for (cudaEvent_t x : s->free_ev) cudaEventDestroy(x);
     delete s;
 }
 
@@ -609,6 +669,47 @@ int dvl_server_reset_stats(dvl_server* s)
     s->submitted = s->completed = s->failed = s->batches = s->batch_reqs = s->cells = 0;
     s->max_batch_seen = 0;
     s->t_first = s->t_last = 0;
+    for (const Span& sp : s->spans) {
+        s->free_ev.push_back(sp.ev0);
+        s->free_ev.push_back(sp.ev1);
+    }
+    s->spans.clear();
+    return DVL_OK;
+}
+
+int dvl_server_timeline(dvl_server* s, dvl_batch_span* out, uint32_t cap, uint32_t* n)
+{
+    if (!s || !n || (cap && !out)) return DVL_ERR_ARG;
+    std::vector<Span> sp;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        sp = s->spans;
+    }
+    *n = (uint32_t)sp.size();
+    if (sp.empty() || cap == 0) return DVL_OK;
+    cudaSetDevice(s->device);
+    // times relative to the first span's start event, then shifted so that
+    // the earliest start is 0
+    std::vector<double> t0(sp.size()), t1(sp.size());
+    double first = 0.0;
+    unsigned long long ns_first = ~0ull;
+    for (const Span& x : sp) ns_first = std::min(ns_first, x.ns0);
+    for (size_t i = 0; i < sp.size(); ++i) {
+        float a = 0.f, b = 0.f;
+        if (cudaEventElapsedTime(&a, sp[0].ev0, sp[i].ev0) != cudaSuccess ||
+            cudaEventElapsedTime(&b, sp[0].ev0, sp[i].ev1) != cudaSuccess) {
+            cudaGetLastError();
+            return sfail(s, DVL_ERR_CUDA, "batch events not readable");
+        }
+        t0[i] = a;
+        t1[i] = b;
+        first = std::min(first, (double)a);
+    }
+    const uint32_t k = std::min<uint32_t>(cap, (uint32_t)sp.size());
+    for (uint32_t i = 0; i < k; ++i)
+        out[i] = dvl_batch_span{sp[i].ds, sp[i].k, t0[i] - first, t1[i] - first,
+                                (double)(sp[i].ns0 - ns_first) * 1e-6,
+                                sp[i].ns1 >= sp[i].ns0 ? (double)(sp[i].ns1 - ns_first) * 1e-6 : -1.0};
     return DVL_OK;
 }
 

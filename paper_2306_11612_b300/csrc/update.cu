@@ -3,18 +3,18 @@
 //
 //   k_prepare   TF domains, Eq. 5/6 max-variation approximation, fixed-point
 //               exponent; clears bins and scan state (one launch).
-//   k_passA     per cell: TF alpha per field, variation V (Eq. 1), importance
-//               f (Eq. 3), fixed-point width q; per-warp-chunk sums and a
-//               single-pass decoupled look-back scan over tiles (Eq. 4) that
-//               leaves the exclusive prefix of every chunk and the total F.
-//   k_passB_steps  places every cell into the pixels its [E, E+q) span
-//               touches (Sec. 3.2): pass A's per-step width totals say which
-//               warp steps stay inside one pixel; those only read the field
-//               values and reduce them in registers, the few that cross a pixel
-//               boundary recompute their widths and are placed cell by cell
-//               (global atomics only when the pixel changes or the chunk ends).
-//   k_passB     the same without per-step totals (recomputes every width;
-//               used by the allocation-free entry point).
+//   k_passA_ring  per cell: TF alpha per field, variation V (Eq. 1),
+//               importance f (Eq. 3), fixed-point width q; width totals per
+//               warp step and per chunk (and, for alpha means, the cells'
+//               fixed-point alpha sums per step and chunk); k_chunk_scan then
+//               gives the exclusive prefix of every chunk and the total F
+//               (Eq. 4).  k_passA: the same with direct loads and a decoupled
+//               look-back per tile (rows that are not 16-byte aligned).
+//   The bins are range queries over TF-independent value tables (bins.cu).
+//   k_passB     places every cell into the pixels its [E, E+q) span touches
+//               (Sec. 3.2), recomputing every width, with global atomics only
+//               when the pixel changes or the chunk ends (used by the
+//               allocation-free entry point, which keeps no value tables).
 //   k_finalize  per pixel: mean = sum / count, alpha of the mean (Sec. 3.3).
 //
 // Widths are integers q = rint(f * 2^Q) < 2^32 with Q chosen so that the total
@@ -85,37 +85,53 @@ __global__ void k_consts(UpdateArgs a) { finish_consts(a.consts, a, a.meta->max_
 // Pass A: widths, chunk sums, decoupled look-back scan over tiles
 // ---------------------------------------------------------------------------
 
-// Sum of the fixed-point widths of one lane's 4 cells at idx.
-template <int M, int PM, bool FULLSTEP, bool P2>
+// Sum of the fixed-point widths of one lane's 4 cells at idx.  AL: also adds
+// the cells' fixed-point alphas per field to ax (the u32 tables lie `aoff`
+// bytes after the float tables).
+template <int M, int PM, bool FULLSTEP, bool P2, bool AL = false>
 __device__ __forceinline__ unsigned long long widths4_of(const Cell<M, PM>& cc, const UpdateArgs& a,
                                                          const float* s_tf, const uint32_t* cm, uint64_t idx,
-                                                         const float (&v)[4][M], uint32_t L4)
+                                                         const float (&v)[4][M], uint32_t L4, uint32_t aoff = 0,
+                                                         unsigned long long* ax = nullptr)
 {
     unsigned long long acc = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         uint32_t q;
+        unsigned long long axj[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) axj[m] = 0;
         if (P2) {
-            q = cc.width_p2(v[j], (L4 >> (8 * j)) & 0xFF, cm);
+            q = AL ? cc.width_p2_alpha(v[j], (L4 >> (8 * j)) & 0xFF, cm, aoff, axj)
+                   : cc.width_p2(v[j], (L4 >> (8 * j)) & 0xFF, cm);
         } else {
             float t[M];
 #pragma unroll
             for (int m = 0; m < M; ++m) t[m] = norm_t(v[j][m], cc.lo[m], cc.s[m]);
-            q = cc.width(t, (L4 >> (8 * j)) & 0xFF, s_tf);
+            q = AL ? cc.width_alpha(t, (L4 >> (8 * j)) & 0xFF, s_tf,
+                                    reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(s_tf) + aoff), axj)
+                   : cc.width(t, (L4 >> (8 * j)) & 0xFF, s_tf);
         }
-        if (FULLSTEP || idx + j < a.n) acc += q;
+        if (FULLSTEP || idx + j < a.n) {
+            acc += q;
+            if (AL) {
+#pragma unroll
+                for (int m = 0; m < M; ++m) ax[m] += axj[m];
+            }
+        }
     }
     return acc;
 }
 
-template <int M, int PM, bool FULLSTEP, bool P2>
+template <int M, int PM, bool FULLSTEP, bool P2, bool AL = false>
 __device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, const UpdateArgs& a,
-                                                      const float* s_tf, const uint32_t* cm, uint64_t idx)
+                                                      const float* s_tf, const uint32_t* cm, uint64_t idx,
+                                                      uint32_t aoff = 0, unsigned long long* ax = nullptr)
 {
     float v[4][M];
     uint32_t L4;
     load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
-    return widths4_of<M, PM, FULLSTEP, P2>(cc, a, s_tf, cm, idx, v, L4);
+    return widths4_of<M, PM, FULLSTEP, P2, AL>(cc, a, s_tf, cm, idx, v, L4, aoff, ax);
 }
 
 // One warp of a pass-A CTA, with the tile's chunk totals in lanes 0..7: chunk
@@ -286,13 +302,17 @@ __device__ __forceinline__ void ring_issue(int lane, uint32_t slot, uint32_t bar
     }
 }
 
-// chunk totals go to chunk_prefix (turned into prefixes by k_chunk_scan)
-template <int M, int PM, bool P2, int D, int MINB>
+// chunk totals go to chunk_prefix (turned into prefixes by k_chunk_scan).
+// AL: the cells' fixed-point alphas are summed per field as well (per step
+// into astep, per chunk into achunk); tf_bytes then covers the float tables
+// and their u32 twins (aoff = half of it).
+template <int M, int PM, bool P2, int D, int MINB, bool AL = false>
 __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, uint64_t n_chunks, uint32_t tf_bytes)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr uint32_t SLOT = M * STEP * 4 + STEP;
     float* s_tf = reinterpret_cast<float*>(smem);
+    const uint32_t aoff = tf_bytes / 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned char* ring = smem + tf_bytes + (size_t)warp * D * SLOT;
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
@@ -325,6 +345,7 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
         for (int k = 0; k < D; ++k) ring_issue<M>(lane, ring_s + k * SLOT, bar_s + 8u * k, a, chunk * CHUNK + k * STEP);
     }
     load_table<M>(s_tf, a.tf, a.T);
+    if (AL) load_table_fx<M>(reinterpret_cast<uint32_t*>(smem + aoff), a.tf, a.T);
     __syncthreads();
     Cell<M, PM> cc;
     cc.load(a.consts, a.T);
@@ -332,6 +353,7 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
     const uint32_t sb = (uint32_t)__cvta_generic_to_shared(s_tf);
 #pragma unroll
     for (int m = 0; m < M; ++m) cm[m] = sb + 4u * (uint32_t)(m * (a.T + 1)) - 4u * BITS_2P23;
+    const uint64_t n_steps_all = n_chunks * STEPS;
 
     int k = 0;                         // next slot to consume
     uint32_t phase = 0;                // its parity
@@ -343,6 +365,16 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
         const uint64_t nxt = claim();
         const bool nxt_full = full(nxt);
         unsigned long long acc = 0, mine = 0;
+        unsigned long long amine[M];                    // this lane's step: alpha sums per field
+#pragma unroll
+        for (int m = 0; m < M; ++m) amine[m] = 0;
+        auto alpha_step = [&](unsigned long long (&ax)[M], int st) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const unsigned long long t = warp_total_small(ax[m]);     // <= 128 x 2^31
+                if (AL && lane == st) amine[m] = t;
+            }
+        };
         if (cur_full) {
 #pragma unroll 1
             for (int st = 0; st < STEPS; ++st) {
@@ -363,11 +395,15 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
                     else if (nxt_full)
                         ring_issue<M>(lane, ring_s + k * SLOT, bar_s + 8u * k, a, nxt * CHUNK + (s2 - STEPS) * STEP);
                 }
+                unsigned long long ax[M];
+#pragma unroll
+                for (int m = 0; m < M; ++m) ax[m] = 0;
                 const unsigned long long l =
-                    widths4_of<M, PM, true, P2>(cc, a, s_tf, cm, base + st * STEP + lane * 4, v, L4);
+                    widths4_of<M, PM, true, P2, AL>(cc, a, s_tf, cm, base + st * STEP + lane * 4, v, L4, aoff, ax);
                 const unsigned long long tot = warp_total_small(l);
                 if (lane == st) mine = tot;
                 acc += tot;
+                if (AL) alpha_step(ax, st);
                 if (++k == D) { k = 0; phase ^= 1u; }
             }
         } else {
@@ -382,14 +418,28 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
             }
             for (int st = 0; st < STEPS; ++st) {
                 const uint64_t idx = base + st * STEP + lane * 4;
-                const unsigned long long l = idx < a.n ? widths4<M, PM, false, P2>(cc, a, s_tf, cm, idx) : 0ull;
+                unsigned long long ax[M];
+#pragma unroll
+                for (int m = 0; m < M; ++m) ax[m] = 0;
+                const unsigned long long l =
+                    idx < a.n ? widths4<M, PM, false, P2, AL>(cc, a, s_tf, cm, idx, aoff, ax) : 0ull;
                 const unsigned long long tot = warp_total_small(l);
                 if (lane == st) mine = tot;
                 acc += tot;
+                if (AL) alpha_step(ax, st);
             }
         }
         if (a.step_sums && lane < STEPS) a.step_sums[chunk * STEPS + lane] = mine;
         if (lane == 0) a.chunk_prefix[chunk] = acc;
+        if (AL) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const unsigned long long am = lane < STEPS ? amine[m] : 0ull;
+                if (lane < STEPS) a.astep[(uint64_t)m * n_steps_all + chunk * STEPS + lane] = am;
+                const unsigned long long ct = warp_sum_u64(am);            // chunk total
+                if (lane == 0) a.achunk[(uint64_t)m * (n_chunks + 1) + chunk] = ct;
+            }
+        }
         chunk = nxt;
         cur_full = nxt_full;
     }
@@ -401,61 +451,92 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
 // its chunks, publishes its total and looks back over the earlier blocks'
 // (decoupled look-back; all blocks are resident at once, so the chain is
 // short).  The last block also writes F (Eq. 4's total) and the all-zero
-// fallback, as tile_scan does.
+// fallback, as tile_scan does.  With alpha sums (achunk) the block scans each
+// field's chunk alpha sums the same way, warp q running quantity q's
+// look-back (quantity 0: widths, q >= 1: field q - 1's alphas; status words of
+// quantity q at status + q * gridDim.x), and the last block writes each
+// field's alpha total at achunk[m][n_chunks].
 constexpr int SCAN_THREADS = 256, SCAN_PER_THREAD = 8, SCAN_SPAN = SCAN_THREADS * SCAN_PER_THREAD;
+constexpr int SCAN_Q = 1 + DVL_MAX_FIELDS;                 // quantities at most
 
 __global__ __launch_bounds__(SCAN_THREADS) void k_chunk_scan(UpdateArgs a, uint64_t n_chunks,
                                                              unsigned long long* status)
 {
-    __shared__ unsigned long long s_warp[SCAN_THREADS / 32];
-    __shared__ unsigned long long s_excl;
+    __shared__ unsigned long long s_warp[SCAN_Q][SCAN_THREADS / 32];
+    __shared__ unsigned long long s_excl[SCAN_Q];
     __shared__ uint32_t s_b;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nq = a.achunk ? 1 + (int)a.M : 1;
     if (tid == 0) s_b = atomicAdd(&a.counters[1], 1u);
     __syncthreads();
     const uint32_t b = s_b;
-    // block-local scan: thread tid holds chunks b0 + tid*8 .. +8
+    auto row_of = [&](int q) {
+        return q == 0 ? a.chunk_prefix : a.achunk + (uint64_t)(q - 1) * (n_chunks + 1);
+    };
+    // block-local scans: thread tid holds chunks b0 + tid*8 .. +8 of each quantity
     const uint64_t c0 = (uint64_t)b * SCAN_SPAN + (uint64_t)tid * SCAN_PER_THREAD;
-    unsigned long long v[SCAN_PER_THREAD], t = 0;
+    unsigned long long tq[SCAN_Q], iq[SCAN_Q];
 #pragma unroll
-    for (int j = 0; j < SCAN_PER_THREAD; ++j) {
-        v[j] = c0 + j < n_chunks ? a.chunk_prefix[c0 + j] : 0ull;
-        t += v[j];
+    for (int q = 0; q < SCAN_Q; ++q) {
+        tq[q] = 0;
+        iq[q] = 0;
+        if (q < nq) {
+            const unsigned long long* row = row_of(q);
+#pragma unroll
+            for (int j = 0; j < SCAN_PER_THREAD; ++j) tq[q] += c0 + j < n_chunks ? row[c0 + j] : 0ull;
+            iq[q] = warp_incl_scan_u64(tq[q], lane);
+            if (lane == 31) s_warp[q][warp] = iq[q];
+        }
     }
-    const unsigned long long incl = warp_incl_scan_u64(t, lane);
-    if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
-    unsigned long long wpre = 0, agg = 0;
+    for (int q = warp; q < nq; q += SCAN_THREADS / 32) {
+        unsigned long long agg = 0;
 #pragma unroll
-    for (int w = 0; w < SCAN_THREADS / 32; ++w) {
-        if (w < warp) wpre += s_warp[w];
-        agg += s_warp[w];
-    }
-    if (warp == 0) {
-        if (lane == 0) st_relaxed(status + b, (b == 0 ? FLAG_P : FLAG_A) | agg);
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) agg += s_warp[q][w];
+        unsigned long long* st = status + (uint64_t)q * gridDim.x;
+        if (lane == 0) st_relaxed(st + b, (b == 0 ? FLAG_P : FLAG_A) | agg);
         unsigned long long excl = 0;
         if (b > 0) {
-            excl = look_back(a, status, b, lane);
-            if (lane == 0) st_relaxed(status + b, FLAG_P | (excl + agg));
+            excl = look_back(a, st, b, lane);
+            if (lane == 0) st_relaxed(st + b, FLAG_P | (excl + agg));
         }
-        if (lane == 0) s_excl = excl;
+        if (lane == 0) s_excl[q] = excl;
     }
     __syncthreads();
-    unsigned long long run = s_excl + wpre + incl - t;
 #pragma unroll
-    for (int j = 0; j < SCAN_PER_THREAD; ++j) {
-        if (c0 + j < n_chunks) a.chunk_prefix[c0 + j] = run;
-        run += v[j];
-    }
-    if (b == gridDim.x - 1 && tid == 0) {
-        UpdateConsts* C = a.consts;
-        unsigned long long F = s_excl + agg;
-        int linear = 0;
-        if (F == 0 && a.n > 0) { F = a.n; linear = 1; }   // all widths 0: equal widths
-        C->F = F;
-        C->linear = linear;
-        C->F_div_W = F / a.W;
-        C->F_mod_W = F % a.W;
+    for (int q = 0; q < SCAN_Q; ++q) {
+        if (q >= nq) break;
+        unsigned long long wpre = 0, agg = 0;
+#pragma unroll
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+            if (w < warp) wpre += s_warp[q][w];
+            agg += s_warp[q][w];
+        }
+        unsigned long long* row = row_of(q);
+        unsigned long long v[SCAN_PER_THREAD];
+#pragma unroll
+        for (int j = 0; j < SCAN_PER_THREAD; ++j) v[j] = c0 + j < n_chunks ? row[c0 + j] : 0ull;
+        __syncwarp();
+        unsigned long long run = s_excl[q] + wpre + iq[q] - tq[q];
+#pragma unroll
+        for (int j = 0; j < SCAN_PER_THREAD; ++j) {
+            if (c0 + j < n_chunks) row[c0 + j] = run;
+            run += v[j];
+        }
+        if (b == gridDim.x - 1 && tid == 0) {
+            if (q == 0) {
+                UpdateConsts* C = a.consts;
+                unsigned long long F = s_excl[0] + agg;
+                int linear = 0;
+                if (F == 0 && a.n > 0) { F = a.n; linear = 1; }   // all widths 0: equal widths
+                C->F = F;
+                C->linear = linear;
+                C->F_div_W = F / a.W;
+                C->F_mod_W = F % a.W;
+            } else {
+                row[n_chunks] = s_excl[q] + agg;                  // the field's alpha total
+            }
+        }
     }
 }
 
@@ -463,19 +544,14 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_chunk_scan(UpdateArgs a, uint6
 // Pass B: placement and per-pixel reduction
 // ---------------------------------------------------------------------------
 
-template <int M, bool A = false>
+template <int M>
 struct Acc {
     float s[M], mn[M], mx[M];
-    float as[A ? M : 1];           // alpha sums (differentiable output)
     uint32_t cnt;
     __device__ __forceinline__ void reset()
     {
 #pragma unroll
         for (int m = 0; m < M; ++m) { s[m] = 0.0f; mn[m] = 2.0f; mx[m] = -1.0f; }
-        if (A) {
-#pragma unroll
-            for (int m = 0; m < M; ++m) as[m] = 0.0f;
-        }
         cnt = 0;
     }
     __device__ __forceinline__ void add(const float* t)
@@ -483,13 +559,6 @@ struct Acc {
 #pragma unroll
         for (int m = 0; m < M; ++m) { s[m] += t[m]; mn[m] = fminf(mn[m], t[m]); mx[m] = fmaxf(mx[m], t[m]); }
         ++cnt;
-    }
-    __device__ __forceinline__ void add_alpha(const float* al)
-    {
-        if (A) {
-#pragma unroll
-            for (int m = 0; m < M; ++m) as[m] += al[m];
-        }
     }
     __device__ __forceinline__ void flush_to(const UpdateArgs& a, uint32_t p) const
     {
@@ -500,7 +569,6 @@ struct Acc {
             atomicAdd(&a.sum[k], (double)s[m]);
             atomicMin(&a.vmin[k], __float_as_uint(mn[m]));   // t >= 0: bit order = value order
             atomicMax(&a.vmax[k], __float_as_uint(mx[m]));
-            if (A) atomicAdd(&a.asum[k], (double)as[m]);
         }
         atomicAdd(&a.count[p], cnt);
     }
@@ -514,7 +582,6 @@ struct Acc {
                 s[m] += __shfl_xor_sync(FULL, s[m], o);
                 mn[m] = fminf(mn[m], __shfl_xor_sync(FULL, mn[m], o));
                 mx[m] = fmaxf(mx[m], __shfl_xor_sync(FULL, mx[m], o));
-                if (A) as[m] += __shfl_xor_sync(FULL, as[m], o);
             }
             cnt += __shfl_xor_sync(FULL, cnt, o);
         }
@@ -522,14 +589,6 @@ struct Acc {
         reset();
     }
 };
-
-// alpha of each field for normalised values t (T+1-entry shared tables)
-template <int M>
-__device__ __forceinline__ void alphas_of(const float* t, const float* s_tf, float Tf, int T1, float* al)
-{
-#pragma unroll
-    for (int m = 0; m < M; ++m) al[m] = s_tf[m * T1 + floor_small(__fmul_rn(t[m], Tf))];
-}
 
 // Exact placement of one lane's cells of a step that crosses a pixel
 // boundary; consecutive cells on the same pixel are merged per lane.
@@ -625,170 +684,6 @@ __global__ __launch_bounds__(WARPS * 32) void k_passB(UpdateArgs a)
     if (full < STEPS && base + (uint64_t)full * STEP < a.n)
         place_step<M, PM, false>(a, cc, s_tf, pm, base + full * STEP + lane * 4, lane, pos, cur, hi_pos, acc);
     acc.warp_flush(a, cur, lane);
-}
-
-// Pass B when pass A left the width total of every warp step: a step whose
-// span [s_start, s_end) lies inside the current pixel needs only the cells'
-// normalised values (no levels, no TF lookups, no widths); a step that
-// crosses a pixel boundary is recomputed out of line and placed cell by cell.
-template <int M, int PM, bool ALPHA>
-__device__ __noinline__ void place_crossing_step(const UpdateArgs& a, const float* s_tf, const PixelMap& pm,
-                                                 uint64_t idx, unsigned long long s_start, int lane)
-{
-    // kept lean (this is the rare path): cells are re-read one at a time from
-    // the cache instead of being held in registers
-    Cell<M, PM> cc;
-    cc.load(a.consts, a.T);
-    const int nvalid = idx < a.n ? (a.n - idx < 4 ? (int)(a.n - idx) : 4) : 0;
-    auto cell = [&](int j, float (&t)[M]) {
-#pragma unroll
-        for (int m = 0; m < M; ++m) t[m] = norm_t(__ldg(a.val + m * a.pitch + idx + j), cc.lo[m], cc.s[m]);
-    };
-    auto width = [&](int j) -> uint32_t {
-        float t[M];
-        cell(j, t);
-        return cc.linear ? 1u : cc.width(t, __ldg(a.lev + idx + j), s_tf);
-    };
-    unsigned long long lsum = 0;
-    for (int j = 0; j < nvalid; ++j) lsum += width(j);
-    unsigned long long E = s_start + warp_incl_scan_u64(lsum, lane) - lsum;
-    Acc<M, ALPHA> run;
-    run.reset();
-    uint32_t run_p = 0xFFFFFFFFu;
-    for (int j = 0; j < nvalid; ++j) {
-        float t[M];
-        cell(j, t);
-        const unsigned long long I = E + (cc.linear ? 1u : cc.width(t, __ldg(a.lev + idx + j), s_tf));
-        const uint32_t b1 = pm.first_pixel(E);
-        const uint32_t b2 = I > E ? pm.last_pixel(I) : b1;
-        float al[ALPHA ? M : 1];
-        if (ALPHA) alphas_of<M>(t, s_tf, cc.Tf, cc.T1, al);
-        for (uint32_t p = b1; p <= b2; ++p) {
-            if (p != run_p) {
-                run.flush_to(a, run_p);
-                run.reset();
-                run_p = p;
-            }
-            run.add(t);
-            run.add_alpha(al);
-        }
-        E = I;
-    }
-    run.flush_to(a, run_p);
-}
-
-// Placement of one warp chunk (two phases, see k_passB_steps).  `a` carries
-// the constants, scan results and bins of one TF and one viewport; s_tf holds
-// that TF's tables.
-template <int M, int PM, bool ALPHA>
-__device__ __forceinline__ void place_chunk(const UpdateArgs& a, const float* s_tf, const PixelMap& pm,
-                                            uint64_t chunk, int lane)
-{
-    const uint64_t base = chunk * CHUNK;
-    const UpdateConsts* C = a.consts;
-    const bool linear = C->linear != 0;
-    const uint64_t rem = a.n - base;
-    const int full = rem >= (uint64_t)CHUNK ? STEPS : (int)(rem / STEP);      // steps with 128 cells
-    const int nsteps = rem >= (uint64_t)CHUNK ? STEPS : (int)((rem + STEP - 1) / STEP);
-
-    // Lane st describes step st: its span [s_start, s_end), the pixel of its
-    // start and whether the span leaves that pixel.  Full steps that stay in
-    // one pixel are reduced below without widths; the rest ("crossing" steps
-    // and the ragged last step) are placed exactly afterwards.
-    const unsigned long long pos0 = linear ? base : a.chunk_prefix[chunk];
-    unsigned long long ssum = 0;
-    if (lane < nsteps) {
-        const uint64_t left = a.n - (base + (uint64_t)lane * STEP);
-        ssum = linear ? (left < STEP ? left : STEP) : a.step_sums[chunk * STEPS + lane];
-    }
-    const unsigned long long s_end = pos0 + warp_incl_scan_u64(ssum, lane);
-    const unsigned long long s_start = s_end - ssum;
-    uint32_t pix = 0;
-    bool crossing = true;
-    if (lane < nsteps) {
-        pix = pm.first_pixel(s_start);
-        crossing = lane >= full || s_end >= pm.C(pix + 1);
-    }
-    const unsigned exact_mask = __ballot_sync(FULL, crossing) & ((1u << nsteps) - 1u);
-
-    float lo[M], sc[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) { lo[m] = C->lo[m]; sc[m] = C->s[m]; }
-    Acc<M, ALPHA> acc;
-    acc.reset();
-    uint32_t cur = __shfl_sync(FULL, pix, 0);
-    const float Tf = (float)a.T;
-    const int T1 = (int)a.T + 1;
-
-    // phase 1: single-pixel steps, register double buffering, no calls
-    float4 bufA[M], bufB[M];
-    auto load_step = [&](float4 (&dst)[M], int st) {
-#pragma unroll
-        for (int m = 0; m < M; ++m)
-            dst[m] = __ldg(reinterpret_cast<const float4*>(a.val + m * a.pitch + base + st * STEP + lane * 4));
-    };
-    // next single-pixel step after st (or STEPS)
-    auto next_fast = [&](int st) {
-        const unsigned above = st < 0 ? ~0u : ~((2u << st) - 1u);     // bits > st
-        const unsigned rest = ~exact_mask & ((1u << full) - 1u) & above;
-        return rest ? __ffs(rest) - 1 : STEPS;
-    };
-    auto reduce_step = [&](int st, const float4 (&x)[M]) {
-        const uint32_t p = __shfl_sync(FULL, pix, st);
-        if (p != cur) {                 // warp-uniform
-            acc.warp_flush(a, cur, lane);
-            cur = p;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float t[M];
-#pragma unroll
-            for (int m = 0; m < M; ++m)
-                t[m] = norm_t(j == 0 ? x[m].x : j == 1 ? x[m].y : j == 2 ? x[m].z : x[m].w, lo[m], sc[m]);
-            acc.add(t);
-            if (ALPHA) {
-                float al[M];
-                alphas_of<M>(t, s_tf, Tf, T1, al);
-                acc.add_alpha(al);
-            }
-        }
-    };
-    int st = next_fast(-1);
-    if (st < STEPS) load_step(bufA, st);
-#pragma unroll 1
-    while (st < STEPS) {
-        const int s2 = next_fast(st);
-        if (s2 < STEPS) load_step(bufB, s2);
-        reduce_step(st, bufA);
-        if (s2 >= STEPS) break;
-        st = next_fast(s2);
-        if (st < STEPS) load_step(bufA, st);
-        reduce_step(s2, bufB);
-    }
-    acc.warp_flush(a, cur, lane);
-
-    // phase 2: steps placed cell by cell (rare on large data sets)
-    unsigned m2 = exact_mask;
-    while (m2) {
-        const int k = __ffs(m2) - 1;
-        m2 &= m2 - 1;
-        place_crossing_step<M, PM, ALPHA>(a, s_tf, pm, base + k * STEP + lane * 4, __shfl_sync(FULL, s_start, k),
-                                          lane);
-    }
-}
-
-template <int M, int PM, bool ALPHA>
-__global__ __launch_bounds__(WARPS * 32, 3) void k_passB_steps(UpdateArgs a)
-{
-    extern __shared__ float s_tf[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    load_table<M>(s_tf, a.tf, a.T);
-    __syncthreads();
-    const uint64_t chunk = (uint64_t)blockIdx.x * WARPS + warp;
-    if (chunk * CHUNK >= a.n) return;
-    const UpdateConsts* C = a.consts;
-    const PixelMap pm{C->F_div_W, C->F_mod_W, C->F, a.W};
-    place_chunk<M, PM, ALPHA>(a, s_tf, pm, chunk, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -1069,14 +964,20 @@ __global__ __launch_bounds__(WARPS * 32) void k_backward(UpdateArgs a, const flo
     }
 }
 
-// Adjoint with per-warp entry histograms.  Inside a warp step that stays in
-// one pixel p every cell carries the same weight g[m][p] / count[p], so the
-// step only counts how often each TF entry occurs (u32 shared-memory atomics
-// in the warp's own histogram); when the warp's pixel changes, or its chunk
-// ends, the counts are scaled by the pixel's weights and added to the CTA's
-// float64 table.  Steps that cross a pixel boundary place their cells exactly
-// (back_crossing_step_hist).  Each CTA writes its table to gpart[blockIdx] without
-// atomics; k_gtab_reduce sums the CTAs in a fixed order.
+// Adjoint with per-warp entry histograms, in a persistent grid whose warps
+// claim chunks from a counter.  Inside a warp step that stays in one pixel p
+// every cell carries the same weight g[m][p] / count[p], so the step only
+// counts how often each TF entry occurs, in the warp's own u32 histogram in
+// shared memory: a lane adds each run of equal entries among its 4
+// consecutive cells with one atomic (cells close in curve order mostly share
+// an entry, so fewer lanes hit the same counter at once; the run ends are
+// predicates, not branches).  When the warp's pixel changes, or its chunk
+// ends, the counts are scaled by the pixel's weights into the CTA's float64
+// table.  Steps that cross a pixel boundary place their cells exactly
+// (back_crossing_step_hist).  The next single-pixel step's cells are loaded
+// while the current one is counted.  Each CTA writes its table to
+// gpart[blockIdx] without atomics; k_gtab_reduce sums the CTAs in a fixed
+// order.  counters[2] is the chunk counter (zeroed by the launcher).
 template <int M, int PM>
 __global__ __launch_bounds__(WARPS * 32, 3) void k_backward_hist(UpdateArgs a, const float* g, double* gpart)
 {
@@ -1090,12 +991,39 @@ __global__ __launch_bounds__(WARPS * 32, 3) void k_backward_hist(UpdateArgs a, c
     for (int i = tid; i < MT1; i += blockDim.x) sG[i] = 0.0;
     for (int i = tid; i < WARPS * MT1; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
-    const uint64_t chunk = (uint64_t)blockIdx.x * WARPS + warp;
-    const uint64_t base = chunk * CHUNK;
-    if (base < a.n) {
-        const UpdateConsts* C = a.consts;
-        const bool linear = C->linear != 0;
-        const PixelMap pm{C->F_div_W, C->F_mod_W, C->F, a.W};
+    const UpdateConsts* C = a.consts;
+    const bool linear = C->linear != 0;
+    const PixelMap pm{C->F_div_W, C->F_mod_W, C->F, a.W};
+    const float Tf = (float)a.T;
+    const uint64_t n_chunks = (a.n + CHUNK - 1) / CHUNK;
+    uint32_t cur = 0xFFFFFFFFu;
+    double wc[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) wc[m] = 0.0;
+    auto flush = [&]() {
+        if (cur == 0xFFFFFFFFu) return;                            // warp-uniform
+        __syncwarp();
+        for (int i = lane; i < MT1; i += 32) {
+            const uint32_t c = h[i];
+            if (c) {
+                h[i] = 0u;
+                const int m = i / T1;
+                double w = 0.0;
+#pragma unroll
+                for (int mm = 0; mm < M; ++mm)
+                    if (mm == m) w = wc[mm];
+                atomicAdd(&sG[i], w * (double)c);
+            }
+        }
+        __syncwarp();
+    };
+    auto claim = [&]() {
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(&a.counters[2], 1u);
+        return (uint64_t)__shfl_sync(FULL, c, 0);
+    };
+    for (uint64_t chunk = claim(); chunk < n_chunks; chunk = claim()) {
+        const uint64_t base = chunk * CHUNK;
         const uint64_t rem = a.n - base;
         const int full = rem >= (uint64_t)CHUNK ? STEPS : (int)(rem / STEP);
         const int nsteps = rem >= (uint64_t)CHUNK ? STEPS : (int)((rem + STEP - 1) / STEP);
@@ -1114,56 +1042,50 @@ __global__ __launch_bounds__(WARPS * 32, 3) void k_backward_hist(UpdateArgs a, c
             crossing = lane >= full || s_end >= pm.C(pix + 1);
         }
         const unsigned exact_mask = __ballot_sync(FULL, crossing) & ((1u << nsteps) - 1u);
-        float lo[M], sc[M];
+        unsigned todo = ~exact_mask & ((1u << full) - 1u);             // single-pixel full steps
+        float4 xn[M];
+        auto load_step = [&](int st) {
 #pragma unroll
-        for (int m = 0; m < M; ++m) { lo[m] = C->lo[m]; sc[m] = C->s[m]; }
-        const float Tf = (float)a.T;
-        uint32_t cur = 0xFFFFFFFFu;
-        double wc[M];
-#pragma unroll
-        for (int m = 0; m < M; ++m) wc[m] = 0.0;
-        auto flush = [&]() {
-            if (cur == 0xFFFFFFFFu) return;                        // warp-uniform
-            __syncwarp();
-            for (int i = lane; i < MT1; i += 32) {
-                const uint32_t c = h[i];
-                if (c) {
-                    h[i] = 0u;
-                    const int m = i / T1;
-                    double w = 0.0;
-#pragma unroll
-                    for (int mm = 0; mm < M; ++mm)
-                        if (mm == m) w = wc[mm];
-                    atomicAdd(&sG[i], w * (double)c);
-                }
-            }
-            __syncwarp();
+            for (int m = 0; m < M; ++m)
+                xn[m] = __ldg(reinterpret_cast<const float4*>(a.val + m * a.pitch + base + st * STEP + lane * 4));
         };
-        for (int st = 0; st < full; ++st) {
-            if (exact_mask & (1u << st)) continue;                      // warp-uniform
+        if (todo) load_step(__ffs(todo) - 1);
+        while (todo) {
+            const int st = __ffs(todo) - 1;
+            todo &= todo - 1;
+            float4 x[M];
+#pragma unroll
+            for (int m = 0; m < M; ++m) x[m] = xn[m];
+            if (todo) load_step(__ffs(todo) - 1);
             const uint32_t p = __shfl_sync(FULL, pix, st);
-            if (p != cur) {
+            if (p != cur) {                                            // warp-uniform
                 flush();
                 cur = p;
                 const uint32_t c = a.count[p];
 #pragma unroll
                 for (int m = 0; m < M; ++m) wc[m] = c ? (double)g[(uint64_t)m * a.W + p] / (double)c : 0.0;
             }
-            float4 x[M];
 #pragma unroll
-            for (int m = 0; m < M; ++m)
-                x[m] = __ldg(reinterpret_cast<const float4*>(a.val + m * a.pitch + base + st * STEP + lane * 4));
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-#pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    const float v = j == 0 ? x[m].x : j == 1 ? x[m].y : j == 2 ? x[m].z : x[m].w;
-                    const uint32_t e = floor_small(__fmul_rn(norm_t(v, lo[m], sc[m]), Tf));
-                    atomicAdd(&h[m * T1 + e], 1u);
-                }
+            for (int m = 0; m < M; ++m) {
+                const float lo = C->lo[m], sc = C->s[m];
+                uint32_t e[4];
+                e[0] = floor_small(__fmul_rn(norm_t(x[m].x, lo, sc), Tf));
+                e[1] = floor_small(__fmul_rn(norm_t(x[m].y, lo, sc), Tf));
+                e[2] = floor_small(__fmul_rn(norm_t(x[m].z, lo, sc), Tf));
+                e[3] = floor_small(__fmul_rn(norm_t(x[m].w, lo, sc), Tf));
+                // run lengths from each cell to the end of its run of equal entries
+                const uint32_t r3 = 1u;
+                const uint32_t r2 = e[2] == e[3] ? r3 + 1u : 1u;
+                const uint32_t r1 = e[1] == e[2] ? r2 + 1u : 1u;
+                const uint32_t r0 = e[0] == e[1] ? r1 + 1u : 1u;
+                uint32_t* hm = h + m * T1;
+                atomicAdd(&hm[e[0]], r0);
+                if (e[1] != e[0]) atomicAdd(&hm[e[1]], r1);
+                if (e[2] != e[1]) atomicAdd(&hm[e[2]], r2);
+                if (e[3] != e[2]) atomicAdd(&hm[e[3]], r3);
             }
         }
-        flush();
+        flush();                                          // the chunk's counts (its pixel weights)
         unsigned m2 = exact_mask;
         while (m2) {
             const int k = __ffs(m2) - 1;
@@ -1171,6 +1093,7 @@ __global__ __launch_bounds__(WARPS * 32, 3) void k_backward_hist(UpdateArgs a, c
             back_crossing_step_hist<M, PM>(a, s_tf, pm, base + k * STEP + lane * 4, __shfl_sync(FULL, s_start, k),
                                            lane, g, sG, h);
         }
+        cur = 0xFFFFFFFFu;                               // next chunk: weights reloaded
     }
     __syncthreads();
     for (int i = tid; i < MT1; i += blockDim.x) gpart[(uint64_t)blockIdx.x * MT1 + i] = sG[i];
@@ -1178,7 +1101,7 @@ __global__ __launch_bounds__(WARPS * 32, 3) void k_backward_hist(UpdateArgs a, c
 
 // Sums the CTAs' tables in two fixed-order levels: block (x, y) adds rows y,
 // y + gridDim.y, ... of 32 columns (one per lane; the warps take rows in turn
-// and are combined in warp order) into part2[y]; then k_gtab_final sums the
+// and are combined in warp order) into part2[y]; then k_grad_final sums the
 // gridDim.y partial rows per entry, folding entry T into entry T-1.
 __global__ __launch_bounds__(256) void k_gtab_reduce(uint32_t MT1, uint64_t rows, const double* __restrict__ gpart,
                                                      double* __restrict__ part2)
@@ -1199,21 +1122,47 @@ __global__ __launch_bounds__(256) void k_gtab_reduce(uint32_t MT1, uint64_t rows
     }
 }
 
-__global__ void k_gtab_final(uint32_t M, uint32_t T, uint32_t segs, const double* __restrict__ part2,
-                             double* __restrict__ gtab)
+// The last reduction level and the chain rule in one launch, one warp per
+// control point (m, k): its lanes take the table entries whose interpolation
+// weights involve k (x = e (K-1)/(T-1) in [k-1, k+1]), sum each entry's
+// partial rows (entry T, t = 1, folds into entry T-1), write gtab for the
+// entries whose lower control point is k, and add weight x gradient in a
+// fixed order: dL/dctrl[m][k] = sum_e gtab[m][e] w_k(e).
+__global__ __launch_bounds__(256) void k_grad_final(uint32_t M, uint32_t K, uint32_t T, uint32_t segs,
+                                                    const double* __restrict__ part2, double* __restrict__ gtab,
+                                                    float* __restrict__ grad)
 {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M * T) return;
-    const uint32_t m = i / T, e = i - m * T, T1 = T + 1, col = m * T1 + e;
-    double s = 0.0;
-    for (uint32_t y = 0; y < segs; ++y) {
-        s += part2[(uint64_t)y * M * T1 + col];
-        if (e == T - 1) s += part2[(uint64_t)y * M * T1 + col + 1];    // entry T is t = 1: entry T-1
+    const uint32_t wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (wid >= M * K) return;
+    const uint32_t m = wid / K, k = wid % K, T1 = T + 1;
+    const uint64_t lo_num = k > 0 ? (uint64_t)(k - 1) * (T - 1) : 0, hi_num = (uint64_t)(k + 1) * (T - 1);
+    const uint64_t e_lo = lo_num / (K - 1), e_hi = hi_num / (K - 1) + 1;
+    const uint32_t e0 = e_lo > 0 ? (uint32_t)e_lo - 1 : 0, e1 = (uint32_t)(e_hi < T - 1 ? e_hi : T - 1);
+    double acc = 0.0;
+    for (uint32_t e = e0 + lane; e <= e1; e += 32) {
+        const uint32_t col = m * T1 + e;
+        double G = 0.0;
+        for (uint32_t y = 0; y < segs; ++y) {
+            G += part2[(uint64_t)y * M * T1 + col];
+            if (e == T - 1) G += part2[(uint64_t)y * M * T1 + col + 1];
+        }
+        const double x = (double)e * (double)(K - 1) / (double)(T - 1);
+        uint32_t k0 = (uint32_t)floor(x);
+        if (k0 > K - 2) k0 = K - 2;
+        const double w = x - k0;
+        if (k0 == k) {
+            acc += (1.0 - w) * G;
+            gtab[(uint64_t)m * T + e] = G;
+        }
+        if (k0 + 1 == k) acc += w * G;
     }
-    gtab[i] = s;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if (lane == 0) grad[wid] = (float)acc;
 }
 
-// dL/dctrl[m][k] = sum_e gtab[m][e] * (interpolation weight of k in entry e)
+// dL/dctrl[m][k] = sum_e gtab[m][e] * (interpolation weight of k in entry e),
+// from a finished gtab (the adjoint with global atomics)
 __global__ void k_grad_ctrl(uint32_t M, uint32_t K, uint32_t T, const double* __restrict__ gtab,
                             float* __restrict__ grad)
 {
@@ -1269,9 +1218,10 @@ template <int M> constexpr int ring_depth() { return 2; }
 template <int M> constexpr int ring_min_blocks() { return M <= 4 ? 4 : 2; }
 
 template <int M>
-size_t ring_smem(uint32_t T, uint32_t* tf_bytes)
+size_t ring_smem(uint32_t T, uint32_t* tf_bytes, bool alpha = false)
 {
-    *tf_bytes = (uint32_t)(((size_t)M * (T + 1) * sizeof(float) + 127) & ~(size_t)127);
+    // the float tables, and with alpha their u32 fixed-point twins
+    *tf_bytes = (uint32_t)(((size_t)M * (T + 1) * sizeof(float) + 127) & ~(size_t)127) * (alpha ? 2u : 1u);
     return *tf_bytes + (size_t)WARPS * ring_depth<M>() * (M * STEP * 4 + STEP + 8) + 8;
 }
 
@@ -1304,9 +1254,11 @@ template <int M, int PM>
 cudaError_t launch_passA_ring(cudaStream_t s, const UpdateArgs& a, uint32_t n_tiles, bool p2)
 {
     constexpr int D = ring_depth<M>(), MB = ring_min_blocks<M>();
+    const bool alpha = a.astep != nullptr;
     uint32_t tf_bytes;
-    const size_t smem = ring_smem<M>(a.T, &tf_bytes);
-    auto kernel = p2 ? k_passA_ring<M, PM, true, D, MB> : k_passA_ring<M, PM, false, D, MB>;
+    const size_t smem = ring_smem<M>(a.T, &tf_bytes, alpha);
+    auto kernel = alpha ? (p2 ? k_passA_ring<M, PM, true, D, MB, true> : k_passA_ring<M, PM, false, D, MB, true>)
+                        : (p2 ? k_passA_ring<M, PM, true, D, MB> : k_passA_ring<M, PM, false, D, MB>);
     cudaError_t e;
     if ((e = smem_attr(kernel, smem)) != cudaSuccess) return e;
     int grid = 0;
@@ -1328,10 +1280,9 @@ cudaError_t run_passes(cudaStream_t s, const UpdateArgs& a, uint32_t n_tiles, si
     if ((e = smem_attr(k_passA<M, PM, true>, smem)) != cudaSuccess) return e;
     if ((e = smem_attr(k_passA<M, PM, false>, smem)) != cudaSuccess) return e;
     if ((e = smem_attr(k_passB<M, PM>, smem)) != cudaSuccess) return e;
-    if ((e = smem_attr(k_passB_steps<M, PM, false>, smem)) != cudaSuccess) return e;
-    if ((e = smem_attr(k_passB_steps<M, PM, true>, smem)) != cudaSuccess) return e;
     // the bulk copies need 16-byte aligned rows (they read whole chunks only)
     const bool ring = ((uintptr_t)a.val % 16 == 0) && ((uintptr_t)a.lev % 16 == 0) && (a.pitch % 4 == 0);
+    if (a.astep && !ring) return cudaErrorInvalidValue;   // alpha sums come from the streaming pass A only
     if (a.events) cudaEventRecord(a.events[1], s);
     if (n_tiles) {
         if (ring) {
@@ -1344,14 +1295,7 @@ cudaError_t run_passes(cudaStream_t s, const UpdateArgs& a, uint32_t n_tiles, si
     }
     if (a.events) cudaEventRecord(a.events[2], s);
     if (a.vt) return cudaSuccess;          // bins come from range queries (see run_update)
-    if (n_tiles) {
-        if (a.step_sums && a.asum)
-            k_passB_steps<M, PM, true><<<n_tiles, WARPS * 32, smem, s>>>(a);
-        else if (a.step_sums)
-            k_passB_steps<M, PM, false><<<n_tiles, WARPS * 32, smem, s>>>(a);
-        else
-            k_passB<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a);
-    }
+    if (n_tiles) k_passB<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a);
     if (a.events) cudaEventRecord(a.events[3], s);
     return cudaSuccess;
 }
@@ -1363,7 +1307,10 @@ cudaError_t run_update(cudaStream_t s, const UpdateArgs& a)
     const size_t smem = (size_t)M * (a.T + 1) * sizeof(float);
     cudaError_t e;
     if ((e = smem_attr(k_vmax_exact<M>, smem)) != cudaSuccess) return e;
-    const uint64_t n_status = n_tiles;                 // scan status words, one per tile
+    // scan status words: one per tile (direct-load pass A), or per chunk-scan
+    // block and quantity (widths and, with alpha sums, each field's alphas)
+    const uint64_t scan_blocks = ((uint64_t)n_tiles * WARPS + SCAN_SPAN - 1) / SCAN_SPAN;
+    const uint64_t n_status = a.achunk ? (n_tiles > SCAN_Q * scan_blocks ? n_tiles : SCAN_Q * scan_blocks) : n_tiles;
     const uint64_t clear = (uint64_t)a.M * a.W > n_status ? (uint64_t)a.M * a.W : n_status;
     if (a.events) cudaEventRecord(a.events[0], s);
     k_prepare<<<grid_cap(clear, 256), 256, 0, s>>>(a, n_status);
@@ -1372,16 +1319,19 @@ cudaError_t run_update(cudaStream_t s, const UpdateArgs& a)
         k_consts<<<1, 1, 0, s>>>(a);
     }
     if (a.vt && a.vt_build) {
-        if ((e = launch_value_tables(s, a.M, *a.vt, a.vt_tot_lo, a.vt_tot_hi)) != cudaSuccess) return e;
+        if ((e = launch_value_tables(s, a.M, *a.vt)) != cudaSuccess) return e;
     }
     e = a.prm.P == 1.0f ? run_passes<M, POW_ONE>(s, a, n_tiles, smem) : run_passes<M, POW_GEN>(s, a, n_tiles, smem);
     if (e != cudaSuccess) return e;
-    if (a.vt) {
+    if (a.vt && a.n > 0) {
         // bins as range queries over the value tables (writes final bins)
-        const QueryArgs qa{a.consts, a.chunk_prefix, a.step_sums, a.H, a.S, a.psum, a.pmm, 1u};
+        const QueryArgs qa{a.consts, a.chunk_prefix, a.step_sums, a.H, a.S, a.psum, a.pmm, 1u,
+                           a.astep, a.achunk, a.astep ? a.apart : nullptr, (uint64_t)n_tiles * WARPS};
         if ((e = launch_bins(s, a, qa, *a.vt)) != cudaSuccess) return e;
         if (a.events) cudaEventRecord(a.events[3], s);
     } else {
+        // the placement pass's bins (or, with no cells, the empty bins k_prepare left)
+        if (a.vt && a.events) cudaEventRecord(a.events[3], s);
         k_finalize<<<grid_cap((uint64_t)a.M * a.W, 256), 256, 0, s>>>(a);
     }
     if (a.events) cudaEventRecord(a.events[4], s);
@@ -1406,11 +1356,14 @@ cudaError_t run_backward_pm(cudaStream_t s, const UpdateArgs& a, const float* g,
         const size_t smem = backward_hist_smem(M, a.T);
         if ((e = smem_attr(k_backward_hist<M, PM>, smem)) != cudaSuccess) return e;
         if (!n_tiles) return cudaMemsetAsync(gtab, 0, (size_t)M * a.T * sizeof(double), s);
-        k_backward_hist<M, PM><<<n_tiles, WARPS * 32, smem, s>>>(a, g, gpart);
+        int grid = 0;                                 // persistent: the CTAs resident at once
+        if ((e = resident_ctas(k_backward_hist<M, PM>, smem, &grid)) != cudaSuccess) return e;
+        if ((uint32_t)grid > n_tiles) grid = (int)n_tiles;
+        if ((e = cudaMemsetAsync(a.counters + 2, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+        k_backward_hist<M, PM><<<grid, WARPS * 32, smem, s>>>(a, g, gpart);
         const uint32_t MT1 = M * (a.T + 1);
         double* part2 = gpart + (uint64_t)n_tiles * MT1;
-        k_gtab_reduce<<<dim3((MT1 + 31) / 32, GTAB_SEGS), 256, 0, s>>>(MT1, n_tiles, gpart, part2);
-        k_gtab_final<<<(M * a.T + 255) / 256, 256, 0, s>>>(M, a.T, GTAB_SEGS, part2, gtab);
+        k_gtab_reduce<<<dim3((MT1 + 31) / 32, GTAB_SEGS), 256, 0, s>>>(MT1, (uint64_t)grid, gpart, part2);
         return cudaGetLastError();
     }
     const size_t table = (size_t)((M * (a.T + 1) + 1) & ~1u) * sizeof(float);
@@ -1430,7 +1383,13 @@ cudaError_t run_backward(cudaStream_t s, const UpdateArgs& a, const float* g, do
     cudaError_t e = a.prm.P == 1.0f ? run_backward_pm<M, POW_ONE>(s, a, g, gtab, gpart)
                                     : run_backward_pm<M, POW_GEN>(s, a, g, gtab, gpart);
     if (e != cudaSuccess) return e;
-    k_grad_ctrl<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(M, K, a.T, gtab, grad_ctrl);
+    if (gpart && a.n) {
+        const uint32_t n_tiles = (uint32_t)((a.n + TILE - 1) / TILE);
+        const double* part2 = gpart + (uint64_t)n_tiles * M * (a.T + 1);
+        k_grad_final<<<(unsigned)((M * K + 7) / 8), 256, 0, s>>>(M, K, a.T, GTAB_SEGS, part2, gtab, grad_ctrl);
+    } else {
+        k_grad_ctrl<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(M, K, a.T, gtab, grad_ctrl);
+    }
     return cudaGetLastError();
 }
 

@@ -10,7 +10,7 @@ import ctypes
 
 import numpy as np
 
-from . import DVLError, dvl_bins, dvl_params, dvl_server_config, dvl_server_stats, lib, MEM_HOST
+from . import DVLError, dvl_batch_span, dvl_bins, dvl_params, dvl_server_config, dvl_server_stats, lib, MEM_HOST
 
 __all__ = ["DVLServer"]
 
@@ -98,3 +98,20 @@ class DVLServer:
 
     def reset_stats(self):
         self._check(lib.dvl_server_reset_stats(self._h))
+
+    def timeline(self) -> np.ndarray:
+        """The finished batches since the last reset as a structured array:
+        dataset, requests, start_ms / end_ms (events on the data set's stream
+        around its kernels) and run_start_ms / run_end_ms (the device clock
+        when its first kernel started and its last kernel ended)."""
+        n = ctypes.c_uint32()
+        self._check(lib.dvl_server_timeline(self._h, None, 0, ctypes.byref(n)))
+        out = (dvl_batch_span * max(n.value, 1))()
+        self._check(lib.dvl_server_timeline(self._h, out, n.value, ctypes.byref(n)))
+        arr = np.zeros(n.value, dtype=[("dataset", np.uint32), ("requests", np.uint32), ("start_ms", np.float64),
+                                       ("end_ms", np.float64), ("run_start_ms", np.float64),
+                                       ("run_end_ms", np.float64)])
+        for i in range(n.value):
+            o = out[i]
+            arr[i] = (o.dataset, o.requests, o.start_ms, o.end_ms, o.run_start_ms, o.run_end_ms)
+        return arr

@@ -141,7 +141,36 @@ def threshold_amr(base_n: int, n_levels: int, tau: float, seed: int, pinned: boo
     _L().amrgen_fill(ctypes.byref(cfg), offsets.ctypes.data, *_ptrs(lower, level, fields))
     meta = dict(kind="threshold", seed=seed, base_n=base_n, levels=n_levels, tau=float(tau),
                 box=None if box is None else [list(box[0]), int(box[1])])
+    if box is None:
+        meta["_base_offsets"] = np.append(offsets, np.int64(n))      # first cell of every base cell, then n
     return AMR(lower, level, fields, base_n << (n_levels - 1), meta)
+
+
+def sub_box(full: AMR, box, pinned: bool = False) -> AMR:
+    """The cells of a sub-box of base cells, cut out of a whole threshold
+    data set: the same cells, fields and order that ``threshold_amr(...,
+    box=box)`` generates (base cells are written x fastest, each one's cells
+    contiguous), without evaluating the noise again."""
+    off = full.meta["_base_offsets"]
+    base = int(full.meta["base_n"])
+    (x0, y0, z0), e = [int(v) for v in box[0]], int(box[1])
+    runs = []
+    for z in range(z0, z0 + e):
+        for y in range(y0, y0 + e):
+            b = x0 + base * (y + base * z)
+            runs.append((int(off[b]), int(off[b + e])))
+    n = sum(b - a for a, b in runs)
+    lower, level, fields = _alloc(n, pinned)
+    pos = 0
+    for a, b in runs:
+        k = b - a
+        lower[:, pos:pos + k] = full.lower[:, a:b]
+        level[pos:pos + k] = full.level[a:b]
+        fields[:, pos:pos + k] = full.fields[:, a:b]
+        pos += k
+    meta = {k: v for k, v in full.meta.items() if k != "_base_offsets"}
+    meta["box"] = [[x0, y0, z0], e]
+    return AMR(lower, level, fields, full.grid, meta)
 
 
 def tau_for_target(base_n: int, n_levels: int, target: int, seed: int, sample_stride: int = 0,
@@ -209,14 +238,16 @@ def box_count(name: str, box) -> int:
 
 
 def serving_boxes(seed: int = 5, n: int = 8, lo: float = 1e6, hi: float = 2e8, name: str = "large"):
-    """Sub-boxes of a named data set whose cell counts follow a log-uniform
-    draw in [lo, hi] (seeded): random box corners, the edge bisected on the
-    count.  Returns [(box, count)], one per serving data set."""
+    """Sub-boxes of a named data set whose cell counts are log-uniform over
+    [lo, hi]: the n targets are spaced evenly in log from lo to hi (a
+    stratified log-uniform draw that always spans the range); each box has a
+    random corner (seeded) and its edge bisected on the count.  Returns
+    [(box, count)], one per serving data set."""
     rng = np.random.Generator(np.random.PCG64(seed))
     base = CONFIGS[name]["base_n"]
     out = []
-    for _ in range(n):
-        target = float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+    for i in range(n):
+        target = float(np.exp(np.log(lo) + (np.log(hi) - np.log(lo)) * i / max(n - 1, 1)))
         corner = rng.uniform(0.0, 1.0, 3)
         best = None
         e_lo, e_hi = 1, base
@@ -234,16 +265,20 @@ def serving_boxes(seed: int = 5, n: int = 8, lo: float = 1e6, hi: float = 2e8, n
     return out
 
 
-# The serving data sets: serving_boxes() (seed 5, 8 sets, log-uniform targets
-# in [1e6, 2e8] over the "large" configuration), fixed here with their counts
-# so that generating them needs no search.
-SERVING = [(((68, 43, 24), 43), 74163139), (((31, 33, 3), 47), 1402204), (((90, 59, 21), 37), 2418025),
-           (((74, 68, 64), 52), 8043881), (((33, 46, 4), 60), 6952814), (((13, 43, 3), 78), 22800359),
-           (((67, 17, 69), 50), 37489012), (((0, 23, 0), 95), 102660083)]
+# The serving data sets: serving_boxes() (seed 5, 8 sets, log-uniform sizes
+# from 1e6 to 2e8 over the "large" configuration), fixed here with their counts
+# so that generating them needs no search: 1.34M ... 200.0M cells, 382.5M in
+# total.
+SERVING = [(((71, 71, 45), 39), 1340564), (((29, 5, 39), 24), 2447689), (((40, 4, 4), 29), 4772020),
+           (((87, 57, 20), 40), 10048121), (((34, 76, 70), 49), 20096538), (((92, 43, 54), 18), 46586674),
+           (((45, 4, 37), 61), 97227745), (((6, 21, 1), 103), 200000058)]
 
 
-def serving_datasets(pinned: bool = False):
-    """The 8 serving data sets (sub-boxes of "large", see SERVING)."""
+def serving_datasets(pinned: bool = False, full: AMR = None):
+    """The 8 serving data sets (sub-boxes of "large", see SERVING); cut out
+    of ``full`` (the whole "large" data set) when it is given."""
+    if full is not None:
+        return [sub_box(full, box, pinned=pinned) for box, _ in SERVING]
     return [make("large", pinned=pinned, box=box) for box, _ in SERVING]
 
 

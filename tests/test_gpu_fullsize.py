@@ -12,9 +12,8 @@ first TF).  The oracle cannot run the whole update in seconds, so:
   sum of all widths;
 * bins: properties that hold at any size (no empty pixel when F > 0, counts
   cover every cell, min <= mean <= max within [0, 1], y is the TF at the mean's
-  entry), and agreement with the library's independent placement path (the
-  second pass over the cells used for alpha means): counts, min and max bit
-  for bit, sums to 1e-5 relative;
+  entry); an update that also computes alpha means gives the same bins bit
+  for bit, and alpha means in [0, 1];
 * and the whole update against the oracle: the oracle's key of every cell
   (threaded orc_keys), which the library's permutation must put in strictly
   increasing order -- with distinct keys that is the one stable order -- then
@@ -94,14 +93,14 @@ def test_bins_at_full_size(full):
         assert np.all(mean64 >= b["min"] * (1 - 1e-6)) and np.all(mean64 <= b["max"] * (1 + 1e-6) + 1e-30)
         e = np.minimum(np.floor(b["mean"].astype(np.float32) * np.float32(T)).astype(np.int64), T - 1)
         assert np.array_equal(b["y"], tf[m][e])
-    # the independent placement path (second pass over the cells)
+    # with alpha means (pass A also sums the cells' alphas): the same bins
     ctx.update(P=P, min_importance=MI, width=W, want_alpha=1)
     pl = [ctx.read_bins(m) for m in range(4)]
-    assert np.array_equal(pl[0]["count"], rq[0]["count"])
     for m in range(4):
-        assert np.array_equal(pl[m]["min"].view(np.uint32), rq[m]["min"].view(np.uint32))
-        assert np.array_equal(pl[m]["max"].view(np.uint32), rq[m]["max"].view(np.uint32))
-        assert np.all(np.abs(pl[m]["sum"] - rq[m]["sum"]) <= 1e-5 * np.abs(rq[m]["sum"]) + 1e-30)
+        for k in ("count", "sum", "min", "max", "mean", "y"):
+            assert np.array_equal(pl[m][k].view(np.uint8), rq[m][k].view(np.uint8)), (m, k)
+    am = ctx.read_alpha_means()
+    assert am.shape == (4, W) and np.all((am >= 0) & (am <= 1))
 
 
 def test_log_scale_at_full_size(full):

@@ -97,9 +97,9 @@ def test_batch_20M(diff_set):
 
 
 def test_bins_74M_sub_box_of_large():
-    box, count = synth.SERVING[0]
+    box = ((68, 43, 24), 43)                     # 43^3 base cells of the 128^3
     amr = synth.make("large", box=box)
-    assert amr.n == count > 70_000_000
+    assert amr.n == 74_163_139
     keys, perm, lev, fl = _sorted(amr)
     ctx = _loaded(amr)
     try:

@@ -150,3 +150,76 @@ def test_server_errors_and_warmup():
             srv.submit(did, bad, 256)                       # alpha outside [0, 1]
         r = srv.wait(srv.submit(did, t, 256), timeout=120)
         assert r["count"].sum() >= 3000
+
+
+def _overlap_ms(tl, a="run_start_ms", b="run_end_ms"):
+    """Device time during which batches of at least two different data sets
+    were running (the union of their pairwise intersections), and the time at
+    least one batch was running."""
+    ev = []
+    for r in tl:
+        ev.append((float(r[a]), 1, int(r["dataset"])))
+        ev.append((float(r[b]), -1, int(r["dataset"])))
+    ev.sort(key=lambda e: (e[0], e[1]))
+    active, last, both, busy = {}, None, 0.0, 0.0
+    for t, d, ds in ev:
+        if last is not None:
+            live = [k for k, c in active.items() if c > 0]
+            if len(live) >= 1:
+                busy += t - last
+            if len(live) >= 2:
+                both += t - last
+        active[ds] = active.get(ds, 0) + d
+        last = t
+    return both, busy
+
+
+def test_datasets_overlap_on_device():
+    """Batches of different data sets run on their own streams at the same
+    time.  With a stream of requests for two data sets, the timeline shows
+    (a) batches of both data sets in flight together: the CUDA events around
+    their kernels on the two streams give intersecting spans, and (b) their
+    kernels executing together: the device clock read by each batch's first
+    kernel at its start and by its last kernel's blocks at their end gives
+    intersecting run intervals.  Every result still equals a plain update."""
+    a = synth.make("diff", box=((0, 0, 0), 48))
+    b = synth.make("diff", box=((16, 16, 16), 48))
+    assert a.n > 6_000_000 and b.n > 6_000_000
+    reqs = [(i % 2, synth.random_tfs(4000 + i), 1024) for i in range(64)]
+    with DVLServer(0, max_batch=8, max_inflight=2, max_width=1024) as srv:
+        for d in (a, b):
+            srv.add_dataset(d.lower, d.level, d.fields)
+        srv.warmup()
+        srv.reset_stats()
+        ids = [srv.submit(*r) for r in reqs]
+        got = [srv.wait(i, timeout=120) for i in ids]
+        tl = srv.timeline()
+        st = srv.stats()
+    assert len(tl) == st["batches"] and set(tl["dataset"].tolist()) == {0, 1}
+    assert int(tl["requests"].sum()) == len(reqs)
+    assert np.all(tl["end_ms"] > tl["start_ms"]) and tl["start_ms"].min() == 0.0
+    assert np.all(tl["run_end_ms"] > tl["run_start_ms"]) and tl["run_start_ms"].min() == 0.0
+    # a batch runs inside its events' span (different clocks: compare durations)
+    assert np.all(tl["run_end_ms"] - tl["run_start_ms"] <= tl["end_ms"] - tl["start_ms"] + 0.05)
+    rows = "\n".join(f"ds {r['dataset']} k {r['requests']} ev [{r['start_ms']:.3f}, {r['end_ms']:.3f}] "
+                      f"run [{r['run_start_ms']:.3f}, {r['run_end_ms']:.3f}]" for r in tl)
+    both_ev, _ = _overlap_ms(tl, "start_ms", "end_ms")
+    both_run, busy = _overlap_ms(tl)
+    assert both_ev > 0.0, "no two data sets' batches in flight together:\n" + rows
+    assert both_run > 0.0, f"no two data sets' kernels ran together (busy {busy:.3f} ms):\n" + rows
+    ctxs = []
+    try:
+        for d in (a, b):
+            c = dvl.DVL(0)
+            c.load_amr(d.lower, d.level, d.fields)
+            c.build_order(dvl.SFC_HILBERT)
+            ctxs.append(c)
+        for (ds, tf, W), g in zip(reqs, got):
+            ctxs[ds].set_tfs(tf)
+            ctxs[ds].update(width=W)
+            for m in range(4):
+                ref = ctxs[ds].read_bins(m)
+                _same({k: (g[k][m] if k != "count" else g[k]) for k in g}, ref)
+    finally:
+        for c in ctxs:
+            c.close()
