@@ -388,14 +388,14 @@ def run_ours(args):
         doms.append(([float(a + f * (b - a)) for a, b in zip(dlo, dhi)],
                      [float(b - f * (b - a)) for a, b in zip(dlo, dhi)]))
     for i in range(2):                                  # warm (first use of the table kernels)
-        ctx.set_tfs(tfs[i], lo=doms[i][0], hi=doms[i][1])
+        ctx.set_tfs(tfs[i % len(tfs)], lo=doms[i][0], hi=doms[i][1])
         ctx.update(**kw)
     torch.cuda.synchronize()
     d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
     d0.record(stream)
     for i in range(n_dom):
-        ctx.set_tfs(tfs[i], lo=doms[2 + i][0], hi=doms[2 + i][1])
+        ctx.set_tfs(tfs[i % len(tfs)], lo=doms[2 + i][0], hi=doms[2 + i][1])
         ctx.update(**kw)
     d1.record(stream)
     d1.synchronize()

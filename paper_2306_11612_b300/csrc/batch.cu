@@ -15,6 +15,13 @@
 namespace dvl {
 
 namespace {
+
+__device__ __forceinline__ float4 lds_f32x4(uint32_t addr)
+{
+    float4 r;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "r"(addr));
+    return r;
+}
 // ---------------------------------------------------------------------------
 // Batched updates: constants of K TFs, and pass A over all of them
 // ---------------------------------------------------------------------------
@@ -42,12 +49,17 @@ __global__ void k_prepare_batch(UpdateArgs a, BatchArgs b)
 // per TF it writes step totals and, per tile, runs its own decoupled
 // look-back scan.  G is a compile-time constant so the TF loop unrolls; per
 // cell the table offsets (all fields) and the level factor 2^(L w) are
-// computed once and reused by every TF of the group.  With P = 1 the
+// computed once and reused by every TF of the group.  A cell's entry of a
+// field is the same for every TF of the batch (one TF domain), so the group's
+// tables are stored TF-innermost -- row (field m, entry e) holds the G TFs'
+// alphas, padded to G + 4 floats so that consecutive entries fall in
+// different shared-memory bank groups -- and one 128-bit load fetches 4 TFs'
+// alphas.  With P = 1 the
 // fixed-point scale 2^Q of each TF is folded into its constants: scaling by a
 // power of two is exact, so rint(max(max(V/maxV, m_b) 2^L, m_a) 2^Q) equals
 // rint(max(max(V (2^Q/maxV), m_b 2^Q) 2^L, m_a 2^Q)) bit for bit.
 template <int M, int PM, int G, int ST>
-__global__ __launch_bounds__(WARPS * 32, M <= 4 ? 3 : 1) void k_passA_batch(UpdateArgs a, BatchArgs b)
+__global__ __launch_bounds__(WARPS * 32, M <= 4 ? (G >= 16 ? 2 : 3) : 1) void k_passA_batch(UpdateArgs a, BatchArgs b)
 {
     extern __shared__ float4 s_dyn[];                  // G x 1 params, then G x M x T1 tables
     __shared__ unsigned long long s_ct[WARPS][G];      // chunk totals per warp and TF
@@ -56,10 +68,12 @@ __global__ __launch_bounds__(WARPS * 32, M <= 4 ? 3 : 1) void k_passA_batch(Upda
     // table stride per field: ST (a compile-time constant >= T + 1, so that
     // the unrolled TF loop addresses its tables with immediate offsets), or
     // T + 1 when ST = 0
+    constexpr uint32_t RS = G + 4;                     // floats per table row (field, entry)
     const uint32_t T = a.T, T1 = ST ? (uint32_t)ST : T + 1, K = b.K, MT1 = M * T1;
     const uint32_t n_tiles = (uint32_t)b.n_tiles, n_groups = (K + G - 1) / G;
     float4* s_par = s_dyn;                             // per TF: (1/maxV, m_b, m_a, 2^Q), see above
-    float* s_tf = reinterpret_cast<float*>(s_dyn + G);
+    float* s_tf = reinterpret_cast<float*>(s_dyn + G); // M x T1 rows of RS floats, TF innermost
+    const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(s_tf);
     const UpdateConsts* C0 = b.consts;
     float lo[M], sc[M];
 #pragma unroll
@@ -71,9 +85,9 @@ __global__ __launch_bounds__(WARPS * 32, M <= 4 ? 3 : 1) void k_passA_batch(Upda
     auto load_group = [&](uint32_t first) {
         g0 = first;
         gk = K - g0 < (uint32_t)G ? K - g0 : (uint32_t)G;
-        for (uint32_t i = tid; i < gk * MT1; i += blockDim.x) {
-            const uint32_t kk = i / MT1, r = i - kk * MT1, m = r / T1, e = r - m * T1;
-            s_tf[i] = b.tfs[((uint64_t)(g0 + kk) * M + m) * T + (e < T ? e : T - 1)];
+        for (uint32_t i = tid; i < MT1 * RS; i += blockDim.x) {
+            const uint32_t row = i / RS, kk = i - row * RS, m = row / T1, e = row - m * T1;
+            s_tf[i] = kk < gk ? b.tfs[((uint64_t)(g0 + kk) * M + m) * T + (e < T ? e : T - 1)] : 0.0f;
         }
         for (uint32_t kk = tid; kk < G; kk += blockDim.x) {
             float4 pr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -116,7 +130,7 @@ __global__ __launch_bounds__(WARPS * 32, M <= 4 ? 3 : 1) void k_passA_batch(Upda
         for (int st = 0; st < STEPS; ++st) {
             if (base + (uint64_t)st * STEP >= a.n) break;            // warp-uniform
             const uint64_t idx = base + st * STEP + lane * 4;
-            uint32_t off[4][M];
+            uint32_t off[4][M];                        // shared address of row (m, entry)
             float lvl[4];
             bool valid[4];
             float v[4][M];
@@ -132,57 +146,69 @@ __global__ __launch_bounds__(WARPS * 32, M <= 4 ? 3 : 1) void k_passA_batch(Upda
                 for (int j = 0; j < 4; ++j) {
 #pragma unroll
                     for (int m = 0; m < M; ++m)
-                        off[j][m] = m * T1 + floor_small(__fmul_rn(norm_t(v[j][m], lo[m], sc[m]), Tf));
+                        off[j][m] = s_base + (m * T1 + floor_small(__fmul_rn(norm_t(v[j][m], lo[m], sc[m]), Tf))) * (RS * 4);
                     lvl[j] = exp2i((int)((L4 >> (8 * j)) & 0xFF) * wshift);
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
 #pragma unroll
-                    for (int m = 0; m < M; ++m) off[j][m] = 0;
+                    for (int m = 0; m < M; ++m) off[j][m] = s_base;
                     lvl[j] = 0.0f;
                 }
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) valid[j] = idx + j < a.n;
             // lane kk keeps TF kk's step total; a step with all 128 cells
-            // present (every step but the data set's last) needs no masks
+            // present (every step but the data set's last) needs no masks.
+            // TFs are evaluated 4 at a time (one 128-bit table load per field).
             unsigned long long mine = 0;
-            auto one_tf = [&](int kk, auto full_tag) {
+            auto one_quad = [&](int kq, auto full_tag) {
                 constexpr bool ALL = decltype(full_tag)::value;     // every cell present
-                const float* tk = s_tf + kk * MT1;
-                const float4 pr = s_par[kk];
-                uint32_t q[4];
+                float4 pr[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) pr[i] = s_par[kq * 4 + i];
+                unsigned long long l[4] = {0, 0, 0, 0};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    float al[M];
+                    float4 a4[M];
 #pragma unroll
-                    for (int m = 0; m < M; ++m) al[m] = tk[off[j][m]];
-                    // Eq. 3 as importance<PM>, with the level factor precomputed
-                    // (and, with P = 1, 2^Q folded into the constants)
-                    const float r = fmaxf(__fmul_rn(spread<M>(al), pr.x), pr.y);
-                    const float x = __fmul_rn(r, lvl[j]);
-                    if (PM == POW_ONE) {
-                        q[j] = __float2uint_rn(fmaxf(x, pr.z));
-                    } else {
-                        const float f = fmaxf(pow_gen(x, n2, P), pr.z);
-                        q[j] = __float2uint_rn(__fmul_rn(f, pr.w));
+                    for (int m = 0; m < M; ++m) a4[m] = lds_f32x4(off[j][m] + (uint32_t)kq * 16u);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        float al[M];
+#pragma unroll
+                        for (int m = 0; m < M; ++m) al[m] = i == 0 ? a4[m].x : i == 1 ? a4[m].y : i == 2 ? a4[m].z : a4[m].w;
+                        // Eq. 3 as importance<PM>, with the level factor precomputed
+                        // (and, with P = 1, 2^Q folded into the constants)
+                        const float r = fmaxf(__fmul_rn(spread<M>(al), pr[i].x), pr[i].y);
+                        const float x = __fmul_rn(r, lvl[j]);
+                        uint32_t q;
+                        if (PM == POW_ONE) {
+                            q = __float2uint_rn(fmaxf(x, pr[i].z));
+                        } else {
+                            const float f = fmaxf(pow_gen(x, n2, P), pr[i].z);
+                            q = __float2uint_rn(__fmul_rn(f, pr[i].w));
+                        }
+                        if (!ALL) q = valid[j] ? q : 0u;
+                        l[i] += q;
                     }
-                    if (!ALL) q[j] = valid[j] ? q[j] : 0u;
                 }
-                const unsigned long long l = ((unsigned long long)q[0] + q[1]) + ((unsigned long long)q[2] + q[3]);
-                const unsigned long long tot = warp_total_small(l);
-                mine = lane == kk ? tot : mine;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const unsigned long long tot = warp_total_small(l[i]);
+                    mine = lane == kq * 4 + i ? tot : mine;
+                }
             };
             if (base + (uint64_t)(st + 1) * STEP <= a.n) {             // warp-uniform
 #pragma unroll
-                for (int kk = 0; kk < G; ++kk) {
-                    if (kk >= (int)gk) break;                          // block-uniform
-                    one_tf(kk, std::true_type{});
+                for (int kq = 0; kq < G / 4; ++kq) {
+                    if (kq * 4 >= (int)gk) break;                      // block-uniform
+                    one_quad(kq, std::true_type{});
                 }
             } else {                                                   // the data set's last step:
 #pragma unroll 1                                                       // not unrolled (compile time)
-                for (int kk = 0; kk < (int)gk; ++kk) one_tf(kk, std::false_type{});
+                for (int kq = 0; kq * 4 < (int)gk; ++kq) one_quad(kq, std::false_type{});
             }
             if (lane < (int)gk) {
                 b.step_sums[((uint64_t)(g0 + lane) * b.n_chunks + chunk) * STEPS + st] = mine;
@@ -255,7 +281,7 @@ constexpr int SMALL_T1 = 257;                    // fixed table stride for T <= 
 size_t passA_batch_smem(uint32_t M, uint32_t T, uint32_t G)
 {
     const uint32_t T1 = T + 1 <= (uint32_t)SMALL_T1 ? SMALL_T1 : T + 1;
-    return (size_t)G * sizeof(float4) + (size_t)G * M * T1 * sizeof(float);
+    return (size_t)G * sizeof(float4) + (size_t)(G + 4) * M * T1 * sizeof(float);
 }
 
 template <int M, int PM, int G, int ST>

@@ -447,14 +447,13 @@ __device__ __forceinline__ void steps_minmax(const ValueTableArgs& v, uint32_t m
 }
 
 // Prefix of the fixed-point alpha sums of field m over steps [0, s): the
-// exclusive prefix of s's chunk plus the steps of that chunk before s.
+// exclusive prefix of s's chunk plus that of s within its chunk (s may be the
+// step count, which ends a chunk when it is a multiple of STEPS).
 __device__ __forceinline__ unsigned long long alpha_prefix(const QueryArgs& qa, uint32_t m, uint64_t s)
 {
     const uint64_t c = s / STEPS, r = s - c * STEPS;
-    unsigned long long x = qa.achunk[(uint64_t)m * (qa.a_chunks + 1) + c];
-    const unsigned long long* st = qa.astep + (uint64_t)m * qa.a_chunks * STEPS + c * STEPS;
-    for (uint64_t i = 0; i < r; ++i) x += st[i];
-    return x;
+    const unsigned long long x = qa.achunk[(uint64_t)m * (qa.a_chunks + 1) + c];
+    return r ? x + qa.astep[(uint64_t)m * qa.a_chunks * STEPS + s] : x;
 }
 
 // One thread per pixel: the bins of cells [lo_p, hi_p].  With s_p the step of
@@ -543,7 +542,7 @@ __device__ __forceinline__ void pixels_field(const UpdateArgs& a, const QueryArg
     a.y[k] = a.tf[m * a.T + tf_entry(mean, (float)a.T, a.T - 1)];
     if (m == 0) a.count[p] = count;
     if (qa.apart) {
-        const double as = (double)asum * (1.0 / 2147483648.0);           // one rounding to double
+        const double as = (double)asum * (1.0 / 536870912.0);            // 2^-29; one rounding to double
         a.asum[k] = as;
         a.amean[k] = __double2float_rn(__ddiv_rn(as, (double)count));
     }

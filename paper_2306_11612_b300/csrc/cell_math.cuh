@@ -169,11 +169,12 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr)
     return r;
 }
 
-// A cell's alpha in the fixed point of the alpha-mean sums: rint(alpha 2^31)
-// (alpha in [0, 1], so at most 2^31; the scaling is exact).  Every kernel
-// that adds alphas converts with this one function, so the sums are exact
-// integers and independent of the order of addition.
-constexpr float ALPHA_FX_ONE = 2147483648.0f;        // 2^31
+// A cell's alpha in the fixed point of the alpha-mean sums: rint(alpha 2^29)
+// (alpha in [0, 1], so at most 2^29 and the 4 cells of a lane fit in 32 bits;
+// the scaling is exact).  Every kernel that adds alphas converts with this one
+// function, so the sums are exact integers and independent of the order of
+// addition.
+constexpr float ALPHA_FX_ONE = 536870912.0f;         // 2^29
 __device__ __forceinline__ uint32_t alpha_fx(float A) { return __float2uint_rn(__fmul_rn(A, ALPHA_FX_ONE)); }
 
 // Per-cell constants in registers, specialised on the field count M and the
@@ -236,7 +237,7 @@ struct Cell {
     // width_p2, also adding each field's fixed-point alpha (alpha_fx of the
     // same entry, from a second table `aoff` bytes after the first) to ax[m]
     __device__ __forceinline__ uint32_t width_p2_alpha(const float* v, uint32_t L, const uint32_t* cm, uint32_t aoff,
-                                                       unsigned long long (&ax)[M]) const
+                                                       uint32_t (&ax)[M]) const
     {
         float al[M];
 #pragma unroll
@@ -253,7 +254,7 @@ struct Cell {
     // width from normalised values, also adding the fixed-point alphas
     // (s_ax: the u32 twin of the table s_tf)
     __device__ __forceinline__ uint32_t width_alpha(const float* t, uint32_t L, const float* s_tf,
-                                                    const uint32_t* s_ax, unsigned long long (&ax)[M]) const
+                                                    const uint32_t* s_ax, uint32_t (&ax)[M]) const
     {
         float al[M];
 #pragma unroll

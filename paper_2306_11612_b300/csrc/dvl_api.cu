@@ -1099,7 +1099,7 @@ int dvl_backward(dvl_ctx* c, const float* grad, int mem_in, float* grad_ctrl, in
     CK(cudaMemsetAsync(c->d_gtab, 0, (size_t)M * T * sizeof(double), c->stream), "clear adjoint");
     UpdateArgs a = make_args(c, c->last_prm);
     float* out = mem_out == DVL_MEM_DEVICE ? grad_ctrl : c->d_gout;
-    const size_t np = backward_gpart_elems(M, T, c->n);
+    const size_t np = backward_gpart_elems(M, T, c->n, c->W_last);
     if (np > c->gpart_cap) {
         CK(cudaStreamSynchronize(c->stream), "synchronize");
         CK(dalloc(c->d_gpart, np), "alloc adjoint");

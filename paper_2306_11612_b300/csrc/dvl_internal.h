@@ -167,11 +167,12 @@ struct UpdateArgs {
     double* asum;              // M x W alpha sums, or null (no alpha means)
     float* amean;              // M x W alpha means (when asum)
     // Alpha means in the same read of the cells as the widths: pass A adds the
-    // cells' alpha per field in fixed point, a_fx = rint(alpha 2^31), per warp
-    // step (astep: M x n_chunks * STEPS) and per chunk (achunk: M x (n_chunks
-    // + 1), turned into the exclusive prefix over chunks); apart holds the
-    // pixel boundaries' partial-step sums ((W + 1) x 2 x M).  Null: no alpha
-    // sums in pass A (the placement pass computes them, or none are asked for).
+    // cells' alpha per field in fixed point, a_fx = rint(alpha 2^29), per warp
+    // step (astep: M x n_chunks * STEPS, the exclusive prefix of the steps
+    // within their chunk) and per chunk (achunk: M x (n_chunks + 1), turned
+    // into the exclusive prefix over chunks by the chunk scan); apart holds
+    // the pixel boundaries' partial-step sums ((W + 1) x 2 x M).  Null: no
+    // alpha sums are asked for.
     unsigned long long* astep;
     unsigned long long* achunk;
     unsigned long long* apart;
@@ -247,7 +248,7 @@ cudaError_t launch_ctrl_table(cudaStream_t s, uint32_t M, uint32_t K, uint32_t T
 // adjoint (deterministic, no global atomics), or null for the atomic one.
 cudaError_t launch_backward(cudaStream_t s, const UpdateArgs& a, const float* g, double* gtab, uint32_t K,
                             float* grad_ctrl, double* gpart);
-size_t backward_gpart_elems(uint32_t M, uint32_t T, uint64_t n);   // 0: tables too large for it
+size_t backward_gpart_elems(uint32_t M, uint32_t T, uint64_t n, uint32_t W);   // 0: tables too large for it
 cudaError_t launch_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* q);
 
 // raster.cu: line-plot image of M x W bin values (lines: bit m per field,

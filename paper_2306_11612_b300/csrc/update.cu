@@ -92,13 +92,13 @@ template <int M, int PM, bool FULLSTEP, bool P2, bool AL = false>
 __device__ __forceinline__ unsigned long long widths4_of(const Cell<M, PM>& cc, const UpdateArgs& a,
                                                          const float* s_tf, const uint32_t* cm, uint64_t idx,
                                                          const float (&v)[4][M], uint32_t L4, uint32_t aoff = 0,
-                                                         unsigned long long* ax = nullptr)
+                                                         uint32_t* ax = nullptr)
 {
     unsigned long long acc = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         uint32_t q;
-        unsigned long long axj[M];
+        uint32_t axj[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) axj[m] = 0;
         if (P2) {
@@ -126,7 +126,7 @@ __device__ __forceinline__ unsigned long long widths4_of(const Cell<M, PM>& cc, 
 template <int M, int PM, bool FULLSTEP, bool P2, bool AL = false>
 __device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, const UpdateArgs& a,
                                                       const float* s_tf, const uint32_t* cm, uint64_t idx,
-                                                      uint32_t aoff = 0, unsigned long long* ax = nullptr)
+                                                      uint32_t aoff = 0, uint32_t* ax = nullptr)
 {
     float v[4][M];
     uint32_t L4;
@@ -368,10 +368,10 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
         unsigned long long amine[M];                    // this lane's step: alpha sums per field
 #pragma unroll
         for (int m = 0; m < M; ++m) amine[m] = 0;
-        auto alpha_step = [&](unsigned long long (&ax)[M], int st) {
+        auto alpha_step = [&](uint32_t (&ax)[M], int st) {
 #pragma unroll
             for (int m = 0; m < M; ++m) {
-                const unsigned long long t = warp_total_small(ax[m]);     // <= 128 x 2^31
+                const unsigned long long t = warp_total_small(ax[m]);     // <= 128 x 2^29
                 if (AL && lane == st) amine[m] = t;
             }
         };
@@ -395,7 +395,7 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
                     else if (nxt_full)
                         ring_issue<M>(lane, ring_s + k * SLOT, bar_s + 8u * k, a, nxt * CHUNK + (s2 - STEPS) * STEP);
                 }
-                unsigned long long ax[M];
+                uint32_t ax[M];
 #pragma unroll
                 for (int m = 0; m < M; ++m) ax[m] = 0;
                 const unsigned long long l =
@@ -418,7 +418,7 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
             }
             for (int st = 0; st < STEPS; ++st) {
                 const uint64_t idx = base + st * STEP + lane * 4;
-                unsigned long long ax[M];
+                uint32_t ax[M];
 #pragma unroll
                 for (int m = 0; m < M; ++m) ax[m] = 0;
                 const unsigned long long l =
@@ -432,12 +432,14 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
         if (a.step_sums && lane < STEPS) a.step_sums[chunk * STEPS + lane] = mine;
         if (lane == 0) a.chunk_prefix[chunk] = acc;
         if (AL) {
+            // per field: the steps' alpha sums as an exclusive prefix within
+            // the chunk, and the chunk total
 #pragma unroll
             for (int m = 0; m < M; ++m) {
                 const unsigned long long am = lane < STEPS ? amine[m] : 0ull;
-                if (lane < STEPS) a.astep[(uint64_t)m * n_steps_all + chunk * STEPS + lane] = am;
-                const unsigned long long ct = warp_sum_u64(am);            // chunk total
-                if (lane == 0) a.achunk[(uint64_t)m * (n_chunks + 1) + chunk] = ct;
+                const unsigned long long incl = warp_incl_scan_u64(am, lane);
+                if (lane < STEPS) a.astep[(uint64_t)m * n_steps_all + chunk * STEPS + lane] = incl - am;
+                if (lane == STEPS - 1) a.achunk[(uint64_t)m * (n_chunks + 1) + chunk] = incl;
             }
         }
         chunk = nxt;
@@ -788,7 +790,7 @@ __device__ __noinline__ void back_crossing_step(const UpdateArgs& a, const float
 template <int M, int PM>
 __device__ __noinline__ void back_crossing_step_hist(const UpdateArgs& a, const float* s_tf, const PixelMap& pm,
                                                      uint64_t idx, unsigned long long s_start, int lane,
-                                                     const float* g, double* sG, uint32_t* h)
+                                                     const double* wtab, double* sG, uint32_t* h)
 {
     Cell<M, PM> cc;
     cc.load(a.consts, a.T);
@@ -827,11 +829,9 @@ __device__ __noinline__ void back_crossing_step_hist(const UpdateArgs& a, const 
                 phi = max(phi, b1);
             } else {
                 for (uint32_t p = b1; p <= b2; ++p) {
-                    const uint32_t c = a.count[p];
-                    if (!c) continue;
+                    if (!a.count[p]) continue;
 #pragma unroll
-                    for (int m = 0; m < M; ++m)
-                        atomicAdd(&sG[m * T1 + e[j][m]], (double)g[(uint64_t)m * a.W + p] / (double)c);
+                    for (int m = 0; m < M; ++m) atomicAdd(&sG[m * T1 + e[j][m]], wtab[(uint64_t)m * a.W + p]);
                 }
             }
             E = I;
@@ -844,11 +844,9 @@ __device__ __noinline__ void back_crossing_step_hist(const UpdateArgs& a, const 
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (!single[j]) continue;
-            const uint32_t c = a.count[pix[j]];
-            if (!c) continue;
+            if (!a.count[pix[j]]) continue;
 #pragma unroll
-            for (int m = 0; m < M; ++m)
-                atomicAdd(&sG[m * T1 + e[j][m]], (double)g[(uint64_t)m * a.W + pix[j]] / (double)c);
+            for (int m = 0; m < M; ++m) atomicAdd(&sG[m * T1 + e[j][m]], wtab[(uint64_t)m * a.W + pix[j]]);
         }
         return;
     }
@@ -860,10 +858,9 @@ __device__ __noinline__ void back_crossing_step_hist(const UpdateArgs& a, const 
                 for (int m = 0; m < M; ++m) atomicAdd(&h[m * T1 + e[j][m]], 1u);
             }
         __syncwarp();
-        const uint32_t c = a.count[p];
         double wc[M];
 #pragma unroll
-        for (int m = 0; m < M; ++m) wc[m] = c ? (double)g[(uint64_t)m * a.W + p] / (double)c : 0.0;
+        for (int m = 0; m < M; ++m) wc[m] = wtab[(uint64_t)m * a.W + p];
         for (int i = lane; i < MT1; i += 32) {
             const uint32_t n = h[i];
             if (n) {
@@ -964,30 +961,48 @@ __global__ __launch_bounds__(WARPS * 32) void k_backward(UpdateArgs a, const flo
     }
 }
 
+constexpr uint32_t GTAB_SEGS = 4;                 // row segments of the first reduction level
+
+// The per-pixel weights of the adjoint, wtab[m][p] = g[m][p] / count[p] in
+// float64 (0 for an empty pixel), once per call instead of once per use.
+__global__ void k_backward_weights(uint32_t M, uint32_t W, const float* __restrict__ g,
+                                   const uint32_t* __restrict__ count, double* __restrict__ wtab)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * W) return;
+    const uint32_t c = count[i % W];
+    wtab[i] = c ? (double)g[i] / (double)c : 0.0;
+}
+
 // Adjoint with per-warp entry histograms, in a persistent grid whose warps
 // claim chunks from a counter.  Inside a warp step that stays in one pixel p
-// every cell carries the same weight g[m][p] / count[p], so the step only
-// counts how often each TF entry occurs, in the warp's own u32 histogram in
-// shared memory: a lane adds each run of equal entries among its 4
-// consecutive cells with one atomic (cells close in curve order mostly share
-// an entry, so fewer lanes hit the same counter at once; the run ends are
-// predicates, not branches).  When the warp's pixel changes, or its chunk
-// ends, the counts are scaled by the pixel's weights into the CTA's float64
-// table.  Steps that cross a pixel boundary place their cells exactly
+// every cell carries the same weight wtab[m][p] = g[m][p] / count[p], so the
+// step only counts how often each TF entry occurs, in the warp's own u32
+// histogram in shared memory: a lane adds each run of equal entries among its
+// 4 consecutive cells with one atomic (cells close in curve order mostly
+// share an entry, so fewer lanes hit the same counter at once; the run ends
+// are predicates, not branches).  When the warp's pixel changes, or its chunk
+// ends, the nonzero counts are packed 32 at a time through a per-warp queue
+// in shared memory and scaled by the pixel's weights into the CTA's float64
+// table (float64 instructions are slow on this part, so they run on full
+// warps only).  Steps that cross a pixel boundary place their cells exactly
 // (back_crossing_step_hist).  The next single-pixel step's cells are loaded
 // while the current one is counted.  Each CTA writes its table to
 // gpart[blockIdx] without atomics; k_gtab_reduce sums the CTAs in a fixed
 // order.  counters[2] is the chunk counter (zeroed by the launcher).
+constexpr int BQ = 64;                               // per-warp queue slots of the flush
 template <int M, int PM>
-__global__ __launch_bounds__(WARPS * 32, 3) void k_backward_hist(UpdateArgs a, const float* g, double* gpart)
+__global__ __launch_bounds__(WARPS * 32, 3) void k_backward_hist(UpdateArgs a, const double* wtab, double* gpart)
 {
-    extern __shared__ float s_tf[];                    // table | float64 sums | WARPS u32 histograms
+    extern __shared__ float s_tf[];   // table | float64 sums | WARPS u32 histograms | WARPS flush queues
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T1 = (int)a.T + 1, MT1 = M * T1;
     load_table<M>(s_tf, a.tf, a.T);
     double* sG = reinterpret_cast<double*>(s_tf + ((MT1 + 1) & ~1));
     uint32_t* hist = reinterpret_cast<uint32_t*>(sG + MT1);
     uint32_t* h = hist + warp * MT1;
+    uint32_t* qi = hist + WARPS * MT1 + warp * 2 * BQ;   // queued entry index
+    uint32_t* qc = qi + BQ;                              // and its count
     for (int i = tid; i < MT1; i += blockDim.x) sG[i] = 0.0;
     for (int i = tid; i < WARPS * MT1; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
@@ -996,25 +1011,52 @@ __global__ __launch_bounds__(WARPS * 32, 3) void k_backward_hist(UpdateArgs a, c
     const PixelMap pm{C->F_div_W, C->F_mod_W, C->F, a.W};
     const float Tf = (float)a.T;
     const uint64_t n_chunks = (a.n + CHUNK - 1) / CHUNK;
+    const unsigned lt = (1u << lane) - 1u;
     uint32_t cur = 0xFFFFFFFFu;
     double wc[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) wc[m] = 0.0;
+    // scales queue slots [0, k) (k <= 32) by their field's weight into sG
+    auto drain = [&](uint32_t k) {
+        if ((uint32_t)lane < k) {
+            const uint32_t i = qi[lane];
+            const int m = (int)(i / (uint32_t)T1);
+            double w = 0.0;
+#pragma unroll
+            for (int mm = 0; mm < M; ++mm)
+                if (mm == m) w = wc[mm];
+            atomicAdd(&sG[i], w * (double)qc[lane]);
+        }
+    };
     auto flush = [&]() {
         if (cur == 0xFFFFFFFFu) return;                            // warp-uniform
         __syncwarp();
-        for (int i = lane; i < MT1; i += 32) {
-            const uint32_t c = h[i];
+        uint32_t fill = 0;
+        for (int base = 0; base < MT1; base += 32) {
+            const int i = base + lane;
+            const uint32_t c = i < MT1 ? h[i] : 0u;
+            const unsigned nz = __ballot_sync(FULL, c != 0u);
             if (c) {
                 h[i] = 0u;
-                const int m = i / T1;
-                double w = 0.0;
-#pragma unroll
-                for (int mm = 0; mm < M; ++mm)
-                    if (mm == m) w = wc[mm];
-                atomicAdd(&sG[i], w * (double)c);
+                const uint32_t pos = fill + __popc(nz & lt);
+                qi[pos] = (uint32_t)i;
+                qc[pos] = c;
+            }
+            fill += __popc(nz);
+            if (fill >= 32) {
+                __syncwarp();
+                drain(32);
+                __syncwarp();
+                if ((uint32_t)lane + 32 < fill) {
+                    qi[lane] = qi[lane + 32];
+                    qc[lane] = qc[lane + 32];
+                }
+                fill -= 32;
+                __syncwarp();
             }
         }
+        __syncwarp();
+        drain(fill);
         __syncwarp();
     };
     auto claim = [&]() {
@@ -1061,9 +1103,8 @@ __global__ __launch_bounds__(WARPS * 32, 3) void k_backward_hist(UpdateArgs a, c
             if (p != cur) {                                            // warp-uniform
                 flush();
                 cur = p;
-                const uint32_t c = a.count[p];
 #pragma unroll
-                for (int m = 0; m < M; ++m) wc[m] = c ? (double)g[(uint64_t)m * a.W + p] / (double)c : 0.0;
+                for (int m = 0; m < M; ++m) wc[m] = wtab[(uint64_t)m * a.W + p];
             }
 #pragma unroll
             for (int m = 0; m < M; ++m) {
@@ -1091,7 +1132,7 @@ __global__ __launch_bounds__(WARPS * 32, 3) void k_backward_hist(UpdateArgs a, c
             const int k = __ffs(m2) - 1;
             m2 &= m2 - 1;
             back_crossing_step_hist<M, PM>(a, s_tf, pm, base + k * STEP + lane * 4, __shfl_sync(FULL, s_start, k),
-                                           lane, g, sG, h);
+                                           lane, wtab, sG, h);
         }
         cur = 0xFFFFFFFFu;                               // next chunk: weights reloaded
     }
@@ -1128,7 +1169,7 @@ __global__ __launch_bounds__(256) void k_gtab_reduce(uint32_t MT1, uint64_t rows
 // partial rows (entry T, t = 1, folds into entry T-1), write gtab for the
 // entries whose lower control point is k, and add weight x gradient in a
 // fixed order: dL/dctrl[m][k] = sum_e gtab[m][e] w_k(e).
-__global__ __launch_bounds__(256) void k_grad_final(uint32_t M, uint32_t K, uint32_t T, uint32_t segs,
+__global__ __launch_bounds__(256) void k_grad_final(uint32_t M, uint32_t K, uint32_t T,
                                                     const double* __restrict__ part2, double* __restrict__ gtab,
                                                     float* __restrict__ grad)
 {
@@ -1141,10 +1182,13 @@ __global__ __launch_bounds__(256) void k_grad_final(uint32_t M, uint32_t K, uint
     double acc = 0.0;
     for (uint32_t e = e0 + lane; e <= e1; e += 32) {
         const uint32_t col = m * T1 + e;
+        const uint32_t span = e == T - 1 ? 2u : 1u;               // entry T (t = 1) folds into T-1
         double G = 0.0;
-        for (uint32_t y = 0; y < segs; ++y) {
-            G += part2[(uint64_t)y * M * T1 + col];
-            if (e == T - 1) G += part2[(uint64_t)y * M * T1 + col + 1];
+#pragma unroll
+        for (uint32_t y = 0; y < GTAB_SEGS; ++y) {
+            const double* row = part2 + (uint64_t)y * M * T1 + col;
+            G += row[0];
+            if (span == 2u) G += row[1];
         }
         const double x = (double)e * (double)(K - 1) / (double)(T - 1);
         uint32_t k0 = (uint32_t)floor(x);
@@ -1338,12 +1382,11 @@ cudaError_t run_update(cudaStream_t s, const UpdateArgs& a)
     return cudaGetLastError();
 }
 
-constexpr uint32_t GTAB_SEGS = 64;                // row segments of the first reduction level
-
 size_t backward_hist_smem(uint32_t M, uint32_t T)
 {
     const size_t MT1 = (size_t)M * (T + 1);
-    return ((MT1 + 1) & ~(size_t)1) * sizeof(float) + MT1 * sizeof(double) + WARPS * MT1 * sizeof(uint32_t);
+    return ((MT1 + 1) & ~(size_t)1) * sizeof(float) + MT1 * sizeof(double) + WARPS * MT1 * sizeof(uint32_t) +
+           (size_t)WARPS * 2 * BQ * sizeof(uint32_t);
 }
 
 template <int M, int PM>
@@ -1360,9 +1403,11 @@ cudaError_t run_backward_pm(cudaStream_t s, const UpdateArgs& a, const float* g,
         if ((e = resident_ctas(k_backward_hist<M, PM>, smem, &grid)) != cudaSuccess) return e;
         if ((uint32_t)grid > n_tiles) grid = (int)n_tiles;
         if ((e = cudaMemsetAsync(a.counters + 2, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-        k_backward_hist<M, PM><<<grid, WARPS * 32, smem, s>>>(a, g, gpart);
         const uint32_t MT1 = M * (a.T + 1);
         double* part2 = gpart + (uint64_t)n_tiles * MT1;
+        double* wtab = part2 + (uint64_t)GTAB_SEGS * MT1;             // M x W pixel weights
+        k_backward_weights<<<(M * a.W + 255) / 256, 256, 0, s>>>(M, a.W, g, a.count, wtab);
+        k_backward_hist<M, PM><<<grid, WARPS * 32, smem, s>>>(a, wtab, gpart);
         k_gtab_reduce<<<dim3((MT1 + 31) / 32, GTAB_SEGS), 256, 0, s>>>(MT1, (uint64_t)grid, gpart, part2);
         return cudaGetLastError();
     }
@@ -1386,7 +1431,7 @@ cudaError_t run_backward(cudaStream_t s, const UpdateArgs& a, const float* g, do
     if (gpart && a.n) {
         const uint32_t n_tiles = (uint32_t)((a.n + TILE - 1) / TILE);
         const double* part2 = gpart + (uint64_t)n_tiles * M * (a.T + 1);
-        k_grad_final<<<(unsigned)((M * K + 7) / 8), 256, 0, s>>>(M, K, a.T, GTAB_SEGS, part2, gtab, grad_ctrl);
+        k_grad_final<<<(unsigned)((M * K + 7) / 8), 256, 0, s>>>(M, K, a.T, part2, gtab, grad_ctrl);
     } else {
         k_grad_ctrl<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(M, K, a.T, gtab, grad_ctrl);
     }
@@ -1420,11 +1465,11 @@ cudaError_t launch_backward(cudaStream_t s, const UpdateArgs& a, const float* g,
     DVL_DISPATCH_M(run_backward, s, a, g, gtab, K, grad_ctrl, gpart)
 }
 
-size_t backward_gpart_elems(uint32_t M, uint32_t T, uint64_t n)
+size_t backward_gpart_elems(uint32_t M, uint32_t T, uint64_t n, uint32_t W)
 {
     if (backward_hist_smem(M, T) > 200 * 1024) return 0;      // tables too large: atomic adjoint
     const uint64_t n_tiles = (n + TILE - 1) / TILE;
-    return (size_t)(n_tiles + GTAB_SEGS) * M * (T + 1);
+    return (size_t)(n_tiles + GTAB_SEGS) * M * (T + 1) + (size_t)M * W;   // CTA rows, segments, weights
 }
 
 cudaError_t launch_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* q)
