@@ -59,7 +59,7 @@ __global__ void k_prepare_batch(UpdateArgs a, BatchArgs b)
 // power of two is exact, so rint(max(max(V/maxV, m_b) 2^L, m_a) 2^Q) equals
 // rint(max(max(V (2^Q/maxV), m_b 2^Q) 2^L, m_a 2^Q)) bit for bit.
 template <int M, int PM, int G, int ST>
-__global__ __launch_bounds__(WARPS * 32, M <= 4 ? (G >= 16 ? 2 : 3) : 1) void k_passA_batch(UpdateArgs a, BatchArgs b)
+__device__ __forceinline__ void passA_batch_body(const UpdateArgs& a, const BatchArgs& b)
 {
     extern __shared__ float4 s_dyn[];                  // G x 1 params, then G x M x T1 tables
     __shared__ unsigned long long s_ct[WARPS][G];      // chunk totals per warp and TF
@@ -163,8 +163,12 @@ __global__ __launch_bounds__(WARPS * 32, M <= 4 ? (G >= 16 ? 2 : 3) : 1) void k_
             // present (every step but the data set's last) needs no masks.
             // TFs are evaluated 4 at a time (one 128-bit table load per field).
             unsigned long long mine = 0;
-            auto one_quad = [&](int kq, auto full_tag) {
+            // NQ: TFs of the quad to evaluate (4, or 0 = the group's last,
+            // partial quad: gk - 4 kq of them, in a loop that is not unrolled)
+            auto one_quad = [&](int kq, auto full_tag, auto nq_tag) {
                 constexpr bool ALL = decltype(full_tag)::value;     // every cell present
+                constexpr int NQ = decltype(nq_tag)::value;
+                const int nq = NQ ? NQ : (int)gk - kq * 4;
                 float4 pr[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) pr[i] = s_par[kq * 4 + i];
@@ -176,6 +180,7 @@ __global__ __launch_bounds__(WARPS * 32, M <= 4 ? (G >= 16 ? 2 : 3) : 1) void k_
                     for (int m = 0; m < M; ++m) a4[m] = lds_f32x4(off[j][m] + (uint32_t)kq * 16u);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
+                        if (!NQ && i >= nq) break;                     // block-uniform
                         float al[M];
 #pragma unroll
                         for (int m = 0; m < M; ++m) al[m] = i == 0 ? a4[m].x : i == 1 ? a4[m].y : i == 2 ? a4[m].z : a4[m].w;
@@ -196,19 +201,24 @@ __global__ __launch_bounds__(WARPS * 32, M <= 4 ? (G >= 16 ? 2 : 3) : 1) void k_
                 }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
+                    if (!NQ && i >= nq) break;
                     const unsigned long long tot = warp_total_small(l[i]);
                     mine = lane == kq * 4 + i ? tot : mine;
                 }
             };
+            using full4 = std::integral_constant<int, 4>;
+            using part = std::integral_constant<int, 0>;
+            const int full_quads = (int)gk / 4;
             if (base + (uint64_t)(st + 1) * STEP <= a.n) {             // warp-uniform
 #pragma unroll
                 for (int kq = 0; kq < G / 4; ++kq) {
-                    if (kq * 4 >= (int)gk) break;                      // block-uniform
-                    one_quad(kq, std::true_type{});
+                    if (kq >= full_quads) break;                       // block-uniform
+                    one_quad(kq, std::true_type{}, full4{});
                 }
+                if ((int)gk % 4) one_quad(full_quads, std::true_type{}, part{});
             } else {                                                   // the data set's last step:
 #pragma unroll 1                                                       // not unrolled (compile time)
-                for (int kq = 0; kq * 4 < (int)gk; ++kq) one_quad(kq, std::false_type{});
+                for (int kq = 0; kq * 4 < (int)gk; ++kq) one_quad(kq, std::false_type{}, part{});
             }
             if (lane < (int)gk) {
                 b.step_sums[((uint64_t)(g0 + lane) * b.n_chunks + chunk) * STEPS + st] = mine;
@@ -268,6 +278,28 @@ __global__ __launch_bounds__(WARPS * 32, M <= 4 ? (G >= 16 ? 2 : 3) : 1) void k_
     }
 }
 
+// The kernel: groups of 16 TFs take 128 registers (2 CTAs per SM fill the
+// register file); smaller groups are capped at 112 registers so that, at 2
+// CTAs per SM, an eighth of the register file stays free for other streams'
+// kernels (the serving loop runs data sets side by side, mostly with small
+// batches).
+template <int M, int PM, int G, int ST>
+__global__ __launch_bounds__(WARPS * 32, 2) void k_passA_batch16(UpdateArgs a, BatchArgs b)
+{
+    passA_batch_body<M, PM, G, ST>(a, b);
+}
+template <int M, int PM, int G, int ST>
+__global__ __maxnreg__(112) void k_passA_batch8(UpdateArgs a, BatchArgs b)
+{
+    passA_batch_body<M, PM, G, ST>(a, b);
+}
+template <int M, int PM, int G, int ST>
+constexpr auto passA_batch_kernel()
+{
+    if constexpr (G >= 16) return k_passA_batch16<M, PM, G, ST>;
+    else return k_passA_batch8<M, PM, G, ST>;
+}
+
 }  // namespace
 
 cudaError_t launch_prepare_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
@@ -289,12 +321,13 @@ cudaError_t run_passA_batch_gs(cudaStream_t s, const UpdateArgs& a, const BatchA
 {
     const size_t smem = passA_batch_smem(M, a.T, G);
     static std::atomic<size_t> set_bytes[MAX_DEVICES];
-    cudaError_t e = smem_attr_once(k_passA_batch<M, PM, G, ST>, smem, set_bytes);
+    constexpr auto kernel = passA_batch_kernel<M, PM, G, ST>();
+    cudaError_t e = smem_attr_once(kernel, smem, set_bytes);
     if (e != cudaSuccess) return e;
     const uint64_t work = b.n_tiles * ((b.K + G - 1) / G);    // (group, tile) tickets
     uint64_t grid = (uint64_t)b.sm_count * b.resid;
     if (grid > work) grid = work;
-    if (grid) k_passA_batch<M, PM, G, ST><<<(unsigned)grid, WARPS * 32, smem, s>>>(a, b);
+    if (grid) kernel<<<(unsigned)grid, WARPS * 32, smem, s>>>(a, b);
     return cudaGetLastError();
 }
 
@@ -333,9 +366,10 @@ cudaError_t occupancy_passA_batch_gs(const UpdateArgs& a, int* blocks)
     const size_t smem = passA_batch_smem(M, a.T, G);
     *blocks = 0;
     if (smem + sizeof(unsigned long long) * WARPS * G + 16 > 227 * 1024) return cudaSuccess;
-    cudaError_t e = smem_attr(k_passA_batch<M, PM, G, ST>, smem);
+    constexpr auto kernel = passA_batch_kernel<M, PM, G, ST>();
+    cudaError_t e = smem_attr(kernel, smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_passA_batch<M, PM, G, ST>, WARPS * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, WARPS * 32, smem);
 }
 
 template <int M, int PM, int G>

@@ -117,6 +117,7 @@ struct dvl_ctx {
     ulonglong2* d_bpsum = nullptr;
     float2* d_bpmm = nullptr;
     unsigned long long* d_bstamps = nullptr;   // 2 words: device clock at batch start / end
+    std::vector<float> b_dom_dev;               // the domains last uploaded to d_bdom
     size_t btf_cap = 0, bk_cap = 0, pairs_cap = 0, bbin_cap = 0, bcnt_cap = 0, bhs_cap = 0;
     std::vector<PairDesc> b_pairs;        // of the last batch
     bool have_batch = false;
@@ -193,6 +194,8 @@ void free_batch(dvl_ctx* c)
     dfree(c->d_bsteps); dfree(c->d_pairs); dfree(c->d_bsum); dfree(c->d_bvmin); dfree(c->d_bvmax);
     dfree(c->d_bcount); dfree(c->d_bmean); dfree(c->d_by); dfree(c->d_bH); dfree(c->d_bS);
     dfree(c->d_bpsum); dfree(c->d_bpmm); dfree(c->d_bstamps);
+    c->b_dom_dev.clear();
+    c->b_pairs.clear();
     c->btf_cap = c->bk_cap = c->pairs_cap = c->bbin_cap = c->bcnt_cap = c->bhs_cap = 0;
     for (auto& kv : c->b_graphs) cudaGraphExecDestroy(kv.second.first);
     c->b_graphs.clear();
@@ -1337,10 +1340,20 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
         }
     }
     CK(cudaMemcpyAsync(c->d_btf, alphas, nTF * sizeof(float), kind_in(mem_kind), c->stream), "copy batch TFs");
-    CK(cudaMemcpyAsync(c->d_bdom, dom.data(), 2 * M * sizeof(float), cudaMemcpyHostToDevice, c->stream),
-       "copy batch domain");
-    CK(cudaMemcpyAsync(c->d_pairs, pairs.data(), n_pairs * sizeof(PairDesc), cudaMemcpyHostToDevice, c->stream),
-       "copy batch pairs");
+    // the domains and pair descriptors come from pageable host memory (a copy
+    // that may wait on the stream): uploaded only when they changed or the
+    // device buffers were reallocated
+    if (need_grow || dom.size() != c->b_dom_dev.size() ||
+        std::memcmp(dom.data(), c->b_dom_dev.data(), dom.size() * sizeof(float)) != 0) {   // bits: NaN = default
+        CK(cudaMemcpyAsync(c->d_bdom, dom.data(), 2 * M * sizeof(float), cudaMemcpyHostToDevice, c->stream),
+           "copy batch domain");
+        c->b_dom_dev = dom;
+    }
+    const bool same_pairs = !need_grow && pairs.size() == c->b_pairs.size() &&
+                            std::memcmp(pairs.data(), c->b_pairs.data(), pairs.size() * sizeof(PairDesc)) == 0;
+    if (!same_pairs)
+        CK(cudaMemcpyAsync(c->d_pairs, pairs.data(), n_pairs * sizeof(PairDesc), cudaMemcpyHostToDevice, c->stream),
+           "copy batch pairs");
     c->b_pairs = pairs;
 
     UpdateArgs a = make_args(c, prm);
