@@ -46,8 +46,8 @@ __global__ void k_prepare_batch(UpdateArgs a, BatchArgs b)
 // from one counter, group by group; a CTA loads a group's tables when its
 // ticket moves to a new group (once or twice per CTA).  Every warp step's
 // cells are loaded and normalised once per group and evaluated for all G TFs;
-// per TF it writes step totals and, per tile, runs its own decoupled
-// look-back scan.  G is a compile-time constant so the TF loop unrolls; per
+// per TF it writes step and chunk totals (no wait on other warps or tiles:
+// k_chunk_scan_batch scans the chunk totals afterwards).  G is a compile-time constant so the TF loop unrolls; per
 // cell the table offsets (all fields) and the level factor 2^(L w) are
 // computed once and reused by every TF of the group.  A cell's entry of a
 // field is the same for every TF of the batch (one TF domain), so the group's
@@ -62,7 +62,6 @@ template <int M, int PM, int G, int ST>
 __device__ __forceinline__ void passA_batch_body(const UpdateArgs& a, const BatchArgs& b)
 {
     extern __shared__ float4 s_dyn[];                  // G x 1 params, then G x M x T1 tables
-    __shared__ unsigned long long s_ct[WARPS][G];      // chunk totals per warp and TF
     __shared__ uint32_t s_tile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // table stride per field: ST (a compile-time constant >= T + 1, so that
@@ -225,56 +224,10 @@ __device__ __forceinline__ void passA_batch_body(const UpdateArgs& a, const Batc
                 ct += mine;
             }
         }
-        if (lane < G) s_ct[warp][lane] = ct;
-        __syncthreads();
-        // one look-back per TF of the group; the warps take the TFs in turn
-        for (uint32_t kk = warp; kk < gk; kk += WARPS) {
-            const uint32_t k = g0 + kk;
-            unsigned long long w = lane < WARPS ? s_ct[lane][kk] : 0ull;
-            unsigned long long incl = warp_incl_scan_u64(w, lane);
-            const unsigned long long agg = __shfl_sync(FULL, incl, WARPS - 1);
-            unsigned long long* status = b.tile_status + (uint64_t)k * b.n_tiles;
-            if (lane == 0) st_relaxed(status + tile, (tile == 0 ? FLAG_P : FLAG_A) | agg);
-            unsigned long long excl = 0;
-            if (tile > 0) {
-                int64_t end = (int64_t)tile - 1;
-                while (true) {
-                    const int64_t jt = end - lane;
-                    unsigned long long sv = FLAG_P;
-                    if (jt >= 0) {
-                        long long spins = 0;
-                        while (true) {
-                            sv = ld_relaxed(status + jt);
-                            if (sv >> 62) break;
-                            if (++spins > a.spin_limit) {
-                                atomicOr(a.err, ERR_TIMEOUT);
-                                sv = FLAG_P;
-                                break;
-                            }
-                            __nanosleep(100);
-                        }
-                    }
-                    const unsigned pmask = __ballot_sync(FULL, (sv & FLAG_P) != 0);
-                    const int first = pmask ? __ffs(pmask) - 1 : 31;
-                    excl += warp_sum_u64(lane <= first ? (sv & VAL_MASK) : 0ull);
-                    if (pmask) break;
-                    end -= 32;
-                }
-                if (lane == 0) st_relaxed(status + tile, FLAG_P | (excl + agg));
-            }
-            if (lane < WARPS) b.chunk_prefix[(uint64_t)k * b.n_chunks + (uint64_t)tile * WARPS + lane] = excl + incl - w;
-            if (lane == 0 && tile == b.n_tiles - 1) {
-                UpdateConsts* Ck = b.consts + k;
-                unsigned long long F = excl + agg;
-                int linear = 0;
-                if (F == 0 && a.n > 0) { F = a.n; linear = 1; }
-                Ck->F = F;
-                Ck->linear = linear;
-                Ck->F_div_W = 0;
-                Ck->F_mod_W = 0;
-            }
-        }
-        __syncthreads();                               // s_ct and s_tile are reused
+        // the warp's chunk total of each TF of the group (lane kk: TF g0 + kk);
+        // k_chunk_scan_batch turns them into prefixes
+        if (lane < (int)gk) b.chunk_prefix[(uint64_t)(g0 + lane) * b.n_chunks + chunk] = ct;
+        __syncthreads();                               // s_tile is reused
     }
 }
 
@@ -298,6 +251,92 @@ constexpr auto passA_batch_kernel()
 {
     if constexpr (G >= 16) return k_passA_batch16<M, PM, G, ST>;
     else return k_passA_batch8<M, PM, G, ST>;
+}
+
+// The chunk totals of TF blockIdx.y become exclusive prefixes: blocks of
+// BSCAN_SPAN chunks taken by tickets (tickets[1 + k]), each scanned in the
+// block, published, and looked back over the earlier blocks' (decoupled
+// look-back with bounded waits; status words of TF k at tile_status + k *
+// n_tiles).  The last block writes the TF's F (Eq. 4's total) and the
+// all-zero fallback.
+constexpr int BSCAN_THREADS = 256, BSCAN_PER_THREAD = 8, BSCAN_SPAN = BSCAN_THREADS * BSCAN_PER_THREAD;
+
+__global__ __launch_bounds__(BSCAN_THREADS) void k_chunk_scan_batch(UpdateArgs a, BatchArgs b)
+{
+    __shared__ unsigned long long s_warp[BSCAN_THREADS / 32];
+    __shared__ unsigned long long s_excl;
+    __shared__ uint32_t s_b;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t k = blockIdx.y;
+    if (tid == 0) s_b = atomicAdd(&b.tickets[1 + k], 1u);
+    __syncthreads();
+    const uint32_t blk = s_b;
+    unsigned long long* row = b.chunk_prefix + (uint64_t)k * b.n_chunks;
+    unsigned long long* status = b.tile_status + (uint64_t)k * b.n_tiles;
+    const uint64_t c0 = (uint64_t)blk * BSCAN_SPAN + (uint64_t)tid * BSCAN_PER_THREAD;
+    unsigned long long v[BSCAN_PER_THREAD], t = 0;
+#pragma unroll
+    for (int j = 0; j < BSCAN_PER_THREAD; ++j) {
+        v[j] = c0 + j < b.n_chunks ? row[c0 + j] : 0ull;
+        t += v[j];
+    }
+    const unsigned long long incl = warp_incl_scan_u64(t, lane);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    unsigned long long wpre = 0, agg = 0;
+#pragma unroll
+    for (int w = 0; w < BSCAN_THREADS / 32; ++w) {
+        if (w < warp) wpre += s_warp[w];
+        agg += s_warp[w];
+    }
+    if (warp == 0) {
+        if (lane == 0) st_relaxed(status + blk, (blk == 0 ? FLAG_P : FLAG_A) | agg);
+        unsigned long long excl = 0;
+        if (blk > 0) {
+            int64_t end = (int64_t)blk - 1;
+            while (true) {
+                const int64_t jt = end - lane;
+                unsigned long long sv = FLAG_P;
+                if (jt >= 0) {
+                    long long spins = 0;
+                    while (true) {
+                        sv = ld_relaxed(status + jt);
+                        if (sv >> 62) break;
+                        if (++spins > a.spin_limit) {
+                            atomicOr(a.err, ERR_TIMEOUT);
+                            sv = FLAG_P;
+                            break;
+                        }
+                        __nanosleep(100);
+                    }
+                }
+                const unsigned pmask = __ballot_sync(FULL, (sv & FLAG_P) != 0);
+                const int first = pmask ? __ffs(pmask) - 1 : 31;
+                excl += warp_sum_u64(lane <= first ? (sv & VAL_MASK) : 0ull);
+                if (pmask) break;
+                end -= 32;
+            }
+            if (lane == 0) st_relaxed(status + blk, FLAG_P | (excl + agg));
+        }
+        if (lane == 0) s_excl = excl;
+    }
+    __syncthreads();
+    unsigned long long run = s_excl + wpre + incl - t;
+#pragma unroll
+    for (int j = 0; j < BSCAN_PER_THREAD; ++j) {
+        if (c0 + j < b.n_chunks) row[c0 + j] = run;
+        run += v[j];
+    }
+    if (blk == gridDim.x - 1 && tid == 0) {
+        UpdateConsts* Ck = b.consts + k;
+        unsigned long long F = s_excl + agg;
+        int linear = 0;
+        if (F == 0 && a.n > 0) { F = a.n; linear = 1; }   // all widths 0: equal widths
+        Ck->F = F;
+        Ck->linear = linear;
+        Ck->F_div_W = 0;
+        Ck->F_mod_W = 0;
+    }
 }
 
 }  // namespace
@@ -327,7 +366,11 @@ cudaError_t run_passA_batch_gs(cudaStream_t s, const UpdateArgs& a, const BatchA
     const uint64_t work = b.n_tiles * ((b.K + G - 1) / G);    // (group, tile) tickets
     uint64_t grid = (uint64_t)b.sm_count * b.resid;
     if (grid > work) grid = work;
-    if (grid) kernel<<<(unsigned)grid, WARPS * 32, smem, s>>>(a, b);
+    if (grid) {
+        kernel<<<(unsigned)grid, WARPS * 32, smem, s>>>(a, b);
+        const uint32_t blocks = (uint32_t)((b.n_chunks + BSCAN_SPAN - 1) / BSCAN_SPAN);
+        k_chunk_scan_batch<<<dim3(blocks, b.K), BSCAN_THREADS, 0, s>>>(a, b);
+    }
     return cudaGetLastError();
 }
 

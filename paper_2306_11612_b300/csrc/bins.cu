@@ -695,6 +695,23 @@ cudaError_t run_tables(cudaStream_t s, const ValueTableArgs& v)
         default: return cudaErrorInvalidValue;    \
     }
 
+template <int M>
+cudaError_t preload_bins_m()
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)k_vt_block<M>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_vt_top);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_vt_level);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_bounds<M, POW_ONE>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_pixels<M>);
+    return e;
+}
+
+cudaError_t preload_bins_kernels(uint32_t M)
+{
+    DVL_DISPATCH_M2(preload_bins_m, M)
+}
+
 cudaError_t launch_value_tables(cudaStream_t s, uint32_t M, const ValueTableArgs& v)
 {
     DVL_DISPATCH_M2(run_tables, M, s, v)

@@ -220,7 +220,8 @@ struct BatchArgs {
     uint8_t* S;
     ulonglong2* psum;          // 2 x M per pixel bound (offset hs_off * 2 * M)
     float2* pmm;
-    uint32_t* tickets;         // [0]: the (group, tile) ticket counter of pass A (zeroed per batch)
+    uint32_t* tickets;         // K + 1, zeroed per batch: [0] pass A's (group, tile) counter,
+                               // [1 + k] TF k's chunk-scan block counter
     int resid;                 // pass A CTAs per SM (persistent grid)
     int sm_count;
     // Device clock (%globaltimer, ns) of the batch's execution: [0] when the
@@ -238,6 +239,11 @@ cudaError_t launch_bins_batch(cudaStream_t s, const UpdateArgs& a, const BatchAr
 cudaError_t launch_value_tables(cudaStream_t s, uint32_t M, const ValueTableArgs& v);
 cudaError_t launch_bins(cudaStream_t s, const UpdateArgs& a, const QueryArgs& qa, const ValueTableArgs& v);
 cudaError_t launch_update(cudaStream_t s, const UpdateArgs& a);
+// Load the per-edit kernels of M fields into the current context ahead of
+// their first launch (update.cu: widths and scan; bins.cu: value tables and
+// pixel queries).
+cudaError_t preload_update_kernels(uint32_t M);
+cudaError_t preload_bins_kernels(uint32_t M);
 // Alpha tables from control points (M x K -> M x T), flags values outside [0,1].
 cudaError_t launch_ctrl_table(cudaStream_t s, uint32_t M, uint32_t K, uint32_t T, const float* ctrl, float* tf,
                               uint32_t* err);

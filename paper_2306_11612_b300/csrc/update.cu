@@ -1452,6 +1452,40 @@ cudaError_t run_widths(cudaStream_t s, const UpdateArgs& a, unsigned long long* 
 
 cudaError_t launch_update(cudaStream_t s, const UpdateArgs& a) { DVL_DISPATCH_M(run_update, s, a) }
 
+// Loads the per-edit kernels of M fields into the context now (a kernel is
+// otherwise loaded at its first launch, which would add tens of ms to the
+// first update after a data set is loaded).
+template <int M>
+cudaError_t preload_m()
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaSuccess;
+    auto touch = [&](const void* f) {
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
+    };
+    touch((const void*)k_prepare);
+    touch((const void*)k_chunk_scan);
+    touch((const void*)k_finalize);
+    touch((const void*)k_passA_ring<M, POW_ONE, true, ring_depth<M>(), ring_min_blocks<M>()>);
+    touch((const void*)k_passA_ring<M, POW_GEN, true, ring_depth<M>(), ring_min_blocks<M>()>);
+    touch((const void*)k_passA_ring<M, POW_ONE, true, ring_depth<M>(), ring_min_blocks<M>(), true>);
+    return e;
+}
+cudaError_t preload_update_kernels(uint32_t M)
+{
+    switch (M) {
+        case 1: return preload_m<1>();
+        case 2: return preload_m<2>();
+        case 3: return preload_m<3>();
+        case 4: return preload_m<4>();
+        case 5: return preload_m<5>();
+        case 6: return preload_m<6>();
+        case 7: return preload_m<7>();
+        case 8: return preload_m<8>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_ctrl_table(cudaStream_t s, uint32_t M, uint32_t K, uint32_t T, const float* ctrl, float* tf,
                               uint32_t* err)
 {
