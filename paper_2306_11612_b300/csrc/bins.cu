@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "bulk.cuh"
 #include "cell_math.cuh"
 #include "dvl_internal.h"
 
@@ -48,6 +49,57 @@ __device__ __forceinline__ u128 fx_of(float t)
     const uint64_t lo = sh < 64 ? mant << sh : 0ull;
     const uint64_t hi = sh <= 40 ? 0ull : (sh < 64 ? mant >> (64 - sh) : mant << (sh - 64));
     return ((u128)hi << 64) | lo;
+}
+
+// floor(t 2^95) for 0 <= t <= 1 as five limbs, with float adds only (the
+// FMA pipe): z = t 2^95 is exact; adding C = 2^95 with round-toward-zero
+// leaves in the sum's mantissa field floor(z / 2^72) (the sum lies in
+// [2^95, 2^96], whose spacing is 2^72), and z minus that multiple of 2^72 is
+// exact (the bits of z below 2^72).  Repeating with C = 2^72, 2^49, 2^26 peels
+// 23 bits at a time; the rest (< 8) is floored against 2^23.  The limbs are
+// returned as the bit patterns of the rounded sums: bits(r_k) - bits(C_k) =
+// floor of that part, so sums of the raw bits lose nothing (wrapping u32
+// arithmetic), and floor(t 2^95) = L0 2^72 + L1 2^49 + L2 2^26 + L3 2^3 + L4.
+__device__ __forceinline__ constexpr uint32_t limb_c(int k)
+{
+    return k == 0 ? 0x6F000000u : k == 1 ? 0x63800000u : k == 2 ? 0x58000000u : k == 3 ? 0x4C800000u : 0x4B000000u;
+}
+__device__ __forceinline__ void fx_limb_bits(float t, uint32_t (&r)[5])
+{
+    const float z0 = __fmul_rn(t, 0x1p95f);
+    const float r0 = __fadd_rz(z0, 0x1p95f);
+    const float z1 = __fsub_rn(z0, __fsub_rn(r0, 0x1p95f));
+    const float r1 = __fadd_rz(z1, 0x1p72f);
+    const float z2 = __fsub_rn(z1, __fsub_rn(r1, 0x1p72f));
+    const float r2 = __fadd_rz(z2, 0x1p49f);
+    const float z3 = __fsub_rn(z2, __fsub_rn(r2, 0x1p49f));
+    const float r3 = __fadd_rz(z3, 0x1p26f);
+    const float z4 = __fsub_rn(z3, __fsub_rn(r3, 0x1p26f));
+    const float r4 = __fadd_rz(z4, 0x1p23f);
+    r[0] = __float_as_uint(r0); r[1] = __float_as_uint(r1); r[2] = __float_as_uint(r2);
+    r[3] = __float_as_uint(r3); r[4] = __float_as_uint(r4);
+}
+
+// The first two limbs only, enough for t = 0 and for t >= 2^-23: then
+// t 2^95 >= 2^72 carries its 24 significant bits at 2^49 and above, so the
+// limbs L2..L4 are 0.
+__device__ __forceinline__ void fx_limb_bits2(float t, uint32_t& r0b, uint32_t& r1b)
+{
+    const float z0 = __fmul_rn(t, 0x1p95f);
+    const float r0 = __fadd_rz(z0, 0x1p95f);
+    const float z1 = __fsub_rn(z0, __fsub_rn(r0, 0x1p95f));
+    r0b = __float_as_uint(r0);
+    r1b = __float_as_uint(__fadd_rz(z1, 0x1p72f));
+}
+
+// The sum of floor(t 2^95) over `count` cells from the limb-bit sums
+// (each limb's sum stays below 2^32 for count <= 256).
+__device__ __forceinline__ u128 fx_from_limbs(const uint32_t (&acc)[5], uint32_t count)
+{
+    uint32_t L[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) L[k] = acc[k] - count * limb_c(k);
+    return ((u128)L[0] << 72) + ((u128)L[1] << 49) + ((u128)L[2] << 26) + ((u128)L[3] << 3) + (u128)L[4];
 }
 
 // Warp sum of per-lane values below 2^120, exact: five 24-bit limbs, each
@@ -78,149 +130,342 @@ __device__ __forceinline__ u128 shfl_up_u128(u128 x, int o)
     return ((u128)hi << 64) | lo;
 }
 
-// One warp per block of VT_BLOCK = 32 steps (4096 cells).  Step by step the
-// warp reads the step's cells (lane: 4 consecutive cells, one float4 per
-// field) and reduces the sum of floor(t 2^95), min and max of t over the
-// step with redux (sums exact in five 24-bit limbs; min/max on the bits of
-// t >= 0, so that empty lanes hold +inf / 0); lane k keeps step k.  Then the
-// lanes scan across the block's steps: the exclusive prefix of the sums, the
-// inclusive prefix and suffix min/max; lane 31's inclusive values are the
-// block's total and (min, max).  Every table row is written once, coalesced.
-template <int M>
-__global__ __launch_bounds__(256) void k_vt_block(ValueTableArgs v)
+// Lane k holds step s0 + k of field m (sum of floor(t 2^95), min, max; lanes
+// >= nst the neutral values).  The lanes scan across the block's steps: the
+// exclusive prefix of the sums, the inclusive prefix and suffix min/max; lane
+// 31's inclusive values are the block's total and (min, max).  Every table
+// row is written once, coalesced.
+__device__ __forceinline__ void vt_block_rows(const ValueTableArgs& v, int m, uint64_t b, int nst, int lane,
+                                              u128 my_sum, uint32_t my_mn, uint32_t my_mx)
 {
-    const int lane = threadIdx.x & 31;
-    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    float lo[M], sc[M];
+    const uint64_t s0 = b * VT_BLOCK;
+    u128 incl = my_sum;
+    uint32_t pmn = my_mn, pmx = my_mx, smn = my_mn, smx = my_mx;
 #pragma unroll
-    for (int m = 0; m < M; ++m) { lo[m] = v.consts->lo[m]; sc[m] = v.consts->s[m]; }
-    if (blockIdx.x == 0 && threadIdx.x < M && v.n_steps % VT_BLOCK == 0)
-        v.loc[(uint64_t)threadIdx.x * (v.n_steps + 1) + v.n_steps] = make_ulonglong2(0ull, 0ull);
-    for (uint64_t b = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); b < v.n_blocks; b += warps) {
-        const uint64_t s0 = b * VT_BLOCK;
-        const int nst = v.n_steps - s0 < (uint64_t)VT_BLOCK ? (int)(v.n_steps - s0) : VT_BLOCK;
-        u128 my_sum[M];
-        uint32_t my_mn[M], my_mx[M];
+    for (int o = 1; o < 32; o <<= 1) {
+        const u128 y = shfl_up_u128(incl, o);
+        const uint32_t a = __shfl_up_sync(FULL, pmn, o), bb = __shfl_up_sync(FULL, pmx, o);
+        const uint32_t c = __shfl_down_sync(FULL, smn, o), d = __shfl_down_sync(FULL, smx, o);
+        if (lane >= o) { incl += y; pmn = min(pmn, a); pmx = max(pmx, bb); }
+        if (lane + o < 32) { smn = min(smn, c); smx = max(smx, d); }
+    }
+    const u128 excl = incl - my_sum;
+    const uint64_t row = (uint64_t)m * v.n_steps, s = s0 + lane;
+    if (lane <= nst && s <= v.n_steps)      // entry n_steps: the prefix at the data set's end
+        v.loc[(uint64_t)m * (v.n_steps + 1) + s] =
+            make_ulonglong2((unsigned long long)(uint64_t)excl, (unsigned long long)(uint64_t)(excl >> 64));
+    if (lane < nst) {
+        v.raw[row + s] = make_float2(__uint_as_float(my_mn), __uint_as_float(my_mx));
+        v.pre[row + s] = make_float2(__uint_as_float(pmn), __uint_as_float(pmx));
+        v.suf[row + s] = make_float2(__uint_as_float(smn), __uint_as_float(smx));
+    }
+    if (lane == 31) {
+        // block total into blk (turned into the exclusive prefix by k_vt_seg_*),
+        // block (min, max) into level 0 of the sparse table
+        v.blk[(uint64_t)m * (v.n_blocks + 1) + b] =
+            make_ulonglong2((unsigned long long)(uint64_t)incl, (unsigned long long)(uint64_t)(incl >> 64));
+        v.bmm[(uint64_t)m * v.b_levels * v.n_blocks + b] = make_float2(__uint_as_float(pmn), __uint_as_float(pmx));
+    }
+}
+
+// Field m of block b with fewer than 32 full steps (the data set's last
+// block), by one warp: lane k reads step k's cells from global memory (a
+// float4 at a time; the padded rows make the reads past the last cell safe,
+// and those cells are skipped) and sums all five limbs.
+template <int M>
+__device__ __noinline__ void vt_last_block_field(const ValueTableArgs& v, uint64_t b, int m, int lane)
+{
+    const uint64_t s0 = b * VT_BLOCK;
+    const int nst = v.n_steps - s0 < (uint64_t)VT_BLOCK ? (int)(v.n_steps - s0) : VT_BLOCK;
+    const float lo = v.consts->lo[m], sc = v.consts->s[m];
+    uint32_t acc[5] = {0u, 0u, 0u, 0u, 0u}, count = 0u, mn = 0x7F800000u, mx = 0u;
+    if (lane < nst) {
+        const uint64_t c0 = (s0 + lane) * STEP;
+        const float4* p = reinterpret_cast<const float4*>(v.val + m * v.pitch + c0);
+        for (int cb = 0; cb < STEP / 32; ++cb) {
+            float4 x[8];
 #pragma unroll
-        for (int m = 0; m < M; ++m) { my_sum[m] = 0; my_mn[m] = 0x7F800000u; my_mx[m] = 0u; }
-        // the next step's cells are loaded before this step's reductions
-        float4 xn[M];
-        {
-            const uint64_t idx = s0 * STEP + lane * 4;
+            for (int j = 0; j < 8; ++j) x[j] = __ldg(p + cb * 8 + j);
 #pragma unroll
-            for (int m = 0; m < M; ++m)
-                xn[m] = idx < v.n ? __ldg(reinterpret_cast<const float4*>(v.val + m * v.pitch + idx))
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll 1
-        for (int st = 0; st < nst; ++st) {
-            const uint64_t idx = (s0 + st) * STEP + lane * 4;
-            float4 x[M];
+            for (int j = 0; j < 8; ++j) {
+                const uint64_t i0 = c0 + (uint64_t)(cb * 8 + j) * 4;
+                const float e[4] = {x[j].x, x[j].y, x[j].z, x[j].w};
 #pragma unroll
-            for (int m = 0; m < M; ++m) x[m] = xn[m];
-            if (st + 1 < nst) {
-                const uint64_t nidx = idx + STEP;
+                for (int q = 0; q < 4; ++q)
+                    if (i0 + q < v.n) {
+                        const float t = norm_t(e[q], lo, sc);
+                        uint32_t r[5];
+                        fx_limb_bits(t, r);
 #pragma unroll
-                for (int m = 0; m < M; ++m)
-                    if (nidx < v.n) xn[m] = __ldg(reinterpret_cast<const float4*>(v.val + m * v.pitch + nidx));
-            }
-            const int valid = idx < v.n ? (v.n - idx < 4 ? (int)(v.n - idx) : 4) : 0;
-#pragma unroll
-            for (int m = 0; m < M; ++m) {
-                const float c[4] = {x[m].x, x[m].y, x[m].z, x[m].w};
-                u128 sum = 0;
-                uint32_t mn = 0x7F800000u, mx = 0u;
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (j < valid) {
-                        const float t = norm_t(c[j], lo[m], sc[m]);
-                        sum += fx_of(t);
+                        for (int z = 0; z < 5; ++z) acc[z] += r[z];
+                        ++count;
                         mn = min(mn, __float_as_uint(t));
                         mx = max(mx, __float_as_uint(t));
                     }
-                sum = warp_sum_limbs(sum);
-                mn = __reduce_min_sync(FULL, mn);
-                mx = __reduce_max_sync(FULL, mx);
-                if (lane == st) { my_sum[m] = sum; my_mn[m] = mn; my_mx[m] = mx; }
-            }
-        }
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-            // lanes >= nst hold the neutral values
-            u128 incl = my_sum[m];
-            uint32_t pmn = my_mn[m], pmx = my_mx[m], smn = my_mn[m], smx = my_mx[m];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const u128 y = shfl_up_u128(incl, o);
-                const uint32_t a = __shfl_up_sync(FULL, pmn, o), bb = __shfl_up_sync(FULL, pmx, o);
-                const uint32_t c = __shfl_down_sync(FULL, smn, o), d = __shfl_down_sync(FULL, smx, o);
-                if (lane >= o) { incl += y; pmn = min(pmn, a); pmx = max(pmx, bb); }
-                if (lane + o < 32) { smn = min(smn, c); smx = max(smx, d); }
-            }
-            const u128 excl = incl - my_sum[m];
-            const uint64_t row = (uint64_t)m * v.n_steps, s = s0 + lane;
-            if (lane <= nst && s <= v.n_steps)      // entry n_steps: the prefix at the data set's end
-                v.loc[(uint64_t)m * (v.n_steps + 1) + s] =
-                    make_ulonglong2((unsigned long long)(uint64_t)excl, (unsigned long long)(uint64_t)(excl >> 64));
-            if (lane < nst) {
-                v.raw[row + s] = make_float2(__uint_as_float(my_mn[m]), __uint_as_float(my_mx[m]));
-                v.pre[row + s] = make_float2(__uint_as_float(pmn), __uint_as_float(pmx));
-                v.suf[row + s] = make_float2(__uint_as_float(smn), __uint_as_float(smx));
-            }
-            if (lane == 31) {
-                // block total into blk (turned into the exclusive prefix by k_vt_top),
-                // block (min, max) into level 0 of the sparse table
-                v.blk[(uint64_t)m * (v.n_blocks + 1) + b] =
-                    make_ulonglong2((unsigned long long)(uint64_t)incl, (unsigned long long)(uint64_t)(incl >> 64));
-                v.bmm[(uint64_t)m * v.b_levels * v.n_blocks + b] = make_float2(__uint_as_float(pmn), __uint_as_float(pmx));
             }
         }
     }
+    vt_block_rows(v, m, b, nst, lane, fx_from_limbs(acc, count), mn, mx);
 }
 
-// One CTA per field: the block totals become their exclusive prefix (entry
-// n_blocks: the field's total).  Thread t takes a contiguous run of blocks.
-constexpr int VT_TOP_THREADS = 1024;
-__global__ __launch_bounds__(VT_TOP_THREADS) void k_vt_top(ValueTableArgs v)
+// Blocks [0, n_full) whose 32 steps are all full, transposed: lane k owns
+// step k of its warp's block and walks that step's cells itself, so a step's
+// sum, min and max need no cross-lane reductions.  The sums are kept as five
+// 32-bit limb sums (fx_limb_bits), mostly from two limbs: a stage whose cells
+// all have t = 0 or t >= 2^-23 needs only L0 and L1; otherwise the warp
+// walks the stage again for all five.  The cells reach shared
+// memory by bulk copies: a stage holds VQ cells of each of the block's 32
+// steps for one field (lane k's copy brings row k), VS stages per warp are
+// in flight, and a (block, field) takes STEP / VQ stages.  Lane k reads its
+// row's float4s starting at column k, so the 8 lanes of a quarter warp hit
+// distinct banks.  Blocks go to the warps round-robin; the grid's last warps
+// (those with the fewest full blocks) also take a last, partial block, a
+// field each (vt_last_block_field).  A wait that runs out
+// (bounded polls) sets ERR_TIMEOUT; the warp then waits, again bounded, for
+// its copies in flight and stops.
+constexpr int VT_WARPS = 4;
+constexpr uint32_t VT_WAIT_POLLS = 4096;       // polls of <= 1 ms
+
+template <int VQ, int VS>
+constexpr size_t vt_tx_smem() { return (size_t)VT_WARPS * VS * (VT_BLOCK * VQ * 4 + 8); }
+
+template <int M, int VQ, int VS>
+__global__ __launch_bounds__(VT_WARPS * 32) void k_vt_tx(ValueTableArgs v, uint64_t n_full)
 {
-    __shared__ u128 s_part[VT_TOP_THREADS];
-    const uint32_t m = blockIdx.x;
-    ulonglong2* blk = v.blk + (uint64_t)m * (v.n_blocks + 1);
-    const uint64_t per = (v.n_blocks + VT_TOP_THREADS - 1) / VT_TOP_THREADS;
-    const uint64_t b0 = threadIdx.x * per, b1 = b0 + per < v.n_blocks ? b0 + per : v.n_blocks;
-    u128 t = 0;
-    for (uint64_t b = b0; b < b1; ++b) t += ((u128)blk[b].y << 64) | blk[b].x;
-    s_part[threadIdx.x] = t;
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int PARTS = STEP / VQ, C4 = VQ / 4;
+    constexpr uint32_t STAGE = VT_BLOCK * VQ * 4;
+    static_assert(STEP % VQ == 0 && VQ >= 32 && (C4 & (C4 - 1)) == 0, "stage rows: a power of two of >= 8 float4s");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t ring_s = sbase + (uint32_t)warp * VS * STAGE;
+    const uint32_t bar_s = sbase + (uint32_t)(VT_WARPS * VS * STAGE) + (uint32_t)warp * VS * 8u;
+    const float4* ring = reinterpret_cast<const float4*>(smem + (size_t)warp * VS * STAGE);
+    const uint64_t gw = (uint64_t)blockIdx.x * VT_WARPS + warp, nw = (uint64_t)gridDim.x * VT_WARPS;
+    if (gw == 0 && lane < M && v.n_steps % VT_BLOCK == 0)     // the prefix entry at the end, in a block of its own
+        v.loc[(uint64_t)lane * (v.n_steps + 1) + v.n_steps] = make_ulonglong2(0ull, 0ull);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < VS; ++k) mbar_init(bar_s + 8u * k, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    // items in order: (block, field, part), blocks gw, gw + nw, ...; the
+    // issue cursor runs up to VS items ahead of the consume cursor
+    struct Cursor {
+        uint64_t b;
+        uint32_t m, h;
+    };
+    auto next = [&](Cursor& c) {
+        if (++c.h == PARTS) {
+            c.h = 0;
+            if (++c.m == M) { c.m = 0; c.b += nw; }
+        }
+    };
+    auto issue = [&](const Cursor& c, int k) {
+        const uint32_t bar = bar_s + 8u * k;
+        proxy_fence_shared();            // the warp's reads of the stage before the copy's writes
+        if (lane == 0) mbar_arrive_expect_tx(bar, STAGE);
+        bulk_g2s(ring_s + k * STAGE + (uint32_t)lane * VQ * 4,
+                 v.val + c.m * v.pitch + (c.b * VT_BLOCK + lane) * STEP + c.h * VQ, VQ * 4, bar);
+    };
+    Cursor ci{gw, 0, 0}, cc{gw, 0, 0};
+    int in_flight = 0;
+    for (int k = 0; k < VS && ci.b < n_full; ++k, ++in_flight) { issue(ci, k); next(ci); }
+    int k = 0;
+    uint32_t phase = 0;
+    bool late = false;
+    uint32_t acc[5] = {0u, 0u, 0u, 0u, 0u};
+    uint32_t mn = 0x7F800000u, mx = 0u;
+    float lo = 0.f, sc = 0.f;
+    for (; cc.b < n_full; next(cc)) {
+        if (cc.h == 0) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) acc[q] = 0u;
+            mn = 0x7F800000u; mx = 0u;
+            lo = __ldg(&v.consts->lo[cc.m]); sc = __ldg(&v.consts->s[cc.m]);
+        }
+        if (!__all_sync(FULL, mbar_wait(bar_s + 8u * k, phase, VT_WAIT_POLLS))) { late = true; break; }   // warp-uniform
+        const float4* row = ring + (size_t)k * (STAGE / 16) + lane * C4;
+        // first pass: min, max and the two-limb sums, valid when every t of
+        // the warp's stage is 0 or >= 2^-23 (t bits - 1 >= bits(2^-23) - 1,
+        // unsigned); otherwise a second pass takes all five limbs
+        uint32_t a0 = 0u, a1 = 0u, okmin = 0xFFFFFFFFu;
+#pragma unroll
+        for (int c = 0; c < C4; ++c) {
+            const float4 x = row[(c + lane) & (C4 - 1)];
+            const float t0 = norm_t(x.x, lo, sc), t1 = norm_t(x.y, lo, sc);
+            const float t2 = norm_t(x.z, lo, sc), t3 = norm_t(x.w, lo, sc);
+            const uint32_t b0 = __float_as_uint(t0), b1 = __float_as_uint(t1);
+            const uint32_t b2 = __float_as_uint(t2), b3 = __float_as_uint(t3);
+            uint32_t p0, q0, p1, q1, p2, q2, p3, q3;
+            fx_limb_bits2(t0, p0, q0); fx_limb_bits2(t1, p1, q1);
+            fx_limb_bits2(t2, p2, q2); fx_limb_bits2(t3, p3, q3);
+            a0 += (p0 + p1) + (p2 + p3);
+            a1 += (q0 + q1) + (q2 + q3);
+            mn = min(min(mn, b0), min(min(b1, b2), b3));
+            mx = max(max(mx, b0), max(max(b1, b2), b3));
+            okmin = min(min(okmin, b0 - 1u), min(min(b1 - 1u, b2 - 1u), b3 - 1u));
+        }
+        if (__all_sync(FULL, okmin >= 0x33FFFFFFu)) {
+            acc[0] += a0;
+            acc[1] += a1;
+#pragma unroll
+            for (int q = 2; q < 5; ++q) acc[q] += (uint32_t)VQ * limb_c(q);    // zero limbs of VQ cells
+        } else {
+#pragma unroll 4
+            for (int c = 0; c < C4; ++c) {
+                const float4 x = row[(c + lane) & (C4 - 1)];
+                uint32_t r0[5], r1[5], r2[5], r3[5];
+                fx_limb_bits(norm_t(x.x, lo, sc), r0); fx_limb_bits(norm_t(x.y, lo, sc), r1);
+                fx_limb_bits(norm_t(x.z, lo, sc), r2); fx_limb_bits(norm_t(x.w, lo, sc), r3);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) acc[q] += (r0[q] + r1[q]) + (r2[q] + r3[q]);
+            }
+        }
+        __syncwarp();                    // every lane has read the stage
+        --in_flight;
+        if (ci.b < n_full) { issue(ci, k); next(ci); ++in_flight; }
+        if (++k == VS) { k = 0; phase ^= 1u; }
+        if (cc.h == PARTS - 1) vt_block_rows(v, (int)cc.m, cc.b, VT_BLOCK, lane, fx_from_limbs(acc, STEP), mn, mx);
+    }
+    if (late) {
+        // the copies in flight fill the stages from k on, in order: each is
+        // waited for once more (bounded) before the warp stops
+        for (; in_flight > 0; --in_flight) {
+            mbar_wait(bar_s + 8u * k, phase, VT_WAIT_POLLS);
+            if (++k == VS) { k = 0; phase ^= 1u; }
+        }
+        if (lane == 0) atomicOr(v.err, ERR_TIMEOUT);
+        return;
+    }
+    if (n_full < v.n_blocks)          // the last block's fields go to the grid's last warps
+        for (uint64_t m = nw - 1 - gw; m < (uint64_t)M; m += nw) vt_last_block_field<M>(v, n_full, (int)m, lane);
+}
+
+// The block totals become their exclusive prefix per field (entry n_blocks:
+// the field's total), in three launches over segments of VT_SEG blocks:
+// k_vt_seg_sum writes each segment's total, k_vt_seg_scan (one warp per
+// field) turns those into exclusive prefixes, and k_vt_seg_apply rescans each
+// segment from its prefix.  Thread t of a segment's CTA takes blocks
+// [t VT_PER, (t + 1) VT_PER) of it.
+constexpr int VT_SEG_THREADS = 256, VT_PER = 8, VT_SEG = VT_SEG_THREADS * VT_PER;
+
+__device__ __forceinline__ u128 ld_u128(const ulonglong2* p)
+{
+    const ulonglong2 x = *p;
+    return ((u128)x.y << 64) | x.x;
+}
+__device__ __forceinline__ void st_u128(ulonglong2* p, u128 x)
+{
+    *p = make_ulonglong2((unsigned long long)(uint64_t)x, (unsigned long long)(uint64_t)(x >> 64));
+}
+
+// Exclusive scan of one value per thread over a CTA of VT_SEG_THREADS
+// threads (warp shuffles, then the warp totals through shared memory);
+// *total receives the CTA's sum.
+__device__ __forceinline__ u128 cta_excl_scan_u128(u128 x, u128* s_warp, u128* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    u128 incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u128 y = shfl_up_u128(incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
-    for (int o = 1; o < VT_TOP_THREADS; o <<= 1) {          // inclusive scan of the thread totals
-        const u128 y = threadIdx.x >= (unsigned)o ? s_part[threadIdx.x - o] : (u128)0;
-        __syncthreads();
-        s_part[threadIdx.x] += y;
-        __syncthreads();
+    u128 before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < VT_SEG_THREADS / 32; ++w) {
+        if (w < warp) before += s_warp[w];
+        all += s_warp[w];
     }
-    u128 run = s_part[threadIdx.x] - t;
-    for (uint64_t b = b0; b < b1; ++b) {
-        const u128 x = ((u128)blk[b].y << 64) | blk[b].x;
-        blk[b] = make_ulonglong2((unsigned long long)(uint64_t)run, (unsigned long long)(uint64_t)(run >> 64));
-        run += x;
-    }
-    if (threadIdx.x == VT_TOP_THREADS - 1) {
-        const u128 tot = s_part[VT_TOP_THREADS - 1];
-        blk[v.n_blocks] = make_ulonglong2((unsigned long long)(uint64_t)tot, (unsigned long long)(uint64_t)(tot >> 64));
+    *total = all;
+    return before + incl - x;
+}
+
+__global__ __launch_bounds__(VT_SEG_THREADS) void k_vt_seg_sum(ValueTableArgs v, ulonglong2* seg)
+{
+    __shared__ u128 s_warp[VT_SEG_THREADS / 32];
+    const uint32_t m = blockIdx.y;
+    const ulonglong2* blk = v.blk + (uint64_t)m * (v.n_blocks + 1);
+    const uint64_t b0 = (uint64_t)blockIdx.x * VT_SEG + (uint64_t)threadIdx.x * VT_PER;
+    u128 t = 0;
+#pragma unroll
+    for (int j = 0; j < VT_PER; ++j)
+        if (b0 + j < v.n_blocks) t += ld_u128(blk + b0 + j);
+    u128 total;
+    cta_excl_scan_u128(t, s_warp, &total);
+    if (threadIdx.x == 0) st_u128(seg + (uint64_t)m * gridDim.x + blockIdx.x, total);
+}
+
+__global__ void k_vt_seg_scan(ulonglong2* seg, uint32_t n_seg)
+{
+    const int lane = threadIdx.x & 31;
+    ulonglong2* p = seg + (uint64_t)blockIdx.x * n_seg;
+    u128 carry = 0;
+    for (uint32_t s0 = 0; s0 < n_seg; s0 += 32) {
+        const uint32_t i = s0 + lane;
+        const u128 x = i < n_seg ? ld_u128(p + i) : (u128)0;
+        u128 incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u128 y = shfl_up_u128(incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (i < n_seg) st_u128(p + i, carry + incl - x);
+        const uint64_t lo = __shfl_sync(FULL, (unsigned long long)(uint64_t)incl, 31);
+        const uint64_t hi = __shfl_sync(FULL, (unsigned long long)(uint64_t)(incl >> 64), 31);
+        carry += ((u128)hi << 64) | lo;
     }
 }
 
-// Level l of the blocks' sparse table: entry i covers blocks [i, i + 2^l)
-// (entries whose run would pass the last block are never read).
-__global__ void k_vt_level(ValueTableArgs v, int l)
+__global__ __launch_bounds__(VT_SEG_THREADS) void k_vt_seg_apply(ValueTableArgs v, const ulonglong2* seg)
+{
+    __shared__ u128 s_warp[VT_SEG_THREADS / 32];
+    const uint32_t m = blockIdx.y;
+    ulonglong2* blk = v.blk + (uint64_t)m * (v.n_blocks + 1);
+    const uint64_t b0 = (uint64_t)blockIdx.x * VT_SEG + (uint64_t)threadIdx.x * VT_PER;
+    u128 x[VT_PER], t = 0;
+#pragma unroll
+    for (int j = 0; j < VT_PER; ++j) {
+        x[j] = b0 + j < v.n_blocks ? ld_u128(blk + b0 + j) : (u128)0;
+        t += x[j];
+    }
+    u128 total;
+    u128 run = ld_u128(seg + (uint64_t)m * gridDim.x + blockIdx.x) + cta_excl_scan_u128(t, s_warp, &total);
+#pragma unroll
+    for (int j = 0; j < VT_PER; ++j) {
+        if (b0 + j < v.n_blocks) st_u128(blk + b0 + j, run);
+        run += x[j];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == VT_SEG_THREADS - 1) st_u128(blk + v.n_blocks, run);
+}
+
+// Levels l, l + 1 and l + 2 (those below b_levels) of the blocks' sparse
+// table from level l - 1: entry i of level l + j covers blocks
+// [i, i + 2^(l + j)), i.e. level l - 1 entries i + r 2^(l - 1) for
+// r < 2^(j + 1) (entries whose run would pass the last block are never read).
+__global__ void k_vt_levels3(ValueTableArgs v, int l)
 {
     const uint32_t m = blockIdx.y;
-    const uint64_t half = 1ull << (l - 1), n = v.n_blocks + 1 - 2 * half;   // i + 2^l <= n_blocks
-    float2* t = v.bmm + (uint64_t)m * v.b_levels * v.n_blocks;
-    const uint64_t prev = (uint64_t)(l - 1) * v.n_blocks, cur = (uint64_t)l * v.n_blocks;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const float2 a = t[prev + i], b = t[prev + i + half];
-        t[cur + i] = make_float2(fminf(a.x, b.x), fmaxf(a.y, b.y));
+    const uint64_t h = 1ull << (l - 1), nb = v.n_blocks;
+    float2* t = v.bmm + (uint64_t)m * v.b_levels * nb;
+    const float2* prev = t + (uint64_t)(l - 1) * nb;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i + 2 * h <= nb;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        float2 acc = prev[i];
+        int r = 1;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (l + j >= v.b_levels || i + (2 * h << j) > nb) break;
+            for (; r < (2 << j); ++r) {
+                const float2 e = prev[i + r * h];
+                acc = make_float2(fminf(acc.x, e.x), fmaxf(acc.y, e.y));
+            }
+            t[(uint64_t)(l + j) * nb + i] = acc;
+        }
     }
 }
 
@@ -665,17 +910,44 @@ cudaError_t run_bins_batch_m(cudaStream_t s, const UpdateArgs& a, const BatchArg
     return a.prm.P == 1.0f ? run_bins_batch<M, POW_ONE>(s, a, b, v) : run_bins_batch<M, POW_GEN>(s, a, b, v);
 }
 
+constexpr int VT_Q = 64, VT_S = 2;          // cells per stage row, stages per warp
+
 template <int M>
 cudaError_t run_tables(cudaStream_t s, const ValueTableArgs& v)
 {
     if (v.n_blocks == 0) return cudaSuccess;
-    const uint64_t cta = (v.n_blocks + 7) / 8;                 // 8 warps (blocks of steps) per CTA
-    k_vt_block<M><<<(unsigned)(cta < 148ull * 4 ? cta : 148ull * 4), 256, 0, s>>>(v);
-    k_vt_top<<<M, VT_TOP_THREADS, 0, s>>>(v);
-    for (int l = 1; l < v.b_levels; ++l) {
+    const uint64_t n_full = v.n / ((uint64_t)VT_BLOCK * STEP);     // blocks of 32 full steps
+    {
+        auto kernel = k_vt_tx<M, VT_Q, VT_S>;
+        constexpr size_t smem = vt_tx_smem<VT_Q, VT_S>();
+        static std::atomic<size_t> set_bytes[MAX_DEVICES];
+        cudaError_t e = smem_attr_once(kernel, smem, set_bytes);
+        int dev = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        // resident CTAs of the device, cached per thread for the last device
+        thread_local int last_dev = -1;
+        thread_local uint64_t resident = 0;
+        if (dev != last_dev) {
+            int per_sm = 0, sms = 0;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, VT_WARPS * 32, smem)) != cudaSuccess ||
+                (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+                return e;
+            resident = (uint64_t)(per_sm > 0 ? per_sm : 1) * sms;
+            last_dev = dev;
+        }
+        const uint64_t need = (n_full + VT_WARPS - 1) / VT_WARPS;
+        const uint64_t grid = need < resident ? (need ? need : 1) : resident;
+        kernel<<<(unsigned)grid, VT_WARPS * 32, smem, s>>>(v, n_full);
+    }
+    const uint32_t n_seg = (uint32_t)((v.n_blocks + VT_SEG - 1) / VT_SEG);
+    k_vt_seg_sum<<<dim3(n_seg, M), VT_SEG_THREADS, 0, s>>>(v, v.seg);
+    k_vt_seg_scan<<<M, 32, 0, s>>>(v.seg, n_seg);
+    k_vt_seg_apply<<<dim3(n_seg, M), VT_SEG_THREADS, 0, s>>>(v, v.seg);
+    for (int l = 1; l < v.b_levels; l += 3) {
         const uint64_t n = v.n_blocks + 1 - (2ull << (l - 1));
         const uint64_t blocks = (n + 255) / 256;
-        k_vt_level<<<dim3((unsigned)(blocks < 1024 ? blocks : 1024), M), 256, 0, s>>>(v, l);
+        k_vt_levels3<<<dim3((unsigned)(blocks < 1024 ? blocks : 1024), M), 256, 0, s>>>(v, l);
     }
     return cudaGetLastError();
 }
@@ -699,9 +971,11 @@ template <int M>
 cudaError_t preload_bins_m()
 {
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)k_vt_block<M>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_vt_top);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_vt_level);
+    cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)k_vt_tx<M, VT_Q, VT_S>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_vt_seg_sum);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_vt_seg_scan);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_vt_seg_apply);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_vt_levels3);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_bounds<M, POW_ONE>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_pixels<M>);
     return e;
@@ -725,6 +999,11 @@ cudaError_t launch_bins(cudaStream_t s, const UpdateArgs& a, const QueryArgs& qa
 cudaError_t launch_bins_batch(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b, const ValueTableArgs& v)
 {
     DVL_DISPATCH_M2(run_bins_batch_m, a.M, s, a, b, v)
+}
+
+uint64_t value_table_segments(uint64_t n_blocks)
+{
+    return (n_blocks + VT_SEG - 1) / VT_SEG;
 }
 
 int value_table_levels(uint64_t n_blocks)

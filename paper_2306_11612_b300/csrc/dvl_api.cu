@@ -208,7 +208,7 @@ void free_dataset(dvl_ctx* c)
     dfree(c->d_val); dfree(c->d_lev); dfree(c->d_perm); dfree(c->d_keys);
     dfree(c->d_keys_alt); dfree(c->d_vals_alt); dfree(c->d_rs_status);
     dfree(c->d_tile_status); dfree(c->d_chunk_prefix); dfree(c->d_step_sums);
-    dfree(c->vt.loc); dfree(c->vt.blk); dfree(c->vt.raw); dfree(c->vt.pre); dfree(c->vt.suf); dfree(c->vt.bmm);
+    dfree(c->vt.loc); dfree(c->vt.blk); dfree(c->vt.raw); dfree(c->vt.pre); dfree(c->vt.suf); dfree(c->vt.bmm); dfree(c->vt.seg);
     c->vt = ValueTableArgs{};
     c->vt_valid = false;
     free_batch(c);
@@ -556,6 +556,7 @@ int dvl_build_order(dvl_ctx* c, int sfc)
         v.val = c->d_val;
         v.pitch = p;
         v.consts = c->d_consts;
+        v.err = c->d_err;
         v.n_steps = (n + STEP - 1) / STEP;
         v.n_blocks = (v.n_steps + VT_BLOCK - 1) / VT_BLOCK;
         v.b_levels = value_table_levels(v.n_blocks);
@@ -566,6 +567,7 @@ int dvl_build_order(dvl_ctx* c, int sfc)
         CK(dalloc(v.pre, M * ns), "alloc value tables");
         CK(dalloc(v.suf, M * ns), "alloc value tables");
         CK(dalloc(v.bmm, M * (v.b_levels ? (size_t)v.b_levels * v.n_blocks : 1)), "alloc value tables");
+        CK(dalloc(v.seg, M * std::max<uint64_t>(value_table_segments(v.n_blocks), 1)), "alloc value tables");
         c->vt_valid = false;
     }
     int rc = take_device_error(c);
@@ -1493,7 +1495,7 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
                                     (uint64_t)c->d_by, (uint64_t)c->d_bcount, (uint64_t)c->d_bH, (uint64_t)c->d_bS,
                                     (uint64_t)c->d_bpsum, (uint64_t)c->d_bpmm, (uint64_t)c->d_bstamps,
                                     (uint64_t)v.loc, (uint64_t)v.blk, (uint64_t)v.raw, (uint64_t)v.pre,
-                                    (uint64_t)v.suf, (uint64_t)v.bmm};
+                                    (uint64_t)v.suf, (uint64_t)v.bmm, (uint64_t)v.seg};
     constexpr size_t MAX_GRAPHS = 32;
     auto hit = c->b_graphs.find(sig);
     if (hit == c->b_graphs.end()) {

@@ -114,6 +114,8 @@ struct ValueTableArgs {
     float2* suf;               // M x n_steps
     float2* bmm;               // M x b_levels x n_blocks: level l, entry i = blocks [i, i + 2^l)
     int b_levels;              // floor(log2(n_blocks)) + 1 (0 when there are no blocks)
+    ulonglong2* seg;           // M x ceil(n_blocks / 2048): segment sums of blk, then their prefixes
+    uint32_t* err;             // error word (ERR_TIMEOUT when a bounded wait runs out)
 };
 struct QueryArgs {
     const UpdateConsts* consts;
@@ -141,6 +143,7 @@ struct QueryArgs {
 };
 // Sparse-table levels over n_blocks blocks: floor(log2(n_blocks)) + 1.
 int value_table_levels(uint64_t n_blocks);
+uint64_t value_table_segments(uint64_t n_blocks);
 
 // update.cu
 struct UpdateArgs {

@@ -157,7 +157,8 @@ uint64_t resident_bytes(uint64_t n, uint32_t M)
     const uint64_t steps = (n + STEP - 1) / STEP, tiles = (n + TILE - 1) / TILE, chunks = tiles * WARPS;
     const uint64_t blocks = (steps + VT_BLOCK - 1) / VT_BLOCK;
     const uint64_t tables = (uint64_t)M * ((steps + 1) * 16 + (blocks + 1) * 16 + steps * 3 * 8 +
-                                           (uint64_t)value_table_levels(blocks) * blocks * 8);
+                                           (uint64_t)value_table_levels(blocks) * blocks * 8 +
+                                           value_table_segments(blocks) * 16);
     return pad * (8ull * M + 1) + n * (4 + 8 + 8 + 4) + tables + tiles * 8 + chunks * 8 + chunks * STEPS * 8;
 }
 
