@@ -16,6 +16,25 @@ namespace dvl {
 
 namespace {
 
+// Two float32 operations in one instruction (round to nearest, each lane of
+// the pair rounded on its own, as the scalar forms).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "sub.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "mul.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
 __device__ __forceinline__ float4 lds_f32x4(uint32_t addr)
 {
     float4 r;
@@ -42,9 +61,8 @@ __global__ void k_prepare_batch(UpdateArgs a, BatchArgs b)
 
 // Pass A for all K transfer functions of a batch (all TFs share the TF
 // domains), in one persistent launch: the TFs form groups of G whose alpha
-// tables fit in shared memory together, and CTAs take (group, tile) tickets
-// from one counter, group by group; a CTA loads a group's tables when its
-// ticket moves to a new group (once or twice per CTA).  Every warp step's
+// tables fit in shared memory together; a CTA holds one group's tables at a
+// time and its warps claim that group's chunks one by one (see below).  Every warp step's
 // cells are loaded and normalised once per group and evaluated for all G TFs;
 // per TF it writes step and chunk totals (no wait on other warps or tiles:
 // k_chunk_scan_batch scans the chunk totals afterwards).  G is a compile-time constant so the TF loop unrolls; per
@@ -61,17 +79,24 @@ __global__ void k_prepare_batch(UpdateArgs a, BatchArgs b)
 template <int M, int PM, int G, int ST>
 __device__ __forceinline__ void passA_batch_body(const UpdateArgs& a, const BatchArgs& b)
 {
-    extern __shared__ float4 s_dyn[];                  // G x 1 params, then G x M x T1 tables
-    __shared__ uint32_t s_tile;
+    extern __shared__ float4 s_dyn[];                  // G params, the floors, the G x M x T1 tables
+    __shared__ uint32_t s_claimed;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // table stride per field: ST (a compile-time constant >= T + 1, so that
     // the unrolled TF loop addresses its tables with immediate offsets), or
     // T + 1 when ST = 0
     constexpr uint32_t RS = G + 4;                     // floats per table row (field, entry)
     const uint32_t T = a.T, T1 = ST ? (uint32_t)ST : T + 1, K = b.K, MT1 = M * T1;
-    const uint32_t n_tiles = (uint32_t)b.n_tiles, n_groups = (K + G - 1) / G;
-    float4* s_par = s_dyn;                             // per TF: (1/maxV, m_b, m_a, 2^Q), see above
-    float* s_tf = reinterpret_cast<float*>(s_dyn + G); // M x T1 rows of RS floats, TF innermost
+    const uint32_t n_groups = (K + G - 1) / G;
+    // per quad of TFs, 4 float4s: (1/maxV), (m_b), (m_a), (2^Q) of its 4 TFs
+    // (see above for P = 1), so that a pair of TFs' values is one register pair
+    float* s_par = reinterpret_cast<float*>(s_dyn);
+    // P = 1: per level L and TF, the lower bound max(m_b 2^(L w), m_a) (x 2^Q)
+    // of Eq. 3's result, since max(max(r, m_b) 2^(L w), m_a) equals
+    // max(r 2^(L w), max(m_b 2^(L w), m_a)) exactly (scaling by 2^(L w) is)
+    float* s_floor = reinterpret_cast<float*>(s_dyn + G);                 // (DVL_MAX_LEVEL + 1) x G
+    const uint32_t floor_s = (uint32_t)__cvta_generic_to_shared(s_floor);
+    float* s_tf = s_floor + (DVL_MAX_LEVEL + 1) * G;   // M x T1 rows of RS floats, TF innermost
     const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(s_tf);
     const UpdateConsts* C0 = b.consts;
     float lo[M], sc[M];
@@ -98,25 +123,36 @@ __device__ __forceinline__ void passA_batch_body(const UpdateArgs& a, const Batc
                 pr = PM == POW_ONE ? make_float4(__fmul_rn(Ck->inv_vmax, qs), __fmul_rn(mb, qs), __fmul_rn(ma, qs), qs)
                                    : make_float4(Ck->inv_vmax, mb, ma, qs);
             }
-            s_par[kk] = pr;
+            float* q4 = s_par + (kk / 4) * 16 + (kk % 4);
+            q4[0] = pr.x; q4[4] = pr.y; q4[8] = pr.z; q4[12] = pr.w;
+            for (int L = 0; L <= DVL_MAX_LEVEL; ++L)
+                s_floor[L * G + kk] = fmaxf(__fmul_rn(pr.y, exp2i(L * wshift)), pr.z);
         }
     };
 
+    // Each CTA starts on group blockIdx.x mod n_groups and then visits the
+    // other groups in turn; within a group its warps claim chunks one at a
+    // time from the group's counter (tickets[1 + K + group]), so no warp waits
+    // for another until the group's chunks run out.
+    const uint64_t n_chunks = b.n_chunks;
+    uint32_t* group_count = b.tickets + 1 + K;
+    for (uint32_t visit = 0, gi = blockIdx.x % n_groups; visit < n_groups;
+         ++visit, gi = gi + 1 == n_groups ? 0 : gi + 1) {
+        if (tid == 0) s_claimed = *(volatile uint32_t*)(group_count + gi);
+        __syncthreads();                               // the previous group's tables are no longer read
+        const uint32_t seen = s_claimed;
+        __syncthreads();                               // s_claimed is rewritten at the next visit
+        if (seen >= n_chunks) continue;                // block-uniform: nothing left of this group
+        load_group(gi * G);
+        __syncthreads();                               // tables ready
     while (true) {
-        if (tid == 0) s_tile = atomicAdd(b.tickets, 1u);
-        __syncthreads();                               // ticket visible; the last tile's work done
-        const uint32_t ticket = s_tile;
-        const uint32_t gi = ticket / n_tiles;          // block-uniform
-        if (gi >= n_groups) break;
-        const uint32_t tile = ticket - gi * n_tiles;
-        if (gi * G != g0) {
-            load_group(gi * G);
-            __syncthreads();                           // tables ready
-        }
+        uint32_t claimed = 0;
+        if (lane == 0) claimed = atomicAdd(group_count + gi, 1u);
+        claimed = __shfl_sync(FULL, claimed, 0);
+        if (claimed >= n_chunks) break;                // warp-uniform
         unsigned long long ct = 0;                     // lane kk: TF kk's chunk total
-        const uint64_t chunk = (uint64_t)tile * WARPS + warp;
+        const uint64_t chunk = claimed;
         const uint64_t base = chunk * CHUNK;
-        __syncwarp();
         // the next step's cells are loaded while this step's TFs run (the
         // same addresses as the step itself reads, one step earlier)
         float vn[4][M];
@@ -131,6 +167,7 @@ __device__ __forceinline__ void passA_batch_body(const UpdateArgs& a, const Batc
             const uint64_t idx = base + st * STEP + lane * 4;
             uint32_t off[4][M];                        // shared address of row (m, entry)
             float lvl[4];
+            uint32_t frow[4];                          // shared address of the cell's level row of s_floor
             bool valid[4];
             float v[4][M];
             const uint32_t L4 = Ln;
@@ -146,7 +183,9 @@ __device__ __forceinline__ void passA_batch_body(const UpdateArgs& a, const Batc
 #pragma unroll
                     for (int m = 0; m < M; ++m)
                         off[j][m] = s_base + (m * T1 + floor_small(__fmul_rn(norm_t(v[j][m], lo[m], sc[m]), Tf))) * (RS * 4);
-                    lvl[j] = exp2i((int)((L4 >> (8 * j)) & 0xFF) * wshift);
+                    const uint32_t Lj = (L4 >> (8 * j)) & 0xFF;
+                    lvl[j] = exp2i((int)Lj * wshift);
+                    frow[j] = floor_s + Lj * (G * 4);
                 }
             } else {
 #pragma unroll
@@ -154,6 +193,7 @@ __device__ __forceinline__ void passA_batch_body(const UpdateArgs& a, const Batc
 #pragma unroll
                     for (int m = 0; m < M; ++m) off[j][m] = s_base;
                     lvl[j] = 0.0f;
+                    frow[j] = floor_s;
                 }
             }
 #pragma unroll
@@ -168,34 +208,52 @@ __device__ __forceinline__ void passA_batch_body(const UpdateArgs& a, const Batc
                 constexpr bool ALL = decltype(full_tag)::value;     // every cell present
                 constexpr int NQ = decltype(nq_tag)::value;
                 const int nq = NQ ? NQ : (int)gk - kq * 4;
-                float4 pr[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) pr[i] = s_par[kq * 4 + i];
+                const float4* pq = reinterpret_cast<const float4*>(s_par) + kq * 4;
+                const float4 PX = pq[0], PY = pq[1], PZ = pq[2], PW = pq[3];
+                const float px[4] = {PX.x, PX.y, PX.z, PX.w}, py[4] = {PY.x, PY.y, PY.z, PY.w};
+                const float pz[4] = {PZ.x, PZ.y, PZ.z, PZ.w}, pw[4] = {PW.x, PW.y, PW.z, PW.w};
                 unsigned long long l[4] = {0, 0, 0, 0};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     float4 a4[M];
 #pragma unroll
                     for (int m = 0; m < M; ++m) a4[m] = lds_f32x4(off[j][m] + (uint32_t)kq * 16u);
+                    // the 4 TFs' spreads (max - min over the fields)
+                    float hi[4], lw[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        if (!NQ && i >= nq) break;                     // block-uniform
                         float al[M];
 #pragma unroll
                         for (int m = 0; m < M; ++m) al[m] = i == 0 ? a4[m].x : i == 1 ? a4[m].y : i == 2 ? a4[m].z : a4[m].w;
-                        // Eq. 3 as importance<PM>, with the level factor precomputed
-                        // (and, with P = 1, 2^Q folded into the constants)
-                        const float r = fmaxf(__fmul_rn(spread<M>(al), pr[i].x), pr[i].y);
-                        const float x = __fmul_rn(r, lvl[j]);
-                        uint32_t q;
-                        if (PM == POW_ONE) {
-                            q = __float2uint_rn(fmaxf(x, pr[i].z));
-                        } else {
-                            const float f = fmaxf(pow_gen(x, n2, P), pr[i].z);
-                            q = __float2uint_rn(__fmul_rn(f, pr[i].w));
+                        spread_ends<M>(al, hi[i], lw[i]);
+                    }
+                    uint32_t q[4];
+                    if (PM == POW_ONE) {
+                        // Eq. 3 with the level factor precomputed, 2^Q folded into
+                        // the constants and the minimum importance into s_floor,
+                        // two TFs per float32x2 instruction
+                        const float4 fl = lds_f32x4(frow[j] + (uint32_t)kq * 16u);
+                        const float flo[4] = {fl.x, fl.y, fl.z, fl.w};
+#pragma unroll
+                        for (int h = 0; h < 4; h += 2) {
+                            const float2 sp = sub2(make_float2(hi[h], hi[h + 1]), make_float2(lw[h], lw[h + 1]));
+                            const float2 r0 = mul2(sp, make_float2(px[h], px[h + 1]));
+                            const float2 x = mul2(r0, make_float2(lvl[j], lvl[j]));
+                            q[h] = __float2uint_rn(fmaxf(x.x, flo[h]));
+                            q[h + 1] = __float2uint_rn(fmaxf(x.y, flo[h + 1]));
                         }
-                        if (!ALL) q = valid[j] ? q : 0u;
-                        l[i] += q;
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float r = fmaxf(__fmul_rn(__fsub_rn(hi[i], lw[i]), px[i]), py[i]);
+                            const float f = fmaxf(pow_gen(__fmul_rn(r, lvl[j]), n2, P), pz[i]);
+                            q[i] = __float2uint_rn(__fmul_rn(f, pw[i]));
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (!NQ && i >= nq) break;                     // block-uniform
+                        l[i] += ALL ? q[i] : (valid[j] ? q[i] : 0u);
                     }
                 }
 #pragma unroll
@@ -227,7 +285,7 @@ __device__ __forceinline__ void passA_batch_body(const UpdateArgs& a, const Batc
         // the warp's chunk total of each TF of the group (lane kk: TF g0 + kk);
         // k_chunk_scan_batch turns them into prefixes
         if (lane < (int)gk) b.chunk_prefix[(uint64_t)(g0 + lane) * b.n_chunks + chunk] = ct;
-        __syncthreads();                               // s_tile is reused
+    }
     }
 }
 
@@ -352,7 +410,8 @@ constexpr int SMALL_T1 = 257;                    // fixed table stride for T <= 
 size_t passA_batch_smem(uint32_t M, uint32_t T, uint32_t G)
 {
     const uint32_t T1 = T + 1 <= (uint32_t)SMALL_T1 ? SMALL_T1 : T + 1;
-    return (size_t)G * sizeof(float4) + (size_t)(G + 4) * M * T1 * sizeof(float);
+    return (size_t)G * sizeof(float4) + (size_t)(DVL_MAX_LEVEL + 1) * G * sizeof(float) +
+           (size_t)(G + 4) * M * T1 * sizeof(float);
 }
 
 template <int M, int PM, int G, int ST>
@@ -363,7 +422,7 @@ cudaError_t run_passA_batch_gs(cudaStream_t s, const UpdateArgs& a, const BatchA
     constexpr auto kernel = passA_batch_kernel<M, PM, G, ST>();
     cudaError_t e = smem_attr_once(kernel, smem, set_bytes);
     if (e != cudaSuccess) return e;
-    const uint64_t work = b.n_tiles * ((b.K + G - 1) / G);    // (group, tile) tickets
+    const uint64_t work = (b.n_chunks * ((b.K + G - 1) / G) + WARPS - 1) / WARPS;   // CTAs with a chunk each
     uint64_t grid = (uint64_t)b.sm_count * b.resid;
     if (grid > work) grid = work;
     if (grid) {

@@ -117,9 +117,10 @@ __device__ __forceinline__ float min3f(float a, float b, float c)
     return r;
 }
 
-// max_m al[m] - min_m al[m] (Eq. 1 for one cell), with three-input steps.
+// max_m al[m] and min_m al[m] (the ends of Eq. 1 for one cell), with
+// three-input steps.
 template <int M>
-__device__ __forceinline__ float spread(const float (&al)[M])
+__device__ __forceinline__ void spread_ends(const float (&al)[M], float& hi_out, float& lw_out)
 {
     float hi = al[0], lw = al[0];
     int m = 1;
@@ -132,6 +133,16 @@ __device__ __forceinline__ float spread(const float (&al)[M])
         hi = fmaxf(hi, al[m]);
         lw = fminf(lw, al[m]);
     }
+    hi_out = hi;
+    lw_out = lw;
+}
+
+// Eq. 1: max_m al[m] - min_m al[m].
+template <int M>
+__device__ __forceinline__ float spread(const float (&al)[M])
+{
+    float hi, lw;
+    spread_ends<M>(al, hi, lw);
     return __fsub_rn(hi, lw);
 }
 

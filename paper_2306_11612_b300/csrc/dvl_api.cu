@@ -106,7 +106,7 @@ struct dvl_ctx {
     float* d_btf = nullptr;               // K x M x T
     float* d_bdom = nullptr;              // 2 x DVL_MAX_FIELDS
     UpdateConsts* d_bconsts = nullptr;    // K
-    uint32_t* d_btickets = nullptr;       // K + 1: pass A's (group, tile) counter, then one scan counter per TF
+    uint32_t* d_btickets = nullptr;       // 2K + 1: unused, one scan counter per TF, one chunk counter per TF group
     unsigned long long *d_btile = nullptr, *d_bprefix = nullptr, *d_bsteps = nullptr;
     PairDesc* d_pairs = nullptr;
     double* d_bsum = nullptr;
@@ -225,7 +225,7 @@ cudaError_t enqueue_batch(dvl_ctx* c, const UpdateArgs& a, const BatchArgs& b, c
     cudaError_t e;
     if (ev) cudaEventRecord(ev[0], s);
     if ((e = cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(c->d_btickets, 0, (size_t)(b.K + 1) * sizeof(uint32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_btickets, 0, (size_t)(2 * b.K + 1) * sizeof(uint32_t), s)) != cudaSuccess) return e;
     if (b.n_tiles &&
         (e = cudaMemsetAsync(c->d_btile, 0, (size_t)b.K * b.n_tiles * sizeof(unsigned long long), s)) != cudaSuccess)
         return e;
@@ -1316,7 +1316,7 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
         CK(grow(c->d_btf, c->btf_cap, nTF), "alloc batch TFs");
         if (K > c->bk_cap) {
             CK(dalloc(c->d_bconsts, K), "alloc batch");
-            CK(dalloc(c->d_btickets, K + 1), "alloc batch");
+            CK(dalloc(c->d_btickets, 2 * K + 1), "alloc batch");
             CK(dalloc(c->d_btile, (size_t)K * n_tiles), "alloc batch scan state");
             CK(dalloc(c->d_bprefix, (size_t)K * n_chunks), "alloc batch scan state");
             CK(dalloc(c->d_bsteps, (size_t)K * n_chunks * STEPS), "alloc batch scan state");

@@ -223,8 +223,8 @@ struct BatchArgs {
     uint8_t* S;
     ulonglong2* psum;          // 2 x M per pixel bound (offset hs_off * 2 * M)
     float2* pmm;
-    uint32_t* tickets;         // K + 1, zeroed per batch: [0] pass A's (group, tile) counter,
-                               // [1 + k] TF k's chunk-scan block counter
+    uint32_t* tickets;         // 2K + 1, zeroed per batch: [1 + k] TF k's chunk-scan block
+                               // counter, [1 + K + g] pass A's chunk counter of TF group g
     int resid;                 // pass A CTAs per SM (persistent grid)
     int sm_count;
     // Device clock (%globaltimer, ns) of the batch's execution: [0] when the

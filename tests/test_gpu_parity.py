@@ -87,7 +87,7 @@ def _random_amr(seed, n, M):
     return np.ascontiguousarray(lo), lev, fields
 
 
-@pytest.mark.parametrize("n", [1, 3, 127, 128, 129, 1023, 1024, 1025, 2047, 2048, 2049, 4097, 8193,
+@pytest.mark.parametrize("n", [1, 3, 127, 128, 129, 1023, 1024, 1025, 2047, 2048, 2049, 4095, 4096, 4097, 8193, 12288, 20479,
                                16383, 16384, 16385, 20000, 70001])
 def test_ragged_sizes(n):
     lo, lev, fields = _random_amr(n, n, 4)
