@@ -102,6 +102,33 @@ __device__ __forceinline__ float importance(float V, uint32_t L, float inv_vmax,
     return fmaxf(f, ma);
 }
 
+// Two float32 operations in one instruction (sm_100 and later; each half
+// rounded on its own, exactly as the scalar form).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "sub.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "mul.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 fma_rz2(float2 a, float2 b, float2 c)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 a, b, c, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "mov.b64 c, {%6, %7};\n\tfma.rz.f32x2 d, a, b, c;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
+
 // Three-input float max / min (single instructions on sm_100 and later); the
 // result is one of the inputs, as with fmaxf / fminf on non-NaN values.
 __device__ __forceinline__ float max3f(float a, float b, float c)
@@ -243,6 +270,41 @@ struct Cell {
         }
         float f = importance<PM>(spread<M>(al), L, inv_vmax, mb, ma, wshift, n2, P);
         return __float2uint_rn(__fmul_rn(f, qscale));
+    }
+
+    // width_p2 of two cells a and b at once (P = 1): the subtraction, the
+    // entry's fma and Eq. 3's multiplies in float32x2 form, bit for bit the
+    // same as two width_p2 calls.  AL: also returns each field's fixed-point
+    // alpha of the two cells in axa[m], axb[m] (see width_p2_alpha).
+    template <bool AL>
+    __device__ __forceinline__ void width2_p2(const float* va, const float* vb, uint32_t La, uint32_t Lb,
+                                              const uint32_t* cm, uint32_t aoff, uint32_t (&axa)[M],
+                                              uint32_t (&axb)[M], uint32_t& qa, uint32_t& qb) const
+    {
+        float ala[M], alb[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const float2 d = sub2(make_float2(va[m], vb[m]), make_float2(lo[m], lo[m]));
+            const float2 e = fma_rz2(make_float2(mul_sat(d.x, s[m]), mul_sat(d.y, s[m])), make_float2(Tf, Tf),
+                                     make_float2(8388608.0f, 8388608.0f));
+            const uint32_t adra = __float_as_uint(e.x) * 4u + cm[m], adrb = __float_as_uint(e.y) * 4u + cm[m];
+            ala[m] = lds_f32(adra);
+            alb[m] = lds_f32(adrb);
+            if (AL) {
+                axa[m] = lds_u32(adra + aoff);
+                axb[m] = lds_u32(adrb + aoff);
+            }
+        }
+        float ha, la, hb, lb;
+        spread_ends<M>(ala, ha, la);
+        spread_ends<M>(alb, hb, lb);
+        const float2 V = sub2(make_float2(ha, hb), make_float2(la, lb));
+        const float2 r0 = mul2(V, make_float2(inv_vmax, inv_vmax));
+        const float2 r = make_float2(fmaxf(r0.x, mb), fmaxf(r0.y, mb));
+        const float2 x = mul2(r, make_float2(exp2i((int)La * wshift), exp2i((int)Lb * wshift)));
+        const float2 f = mul2(make_float2(fmaxf(x.x, ma), fmaxf(x.y, ma)), make_float2(qscale, qscale));
+        qa = __float2uint_rn(f.x);
+        qb = __float2uint_rn(f.y);
     }
 
     // width_p2, also adding each field's fixed-point alpha (alpha_fx of the

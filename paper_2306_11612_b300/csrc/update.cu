@@ -95,6 +95,23 @@ __device__ __forceinline__ unsigned long long widths4_of(const Cell<M, PM>& cc, 
                                                          uint32_t* ax = nullptr)
 {
     unsigned long long acc = 0;
+    if (P2 && PM == POW_ONE) {
+        // pairs of cells in float32x2 form
+#pragma unroll
+        for (int j = 0; j < 4; j += 2) {
+            uint32_t axa[M], axb[M], qa, qb;
+            cc.template width2_p2<AL>(v[j], v[j + 1], (L4 >> (8 * j)) & 0xFF, (L4 >> (8 * j + 8)) & 0xFF, cm, aoff,
+                                      axa, axb, qa, qb);
+            const bool ina = FULLSTEP || idx + j < a.n, inb = FULLSTEP || idx + j + 1 < a.n;
+            if (ina) acc += qa;
+            if (inb) acc += qb;
+            if (AL) {
+#pragma unroll
+                for (int m = 0; m < M; ++m) ax[m] += (ina ? axa[m] : 0u) + (inb ? axb[m] : 0u);
+            }
+        }
+        return acc;
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         uint32_t q;
