@@ -5,12 +5,16 @@
 //
 // One scheduler thread owns every context.  A batch's alpha tables and
 // results live in pinned buffers of its data set; after the batch and the
-// copies of its bins are queued on the data set's stream, a host callback on
-// that stream wakes the scheduler, which hands the results to the waiting
-// requests.
+// copies of its bins are queued on the data set's stream, an event follows
+// them.  While batches are in flight the scheduler polls those events
+// (no thread hand-off between the device finishing and the results being
+// handed out) and keeps launching; with nothing in flight it polls the queues
+// for a short while before it sleeps, and a waiting caller likewise polls its
+// request's flag for a short while before it sleeps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -51,6 +55,7 @@ struct Request {
     std::vector<float> alpha;           // M x T
     double t_submit = 0, t_done = 0;
     bool done = false;
+    std::atomic<bool> ready{false};     // done, readable without the lock (set after `done`)
     int status = DVL_OK;
     std::vector<float> mean, mn, mx, y;  // M x W
     std::vector<double> sum;
@@ -87,7 +92,7 @@ struct Dataset {
     std::deque<Request*> queue;
     // batch on the GPU
     bool busy = false;
-    bool finished = false;               // set by the stream callback
+    cudaEvent_t done_ev = nullptr;       // after the batch's result copies, on its stream
     std::vector<Request*> batch;
     uint32_t K = 0;
     Pinned<float> h_alpha, r_mean, r_mn, r_mx, r_y;
@@ -120,6 +125,7 @@ struct dvl_server {
     std::thread th;
     bool stop = false;
     uint64_t next_id = 1;
+    std::atomic<uint64_t> queued_total{0};   // requests ever queued (the scheduler polls it without the lock)
     uint64_t mem_used = 0;
     int inflight = 0;
     std::string last_error;
@@ -171,17 +177,11 @@ uint64_t per_tf_bytes(uint64_t n, uint32_t M, uint32_t T, uint32_t W)
            sizeof(PairDesc);
 }
 
-void CUDART_CB on_batch_done(void* arg);
-
-struct CallbackArg {
-    dvl_server* srv;
-    Dataset* d;
-};
-
 void finish_request(dvl_server* s, Request* r, int status, double t)
 {
     r->status = status;
     r->done = true;
+    r->ready.store(true, std::memory_order_release);
     r->t_done = t;
     if (status == DVL_OK) {
         ++s->completed;
@@ -229,7 +229,6 @@ void complete_batch(dvl_server* s, Dataset* d, int rc)
     }
     d->batch.clear();
     d->busy = false;
-    d->finished = false;
     --s->inflight;
     s->cv_done.notify_all();
 }
@@ -258,7 +257,6 @@ bool launch_batch(dvl_server* s, Dataset* d, std::unique_lock<std::mutex>& lk)
     d->batch.assign(d->queue.begin(), d->queue.begin() + k);
     d->queue.erase(d->queue.begin(), d->queue.begin() + k);
     d->busy = true;
-    d->finished = false;
     d->K = K;
     ++s->inflight;
     ++s->batches;
@@ -320,9 +318,12 @@ bool launch_batch(dvl_server* s, Dataset* d, std::unique_lock<std::mutex>& lk)
         rc = DVL_ERR_CUDA;
     }
     if (rc == DVL_OK) {
-        auto* arg = new CallbackArg{s, d};
-        if (cudaLaunchHostFunc(st, on_batch_done, arg) != cudaSuccess) {
-            delete arg;
+        if (!d->done_ev && cudaEventCreateWithFlags(&d->done_ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            d->done_ev = nullptr;
+            rc = DVL_ERR_CUDA;
+        } else if (cudaEventRecord(d->done_ev, st) != cudaSuccess) {
+            cudaGetLastError();
             rc = DVL_ERR_CUDA;
         }
     }
@@ -345,41 +346,44 @@ bool launch_batch(dvl_server* s, Dataset* d, std::unique_lock<std::mutex>& lk)
     return true;
 }
 
-void CUDART_CB on_batch_done(void* p)
+constexpr double SPIN_IDLE_S = 300e-6;     // the scheduler polls empty queues this long before it sleeps
+constexpr double SPIN_WAIT_S = 2e-3;       // a caller polls its request this long before it sleeps
+
+// A batch is finished when its completion event has passed (or the event
+// reports an error, which dvl_sync then returns).  CUDA call: lock not held.
+bool batch_finished(Dataset* d)
 {
-    // runs on a CUDA driver thread: no CUDA calls here, only the wake-up
-    auto* arg = static_cast<CallbackArg*>(p);
-    dvl_server* s = arg->srv;
-    {
-        std::lock_guard<std::mutex> g(s->mu);
-        arg->d->finished = true;
+    const cudaError_t e = cudaEventQuery(d->done_ev);
+    if (e == cudaErrorNotReady) {
+        if (cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();
+        return false;
     }
-    s->cv_sched.notify_one();
-    delete arg;
+    return true;
 }
 
 void scheduler(dvl_server* s)
 {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
+    double idle_since = now_s();
+    std::vector<Dataset*> busy, done;
+    std::vector<int> rc;
     while (true) {
-        // finished batches: sync (device-side errors) without the lock, then
-        // hand out the results
-        std::vector<Dataset*> done;
-        for (size_t i = 0; i < s->ds.size(); ++i) {
-            Dataset* d = s->ds[i].get();
-            if (d->busy && d->finished) {
-                d->finished = false;
-                done.push_back(d);
-            }
-        }
-        if (!done.empty()) {
-            std::vector<int> rc(done.size());
+        // finished batches: poll the in-flight batches' events, sync (device-
+        // side errors) and hand out the results; CUDA calls without the lock
+        busy.clear();
+        for (auto& dp : s->ds)
+            if (dp->busy && dp->done_ev) busy.push_back(dp.get());
+        if (!busy.empty()) {
+            done.clear();
             lk.unlock();
+            for (Dataset* d : busy)
+                if (batch_finished(d)) done.push_back(d);
+            rc.assign(done.size(), DVL_OK);
             for (size_t i = 0; i < done.size(); ++i) rc[i] = dvl_sync(done[i]->ctx);
             lk.lock();
             for (size_t i = 0; i < done.size(); ++i) complete_batch(s, done[i], rc[i]);
-            continue;
+            if (!done.empty()) idle_since = now_s();
         }
         if (s->stop && s->inflight == 0) break;
         bool launched = false;
@@ -389,15 +393,41 @@ void scheduler(dvl_server* s)
                 Dataset* d = s->ds[i].get();
                 if (!d->busy && !d->queue.empty()) launched |= launch_batch(s, d, lk);
             }
-        if (launched) continue;
+        if (launched) {
+            idle_since = now_s();
+            continue;
+        }
+        if (s->inflight > 0 || now_s() - idle_since < SPIN_IDLE_S) {
+            // batches in flight, or a closed-loop caller about to submit its
+            // next request: poll without the lock (so that submitting and
+            // waiting threads are not held up) until a batch's event passes,
+            // a request is queued or the idle window ends
+            const uint64_t q0 = s->queued_total.load(std::memory_order_acquire);
+            busy.clear();
+            for (auto& dp : s->ds)
+                if (dp->busy && dp->done_ev) busy.push_back(dp.get());
+            const bool idle = s->inflight == 0;
+            lk.unlock();
+            while (true) {
+                if (s->queued_total.load(std::memory_order_acquire) != q0) break;
+                bool any = false;
+                for (Dataset* d : busy)
+                    if (batch_finished(d)) any = true;
+                if (any) break;
+                if (idle && now_s() - idle_since >= SPIN_IDLE_S) break;
+                const double t = now_s();
+                while (now_s() - t < 2e-6) std::this_thread::yield();   // ~2 us between polls
+            }
+            lk.lock();
+            continue;
+        }
         s->cv_sched.wait(lk, [&] {
+            if (s->stop) return true;
             for (auto& dp : s->ds)
-                if (dp->busy && dp->finished) return true;
-            if (s->stop) return s->inflight == 0;
-            for (auto& dp : s->ds)
-                if (!dp->busy && !dp->queue.empty() && s->inflight < (int)s->cfg.max_inflight) return true;
+                if (!dp->busy && !dp->queue.empty()) return true;
             return false;
         });
+        idle_since = now_s();
     }
     // requests never launched fail
     const double t = now_s();
@@ -477,7 +507,10 @@ void dvl_server_destroy(dvl_server* s)
     s->cv_sched.notify_all();
     if (s->th.joinable()) s->th.join();
     for (auto& kv : s->reqs) delete kv.second;
-    for (auto& dp : s->ds) dvl_destroy(dp->ctx);
+    for (auto& dp : s->ds) {
+        if (dp->done_ev) cudaEventDestroy(dp->done_ev);
+        dvl_destroy(dp->ctx);
+    }
     for (const Span& sp : s->spans) {
         cudaEventDestroy(sp.ev0);
         cudaEventDestroy(sp.ev1);
@@ -554,6 +587,7 @@ int dvl_server_submit(dvl_server* s, uint32_t dataset, const float* alpha, uint3
         ++s->submitted;
         s->reqs[r->id] = r;
         s->ds[dataset]->queue.push_back(r);
+        s->queued_total.fetch_add(1, std::memory_order_release);
         *id = r->id;
     }
     s->cv_sched.notify_one();
@@ -569,6 +603,14 @@ int dvl_server_wait(dvl_server* s, uint64_t id, double timeout_s, const dvl_bins
     if (it == s->reqs.end()) return sfail(s, DVL_ERR_ARG, "unknown request %llu", (unsigned long long)id);
     Request* r = it->second;
     auto ready = [&] { return r->done; };
+    if (!r->done) {
+        // poll the request's flag for a short while without the lock, then sleep
+        lk.unlock();
+        const double t0 = now_s(), spin = timeout_s < 0 ? SPIN_WAIT_S : std::min(SPIN_WAIT_S, timeout_s);
+        while (!r->ready.load(std::memory_order_acquire) && now_s() - t0 < spin) std::this_thread::yield();
+        lk.lock();
+        if (timeout_s >= 0) timeout_s = std::max(0.0, timeout_s - (now_s() - t0));
+    }
     if (timeout_s < 0) {
         s->cv_done.wait(lk, ready);
     } else if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready)) {
@@ -616,6 +658,7 @@ int dvl_server_warmup(dvl_server* s)
                 r->t_submit = now_s();
                 s->reqs[r->id] = r;
                 s->ds[d]->queue.push_back(r);
+                s->queued_total.fetch_add(1, std::memory_order_release);
                 ids.push_back(r->id);
             }
         }

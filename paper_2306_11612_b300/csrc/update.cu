@@ -110,30 +110,30 @@ __device__ __forceinline__ unsigned long long widths4_of(const Cell<M, PM>& cc, 
                 for (int m = 0; m < M; ++m) ax[m] += (ina ? axa[m] : 0u) + (inb ? axb[m] : 0u);
             }
         }
-        return acc;
-    }
+    } else {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        uint32_t q;
-        uint32_t axj[M];
+        for (int j = 0; j < 4; ++j) {
+            uint32_t q;
+            uint32_t axj[M];
 #pragma unroll
-        for (int m = 0; m < M; ++m) axj[m] = 0;
-        if (P2) {
-            q = AL ? cc.width_p2_alpha(v[j], (L4 >> (8 * j)) & 0xFF, cm, aoff, axj)
-                   : cc.width_p2(v[j], (L4 >> (8 * j)) & 0xFF, cm);
-        } else {
-            float t[M];
+            for (int m = 0; m < M; ++m) axj[m] = 0;
+            if (P2) {
+                q = AL ? cc.width_p2_alpha(v[j], (L4 >> (8 * j)) & 0xFF, cm, aoff, axj)
+                       : cc.width_p2(v[j], (L4 >> (8 * j)) & 0xFF, cm);
+            } else {
+                float t[M];
 #pragma unroll
-            for (int m = 0; m < M; ++m) t[m] = norm_t(v[j][m], cc.lo[m], cc.s[m]);
-            q = AL ? cc.width_alpha(t, (L4 >> (8 * j)) & 0xFF, s_tf,
-                                    reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(s_tf) + aoff), axj)
-                   : cc.width(t, (L4 >> (8 * j)) & 0xFF, s_tf);
-        }
-        if (FULLSTEP || idx + j < a.n) {
-            acc += q;
-            if (AL) {
+                for (int m = 0; m < M; ++m) t[m] = norm_t(v[j][m], cc.lo[m], cc.s[m]);
+                q = AL ? cc.width_alpha(t, (L4 >> (8 * j)) & 0xFF, s_tf,
+                                        reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(s_tf) + aoff), axj)
+                       : cc.width(t, (L4 >> (8 * j)) & 0xFF, s_tf);
+            }
+            if (FULLSTEP || idx + j < a.n) {
+                acc += q;
+                if (AL) {
 #pragma unroll
-                for (int m = 0; m < M; ++m) ax[m] += axj[m];
+                    for (int m = 0; m < M; ++m) ax[m] += axj[m];
+                }
             }
         }
     }
@@ -301,7 +301,9 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
 // warp's next chunk, so a warp's loads never wait on its own arithmetic and
 // the bytes in flight cost no registers.  Step totals come from two warp
 // reductions per step.  Partial chunks (the data set's end) read global
-// memory directly.
+// memory directly.  A wait that runs out (bounded polls) stops the warp: it
+// waits once more, bounded, for each copy it still has in flight, raises
+// ERR_TIMEOUT and returns.
 constexpr uint32_t RING_WAIT_POLLS = 4096;      // mbarrier polls (<= 1 ms each) before a wait gives up
 
 // Requests warp step idx into a slot: lanes 0..M-1 copy one field row each,
@@ -357,9 +359,11 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
         mbar_init_fence();
     }
     __syncwarp();
+    int inflight = 0;                  // copies issued and not yet consumed (warp-uniform)
     if (cur_full) {
 #pragma unroll
         for (int k = 0; k < D; ++k) ring_issue<M>(lane, ring_s + k * SLOT, bar_s + 8u * k, a, chunk * CHUNK + k * STEP);
+        inflight = D;
     }
     load_table<M>(s_tf, a.tf, a.T);
     if (AL) load_table_fx<M>(reinterpret_cast<uint32_t*>(smem + aoff), a.tf, a.T);
@@ -395,8 +399,13 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
         if (cur_full) {
 #pragma unroll 1
             for (int st = 0; st < STEPS; ++st) {
-                if (!late) late = !mbar_wait(bar_s + 8u * k, phase, RING_WAIT_POLLS);   // after one
-                float v[4][M];                                                         // give-up: no more waits
+                // a wait that runs out (for any lane) ends the warp's work
+                if (!__all_sync(FULL, mbar_wait(bar_s + 8u * k, phase, RING_WAIT_POLLS))) {
+                    late = true;
+                    break;
+                }
+                --inflight;
+                float v[4][M];
                 const float4* f4 = reinterpret_cast<const float4*>(ring + k * SLOT);
 #pragma unroll
                 for (int m = 0; m < M; ++m) {
@@ -407,10 +416,13 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
                 __syncwarp();             // every lane has read the slot
                 {
                     const int s2 = st + D;
-                    if (s2 < STEPS)
+                    if (s2 < STEPS) {
                         ring_issue<M>(lane, ring_s + k * SLOT, bar_s + 8u * k, a, base + s2 * STEP);
-                    else if (nxt_full)
+                        ++inflight;
+                    } else if (nxt_full) {
                         ring_issue<M>(lane, ring_s + k * SLOT, bar_s + 8u * k, a, nxt * CHUNK + (s2 - STEPS) * STEP);
+                        ++inflight;
+                    }
                 }
                 uint32_t ax[M];
 #pragma unroll
@@ -432,6 +444,7 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
                     ring_issue<M>(lane, ring_s + kk * SLOT, bar_s + 8u * kk, a, nxt * CHUNK + j * STEP);
                     if (++kk == D) kk = 0;
                 }
+                inflight += D;
             }
             for (int st = 0; st < STEPS; ++st) {
                 const uint64_t idx = base + st * STEP + lane * 4;
@@ -446,6 +459,7 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
                 if (AL) alpha_step(ax, st);
             }
         }
+        if (late) break;
         if (a.step_sums && lane < STEPS) a.step_sums[chunk * STEPS + lane] = mine;
         if (lane == 0) a.chunk_prefix[chunk] = acc;
         if (AL) {
@@ -461,6 +475,14 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
         }
         chunk = nxt;
         cur_full = nxt_full;
+    }
+    if (late) {
+        // the copies still in flight fill the slots from k on, in order: each
+        // is waited for once more (bounded) before the warp stops
+        for (; inflight > 0; --inflight) {
+            mbar_wait(bar_s + 8u * k, phase, RING_WAIT_POLLS);
+            if (++k == D) { k = 0; phase ^= 1u; }
+        }
     }
     if ((late || injected) && lane == 0) atomicOr(a.err, ERR_TIMEOUT);
 }

@@ -186,9 +186,11 @@ def test_datasets_overlap_on_device():
     benchmark's serving record reports that share of busy time at the
     offered and the saturated load.  Every result still equals a plain
     update."""
-    a = synth.make("diff", box=((0, 0, 0), 48))
-    b = synth.make("diff", box=((16, 16, 16), 48))
-    assert a.n > 6_000_000 and b.n > 6_000_000
+    # data sets large enough that a batch's device time (~0.4 ms) exceeds the
+    # host time of launching the next one
+    a = synth.make("paper", box=((0, 0, 0), 48))
+    b = synth.make("paper", box=((16, 16, 16), 48))
+    assert a.n > 12_000_000 and b.n > 12_000_000
     reqs = [(i % 2, synth.random_tfs(4000 + i), 1024) for i in range(64)]
     with DVLServer(0, max_batch=8, max_inflight=2, max_width=1024) as srv:
         for d in (a, b):
