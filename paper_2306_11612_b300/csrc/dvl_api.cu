@@ -546,7 +546,7 @@ int dvl_build_order(dvl_ctx* c, int sfc)
     const uint64_t tiles = (n + TILE - 1) / TILE;
     // one status word per tile, and at least one per chunk-scan block and
     // quantity (the widths and each field's alpha sums)
-    const uint64_t scan_blocks = (tiles * WARPS + 2047) / 2048;
+    const uint64_t scan_blocks = (tiles * WARPS + 511) / 512;           // chunk-scan blocks of 512 chunks
     CK(dalloc(c->d_tile_status, std::max<uint64_t>(tiles, (1 + DVL_MAX_FIELDS) * scan_blocks)), "alloc scan state");
     CK(dalloc(c->d_chunk_prefix, tiles * WARPS), "alloc scan state");
     CK(dalloc(c->d_step_sums, tiles * WARPS * STEPS), "alloc scan state");

@@ -497,7 +497,7 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
 // look-back (quantity 0: widths, q >= 1: field q - 1's alphas; status words of
 // quantity q at status + q * gridDim.x), and the last block writes each
 // field's alpha total at achunk[m][n_chunks].
-constexpr int SCAN_THREADS = 256, SCAN_PER_THREAD = 8, SCAN_SPAN = SCAN_THREADS * SCAN_PER_THREAD;
+constexpr int SCAN_THREADS = 256, SCAN_PER_THREAD = 2, SCAN_SPAN = SCAN_THREADS * SCAN_PER_THREAD;
 constexpr int SCAN_Q = 1 + DVL_MAX_FIELDS;                 // quantities at most
 
 __global__ __launch_bounds__(SCAN_THREADS) void k_chunk_scan(UpdateArgs a, uint64_t n_chunks,
@@ -514,17 +514,28 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_chunk_scan(UpdateArgs a, uint6
     auto row_of = [&](int q) {
         return q == 0 ? a.chunk_prefix : a.achunk + (uint64_t)(q - 1) * (n_chunks + 1);
     };
-    // block-local scans: thread tid holds chunks b0 + tid*8 .. +8 of each quantity
+    // block-local scans: thread tid holds chunks b0 + tid*PER .. +PER of each
+    // quantity (kept in registers for the write-back)
     const uint64_t c0 = (uint64_t)b * SCAN_SPAN + (uint64_t)tid * SCAN_PER_THREAD;
-    unsigned long long tq[SCAN_Q], iq[SCAN_Q];
+    unsigned long long tq[SCAN_Q], iq[SCAN_Q], vq[SCAN_Q][SCAN_PER_THREAD];
 #pragma unroll
     for (int q = 0; q < SCAN_Q; ++q) {
         tq[q] = 0;
         iq[q] = 0;
+#pragma unroll
+        for (int j = 0; j < SCAN_PER_THREAD; ++j) vq[q][j] = 0;
         if (q < nq) {
             const unsigned long long* row = row_of(q);
 #pragma unroll
-            for (int j = 0; j < SCAN_PER_THREAD; ++j) tq[q] += c0 + j < n_chunks ? row[c0 + j] : 0ull;
+            for (int j = 0; j < SCAN_PER_THREAD; ++j) {
+                vq[q][j] = c0 + j < n_chunks ? row[c0 + j] : 0ull;
+                tq[q] += vq[q][j];
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < SCAN_Q; ++q) {
+        if (q < nq) {
             iq[q] = warp_incl_scan_u64(tq[q], lane);
             if (lane == 31) s_warp[q][warp] = iq[q];
         }
@@ -554,15 +565,11 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_chunk_scan(UpdateArgs a, uint6
             agg += s_warp[q][w];
         }
         unsigned long long* row = row_of(q);
-        unsigned long long v[SCAN_PER_THREAD];
-#pragma unroll
-        for (int j = 0; j < SCAN_PER_THREAD; ++j) v[j] = c0 + j < n_chunks ? row[c0 + j] : 0ull;
-        __syncwarp();
         unsigned long long run = s_excl[q] + wpre + iq[q] - tq[q];
 #pragma unroll
         for (int j = 0; j < SCAN_PER_THREAD; ++j) {
             if (c0 + j < n_chunks) row[c0 + j] = run;
-            run += v[j];
+            run += vq[q][j];
         }
         if (b == gridDim.x - 1 && tid == 0) {
             if (q == 0) {
