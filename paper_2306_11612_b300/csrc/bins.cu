@@ -37,17 +37,31 @@ typedef unsigned __int128 u128;
 constexpr int FX_BITS = 95;          // fixed-point fraction bits of t
 
 // floor(t * 2^95) for 0 <= t <= 1 (t a float32): t = mant * 2^(ex-150), so the
-// value is mant shifted left by ex - 150 + 95 (mant < 2^24, shift at most 72).
+// value is mant shifted left by sh = ex - 150 + 95 (mant < 2^24, sh <= 72).
+// Without branches (the lanes' cells differ in magnitude): PTX shifts clamp
+// amounts >= 64 (and negative amounts, read as unsigned) to 64, giving 0, so
+// lo = mant << sh or mant >> -sh and hi = mant << (sh - 64) or
+// mant >> (64 - sh) each take two shifts.  For a zero or subnormal t the
+// exponent field is 0, sh = -55 and every shift gives 0 (the value is below 1).
+__device__ __forceinline__ uint64_t shl_clamp(uint64_t x, uint32_t s)
+{
+    uint64_t r;
+    asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+    return r;
+}
+__device__ __forceinline__ uint64_t shr_clamp(uint64_t x, uint32_t s)
+{
+    uint64_t r;
+    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+    return r;
+}
 __device__ __forceinline__ u128 fx_of(float t)
 {
-    const uint32_t b = __float_as_uint(t);
-    const int ex = (int)(b >> 23);                    // t >= +0: no sign bit
-    if (ex == 0) return 0;                            // zero or subnormal: below 2^-126
+    const uint32_t b = __float_as_uint(t);              // t >= +0: no sign bit
     const uint64_t mant = (b & 0x7FFFFFu) | 0x800000u;
-    const int sh = ex - 150 + FX_BITS;
-    if (sh < 0) return sh > -24 ? (u128)(mant >> -sh) : (u128)0;
-    const uint64_t lo = sh < 64 ? mant << sh : 0ull;
-    const uint64_t hi = sh <= 40 ? 0ull : (sh < 64 ? mant >> (64 - sh) : mant << (sh - 64));
+    const int sh = (int)(b >> 23) - 150 + FX_BITS;
+    const uint64_t lo = shl_clamp(mant, (uint32_t)sh) | shr_clamp(mant, (uint32_t)-sh);
+    const uint64_t hi = shl_clamp(mant, (uint32_t)(sh - 64)) | shr_clamp(mant, (uint32_t)(64 - sh));
     return ((u128)hi << 64) | lo;
 }
 
@@ -502,27 +516,26 @@ __device__ __forceinline__ uint64_t find_chunk(const unsigned long long* prefix,
 // With alpha sums (qa.apart), also the fixed-point alpha sums of the same two
 // cell sets, the alpha of a cell from the CTA's shared tables s_tf (T + 1
 // entries per field).
+// tt[k][m]: the normalised values of the lane's 4 cells of the step (those
+// past the data set's end are not used).
 template <int M>
-__device__ __forceinline__ void step_partials(const UpdateArgs& a, const UpdateConsts* C, const QueryArgs& qa,
-                                              uint32_t j, uint64_t stb, uint64_t ste, uint64_t H, uint64_t first,
-                                              int lane, const float* s_tf)
+__device__ __forceinline__ void step_partials(const UpdateArgs& a, const QueryArgs& qa, uint32_t j, uint64_t stb,
+                                              uint64_t ste, uint64_t H, uint64_t first, int lane, const float* s_tf,
+                                              const float (&tt)[4][M])
 {
     const uint64_t idx = stb + lane * 4;
     const float Tf = (float)a.T;
     const uint32_t T1 = a.T + 1;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-        const float lo = C->lo[m], sc = C->s[m];
         u128 ts = 0, hs = 0;
         unsigned long long ta = 0, ha = 0;
         uint32_t tmn = 0x7F800000u, tmx = 0u, hmn = 0x7F800000u, hmx = 0u;
         if (idx < ste) {
-            const float4 x = __ldg(reinterpret_cast<const float4*>(a.val + m * a.pitch + idx));
-            const float c[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const uint64_t cell = idx + k;
-                const float t = norm_t(c[k], lo, sc);
+                const float t = tt[k][m];
                 const uint32_t tb = __float_as_uint(t);
                 const u128 f = fx_of(t);
                 const uint32_t af = qa.apart ? alpha_fx(s_tf[m * T1 + floor_small(__fmul_rn(t, Tf))]) : 0u;
@@ -581,9 +594,21 @@ __device__ __forceinline__ void bounds_one(const UpdateArgs& a, const QueryArgs&
     const u128 jF = (u128)j * F;
     unsigned long long H;
     bool S;
+    float tt[4][M];                                       // the normalised values of the lane's cells
     if (C->linear) {                                      // widths 1: E_c = c
         H = X < a.n ? X : a.n;
         S = H >= 1 && (u128)H * a.W > jF;
+        const uint64_t idx = (H - 1) / STEP * STEP + lane * 4;
+        if (H >= 1 && idx < a.n) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const float4 x = __ldg(reinterpret_cast<const float4*>(a.val + m * a.pitch + idx));
+                tt[0][m] = norm_t(x.x, C->lo[m], C->s[m]);
+                tt[1][m] = norm_t(x.y, C->lo[m], C->s[m]);
+                tt[2][m] = norm_t(x.z, C->lo[m], C->s[m]);
+                tt[3][m] = norm_t(x.w, C->lo[m], C->s[m]);
+            }
+        }
     } else {
         const uint64_t n_chunks = (a.n + CHUNK - 1) / CHUNK;
         const uint64_t chunk = find_chunk(qa.chunk_prefix, n_chunks, X, lane), base = chunk * CHUNK;
@@ -604,10 +629,9 @@ __device__ __forceinline__ void bounds_one(const UpdateArgs& a, const QueryArgs&
             load4<M>(a.val, a.pitch, a.lev, idx, v, L4);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                float t[M];
 #pragma unroll
-                for (int m = 0; m < M; ++m) t[m] = norm_t(v[c][m], cc.lo[m], cc.s[m]);
-                if (idx + c < a.n) q[c] = cc.width(t, (L4 >> (8 * c)) & 0xFF, s_tf);
+                for (int m = 0; m < M; ++m) tt[c][m] = norm_t(v[c][m], cc.lo[m], cc.s[m]);
+                if (idx + c < a.n) q[c] = cc.width(tt[c], (L4 >> (8 * c)) & 0xFF, s_tf);
             }
         }
         const unsigned long long lsum = (unsigned long long)q[0] + q[1] + q[2] + q[3];
@@ -635,7 +659,7 @@ __device__ __forceinline__ void bounds_one(const UpdateArgs& a, const QueryArgs&
     // partial terms over the step of cell H-1 (H >= 1: the step's first cell starts before X)
     const uint64_t stb = (H - 1) / STEP * STEP;
     const uint64_t ste = stb + STEP < a.n ? stb + STEP : a.n;
-    step_partials<M>(a, C, qa, j, stb, ste, H, S ? H - 1 : H, lane, s_tf);
+    step_partials<M>(a, qa, j, stb, ste, H, S ? H - 1 : H, lane, s_tf, tt);
     if (lane == 0) {
         qa.H[j] = H;
         qa.S[j] = S;
