@@ -116,19 +116,6 @@ __device__ __forceinline__ u128 fx_from_limbs(const uint32_t (&acc)[5], uint32_t
     return ((u128)L[0] << 72) + ((u128)L[1] << 49) + ((u128)L[2] << 26) + ((u128)L[3] << 3) + (u128)L[4];
 }
 
-// Warp sum of per-lane values below 2^120, exact: five 24-bit limbs, each
-// summed by one redux (32 x 2^24 < 2^32), then recombined.
-__device__ __forceinline__ u128 warp_sum_limbs(u128 x)
-{
-    u128 r = 0;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const uint32_t limb = (uint32_t)(x >> (24 * k)) & 0xFFFFFFu;
-        r += (u128)__reduce_add_sync(FULL, limb) << (24 * k);
-    }
-    return r;
-}
-
 __device__ __forceinline__ double fx_to_double(u128 x)
 {
     const double hi = (double)(uint64_t)(x >> 64), lo = (double)(uint64_t)x;
@@ -528,7 +515,9 @@ __device__ __forceinline__ void step_partials(const UpdateArgs& a, const QueryAr
     const uint32_t T1 = a.T + 1;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-        u128 ts = 0, hs = 0;
+        // the sums of floor(t 2^95) as five limb-bit sums (fx_limb_bits; float
+        // adds on the FMA pipe, then one 32-bit redux per limb)
+        uint32_t tl[5] = {0u, 0u, 0u, 0u, 0u}, hl[5] = {0u, 0u, 0u, 0u, 0u};
         unsigned long long ta = 0, ha = 0;
         uint32_t tmn = 0x7F800000u, tmx = 0u, hmn = 0x7F800000u, hmx = 0u;
         if (idx < ste) {
@@ -537,24 +526,32 @@ __device__ __forceinline__ void step_partials(const UpdateArgs& a, const QueryAr
                 const uint64_t cell = idx + k;
                 const float t = tt[k][m];
                 const uint32_t tb = __float_as_uint(t);
-                const u128 f = fx_of(t);
+                uint32_t r[5];
+                fx_limb_bits(t, r);
                 const uint32_t af = qa.apart ? alpha_fx(s_tf[m * T1 + floor_small(__fmul_rn(t, Tf))]) : 0u;
                 if (cell < H) {
-                    ts += f;
+#pragma unroll
+                    for (int z = 0; z < 5; ++z) tl[z] += r[z];
                     ta += af;
                     tmn = min(tmn, tb);
                     tmx = max(tmx, tb);
                 }
                 if (cell >= first && cell < ste) {
-                    hs += f;
+#pragma unroll
+                    for (int z = 0; z < 5; ++z) hl[z] += r[z];
                     ha += af;
                     hmn = min(hmn, tb);
                     hmx = max(hmx, tb);
                 }
             }
         }
-        ts = warp_sum_limbs(ts);
-        hs = warp_sum_limbs(hs);
+#pragma unroll
+        for (int z = 0; z < 5; ++z) {
+            tl[z] = __reduce_add_sync(FULL, tl[z]);
+            hl[z] = __reduce_add_sync(FULL, hl[z]);
+        }
+        const u128 ts = fx_from_limbs(tl, (uint32_t)(H - stb));      // cells [stb, H)
+        const u128 hs = fx_from_limbs(hl, (uint32_t)(ste - first));  // cells [first, ste)
         tmn = __reduce_min_sync(FULL, tmn);
         tmx = __reduce_max_sync(FULL, tmx);
         hmn = __reduce_min_sync(FULL, hmn);
