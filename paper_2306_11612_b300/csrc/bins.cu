@@ -106,6 +106,19 @@ __device__ __forceinline__ void fx_limb_bits2(float t, uint32_t& r0b, uint32_t& 
     r1b = __float_as_uint(__fadd_rz(z1, 0x1p72f));
 }
 
+// The third limb's bits alone (L0 and L1 as fx_limb_bits2 gives them), enough
+// with the first two for t = 0 and for t >= 2^-46: then t 2^95 >= 2^49 carries
+// its bits at 2^26 and above, so L3 and L4 are 0.
+__device__ __forceinline__ uint32_t fx_limb_bits_2(float t)
+{
+    const float z0 = __fmul_rn(t, 0x1p95f);
+    const float r0 = __fadd_rz(z0, 0x1p95f);
+    const float z1 = __fsub_rn(z0, __fsub_rn(r0, 0x1p95f));
+    const float r1 = __fadd_rz(z1, 0x1p72f);
+    const float z2 = __fsub_rn(z1, __fsub_rn(r1, 0x1p72f));
+    return __float_as_uint(__fadd_rz(z2, 0x1p49f));
+}
+
 // The sum of floor(t 2^95) over `count` cells from the limb-bit sums
 // (each limb's sum stays below 2^32 for count <= 256).
 __device__ __forceinline__ u128 fx_from_limbs(const uint32_t (&acc)[5], uint32_t count)
@@ -214,7 +227,7 @@ __device__ __noinline__ void vt_last_block_field(const ValueTableArgs& v, uint64
 // sum, min and max need no cross-lane reductions.  The sums are kept as five
 // 32-bit limb sums (fx_limb_bits), mostly from two limbs: a stage whose cells
 // all have t = 0 or t >= 2^-23 needs only L0 and L1; otherwise the warp
-// walks the stage again for all five.  The cells reach shared
+// walks the stage again for L2 alone (all t = 0 or >= 2^-46) or all five.  The cells reach shared
 // memory by bulk copies: a stage holds VQ cells of each of the block's 32
 // steps for one field (lane k's copy brings row k), VS stages per warp are
 // in flight, and a (block, field) takes STEP / VQ stages.  Lane k reads its
@@ -313,6 +326,19 @@ __global__ __launch_bounds__(VT_WARPS * 32) void k_vt_tx(ValueTableArgs v, uint6
             acc[1] += a1;
 #pragma unroll
             for (int q = 2; q < 5; ++q) acc[q] += (uint32_t)VQ * limb_c(q);    // zero limbs of VQ cells
+        } else if (__all_sync(FULL, okmin >= 0x287FFFFFu)) {                   // t = 0 or t >= 2^-46
+            acc[0] += a0;
+            acc[1] += a1;
+            uint32_t a2 = 0u;
+#pragma unroll 4
+            for (int c = 0; c < C4; ++c) {
+                const float4 x = row[(c + lane) & (C4 - 1)];
+                a2 += (fx_limb_bits_2(norm_t(x.x, lo, sc)) + fx_limb_bits_2(norm_t(x.y, lo, sc))) +
+                      (fx_limb_bits_2(norm_t(x.z, lo, sc)) + fx_limb_bits_2(norm_t(x.w, lo, sc)));
+            }
+            acc[2] += a2;
+#pragma unroll
+            for (int q = 3; q < 5; ++q) acc[q] += (uint32_t)VQ * limb_c(q);
         } else {
 #pragma unroll 4
             for (int c = 0; c < C4; ++c) {
