@@ -16,8 +16,11 @@
  * batch or on the GPU (the batched path is exact integer arithmetic).
  *
  * Threading: one scheduler thread per server drives all GPU work; the calls
- * below may come from any host threads.  All functions return DVL_OK or a
- * negative dvl_status code (dvl.h). */
+ * below may come from any host threads.  For low latency the scheduler polls
+ * (one host core busy) while batches are in flight and for 0.3 ms after its
+ * last activity, then sleeps until a request arrives; dvl_server_wait polls
+ * its request for up to 2 ms before it sleeps.  All functions return DVL_OK
+ * or a negative dvl_status code (dvl.h). */
 #ifndef DVL_SERVE_H
 #define DVL_SERVE_H
 
