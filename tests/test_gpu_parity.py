@@ -96,6 +96,30 @@ def test_ragged_sizes(n):
     check_update(lo, lev, fields, alpha, oracle.SFC_HILBERT, P=1.0, width=512)
 
 
+def test_fixed_point_sums_across_magnitudes():
+    """The value tables keep the exact sums of floor(t 2^95) in five 23-bit
+    limbs and skip the lower ones for stretches of cells whose t is 0 or at
+    least 2^-23 (two limbs) or 2^-46 (three).  With the TF domain [0, 1], t
+    equals the field value, so spatially smooth fields put whole runs of
+    pixels in each regime: t from 1 down to 2^-130 (subnormals, and values
+    whose bits lie only in the lowest limbs), t in [2^-46, 2^-23), exact
+    zeros next to 2^-70, and a random mix.  Sums must match the oracle to
+    1e-5 relative in every pixel, the tiniest included."""
+    n = 300_000
+    lower, level, _ = _random_amr(77, n, 1)
+    rng = np.random.default_rng(78)
+    x, y, z = (lower.astype(np.float64) + 0.5) / 1024.0
+    f = np.empty((4, n), np.float32)
+    f[0] = np.exp2(-130.0 * x).astype(np.float32)
+    f[1] = np.where(x < 0.5, 0.75, np.exp2(-40.0) * (1.0 + y)).astype(np.float32)
+    f[2] = np.where(z < 0.5, 0.0, np.exp2(-70.0) * (1.0 + x)).astype(np.float32)
+    f[3] = (rng.random(n) * np.exp2(-60.0 * rng.random(n))).astype(np.float32)
+    dom = (np.zeros(4, np.float32), np.ones(4, np.float32))
+    alpha = synth.random_tfs(79)
+    for W in (1024, 8192):
+        check_update(lower, level, f, alpha, oracle.SFC_HILBERT, dom=dom, P=1.0, width=W)
+
+
 @pytest.mark.parametrize("M", [1, 2, 3, 5, 8])
 def test_field_counts(M):
     lo, lev, fields = _random_amr(100 + M, 30000, M)
