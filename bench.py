@@ -46,6 +46,10 @@ sys.path.insert(0, ROOT)
 # (64 B), all over the 4 fields, and the bins written (4 x 24 + 4 B).
 SCAN_BYTES = 8 / 128 + 8 / 2048
 BYTES_PASS_A = 4 * 4 + 1 + SCAN_BYTES
+# With the kept per-cell TF entries (tables of <= 256 entries, the default)
+# the width pass reads one entry byte per field and the level byte instead of
+# the field values: 4 + 1 B/cell plus the totals it writes.
+BYTES_PASS_A_ENT = 4 * 1 + 1 + SCAN_BYTES
 BYTES_BOUNDS_PER_PIXEL = 128 * 17 + 16 * 8 + 3 * 32 * 8 + 8 + 1 + 2 * 4 * 24
 BYTES_PIXELS_PER_PIXEL = 2 * 9 + 2 * 4 * 24 + 2 * 4 * 16 + 4 * 4 * 4 + 4 * 24 + 4
 BYTES_BINS_PER_PIXEL = BYTES_BOUNDS_PER_PIXEL + BYTES_PIXELS_PER_PIXEL
@@ -54,6 +58,9 @@ BYTES_BINS_PER_PIXEL = BYTES_BOUNDS_PER_PIXEL + BYTES_PIXELS_PER_PIXEL
 # 8-B (min, max) pairs written (4 x 40 / 128 B/cell); block arrays are
 # 1/32 of that.
 BYTES_TABLES = 4 * 4 + 4 * 40 / 128 * (1 + 1 / 32)
+# with the entries: the entry kernel reads the fields again (16 B/cell) and
+# writes one byte per field
+BYTES_TABLES_ENT = BYTES_TABLES + 4 * 4 + 4
 CPU_SAMPLE_BOX = ((0, 0, 0), 32)     # 32^3 of the 128^3 base cells (1/64 of the domain)
 LAUNCHES_PER_UPDATE = 5              # prepare, width pass, chunk scan, pixel bounds, pixel bins
 LOG_FIELDS = (0, 2, 3)                   # dens, pres, velmag on the log10 scale
@@ -378,6 +385,33 @@ def run_ours(args):
                 "p99_ms": sorted(tail)[min(len(tail) - 1, int(0.99 * len(tail)))],
                 "edits": f"{len(per_edit) - len(tail)}..{len(per_edit) - 1}"}
     stages = ctx.get_timings()
+    ent = bool(ctx.get_stats()["entries"])
+    bytes_pass_a = BYTES_PASS_A_ENT if ent else BYTES_PASS_A
+    bytes_tables = BYTES_TABLES_ENT if ent else BYTES_TABLES
+    # the same edits with the width pass streaming the field values instead of
+    # the kept entries (DVL_OPT_ENTRIES = 0), for comparison
+    field_stream = None
+    if ent:
+        ctx.set_option(dvl.OPT_ENTRIES, 0)
+        for i in range(2):
+            ctx.set_tfs(tfs[i % len(tfs)])
+            ctx.update(**kw)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for i in range(10):
+            ctx.set_tfs(tfs[i % len(tfs)])
+            ctx.update(**kw)
+        f1.record(stream)
+        f1.synchronize()
+        fs = ctx.get_timings()
+        field_stream = {"ms_per_edit": f0.elapsed_time(f1) / 10, "pass_a_ms": fs["pass_a"],
+                        "pass_a_gbs": BYTES_PASS_A * amr.n / (fs["pass_a"] * 1e-3) / 1e9,
+                        "note": "DVL_OPT_ENTRIES = 0: the width pass reads the field values (17 B/cell)"}
+        ctx.set_option(dvl.OPT_ENTRIES, 1)
+        ctx.set_tfs(tfs[0])
+        ctx.update(**kw)
+        ctx.sync()
+        ctx.get_timings()
     # TF-domain edits: every field's [lo, hi] moves, so each update first
     # rebuilds the value tables (once per domain) and then runs as usual
     dlo, dhi = ctx.read_data_range()
@@ -484,7 +518,7 @@ def run_ours(args):
     peak, peak_kind = measured_peak()
     traffic = traffic_record()
     kern = {}
-    alg = {"dvl_pass_a": BYTES_PASS_A * amr.n, "dvl_bins": BYTES_BINS_PER_PIXEL * args.width}
+    alg = {"dvl_pass_a": bytes_pass_a * amr.n, "dvl_bins": BYTES_BINS_PER_PIXEL * args.width}
     for name, key in [("dvl_pass_a", "pass_a"), ("dvl_bins", "pass_b")]:
         t_ms = stages[key]
         gbs = alg[name] / (t_ms * 1e-3) / 1e9
@@ -496,6 +530,7 @@ def run_ours(args):
                 "frac": kern[dom]["achieved_gbs"] / peak, "kernel": dom,
                 "traffic": None if tr is None else tr["dram_bytes_per_cell"] * amr.n,
                 "algorithmic_bytes": alg[dom],
+                "streamed": "per-cell TF entries and levels (5 B/cell)" if ent else "field values and levels (17 B/cell)",
                 "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json), burst copy" if peak_kind == "measured"
                 else "fallback 6.4 TB/s"}
     step_gbs = edit_bytes / (ms / args.steps * 1e-3) / 1e9
@@ -507,14 +542,16 @@ def run_ours(args):
             "kernels": dict(kern, prepare_ms=stages["prepare"], finalize_ms=stages["finalize"],
                             edit_bytes_per_cell=edit_bytes / amr.n, edit_gbs=step_gbs, edit_frac=step_gbs / peak,
                             first_update_ms_with_value_tables=t_first,
+                            field_stream=field_stream,
                             domain_change=dict(
                                 ms_per_edit=dom_ms, wall_ms_per_edit=dom_wall_ms, edits=n_dom,
                                 value_tables_ms=dom_stages["prepare"] - stages["prepare"],
-                                tables_gbs=BYTES_TABLES * amr.n / ((dom_stages["prepare"] - stages["prepare"]) * 1e-3) / 1e9,
-                                tables_frac=BYTES_TABLES * amr.n / ((dom_stages["prepare"] - stages["prepare"]) * 1e-3)
+                                tables_gbs=bytes_tables * amr.n / ((dom_stages["prepare"] - stages["prepare"]) * 1e-3) / 1e9,
+                                tables_frac=bytes_tables * amr.n / ((dom_stages["prepare"] - stages["prepare"]) * 1e-3)
                                 / 1e9 / peak,
-                                note="set_tfs with new [lo, hi] for every field + dvl_update (value tables rebuilt "
-                                     "inside the update); device time by CUDA events, wall time on the host"),
+                                note="set_tfs with new [lo, hi] for every field + dvl_update (value tables and "
+                                     "per-cell TF entries rebuilt inside the update); device time by CUDA events, "
+                                     "wall time on the host"),
                             rasterize_ms=raster_ms, rasterize_image=f"{RASTER_H} x {args.width}, 4 polylines + bars",
                             brush_ms=brush_ms, brush_cells=roi["n_cells"], select_keys_ms=select_ms,
                             log_scale={"fields": "dens, pres, velmag", "set_scale_ms_per_field": log_set_ms,
@@ -1073,6 +1110,7 @@ DIFF_W, DIFF_K = 2048, 64
 # queries.  The adjoint reads the fields once more (16 B; the levels only at
 # pixel crossings) with the per-pixel gradients from L2.
 DIFF_FWD_BYTES = 17 + SCAN_BYTES + 4 * 8 / 128 + 4 * 8 / 2048
+DIFF_FWD_BYTES_ENT = DIFF_FWD_BYTES - 4 * 3    # entries: 1 B per field instead of 4
 DIFF_BWD_BYTES = 16
 
 
@@ -1140,9 +1178,12 @@ def run_diff(args, emit=True):
     b.record(stream)
     b.synchronize()
     parts["adjoint_ms"] = a.elapsed_time(b) / 10
+    ctx.update(want_alpha=1, **kw)
+    ent = bool(ctx.get_stats()["entries"])
     ctx.close()
     peak, _ = measured_peak()
-    fwd_gbs = DIFF_FWD_BYTES * amr.n / (parts["forward_ms"] * 1e-3) / 1e9
+    fwd_bytes = DIFF_FWD_BYTES_ENT if ent else DIFF_FWD_BYTES
+    fwd_gbs = fwd_bytes * amr.n / (parts["forward_ms"] * 1e-3) / 1e9
     bwd_gbs = DIFF_BWD_BYTES * amr.n / (parts["adjoint_ms"] * 1e-3) / 1e9
     line = {"metric": "TF-tuning gradient step (forward alpha means + adjoint), cells/s", "value": amr.n / (ms * 1e-3),
             "unit": "cells/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -1154,6 +1195,7 @@ def run_diff(args, emit=True):
             "parts": parts, "final_loss": float(loss.item()),
             "roofline": {"bound": "hbm", "kernel": "forward (pass A with alpha sums, range-query bins)",
                          "achieved": fwd_gbs, "peak": peak, "unit": "GB/s", "frac": fwd_gbs / peak,
+                         "algorithmic_bytes_per_cell": fwd_bytes,
                          "traffic": None, "adjoint_gbs": bwd_gbs, "adjoint_frac": bwd_gbs / peak},
             "clocks": clk.summary(), "e2e": None,
             # forward: control-point tables, prepare, width pass, chunk scan, alpha-means placement,

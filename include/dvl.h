@@ -114,6 +114,9 @@ typedef struct {
     uint64_t n_cells;
     uint32_t n_fields;
     uint32_t max_level;
+    uint32_t entries;    /* 1 if the width pass streamed the cells' kept TF
+                            entries (DVL_OPT_ENTRIES), 0 if their field values */
+    uint32_t pad;
 } dvl_stats;
 
 /* Creates a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -309,8 +312,16 @@ int dvl_get_timings(dvl_ctx* ctx, double* ms, int n);
  *                           dvl_update (read with dvl_get_timings); 0 = off
  *                           (default).  A timed dvl_update_batch runs its
  *                           kernels as plain launches instead of the graph
- *                           (stages: prepare, pass A, bins, -). */
-enum { DVL_OPT_SPIN_LIMIT = 1, DVL_OPT_FAULT_NO_PUBLISH = 2, DVL_OPT_TIMING = 3 };
+ *                           (stages: prepare, pass A, bins, -).
+ *   DVL_OPT_ENTRIES         1 (default) = with alpha tables of at most 256
+ *                           entries, dvl_update keeps each cell's TF entry per
+ *                           field (n_fields bytes a cell, built in the first
+ *                           update after a TF-domain, table-size or data
+ *                           change, like the value tables) and its width pass
+ *                           reads those instead of the field values; 0 = the
+ *                           width pass reads the field values.  The results
+ *                           are the same bit for bit. */
+enum { DVL_OPT_SPIN_LIMIT = 1, DVL_OPT_FAULT_NO_PUBLISH = 2, DVL_OPT_TIMING = 3, DVL_OPT_ENTRIES = 4 };
 int dvl_set_option(dvl_ctx* ctx, int option, int64_t value);
 
 /* Line-plot image of the bins of the last dvl_update (the RasterizeLines

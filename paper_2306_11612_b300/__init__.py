@@ -27,7 +27,7 @@ MEM_HOST, MEM_DEVICE = 0, 1
 MINIMP_BEFORE_SCALE, MINIMP_AFTER_POWER = 0, 1
 VMAX_APPROX, VMAX_EXACT = 0, 1
 WIDTH_EDGE, WIDTH_VOLUME = 0, 1
-OPT_SPIN_LIMIT, OPT_FAULT_NO_PUBLISH, OPT_TIMING = 1, 2, 3
+OPT_SPIN_LIMIT, OPT_FAULT_NO_PUBLISH, OPT_TIMING, OPT_ENTRIES = 1, 2, 3, 4
 PLOT_MEAN, PLOT_Y = 0, 1
 SCALE_LINEAR, SCALE_LOG10 = 0, 1
 
@@ -82,7 +82,8 @@ class dvl_stats(ctypes.Structure):
     _fields_ = [("vmax", ctypes.c_float), ("inv_vmax", ctypes.c_float), ("f_upper", ctypes.c_float),
                 ("Q", ctypes.c_int32), ("i", ctypes.c_int32), ("j", ctypes.c_int32),
                 ("linear", ctypes.c_int32), ("pow_exact", ctypes.c_int32), ("F", ctypes.c_uint64),
-                ("n_cells", ctypes.c_uint64), ("n_fields", ctypes.c_uint32), ("max_level", ctypes.c_uint32)]
+                ("n_cells", ctypes.c_uint64), ("n_fields", ctypes.c_uint32), ("max_level", ctypes.c_uint32),
+                ("entries", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 def _load():

@@ -307,6 +307,55 @@ struct Cell {
         qb = __float2uint_rn(f.y);
     }
 
+    // The width from the cell's TF entries e[m] (precomputed for the TF
+    // domain: min(floor(t T), T - 1), the entry every path above reads),
+    // tb[m] = shared address of field m's table; the same value as width().
+    __device__ __forceinline__ uint32_t width_ent(const uint32_t* e, uint32_t L, const uint32_t* tb) const
+    {
+        float al[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) al[m] = lds_f32(tb[m] + 4u * e[m]);
+        float f = importance<PM>(spread<M>(al), L, inv_vmax, mb, ma, wshift, n2, P);
+        return __float2uint_rn(__fmul_rn(f, qscale));
+    }
+
+    // width_ent of two cells at once (P = 1), Eq. 3's arithmetic in
+    // float32x2 form as in width2_p2.  AL: also returns each field's
+    // fixed-point alpha of the two cells (the u32 twin tables lie `aoff`
+    // bytes after the float ones).
+    template <bool AL>
+    //   four = 4 and w23 = wshift << 23 are run-time values, so that the
+    // table addresses (tb + 4 e) and the level factors (the bits of
+    // 2^(L wshift) = L (wshift << 23) + bits(1)) are integer multiply-adds on
+    // the FMA pipe rather than shifts and adds on the busier integer pipe.
+    __device__ __forceinline__ void width2_ent(const uint32_t* ea, const uint32_t* eb, uint32_t La, uint32_t Lb,
+                                               const uint32_t* tb, uint32_t aoff, uint32_t (&axa)[M],
+                                               uint32_t (&axb)[M], uint32_t& qa, uint32_t& qb, uint32_t four,
+                                               uint32_t w23) const
+    {
+        float ala[M], alb[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const uint32_t adra = ea[m] * four + tb[m], adrb = eb[m] * four + tb[m];
+            ala[m] = lds_f32(adra);
+            alb[m] = lds_f32(adrb);
+            if (AL) {
+                axa[m] = lds_u32(adra + aoff);
+                axb[m] = lds_u32(adrb + aoff);
+            }
+        }
+        float ha, la, hb, lb;
+        spread_ends<M>(ala, ha, la);
+        spread_ends<M>(alb, hb, lb);
+        const float2 V = sub2(make_float2(ha, hb), make_float2(la, lb));
+        const float2 r0 = mul2(V, make_float2(inv_vmax, inv_vmax));
+        const float2 r = make_float2(fmaxf(r0.x, mb), fmaxf(r0.y, mb));
+        const float2 x = mul2(r, make_float2(__uint_as_float(La * w23 + 0x3F800000u), __uint_as_float(Lb * w23 + 0x3F800000u)));
+        const float2 f = mul2(make_float2(fmaxf(x.x, ma), fmaxf(x.y, ma)), make_float2(qscale, qscale));
+        qa = __float2uint_rn(f.x);
+        qb = __float2uint_rn(f.y);
+    }
+
     // width_p2, also adding each field's fixed-point alpha (alpha_fx of the
     // same entry, from a second table `aoff` bytes after the first) to ax[m]
     __device__ __forceinline__ uint32_t width_p2_alpha(const float* v, uint32_t L, const uint32_t* cm, uint32_t aoff,

@@ -91,6 +91,13 @@ struct dvl_ctx {
     ValueTableArgs vt{};
     bool vt_valid = false;
     std::vector<float> vt_dom;
+    // per-cell TF entries (M x pitch bytes) for the domains ent_dom and T = ent_T
+    uint8_t* d_ent = nullptr;
+    bool ent_valid = false;
+    std::vector<float> ent_dom;
+    uint32_t ent_T = 0;
+    int use_ent = 1;
+    bool last_ent = false;            // the last update's width pass streamed the entries
     unsigned long long* d_H = nullptr;
     uint8_t* d_S = nullptr;
     ulonglong2* d_psum = nullptr;     // boundary partial terms, 2 x M per boundary
@@ -211,6 +218,8 @@ void free_dataset(dvl_ctx* c)
     dfree(c->vt.loc); dfree(c->vt.blk); dfree(c->vt.raw); dfree(c->vt.pre); dfree(c->vt.suf); dfree(c->vt.bmm); dfree(c->vt.seg);
     c->vt = ValueTableArgs{};
     c->vt_valid = false;
+    dfree(c->d_ent);
+    c->ent_valid = false;
     free_batch(c);
     c->state = 0;
     c->have_update = false;
@@ -330,6 +339,7 @@ int gather_values(dvl_ctx* c, const uint8_t* lin, uint8_t* lout)
         if (rc) return rc;
     }
     c->vt_valid = false;
+    c->ent_valid = false;
     return DVL_OK;
 }
 
@@ -431,6 +441,9 @@ int dvl_set_option(dvl_ctx* c, int option, int64_t value)
             return DVL_OK;
         case DVL_OPT_TIMING:
             c->timing = value ? 1 : 0;
+            return DVL_OK;
+        case DVL_OPT_ENTRIES:
+            c->use_ent = value ? 1 : 0;
             return DVL_OK;
         default:
             return fail(c, DVL_ERR_ARG, "unknown option %d", option);
@@ -569,6 +582,7 @@ int dvl_build_order(dvl_ctx* c, int sfc)
         CK(dalloc(v.bmm, M * (v.b_levels ? (size_t)v.b_levels * v.n_blocks : 1)), "alloc value tables");
         CK(dalloc(v.seg, M * std::max<uint64_t>(value_table_segments(v.n_blocks), 1)), "alloc value tables");
         c->vt_valid = false;
+        c->ent_valid = false;
     }
     int rc = take_device_error(c);
     if (rc) return rc;
@@ -825,6 +839,8 @@ static UpdateArgs make_args(dvl_ctx* c, const dvl_params& p)
     a.apart = nullptr;
     a.vt = nullptr;
     a.vt_build = 0;
+    a.ent = nullptr;
+    a.ent_build = 0;
     a.H = c->d_H;
     a.S = c->d_S;
     a.psum = c->d_psum;
@@ -866,9 +882,19 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
     }
     const bool build_vt = !c->vt_valid || c->vt_dom.size() != c->h_dom.size() ||
                           std::memcmp(c->vt_dom.data(), c->h_dom.data(), c->h_dom.size() * sizeof(float)) != 0;
+    // per-cell TF entries (tables of <= 256 entries): kept per domain and T
+    const bool use_ent = c->use_ent && c->T <= 256 && c->n > 0;
+    bool build_ent = false;
+    if (use_ent) {
+        if (!c->d_ent) CK(dalloc(c->d_ent, (size_t)c->M * c->pitch), "alloc TF entries");
+        build_ent = !c->ent_valid || c->ent_T != c->T || c->ent_dom.size() != c->h_dom.size() ||
+                    std::memcmp(c->ent_dom.data(), c->h_dom.data(), c->h_dom.size() * sizeof(float)) != 0;
+    }
     UpdateArgs a = make_args(c, *p);
     a.vt = &c->vt;
     a.vt_build = build_vt ? 1 : 0;
+    a.ent = use_ent ? c->d_ent : nullptr;
+    a.ent_build = build_ent ? 1 : 0;
     if (p->want_alpha) {
         a.asum = c->d_asum;
         a.amean = c->d_amean;
@@ -887,6 +913,12 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
         c->vt_valid = true;
         c->vt_dom = c->h_dom;
     }
+    if (build_ent) {
+        c->ent_valid = true;
+        c->ent_dom = c->h_dom;
+        c->ent_T = c->T;
+    }
+    c->last_ent = use_ent;
     c->fault_no_publish = 0;
     c->W_last = p->width;
     c->last_prm = *p;
@@ -1193,6 +1225,8 @@ int dvl_get_stats(dvl_ctx* c, dvl_stats* out)
     out->n_cells = c->n;
     out->n_fields = c->M;
     out->max_level = meta.max_level;
+    out->entries = c->last_ent ? 1u : 0u;
+    out->pad = 0;
     return DVL_OK;
 }
 

@@ -187,6 +187,14 @@ struct UpdateArgs {
     // range-query bins (null vt: the placement pass k_passB* is used instead)
     const ValueTableArgs* vt;
     int vt_build;              // rebuild the value tables after k_prepare
+    // Per-cell TF entries for the current TF domains and T <= 256, M rows of
+    // pitch bytes in curve order: entry m of cell c = min(floor(t T), T - 1)
+    // (the alpha-table index of Sec. 3.3's normalised value).  They depend on
+    // the data, the domains and T only, so pass A streams them (M + 1 bytes a
+    // cell with the levels) instead of the field values.  Null: pass A reads
+    // the fields.
+    uint8_t* ent;
+    int ent_build;             // rebuild the entries after k_prepare
     unsigned long long* H;
     uint8_t* S;
     ulonglong2* psum;          // boundary partial sums (see QueryArgs)

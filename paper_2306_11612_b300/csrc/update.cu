@@ -151,6 +151,76 @@ __device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, con
     return widths4_of<M, PM, FULLSTEP, P2, AL>(cc, a, s_tf, cm, idx, v, L4, aoff, ax);
 }
 
+// Sum of the fixed-point widths of one lane's 4 cells from their TF entries
+// (E[m]: the 4 cells' entries of field m, one byte each, cell j in byte j);
+// AL: also adds their fixed-point alphas per field to ax.  Whole steps only.
+template <int M, int PM, bool AL>
+__device__ __forceinline__ unsigned long long widths4_ent(const Cell<M, PM>& cc, const uint32_t (&E)[M],
+                                                          uint32_t L4, const uint32_t* tb, uint32_t aoff,
+                                                          uint32_t* ax, uint32_t four, uint32_t w23)
+{
+    unsigned long long acc = 0;
+    if (PM == POW_ONE) {
+#pragma unroll
+        for (int j = 0; j < 4; j += 2) {
+            uint32_t ea[M], eb[M], axa[M], axb[M], qa, qb;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                ea[m] = (E[m] >> (8 * j)) & 0xFFu;
+                eb[m] = (E[m] >> (8 * j + 8)) & 0xFFu;
+            }
+            cc.template width2_ent<AL>(ea, eb, (L4 >> (8 * j)) & 0xFF, (L4 >> (8 * j + 8)) & 0xFF, tb, aoff, axa,
+                                       axb, qa, qb, four, w23);
+            acc += (unsigned long long)qa + qb;
+            if (AL) {
+#pragma unroll
+                for (int m = 0; m < M; ++m) ax[m] += axa[m] + axb[m];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint32_t e[M];
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                e[m] = (E[m] >> (8 * j)) & 0xFFu;
+                if (AL) ax[m] += lds_u32(tb[m] + 4u * e[m] + aoff);
+            }
+            acc += cc.width_ent(e, (L4 >> (8 * j)) & 0xFF, tb);
+        }
+    }
+    return acc;
+}
+
+// The TF entries of every cell for the current domains (k_prepare's lo and
+// s), T <= 256: the same entry as the width paths read, min(floor(t T), T),
+// with entry T (a copy of T - 1 in the tables) stored as T - 1.  Four cells
+// per thread; the rows' padding past the last cell is read and written too
+// (its entries are never used).
+template <int M>
+__global__ __launch_bounds__(256) void k_entries(UpdateArgs a)
+{
+    const UpdateConsts* C = a.consts;
+    const float Tf = (float)a.T;
+    const uint32_t Tm1 = a.T - 1;
+    const uint64_t n4 = (a.n + 3) / 4;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4; i += (uint64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const float lo = C->lo[m], sc = C->s[m];
+            const float4 x = __ldg(reinterpret_cast<const float4*>(a.val + m * a.pitch) + i);
+            const float c[4] = {x.x, x.y, x.z, x.w};
+            uint32_t packed = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t e = floor_small(__fmul_rn(norm_t(c[j], lo, sc), Tf));
+                packed |= (e < Tm1 ? e : Tm1) << (8 * j);
+            }
+            reinterpret_cast<uint32_t*>(a.ent + m * a.pitch)[i] = packed;
+        }
+    }
+}
+
 // One warp of a pass-A CTA, with the tile's chunk totals in lanes 0..7: chunk
 // offsets within the tile, the tile's exclusive prefix by decoupled look-back
 // (bounded waits), the chunk prefixes, and F after the last tile.
@@ -310,14 +380,24 @@ constexpr uint32_t RING_WAIT_POLLS = 4096;      // mbarrier polls (<= 1 ms each)
 // lane M the levels, lane 0 arms the barrier with the step's byte count (a
 // copy may complete first: the phase cannot end before that arrival).  Called
 // by the whole warp after every lane has finished reading the slot.
-template <int M>
+// EN: the field rows are the cells' TF entries (STEP bytes each) instead of
+// their values (4 STEP bytes).
+// With EN a slot holds EN_UNIT cells (4 warp steps): M entry rows and the
+// level row of EN_UNIT bytes each.
+constexpr int EN_UNIT = 4 * STEP;
+template <int M, bool EN>
 __device__ __forceinline__ void ring_issue(int lane, uint32_t slot, uint32_t bar, const UpdateArgs& a, uint64_t idx)
 {
+    constexpr uint32_t ROW = EN ? EN_UNIT : STEP * 4, LROW = EN ? EN_UNIT : STEP;
     if (lane <= M) {
         proxy_fence_shared();          // the warp's reads of the slot before the copy's writes
-        if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(M * STEP * 4 + STEP));
-        if (lane < M) bulk_g2s(slot + (uint32_t)(lane * STEP * 4), a.val + lane * a.pitch + idx, STEP * 4, bar);
-        else bulk_g2s(slot + (uint32_t)(M * STEP * 4), a.lev + idx, STEP, bar);
+        if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(M * ROW + LROW));
+        if (lane < M) {
+            if (EN) bulk_g2s(slot + (uint32_t)lane * ROW, a.ent + lane * a.pitch + idx, ROW, bar);
+            else bulk_g2s(slot + (uint32_t)lane * ROW, a.val + lane * a.pitch + idx, ROW, bar);
+        } else {
+            bulk_g2s(slot + (uint32_t)(M * ROW), a.lev + idx, LROW, bar);
+        }
     }
 }
 
@@ -325,11 +405,14 @@ __device__ __forceinline__ void ring_issue(int lane, uint32_t slot, uint32_t bar
 // AL: the cells' fixed-point alphas are summed per field as well (per step
 // into astep, per chunk into achunk); tf_bytes then covers the float tables
 // and their u32 twins (aoff = half of it).
-template <int M, int PM, bool P2, int D, int MINB, bool AL = false>
+// EN: whole steps stream the cells' TF entries (a.ent) instead of their
+// field values, M + 1 bytes a cell (partial chunks still read the fields).
+template <int M, int PM, bool P2, int D, int MINB, bool AL = false, bool EN = false>
 __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, uint64_t n_chunks, uint32_t tf_bytes)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    constexpr uint32_t SLOT = M * STEP * 4 + STEP;
+    constexpr uint32_t SLOT = EN ? (M + 1) * EN_UNIT : M * STEP * 4 + STEP;
+    constexpr int UNIT = EN ? EN_UNIT : STEP, UNITS = CHUNK / UNIT;   // cells per slot, slots per chunk
     float* s_tf = reinterpret_cast<float*>(smem);
     const uint32_t aoff = tf_bytes / 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -362,7 +445,7 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
     int inflight = 0;                  // copies issued and not yet consumed (warp-uniform)
     if (cur_full) {
 #pragma unroll
-        for (int k = 0; k < D; ++k) ring_issue<M>(lane, ring_s + k * SLOT, bar_s + 8u * k, a, chunk * CHUNK + k * STEP);
+        for (int k = 0; k < D; ++k) ring_issue<M, EN>(lane, ring_s + k * SLOT, bar_s + 8u * k, a, chunk * CHUNK + k * UNIT);
         inflight = D;
     }
     load_table<M>(s_tf, a.tf, a.T);
@@ -370,11 +453,16 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
     __syncthreads();
     Cell<M, PM> cc;
     cc.load(a.consts, a.T);
-    uint32_t cm[M];
+    uint32_t cm[M], tb[M];
     const uint32_t sb = (uint32_t)__cvta_generic_to_shared(s_tf);
 #pragma unroll
-    for (int m = 0; m < M; ++m) cm[m] = sb + 4u * (uint32_t)(m * (a.T + 1)) - 4u * BITS_2P23;
+    for (int m = 0; m < M; ++m) {
+        tb[m] = sb + 4u * (uint32_t)(m * (a.T + 1));
+        cm[m] = tb[m] - 4u * BITS_2P23;
+    }
     const uint64_t n_steps_all = n_chunks * STEPS;
+    // 4 and wshift << 23 as values the compiler cannot fold (see width2_ent)
+    const uint32_t four = 4u + (a.T >> 31), w23 = (uint32_t)cc.wshift << 23;
 
     int k = 0;                         // next slot to consume
     uint32_t phase = 0;                // its parity
@@ -398,7 +486,7 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
         };
         if (cur_full) {
 #pragma unroll 1
-            for (int st = 0; st < STEPS; ++st) {
+            for (int st = 0; st < UNITS; ++st) {
                 // a wait that runs out (for any lane) ends the warp's work
                 if (!__all_sync(FULL, mbar_wait(bar_s + 8u * k, phase, RING_WAIT_POLLS))) {
                     late = true;
@@ -406,34 +494,86 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
                 }
                 --inflight;
                 float v[4][M];
-                const float4* f4 = reinterpret_cast<const float4*>(ring + k * SLOT);
+                uint4 W4[M], LV;                // EN: the lane's 16 cells (one byte each)
+                uint32_t L4 = 0;
+                if constexpr (EN) {
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    const float4 x = f4[m * 32 + lane];
-                    v[0][m] = x.x; v[1][m] = x.y; v[2][m] = x.z; v[3][m] = x.w;
+                    for (int m = 0; m < M; ++m) W4[m] = reinterpret_cast<const uint4*>(ring + k * SLOT + m * EN_UNIT)[lane];
+                    LV = reinterpret_cast<const uint4*>(ring + k * SLOT + M * EN_UNIT)[lane];
+                } else {
+                    const float4* f4 = reinterpret_cast<const float4*>(ring + k * SLOT);
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        const float4 x = f4[m * 32 + lane];
+                        v[0][m] = x.x; v[1][m] = x.y; v[2][m] = x.z; v[3][m] = x.w;
+                    }
+                    L4 = reinterpret_cast<const uint32_t*>(ring + k * SLOT + M * STEP * 4)[lane];
                 }
-                const uint32_t L4 = reinterpret_cast<const uint32_t*>(ring + k * SLOT + M * STEP * 4)[lane];
                 __syncwarp();             // every lane has read the slot
                 {
                     const int s2 = st + D;
-                    if (s2 < STEPS) {
-                        ring_issue<M>(lane, ring_s + k * SLOT, bar_s + 8u * k, a, base + s2 * STEP);
+                    if (s2 < UNITS) {
+                        ring_issue<M, EN>(lane, ring_s + k * SLOT, bar_s + 8u * k, a, base + s2 * UNIT);
                         ++inflight;
                     } else if (nxt_full) {
-                        ring_issue<M>(lane, ring_s + k * SLOT, bar_s + 8u * k, a, nxt * CHUNK + (s2 - STEPS) * STEP);
+                        ring_issue<M, EN>(lane, ring_s + k * SLOT, bar_s + 8u * k, a, nxt * CHUNK + (s2 - UNITS) * UNIT);
                         ++inflight;
                     }
                 }
-                uint32_t ax[M];
+                if constexpr (EN) {
+                    // lane l holds cells 16 l .. 16 l + 15 of the slot: lanes
+                    // 8 g .. 8 g + 7 make up warp step 4 st + g
+                    unsigned long long l = 0, ax64[M];
 #pragma unroll
-                for (int m = 0; m < M; ++m) ax[m] = 0;
-                const unsigned long long l =
-                    widths4_of<M, PM, true, P2, AL>(cc, a, s_tf, cm, base + st * STEP + lane * 4, v, L4, aoff, ax);
-                const unsigned long long tot = warp_total_small(l);
-                if (lane == st) mine = tot;
-                acc += tot;
-                if (AL) alpha_step(ax, st);
+                    for (int m = 0; m < M; ++m) ax64[m] = 0;
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        uint32_t E[M], ax[M];
+#pragma unroll
+                        for (int m = 0; m < M; ++m) {
+                            E[m] = w == 0 ? W4[m].x : w == 1 ? W4[m].y : w == 2 ? W4[m].z : W4[m].w;
+                            ax[m] = 0;
+                        }
+                        const uint32_t L = w == 0 ? LV.x : w == 1 ? LV.y : w == 2 ? LV.z : LV.w;
+                        l += widths4_ent<M, PM, AL>(cc, E, L, tb, aoff, ax, four, w23);
+                        if (AL) {
+#pragma unroll
+                            for (int m = 0; m < M; ++m) ax64[m] += ax[m];
+                        }
+                    }
+                    // step totals: sums over the lane groups of 8; lane st'
+                    // (of steps 4 st .. 4 st + 3) keeps step st''s total
+#pragma unroll
+                    for (int o = 1; o < 8; o <<= 1) l += __shfl_xor_sync(FULL, l, o);
+                    const unsigned long long tot = __shfl_sync(FULL, l, 8 * (lane & 3));
+                    if ((lane >> 2) == st) mine = tot;
+                    acc += l;                 // the lane group's steps; groups combined at the chunk's end
+                    if (AL) {
+#pragma unroll
+                        for (int m = 0; m < M; ++m) {
+                            unsigned long long t = ax64[m];
+#pragma unroll
+                            for (int o = 1; o < 8; o <<= 1) t += __shfl_xor_sync(FULL, t, o);
+                            t = __shfl_sync(FULL, t, 8 * (lane & 3));
+                            if ((lane >> 2) == st) amine[m] = t;
+                        }
+                    }
+                } else {
+                    uint32_t ax[M];
+#pragma unroll
+                    for (int m = 0; m < M; ++m) ax[m] = 0;
+                    const unsigned long long l =
+                        widths4_of<M, PM, true, P2, AL>(cc, a, s_tf, cm, base + st * STEP + lane * 4, v, L4, aoff, ax);
+                    const unsigned long long tot = warp_total_small(l);
+                    if (lane == st) mine = tot;
+                    acc += tot;
+                    if (AL) alpha_step(ax, st);
+                }
                 if (++k == D) { k = 0; phase ^= 1u; }
+            }
+            if constexpr (EN) {
+                acc += __shfl_xor_sync(FULL, acc, 8);     // the 4 lane groups' sums: the chunk total
+                acc += __shfl_xor_sync(FULL, acc, 16);
             }
         } else {
             if (nxt_full) {
@@ -441,7 +581,7 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
                 int kk = k;
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
-                    ring_issue<M>(lane, ring_s + kk * SLOT, bar_s + 8u * kk, a, nxt * CHUNK + j * STEP);
+                    ring_issue<M, EN>(lane, ring_s + kk * SLOT, bar_s + 8u * kk, a, nxt * CHUNK + j * UNIT);
                     if (++kk == D) kk = 0;
                 }
                 inflight += D;
@@ -1306,13 +1446,16 @@ int grid_cap(uint64_t work, int threads)
 // and 5 CTAs with a 48-register cap were 0.5-1.5 % slower.)
 template <int M> constexpr int ring_depth() { return 2; }
 template <int M> constexpr int ring_min_blocks() { return M <= 4 ? 4 : 2; }
+// streaming the entries: slots of (M + 1) x 512 bytes, kept 2 deep
+template <int M> constexpr int ring_depth_ent() { return 2; }
 
 template <int M>
-size_t ring_smem(uint32_t T, uint32_t* tf_bytes, bool alpha = false)
+size_t ring_smem(uint32_t T, uint32_t* tf_bytes, bool alpha = false, bool ent = false)
 {
     // the float tables, and with alpha their u32 fixed-point twins
     *tf_bytes = (uint32_t)(((size_t)M * (T + 1) * sizeof(float) + 127) & ~(size_t)127) * (alpha ? 2u : 1u);
-    return *tf_bytes + (size_t)WARPS * ring_depth<M>() * (M * STEP * 4 + STEP + 8) + 8;
+    const size_t slot = ent ? (size_t)(M + 1) * EN_UNIT : (size_t)M * STEP * 4 + STEP;
+    return *tf_bytes + (size_t)WARPS * (ent ? ring_depth_ent<M>() : ring_depth<M>()) * (slot + 8) + 8;
 }
 
 // The persistent grid: as many CTAs as are resident at once (the occupancy of
@@ -1343,12 +1486,16 @@ cudaError_t resident_ctas(K kernel, size_t smem, int* out)
 template <int M, int PM>
 cudaError_t launch_passA_ring(cudaStream_t s, const UpdateArgs& a, uint32_t n_tiles, bool p2)
 {
-    constexpr int D = ring_depth<M>(), MB = ring_min_blocks<M>();
-    const bool alpha = a.astep != nullptr;
+    constexpr int D = ring_depth<M>(), MB = ring_min_blocks<M>(), DE = ring_depth_ent<M>();
+    const bool alpha = a.astep != nullptr, ent = a.ent != nullptr;
     uint32_t tf_bytes;
-    const size_t smem = ring_smem<M>(a.T, &tf_bytes, alpha);
-    auto kernel = alpha ? (p2 ? k_passA_ring<M, PM, true, D, MB, true> : k_passA_ring<M, PM, false, D, MB, true>)
-                        : (p2 ? k_passA_ring<M, PM, true, D, MB> : k_passA_ring<M, PM, false, D, MB>);
+    const size_t smem = ring_smem<M>(a.T, &tf_bytes, alpha, ent);
+    // (p2 also selects the partial chunks' entry computation in the entry-streaming kernels)
+    auto kernel =
+        ent ? (alpha ? (p2 ? k_passA_ring<M, PM, true, DE, MB, true, true> : k_passA_ring<M, PM, false, DE, MB, true, true>)
+                     : (p2 ? k_passA_ring<M, PM, true, DE, MB, false, true> : k_passA_ring<M, PM, false, DE, MB, false, true>))
+            : alpha ? (p2 ? k_passA_ring<M, PM, true, D, MB, true> : k_passA_ring<M, PM, false, D, MB, true>)
+                    : (p2 ? k_passA_ring<M, PM, true, D, MB> : k_passA_ring<M, PM, false, D, MB>);
     cudaError_t e;
     if ((e = smem_attr(kernel, smem)) != cudaSuccess) return e;
     int grid = 0;
@@ -1411,6 +1558,7 @@ cudaError_t run_update(cudaStream_t s, const UpdateArgs& a)
     if (a.vt && a.vt_build) {
         if ((e = launch_value_tables(s, a.M, *a.vt)) != cudaSuccess) return e;
     }
+    if (a.ent && a.ent_build && a.n > 0) k_entries<M><<<grid_cap((a.n + 3) / 4, 256), 256, 0, s>>>(a);
     e = a.prm.P == 1.0f ? run_passes<M, POW_ONE>(s, a, n_tiles, smem) : run_passes<M, POW_GEN>(s, a, n_tiles, smem);
     if (e != cudaSuccess) return e;
     if (a.vt && a.n > 0) {
@@ -1515,6 +1663,9 @@ cudaError_t preload_m()
     touch((const void*)k_passA_ring<M, POW_ONE, true, ring_depth<M>(), ring_min_blocks<M>()>);
     touch((const void*)k_passA_ring<M, POW_GEN, true, ring_depth<M>(), ring_min_blocks<M>()>);
     touch((const void*)k_passA_ring<M, POW_ONE, true, ring_depth<M>(), ring_min_blocks<M>(), true>);
+    touch((const void*)k_passA_ring<M, POW_ONE, true, ring_depth_ent<M>(), ring_min_blocks<M>(), false, true>);
+    touch((const void*)k_passA_ring<M, POW_ONE, true, ring_depth_ent<M>(), ring_min_blocks<M>(), true, true>);
+    touch((const void*)k_entries<M>);
     return e;
 }
 cudaError_t preload_update_kernels(uint32_t M)

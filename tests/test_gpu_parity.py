@@ -96,6 +96,52 @@ def test_ragged_sizes(n):
     check_update(lo, lev, fields, alpha, oracle.SFC_HILBERT, P=1.0, width=512)
 
 
+def test_entry_stream_equals_field_stream(small):
+    """With tables of at most 256 entries the width pass streams each cell's
+    kept TF entries instead of its field values; the entries follow the TF
+    domain, the table size and the data.  Over a sequence of edits on one
+    context (alpha only, a new domain, a smaller table, a table of more than
+    256 entries, new field values, back to 256 entries) every result equals
+    that of a context that streams the field values, bit for bit, widths and
+    alpha means included."""
+    rng = np.random.default_rng(31)
+    lower, level, fields = small.lower, small.level, small.fields
+    ctxs = []
+    for use in (1, 0):
+        c = dvl.DVL(0)
+        c.set_option(dvl.OPT_ENTRIES, use)
+        c.load_amr(lower, level, fields)
+        c.build_order(oracle.SFC_HILBERT)
+        ctxs.append(c)
+    lo_d = np.min(fields, axis=1)
+    hi_d = np.max(fields, axis=1)
+    f2 = (fields * rng.uniform(0.5, 1.5, fields.shape)).astype(np.float32)
+    steps = [("alpha", synth.random_tfs(40), None), ("alpha", synth.random_tfs(41), None),
+             ("domain", synth.random_tfs(41), (lo_d + 0.1 * (hi_d - lo_d), lo_d + 0.7 * (hi_d - lo_d))),
+             ("T64", synth.random_tfs(42, n_entries=64), None), ("T512", synth.random_tfs(43, n_entries=512), None),
+             ("fields", synth.random_tfs(44), None), ("T256", synth.random_tfs(45), None)]
+    try:
+        for name, alpha, dom in steps:
+            outs = []
+            for c in ctxs:
+                if name == "fields":
+                    c.set_fields(f2)
+                for m in range(fields.shape[0]):
+                    lo, hi = (math.nan, math.nan) if dom is None else (float(dom[0][m]), float(dom[1][m]))
+                    c.set_tf(m, alpha[m], lo, hi)
+                c.update(width=1536, want_alpha=1)
+                outs.append((c.read_widths(), [c.read_bins(m) for m in range(fields.shape[0])], c.read_alpha_means()))
+            (qa, ba, aa), (qb, bb, ab) = outs
+            assert np.array_equal(qa, qb), name
+            for x, y in zip(ba, bb):
+                for k in x:
+                    assert np.array_equal(np.asarray(x[k]).view(np.uint8), np.asarray(y[k]).view(np.uint8)), (name, k)
+            assert np.array_equal(np.asarray(aa).view(np.uint8), np.asarray(ab).view(np.uint8)), name
+    finally:
+        for c in ctxs:
+            c.close()
+
+
 def test_fixed_point_sums_across_magnitudes():
     """The value tables keep the exact sums of floor(t 2^95) in five 23-bit
     limbs and skip the lower ones for stretches of cells whose t is 0 or at
