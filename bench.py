@@ -58,9 +58,8 @@ BYTES_BINS_PER_PIXEL = BYTES_BOUNDS_PER_PIXEL + BYTES_PIXELS_PER_PIXEL
 # 8-B (min, max) pairs written (4 x 40 / 128 B/cell); block arrays are
 # 1/32 of that.
 BYTES_TABLES = 4 * 4 + 4 * 40 / 128 * (1 + 1 / 32)
-# with the entries: the entry kernel reads the fields again (16 B/cell) and
-# writes one byte per field
-BYTES_TABLES_ENT = BYTES_TABLES + 4 * 4 + 4
+# with the entries: the same pass writes one entry byte per field
+BYTES_TABLES_ENT = BYTES_TABLES + 4
 CPU_SAMPLE_BOX = ((0, 0, 0), 32)     # 32^3 of the 128^3 base cells (1/64 of the domain)
 LAUNCHES_PER_UPDATE = 5              # prepare, width pass, chunk scan, pixel bounds, pixel bins
 LOG_FIELDS = (0, 2, 3)                   # dens, pres, velmag on the log10 scale

@@ -208,6 +208,10 @@ __device__ __noinline__ void vt_last_block_field(const ValueTableArgs& v, uint64
                 for (int q = 0; q < 4; ++q)
                     if (i0 + q < v.n) {
                         const float t = norm_t(e[q], lo, sc);
+                        if (v.ent) {
+                            const uint32_t en = floor_small(__fmul_rn(t, (float)v.T));
+                            v.ent[m * v.pitch + i0 + q] = (uint8_t)(en < v.T - 1u ? en : v.T - 1u);
+                        }
                         uint32_t r[5];
                         fx_limb_bits(t, r);
 #pragma unroll
@@ -240,10 +244,12 @@ __device__ __noinline__ void vt_last_block_field(const ValueTableArgs& v, uint64
 constexpr int VT_WARPS = 4;
 constexpr uint32_t VT_WAIT_POLLS = 4096;       // polls of <= 1 ms
 
+// the stages and their barriers, then per warp one stage's entries (VQ bytes
+// of each of the 32 rows) on their way out
 template <int VQ, int VS>
-constexpr size_t vt_tx_smem() { return (size_t)VT_WARPS * VS * (VT_BLOCK * VQ * 4 + 8); }
+constexpr size_t vt_tx_smem() { return (size_t)VT_WARPS * VS * (VT_BLOCK * VQ * 4 + 8) + (size_t)VT_WARPS * VT_BLOCK * VQ; }
 
-template <int M, int VQ, int VS>
+template <int M, int VQ, int VS, bool ENT = false>
 __global__ __launch_bounds__(VT_WARPS * 32) void k_vt_tx(ValueTableArgs v, uint64_t n_full)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -292,6 +298,8 @@ __global__ __launch_bounds__(VT_WARPS * 32) void k_vt_tx(ValueTableArgs v, uint6
     uint32_t acc[5] = {0u, 0u, 0u, 0u, 0u};
     uint32_t mn = 0x7F800000u, mx = 0u;
     float lo = 0.f, sc = 0.f;
+    const float Tf = (float)v.T;
+    const uint32_t Tm1 = v.T - 1u;
     for (; cc.b < n_full; next(cc)) {
         if (cc.h == 0) {
 #pragma unroll
@@ -301,6 +309,13 @@ __global__ __launch_bounds__(VT_WARPS * 32) void k_vt_tx(ValueTableArgs v, uint6
         }
         if (!__all_sync(FULL, mbar_wait(bar_s + 8u * k, phase, VT_WAIT_POLLS))) { late = true; break; }   // warp-uniform
         const float4* row = ring + (size_t)k * (STAGE / 16) + lane * C4;
+        // ENT: the entries of the lane's VQ cells, min(floor(t T), T - 1) as
+        // k_entries writes them, 4 cells to a u32, go to the warp's row
+        // buffer in shared memory and from there to global memory in whole
+        // 16-byte pieces (the rows' VQ-byte segments are contiguous)
+        uint32_t* ebuf = reinterpret_cast<uint32_t*>(smem + (size_t)VT_WARPS * VS * (STAGE + 8)) +
+                         (size_t)warp * (VT_BLOCK * VQ / 4);
+        uint32_t* erow = ebuf + lane * (VQ / 4);
         // first pass: min, max and the two-limb sums, valid when every t of
         // the warp's stage is 0 or >= 2^-23 (t bits - 1 >= bits(2^-23) - 1,
         // unsigned); otherwise a second pass takes all five limbs
@@ -320,6 +335,22 @@ __global__ __launch_bounds__(VT_WARPS * 32) void k_vt_tx(ValueTableArgs v, uint6
             mn = min(min(mn, b0), min(min(b1, b2), b3));
             mx = max(max(mx, b0), max(max(b1, b2), b3));
             okmin = min(min(okmin, b0 - 1u), min(min(b1 - 1u, b2 - 1u), b3 - 1u));
+            if (ENT) {
+                const uint32_t e0 = min(floor_small(__fmul_rn(t0, Tf)), Tm1), e1 = min(floor_small(__fmul_rn(t1, Tf)), Tm1);
+                const uint32_t e2 = min(floor_small(__fmul_rn(t2, Tf)), Tm1), e3 = min(floor_small(__fmul_rn(t3, Tf)), Tm1);
+                erow[(c + lane) & (C4 - 1)] = e0 | e1 << 8 | e2 << 16 | e3 << 24;
+            }
+        }
+        if (ENT) {
+            __syncwarp();
+            const uint4* eb4 = reinterpret_cast<const uint4*>(ebuf);
+#pragma unroll
+            for (int r4 = 0; r4 < VT_BLOCK * VQ / 16 / 32; ++r4) {
+                const int q = r4 * 32 + lane, row = q / (VQ / 16), part = q % (VQ / 16);
+                reinterpret_cast<uint4*>(v.ent + cc.m * v.pitch + (cc.b * VT_BLOCK + row) * STEP + cc.h * VQ)[part] =
+                    eb4[q];
+            }
+            __syncwarp();                // the buffer is refilled at the next stage
         }
         if (__all_sync(FULL, okmin >= 0x33FFFFFFu)) {
             acc[0] += a0;
@@ -965,26 +996,27 @@ cudaError_t run_tables(cudaStream_t s, const ValueTableArgs& v)
     if (v.n_blocks == 0) return cudaSuccess;
     const uint64_t n_full = v.n / ((uint64_t)VT_BLOCK * STEP);     // blocks of 32 full steps
     {
-        auto kernel = k_vt_tx<M, VT_Q, VT_S>;
+        const int ve = v.ent ? 1 : 0;                              // with the entries or without
+        auto kernel = ve ? k_vt_tx<M, VT_Q, VT_S, true> : k_vt_tx<M, VT_Q, VT_S>;
         constexpr size_t smem = vt_tx_smem<VT_Q, VT_S>();
-        static std::atomic<size_t> set_bytes[MAX_DEVICES];
-        cudaError_t e = smem_attr_once(kernel, smem, set_bytes);
+        static std::atomic<size_t> set_bytes[2][MAX_DEVICES];
+        cudaError_t e = smem_attr_once(kernel, smem, set_bytes[ve]);
         int dev = 0;
         if (e == cudaSuccess) e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
         // resident CTAs of the device, cached per thread for the last device
-        thread_local int last_dev = -1;
-        thread_local uint64_t resident = 0;
-        if (dev != last_dev) {
+        thread_local int last_dev[2] = {-1, -1};
+        thread_local uint64_t resident[2] = {0, 0};
+        if (dev != last_dev[ve]) {
             int per_sm = 0, sms = 0;
             if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, VT_WARPS * 32, smem)) != cudaSuccess ||
                 (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
                 return e;
-            resident = (uint64_t)(per_sm > 0 ? per_sm : 1) * sms;
-            last_dev = dev;
+            resident[ve] = (uint64_t)(per_sm > 0 ? per_sm : 1) * sms;
+            last_dev[ve] = dev;
         }
         const uint64_t need = (n_full + VT_WARPS - 1) / VT_WARPS;
-        const uint64_t grid = need < resident ? (need ? need : 1) : resident;
+        const uint64_t grid = need < resident[ve] ? (need ? need : 1) : resident[ve];
         kernel<<<(unsigned)grid, VT_WARPS * 32, smem, s>>>(v, n_full);
     }
     const uint32_t n_seg = (uint32_t)((v.n_blocks + VT_SEG - 1) / VT_SEG);
@@ -1019,6 +1051,7 @@ cudaError_t preload_bins_m()
 {
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)k_vt_tx<M, VT_Q, VT_S>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_vt_tx<M, VT_Q, VT_S, true>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_vt_seg_sum);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_vt_seg_scan);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)k_vt_seg_apply);

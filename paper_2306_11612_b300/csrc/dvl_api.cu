@@ -894,7 +894,12 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
     a.vt = &c->vt;
     a.vt_build = build_vt ? 1 : 0;
     a.ent = use_ent ? c->d_ent : nullptr;
-    a.ent_build = build_ent ? 1 : 0;
+    // entries and value tables rebuilt together: the table pass writes the
+    // entries as well (one read of the fields)
+    const bool fuse_ent = build_ent && build_vt;
+    c->vt.ent = fuse_ent ? c->d_ent : nullptr;
+    c->vt.T = c->T;
+    a.ent_build = build_ent && !fuse_ent ? 1 : 0;
     if (p->want_alpha) {
         a.asum = c->d_asum;
         a.amean = c->d_amean;
@@ -908,7 +913,9 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
         c->ev.push_back(set);
         a.events = c->ev.back().data();
     }
-    CK(launch_update(c->stream, a), "update kernels");
+    const cudaError_t le = launch_update(c->stream, a);
+    c->vt.ent = nullptr;                      // other paths (batches) never write the entries
+    CK(le, "update kernels");
     if (build_vt) {
         c->vt_valid = true;
         c->vt_dom = c->h_dom;

@@ -115,6 +115,8 @@ struct ValueTableArgs {
     float2* bmm;               // M x b_levels x n_blocks: level l, entry i = blocks [i, i + 2^l)
     int b_levels;              // floor(log2(n_blocks)) + 1 (0 when there are no blocks)
     ulonglong2* seg;           // M x ceil(n_blocks / 2048): segment sums of blk, then their prefixes
+    uint8_t* ent;              // if not null: the cells' TF entries are written in the same pass
+    uint32_t T;                //   (UpdateArgs::ent; T <= 256 entries)
     uint32_t* err;             // error word (ERR_TIMEOUT when a bounded wait runs out)
 };
 struct QueryArgs {
