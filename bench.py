@@ -525,11 +525,22 @@ def run_ours(args):
     dom = max(kern, key=lambda k: kern[k]["ms"])
     edit_bytes = alg["dvl_pass_a"] + alg["dvl_bins"]
     tr = traffic.get(dom)
+    # the same kernel against the instruction issue rate (its warp
+    # instructions per cell from the committed ncu capture; one instruction
+    # per scheduler per clock at the sampled SM clock)
+    issue_roof = None
+    if tr is not None and ent and "warp_inst_per_cell" in tr:
+        mhz = clk.summary().get("sm_mhz") or 2032.0
+        ips = tr["warp_inst_per_cell"] * amr.n / (kern[dom]["ms"] * 1e-3)
+        peak_ips = torch.cuda.get_device_properties(local).multi_processor_count * 4 * mhz * 1e6
+        issue_roof = {"achieved_warp_inst_per_s": ips, "peak": peak_ips, "frac": ips / peak_ips,
+                      "warp_inst_per_cell": tr["warp_inst_per_cell"], "sm_mhz": mhz}
     roofline = {"bound": "hbm", "achieved": kern[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
                 "frac": kern[dom]["achieved_gbs"] / peak, "kernel": dom,
                 "traffic": None if tr is None else tr["dram_bytes_per_cell"] * amr.n,
                 "algorithmic_bytes": alg[dom],
                 "streamed": "per-cell TF entries and levels (5 B/cell)" if ent else "field values and levels (17 B/cell)",
+                "issue": issue_roof,
                 "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json), burst copy" if peak_kind == "measured"
                 else "fallback 6.4 TB/s"}
     step_gbs = edit_bytes / (ms / args.steps * 1e-3) / 1e9
