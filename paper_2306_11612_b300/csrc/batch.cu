@@ -57,7 +57,9 @@ __global__ void k_prepare_batch(UpdateArgs a, BatchArgs b)
 // fixed-point scale 2^Q of each TF is folded into its constants: scaling by a
 // power of two is exact, so rint(max(max(V/maxV, m_b) 2^L, m_a) 2^Q) equals
 // rint(max(max(V (2^Q/maxV), m_b 2^Q) 2^L, m_a 2^Q)) bit for bit.
-template <int M, int PM, int G, int ST>
+// ENT: the cells' kept TF entries (a.ent, one byte per cell and field) are
+// read instead of the field values.
+template <int M, int PM, int G, int ST, bool ENT = false>
 __device__ __forceinline__ void passA_batch_body(const UpdateArgs& a, const BatchArgs& b)
 {
     extern __shared__ float4 s_dyn[];                  // G params, the floors, the G x M x T1 tables
@@ -137,12 +139,23 @@ __device__ __forceinline__ void passA_batch_body(const UpdateArgs& a, const Batc
         // the next step's cells are loaded while this step's TFs run (the
         // same addresses as the step itself reads, one step earlier)
         float vn[4][M];
+        uint32_t En[M];                                // ENT: the 4 cells' entries of field m
         uint32_t Ln = 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int m = 0; m < M; ++m) {
+            En[m] = 0u;
 #pragma unroll
-            for (int m = 0; m < M; ++m) vn[j][m] = 0.0f;
-        if (base + lane * 4 < a.n) load4<M>(a.val, a.pitch, a.lev, base + lane * 4, vn, Ln);
+            for (int j = 0; j < 4; ++j) vn[j][m] = 0.0f;
+        }
+        auto load_ent4 = [&](uint64_t i) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) En[m] = __ldg(reinterpret_cast<const uint32_t*>(a.ent + m * a.pitch + i));
+            Ln = __ldg(reinterpret_cast<const uint32_t*>(a.lev + i));
+        };
+        if (base + lane * 4 < a.n) {
+            if (ENT) load_ent4(base + lane * 4);
+            else load4<M>(a.val, a.pitch, a.lev, base + lane * 4, vn, Ln);
+        }
         for (int st = 0; st < STEPS; ++st) {
             if (base + (uint64_t)st * STEP >= a.n) break;            // warp-uniform
             const uint64_t idx = base + st * STEP + lane * 4;
@@ -151,19 +164,31 @@ __device__ __forceinline__ void passA_batch_body(const UpdateArgs& a, const Batc
             uint32_t frow[4];                          // shared address of the cell's level row of s_floor
             bool valid[4];
             float v[4][M];
+            uint32_t E[M];
             const uint32_t L4 = Ln;
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int m = 0; m < M; ++m) {
+                E[m] = En[m];
 #pragma unroll
-                for (int m = 0; m < M; ++m) v[j][m] = vn[j][m];
+                for (int j = 0; j < 4; ++j) v[j][m] = vn[j][m];
+            }
             const uint64_t nidx = idx + STEP;
-            if (st + 1 < STEPS && nidx < a.n) load4<M>(a.val, a.pitch, a.lev, nidx, vn, Ln);
+            if (st + 1 < STEPS && nidx < a.n) {
+                if (ENT) load_ent4(nidx);
+                else load4<M>(a.val, a.pitch, a.lev, nidx, vn, Ln);
+            }
             if (idx < a.n) {
+                // past the data set's end the entry bytes are not written:
+                // those cells (masked below) read entry 0
+                const uint32_t keep = ENT && idx + 4 > a.n ? (1u << (8 * (uint32_t)(a.n - idx))) - 1u : 0xFFFFFFFFu;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
 #pragma unroll
-                    for (int m = 0; m < M; ++m)
-                        off[j][m] = s_base + (m * T1 + floor_small(__fmul_rn(norm_t(v[j][m], lo[m], sc[m]), Tf))) * (RS * 4);
+                    for (int m = 0; m < M; ++m) {
+                        const uint32_t e = ENT ? ((E[m] & keep) >> (8 * j)) & 0xFFu
+                                               : floor_small(__fmul_rn(norm_t(v[j][m], lo[m], sc[m]), Tf));
+                        off[j][m] = s_base + (m * T1 + e) * (RS * 4);
+                    }
                     const uint32_t Lj = (L4 >> (8 * j)) & 0xFF;
                     lvl[j] = exp2i((int)Lj * wshift);
                     frow[j] = floor_s + Lj * (G * 4);
@@ -275,21 +300,21 @@ __device__ __forceinline__ void passA_batch_body(const UpdateArgs& a, const Batc
 // CTAs per SM, an eighth of the register file stays free for other streams'
 // kernels (the serving loop runs data sets side by side, mostly with small
 // batches).
-template <int M, int PM, int G, int ST>
+template <int M, int PM, int G, int ST, bool ENT>
 __global__ __launch_bounds__(WARPS * 32, 2) void k_passA_batch16(UpdateArgs a, BatchArgs b)
 {
-    passA_batch_body<M, PM, G, ST>(a, b);
+    passA_batch_body<M, PM, G, ST, ENT>(a, b);
 }
-template <int M, int PM, int G, int ST>
+template <int M, int PM, int G, int ST, bool ENT>
 __global__ __maxnreg__(112) void k_passA_batch8(UpdateArgs a, BatchArgs b)
 {
-    passA_batch_body<M, PM, G, ST>(a, b);
+    passA_batch_body<M, PM, G, ST, ENT>(a, b);
 }
-template <int M, int PM, int G, int ST>
+template <int M, int PM, int G, int ST, bool ENT = false>
 constexpr auto passA_batch_kernel()
 {
-    if constexpr (G >= 16) return k_passA_batch16<M, PM, G, ST>;
-    else return k_passA_batch8<M, PM, G, ST>;
+    if constexpr (G >= 16) return k_passA_batch16<M, PM, G, ST, ENT>;
+    else return k_passA_batch8<M, PM, G, ST, ENT>;
 }
 
 // The chunk totals of TF blockIdx.y become exclusive prefixes: blocks of
@@ -395,12 +420,12 @@ size_t passA_batch_smem(uint32_t M, uint32_t T, uint32_t G)
            (size_t)(G + 4) * M * T1 * sizeof(float);
 }
 
-template <int M, int PM, int G, int ST>
+template <int M, int PM, int G, int ST, bool ENT>
 cudaError_t run_passA_batch_gs(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
 {
     const size_t smem = passA_batch_smem(M, a.T, G);
     static std::atomic<size_t> set_bytes[MAX_DEVICES];
-    constexpr auto kernel = passA_batch_kernel<M, PM, G, ST>();
+    constexpr auto kernel = passA_batch_kernel<M, PM, G, ST, ENT>();
     cudaError_t e = smem_attr_once(kernel, smem, set_bytes);
     if (e != cudaSuccess) return e;
     const uint64_t work = (b.n_chunks * ((b.K + G - 1) / G) + WARPS - 1) / WARPS;   // CTAs with a chunk each
@@ -417,8 +442,9 @@ cudaError_t run_passA_batch_gs(cudaStream_t s, const UpdateArgs& a, const BatchA
 template <int M, int PM, int G>
 cudaError_t run_passA_batch_g(cudaStream_t s, const UpdateArgs& a, const BatchArgs& b)
 {
-    return a.T + 1 <= (uint32_t)SMALL_T1 ? run_passA_batch_gs<M, PM, G, SMALL_T1>(s, a, b)
-                                         : run_passA_batch_gs<M, PM, G, 0>(s, a, b);
+    if (a.T + 1 > (uint32_t)SMALL_T1) return run_passA_batch_gs<M, PM, G, 0, false>(s, a, b);
+    return a.ent ? run_passA_batch_gs<M, PM, G, SMALL_T1, true>(s, a, b)
+                 : run_passA_batch_gs<M, PM, G, SMALL_T1, false>(s, a, b);
 }
 
 template <int M, int PM>
@@ -443,13 +469,13 @@ cudaError_t launch_passA_batch(cudaStream_t s, const UpdateArgs& a, const BatchA
     DVL_DISPATCH_M(run_passA_batch_m, s, a, b)
 }
 
-template <int M, int PM, int G, int ST>
+template <int M, int PM, int G, int ST, bool ENT>
 cudaError_t occupancy_passA_batch_gs(const UpdateArgs& a, int* blocks)
 {
     const size_t smem = passA_batch_smem(M, a.T, G);
     *blocks = 0;
     if (smem + sizeof(unsigned long long) * WARPS * G + 16 > 227 * 1024) return cudaSuccess;
-    constexpr auto kernel = passA_batch_kernel<M, PM, G, ST>();
+    constexpr auto kernel = passA_batch_kernel<M, PM, G, ST, ENT>();
     cudaError_t e = smem_attr(kernel, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, WARPS * 32, smem);
@@ -458,8 +484,9 @@ cudaError_t occupancy_passA_batch_gs(const UpdateArgs& a, int* blocks)
 template <int M, int PM, int G>
 cudaError_t occupancy_passA_batch_g(const UpdateArgs& a, int* blocks)
 {
-    return a.T + 1 <= (uint32_t)SMALL_T1 ? occupancy_passA_batch_gs<M, PM, G, SMALL_T1>(a, blocks)
-                                         : occupancy_passA_batch_gs<M, PM, G, 0>(a, blocks);
+    if (a.T + 1 > (uint32_t)SMALL_T1) return occupancy_passA_batch_gs<M, PM, G, 0, false>(a, blocks);
+    return a.ent ? occupancy_passA_batch_gs<M, PM, G, SMALL_T1, true>(a, blocks)
+                 : occupancy_passA_batch_gs<M, PM, G, SMALL_T1, false>(a, blocks);
 }
 
 template <int M, int PM>

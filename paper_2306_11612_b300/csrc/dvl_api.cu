@@ -226,7 +226,7 @@ void free_dataset(dvl_ctx* c)
 }
 
 cudaError_t enqueue_batch(dvl_ctx* c, const UpdateArgs& a, const BatchArgs& b, const ValueTableArgs& v,
-                                 bool build_vt, cudaEvent_t* ev = nullptr)
+                                 bool build_vt, cudaEvent_t* ev = nullptr, bool build_ent = false)
 {
     // memsets and launches only, so that the sequence can be captured; ev
     // (uncaptured runs only): 5 events around prepare, pass A and the bins
@@ -250,6 +250,11 @@ cudaError_t enqueue_batch(dvl_ctx* c, const UpdateArgs& a, const BatchArgs& b, c
         return cudaMemsetAsync(c->d_bcount, 0, nc * sizeof(uint32_t), s);
     }
     if (build_vt && (e = launch_value_tables(s, a.M, v)) != cudaSuccess) return e;
+    if (build_ent && !(build_vt && v.ent)) {             // entries alone (the table pass did not write them)
+        UpdateArgs ae = a;
+        ae.consts = b.consts;                            // lo / s of the batch's domains
+        if ((e = launch_entries(s, ae)) != cudaSuccess) return e;
+    }
     if (ev) cudaEventRecord(ev[1], s);
     if ((e = launch_passA_batch(s, a, b)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], s);
@@ -1450,6 +1455,29 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
 
     const bool build_vt = !c->vt_valid || c->vt_dom.size() != dom.size() ||
                           std::memcmp(c->vt_dom.data(), dom.data(), dom.size() * sizeof(float)) != 0;
+    // per-cell TF entries (tables of <= 256 entries), shared with dvl_update:
+    // built with the value tables when both are due, else alone
+    const bool use_ent = c->use_ent && T <= 256 && c->n > 0;
+    bool build_ent = false;
+    if (use_ent) {
+        if (!c->d_ent) CK(dalloc(c->d_ent, (size_t)c->M * c->pitch), "alloc TF entries");
+        build_ent = !c->ent_valid || c->ent_T != T || c->ent_dom.size() != dom.size() ||
+                    std::memcmp(c->ent_dom.data(), dom.data(), dom.size() * sizeof(float)) != 0;
+        a.ent = c->d_ent;
+    }
+    v.ent = build_ent && build_vt ? c->d_ent : nullptr;
+    v.T = T;
+    auto mark_built = [&]() {
+        if (build_vt) {
+            c->vt_valid = true;
+            c->vt_dom = dom;
+        }
+        if (build_ent) {
+            c->ent_valid = true;
+            c->ent_dom = dom;
+            c->ent_T = T;
+        }
+    };
     const uint32_t P1 = prm.P == 1.0f;
     const std::vector<uint64_t> shape{c->n, M, T, K, P1};
     auto tuned = c->b_tuned.find(shape);
@@ -1459,11 +1487,8 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
         // timed on this data set (all configurations give identical results)
         b.G = K <= 4 ? 4 : 8;
         b.resid = 1;
-        CK(enqueue_batch(c, a, b, v, build_vt), "batch kernels");
-        if (build_vt) {
-            c->vt_valid = true;
-            c->vt_dom = dom;
-        }
+        CK(enqueue_batch(c, a, b, v, build_vt, nullptr, build_ent), "batch kernels");
+        mark_built();
         std::vector<std::pair<int, int>> cand;
         for (uint32_t G : {4u, 8u, 16u}) {        // compiled group sizes
             int blocks = 0;
@@ -1501,13 +1526,13 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
         cudaEventDestroy(e1);
         if (err != cudaSuccess) return cuda_fail(c, err, "batch autotune");
         tuned = c->b_tuned.emplace(shape, pick).first;
-    } else if (build_vt) {
+    } else if (build_vt || build_ent) {
         b.G = tuned->second.first;
         b.resid = tuned->second.second;
-        CK(enqueue_batch(c, a, b, v, true), "batch kernels");
-        c->vt_valid = true;
-        c->vt_dom = dom;
+        CK(enqueue_batch(c, a, b, v, build_vt, nullptr, build_ent), "batch kernels");
+        mark_built();
     }
+    v.ent = nullptr;                                 // the timed and captured runs build nothing
     b.G = tuned->second.first;
     b.resid = tuned->second.second;
     c->b_G = b.G;
@@ -1536,7 +1561,7 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
                                     (uint64_t)c->d_by, (uint64_t)c->d_bcount, (uint64_t)c->d_bH, (uint64_t)c->d_bS,
                                     (uint64_t)c->d_bpsum, (uint64_t)c->d_bpmm, (uint64_t)c->d_bstamps,
                                     (uint64_t)v.loc, (uint64_t)v.blk, (uint64_t)v.raw, (uint64_t)v.pre,
-                                    (uint64_t)v.suf, (uint64_t)v.bmm, (uint64_t)v.seg};
+                                    (uint64_t)v.suf, (uint64_t)v.bmm, (uint64_t)v.seg, (uint64_t)a.ent};
     constexpr size_t MAX_GRAPHS = 32;
     auto hit = c->b_graphs.find(sig);
     if (hit == c->b_graphs.end()) {

@@ -256,6 +256,8 @@ cudaError_t launch_update(cudaStream_t s, const UpdateArgs& a);
 // their first launch (update.cu: widths and scan; bins.cu: value tables and
 // pixel queries).
 cudaError_t preload_update_kernels(uint32_t M);
+// The per-cell TF entries (a.ent) for the domains of a.consts and T = a.T.
+cudaError_t launch_entries(cudaStream_t s, const UpdateArgs& a);
 cudaError_t preload_bins_kernels(uint32_t M);
 // Alpha tables from control points (M x K -> M x T), flags values outside [0,1].
 cudaError_t launch_ctrl_table(cudaStream_t s, uint32_t M, uint32_t K, uint32_t T, const float* ctrl, float* tf,

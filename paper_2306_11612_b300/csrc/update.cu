@@ -1668,6 +1668,18 @@ cudaError_t preload_m()
     touch((const void*)k_entries<M>);
     return e;
 }
+template <int M>
+cudaError_t run_entries(cudaStream_t s, const UpdateArgs& a)
+{
+    if (a.n > 0) k_entries<M><<<grid_cap((a.n + 3) / 4, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_entries(cudaStream_t s, const UpdateArgs& a)
+{
+    DVL_DISPATCH_M(run_entries, s, a)
+}
+
 cudaError_t preload_update_kernels(uint32_t M)
 {
     switch (M) {
