@@ -105,6 +105,35 @@ def test_batch_ragged_sizes(n):
         ctx.close()
 
 
+def test_batch_entries_equal_field_values():
+    """The batched width pass reads the cells' kept TF entries (tables of at
+    most 256 entries) or, with DVL_OPT_ENTRIES = 0, their field values; over
+    a table size change (entries rebuilt alone), a domain change (rebuilt
+    with the value tables) and a table of more than 256 entries, both give
+    the same bins bit for bit."""
+    amr = synth.make("small")
+    ctxs = [_ctx(amr.lower, amr.level, amr.fields) for _ in range(2)]
+    ctxs[1].set_option(dvl.OPT_ENTRIES, 0)
+    lo = np.min(amr.fields, axis=1)
+    hi = np.max(amr.fields, axis=1)
+    dom = list(lo + 0.2 * (hi - lo)) + list(lo + 0.6 * (hi - lo))
+    runs = [(_tfs(5, 9), None), (_tfs(6, 9, T=100), None), (_tfs(7, 9, T=100), dom), (_tfs(8, 5, T=400), dom),
+            (_tfs(9, 9), None)]
+    try:
+        for alphas, d in runs:
+            pairs = [(k, 257 + 31 * k) for k in range(alphas.shape[0])]
+            out = []
+            for c in ctxs:
+                c.update_batch(alphas, pairs, domain=d)
+                out.append([[c.read_batch_bins(q, m) for m in range(4)] for q in range(len(pairs))])
+            for qa, qb in zip(*out):
+                for x, y in zip(qa, qb):
+                    _same(x, y)
+    finally:
+        for c in ctxs:
+            c.close()
+
+
 def test_batch_graph_replay_and_device_tfs():
     amr = synth.make("small")
     K = 24
