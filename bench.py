@@ -1122,6 +1122,7 @@ DIFF_W, DIFF_K = 2048, 64
 DIFF_FWD_BYTES = 17 + SCAN_BYTES + 4 * 8 / 128 + 4 * 8 / 2048
 DIFF_FWD_BYTES_ENT = DIFF_FWD_BYTES - 4 * 3    # entries: 1 B per field instead of 4
 DIFF_BWD_BYTES = 16
+DIFF_BWD_BYTES_ENT = 4                          # entries: 1 B per field
 
 
 def run_diff(args, emit=True):
@@ -1194,7 +1195,7 @@ def run_diff(args, emit=True):
     peak, _ = measured_peak()
     fwd_bytes = DIFF_FWD_BYTES_ENT if ent else DIFF_FWD_BYTES
     fwd_gbs = fwd_bytes * amr.n / (parts["forward_ms"] * 1e-3) / 1e9
-    bwd_gbs = DIFF_BWD_BYTES * amr.n / (parts["adjoint_ms"] * 1e-3) / 1e9
+    bwd_gbs = (DIFF_BWD_BYTES_ENT if ent else DIFF_BWD_BYTES) * amr.n / (parts["adjoint_ms"] * 1e-3) / 1e9
     line = {"metric": "TF-tuning gradient step (forward alpha means + adjoint), cells/s", "value": amr.n / (ms * 1e-3),
             "unit": "cells/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 gradient sums)",

@@ -98,6 +98,7 @@ struct dvl_ctx {
     uint32_t ent_T = 0;
     int use_ent = 1;
     bool last_ent = false;            // the last update's width pass streamed the entries
+    uint64_t ent_gen = 0, last_ent_gen = 0;   // builds of the entries; the one the last update used
     unsigned long long* d_H = nullptr;
     uint8_t* d_S = nullptr;
     ulonglong2* d_psum = nullptr;     // boundary partial terms, 2 x M per boundary
@@ -929,8 +930,10 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
         c->ent_valid = true;
         c->ent_dom = c->h_dom;
         c->ent_T = c->T;
+        ++c->ent_gen;
     }
     c->last_ent = use_ent;
+    c->last_ent_gen = c->ent_gen;
     c->fault_no_publish = 0;
     c->W_last = p->width;
     c->last_prm = *p;
@@ -1149,6 +1152,8 @@ int dvl_backward(dvl_ctx* c, const float* grad, int mem_in, float* grad_ctrl, in
     }
     CK(cudaMemsetAsync(c->d_gtab, 0, (size_t)M * T * sizeof(double), c->stream), "clear adjoint");
     UpdateArgs a = make_args(c, c->last_prm);
+    // the entries of the last update, if they are still the ones it read
+    if (c->last_ent && c->ent_valid && c->ent_gen == c->last_ent_gen) a.ent = c->d_ent;
     float* out = mem_out == DVL_MEM_DEVICE ? grad_ctrl : c->d_gout;
     const size_t np = backward_gpart_elems(M, T, c->n, c->W_last);
     if (np > c->gpart_cap) {
@@ -1476,6 +1481,7 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
             c->ent_valid = true;
             c->ent_dom = dom;
             c->ent_T = T;
+            ++c->ent_gen;
         }
     };
     const uint32_t P1 = prm.P == 1.0f;

@@ -1177,7 +1177,9 @@ __global__ void k_backward_weights(uint32_t M, uint32_t W, const float* __restri
 // gpart[blockIdx] without atomics; k_gtab_reduce sums the CTAs in a fixed
 // order.  counters[2] is the chunk counter (zeroed by the launcher).
 constexpr int BQ = 64;                               // per-warp queue slots of the flush
-template <int M, int PM>
+// ENT: single-pixel steps read the cells' kept TF entries (a.ent) instead of
+// normalising their field values.
+template <int M, int PM, bool ENT = false>
 __global__ __launch_bounds__(WARPS * 32, 3) void k_backward_hist(UpdateArgs a, const double* wtab, double* gpart)
 {
     extern __shared__ float s_tf[];   // table | float64 sums | WARPS u32 histograms | WARPS flush queues
@@ -1272,18 +1274,25 @@ __global__ __launch_bounds__(WARPS * 32, 3) void k_backward_hist(UpdateArgs a, c
         const unsigned exact_mask = __ballot_sync(FULL, crossing) & ((1u << nsteps) - 1u);
         unsigned todo = ~exact_mask & ((1u << full) - 1u);             // single-pixel full steps
         float4 xn[M];
+        uint32_t en[M];
         auto load_step = [&](int st) {
 #pragma unroll
-            for (int m = 0; m < M; ++m)
-                xn[m] = __ldg(reinterpret_cast<const float4*>(a.val + m * a.pitch + base + st * STEP + lane * 4));
+            for (int m = 0; m < M; ++m) {
+                if (ENT) en[m] = __ldg(reinterpret_cast<const uint32_t*>(a.ent + m * a.pitch + base + st * STEP + lane * 4));
+                else xn[m] = __ldg(reinterpret_cast<const float4*>(a.val + m * a.pitch + base + st * STEP + lane * 4));
+            }
         };
         if (todo) load_step(__ffs(todo) - 1);
         while (todo) {
             const int st = __ffs(todo) - 1;
             todo &= todo - 1;
             float4 x[M];
+            uint32_t ex[M];
 #pragma unroll
-            for (int m = 0; m < M; ++m) x[m] = xn[m];
+            for (int m = 0; m < M; ++m) {
+                x[m] = xn[m];
+                ex[m] = en[m];
+            }
             if (todo) load_step(__ffs(todo) - 1);
             const uint32_t p = __shfl_sync(FULL, pix, st);
             if (p != cur) {                                            // warp-uniform
@@ -1294,12 +1303,20 @@ __global__ __launch_bounds__(WARPS * 32, 3) void k_backward_hist(UpdateArgs a, c
             }
 #pragma unroll
             for (int m = 0; m < M; ++m) {
-                const float lo = C->lo[m], sc = C->s[m];
                 uint32_t e[4];
-                e[0] = floor_small(__fmul_rn(norm_t(x[m].x, lo, sc), Tf));
-                e[1] = floor_small(__fmul_rn(norm_t(x[m].y, lo, sc), Tf));
-                e[2] = floor_small(__fmul_rn(norm_t(x[m].z, lo, sc), Tf));
-                e[3] = floor_small(__fmul_rn(norm_t(x[m].w, lo, sc), Tf));
+                if (ENT) {
+                    // entry T (a copy of T - 1 in the tables) is kept as T - 1: a
+                    // cell with t = 1 counts toward entry T - 1 here, which the
+                    // final chain rule (k_grad_final) folds in the same way
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) e[j] = (ex[m] >> (8 * j)) & 0xFFu;
+                } else {
+                    const float lo = C->lo[m], sc = C->s[m];
+                    e[0] = floor_small(__fmul_rn(norm_t(x[m].x, lo, sc), Tf));
+                    e[1] = floor_small(__fmul_rn(norm_t(x[m].y, lo, sc), Tf));
+                    e[2] = floor_small(__fmul_rn(norm_t(x[m].z, lo, sc), Tf));
+                    e[3] = floor_small(__fmul_rn(norm_t(x[m].w, lo, sc), Tf));
+                }
                 // run lengths from each cell to the end of its run of equal entries
                 const uint32_t r3 = 1u;
                 const uint32_t r2 = e[2] == e[3] ? r3 + 1u : 1u;
@@ -1591,17 +1608,18 @@ cudaError_t run_backward_pm(cudaStream_t s, const UpdateArgs& a, const float* g,
     if (gpart) {
         // histogram adjoint: per-CTA tables, then a fixed-order reduction
         const size_t smem = backward_hist_smem(M, a.T);
-        if ((e = smem_attr(k_backward_hist<M, PM>, smem)) != cudaSuccess) return e;
+        auto kh = a.ent ? k_backward_hist<M, PM, true> : k_backward_hist<M, PM, false>;
+        if ((e = smem_attr(kh, smem)) != cudaSuccess) return e;
         if (!n_tiles) return cudaMemsetAsync(gtab, 0, (size_t)M * a.T * sizeof(double), s);
         int grid = 0;                                 // persistent: the CTAs resident at once
-        if ((e = resident_ctas(k_backward_hist<M, PM>, smem, &grid)) != cudaSuccess) return e;
+        if ((e = resident_ctas(kh, smem, &grid)) != cudaSuccess) return e;
         if ((uint32_t)grid > n_tiles) grid = (int)n_tiles;
         if ((e = cudaMemsetAsync(a.counters + 2, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
         const uint32_t MT1 = M * (a.T + 1);
         double* part2 = gpart + (uint64_t)n_tiles * MT1;
         double* wtab = part2 + (uint64_t)GTAB_SEGS * MT1;             // M x W pixel weights
         k_backward_weights<<<(M * a.W + 255) / 256, 256, 0, s>>>(M, a.W, g, a.count, wtab);
-        k_backward_hist<M, PM><<<grid, WARPS * 32, smem, s>>>(a, wtab, gpart);
+        kh<<<grid, WARPS * 32, smem, s>>>(a, wtab, gpart);
         k_gtab_reduce<<<dim3((MT1 + 31) / 32, GTAB_SEGS), 256, 0, s>>>(MT1, (uint64_t)grid, gpart, part2);
         return cudaGetLastError();
     }
