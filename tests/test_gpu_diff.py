@@ -140,6 +140,31 @@ def test_gradient_at_diff_config_scale():
         ctx.close()
 
 
+def test_gradient_after_a_batch_with_other_domains():
+    """The adjoint reads the cells' kept TF entries only while they are the
+    ones the last update read: a batched update with other TF domains in
+    between rebuilds them, and the adjoint then normalises the field values
+    itself; the gradient is the same as before the batch (float64 sums whose
+    order may differ: 1e-6 relative)."""
+    amr = synth.make("small")
+    W = 300
+    ctrl, target = _case(5, amr, W=W)
+    ctx = _ctx(amr)
+    try:
+        ctx.set_tf_ctrl(ctrl, 256)
+        ctx.update(width=W, want_alpha=1)
+        g = (2.0 * (ctx.read_alpha_means() - target)).astype(np.float32)
+        g1 = ctx.backward(g).copy()
+        lo = np.min(amr.fields, axis=1)
+        hi = np.max(amr.fields, axis=1)
+        dom = list(lo + 0.3 * (hi - lo)) + list(lo + 0.8 * (hi - lo))
+        ctx.update_batch(np.stack([synth.random_tfs(9)] * 2), [(0, 128), (1, 64)], domain=dom)
+        g2 = ctx.backward(g)
+        assert np.allclose(g2, g1, rtol=1e-6, atol=1e-9 * np.max(np.abs(g1)))
+    finally:
+        ctx.close()
+
+
 def test_state_errors():
     amr = synth.make("small")
     ctx = _ctx(amr)
