@@ -222,6 +222,7 @@ template <int M, int PM>
 struct Cell {
     float lo[M], s[M];
     float inv_vmax, mb, ma, qscale, P, Tf;
+    float ivq, mbq, maq;               // inv_vmax, mb and ma times 2^Q (see q2_pow1)
     int n2, wshift, T1;
     bool linear;
 
@@ -234,6 +235,9 @@ struct Cell {
         mb = after ? 0.0f : C->min_imp;
         ma = after ? C->min_imp : 0.0f;
         qscale = C->qscale;
+        ivq = __fmul_rn(inv_vmax, qscale);
+        mbq = __fmul_rn(mb, qscale);
+        maq = __fmul_rn(ma, qscale);
         P = C->P;
         n2 = C->pow_n2;
         wshift = C->width_shift;
@@ -272,6 +276,27 @@ struct Cell {
         return __float2uint_rn(__fmul_rn(f, qscale));
     }
 
+    // Eq. 3 with P = 1 and the fixed-point width of two cells from the ends
+    // of their spreads (ha - la, hb - lb) and their level factors Sa, Sb
+    // (2^(L wshift)).  With qs = 2^Q,
+    //   rint(max(max(fl(V inv), mb) S, ma) qs)
+    //     = rint(max(fl(V fl(inv qs)) S, fl(mb qs) S, fl(ma qs))):
+    // Q is chosen so that fu 2^Q <= 2^31, which keeps inv qs, mb qs and ma qs
+    // finite and inv qs normal (inv >= 1); scaling by a power of two is exact
+    // in the normal range, rounding is monotone (it commutes with max), and a
+    // value that leaves the normal range lies far below 1/2 on both sides.
+    // One 3-input max per cell instead of two maxima and a multiply.
+    __device__ __forceinline__ void q2_pow1(float ha, float la, float hb, float lb, float Sa, float Sb,
+                                            uint32_t& qa, uint32_t& qb) const
+    {
+        const float2 S = make_float2(Sa, Sb);
+        const float2 V = sub2(make_float2(ha, hb), make_float2(la, lb));
+        const float2 x = mul2(mul2(V, make_float2(ivq, ivq)), S);
+        const float2 fl = mul2(make_float2(mbq, mbq), S);
+        qa = __float2uint_rn(max3f(x.x, fl.x, maq));
+        qb = __float2uint_rn(max3f(x.y, fl.y, maq));
+    }
+
     // width_p2 of two cells a and b at once (P = 1): the subtraction, the
     // entry's fma and Eq. 3's multiplies in float32x2 form, bit for bit the
     // same as two width_p2 calls.  AL: also returns each field's fixed-point
@@ -298,13 +323,7 @@ struct Cell {
         float ha, la, hb, lb;
         spread_ends<M>(ala, ha, la);
         spread_ends<M>(alb, hb, lb);
-        const float2 V = sub2(make_float2(ha, hb), make_float2(la, lb));
-        const float2 r0 = mul2(V, make_float2(inv_vmax, inv_vmax));
-        const float2 r = make_float2(fmaxf(r0.x, mb), fmaxf(r0.y, mb));
-        const float2 x = mul2(r, make_float2(exp2i((int)La * wshift), exp2i((int)Lb * wshift)));
-        const float2 f = mul2(make_float2(fmaxf(x.x, ma), fmaxf(x.y, ma)), make_float2(qscale, qscale));
-        qa = __float2uint_rn(f.x);
-        qb = __float2uint_rn(f.y);
+        q2_pow1(ha, la, hb, lb, exp2i((int)La * wshift), exp2i((int)Lb * wshift), qa, qb);
     }
 
     // The width from the cell's TF entries e[m] (precomputed for the TF
@@ -347,13 +366,8 @@ struct Cell {
         float ha, la, hb, lb;
         spread_ends<M>(ala, ha, la);
         spread_ends<M>(alb, hb, lb);
-        const float2 V = sub2(make_float2(ha, hb), make_float2(la, lb));
-        const float2 r0 = mul2(V, make_float2(inv_vmax, inv_vmax));
-        const float2 r = make_float2(fmaxf(r0.x, mb), fmaxf(r0.y, mb));
-        const float2 x = mul2(r, make_float2(__uint_as_float(La * w23 + 0x3F800000u), __uint_as_float(Lb * w23 + 0x3F800000u)));
-        const float2 f = mul2(make_float2(fmaxf(x.x, ma), fmaxf(x.y, ma)), make_float2(qscale, qscale));
-        qa = __float2uint_rn(f.x);
-        qb = __float2uint_rn(f.y);
+        q2_pow1(ha, la, hb, lb, __uint_as_float(La * w23 + 0x3F800000u), __uint_as_float(Lb * w23 + 0x3F800000u), qa,
+                qb);
     }
 
     // width_p2, also adding each field's fixed-point alpha (alpha_fx of the

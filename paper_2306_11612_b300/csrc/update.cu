@@ -151,6 +151,9 @@ __device__ __forceinline__ unsigned long long widths4(const Cell<M, PM>& cc, con
     return widths4_of<M, PM, FULLSTEP, P2, AL>(cc, a, s_tf, cm, idx, v, L4, aoff, ax);
 }
 
+// Byte j of w (j a compile-time constant): one byte permute.
+__device__ __forceinline__ uint32_t byte_at(uint32_t w, int j) { return __byte_perm(w, 0u, 0x4440u | (uint32_t)j); }
+
 // Sum of the fixed-point widths of one lane's 4 cells from their TF entries
 // (E[m]: the 4 cells' entries of field m, one byte each, cell j in byte j);
 // AL: also adds their fixed-point alphas per field to ax.  Whole steps only.
@@ -166,11 +169,11 @@ __device__ __forceinline__ unsigned long long widths4_ent(const Cell<M, PM>& cc,
             uint32_t ea[M], eb[M], axa[M], axb[M], qa, qb;
 #pragma unroll
             for (int m = 0; m < M; ++m) {
-                ea[m] = (E[m] >> (8 * j)) & 0xFFu;
-                eb[m] = (E[m] >> (8 * j + 8)) & 0xFFu;
+                ea[m] = byte_at(E[m], j);
+                eb[m] = byte_at(E[m], j + 1);
             }
-            cc.template width2_ent<AL>(ea, eb, (L4 >> (8 * j)) & 0xFF, (L4 >> (8 * j + 8)) & 0xFF, tb, aoff, axa,
-                                       axb, qa, qb, four, w23);
+            cc.template width2_ent<AL>(ea, eb, byte_at(L4, j), byte_at(L4, j + 1), tb, aoff, axa, axb, qa, qb, four,
+                                       w23);
             acc += (unsigned long long)qa + qb;
             if (AL) {
 #pragma unroll
