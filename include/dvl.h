@@ -213,9 +213,10 @@ int dvl_set_tfs(dvl_ctx* ctx, uint32_t n_fields, const float* alpha, uint32_t n_
  * the per-pixel mean and alpha.  Asynchronous; read results with
  * dvl_read_bins.  The first update after a TF-domain, table-size or data
  * change also rebuilds the context's value tables and (DVL_OPT_ENTRIES, at
- * most 256 table entries) the per-cell TF entries, about n_fields bytes a
- * cell held until the data set is replaced; later alpha-only edits stream
- * those entries instead of the field values.
+ * most 256 table entries) the per-cell TF entries, n_fields + 1 bytes a
+ * cell (the entries and a copy of the levels in their order) held until the
+ * data set is replaced; later alpha-only edits stream those bytes instead of
+ * the field values.
  * Errors: DVL_ERR_ARG (params), DVL_ERR_STATE, DVL_ERR_NOMEM,
  * DVL_ERR_CUDA.  Device-side failures (DVL_ERR_RANGE for a width bound that
  * cannot be represented, DVL_ERR_TIMEOUT) surface at the next synchronising

@@ -148,8 +148,9 @@ __device__ __forceinline__ void passA_batch_body(const UpdateArgs& a, const Batc
             for (int j = 0; j < 4; ++j) vn[j][m] = 0.0f;
         }
         auto load_ent4 = [&](uint64_t i) {
+            const uint64_t ip = ent_pos(i);            // 4 cells of one 32-cell piece
 #pragma unroll
-            for (int m = 0; m < M; ++m) En[m] = __ldg(reinterpret_cast<const uint32_t*>(a.ent + m * a.pitch + i));
+            for (int m = 0; m < M; ++m) En[m] = __ldg(reinterpret_cast<const uint32_t*>(a.ent + m * a.pitch + ip));
             Ln = __ldg(reinterpret_cast<const uint32_t*>(a.lev + i));
         };
         if (base + lane * 4 < a.n) {

@@ -210,7 +210,7 @@ __device__ __noinline__ void vt_last_block_field(const ValueTableArgs& v, uint64
                         const float t = norm_t(e[q], lo, sc);
                         if (v.ent) {
                             const uint32_t en = floor_small(__fmul_rn(t, (float)v.T));
-                            v.ent[m * v.pitch + i0 + q] = (uint8_t)(en < v.T - 1u ? en : v.T - 1u);
+                            v.ent[m * v.pitch + ent_pos(i0 + q)] = (uint8_t)(en < v.T - 1u ? en : v.T - 1u);
                         }
                         uint32_t r[5];
                         fx_limb_bits(t, r);
@@ -347,8 +347,8 @@ __global__ __launch_bounds__(VT_WARPS * 32) void k_vt_tx(ValueTableArgs v, uint6
 #pragma unroll
             for (int r4 = 0; r4 < VT_BLOCK * VQ / 16 / 32; ++r4) {
                 const int q = r4 * 32 + lane, row = q / (VQ / 16), part = q % (VQ / 16);
-                reinterpret_cast<uint4*>(v.ent + cc.m * v.pitch + (cc.b * VT_BLOCK + row) * STEP + cc.h * VQ)[part] =
-                    eb4[q];
+                const uint64_t i16 = (uint64_t)(cc.b * VT_BLOCK + row) * STEP + cc.h * VQ + part * 16;   // 16 cells
+                *reinterpret_cast<uint4*>(v.ent + cc.m * v.pitch + ent_pos(i16)) = eb4[q];
             }
             __syncwarp();                // the buffer is refilled at the next stage
         }

@@ -91,9 +91,11 @@ struct dvl_ctx {
     ValueTableArgs vt{};
     bool vt_valid = false;
     std::vector<float> vt_dom;
-    // per-cell TF entries (M x pitch bytes) for the domains ent_dom and T = ent_T
+    // per-cell TF entries (M x pitch bytes at positions ent_pos) for the
+    // domains ent_dom and T = ent_T, then a row of the levels at the same
+    // positions (entlev_valid: written for the current data set)
     uint8_t* d_ent = nullptr;
-    bool ent_valid = false;
+    bool ent_valid = false, entlev_valid = false;
     std::vector<float> ent_dom;
     uint32_t ent_T = 0;
     int use_ent = 1;
@@ -221,6 +223,7 @@ void free_dataset(dvl_ctx* c)
     c->vt_valid = false;
     dfree(c->d_ent);
     c->ent_valid = false;
+    c->entlev_valid = false;
     free_batch(c);
     c->state = 0;
     c->have_update = false;
@@ -346,6 +349,7 @@ int gather_values(dvl_ctx* c, const uint8_t* lin, uint8_t* lout)
     }
     c->vt_valid = false;
     c->ent_valid = false;
+    c->entlev_valid = false;
     return DVL_OK;
 }
 
@@ -589,6 +593,7 @@ int dvl_build_order(dvl_ctx* c, int sfc)
         CK(dalloc(v.seg, M * std::max<uint64_t>(value_table_segments(v.n_blocks), 1)), "alloc value tables");
         c->vt_valid = false;
         c->ent_valid = false;
+        c->entlev_valid = false;
     }
     int rc = take_device_error(c);
     if (rc) return rc;
@@ -847,6 +852,7 @@ static UpdateArgs make_args(dvl_ctx* c, const dvl_params& p)
     a.vt_build = 0;
     a.ent = nullptr;
     a.ent_build = 0;
+    a.ent_lev_build = 0;
     a.H = c->d_H;
     a.S = c->d_S;
     a.psum = c->d_psum;
@@ -892,7 +898,7 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
     const bool use_ent = c->use_ent && c->T <= 256 && c->n > 0;
     bool build_ent = false;
     if (use_ent) {
-        if (!c->d_ent) CK(dalloc(c->d_ent, (size_t)c->M * c->pitch), "alloc TF entries");
+        if (!c->d_ent) CK(dalloc(c->d_ent, (size_t)(c->M + 1) * c->pitch), "alloc TF entries");
         build_ent = !c->ent_valid || c->ent_T != c->T || c->ent_dom.size() != c->h_dom.size() ||
                     std::memcmp(c->ent_dom.data(), c->h_dom.data(), c->h_dom.size() * sizeof(float)) != 0;
     }
@@ -906,6 +912,7 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
     c->vt.ent = fuse_ent ? c->d_ent : nullptr;
     c->vt.T = c->T;
     a.ent_build = build_ent && !fuse_ent ? 1 : 0;
+    a.ent_lev_build = use_ent && !c->entlev_valid ? 1 : 0;
     if (p->want_alpha) {
         a.asum = c->d_asum;
         a.amean = c->d_amean;
@@ -932,6 +939,7 @@ int dvl_update(dvl_ctx* c, const dvl_params* p)
         c->ent_T = c->T;
         ++c->ent_gen;
     }
+    if (use_ent) c->entlev_valid = true;
     c->last_ent = use_ent;
     c->last_ent_gen = c->ent_gen;
     c->fault_no_publish = 0;
@@ -1465,7 +1473,7 @@ int dvl_update_batch(dvl_ctx* c, const float* alphas, uint32_t K, uint32_t T, in
     const bool use_ent = c->use_ent && T <= 256 && c->n > 0;
     bool build_ent = false;
     if (use_ent) {
-        if (!c->d_ent) CK(dalloc(c->d_ent, (size_t)c->M * c->pitch), "alloc TF entries");
+        if (!c->d_ent) CK(dalloc(c->d_ent, (size_t)(c->M + 1) * c->pitch), "alloc TF entries");
         build_ent = !c->ent_valid || c->ent_T != T || c->ent_dom.size() != dom.size() ||
                     std::memcmp(c->ent_dom.data(), dom.data(), dom.size() * sizeof(float)) != 0;
         a.ent = c->d_ent;

@@ -22,6 +22,21 @@ constexpr int STEPS = CHUNK / STEP;
 constexpr int TILE = WARPS * CHUNK;       // 16384 cells
 constexpr int PAD = 2048;                 // field/level arrays padded to a chunk
 
+// Position of cell i in the per-cell TF entry rows.  Each chunk of CHUNK
+// cells is kept piece-major: its STEPS warp steps of STEP cells are cut into
+// 4 pieces of 32 cells, and piece p of every step is stored before piece
+// p + 1 of any (position p * 32 * STEPS + s * 32 + j for cell s * STEP +
+// p * 32 + j of the chunk).  A run of 512 positions then holds one piece of
+// each of the chunk's 16 steps, so a warp reading 16 bytes a lane sees the
+// same step in lanes 2 s and 2 s + 1 from one such run to the next, while a
+// step's cells still fill whole 32-byte sectors.  Pieces of 32 cells (and so
+// every aligned group of 4 or 16) stay contiguous.
+__host__ __device__ __forceinline__ uint64_t ent_pos(uint64_t i)
+{
+    static_assert(CHUNK == 2048 && STEP == 128, "entry layout: 16 steps of 4 pieces a chunk");
+    return (i & ~(uint64_t)(CHUNK - 1)) | ((i >> 5) & 3u) << 9 | ((i >> 7) & 15u) << 5 | (i & 31u);
+}
+
 // ---- radix sort geometry ---------------------------------------------------
 constexpr int RS_THREADS = 256;
 constexpr int RS_KPT = 16;                // keys per thread
@@ -190,13 +205,15 @@ struct UpdateArgs {
     const ValueTableArgs* vt;
     int vt_build;              // rebuild the value tables after k_prepare
     // Per-cell TF entries for the current TF domains and T <= 256, M rows of
-    // pitch bytes in curve order: entry m of cell c = min(floor(t T), T - 1)
-    // (the alpha-table index of Sec. 3.3's normalised value).  They depend on
-    // the data, the domains and T only, so pass A streams them (M + 1 bytes a
-    // cell with the levels) instead of the field values.  Null: pass A reads
-    // the fields.
+    // pitch bytes at positions ent_pos(c): entry m of cell c = min(floor(t T),
+    // T - 1) (the alpha-table index of Sec. 3.3's normalised value), and in
+    // row M the cells' levels at the same positions.  They depend on the data,
+    // the domains and T only (the level row on the data only), so pass A
+    // streams them (M + 1 bytes a cell) instead of the field values.  Null:
+    // pass A reads the fields.
     uint8_t* ent;
     int ent_build;             // rebuild the entries after k_prepare
+    int ent_lev_build;         // rewrite the level row (new data set)
     unsigned long long* H;
     uint8_t* S;
     ulonglong2* psum;          // boundary partial sums (see QueryArgs)

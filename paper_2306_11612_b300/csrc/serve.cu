@@ -156,7 +156,8 @@ int sfail(dvl_server* s, int code, const char* fmt, ...)
 // Estimated device bytes of one resident data set: input and sorted fields,
 // levels, order and sort scratch, the value tables (prefix sums within and
 // over blocks of steps, per-step and in-block min/max, the blocks' sparse
-// table), the per-cell TF entries and the single-update scan state.
+// table), the per-cell TF entries with their level row and the single-update
+// scan state.
 uint64_t resident_bytes(uint64_t n, uint32_t M)
 {
     const uint64_t pad = (n + PAD - 1) / PAD * PAD;
@@ -165,7 +166,7 @@ uint64_t resident_bytes(uint64_t n, uint32_t M)
     const uint64_t tables = (uint64_t)M * ((steps + 1) * 16 + (blocks + 1) * 16 + steps * 3 * 8 +
                                            (uint64_t)value_table_levels(blocks) * blocks * 8 +
                                            value_table_segments(blocks) * 16);
-    return pad * (9ull * M + 1) + n * (4 + 8 + 8 + 4) + tables + tiles * 8 + chunks * 8 + chunks * STEPS * 8;
+    return pad * (9ull * M + 2) + n * (4 + 8 + 8 + 4) + tables + tiles * 8 + chunks * 8 + chunks * STEPS * 8;
 }
 
 // Estimated batch-buffer bytes per TF slot (one pair of width W per slot).

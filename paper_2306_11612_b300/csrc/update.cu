@@ -197,9 +197,10 @@ __device__ __forceinline__ unsigned long long widths4_ent(const Cell<M, PM>& cc,
 
 // The TF entries of every cell for the current domains (k_prepare's lo and
 // s), T <= 256: the same entry as the width paths read, min(floor(t T), T),
-// with entry T (a copy of T - 1 in the tables) stored as T - 1.  Four cells
-// per thread; the rows' padding past the last cell is read and written too
-// (its entries are never used).
+// with entry T (a copy of T - 1 in the tables) stored as T - 1, at the
+// cells' entry positions (ent_pos).  Four cells per thread; the rows'
+// padding past the last cell is read and written too (its entries are never
+// used).
 template <int M>
 __global__ __launch_bounds__(256) void k_entries(UpdateArgs a)
 {
@@ -219,9 +220,19 @@ __global__ __launch_bounds__(256) void k_entries(UpdateArgs a)
                 const uint32_t e = floor_small(__fmul_rn(norm_t(c[j], lo, sc), Tf));
                 packed |= (e < Tm1 ? e : Tm1) << (8 * j);
             }
-            reinterpret_cast<uint32_t*>(a.ent + m * a.pitch)[i] = packed;
+            *reinterpret_cast<uint32_t*>(a.ent + m * a.pitch + ent_pos(4 * i)) = packed;
         }
     }
+}
+
+// Row M of the entries: the cells' levels at their entry positions (once per
+// data set).  16 cells per thread, padding included.
+__global__ __launch_bounds__(256) void k_ent_levels(UpdateArgs a)
+{
+    const uint64_t n16 = (a.n + 15) / 16;
+    uint8_t* row = a.ent + (uint64_t)a.M * a.pitch;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n16; i += (uint64_t)gridDim.x * blockDim.x)
+        *reinterpret_cast<uint4*>(row + ent_pos(16 * i)) = __ldg(reinterpret_cast<const uint4*>(a.lev) + i);
 }
 
 // One warp of a pass-A CTA, with the tile's chunk totals in lanes 0..7: chunk
@@ -383,10 +394,11 @@ constexpr uint32_t RING_WAIT_POLLS = 4096;      // mbarrier polls (<= 1 ms each)
 // lane M the levels, lane 0 arms the barrier with the step's byte count (a
 // copy may complete first: the phase cannot end before that arrival).  Called
 // by the whole warp after every lane has finished reading the slot.
-// EN: the field rows are the cells' TF entries (STEP bytes each) instead of
-// their values (4 STEP bytes).
-// With EN a slot holds EN_UNIT cells (4 warp steps): M entry rows and the
-// level row of EN_UNIT bytes each.
+// EN: the field rows are the cells' TF entries instead of their values, and
+// the level row is the entries' row M (both at the entry positions ent_pos).
+// With EN a slot holds EN_UNIT positions (one 32-cell piece of each of a
+// chunk's 16 warp steps): M entry rows and the level row of EN_UNIT bytes
+// each.
 constexpr int EN_UNIT = 4 * STEP;
 template <int M, bool EN>
 __device__ __forceinline__ void ring_issue(int lane, uint32_t slot, uint32_t bar, const UpdateArgs& a, uint64_t idx)
@@ -395,9 +407,10 @@ __device__ __forceinline__ void ring_issue(int lane, uint32_t slot, uint32_t bar
     if (lane <= M) {
         proxy_fence_shared();          // the warp's reads of the slot before the copy's writes
         if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(M * ROW + LROW));
-        if (lane < M) {
-            if (EN) bulk_g2s(slot + (uint32_t)lane * ROW, a.ent + lane * a.pitch + idx, ROW, bar);
-            else bulk_g2s(slot + (uint32_t)lane * ROW, a.val + lane * a.pitch + idx, ROW, bar);
+        if (EN) {
+            bulk_g2s(slot + (uint32_t)lane * ROW, a.ent + lane * a.pitch + idx, ROW, bar);   // row M: the levels
+        } else if (lane < M) {
+            bulk_g2s(slot + (uint32_t)lane * ROW, a.val + lane * a.pitch + idx, ROW, bar);
         } else {
             bulk_g2s(slot + (uint32_t)(M * ROW), a.lev + idx, LROW, bar);
         }
@@ -524,11 +537,10 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
                     }
                 }
                 if constexpr (EN) {
-                    // lane l holds cells 16 l .. 16 l + 15 of the slot: lanes
-                    // 8 g .. 8 g + 7 make up warp step 4 st + g
-                    unsigned long long l = 0, ax64[M];
-#pragma unroll
-                    for (int m = 0; m < M; ++m) ax64[m] = 0;
+                    // the slot holds piece st of every step of the chunk
+                    // (ent_pos): lane l has 16 cells of step l >> 1, the same
+                    // step in every slot, so its sums run over the chunk and
+                    // meet their other half (lane l ^ 1) at its end
 #pragma unroll
                     for (int w = 0; w < 4; ++w) {
                         uint32_t E[M], ax[M];
@@ -538,27 +550,10 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
                             ax[m] = 0;
                         }
                         const uint32_t L = w == 0 ? LV.x : w == 1 ? LV.y : w == 2 ? LV.z : LV.w;
-                        l += widths4_ent<M, PM, AL>(cc, E, L, tb, aoff, ax, four, w23);
+                        acc += widths4_ent<M, PM, AL>(cc, E, L, tb, aoff, ax, four, w23);
                         if (AL) {
 #pragma unroll
-                            for (int m = 0; m < M; ++m) ax64[m] += ax[m];
-                        }
-                    }
-                    // step totals: sums over the lane groups of 8; lane st'
-                    // (of steps 4 st .. 4 st + 3) keeps step st''s total
-#pragma unroll
-                    for (int o = 1; o < 8; o <<= 1) l += __shfl_xor_sync(FULL, l, o);
-                    const unsigned long long tot = __shfl_sync(FULL, l, 8 * (lane & 3));
-                    if ((lane >> 2) == st) mine = tot;
-                    acc += l;                 // the lane group's steps; groups combined at the chunk's end
-                    if (AL) {
-#pragma unroll
-                        for (int m = 0; m < M; ++m) {
-                            unsigned long long t = ax64[m];
-#pragma unroll
-                            for (int o = 1; o < 8; o <<= 1) t += __shfl_xor_sync(FULL, t, o);
-                            t = __shfl_sync(FULL, t, 8 * (lane & 3));
-                            if ((lane >> 2) == st) amine[m] = t;
+                            for (int m = 0; m < M; ++m) amine[m] += ax[m];
                         }
                     }
                 } else {
@@ -575,8 +570,21 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
                 if (++k == D) { k = 0; phase ^= 1u; }
             }
             if constexpr (EN) {
-                acc += __shfl_xor_sync(FULL, acc, 8);     // the 4 lane groups' sums: the chunk total
-                acc += __shfl_xor_sync(FULL, acc, 16);
+                if (!late) {
+                    // step totals (both halves of a step; lane s < 16 keeps
+                    // step s), then the chunk total
+                    acc += __shfl_xor_sync(FULL, acc, 1);
+                    mine = __shfl_sync(FULL, acc, (2 * lane) & 31);
+                    if (AL) {
+#pragma unroll
+                        for (int m = 0; m < M; ++m) {
+                            amine[m] += __shfl_xor_sync(FULL, amine[m], 1);
+                            amine[m] = __shfl_sync(FULL, amine[m], (2 * lane) & 31);
+                        }
+                    }
+#pragma unroll
+                    for (int o = 2; o < 32; o <<= 1) acc += __shfl_xor_sync(FULL, acc, o);
+                }
             }
         } else {
             if (nxt_full) {
@@ -1281,7 +1289,9 @@ __global__ __launch_bounds__(WARPS * 32, 3) void k_backward_hist(UpdateArgs a, c
         auto load_step = [&](int st) {
 #pragma unroll
             for (int m = 0; m < M; ++m) {
-                if (ENT) en[m] = __ldg(reinterpret_cast<const uint32_t*>(a.ent + m * a.pitch + base + st * STEP + lane * 4));
+                if (ENT)
+                    en[m] = __ldg(reinterpret_cast<const uint32_t*>(a.ent + m * a.pitch +
+                                                                    ent_pos(base + st * STEP + lane * 4)));
                 else xn[m] = __ldg(reinterpret_cast<const float4*>(a.val + m * a.pitch + base + st * STEP + lane * 4));
             }
         };
@@ -1579,6 +1589,7 @@ cudaError_t run_update(cudaStream_t s, const UpdateArgs& a)
         if ((e = launch_value_tables(s, a.M, *a.vt)) != cudaSuccess) return e;
     }
     if (a.ent && a.ent_build && a.n > 0) k_entries<M><<<grid_cap((a.n + 3) / 4, 256), 256, 0, s>>>(a);
+    if (a.ent && a.ent_lev_build && a.n > 0) k_ent_levels<<<grid_cap((a.n + 15) / 16, 256), 256, 0, s>>>(a);
     e = a.prm.P == 1.0f ? run_passes<M, POW_ONE>(s, a, n_tiles, smem) : run_passes<M, POW_GEN>(s, a, n_tiles, smem);
     if (e != cudaSuccess) return e;
     if (a.vt && a.n > 0) {
