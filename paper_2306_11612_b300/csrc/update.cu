@@ -396,14 +396,14 @@ constexpr uint32_t RING_WAIT_POLLS = 4096;      // mbarrier polls (<= 1 ms each)
 // by the whole warp after every lane has finished reading the slot.
 // EN: the field rows are the cells' TF entries instead of their values, and
 // the level row is the entries' row M (both at the entry positions ent_pos).
-// With EN a slot holds EN_UNIT positions (one 32-cell piece of each of a
-// chunk's 16 warp steps): M entry rows and the level row of EN_UNIT bytes
-// each.
-constexpr int EN_UNIT = 4 * STEP;
-template <int M, bool EN>
+// With EN > 0 a slot holds EN runs of 512 entry positions (each one 32-cell
+// piece of every warp step of a chunk): M entry rows and the level row of
+// en_unit(EN) bytes each.
+__host__ __device__ constexpr int en_unit(int EN) { return EN * 4 * STEP; }
+template <int M, int EN>
 __device__ __forceinline__ void ring_issue(int lane, uint32_t slot, uint32_t bar, const UpdateArgs& a, uint64_t idx)
 {
-    constexpr uint32_t ROW = EN ? EN_UNIT : STEP * 4, LROW = EN ? EN_UNIT : STEP;
+    constexpr uint32_t ROW = EN ? en_unit(EN) : STEP * 4, LROW = EN ? en_unit(EN) : STEP;
     if (lane <= M) {
         proxy_fence_shared();          // the warp's reads of the slot before the copy's writes
         if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(M * ROW + LROW));
@@ -423,10 +423,11 @@ __device__ __forceinline__ void ring_issue(int lane, uint32_t slot, uint32_t bar
 // and their u32 twins (aoff = half of it).
 // EN: whole steps stream the cells' TF entries (a.ent) instead of their
 // field values, M + 1 bytes a cell (partial chunks still read the fields).
-template <int M, int PM, bool P2, int D, int MINB, bool AL = false, bool EN = false>
+template <int M, int PM, bool P2, int D, int MINB, bool AL = false, int EN = 0>
 __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, uint64_t n_chunks, uint32_t tf_bytes)
 {
     extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int EN_UNIT = en_unit(EN), EN_H = EN > 0 ? EN : 1;
     constexpr uint32_t SLOT = EN ? (M + 1) * EN_UNIT : M * STEP * 4 + STEP;
     constexpr int UNIT = EN ? EN_UNIT : STEP, UNITS = CHUNK / UNIT;   // cells per slot, slots per chunk
     float* s_tf = reinterpret_cast<float*>(smem);
@@ -510,12 +511,16 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
                 }
                 --inflight;
                 float v[4][M];
-                uint4 W4[M], LV;                // EN: the lane's 16 cells (one byte each)
+                uint4 W4[EN_H][M], LV[EN_H];    // EN: the lane's 16 cells of each half (one byte each)
                 uint32_t L4 = 0;
                 if constexpr (EN) {
 #pragma unroll
-                    for (int m = 0; m < M; ++m) W4[m] = reinterpret_cast<const uint4*>(ring + k * SLOT + m * EN_UNIT)[lane];
-                    LV = reinterpret_cast<const uint4*>(ring + k * SLOT + M * EN_UNIT)[lane];
+                    for (int h = 0; h < EN_H; ++h) {
+#pragma unroll
+                        for (int m = 0; m < M; ++m)
+                            W4[h][m] = reinterpret_cast<const uint4*>(ring + k * SLOT + m * EN_UNIT + h * 512)[lane];
+                        LV[h] = reinterpret_cast<const uint4*>(ring + k * SLOT + M * EN_UNIT + h * 512)[lane];
+                    }
                 } else {
                     const float4* f4 = reinterpret_cast<const float4*>(ring + k * SLOT);
 #pragma unroll
@@ -537,19 +542,22 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
                     }
                 }
                 if constexpr (EN) {
-                    // the slot holds piece st of every step of the chunk
-                    // (ent_pos): lane l has 16 cells of step l >> 1, the same
-                    // step in every slot, so its sums run over the chunk and
-                    // meet their other half (lane l ^ 1) at its end
+                    // each 512-position run of the slot holds one piece of
+                    // every step of the chunk (ent_pos): lane l has 16 cells
+                    // of step l >> 1 in each, the same step in every slot, so
+                    // its sums run over the chunk and meet their other half
+                    // (lane l ^ 1) at its end
 #pragma unroll
-                    for (int w = 0; w < 4; ++w) {
+                    for (int w = 0; w < 4 * EN_H; ++w) {
                         uint32_t E[M], ax[M];
+                        const int h = w >> 2, c = w & 3;
 #pragma unroll
                         for (int m = 0; m < M; ++m) {
-                            E[m] = w == 0 ? W4[m].x : w == 1 ? W4[m].y : w == 2 ? W4[m].z : W4[m].w;
+                            const uint4& q = W4[h][m];
+                            E[m] = c == 0 ? q.x : c == 1 ? q.y : c == 2 ? q.z : q.w;
                             ax[m] = 0;
                         }
-                        const uint32_t L = w == 0 ? LV.x : w == 1 ? LV.y : w == 2 ? LV.z : LV.w;
+                        const uint32_t L = c == 0 ? LV[h].x : c == 1 ? LV[h].y : c == 2 ? LV[h].z : LV[h].w;
                         acc += widths4_ent<M, PM, AL>(cc, E, L, tb, aoff, ax, four, w23);
                         if (AL) {
 #pragma unroll
@@ -1476,62 +1484,88 @@ int grid_cap(uint64_t work, int threads)
 // and 5 CTAs with a 48-register cap were 0.5-1.5 % slower.)
 template <int M> constexpr int ring_depth() { return 2; }
 template <int M> constexpr int ring_min_blocks() { return M <= 4 ? 4 : 2; }
-// streaming the entries: slots of (M + 1) x 512 bytes, kept 2 deep
+// Streaming the entries: slots of (M + 1) x 512 bytes at 4 CTAs per SM, or,
+// once every warp of the grid has many chunks to take, slots of twice that at
+// 2 CTAs per SM (the per-slot wait, copies and bookkeeping shared by twice the
+// cells: 0.435 -> 0.415 ms on 413.6M cells, but 10 % slower on 20M cells
+// where a warp has only a few chunks); 2 slots deep either way.
 template <int M> constexpr int ring_depth_ent() { return 2; }
+template <int M> constexpr int ring_min_blocks_ent(int EN) { return EN == 1 ? ring_min_blocks<M>() : 2; }
+constexpr uint64_t WIDE_SLOT_CHUNKS_PER_WARP = 16;
 
 template <int M>
-size_t ring_smem(uint32_t T, uint32_t* tf_bytes, bool alpha = false, bool ent = false)
+size_t ring_smem(uint32_t T, uint32_t* tf_bytes, bool alpha = false, int en = 0)
 {
     // the float tables, and with alpha their u32 fixed-point twins
     *tf_bytes = (uint32_t)(((size_t)M * (T + 1) * sizeof(float) + 127) & ~(size_t)127) * (alpha ? 2u : 1u);
-    const size_t slot = ent ? (size_t)(M + 1) * EN_UNIT : (size_t)M * STEP * 4 + STEP;
-    return *tf_bytes + (size_t)WARPS * (ent ? ring_depth_ent<M>() : ring_depth<M>()) * (slot + 8) + 8;
+    const size_t slot = en ? (size_t)(M + 1) * en_unit(en) : (size_t)M * STEP * 4 + STEP;
+    return *tf_bytes + (size_t)WARPS * (en ? ring_depth_ent<M>() : ring_depth<M>()) * (slot + 8) + 8;
 }
 
 // The persistent grid: as many CTAs as are resident at once (the occupancy of
-// the kernel at this shared-memory size, cached per thread for the last key).
+// the kernel at this shared-memory size, cached per thread for the last few
+// keys: an update may ask for two kernels).
 template <typename K>
 cudaError_t resident_ctas(K kernel, size_t smem, int* out)
 {
-    thread_local const void* last_k = nullptr;
-    thread_local size_t last_smem = 0;
-    thread_local int last_dev = -1, last_n = 0;
+    struct Key {
+        const void* k;
+        size_t smem;
+        int dev, n;
+    };
+    constexpr int SLOTS = 4;
+    thread_local Key cache[SLOTS] = {};
+    thread_local int next = 0;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (last_k != (const void*)kernel || last_smem != smem || last_dev != dev) {
-        int per_sm = 0, sms = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, WARPS * 32, smem)) != cudaSuccess)
-            return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        last_k = (const void*)kernel;
-        last_smem = smem;
-        last_dev = dev;
-        last_n = (per_sm > 0 ? per_sm : 1) * sms;
-    }
-    *out = last_n;
+    for (const Key& c : cache)
+        if (c.k == (const void*)kernel && c.smem == smem && c.dev == dev) {
+            *out = c.n;
+            return cudaSuccess;
+        }
+    int per_sm = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, WARPS * 32, smem)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    cache[next] = Key{(const void*)kernel, smem, dev, (per_sm > 0 ? per_sm : 1) * sms};
+    *out = cache[next].n;
+    next = (next + 1) % SLOTS;
     return cudaSuccess;
 }
 
 template <int M, int PM>
 cudaError_t launch_passA_ring(cudaStream_t s, const UpdateArgs& a, uint32_t n_tiles, bool p2)
 {
-    constexpr int D = ring_depth<M>(), MB = ring_min_blocks<M>(), DE = ring_depth_ent<M>();
+    constexpr int D = ring_depth<M>(), MB = ring_min_blocks<M>(), DE = ring_depth_ent<M>(),
+                  MB1 = ring_min_blocks_ent<M>(1), MB2 = ring_min_blocks_ent<M>(2);
     const bool alpha = a.astep != nullptr, ent = a.ent != nullptr;
+    const uint64_t n_chunks = (uint64_t)n_tiles * WARPS;
+    cudaError_t e;
     uint32_t tf_bytes;
-    const size_t smem = ring_smem<M>(a.T, &tf_bytes, alpha, ent);
+    int grid = 0;
+    if (ent && !alpha && p2) {
+        // wide slots when every warp of their grid gets many chunks
+        auto wide = k_passA_ring<M, PM, true, DE, MB2, false, 2>;
+        const size_t smem2 = ring_smem<M>(a.T, &tf_bytes, false, 2);
+        if ((e = smem_attr(wide, smem2)) != cudaSuccess) return e;
+        if ((e = resident_ctas(wide, smem2, &grid)) != cudaSuccess) return e;
+        if (n_chunks >= WIDE_SLOT_CHUNKS_PER_WARP * (uint64_t)grid * WARPS) {
+            wide<<<grid, WARPS * 32, smem2, s>>>(a, n_chunks, tf_bytes);
+            const uint32_t blocks = (uint32_t)((n_chunks + SCAN_SPAN - 1) / SCAN_SPAN);
+            k_chunk_scan<<<blocks, SCAN_THREADS, 0, s>>>(a, n_chunks, a.tile_status);
+            return cudaSuccess;
+        }
+    }
+    const size_t smem = ring_smem<M>(a.T, &tf_bytes, alpha, ent ? 1 : 0);
     // (p2 also selects the partial chunks' entry computation in the entry-streaming kernels)
     auto kernel =
-        ent ? (alpha ? (p2 ? k_passA_ring<M, PM, true, DE, MB, true, true> : k_passA_ring<M, PM, false, DE, MB, true, true>)
-                     : (p2 ? k_passA_ring<M, PM, true, DE, MB, false, true> : k_passA_ring<M, PM, false, DE, MB, false, true>))
+        ent ? (alpha ? (p2 ? k_passA_ring<M, PM, true, DE, MB1, true, 1> : k_passA_ring<M, PM, false, DE, MB1, true, 1>)
+                     : (p2 ? k_passA_ring<M, PM, true, DE, MB1, false, 1> : k_passA_ring<M, PM, false, DE, MB1, false, 1>))
             : alpha ? (p2 ? k_passA_ring<M, PM, true, D, MB, true> : k_passA_ring<M, PM, false, D, MB, true>)
                     : (p2 ? k_passA_ring<M, PM, true, D, MB> : k_passA_ring<M, PM, false, D, MB>);
-    cudaError_t e;
     if ((e = smem_attr(kernel, smem)) != cudaSuccess) return e;
-    int grid = 0;
     if ((e = resident_ctas(kernel, smem, &grid)) != cudaSuccess) return e;
     if ((uint32_t)grid > n_tiles) grid = (int)n_tiles;
-    const uint64_t n_chunks = (uint64_t)n_tiles * WARPS;
     kernel<<<grid, WARPS * 32, smem, s>>>(a, n_chunks, tf_bytes);
     // the scan's block states use the (here unused) tile status words
     const uint32_t blocks = (uint32_t)((n_chunks + SCAN_SPAN - 1) / SCAN_SPAN);
@@ -1695,8 +1729,9 @@ cudaError_t preload_m()
     touch((const void*)k_passA_ring<M, POW_ONE, true, ring_depth<M>(), ring_min_blocks<M>()>);
     touch((const void*)k_passA_ring<M, POW_GEN, true, ring_depth<M>(), ring_min_blocks<M>()>);
     touch((const void*)k_passA_ring<M, POW_ONE, true, ring_depth<M>(), ring_min_blocks<M>(), true>);
-    touch((const void*)k_passA_ring<M, POW_ONE, true, ring_depth_ent<M>(), ring_min_blocks<M>(), false, true>);
-    touch((const void*)k_passA_ring<M, POW_ONE, true, ring_depth_ent<M>(), ring_min_blocks<M>(), true, true>);
+    touch((const void*)k_passA_ring<M, POW_ONE, true, ring_depth_ent<M>(), ring_min_blocks_ent<M>(1), false, 1>);
+    touch((const void*)k_passA_ring<M, POW_ONE, true, ring_depth_ent<M>(), ring_min_blocks_ent<M>(2), false, 2>);
+    touch((const void*)k_passA_ring<M, POW_ONE, true, ring_depth_ent<M>(), ring_min_blocks_ent<M>(1), true, 1>);
     touch((const void*)k_entries<M>);
     return e;
 }
