@@ -388,6 +388,11 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
 // memory directly.  A wait that runs out (bounded polls) stops the warp: it
 // waits once more, bounded, for each copy it still has in flight, raises
 // ERR_TIMEOUT and returns.
+// The chunk scan's blocks (k_chunk_scan): SCAN_SPAN chunks each; the width
+// pass adds each chunk's totals into its block's segment sums (status words
+// of quantity q at status + q * n_blocks, cleared by k_prepare).
+constexpr int SCAN_THREADS = 256, SCAN_PER_THREAD = 2, SCAN_SPAN = SCAN_THREADS * SCAN_PER_THREAD;
+constexpr int SCAN_Q = 1 + DVL_MAX_FIELDS;                 // quantities at most
 constexpr uint32_t RING_WAIT_POLLS = 4096;      // mbarrier polls (<= 1 ms each) before a wait gives up
 
 // Requests warp step idx into a slot: lanes 0..M-1 copy one field row each,
@@ -478,6 +483,7 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
         cm[m] = tb[m] - 4u * BITS_2P23;
     }
     const uint64_t n_steps_all = n_chunks * STEPS;
+    const uint64_t scan_blocks = (n_chunks + SCAN_SPAN - 1) / SCAN_SPAN;
     // 4 and wshift << 23 as values the compiler cannot fold (see width2_ent)
     const uint32_t four = 4u + (a.T >> 31), w23 = (uint32_t)cc.wshift << 23;
 
@@ -620,7 +626,10 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
         }
         if (late) break;
         if (a.step_sums && lane < STEPS) a.step_sums[chunk * STEPS + lane] = mine;
-        if (lane == 0) a.chunk_prefix[chunk] = acc;
+        if (lane == 0) {
+            a.chunk_prefix[chunk] = acc;
+            atomicAdd(a.tile_status + chunk / SCAN_SPAN, acc);          // the scan block's sum
+        }
         if (AL) {
             // per field: the steps' alpha sums as an exclusive prefix within
             // the chunk, and the chunk total
@@ -629,7 +638,10 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
                 const unsigned long long am = lane < STEPS ? amine[m] : 0ull;
                 const unsigned long long incl = warp_incl_scan_u64(am, lane);
                 if (lane < STEPS) a.astep[(uint64_t)m * n_steps_all + chunk * STEPS + lane] = incl - am;
-                if (lane == STEPS - 1) a.achunk[(uint64_t)m * (n_chunks + 1) + chunk] = incl;
+                if (lane == STEPS - 1) {
+                    a.achunk[(uint64_t)m * (n_chunks + 1) + chunk] = incl;
+                    atomicAdd(a.tile_status + (1 + m) * scan_blocks + chunk / SCAN_SPAN, incl);
+                }
             }
         }
         chunk = nxt;
@@ -647,29 +659,23 @@ __global__ __launch_bounds__(WARPS * 32, MINB) void k_passA_ring(UpdateArgs a, u
 }
 
 // The chunk totals (in chunk_prefix) become exclusive prefixes in one launch
-// over blocks of SCAN_SPAN chunks, taken by tickets (counters[1]): a block scans
-// its chunks, publishes its total and looks back over the earlier blocks'
-// (decoupled look-back; all blocks are resident at once, so the chain is
-// short).  The last block also writes F (Eq. 4's total) and the all-zero
-// fallback, as tile_scan does.  With alpha sums (achunk) the block scans each
-// field's chunk alpha sums the same way, warp q running quantity q's
-// look-back (quantity 0: widths, q >= 1: field q - 1's alphas; status words of
-// quantity q at status + q * gridDim.x), and the last block writes each
-// field's alpha total at achunk[m][n_chunks].
-constexpr int SCAN_THREADS = 256, SCAN_PER_THREAD = 2, SCAN_SPAN = SCAN_THREADS * SCAN_PER_THREAD;
-constexpr int SCAN_Q = 1 + DVL_MAX_FIELDS;                 // quantities at most
-
+// over blocks of SCAN_SPAN chunks: the width pass has already summed each
+// block's chunks into its status word, so a block scans its own chunks and
+// adds the sum of the earlier blocks' words (one round of loads; no block
+// waits for another).  The last block also writes F (Eq. 4's total) and the
+// all-zero fallback, as tile_scan does.  With alpha sums (achunk) the block
+// scans each field's chunk alpha sums the same way, warp q summing quantity
+// q's earlier blocks (quantity 0: widths, q >= 1: field q - 1's alphas;
+// status words of quantity q at status + q * gridDim.x), and the last block
+// writes each field's alpha total at achunk[m][n_chunks].
 __global__ __launch_bounds__(SCAN_THREADS) void k_chunk_scan(UpdateArgs a, uint64_t n_chunks,
                                                              unsigned long long* status)
 {
     __shared__ unsigned long long s_warp[SCAN_Q][SCAN_THREADS / 32];
     __shared__ unsigned long long s_excl[SCAN_Q];
-    __shared__ uint32_t s_b;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nq = a.achunk ? 1 + (int)a.M : 1;
-    if (tid == 0) s_b = atomicAdd(&a.counters[1], 1u);
-    __syncthreads();
-    const uint32_t b = s_b;
+    const uint32_t b = blockIdx.x;
     auto row_of = [&](int q) {
         return q == 0 ? a.chunk_prefix : a.achunk + (uint64_t)(q - 1) * (n_chunks + 1);
     };
@@ -701,16 +707,11 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_chunk_scan(UpdateArgs a, uint6
     }
     __syncthreads();
     for (int q = warp; q < nq; q += SCAN_THREADS / 32) {
-        unsigned long long agg = 0;
-#pragma unroll
-        for (int w = 0; w < SCAN_THREADS / 32; ++w) agg += s_warp[q][w];
-        unsigned long long* st = status + (uint64_t)q * gridDim.x;
-        if (lane == 0) st_relaxed(st + b, (b == 0 ? FLAG_P : FLAG_A) | agg);
+        const unsigned long long* st = status + (uint64_t)q * gridDim.x;
         unsigned long long excl = 0;
-        if (b > 0) {
-            excl = look_back(a, st, b, lane);
-            if (lane == 0) st_relaxed(st + b, FLAG_P | (excl + agg));
-        }
+        for (uint32_t i = lane; i < b; i += 32) excl += st[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) excl += __shfl_xor_sync(FULL, excl, o);
         if (lane == 0) s_excl[q] = excl;
     }
     __syncthreads();
