@@ -321,10 +321,11 @@ int dvl_get_timings(dvl_ctx* ctx, double* ms, int n);
  *                           (stages: prepare, pass A, bins, -).
  *   DVL_OPT_ENTRIES         1 (default) = with alpha tables of at most 256
  *                           entries, dvl_update keeps each cell's TF entry per
- *                           field (n_fields bytes a cell, built in the first
- *                           update after a TF-domain, table-size or data
- *                           change, like the value tables) and its width pass
- *                           reads those instead of the field values; 0 = the
+ *                           field and a copy of its level (n_fields + 1 bytes
+ *                           a cell, built in the first update after a
+ *                           TF-domain, table-size or data change, like the
+ *                           value tables) and its width pass reads those
+ *                           instead of the field values; 0 = the
  *                           width pass reads the field values.  The results
  *                           are the same bit for bit. */
 enum { DVL_OPT_SPIN_LIMIT = 1, DVL_OPT_FAULT_NO_PUBLISH = 2, DVL_OPT_TIMING = 3, DVL_OPT_ENTRIES = 4 };
