@@ -1486,13 +1486,15 @@ int grid_cap(uint64_t work, int threads)
 template <int M> constexpr int ring_depth() { return 2; }
 template <int M> constexpr int ring_min_blocks() { return M <= 4 ? 4 : 2; }
 // Streaming the entries: slots of (M + 1) x 512 bytes at 4 CTAs per SM, or,
-// once every warp of the grid has many chunks to take, slots of twice that at
-// 2 CTAs per SM (the per-slot wait, copies and bookkeeping shared by twice the
-// cells: 0.435 -> 0.415 ms on 413.6M cells, but 10 % slower on 20M cells
-// where a warp has only a few chunks); 2 slots deep either way.
+// once every warp of that grid has at least 6 chunks to take, slots of twice
+// that at 2 CTAs per SM (the per-slot wait, copies and bookkeeping shared by
+// twice the cells: 0.435 -> 0.415 ms on 413.6M cells, 85 chunks a warp;
+// 0.060 -> 0.056 ms on 35.8M cells, 7.4 chunks a warp; but 5-10 % slower on
+// 20M cells, 4.1 chunks a warp, where the grid's start and end show); 2
+// slots deep either way.
 template <int M> constexpr int ring_depth_ent() { return 2; }
 template <int M> constexpr int ring_min_blocks_ent(int EN) { return EN == 1 ? ring_min_blocks<M>() : 2; }
-constexpr uint64_t WIDE_SLOT_CHUNKS_PER_WARP = 16;
+constexpr uint64_t WIDE_SLOT_CHUNKS_PER_WARP = 6;
 
 template <int M>
 size_t ring_smem(uint32_t T, uint32_t* tf_bytes, bool alpha = false, int en = 0)
