@@ -6,9 +6,10 @@
 //   k_passA_ring  per cell: TF alpha per field, variation V (Eq. 1),
 //               importance f (Eq. 3), fixed-point width q; width totals per
 //               warp step and per chunk (and, for alpha means, the cells'
-//               fixed-point alpha sums per step and chunk); k_chunk_scan then
-//               gives the exclusive prefix of every chunk and the total F
-//               (Eq. 4).  k_passA: the same with direct loads and a decoupled
+//               fixed-point alpha sums per step and chunk), each chunk's
+//               totals also added into its scan block's sum; k_chunk_scan
+//               then gives the exclusive prefix of every chunk and the total
+//               F (Eq. 4).  k_passA: the same with direct loads and a decoupled
 //               look-back per tile (rows that are not 16-byte aligned).
 //   The bins are range queries over TF-independent value tables (bins.cu).
 //   k_passB     places every cell into the pixels its [E, E+q) span touches
@@ -379,15 +380,18 @@ __global__ __launch_bounds__(WARPS * 32) void k_passA(UpdateArgs a, uint32_t n_t
 // No warp ever waits for another (no tile barrier, no look-back), so the
 // stream of copies never stalls on the scan's chain of tiles.
 //
-// Every warp owns a ring of D slots, one warp step (128 cells: M field rows of
-// 512 B and 128 level bytes) each.  Its lane 0 keeps D steps in flight,
-// refilling a slot as soon as the warp has read it and running on into the
-// warp's next chunk, so a warp's loads never wait on its own arithmetic and
-// the bytes in flight cost no registers.  Step totals come from two warp
-// reductions per step.  Partial chunks (the data set's end) read global
-// memory directly.  A wait that runs out (bounded polls) stops the warp: it
-// waits once more, bounded, for each copy it still has in flight, raises
-// ERR_TIMEOUT and returns.
+// Every warp owns a ring of D slots.  Streaming the field values a slot is
+// one warp step (128 cells: M field rows of 512 B and 128 level bytes) and the
+// step totals come from two warp reductions per step; streaming the per-cell
+// TF entries a slot is one or two 512-position runs of the entry order
+// (ent_pos), each lane stays on one step for the whole chunk, and the totals
+// are reduced once per chunk.  Lanes 0..M keep D slots in flight, refilling a
+// slot as soon as the warp has read it and running on into the warp's next
+// chunk, so a warp's loads never wait on its own arithmetic and the bytes in
+// flight cost no registers.  Partial chunks (the data set's end) read the
+// field values from global memory directly.  A wait that runs out (bounded
+// polls) stops the warp: it waits once more, bounded, for each copy it still
+// has in flight, raises ERR_TIMEOUT and returns.
 // The chunk scan's blocks (k_chunk_scan): SCAN_SPAN chunks each; the width
 // pass adds each chunk's totals into its block's segment sums (status words
 // of quantity q at status + q * n_blocks, cleared by k_prepare).
